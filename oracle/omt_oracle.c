@@ -1,0 +1,495 @@
+/*
+ * omt_oracle.c -- plain, slow FP64 CPU oracle of the box-tracking hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline use it.  It shares no code, header, table or constant with the
+ * CUDA library; it is written straight from the definitions below, in the
+ * order the method states them, with no blocking, fusion or reordering.
+ *
+ * What the paper fixes and what comes from the published methods:
+ *   - Section V-A (preprocessing): the frame is downscaled by a Gaussian
+ *     pyramid.  The paper gives no kernel, so the 5-tap binomial
+ *     [1 4 6 4 1]/16 in each direction (Burt & Adelson) is used, with a
+ *     reflect-101 border, decimation to the even pixels and level sizes
+ *     rounded up: W_L = (W_{L-1} + 1) / 2.
+ *   - Section V-A (feature calculation) + Section IV: the motion between
+ *     I_{t-1} and I_t.  The dense field is replaced by sparse pyramidal
+ *     Lucas-Kanade (Bouguet's formulation) on Shi-Tomasi corners.
+ *   - Section V-A (prediction): each box moves by an aggregate of the motion
+ *     inside it; the paper's aggregate is the mean, the median is the
+ *     default here and the mean is a flag.
+ * Conventions: pixel centres at integer coordinates; a level-L coordinate
+ * is the level-0 coordinate times 2^-L; boxes are (x0, y0, x1, y1) floats,
+ * half-open, in level-0 pixels.
+ *
+ * Pins: every function here is checked by the not-gpu tests against closed
+ * forms, invariants, brute force or library routines (see tests/).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 1
+#define ORC_LOST_EIG 2
+#define ORC_LOST_OOB 4
+#define ORC_NONCONV 8
+
+/* ---------------------------------------------------------------- borders */
+
+/* Reflect-101 index (mirror about the edge pixel, edge not repeated);
+ * folds any offset back into [0, n).  A single-pixel axis maps to 0. */
+static int reflect101(int i, int n)
+{
+    if (n == 1) return 0;
+    int period = 2 * n - 2;
+    i %= period;
+    if (i < 0) i += period;
+    return i < n ? i : period - i;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int orc_reflect101(int i, int n) { return reflect101(i, n); }
+
+/* ---------------------------------------------------------------- pyramid */
+
+/* Size of pyramid level L: each level halves the previous one, rounding up. */
+void orc_level_size(int w, int h, int level, int *lw, int *lh)
+{
+    for (int l = 0; l < level; ++l) { w = (w + 1) >> 1; h = (h + 1) >> 1; }
+    *lw = w; *lh = h;
+}
+
+/* One Gaussian (binomial 5x5) reduce step, Section V-A preprocessing:
+ *   out(X, Y) = sum_{i,j=-2..2} k_i k_j in(r(2X+i), r(2Y+j)) / 256,
+ * k = (1, 4, 6, 4, 1), r = reflect-101.  The full 2-D sum is written out,
+ * term by term, as the definition states it. */
+static void reduce_level(const double *in, int w, int h, double *out, int ow, int oh)
+{
+    static const double k[5] = {1.0, 4.0, 6.0, 4.0, 1.0};
+    for (int Y = 0; Y < oh; ++Y)
+        for (int X = 0; X < ow; ++X) {
+            double s = 0.0;
+            for (int j = -2; j <= 2; ++j)
+                for (int i = -2; i <= 2; ++i) {
+                    int x = reflect101(2 * X + i, w), y = reflect101(2 * Y + j, h);
+                    s += k[i + 2] * k[j + 2] * in[(size_t)y * w + x];
+                }
+            out[(size_t)Y * ow + X] = s / 256.0;
+        }
+}
+
+/* Scharr derivative of one level, in intensity per level pixel:
+ *   Ix(x, y) = sum_{d=-1..1} s_d (I(r(x+1), r(y+d)) - I(r(x-1), r(y+d))) / 32
+ *   Iy(x, y) = sum_{d=-1..1} s_d (I(r(x+d), r(y+1)) - I(r(x+d), r(y-1))) / 32
+ * with s = (3, 10, 3): the central difference [-1 0 1]/2 across, smoothed by
+ * [3 10 3]/16 along the other axis.  grad is interleaved (Ix, Iy). */
+static void scharr_level(const double *I, int w, int h, double *grad)
+{
+    static const double s[3] = {3.0, 10.0, 3.0};
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double gx = 0.0, gy = 0.0;
+            for (int d = -1; d <= 1; ++d) {
+                int yy = reflect101(y + d, h), xx = reflect101(x + d, w);
+                gx += s[d + 1] * (I[(size_t)yy * w + reflect101(x + 1, w)] -
+                                  I[(size_t)yy * w + reflect101(x - 1, w)]);
+                gy += s[d + 1] * (I[(size_t)reflect101(y + 1, h) * w + xx] -
+                                  I[(size_t)reflect101(y - 1, h) * w + xx]);
+            }
+            grad[2 * ((size_t)y * w + x) + 0] = gx / 32.0;
+            grad[2 * ((size_t)y * w + x) + 1] = gy / 32.0;
+        }
+}
+
+/* Number of doubles in the packed image planes of all levels. */
+size_t orc_pyramid_elems(int w, int h, int levels)
+{
+    size_t n = 0;
+    for (int l = 0; l < levels; ++l) { int lw, lh; orc_level_size(w, h, l, &lw, &lh); n += (size_t)lw * lh; }
+    return n;
+}
+
+/* Image pyramid and per-level gradients.
+ * img:  levels planes packed back to back (level 0 = the frame as doubles);
+ * grad: levels planes of interleaved (Ix, Iy), twice img's element count. */
+static void pyramid_from_level0(int w, int h, int levels, double *img, double *grad)
+{
+    size_t off = 0;
+    int lw = w, lh = h;
+    for (int l = 0; l < levels; ++l) {
+        scharr_level(img + off, lw, lh, grad + 2 * off);
+        if (l + 1 < levels) {
+            int nw = (lw + 1) >> 1, nh = (lh + 1) >> 1;
+            reduce_level(img + off, lw, lh, img + off + (size_t)lw * lh, nw, nh);
+            off += (size_t)lw * lh;
+            lw = nw; lh = nh;
+        }
+    }
+}
+
+void orc_pyramid(const uint8_t *frame, int w, int h, long pitch, int levels,
+                 double *img, double *grad)
+{
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) img[(size_t)y * w + x] = frame[(size_t)y * pitch + x];
+    pyramid_from_level0(w, h, levels, img, grad);
+}
+
+/* Same pyramid from an unquantised (real-valued) level 0, for the pins that
+ * need renders free of the u8 rounding. */
+void orc_pyramid_f64(const double *frame, int w, int h, int levels, double *img, double *grad)
+{
+    memcpy(img, frame, sizeof(double) * (size_t)w * h);
+    pyramid_from_level0(w, h, levels, img, grad);
+}
+
+/* ---------------------------------------------------------------- corners */
+
+/* floor(sqrt(D)) by bisection on integers: s*s <= D < (s+1)*(s+1). */
+uint64_t orc_isqrt(uint64_t D)
+{
+    uint64_t lo = 0, hi = 1ull << 32;
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (mid * mid <= D) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* Raw integer Scharr of the u8 frame (32 x the level-0 gradient). */
+void orc_scharr_raw(const uint8_t *f, int w, int h, long pitch, int32_t *gx, int32_t *gy)
+{
+    static const int s[3] = {3, 10, 3};
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int ax = 0, ay = 0;
+            for (int d = -1; d <= 1; ++d) {
+                int yy = reflect101(y + d, h), xx = reflect101(x + d, w);
+                ax += s[d + 1] * ((int)f[(size_t)yy * pitch + reflect101(x + 1, w)] -
+                                  (int)f[(size_t)yy * pitch + reflect101(x - 1, w)]);
+                ay += s[d + 1] * ((int)f[(size_t)reflect101(y + 1, h) * pitch + xx] -
+                                  (int)f[(size_t)reflect101(y - 1, h) * pitch + xx]);
+            }
+            gx[(size_t)y * w + x] = ax;
+            gy[(size_t)y * w + x] = ay;
+        }
+}
+
+/* Shi-Tomasi response in exact integers.  Structure tensor over the 3x3
+ * block around each pixel (gradient sampled with reflect-101):
+ *   a = sum gx^2, b = sum gx gy, c = sum gy^2,
+ * eigenvalues ((a+c) +- sqrt((a-c)^2 + 4 b^2)) / 2, so
+ *   R = (a + c) - isqrt((a - c)^2 + 4 b^2)
+ * lies in [2 lambda_min, 2 lambda_min + 1). */
+void orc_corner_response(const uint8_t *f, int w, int h, long pitch, int64_t *R)
+{
+    int32_t *gx = (int32_t *)malloc(sizeof(int32_t) * (size_t)w * h);
+    int32_t *gy = (int32_t *)malloc(sizeof(int32_t) * (size_t)w * h);
+    orc_scharr_raw(f, w, h, pitch, gx, gy);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int64_t a = 0, b = 0, c = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    size_t q = (size_t)reflect101(y + dy, h) * w + reflect101(x + dx, w);
+                    a += (int64_t)gx[q] * gx[q];
+                    b += (int64_t)gx[q] * gy[q];
+                    c += (int64_t)gy[q] * gy[q];
+                }
+            uint64_t D = (uint64_t)((a - c) * (a - c)) + 4ull * (uint64_t)(b * b);
+            R[(size_t)y * w + x] = (a + c) - (int64_t)orc_isqrt(D);
+        }
+    free(gx);
+    free(gy);
+}
+
+typedef struct { int64_t R; int64_t idx; int x, y; } cand_t;
+
+static int cand_cmp(const void *pa, const void *pb)
+{
+    const cand_t *a = (const cand_t *)pa, *b = (const cand_t *)pb;
+    if (a->R != b->R) return a->R > b->R ? -1 : 1;      /* R descending */
+    return a->idx < b->idx ? -1 : (a->idx > b->idx);     /* raster index ascending */
+}
+
+/* Shi-Tomasi corner selection inside each box, on the u8 frame t.
+ *  1. eligible pixels: x0 <= x < x1, y0 <= y < y1, 1 <= x <= W-2, 1 <= y <= H-2;
+ *  2. R_max = max R over the eligible pixels;
+ *  3. candidates: R > 0, qden * R > qnum * R_max, and R >= R of all 8
+ *     neighbours (which may lie outside the box);
+ *  4. order by (R descending, y*W + x ascending);
+ *  5. greedy: accept a candidate if dx^2 + dy^2 >= fl32(min_dist^2) to every
+ *     point accepted so far; stop at max_corners.
+ * pts: nboxes * max_corners (x, y) pairs; counts: per box.
+ * Returns the number of boxes processed. */
+int orc_select_corners(const uint8_t *f, int w, int h, long pitch, const float *boxes, int nboxes,
+                       int max_corners, int qnum, int qden, float min_dist,
+                       float *pts, int32_t *counts)
+{
+    int64_t *R = (int64_t *)malloc(sizeof(int64_t) * (size_t)w * h);
+    orc_corner_response(f, w, h, pitch, R);
+    float md2f = min_dist * min_dist;       /* threshold taken in FP32 */
+    double md2 = (double)md2f;
+    cand_t *cand = (cand_t *)malloc(sizeof(cand_t) * ((size_t)w * h + 1));
+    int *acc = (int *)malloc(sizeof(int) * 2 * (size_t)(max_corners > 0 ? max_corners : 1));
+    for (int bi = 0; bi < nboxes; ++bi) {
+        double x0 = boxes[4 * bi + 0], y0 = boxes[4 * bi + 1];
+        double x1 = boxes[4 * bi + 2], y1 = boxes[4 * bi + 3];
+        int64_t rmax = 0;
+        for (int y = 1; y <= h - 2; ++y)
+            for (int x = 1; x <= w - 2; ++x)
+                if (x >= x0 && x < x1 && y >= y0 && y < y1 && R[(size_t)y * w + x] > rmax)
+                    rmax = R[(size_t)y * w + x];
+        size_t nc = 0;
+        for (int y = 1; y <= h - 2; ++y)
+            for (int x = 1; x <= w - 2; ++x) {
+                if (!(x >= x0 && x < x1 && y >= y0 && y < y1)) continue;
+                int64_t r = R[(size_t)y * w + x];
+                if (r <= 0 || (int64_t)qden * r <= (int64_t)qnum * rmax) continue;
+                int ismax = 1;
+                for (int dy = -1; dy <= 1 && ismax; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx)
+                        if ((dx || dy) && R[(size_t)(y + dy) * w + (x + dx)] > r) { ismax = 0; break; }
+                if (!ismax) continue;
+                cand[nc].R = r;
+                cand[nc].idx = (int64_t)y * w + x;
+                cand[nc].x = x;
+                cand[nc].y = y;
+                ++nc;
+            }
+        qsort(cand, nc, sizeof(cand_t), cand_cmp);
+        int na = 0;
+        for (size_t c = 0; c < nc && na < max_corners; ++c) {
+            int ok = 1;
+            for (int a = 0; a < na; ++a) {
+                int64_t dx = cand[c].x - acc[2 * a], dy = cand[c].y - acc[2 * a + 1];
+                if ((double)(dx * dx + dy * dy) < md2) { ok = 0; break; }
+            }
+            if (!ok) continue;
+            acc[2 * na] = cand[c].x;
+            acc[2 * na + 1] = cand[c].y;
+            pts[2 * ((size_t)bi * max_corners + na) + 0] = (float)cand[c].x;
+            pts[2 * ((size_t)bi * max_corners + na) + 1] = (float)cand[c].y;
+            ++na;
+        }
+        counts[bi] = na;
+    }
+    free(acc);
+    free(cand);
+    free(R);
+    return nboxes;
+}
+
+/* --------------------------------------------------------------------- LK */
+
+typedef struct { const double *img, *grad; int w, h; } level_t;
+
+/* Bilinear sample of channel k of an ch-channel plane at integer tap
+ * (ix, iy) with fractional weights (a, b); each of the four taps is clamped
+ * to the plane (replicate border). */
+static double bilin(const double *P, int ch, int k, int w, int h, int ix, int iy, double a, double b)
+{
+    int x0 = clampi(ix, 0, w - 1), x1 = clampi(ix + 1, 0, w - 1);
+    int y0 = clampi(iy, 0, h - 1), y1 = clampi(iy + 1, 0, h - 1);
+    return (1.0 - a) * (1.0 - b) * P[((size_t)y0 * w + x0) * ch + k] +
+           a * (1.0 - b) * P[((size_t)y0 * w + x1) * ch + k] +
+           (1.0 - a) * b * P[((size_t)y1 * w + x0) * ch + k] +
+           a * b * P[((size_t)y1 * w + x1) * ch + k];
+}
+
+/* Pyramidal iterative Lucas-Kanade for one point u (Bouguet's scheme):
+ * g = 0 at the top level Lm; for L = Lm..0:
+ *   p = u 2^-L, N = win^2, w = (win - 1) / 2;
+ *   G = sum over the window (i, j) in [-w, w]^2 of [Ix^2 IxIy; IxIy Iy^2],
+ *       I, Ix, Iy sampled bilinearly at p + (i, j) in frame t's level L;
+ *   lost (LOST_EIG) if lambda_min(G)/N < tau or lambda_min <= 0;
+ *   nu = 0; for k = 1..K:
+ *       centre c = p + g + nu; lost (LOST_OOB) if c leaves
+ *       [-w, W_L-1+w] x [-w, H_L-1+w];
+ *       dI = I(p + (i,j)) - J(c + (i,j)), J frame t+1's level L, bilinear;
+ *       b = sum dI (Ix, Iy);  eta = G^{-1} b;  nu += eta;
+ *       stop when eta_x^2 + eta_y^2 < eps^2 (else NONCONV after K);
+ *   g = 2 (g + nu) if L > 0, else d = g + nu.
+ * v = u + d; LOST_OOB if v is outside [0, W-1] x [0, H-1].  A lost point
+ * keeps v = u.  iters (per level) and mineig (lambda_min/N per level, NAN
+ * where not reached) are optional diagnostics. */
+static void lk_point(const level_t *P, const level_t *J, int levels, int win, int max_iter,
+                     double eps, double tau, double ux, double uy,
+                     double *vx, double *vy, uint8_t *status, uint8_t *iters, double *mineig,
+                     double *Ib, double *Ixb, double *Iyb)
+{
+    const int w = (win - 1) / 2;
+    const double N = (double)win * win;
+    double gx = 0.0, gy = 0.0, dx = 0.0, dy = 0.0;
+    int nonconv = 0;
+    uint8_t st = ORC_OK;
+    for (int L = 0; L < levels; ++L) {
+        if (iters) iters[L] = 0;
+        if (mineig) mineig[L] = NAN;
+    }
+    for (int L = levels - 1; L >= 0; --L) {
+        const level_t *pl = &P[L], *jl = &J[L];
+        double sc = ldexp(1.0, -L);
+        double px = ux * sc, py = uy * sc;
+        double fx = floor(px), fy = floor(py);
+        int ix = (int)fx, iy = (int)fy;
+        double a = px - fx, b = py - fy;
+        double Gxx = 0.0, Gxy = 0.0, Gyy = 0.0;
+        int t = 0;
+        for (int j = -w; j <= w; ++j)
+            for (int i = -w; i <= w; ++i, ++t) {
+                Ib[t] = bilin(pl->img, 1, 0, pl->w, pl->h, ix + i, iy + j, a, b);
+                Ixb[t] = bilin(pl->grad, 2, 0, pl->w, pl->h, ix + i, iy + j, a, b);
+                Iyb[t] = bilin(pl->grad, 2, 1, pl->w, pl->h, ix + i, iy + j, a, b);
+                Gxx += Ixb[t] * Ixb[t];
+                Gxy += Ixb[t] * Iyb[t];
+                Gyy += Iyb[t] * Iyb[t];
+            }
+        double lam = 0.5 * ((Gxx + Gyy) - sqrt((Gxx - Gyy) * (Gxx - Gyy) + 4.0 * Gxy * Gxy));
+        if (mineig) mineig[L] = lam / N;
+        if (!(lam / N >= tau) || !(lam > 0.0)) { st = ORC_LOST_EIG; break; }
+        double det = Gxx * Gyy - Gxy * Gxy;
+        double nux = 0.0, nuy = 0.0;
+        int k = 0, conv = 0;
+        while (k < max_iter) {
+            double cx = px + gx + nux, cy = py + gy + nuy;
+            if (cx < -w || cx > pl->w - 1 + w || cy < -w || cy > pl->h - 1 + w) { st = ORC_LOST_OOB; break; }
+            double fcx = floor(cx), fcy = floor(cy);
+            int jx = (int)fcx, jy = (int)fcy;
+            double aj = cx - fcx, bj = cy - fcy;
+            double bx = 0.0, by = 0.0;
+            t = 0;
+            for (int j = -w; j <= w; ++j)
+                for (int i = -w; i <= w; ++i, ++t) {
+                    double dI = Ib[t] - bilin(jl->img, 1, 0, jl->w, jl->h, jx + i, jy + j, aj, bj);
+                    bx += dI * Ixb[t];
+                    by += dI * Iyb[t];
+                }
+            double ex = (Gyy * bx - Gxy * by) / det;
+            double ey = (Gxx * by - Gxy * bx) / det;
+            nux += ex;
+            nuy += ey;
+            ++k;
+            if (ex * ex + ey * ey < eps * eps) { conv = 1; break; }
+        }
+        if (iters) iters[L] = (uint8_t)k;
+        if (st != ORC_OK) break;
+        if (!conv) nonconv = 1;
+        if (L > 0) { gx = 2.0 * (gx + nux); gy = 2.0 * (gy + nuy); }
+        else { dx = gx + nux; dy = gy + nuy; }
+    }
+    if (st == ORC_OK) {
+        double ox = ux + dx, oy = uy + dy;
+        if (ox < 0.0 || ox > P[0].w - 1 || oy < 0.0 || oy > P[0].h - 1) st = ORC_LOST_OOB;
+        else { *vx = ox; *vy = oy; }
+    }
+    if (st != ORC_OK) { *vx = ux; *vy = uy; }
+    else if (nonconv) st |= ORC_NONCONV;
+    *status = st;
+}
+
+/* Track n points from frame t (prev) to frame t+1 (next).  Pyramids are
+ * given as orc_pyramid() output for each frame.  pts_out is (x, y) doubles;
+ * iters is n*levels (level index L), mineig n*levels; both nullable.
+ * nthreads <= 0 uses the OpenMP default. */
+void orc_lk_track(const double *prev_img, const double *prev_grad,
+                  const double *next_img, const double *next_grad,
+                  int w, int h, int levels, const float *pts, int n,
+                  int win, int max_iter, double eps, double tau,
+                  double *pts_out, uint8_t *status, uint8_t *iters, double *mineig, int nthreads)
+{
+    level_t P[16], J[16];
+    size_t off = 0;
+    for (int l = 0; l < levels; ++l) {
+        int lw, lh;
+        orc_level_size(w, h, l, &lw, &lh);
+        P[l].img = prev_img + off; P[l].grad = prev_grad + 2 * off; P[l].w = lw; P[l].h = lh;
+        J[l].img = next_img + off; J[l].grad = next_grad + 2 * off; J[l].w = lw; J[l].h = lh;
+        off += (size_t)lw * lh;
+    }
+    int nwin = win * win;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        double *buf = (double *)malloc(sizeof(double) * 3 * (size_t)nwin);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int i = 0; i < n; ++i)
+            lk_point(P, J, levels, win, max_iter, eps, tau, pts[2 * i], pts[2 * i + 1],
+                     &pts_out[2 * i], &pts_out[2 * i + 1], &status[i],
+                     iters ? iters + (size_t)i * levels : NULL,
+                     mineig ? mineig + (size_t)i * levels : NULL,
+                     buf, buf + nwin, buf + 2 * nwin);
+        free(buf);
+    }
+}
+
+/* ------------------------------------------------------------- box update */
+
+static int dbl_cmp(const void *pa, const void *pb)
+{
+    double a = *(const double *)pa, b = *(const double *)pb;
+    return a < b ? -1 : (a > b);
+}
+
+/* Section V-A prediction: each box moves by an aggregate of the displacements
+ * of its tracked (OK) points; the size is kept.  aggregator 0 = median of dx
+ * and of dy separately (even count: mean of the two middle values), 1 = mean
+ * (the paper's choice).  offsets is the CSR of points per box (nboxes + 1).
+ * A box with no OK point stays where it is and gets nvalid = 0. */
+void orc_update_boxes(const float *boxes, const int32_t *offsets, const float *pts,
+                      const float *pts_out, const uint8_t *status, int nboxes, int aggregator,
+                      double *boxes_out, int32_t *nvalid)
+{
+    for (int bi = 0; bi < nboxes; ++bi) {
+        int lo = offsets[bi], hi = offsets[bi + 1];
+        int cap = hi > lo ? hi - lo : 1;
+        double *dx = (double *)malloc(sizeof(double) * cap);
+        double *dy = (double *)malloc(sizeof(double) * cap);
+        int m = 0;
+        for (int i = lo; i < hi; ++i)
+            if (status[i] & ORC_OK) {
+                dx[m] = (double)pts_out[2 * i] - (double)pts[2 * i];
+                dy[m] = (double)pts_out[2 * i + 1] - (double)pts[2 * i + 1];
+                ++m;
+            }
+        double mx = 0.0, my = 0.0;
+        if (m > 0) {
+            if (aggregator == 1) {
+                for (int i = 0; i < m; ++i) { mx += dx[i]; my += dy[i]; }
+                mx /= m;
+                my /= m;
+            } else {
+                qsort(dx, m, sizeof(double), dbl_cmp);
+                qsort(dy, m, sizeof(double), dbl_cmp);
+                if (m & 1) { mx = dx[m / 2]; my = dy[m / 2]; }
+                else { mx = 0.5 * (dx[m / 2 - 1] + dx[m / 2]); my = 0.5 * (dy[m / 2 - 1] + dy[m / 2]); }
+            }
+        }
+        boxes_out[4 * bi + 0] = boxes[4 * bi + 0] + mx;
+        boxes_out[4 * bi + 1] = boxes[4 * bi + 1] + my;
+        boxes_out[4 * bi + 2] = boxes[4 * bi + 2] + mx;
+        boxes_out[4 * bi + 3] = boxes[4 * bi + 3] + my;
+        nvalid[bi] = m;
+        free(dx);
+        free(dy);
+    }
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

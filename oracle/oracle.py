@@ -1,0 +1,182 @@
+"""ctypes wrapper of the FP64 CPU oracle (omt_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU baseline, never by the product path.  It builds
+``liboracle.so`` next to this file with gcc on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from ctypes import POINTER, c_double, c_float, c_int, c_int32, c_int64, c_long, c_size_t, c_uint8, c_uint64
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "omt_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+OK, LOST_EIG, LOST_OOB, NONCONV = 1, 2, 4, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (plain C, -O2, OpenMP) if missing or stale."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                               "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        L.orc_reflect101.argtypes = [c_int, c_int]
+        L.orc_reflect101.restype = c_int
+        L.orc_level_size.argtypes = [c_int, c_int, c_int, POINTER(c_int), POINTER(c_int)]
+        L.orc_pyramid_elems.argtypes = [c_int, c_int, c_int]
+        L.orc_pyramid_elems.restype = c_size_t
+        L.orc_pyramid.argtypes = [POINTER(c_uint8), c_int, c_int, c_long, c_int,
+                                  POINTER(c_double), POINTER(c_double)]
+        L.orc_pyramid_f64.argtypes = [POINTER(c_double), c_int, c_int, c_int,
+                                      POINTER(c_double), POINTER(c_double)]
+        L.orc_isqrt.argtypes = [c_uint64]
+        L.orc_isqrt.restype = c_uint64
+        L.orc_scharr_raw.argtypes = [POINTER(c_uint8), c_int, c_int, c_long,
+                                     POINTER(c_int32), POINTER(c_int32)]
+        L.orc_corner_response.argtypes = [POINTER(c_uint8), c_int, c_int, c_long, POINTER(c_int64)]
+        L.orc_select_corners.argtypes = [POINTER(c_uint8), c_int, c_int, c_long, POINTER(c_float), c_int,
+                                         c_int, c_int, c_int, c_float, POINTER(c_float), POINTER(c_int32)]
+        L.orc_select_corners.restype = c_int
+        L.orc_lk_track.argtypes = [POINTER(c_double)] * 4 + [
+            c_int, c_int, c_int, POINTER(c_float), c_int, c_int, c_int, c_double, c_double,
+            POINTER(c_double), POINTER(c_uint8), POINTER(c_uint8), POINTER(c_double), c_int]
+        L.orc_update_boxes.argtypes = [POINTER(c_float), POINTER(c_int32), POINTER(c_float),
+                                       POINTER(c_float), POINTER(c_uint8), c_int, c_int,
+                                       POINTER(c_double), POINTER(c_int32)]
+        L.orc_max_threads.restype = c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(POINTER(t)) if a is not None else None
+
+
+def level_size(w: int, h: int, level: int):
+    a, b = c_int(), c_int()
+    lib().orc_level_size(w, h, level, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+class Pyramid:
+    """Oracle pyramid of one frame: img[L] (h_L, w_L) and grad[L] (h_L, w_L, 2)."""
+
+    def __init__(self, frame: np.ndarray, levels: int):
+        """frame: uint8 (a video frame) or float64 (an unquantised render)."""
+        h, w = frame.shape
+        self.w, self.h, self.levels = w, h, levels
+        n = lib().orc_pyramid_elems(w, h, levels)
+        self.img_flat = np.zeros(n, np.float64)
+        self.grad_flat = np.zeros(2 * n, np.float64)
+        if frame.dtype == np.uint8:
+            f = np.ascontiguousarray(frame)
+            lib().orc_pyramid(_p(f, c_uint8), w, h, w, levels, _p(self.img_flat, c_double),
+                              _p(self.grad_flat, c_double))
+        else:
+            f = np.ascontiguousarray(frame, dtype=np.float64)
+            lib().orc_pyramid_f64(_p(f, c_double), w, h, levels, _p(self.img_flat, c_double),
+                                  _p(self.grad_flat, c_double))
+        self.img, self.grad = [], []
+        off = 0
+        for L in range(levels):
+            lw, lh = level_size(w, h, L)
+            self.img.append(self.img_flat[off:off + lw * lh].reshape(lh, lw))
+            self.grad.append(self.grad_flat[2 * off:2 * (off + lw * lh)].reshape(lh, lw, 2))
+            off += lw * lh
+
+
+def isqrt(d: int) -> int:
+    return int(lib().orc_isqrt(d))
+
+
+def reflect101(i: int, n: int) -> int:
+    return lib().orc_reflect101(i, n)
+
+
+def scharr_raw(frame: np.ndarray):
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    h, w = f.shape
+    gx = np.zeros((h, w), np.int32)
+    gy = np.zeros((h, w), np.int32)
+    lib().orc_scharr_raw(_p(f, c_uint8), w, h, w, _p(gx, c_int32), _p(gy, c_int32))
+    return gx, gy
+
+
+def corner_response(frame: np.ndarray) -> np.ndarray:
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    h, w = f.shape
+    R = np.zeros((h, w), np.int64)
+    lib().orc_corner_response(_p(f, c_uint8), w, h, w, _p(R, c_int64))
+    return R
+
+
+def select_corners(frame: np.ndarray, boxes: np.ndarray, max_corners: int,
+                   quality=(1, 100), min_dist: float = 5.0):
+    """Returns (pts (nboxes, max_corners, 2) float32, counts (nboxes,) int32)."""
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    h, w = f.shape
+    b = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 4)
+    nb = b.shape[0]
+    pts = np.zeros((nb, max(max_corners, 0), 2), np.float32)
+    counts = np.zeros(nb, np.int32)
+    lib().orc_select_corners(_p(f, c_uint8), w, h, w, _p(b, c_float), nb, max_corners,
+                             int(quality[0]), int(quality[1]), float(min_dist),
+                             _p(pts, c_float), _p(counts, c_int32))
+    return pts, counts
+
+
+def lk_track(prev: Pyramid, nxt: Pyramid, pts: np.ndarray, win: int = 21, max_iter: int = 30,
+             eps: float = 0.01, min_eig: float = 1e-3, nthreads: int = 0, diagnostics: bool = False):
+    """Returns (pts_out (n, 2) float64, status (n,) uint8[, iters (n, L), mineig (n, L)])."""
+    assert prev.w == nxt.w and prev.h == nxt.h and prev.levels == nxt.levels
+    p = np.ascontiguousarray(pts, dtype=np.float32).reshape(-1, 2)
+    n = p.shape[0]
+    out = np.zeros((n, 2), np.float64)
+    st = np.zeros(n, np.uint8)
+    it = np.zeros((n, prev.levels), np.uint8) if diagnostics else None
+    me = np.zeros((n, prev.levels), np.float64) if diagnostics else None
+    lib().orc_lk_track(_p(prev.img_flat, c_double), _p(prev.grad_flat, c_double),
+                       _p(nxt.img_flat, c_double), _p(nxt.grad_flat, c_double),
+                       prev.w, prev.h, prev.levels, _p(p, c_float), n, win, max_iter,
+                       float(eps), float(min_eig), _p(out, c_double), _p(st, c_uint8),
+                       _p(it, c_uint8), _p(me, c_double), int(nthreads))
+    if diagnostics:
+        return out, st, it, me
+    return out, st
+
+
+def update_boxes(boxes, offsets, pts, pts_out, status, aggregator: int = 0):
+    """Returns (boxes_out (nboxes, 4) float64, nvalid (nboxes,) int32)."""
+    b = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 4)
+    o = np.ascontiguousarray(offsets, dtype=np.int32)
+    p = np.ascontiguousarray(pts, dtype=np.float32).reshape(-1, 2)
+    q = np.ascontiguousarray(pts_out, dtype=np.float32).reshape(-1, 2)
+    s = np.ascontiguousarray(status, dtype=np.uint8)
+    nb = b.shape[0]
+    out = np.zeros((nb, 4), np.float64)
+    nv = np.zeros(nb, np.int32)
+    lib().orc_update_boxes(_p(b, c_float), _p(o, c_int32), _p(p, c_float), _p(q, c_float),
+                           _p(s, c_uint8), nb, int(aggregator), _p(out, c_double), _p(nv, c_int32))
+    return out, nv
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()

@@ -1,0 +1,235 @@
+"""Pins of the oracle's pyramidal Lucas-Kanade tracker.
+
+Ties the tracker to: exact zero flow on identical frames, a brute-force
+integer SSD search on tiny images, shifts that bilinear interpolation
+resolves without bias, analytic sub-pixel shifts of low-frequency renders,
+the normal equations re-evaluated at the converged position with scipy's
+bilinear interpolation, and the aperture problem (1-D texture).
+"""
+import numpy as np
+import pytest
+import scipy.ndimage as ndi
+
+from paper_1910_06017_b300 import synth
+
+OK, LOST_EIG, LOST_OOB, NONCONV = 1, 2, 4, 8
+
+
+def _interior_points(rng, w, h, n, margin):
+    return np.stack([rng.uniform(margin, w - 1 - margin, n),
+                     rng.uniform(margin, h - 1 - margin, n)], 1).astype(np.float32)
+
+
+def test_identical_frames_zero_flow(oracle):
+    p = synth.sd_pair()
+    P = oracle.Pyramid(p.frame0, 3)
+    rng = np.random.default_rng(1)
+    pts = _interior_points(rng, 720, 576, 300, 0.0)
+    pts = np.concatenate([pts, np.array([[0, 0], [719, 575], [0, 575], [12.5, 0.25]], np.float32)])
+    out, st, it, me = oracle.lk_track(P, P, pts, win=21, max_iter=30, eps=0.01, min_eig=1e-3,
+                                      diagnostics=True)
+    ok = (st & OK) > 0
+    assert ok.sum() > 290
+    # b = 0 exactly, hence eta = 0, convergence at k = 1 and d = 0 exactly
+    np.testing.assert_array_equal(out[ok], pts[ok].astype(np.float64))
+    assert np.all(it[ok] == 1)
+
+
+@pytest.mark.parametrize("shift", [(2, -1), (-3, 3), (0, 2), (1, 1), (-2, -3)])
+def test_integer_shift_equals_ssd_argmin(oracle, shift):
+    rng = np.random.default_rng(20 + shift[0] * 7 + shift[1])
+    w = h = 32
+    tex = synth.Texture.draw(rng, w, h, n_blobs=10, sigma=(3.0, 6.0), period=(10.0, 20.0))
+    f0 = synth.render_shift(tex, w, h, 0, 0)
+    f1 = synth.render_shift(tex, w, h, shift[0], shift[1])
+    win, r = 9, 4
+    pts = np.array([[x, y] for x in (12, 16, 19) for y in (12, 15, 19)], np.float32)
+    P0, P1 = oracle.Pyramid(f0, 2), oracle.Pyramid(f1, 2)
+    out, st = oracle.lk_track(P0, P1, pts, win=win, max_iter=50, eps=1e-4, min_eig=1e-3)
+    i0 = f0.astype(np.int64)
+    i1 = f1.astype(np.int64)
+    for k, (x, y) in enumerate(pts.astype(int)):
+        best, arg = None, None
+        for sy in range(-r, r + 1):
+            for sx in range(-r, r + 1):
+                a = i0[y - 4:y + 5, x - 4:x + 5]
+                yy, xx = y + sy, x + sx
+                if yy - 4 < 0 or xx - 4 < 0 or yy + 5 > h or xx + 5 > w:
+                    continue
+                b = i1[yy - 4:yy + 5, xx - 4:xx + 5]
+                s = int(((a - b) ** 2).sum())
+                if best is None or s < best:
+                    best, arg = s, (sx, sy)
+        assert arg == tuple(shift)
+        if st[k] & OK:
+            assert tuple(np.round(out[k] - pts[k]).astype(int)) == arg
+    # a weakly textured window may legitimately diverge; most must track
+    assert np.sum((st & OK) > 0) >= 7
+
+
+@pytest.mark.parametrize("shift,levels", [((1.37, -0.62), 1), ((0.5, -1.5), 1), ((1.37, -0.62), 3),
+                                          ((5.3, -3.7), 3), ((-9.25, 6.5), 4)])
+def test_bilinear_surface_shift_is_exact(oracle, shift, levels):
+    # On I = c0 + c1 x + c2 y + c3 x y bilinear interpolation is exact, the
+    # binomial reduce keeps the surface bilinear (level L is I at 2^L X, 2^L Y)
+    # and the Scharr derivative is exact, so away from the reflected border
+    # the Lucas-Kanade fixed point is the true shift for any sub-pixel value.
+    w = h = 256
+    f0 = synth.render_bilinear(w, h)
+    f1 = synth.render_bilinear(w, h, dx=shift[0], dy=shift[1])
+    P0, P1 = oracle.Pyramid(f0, levels), oracle.Pyramid(f1, levels)
+    pts = _interior_points(np.random.default_rng(3), w, h, 40, 100.0)
+    pts = np.concatenate([pts, np.array([[128, 128], [120, 131]], np.float32)])
+    out, st, it, me = oracle.lk_track(P0, P1, pts, win=11, max_iter=200, eps=1e-9, min_eig=1e-3,
+                                      diagnostics=True)
+    assert np.all(st == OK)
+    err = np.abs(out - pts - np.array(shift))
+    assert err.max() <= 1e-6, err.max()
+
+
+def test_subpixel_bias_on_textures_is_bounded(oracle):
+    # On textures, I and J are interpolated at different sub-pixel phases; the
+    # mismatch is about a(1-a)/2 * omega^2 * A in intensity, i.e. ~1e-2 px at
+    # 24 px periods.  Check the size of that bias, not its absence.
+    p = synth.sd_pair(low_frequency=True, quantised=False)
+    P0, P1 = oracle.Pyramid(p.frame0, 3), oracle.Pyramid(p.frame1, 3)
+    pts = _interior_points(np.random.default_rng(6), 720, 576, 200, 24.0)
+    out, st = oracle.lk_track(P0, P1, pts, win=21, max_iter=100, eps=1e-6, min_eig=1e-3)
+    assert np.all(st & OK)
+    err = np.hypot(*(out - pts - np.array([1.37, -0.62])).T)
+    assert np.median(err) <= 2e-2 and err.max() <= 0.2, (np.median(err), err.max())
+
+
+def test_quantised_sd_pair_bias_bounded(oracle):
+    # u8 rounding and bilinear bias on the full-frequency texture leave a few
+    # 1e-3 px; the median box displacement must still be within 1e-2 px
+    p = synth.sd_pair()
+    P0, P1 = oracle.Pyramid(p.frame0, 3), oracle.Pyramid(p.frame1, 3)
+    pts, cnt = oracle.select_corners(p.frame0, p.boxes, 50)
+    allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+    out, st = oracle.lk_track(P0, P1, allp, win=21, max_iter=30, eps=0.01, min_eig=1e-3)
+    assert np.all(st & OK)
+    d = out - allp
+    assert np.all(np.abs(np.median(d, 0) - [1.37, -0.62]) <= 1e-2)
+
+
+def test_fixed_point_satisfies_normal_equations(oracle):
+    # Re-evaluate G and b at the converged position with scipy's bilinear
+    # interpolation (order 1, replicate border) and scipy's Scharr convolution:
+    # the next Newton step G^-1 b must vanish at the oracle's fixed point.
+    rng = np.random.default_rng(8)
+    w, h = 120, 96
+    tex = synth.Texture.low_frequency(rng, w, h)
+    f0 = synth.render_shift(tex, w, h, 0, 0)
+    f1 = synth.render_shift(tex, w, h, 0.83, -1.21)
+    P0, P1 = oracle.Pyramid(f0, 2), oracle.Pyramid(f1, 2)
+    pts = _interior_points(np.random.default_rng(9), w, h, 20, 20.0)
+    out, st = oracle.lk_track(P0, P1, pts, win=15, max_iter=200, eps=1e-8, min_eig=1e-3)
+    assert np.all(st & OK)
+    I = f0.astype(np.float64)
+    J = f1.astype(np.float64)
+    sx = np.array([[-3.0, 0, 3], [-10, 0, 10], [-3, 0, 3]]) / 32.0
+    Ix = ndi.correlate(I, sx, mode="mirror")
+    Iy = ndi.correlate(I, sx.T, mode="mirror")
+    o = np.arange(-7, 8, dtype=np.float64)
+    for (ux, uy), (vx, vy) in zip(pts.astype(np.float64), out):
+        oy, ox = np.meshgrid(o, o, indexing="ij")
+        cu = [uy + oy.ravel(), ux + ox.ravel()]
+        cv = [vy + oy.ravel(), vx + ox.ravel()]
+        a = ndi.map_coordinates(I, cu, order=1, mode="nearest")
+        gx = ndi.map_coordinates(Ix, cu, order=1, mode="nearest")
+        gy = ndi.map_coordinates(Iy, cu, order=1, mode="nearest")
+        b = ndi.map_coordinates(J, cv, order=1, mode="nearest")
+        G = np.array([[gx @ gx, gx @ gy], [gx @ gy, gy @ gy]])
+        r = np.array([(a - b) @ gx, (a - b) @ gy])
+        step = np.linalg.solve(G, r)
+        assert np.hypot(*step) < 1e-6
+
+
+def test_one_dimensional_texture_is_lost(oracle):
+    # I depends on x only: Iy = 0 exactly, G is singular and lambda_min = 0
+    w, h = 96, 64
+    x = np.arange(w, dtype=np.float64)
+    row0 = 128 + 80 * np.sin(2 * np.pi * x / 17.0)
+    row1 = 128 + 80 * np.sin(2 * np.pi * (x - 1.3) / 17.0)
+    f0 = synth.quantise(np.tile(row0, (h, 1)))
+    f1 = synth.quantise(np.tile(row1, (h, 1)))
+    P0, P1 = oracle.Pyramid(f0, 2), oracle.Pyramid(f1, 2)
+    pts = _interior_points(np.random.default_rng(2), w, h, 10, 12.0)
+    out, st, it, me = oracle.lk_track(P0, P1, pts, win=11, max_iter=20, eps=0.01, min_eig=1e-3,
+                                      diagnostics=True)
+    assert np.all(st == LOST_EIG)
+    np.testing.assert_array_equal(out, pts.astype(np.float64))
+    assert np.all(me[:, 1] == 0.0)
+
+
+def test_out_of_image_is_lost(oracle):
+    # Bilinear surface moved by (20, 0): the first Newton step is exactly the
+    # shift (the x*y term vanishes when dy = 0), so a point at x = 500 of a
+    # 512-wide frame jumps to a centre of 520 > W - 1 + w = 516 and is lost;
+    # the central point tracks exactly.
+    w = h = 512
+    f0 = synth.render_bilinear(w, h)
+    f1 = synth.render_bilinear(w, h, dx=20.0, dy=0.0)
+    P0, P1 = oracle.Pyramid(f0, 1), oracle.Pyramid(f1, 1)
+    pts = np.array([[500.0, 256.0], [256.0, 256.0]], np.float32)
+    out, st, it, me = oracle.lk_track(P0, P1, pts, win=11, max_iter=30, eps=1e-6, min_eig=1e-3,
+                                      diagnostics=True)
+    assert st[0] == LOST_OOB and it[0, 0] == 1
+    np.testing.assert_array_equal(out[0], pts[0].astype(np.float64))
+    assert st[1] == OK
+    assert np.abs(out[1] - [276.0, 256.0]).max() <= 1e-9
+
+
+def test_status_is_consistent_near_borders(oracle):
+    # Whatever the tracker does near the frame edge, an OK point ends inside
+    # [0, W-1] x [0, H-1] and a lost point reports its input position.
+    rng = np.random.default_rng(12)
+    w, h = 96, 80
+    tex = synth.Texture.low_frequency(rng, w + 40, h + 40)
+    f0 = synth.render_shift(tex, w, h, 0, 0)
+    f1 = synth.render_shift(tex, w, h, 6.0, -5.0)
+    P0, P1 = oracle.Pyramid(f0, 2), oracle.Pyramid(f1, 2)
+    pts = np.concatenate([_interior_points(rng, w, h, 100, 0.0),
+                          np.array([[w - 1, 3], [w - 2.5, h - 1], [0, 0]], np.float32)])
+    out, st = oracle.lk_track(P0, P1, pts, win=11, max_iter=30, eps=0.01, min_eig=1e-3)
+    ok = (st & OK) > 0
+    assert np.all(out[ok] >= 0) and np.all(out[ok, 0] <= w - 1) and np.all(out[ok, 1] <= h - 1)
+    np.testing.assert_array_equal(out[~ok], pts[~ok].astype(np.float64))
+    assert set(np.unique(st[~ok])) <= {LOST_EIG, LOST_OOB}
+
+
+def test_nonconvergence_flag(oracle):
+    rng = np.random.default_rng(13)
+    w, h = 96, 80
+    tex = synth.Texture.low_frequency(rng, w, h)
+    f0 = synth.render_shift(tex, w, h, 0, 0)
+    f1 = synth.render_shift(tex, w, h, 2.7, -1.9)
+    P0, P1 = oracle.Pyramid(f0, 1), oracle.Pyramid(f1, 1)
+    pts = np.array([[48.0, 40.0]], np.float32)
+    out, st, it, me = oracle.lk_track(P0, P1, pts, win=15, max_iter=1, eps=1e-6, min_eig=1e-3,
+                                      diagnostics=True)
+    assert st[0] == OK | NONCONV
+    assert it[0, 0] == 1
+
+
+def test_large_shift_needs_pyramid(oracle):
+    # A 17.8 px shift is far outside one 15x15 window's basin on a
+    # full-frequency texture; three levels bring it within reach.
+    rng = np.random.default_rng(14)
+    w, h = 200, 160
+    tex = synth.Texture.draw(rng, w, h, n_blobs=16)
+    f0 = synth.render_shift(tex, w, h, 0, 0)
+    f1 = synth.render_shift(tex, w, h, 13.4, -11.7)
+    pts, cnt = oracle.select_corners(f0, np.array([[40, 40, w - 40, h - 40]], np.float32), 30)
+    pts = pts[0, :cnt[0]]
+    assert len(pts) == 30
+
+    def n_tracked(levels):
+        P0, P1 = oracle.Pyramid(f0, levels), oracle.Pyramid(f1, levels)
+        out, st = oracle.lk_track(P0, P1, pts, win=15, max_iter=100, eps=1e-3, min_eig=1e-3)
+        e = np.abs(out - pts - [13.4, -11.7]).max(1)
+        return int(np.sum(((st & OK) > 0) & (e < 0.1)))
+
+    assert n_tracked(1) <= 3
+    assert n_tracked(3) == 30
