@@ -1,0 +1,236 @@
+/*
+ * omt.h -- C-ABI of the B300 (sm_103a) box-tracking hot path.
+ *
+ * The path moves each tracked box from frame t to frame t+1 (Section V-A of
+ * the paper: preprocessing -> feature calculation -> prediction):
+ *
+ *   omt_build_pyramid   Gaussian pyramid + Scharr gradients of a u8 frame
+ *   omt_corner_response Shi-Tomasi response of a whole frame (exact integers)
+ *   omt_select_corners  Shi-Tomasi corners inside each box of frame t
+ *   omt_lk_track        pyramidal Lucas-Kanade from frame t to frame t+1
+ *   omt_update_boxes    per-box median (or mean) displacement
+ *
+ * Conventions shared by every call
+ *   - Pixel centres sit at integer coordinates; a level-L coordinate is the
+ *     level-0 coordinate times 2^-L; level sizes are W_L = (W_{L-1} + 1) / 2.
+ *   - Boxes are float4 (x0, y0, x1, y1), half-open, in level-0 pixels.
+ *   - Points are float2 (x, y) in level-0 pixels.
+ *   - Every pointer argument marked "device" must point to device memory of
+ *     the current CUDA device.  The caller owns every buffer; the library
+ *     never allocates or frees device memory.
+ *   - Every call is asynchronous on the given stream (a cudaStream_t passed
+ *     as void*, NULL = legacy default stream) with no host synchronisation.
+ *   - Arguments are validated on the host before anything is launched; an
+ *     invalid call returns OMT_EINVAL and launches nothing.  A failed launch
+ *     returns OMT_ECUDA.  Kernels contain no waits and cannot hang.
+ *   - Calls on different streams may run concurrently from different host
+ *     threads; the library keeps no mutable global state.
+ */
+#ifndef OMT_H
+#define OMT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+
+enum omt_status {
+    OMT_OK = 0,
+    OMT_EINVAL = -1,   /* bad argument (checked on the host, nothing launched) */
+    OMT_ENOMEM = -2,   /* a caller buffer is smaller than the call needs     */
+    OMT_ECUDA = -3,    /* a CUDA launch or runtime call failed               */
+    OMT_ETIMEOUT = -4, /* reserved for bounded device waits                  */
+    OMT_ECHECK = -5    /* a device-side consistency check failed             */
+};
+
+/* Storage of pyramid levels >= 1 and of all gradient planes.  Level 0 is
+ * always the u8 frame.  Arithmetic is FP32 in both cases. */
+enum omt_storage {
+    OMT_F32 = 0, /* levels as float, gradients as float2                       */
+    OMT_F16 = 1  /* levels as half(I - 128), gradients as half2 (intensity/px) */
+};
+
+/* Per-point status bits written by omt_lk_track.  Exactly one of OK,
+ * LOST_EIG, LOST_OOB is set; NONCONV may accompany OK. */
+enum omt_point_status {
+    OMT_PT_OK = 1,       /* tracked                                            */
+    OMT_PT_LOST_EIG = 2, /* lambda_min(G)/win^2 < min_eig (or <= 0) at a level */
+    OMT_PT_LOST_OOB = 4, /* left the frame (see omt_lk_track)                  */
+    OMT_PT_NONCONV = 8   /* some level hit max_iter without converging (info)  */
+};
+
+#define OMT_MAX_LEVELS 8
+#define OMT_MIN_WIN 3
+#define OMT_MAX_WIN 31
+#define OMT_MAX_CORNERS 4096
+
+/* ----------------------------------------------------------- parameters */
+
+typedef struct omt_params {
+    int32_t levels;      /* pyramid levels, 1..OMT_MAX_LEVELS                     */
+    int32_t win;         /* LK window side, odd, OMT_MIN_WIN..OMT_MAX_WIN         */
+    int32_t max_iter;    /* LK iterations per level, 1..255                       */
+    float eps;           /* LK stops when |eta|^2 < eps^2 (level pixels), >= 0    */
+    float min_eig;       /* tau: lost when lambda_min(G)/win^2 < tau, >= 0        */
+    int32_t quality_num; /* corner quality as the exact rational num/den:          */
+    int32_t quality_den; /*   candidate iff den * R > num * R_max(box)           */
+    float min_dist;      /* corners keep dx^2 + dy^2 >= fl32(min_dist^2), >= 0    */
+    int32_t max_corners; /* corners per box, 0..OMT_MAX_CORNERS                   */
+    int32_t storage;     /* enum omt_storage                                      */
+    int32_t aggregator;  /* 0 = median (default), 1 = mean (the paper's choice)   */
+} omt_params;
+
+/* Defaults: 3 levels, 21x21 window, 30 iterations, eps 0.01, tau 1e-3,
+ * quality 1/100, min distance 5, 50 corners, F32 storage, median. */
+void omt_default_params(omt_params *p);
+
+/* OMT_OK if every field is in range, else OMT_EINVAL. */
+int omt_validate_params(const omt_params *p);
+
+/* ---------------------------------------------------------------- pyramid */
+
+typedef struct omt_level {
+    int32_t w, h;        /* level size                                    */
+    int64_t img_off;     /* byte offset of the image plane from base      */
+    int64_t img_pitch;   /* bytes per image row (multiple of 128)         */
+    int64_t grad_off;    /* byte offset of the (Ix, Iy) plane from base   */
+    int64_t grad_pitch;  /* bytes per gradient row (multiple of 128)      */
+} omt_level;
+
+/* Describes one frame's pyramid inside a caller-owned device buffer.
+ * Layout, level by level: image plane (level 0: u8; level >= 1: float or
+ * half(I - 128)), then the gradient plane (float2 or half2, Ix then Iy, in
+ * intensity per level pixel).  Every plane starts on a 256-byte boundary. */
+typedef struct omt_pyramid {
+    int32_t w, h, levels, storage;
+    void *base;          /* device, caller-owned, 256-byte aligned        */
+    size_t bytes;        /* size of the buffer at base                    */
+    omt_level lv[OMT_MAX_LEVELS];
+} omt_pyramid;
+
+/* Bytes a pyramid of this shape needs (0 if the shape is invalid). */
+size_t omt_pyramid_bytes(int32_t w, int32_t h, int32_t levels, int32_t storage);
+
+/* Fill *pyr for a buffer of `bytes` bytes at device address `base`.
+ * OMT_EINVAL on a bad shape or a misaligned base, OMT_ENOMEM if bytes is
+ * smaller than omt_pyramid_bytes().  Host-only; launches nothing. */
+int omt_pyramid_init(omt_pyramid *pyr, int32_t w, int32_t h, int32_t levels, int32_t storage,
+                     void *base, size_t bytes);
+
+/* Section V-A (preprocessing): build the pyramid of one u8 frame.
+ *   frame  device, h rows of `pitch` bytes (pitch >= w), read only
+ *   pyr    host struct from omt_pyramid_init with the same w, h; its levels
+ *          and storage must equal prm->levels and prm->storage
+ * Level 0 is a copy of the frame.  Level L >= 1 is the 5x5 binomial
+ * ([1 4 6 4 1]/16 each way) of level L-1 with reflect-101 borders,
+ * decimated to the even pixels.  Gradients per level:
+ *   Ix = sum_d s_d (I(x+1, y+d) - I(x-1, y+d)) / 32, s = (3, 10, 3),
+ *   Iy likewise, reflect-101.  In F32 storage levels 0..2 and the gradients
+ * of levels 0..1 are exact (dyadic values); deeper levels carry FP32
+ * rounding. */
+int omt_build_pyramid(const uint8_t *frame, int32_t w, int32_t h, size_t pitch,
+                      const omt_params *prm, const omt_pyramid *pyr, void *stream);
+
+/* ---------------------------------------------------------------- corners */
+
+/* Shi-Tomasi response of every pixel of a pyramid's level 0, exact:
+ *   a, b, c = 3x3 sums (reflect-101) of gx^2, gx gy, gy^2 with the raw
+ *   integer Scharr gx = 32 Ix, gy = 32 Iy of the u8 frame;
+ *   R = (a + c) - isqrt((a - c)^2 + 4 b^2)   in [2 lambda_min, 2 lambda_min + 1).
+ * out   device uint32[h * w] (row-major, no padding): bits 0..29 hold R,
+ *       bit 30 is set where 1 <= x <= w-2, 1 <= y <= h-2 and R is >= each
+ *       of its 8 neighbours (non-strict 3x3 maximum). */
+int omt_corner_response(const omt_pyramid *pyr, uint32_t *out, void *stream);
+
+/* Scratch bytes omt_select_corners needs for this frame size and box set. */
+size_t omt_corner_scratch_bytes(int32_t w, int32_t h, int32_t nboxes, int32_t max_corners);
+
+/* Section V-A (feature calculation, sparse form): Shi-Tomasi corners of
+ * frame t inside each box.  Per box, independently:
+ *   eligible pixels  x0 <= x < x1, y0 <= y < y1, 1 <= x <= W-2, 1 <= y <= H-2;
+ *   candidates       R > 0, den*R > num*R_max (R_max over the eligible pixels),
+ *                    and a non-strict 3x3 maximum (neighbours may lie outside
+ *                    the box);
+ *   order            R descending, then raster index y*W + x ascending;
+ *   greedy           keep a candidate if dx^2 + dy^2 >= fl32(min_dist^2) to
+ *                    every point kept so far, stop at max_corners.
+ * Arguments:
+ *   pyr       frame t's pyramid (only level 0 is read)
+ *   boxes     device float4[nboxes]
+ *   scratch   device, >= omt_corner_scratch_bytes(), 256-byte aligned;
+ *             contents on entry are ignored
+ *   pts       device float2[nboxes * max_corners]: the kept corners of all
+ *             boxes back to back in box order (integer-valued coordinates)
+ *   offsets   device int32[nboxes + 1]: CSR, box b owns pts[offsets[b] ..
+ *             offsets[b+1]); offsets[nboxes] is the total count
+ * The result is deterministic and identical bit for bit to the definition. */
+int omt_select_corners(const omt_pyramid *pyr, const float *boxes, int32_t nboxes,
+                       const omt_params *prm, void *scratch, size_t scratch_bytes,
+                       float *pts, int32_t *offsets, void *stream);
+
+/* --------------------------------------------------------------------- LK */
+
+/* Pyramidal iterative Lucas-Kanade (Bouguet), standing in for the dense
+ * motion field of Section V-A (feature calculation) / Section IV.
+ * For each point u: g = 0 at the top level; for L = levels-1 .. 0:
+ *   p = u 2^-L, N = win^2, w = (win-1)/2;
+ *   G = sum over (i, j) in [-w, w]^2 of [Ix^2 IxIy; IxIy Iy^2], with I, Ix,
+ *       Iy of frame t sampled bilinearly at p + (i, j) (taps clamped);
+ *   LOST_EIG if lambda_min(G)/N < min_eig or lambda_min <= 0;
+ *   nu = 0; for k = 1..max_iter:
+ *       LOST_OOB if the centre c = p + g + nu leaves
+ *           [-w, W_L-1+w] x [-w, H_L-1+w];
+ *       b = sum (I(p + (i,j)) - J(c + (i,j))) (Ix, Iy), J frame t+1, bilinear;
+ *       eta = G^-1 b; nu += eta; stop when eta_x^2 + eta_y^2 < eps^2;
+ *   g = 2 (g + nu) for L > 0, else d = g + nu.
+ * v = u + d, LOST_OOB if v is outside [0, W-1] x [0, H-1]; lost points
+ * report v = u.  NONCONV marks a level that used all max_iter iterations.
+ * Arguments:
+ *   prev, next  pyramids of frames t and t+1 (same w, h, levels, storage,
+ *               equal to prm->levels and prm->storage)
+ *   pts         device float2[n_max]
+ *   n_max       capacity of the point arrays (host value)
+ *   n_dev       device int32 or NULL: if given, only min(*n_dev, n_max)
+ *               points are tracked (lets the count come from
+ *               omt_select_corners without a host round trip)
+ *   pts_out     device float2[n_max]
+ *   status      device uint8[n_max] (enum omt_point_status bits)
+ *   iters       device uint8[n_max * levels] or NULL: iterations used per
+ *               level, entry [i * levels + L]
+ * Arithmetic is FP32 with a fixed reduction order: results do not depend on
+ * the launch shape or on the other points of the batch. */
+int omt_lk_track(const omt_pyramid *prev, const omt_pyramid *next, const float *pts,
+                 int32_t n_max, const int32_t *n_dev, const omt_params *prm,
+                 float *pts_out, uint8_t *status, uint8_t *iters, void *stream);
+
+/* ------------------------------------------------------------- box update */
+
+/* Section V-A (prediction): every box moves by an aggregate of the
+ * displacements pts_out - pts of its OK points; its size is kept.
+ * prm->aggregator 0: per-axis median (even count: mean of the two middle
+ * values); 1: mean.  A box without OK points keeps its place, nvalid = 0.
+ *   boxes      device float4[nboxes]
+ *   offsets    device int32[nboxes + 1] CSR into the point arrays
+ *   pts, pts_out, status   device, as written by omt_lk_track
+ *   boxes_out  device float4[nboxes] (must not alias boxes)
+ *   nvalid     device int32[nboxes] or NULL: OK points per box */
+int omt_update_boxes(const float *boxes, const int32_t *offsets, const float *pts,
+                     const float *pts_out, const uint8_t *status, int32_t nboxes,
+                     const omt_params *prm, float *boxes_out, int32_t *nvalid, void *stream);
+
+/* ---------------------------------------------------------------- misc */
+
+const char *omt_error_string(int32_t code);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int32_t omt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMT_H */
