@@ -1,0 +1,193 @@
+// api.cu -- the C-ABI of libomt: host-side validation, pyramid layout and
+// dispatch to the kernels.  Every check happens before the first launch.
+#include <math.h>
+#include <string.h>
+
+#include "omt_internal.cuh"
+
+using namespace omt;
+
+namespace {
+
+constexpr int32_t kVersion = 100;  // 0.1.0
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool shape_ok(int32_t w, int32_t h, int32_t levels, int32_t storage) {
+    return w >= 1 && h >= 1 && (int64_t)w * h <= (int64_t)1 << 31 && w <= (1 << 16) &&
+           h <= (1 << 16) && levels >= 1 && levels <= OMT_MAX_LEVELS &&
+           (storage == OMT_F32 || storage == OMT_F16);
+}
+
+// Plane layout of a pyramid; returns the total byte count.
+size_t layout(int32_t w, int32_t h, int32_t levels, int32_t storage, omt_level *lv) {
+    size_t off = 0;
+    const size_t esz = storage == OMT_F32 ? 4 : 2;
+    int32_t lw = w, lh = h;
+    for (int L = 0; L < levels; ++L) {
+        omt_level l;
+        l.w = lw;
+        l.h = lh;
+        l.img_pitch = (int64_t)align_up((size_t)lw * (L == 0 ? 1 : esz), 128);
+        l.img_off = (int64_t)off;
+        off = align_up(off + (size_t)l.img_pitch * lh, 256);
+        l.grad_pitch = (int64_t)align_up((size_t)lw * 2 * esz, 128);
+        l.grad_off = (int64_t)off;
+        off = align_up(off + (size_t)l.grad_pitch * lh, 256);
+        if (lv) lv[L] = l;
+        lw = (lw + 1) >> 1;
+        lh = (lh + 1) >> 1;
+    }
+    return off;
+}
+
+bool pyr_ok(const omt_pyramid *p) {
+    if (!p || !p->base || !shape_ok(p->w, p->h, p->levels, p->storage)) return false;
+    if (((uintptr_t)p->base & 255) != 0) return false;
+    omt_level lv[OMT_MAX_LEVELS];
+    const size_t need = layout(p->w, p->h, p->levels, p->storage, lv);
+    if (p->bytes < need) return false;
+    return memcmp(lv, p->lv, sizeof(omt_level) * p->levels) == 0;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int from_cuda(cudaError_t e) { return e == cudaSuccess ? OMT_OK : OMT_ECUDA; }
+
+}  // namespace
+
+extern "C" {
+
+void omt_default_params(omt_params *p) {
+    if (!p) return;
+    p->levels = 3;
+    p->win = 21;
+    p->max_iter = 30;
+    p->eps = 0.01f;
+    p->min_eig = 1e-3f;
+    p->quality_num = 1;
+    p->quality_den = 100;
+    p->min_dist = 5.0f;
+    p->max_corners = 50;
+    p->storage = OMT_F32;
+    p->aggregator = 0;
+}
+
+int omt_validate_params(const omt_params *p) {
+    if (!p) return OMT_EINVAL;
+    if (p->levels < 1 || p->levels > OMT_MAX_LEVELS) return OMT_EINVAL;
+    if (p->win < OMT_MIN_WIN || p->win > OMT_MAX_WIN || (p->win & 1) == 0) return OMT_EINVAL;
+    if (p->max_iter < 1 || p->max_iter > 255) return OMT_EINVAL;
+    if (!(p->eps >= 0.0f) || !isfinite(p->eps)) return OMT_EINVAL;
+    if (!(p->min_eig >= 0.0f) || !isfinite(p->min_eig)) return OMT_EINVAL;
+    if (p->quality_num < 0 || p->quality_den < 1 || p->quality_num > 65535 ||
+        p->quality_den > 65535)
+        return OMT_EINVAL;
+    if (!(p->min_dist >= 0.0f) || !(p->min_dist <= 65536.0f)) return OMT_EINVAL;
+    if (p->max_corners < 0 || p->max_corners > OMT_MAX_CORNERS) return OMT_EINVAL;
+    if (p->storage != OMT_F32 && p->storage != OMT_F16) return OMT_EINVAL;
+    if (p->aggregator != 0 && p->aggregator != 1) return OMT_EINVAL;
+    return OMT_OK;
+}
+
+size_t omt_pyramid_bytes(int32_t w, int32_t h, int32_t levels, int32_t storage) {
+    if (!shape_ok(w, h, levels, storage)) return 0;
+    return layout(w, h, levels, storage, nullptr);
+}
+
+int omt_pyramid_init(omt_pyramid *pyr, int32_t w, int32_t h, int32_t levels, int32_t storage,
+                     void *base, size_t bytes) {
+    if (!pyr || !base || !shape_ok(w, h, levels, storage) || !aligned(base, 256))
+        return OMT_EINVAL;
+    memset(pyr, 0, sizeof(*pyr));
+    const size_t need = layout(w, h, levels, storage, pyr->lv);
+    if (bytes < need) return OMT_ENOMEM;
+    pyr->w = w;
+    pyr->h = h;
+    pyr->levels = levels;
+    pyr->storage = storage;
+    pyr->base = base;
+    pyr->bytes = bytes;
+    return OMT_OK;
+}
+
+int omt_build_pyramid(const uint8_t *frame, int32_t w, int32_t h, size_t pitch,
+                      const omt_params *prm, const omt_pyramid *pyr, void *stream) {
+    if (!frame || omt_validate_params(prm) != OMT_OK || !pyr_ok(pyr)) return OMT_EINVAL;
+    if (pyr->w != w || pyr->h != h || pyr->levels != prm->levels || pyr->storage != prm->storage)
+        return OMT_EINVAL;
+    if (pitch < (size_t)w) return OMT_EINVAL;
+    return from_cuda(launch_pyramid(frame, w, h, pitch, *pyr, (cudaStream_t)stream));
+}
+
+int omt_corner_response(const omt_pyramid *pyr, uint32_t *out, void *stream) {
+    if (!pyr_ok(pyr) || !out || !aligned(out, 4)) return OMT_EINVAL;
+    return from_cuda(launch_corner_response(*pyr, out, nullptr, 0, (cudaStream_t)stream));
+}
+
+size_t omt_corner_scratch_bytes(int32_t w, int32_t h, int32_t nboxes, int32_t max_corners) {
+    if (w < 1 || h < 1 || nboxes < 0 || max_corners < 0 || max_corners > OMT_MAX_CORNERS)
+        return 0;
+    return select_scratch_bytes(w, h, nboxes, max_corners);
+}
+
+int omt_select_corners(const omt_pyramid *pyr, const float *boxes, int32_t nboxes,
+                       const omt_params *prm, void *scratch, size_t scratch_bytes, float *pts,
+                       int32_t *offsets, void *stream) {
+    if (omt_validate_params(prm) != OMT_OK || !pyr_ok(pyr) || nboxes < 0) return OMT_EINVAL;
+    if (nboxes > 0 && (!boxes || !aligned(boxes, 16) || !pts || !aligned(pts, 8)))
+        return OMT_EINVAL;
+    if (!offsets || !scratch || !aligned(scratch, 256)) return OMT_EINVAL;
+    if ((int64_t)nboxes * prm->max_corners > ((int64_t)1 << 31) - 1) return OMT_EINVAL;
+    if (scratch_bytes < select_scratch_bytes(pyr->w, pyr->h, nboxes, prm->max_corners))
+        return OMT_ENOMEM;
+    return from_cuda(launch_select_corners(*pyr, (const float4 *)boxes, nboxes, *prm, scratch,
+                                           (float2 *)pts, offsets, (cudaStream_t)stream));
+}
+
+int omt_lk_track(const omt_pyramid *prev, const omt_pyramid *next, const float *pts,
+                 int32_t n_max, const int32_t *n_dev, const omt_params *prm, float *pts_out,
+                 uint8_t *status, uint8_t *iters, void *stream) {
+    if (omt_validate_params(prm) != OMT_OK || !pyr_ok(prev) || !pyr_ok(next)) return OMT_EINVAL;
+    if (prev->w != next->w || prev->h != next->h || prev->levels != next->levels ||
+        prev->storage != next->storage || prev->levels != prm->levels ||
+        prev->storage != prm->storage)
+        return OMT_EINVAL;
+    if (n_max < 0) return OMT_EINVAL;
+    if (n_max > 0 && (!pts || !pts_out || !status || !aligned(pts, 8) || !aligned(pts_out, 8)))
+        return OMT_EINVAL;
+    return from_cuda(launch_lk(*prev, *next, (const float2 *)pts, n_max, n_dev, *prm,
+                               (float2 *)pts_out, status, iters, (cudaStream_t)stream));
+}
+
+int omt_update_boxes(const float *boxes, const int32_t *offsets, const float *pts,
+                     const float *pts_out, const uint8_t *status, int32_t nboxes,
+                     const omt_params *prm, float *boxes_out, int32_t *nvalid, void *stream) {
+    if (omt_validate_params(prm) != OMT_OK || nboxes < 0) return OMT_EINVAL;
+    if (nboxes == 0) return OMT_OK;
+    if (!boxes || !offsets || !boxes_out || !aligned(boxes, 16) || !aligned(boxes_out, 16))
+        return OMT_EINVAL;
+    if (boxes == boxes_out) return OMT_EINVAL;
+    if (!pts || !pts_out || !status || !aligned(pts, 8) || !aligned(pts_out, 8))
+        return OMT_EINVAL;
+    return from_cuda(launch_update_boxes((const float4 *)boxes, offsets, (const float2 *)pts,
+                                         (const float2 *)pts_out, status, nboxes,
+                                         prm->aggregator, (float4 *)boxes_out, nvalid,
+                                         (cudaStream_t)stream));
+}
+
+const char *omt_error_string(int32_t code) {
+    switch (code) {
+        case OMT_OK: return "success";
+        case OMT_EINVAL: return "invalid argument";
+        case OMT_ENOMEM: return "caller buffer too small";
+        case OMT_ECUDA: return "CUDA launch or runtime error";
+        case OMT_ETIMEOUT: return "bounded device wait timed out";
+        case OMT_ECHECK: return "device-side check failed";
+        default: return "unknown error";
+    }
+}
+
+int32_t omt_version(void) { return kVersion; }
+
+}  // extern "C"

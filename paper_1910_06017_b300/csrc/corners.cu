@@ -1,0 +1,463 @@
+// corners.cu -- K2: Shi-Tomasi response and per-box corner selection.
+//
+// Three launches per call:
+//   1. response_kernel   32x16 tiles of level 0 (only tiles that touch an
+//                        eligible pixel of some box when boxes are given):
+//                        integer Scharr -> 3x3 structure tensor -> exact
+//                        R = (a+c) - isqrt((a-c)^2 + 4b^2) -> non-strict 3x3
+//                        maximum flag, packed as R | flag << 30 into a
+//                        frame-sized uint32 map.
+//   2. select_kernel     one CTA per box: R_max, candidate keys
+//                        (R << 32 | ~(y*W + x)), bitonic sort in shared memory,
+//                        greedy minimum-distance acceptance by one warp.  Boxes
+//                        with more candidates than fit in shared memory are
+//                        consumed in descending chunks found by an exact MSD
+//                        radix select over the keys.
+//   3. compact_kernel    exclusive scan of the per-box counts into the CSR
+//                        offsets and a copy of the kept points, box by box.
+// Everything is integer arithmetic, so the result equals the definition bit
+// for bit, and the atomics only change the order in which unique keys are
+// gathered, never the sorted order.
+#include "omt_internal.cuh"
+
+namespace omt {
+namespace {
+
+constexpr uint32_t R_MASK = 0x3FFFFFFFu;
+constexpr uint32_t MAX_FLAG = 1u << 30;
+
+// ----------------------------------------------------------- exact isqrt
+// floor(sqrt(D)) for D < 2^62: a correctly rounded FP32 estimate, one Newton
+// correction of its residual, then at most a few unit steps.
+__device__ __forceinline__ uint32_t isqrt_u64(uint64_t D) {
+    if (D == 0) return 0;
+    const float f = __ull2float_rn(D);
+    int64_t s = (int64_t)sqrtf(f);
+    if (s > 0) {
+        const int64_t r = (int64_t)D - s * s;
+        s += (int64_t)floorf((float)r / (2.0f * (float)s));
+    }
+    if (s < 0) s = 0;
+#pragma unroll 1
+    for (int k = 0; k < 8 && (uint64_t)s * (uint64_t)s > D; ++k) --s;
+#pragma unroll 1
+    for (int k = 0; k < 8 && (uint64_t)(s + 1) * (uint64_t)(s + 1) <= D; ++k) ++s;
+    return (uint32_t)s;
+}
+
+// ------------------------------------------------------ response map kernel
+constexpr int RTX = 32, RTY = 16, RNT = 256;
+
+struct RespArgs {
+    const uint8_t *img;
+    int64_t pitch;
+    int w, h;
+    uint32_t *out;        // w*h, row-major, no padding
+    const float4 *boxes;  // nullptr: whole frame
+    int nboxes;
+};
+
+__device__ __forceinline__ int px(const RespArgs &a, int x, int y) {
+    return (int)__ldg(a.img + (int64_t)y * a.pitch + x);
+}
+
+__global__ void __launch_bounds__(RNT) response_kernel(RespArgs a) {
+    __shared__ int2 g[RTY + 4][RTX + 4];
+    __shared__ uint32_t R[RTY + 2][RTX + 2];
+    const int ox = blockIdx.x * RTX, oy = blockIdx.y * RTY;
+    const int tid = threadIdx.x;
+
+    if (a.boxes) {
+        // Skip tiles that hold no eligible pixel of any box.
+        int hit = 0;
+        const int tx1 = min(ox + RTX - 1, a.w - 1), ty1 = min(oy + RTY - 1, a.h - 1);
+        for (int b = tid; b < a.nboxes && !hit; b += RNT) {
+            int xlo, xhi, ylo, yhi;
+            if (box_pixel_range(a.boxes[b], a.w, a.h, xlo, xhi, ylo, yhi))
+                hit = xlo <= tx1 && xhi >= ox && ylo <= ty1 && yhi >= oy;
+        }
+        if (!__syncthreads_or(hit)) return;
+    }
+
+    // Raw Scharr at the pixels r101(q) for q in the tile +- 2.
+    for (int i = tid; i < (RTY + 4) * (RTX + 4); i += RNT) {
+        const int r = i / (RTX + 4), c = i - r * (RTX + 4);
+        const int x = reflect101(ox - 2 + c, a.w), y = reflect101(oy - 2 + r, a.h);
+        const int xm = reflect101(x - 1, a.w), xp = reflect101(x + 1, a.w);
+        const int ym = reflect101(y - 1, a.h), yp = reflect101(y + 1, a.h);
+        const int i00 = px(a, xm, ym), i01 = px(a, x, ym), i02 = px(a, xp, ym);
+        const int i10 = px(a, xm, y), i12 = px(a, xp, y);
+        const int i20 = px(a, xm, yp), i21 = px(a, x, yp), i22 = px(a, xp, yp);
+        const int gx = 3 * (i02 - i00) + 10 * (i12 - i10) + 3 * (i22 - i20);
+        const int gy = 3 * (i20 - i00) + 10 * (i21 - i01) + 3 * (i22 - i02);
+        g[r][c] = make_int2(gx, gy);
+    }
+    __syncthreads();
+
+    // Structure tensor and response at the tile +- 1 (in-image positions).
+    for (int i = tid; i < (RTY + 2) * (RTX + 2); i += RNT) {
+        const int r = i / (RTX + 2), c = i - r * (RTX + 2);
+        const int x = ox - 1 + c, y = oy - 1 + r;
+        uint32_t val = 0;
+        if (x >= 0 && x < a.w && y >= 0 && y < a.h) {
+            int sa = 0, sb = 0, sc = 0;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int2 q = g[r + dy][c + dx];
+                    sa += q.x * q.x;
+                    sb += q.x * q.y;
+                    sc += q.y * q.y;
+                }
+            const int64_t amc = (int64_t)sa - sc;
+            const uint64_t D = (uint64_t)(amc * amc) + 4ull * (uint64_t)((int64_t)sb * sb);
+            val = (uint32_t)((int64_t)sa + sc - (int64_t)isqrt_u64(D));
+        }
+        R[r][c] = val;
+    }
+    __syncthreads();
+
+    for (int i = tid; i < RTY * RTX; i += RNT) {
+        const int r = i / RTX, c = i - r * RTX;
+        const int x = ox + c, y = oy + r;
+        if (x >= a.w || y >= a.h) continue;
+        const uint32_t v = R[r + 1][c + 1];
+        uint32_t flag = 0;
+        if (x >= 1 && x <= a.w - 2 && y >= 1 && y <= a.h - 2) {
+            bool m = true;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) m = m && (v >= R[r + dy][c + dx]);
+            flag = m ? MAX_FLAG : 0u;
+        }
+        a.out[(int64_t)y * a.w + x] = v | flag;
+    }
+}
+
+// ------------------------------------------------------------ select kernel
+constexpr int SNT = 512;
+constexpr int SCAP = 8192;  // keys sorted at once in shared memory
+
+struct SelectArgs {
+    const uint32_t *rmap;
+    int w, h;
+    const float4 *boxes;
+    int maxc;
+    int qnum, qden;
+    int64_t md2c;   // reject when dx^2 + dy^2 < md2c (= ceil(fl32(min_dist^2)))
+    float2 *pad_pts;
+    int32_t *pad_counts;
+};
+
+__device__ __forceinline__ uint64_t make_key(uint32_t R, uint32_t idx) {
+    return ((uint64_t)R << 32) | (uint64_t)(0xFFFFFFFFu - idx);
+}
+
+// Ascending bitonic sort of keys[0..N), N a power of two <= SCAP.
+__device__ void bitonic_sort(uint64_t *keys, int N) {
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += SNT) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = keys[i], y = keys[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        keys[i] = y;
+                        keys[ixj] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Greedy minimum-distance acceptance over the n largest keys of the sorted
+// array (descending order from index N-1), by warp 0.  nacc is shared.
+__device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N, int n,
+                       int2 *acc, int *s_nacc) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int nacc = *s_nacc;
+    for (int base = 0; base < n && nacc < a.maxc; base += 32) {
+        const int j = base + lane;
+        const bool valid = j < n;
+        const uint64_t key = valid ? keys[N - 1 - j] : 0ull;
+        const uint32_t idx = 0xFFFFFFFFu - (uint32_t)key;
+        const int y = (int)(idx / (uint32_t)a.w), x = (int)(idx - (uint32_t)y * (uint32_t)a.w);
+        bool ok = valid;
+        for (int t = 0; t < nacc && ok; ++t) {
+            const int2 q = acc[t];
+            const int64_t dx = x - q.x, dy = y - q.y;
+            if (dx * dx + dy * dy < a.md2c) ok = false;
+        }
+        unsigned m = __ballot_sync(FULL_MASK, ok);
+        while (m && nacc < a.maxc) {
+            const int src = __ffs(m) - 1;
+            const int xs = __shfl_sync(FULL_MASK, x, src), ys = __shfl_sync(FULL_MASK, y, src);
+            if (lane == 0) {
+                acc[nacc] = make_int2(xs, ys);
+                a.pad_pts[(int64_t)box * a.maxc + nacc] = make_float2((float)xs, (float)ys);
+            }
+            ++nacc;
+            if (ok && lane > src) {
+                const int64_t dx = x - xs, dy = y - ys;
+                if (dx * dx + dy * dy < a.md2c) ok = false;
+            }
+            m = __ballot_sync(FULL_MASK, ok && lane > src);
+        }
+        __syncwarp();
+    }
+    if (lane == 0) *s_nacc = nacc;
+}
+
+__global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *keys = (uint64_t *)smem;
+    int2 *acc = (int2 *)(keys + SCAP);
+    __shared__ unsigned hist[256];
+    __shared__ int s_count, s_nacc, s_sel, s_k;
+    __shared__ uint32_t s_rmax;
+    const int box = blockIdx.x, tid = threadIdx.x;
+
+    int xlo, xhi, ylo, yhi;
+    if (!box_pixel_range(a.boxes[box], a.w, a.h, xlo, xhi, ylo, yhi) || a.maxc == 0) {
+        if (tid == 0) a.pad_counts[box] = 0;
+        return;
+    }
+    const int nx = xhi - xlo + 1;
+    const int E = nx * (yhi - ylo + 1);
+
+    // Pass 1: R_max over the eligible pixels.
+    uint32_t m = 0;
+    for (int i = tid; i < E; i += SNT) {
+        const int y = ylo + i / nx, x = xlo + i % nx;
+        m = max(m, __ldg(a.rmap + (int64_t)y * a.w + x) & R_MASK);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
+    if (tid == 0) {
+        s_rmax = 0;
+        s_count = 0;
+        s_nacc = 0;
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) atomicMax(&s_rmax, m);
+    __syncthreads();
+    const int64_t thr = (int64_t)a.qnum * (int64_t)s_rmax;
+
+    // Pass 2: gather the candidate keys (all of them if they fit).
+    for (int i = tid; i < E; i += SNT) {
+        const int y = ylo + i / nx, x = xlo + i % nx;
+        const uint32_t v = __ldg(a.rmap + (int64_t)y * a.w + x);
+        const uint32_t R = v & R_MASK;
+        if ((v & MAX_FLAG) && R > 0 && (int64_t)a.qden * R > thr) {
+            const int pos = atomicAdd(&s_count, 1);
+            if (pos < SCAP) keys[pos] = make_key(R, (uint32_t)(y * a.w + x));
+        }
+    }
+    __syncthreads();
+    const int total = s_count;
+
+    if (total <= SCAP) {
+        int N = 1;
+        while (N < total) N <<= 1;
+        for (int i = total + tid; i < N; i += SNT) keys[i] = 0ull;
+        __syncthreads();
+        bitonic_sort(keys, N);
+        greedy(a, box, keys, N, total, acc, &s_nacc);
+        __syncthreads();
+    } else {
+        // Descending chunks of SCAP keys: lo = the SCAP-th largest key below hi.
+        uint64_t hi = ~0ull;
+        for (;;) {
+            uint64_t prefix = 0, pmask = 0;
+            int k = SCAP;
+            bool take_all = false;
+            for (int shift = 56; shift >= 0; shift -= 8) {
+                for (int i = tid; i < 256; i += SNT) hist[i] = 0;
+                __syncthreads();
+                for (int i = tid; i < E; i += SNT) {
+                    const int y = ylo + i / nx, x = xlo + i % nx;
+                    const uint32_t v = __ldg(a.rmap + (int64_t)y * a.w + x);
+                    const uint32_t R = v & R_MASK;
+                    if ((v & MAX_FLAG) && R > 0 && (int64_t)a.qden * R > thr) {
+                        const uint64_t key = make_key(R, (uint32_t)(y * a.w + x));
+                        if (key < hi && (key & pmask) == prefix)
+                            atomicAdd(&hist[(key >> shift) & 255u], 1u);
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    unsigned cum = 0, tot = 0;
+                    for (int b = 0; b < 256; ++b) tot += hist[b];
+                    if (shift == 56 && tot <= (unsigned)k) {
+                        s_sel = -1;
+                    } else {
+                        int sel = 0;
+                        for (int b = 255; b >= 0; --b) {
+                            if (cum + hist[b] >= (unsigned)k) {
+                                sel = b;
+                                break;
+                            }
+                            cum += hist[b];
+                        }
+                        s_sel = sel;
+                        s_k = k - (int)cum;
+                    }
+                }
+                __syncthreads();
+                if (s_sel < 0) {
+                    take_all = true;
+                    break;
+                }
+                prefix |= (uint64_t)s_sel << shift;
+                pmask |= 0xFFull << shift;
+                k = s_k;
+                __syncthreads();
+            }
+            const uint64_t lo = take_all ? 0ull : prefix;
+            if (tid == 0) s_count = 0;
+            __syncthreads();
+            for (int i = tid; i < E; i += SNT) {
+                const int y = ylo + i / nx, x = xlo + i % nx;
+                const uint32_t v = __ldg(a.rmap + (int64_t)y * a.w + x);
+                const uint32_t R = v & R_MASK;
+                if ((v & MAX_FLAG) && R > 0 && (int64_t)a.qden * R > thr) {
+                    const uint64_t key = make_key(R, (uint32_t)(y * a.w + x));
+                    if (key >= lo && key < hi) {
+                        const int pos = atomicAdd(&s_count, 1);
+                        if (pos < SCAP) keys[pos] = key;
+                    }
+                }
+            }
+            __syncthreads();
+            const int n = min(s_count, SCAP);
+            int N = 1;
+            while (N < n) N <<= 1;
+            for (int i = n + tid; i < N; i += SNT) keys[i] = 0ull;
+            __syncthreads();
+            bitonic_sort(keys, N);
+            greedy(a, box, keys, N, n, acc, &s_nacc);
+            __syncthreads();
+            if (take_all || s_nacc >= a.maxc || lo == 0ull) break;
+            hi = lo;
+            __syncthreads();
+        }
+    }
+    if (tid == 0) a.pad_counts[box] = s_nacc;
+}
+
+// ----------------------------------------------------------- compact kernel
+constexpr int CNT = 1024;
+
+__global__ void __launch_bounds__(CNT) compact_kernel(const int32_t *pad_counts,
+                                                      const float2 *pad_pts, int nboxes,
+                                                      int maxc, float2 *pts, int32_t *offsets) {
+    __shared__ int warp_tot[CNT / 32];
+    __shared__ int s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nboxes; base += CNT) {
+        const int b = base + tid;
+        const int c = b < nboxes ? pad_counts[b] : 0;
+        int v = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL_MASK, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) warp_tot[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int t = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(FULL_MASK, t, o);
+                if (lane >= o) t += u;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        const int excl = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + v - c;
+        if (b < nboxes) offsets[b] = excl;
+        __syncthreads();
+        if (tid == CNT - 1) s_carry = carry + warp_tot[CNT / 32 - 1];
+        __syncthreads();
+    }
+    if (tid == 0) offsets[nboxes] = s_carry;
+    __syncthreads();
+    for (int b = wid; b < nboxes; b += CNT / 32) {
+        const int c = pad_counts[b], o = offsets[b];
+        for (int i = lane; i < c; i += 32) pts[o + i] = pad_pts[(int64_t)b * maxc + i];
+    }
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+size_t select_scratch_bytes(int w, int h, int nboxes, int max_corners) {
+    return align256((size_t)w * h * 4) + align256((size_t)nboxes * max_corners * 8) +
+           align256((size_t)nboxes * 4 + 4);
+}
+
+cudaError_t launch_corner_response(const omt_pyramid &pyr, uint32_t *out, const float4 *boxes,
+                                   int nboxes, cudaStream_t s) {
+    RespArgs a;
+    a.img = (const uint8_t *)pyr.base + pyr.lv[0].img_off;
+    a.pitch = pyr.lv[0].img_pitch;
+    a.w = pyr.w;
+    a.h = pyr.h;
+    a.out = out;
+    a.boxes = boxes;
+    a.nboxes = nboxes;
+    dim3 grid((pyr.w + RTX - 1) / RTX, (pyr.h + RTY - 1) / RTY);
+    response_kernel<<<grid, RNT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, int nboxes,
+                                  const omt_params &prm, void *scratch, float2 *pts,
+                                  int32_t *offsets, cudaStream_t s) {
+    uint8_t *sp = (uint8_t *)scratch;
+    uint32_t *rmap = (uint32_t *)sp;
+    sp += align256((size_t)pyr.w * pyr.h * 4);
+    float2 *pad_pts = (float2 *)sp;
+    sp += align256((size_t)nboxes * prm.max_corners * 8);
+    int32_t *pad_counts = (int32_t *)sp;
+
+    cudaError_t e;
+    if (nboxes > 0) {
+        e = launch_corner_response(pyr, rmap, boxes, nboxes, s);
+        if (e != cudaSuccess) return e;
+        SelectArgs a;
+        a.rmap = rmap;
+        a.w = pyr.w;
+        a.h = pyr.h;
+        a.boxes = boxes;
+        a.maxc = prm.max_corners;
+        a.qnum = prm.quality_num;
+        a.qden = prm.quality_den;
+        const float md2 = prm.min_dist * prm.min_dist;
+        a.md2c = (int64_t)ceil((double)md2);
+        a.pad_pts = pad_pts;
+        a.pad_counts = pad_counts;
+        const size_t smem = (size_t)SCAP * 8 + (size_t)prm.max_corners * 8;
+        e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        select_kernel<<<nboxes, SNT, smem, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    compact_kernel<<<1, CNT, 0, s>>>(pad_counts, pad_pts, nboxes, prm.max_corners, pts, offsets);
+    return cudaGetLastError();
+}
+
+}  // namespace omt

@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libomt (include/omt.h).
+
+Argument marshalling only: every step of the tracking path runs in the CUDA
+kernels behind the C-ABI.  Torch provides device memory and streams.  There
+is no CPU fallback: if libomt.so is missing or fails to load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, c_float, c_int32, c_int64, c_size_t, c_uint8, c_uint32, c_void_p
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libomt.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECHECK = 0, -1, -2, -3, -4, -5
+F32, F16 = 0, 1
+PT_OK, PT_LOST_EIG, PT_LOST_OOB, PT_NONCONV = 1, 2, 4, 8
+MAX_LEVELS = 8
+MAX_CORNERS = 4096
+
+EXPORTED = [
+    "omt_default_params", "omt_validate_params", "omt_pyramid_bytes", "omt_pyramid_init",
+    "omt_build_pyramid", "omt_corner_response", "omt_corner_scratch_bytes",
+    "omt_select_corners", "omt_lk_track", "omt_update_boxes", "omt_error_string",
+    "omt_version",
+]
+
+
+class OmtError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {error_string(code)} ({code})")
+        self.code = code
+
+
+class Params(Structure):
+    _fields_ = [("levels", c_int32), ("win", c_int32), ("max_iter", c_int32), ("eps", c_float),
+                ("min_eig", c_float), ("quality_num", c_int32), ("quality_den", c_int32),
+                ("min_dist", c_float), ("max_corners", c_int32), ("storage", c_int32),
+                ("aggregator", c_int32)]
+
+    def replace(self, **kw) -> "Params":
+        p = Params()
+        ctypes.pointer(p)[0] = self
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Level(Structure):
+    _fields_ = [("w", c_int32), ("h", c_int32), ("img_off", c_int64), ("img_pitch", c_int64),
+                ("grad_off", c_int64), ("grad_pitch", c_int64)]
+
+
+class PyramidDesc(Structure):
+    _fields_ = [("w", c_int32), ("h", c_int32), ("levels", c_int32), ("storage", c_int32),
+                ("base", c_void_p), ("bytes", c_size_t), ("lv", Level * MAX_LEVELS)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libomt.so (raises if it is missing; never falls back)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libomt.so not built at {LIB_PATH}; run python -m paper_1910_06017_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        P = POINTER(PyramidDesc)
+        L.omt_default_params.argtypes = [POINTER(Params)]
+        L.omt_default_params.restype = None
+        L.omt_validate_params.argtypes = [POINTER(Params)]
+        L.omt_pyramid_bytes.argtypes = [c_int32, c_int32, c_int32, c_int32]
+        L.omt_pyramid_bytes.restype = c_size_t
+        L.omt_pyramid_init.argtypes = [P, c_int32, c_int32, c_int32, c_int32, c_void_p, c_size_t]
+        L.omt_build_pyramid.argtypes = [c_void_p, c_int32, c_int32, c_size_t, POINTER(Params), P, c_void_p]
+        L.omt_corner_response.argtypes = [P, c_void_p, c_void_p]
+        L.omt_corner_scratch_bytes.argtypes = [c_int32, c_int32, c_int32, c_int32]
+        L.omt_corner_scratch_bytes.restype = c_size_t
+        L.omt_select_corners.argtypes = [P, c_void_p, c_int32, POINTER(Params), c_void_p, c_size_t,
+                                         c_void_p, c_void_p, c_void_p]
+        L.omt_lk_track.argtypes = [P, P, c_void_p, c_int32, c_void_p, POINTER(Params), c_void_p,
+                                   c_void_p, c_void_p, c_void_p]
+        L.omt_update_boxes.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                       POINTER(Params), c_void_p, c_void_p, c_void_p]
+        L.omt_error_string.argtypes = [c_int32]
+        L.omt_error_string.restype = ctypes.c_char_p
+        L.omt_version.restype = c_int32
+        _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().omt_error_string(code).decode()
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise OmtError(code, what)
+
+
+def _ptr(t):
+    """Device address of a torch tensor, or None."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().omt_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "quality" and isinstance(v, (tuple, list)):
+            p.quality_num, p.quality_den = int(v[0]), int(v[1])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def validate_params(p: Params) -> int:
+    return lib().omt_validate_params(ctypes.byref(p))
+
+
+def pyramid_bytes(w: int, h: int, levels: int, storage: int = F32) -> int:
+    return int(lib().omt_pyramid_bytes(w, h, levels, storage))
+
+
+class Pyramid:
+    """A frame's pyramid in a torch-allocated device buffer."""
+
+    def __init__(self, w: int, h: int, levels: int, storage: int = F32, device="cuda", buffer=None):
+        import torch
+        n = pyramid_bytes(w, h, levels, storage)
+        if n == 0:
+            raise OmtError(EINVAL, "pyramid shape")
+        self.buffer = torch.empty(n, dtype=torch.uint8, device=device) if buffer is None else buffer
+        self.desc = PyramidDesc()
+        _check(lib().omt_pyramid_init(ctypes.byref(self.desc), w, h, levels, storage,
+                                      _ptr(self.buffer), self.buffer.numel()), "omt_pyramid_init")
+        self.w, self.h, self.levels, self.storage = w, h, levels, storage
+
+    def level_size(self, L: int):
+        return self.desc.lv[L].w, self.desc.lv[L].h
+
+    def image(self, L: int):
+        """Level L as a torch tensor (uint8 for L = 0, float32/float16 otherwise)."""
+        import torch
+        lv = self.desc.lv[L]
+        raw = self.buffer[lv.img_off: lv.img_off + lv.img_pitch * lv.h].view(lv.h, lv.img_pitch)
+        if L == 0:
+            return raw[:, :lv.w]
+        dt = torch.float32 if self.storage == F32 else torch.float16
+        return raw.view(dt)[:, :lv.w]
+
+    def grad(self, L: int):
+        """Level L gradients (h, w, 2) as float32 or float16."""
+        import torch
+        lv = self.desc.lv[L]
+        raw = self.buffer[lv.grad_off: lv.grad_off + lv.grad_pitch * lv.h].view(lv.h, lv.grad_pitch)
+        dt = torch.float32 if self.storage == F32 else torch.float16
+        return raw.view(dt)[:, :2 * lv.w].reshape(lv.h, lv.w, 2)
+
+
+def build_pyramid(frame, pyr: Pyramid, params: Params, stream=None):
+    """frame: 2-D uint8 CUDA tensor (rows may be padded: stride(0) is the pitch)."""
+    assert frame.dtype.itemsize == 1 and frame.dim() == 2 and frame.stride(1) == 1
+    h, w = frame.shape
+    _check(lib().omt_build_pyramid(_ptr(frame), w, h, frame.stride(0), ctypes.byref(params),
+                                   ctypes.byref(pyr.desc), _stream(stream)), "omt_build_pyramid")
+
+
+def corner_response(pyr: Pyramid, out, stream=None):
+    """out: int32/uint32-sized CUDA tensor of h*w elements."""
+    _check(lib().omt_corner_response(ctypes.byref(pyr.desc), _ptr(out), _stream(stream)),
+           "omt_corner_response")
+
+
+def corner_scratch_bytes(w: int, h: int, nboxes: int, max_corners: int) -> int:
+    return int(lib().omt_corner_scratch_bytes(w, h, nboxes, max_corners))
+
+
+def select_corners(pyr: Pyramid, boxes, params: Params, scratch, pts, offsets, stream=None):
+    """boxes float32 (nb, 4); pts float32 (nb*max_corners, 2); offsets int32 (nb+1)."""
+    nb = boxes.shape[0] if boxes is not None else 0
+    _check(lib().omt_select_corners(ctypes.byref(pyr.desc), _ptr(boxes), nb, ctypes.byref(params),
+                                    _ptr(scratch), scratch.numel() * scratch.element_size(),
+                                    _ptr(pts), _ptr(offsets), _stream(stream)), "omt_select_corners")
+
+
+def lk_track(prev: Pyramid, nxt: Pyramid, pts, params: Params, pts_out, status, iters=None,
+             n_max=None, n_dev=None, stream=None):
+    n = pts.shape[0] if n_max is None else n_max
+    _check(lib().omt_lk_track(ctypes.byref(prev.desc), ctypes.byref(nxt.desc), _ptr(pts), n,
+                              _ptr(n_dev), ctypes.byref(params), _ptr(pts_out), _ptr(status),
+                              _ptr(iters), _stream(stream)), "omt_lk_track")
+
+
+def update_boxes(boxes, offsets, pts, pts_out, status, params: Params, boxes_out, nvalid=None,
+                 stream=None):
+    nb = boxes.shape[0]
+    _check(lib().omt_update_boxes(_ptr(boxes), _ptr(offsets), _ptr(pts), _ptr(pts_out),
+                                  _ptr(status), nb, ctypes.byref(params), _ptr(boxes_out),
+                                  _ptr(nvalid), _stream(stream)), "omt_update_boxes")
+
+
+class StreamTracker:
+    """Per-stream state for the plain path: two pyramids (t, t+1) that swap
+    roles, and the buffers one step needs.  step() runs the whole hot path
+    (pyramid of the new frame, corners of frame t inside the boxes, LK, box
+    update) as five asynchronous C-ABI calls with no host synchronisation."""
+
+    def __init__(self, w: int, h: int, params: Params, max_boxes: int, device="cuda"):
+        import torch
+        self.w, self.h, self.params = w, h, params
+        self.pyr = [Pyramid(w, h, params.levels, params.storage, device),
+                    Pyramid(w, h, params.levels, params.storage, device)]
+        self.cur = 0
+        self.max_boxes = max_boxes
+        cap = max(1, max_boxes * params.max_corners)
+        self.scratch = torch.empty(corner_scratch_bytes(w, h, max_boxes, params.max_corners),
+                                   dtype=torch.uint8, device=device)
+        self.pts = torch.empty((cap, 2), dtype=torch.float32, device=device)
+        self.pts_out = torch.empty((cap, 2), dtype=torch.float32, device=device)
+        self.status = torch.empty(cap, dtype=torch.uint8, device=device)
+        self.iters = torch.empty((cap, params.levels), dtype=torch.uint8, device=device)
+        self.offsets = torch.empty(max_boxes + 1, dtype=torch.int32, device=device)
+        self.boxes_out = torch.empty((max(1, max_boxes), 4), dtype=torch.float32, device=device)
+        self.nvalid = torch.empty(max(1, max_boxes), dtype=torch.int32, device=device)
+
+    def prime(self, frame, stream=None):
+        build_pyramid(frame, self.pyr[self.cur], self.params, stream)
+
+    def step(self, frame_next, boxes, stream=None, with_iters: bool = True):
+        """Track boxes (nb, 4) of frame t into frame t+1; returns boxes_out[:nb]."""
+        nb = boxes.shape[0]
+        assert nb <= self.max_boxes
+        prev, nxt = self.pyr[self.cur], self.pyr[1 - self.cur]
+        build_pyramid(frame_next, nxt, self.params, stream)
+        select_corners(prev, boxes, self.params, self.scratch, self.pts, self.offsets, stream)
+        cap = nb * self.params.max_corners
+        lk_track(prev, nxt, self.pts, self.params, self.pts_out, self.status,
+                 self.iters if with_iters else None, n_max=cap, n_dev=self.offsets[nb:nb + 1],
+                 stream=stream)
+        update_boxes(boxes, self.offsets, self.pts, self.pts_out, self.status, self.params,
+                     self.boxes_out[:nb], self.nvalid[:nb], stream)
+        self.cur = 1 - self.cur
+        return self.boxes_out[:nb]
