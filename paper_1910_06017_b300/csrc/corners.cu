@@ -272,8 +272,11 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
         __syncthreads();
     } else {
         // Descending chunks of SCAP keys: lo = the SCAP-th largest key below hi.
+        // Each round consumes exactly SCAP keys below hi, so total / SCAP + 1
+        // rounds exhaust the box; the bound only makes that explicit.
         uint64_t hi = ~0ull;
-        for (;;) {
+        const int max_rounds = total / SCAP + 2;
+        for (int round = 0; round < max_rounds; ++round) {
             uint64_t prefix = 0, pmask = 0;
             int k = SCAP;
             bool take_all = false;
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
             bitonic_sort(keys, N);
             greedy(a, box, keys, N, n, acc, &s_nacc);
             __syncthreads();
-            if (take_all || s_nacc >= a.maxc || lo == 0ull) break;
+            if (take_all || s_nacc >= a.maxc || lo == 0ull || lo >= hi) break;
             hi = lo;
             __syncthreads();
         }

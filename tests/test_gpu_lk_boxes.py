@@ -1,0 +1,294 @@
+"""GPU parity of K3 (pyramidal LK) and K4 (box update) against the FP64
+oracle, through the C-ABI, and end-to-end steps of the whole path.
+
+Bar for FP32 flow: within 1e-3 px of the oracle on every point whose per-
+level iteration counts agree (a differing stopping iteration near eps moves
+the result by up to about eps and is counted and bounded separately);
+within 1e-3 px on all points in fixed-iteration mode (eps = 0); statuses
+identical outside the guard band lambda_min/N in [0.9 tau, 1.1 tau].
+FP16-stored pyramids: within 0.02 px.
+"""
+import numpy as np
+import pytest
+
+from paper_1910_06017_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+OK, LOST_EIG, LOST_OOB, NONCONV = 1, 2, 4, 8
+FLOW_TOL = 1e-3
+F16_TOL = 0.02
+
+
+@pytest.fixture(scope="module")
+def omt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_06017_b300 import omt as m
+    m.lib()
+    return m
+
+
+def _pyr(omt, frame, levels, storage=0):
+    h, w = frame.shape
+    P = omt.Pyramid(w, h, levels, storage)
+    omt.build_pyramid(torch.from_numpy(np.ascontiguousarray(frame)).cuda(), P,
+                      omt.default_params(levels=levels, storage=storage))
+    return P
+
+
+def gpu_lk(omt, f0, f1, pts, storage=0, **kw):
+    params = omt.default_params(storage=storage, **kw)
+    P0, P1 = _pyr(omt, f0, params.levels, storage), _pyr(omt, f1, params.levels, storage)
+    n = len(pts)
+    p = torch.from_numpy(np.ascontiguousarray(pts, np.float32).reshape(-1, 2)).cuda()
+    out = torch.full((max(n, 1), 2), np.nan, device="cuda")
+    st = torch.full((max(n, 1),), 255, dtype=torch.uint8, device="cuda")
+    it = torch.full((max(n, 1), params.levels), 255, dtype=torch.uint8, device="cuda")
+    omt.lk_track(P0, P1, p, params, out, st, it, n_max=n)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()[:n], st.cpu().numpy()[:n], it.cpu().numpy()[:n]
+
+
+def oracle_lk(oracle, f0, f1, pts, levels=3, win=21, max_iter=30, eps=0.01, min_eig=1e-3):
+    O0, O1 = oracle.Pyramid(f0, levels), oracle.Pyramid(f1, levels)
+    return oracle.lk_track(O0, O1, pts, win=win, max_iter=max_iter, eps=eps, min_eig=min_eig,
+                           diagnostics=True)
+
+
+def compare(omt, oracle, f0, f1, pts, storage=0, tol=FLOW_TOL, min_ok=0.9, **kw):
+    params = dict(levels=3, win=21, max_iter=30, eps=0.01, min_eig=1e-3)
+    params.update(kw)
+    g_out, g_st, g_it = gpu_lk(omt, f0, f1, pts, storage, **params)
+    o_out, o_st, o_it, o_me = oracle_lk(oracle, f0, f1, pts, **params)
+    tau = params["min_eig"]
+    band = np.any((o_me >= 0.9 * tau) & (o_me <= 1.1 * tau), axis=1)
+    same_status = g_st == o_st
+    assert np.all(same_status | band), np.nonzero(~(same_status | band))[0][:10]
+    ok = (g_st & OK) > 0
+    assert ok.mean() >= min_ok, ok.mean()
+    agree = np.all(g_it == o_it, axis=1) & same_status
+    if storage == 0:
+        both = agree & ok
+        err = np.abs(g_out[both] - o_out[both]).max(initial=0.0)
+        assert err <= tol, err
+        # points whose stopping iteration differs stay within ~eps
+        differ = (~agree) & ok & (o_st & OK > 0)
+        if differ.any():
+            assert np.abs(g_out[differ] - o_out[differ]).max() <= 2 * params["eps"] + tol
+        assert differ.mean() <= 0.05
+    else:
+        both = ok & ((o_st & OK) > 0)
+        err = np.abs(g_out[both] - o_out[both]).max(initial=0.0)
+        assert err <= tol, err
+    lost = ~ok
+    np.testing.assert_array_equal(g_out[lost], np.asarray(pts, np.float32)[lost])
+    return g_out, g_st, o_out, o_st
+
+
+def test_lk_sd_pair_corners(omt, oracle):
+    p = synth.sd_pair()
+    pts, cnt = oracle.select_corners(p.frame0, p.boxes, 50)
+    allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+    compare(omt, oracle, p.frame0, p.frame1, allp)
+
+
+def test_lk_fixed_iterations_all_points(omt, oracle):
+    p = synth.sd_pair()
+    rng = np.random.default_rng(3)
+    pts = np.stack([rng.uniform(0, 719, 2000), rng.uniform(0, 575, 2000)], 1).astype(np.float32)
+    g_out, g_st, g_it = gpu_lk(omt, p.frame0, p.frame1, pts, levels=3, win=21, max_iter=10, eps=0.0)
+    o_out, o_st, o_it, o_me = oracle_lk(oracle, p.frame0, p.frame1, pts, max_iter=10, eps=0.0)
+    band = np.any((o_me >= 0.9e-3) & (o_me <= 1.1e-3), axis=1)
+    assert np.all((g_st == o_st) | band)
+    both = ((g_st & OK) > 0) & (g_st == o_st)
+    assert both.mean() > 0.8
+    assert np.abs(g_out[both] - o_out[both]).max() <= FLOW_TOL
+
+
+def test_lk_identical_frames_exact_zero(omt, oracle):
+    p = synth.sd_pair()
+    rng = np.random.default_rng(4)
+    pts = np.stack([rng.uniform(0, 719, 500), rng.uniform(0, 575, 500)], 1).astype(np.float32)
+    out, st, it = gpu_lk(omt, p.frame0, p.frame0, pts)
+    ok = (st & OK) > 0
+    assert ok.mean() > 0.9
+    np.testing.assert_array_equal(out[ok], pts[ok])
+    assert np.all(it[ok] == 1)
+
+
+@pytest.mark.parametrize("win,levels", [(3, 1), (7, 2), (15, 4), (21, 5), (31, 5), (9, 8)])
+def test_lk_window_and_level_sweep(omt, oracle, win, levels):
+    rng = np.random.default_rng(win * 10 + levels)
+    w, h = 331, 257
+    tex = synth.Texture.draw(rng, w, h, n_blobs=24)
+    f0 = synth.render_shift(tex, w, h)
+    f1 = synth.render_shift(tex, w, h, 2.3, -1.7)
+    pts = np.stack([rng.uniform(0, w - 1, 600), rng.uniform(0, h - 1, 600)], 1).astype(np.float32)
+    compare(omt, oracle, f0, f1, pts, win=win, levels=levels, min_ok=0.5)
+
+
+def test_lk_borders_and_oob(omt, oracle):
+    rng = np.random.default_rng(12)
+    w, h = 96, 80
+    tex = synth.Texture.low_frequency(rng, w + 40, h + 40)
+    f0 = synth.render_shift(tex, w, h, 0, 0)
+    f1 = synth.render_shift(tex, w, h, 6.0, -5.0)
+    pts = np.concatenate([np.stack([rng.uniform(0, w - 1, 300), rng.uniform(0, h - 1, 300)], 1),
+                          np.array([[w - 1, 3], [w - 2.5, h - 1], [0, 0], [95, 79]])]).astype(np.float32)
+    compare(omt, oracle, f0, f1, pts, levels=2, win=11, min_ok=0.3)
+
+
+def test_lk_one_dimensional_texture_lost(omt):
+    w, h = 96, 64
+    x = np.arange(w, dtype=np.float64)
+    f0 = synth.quantise(np.tile(128 + 80 * np.sin(2 * np.pi * x / 17.0), (h, 1)))
+    f1 = synth.quantise(np.tile(128 + 80 * np.sin(2 * np.pi * (x - 1.3) / 17.0), (h, 1)))
+    pts = np.stack([np.linspace(12, 80, 10), np.linspace(12, 50, 10)], 1).astype(np.float32)
+    out, st, it = gpu_lk(omt, f0, f1, pts, levels=2, win=11)
+    assert np.all(st == LOST_EIG)
+    np.testing.assert_array_equal(out, pts)
+
+
+def test_lk_empty_and_device_count(omt, oracle):
+    p = synth.sd_pair()
+    out, st, it = gpu_lk(omt, p.frame0, p.frame1, np.zeros((0, 2), np.float32))
+    assert out.shape == (0, 2)
+    # n_dev limits the work to the first points; the rest stay untouched
+    params = omt.default_params()
+    P0, P1 = _pyr(omt, p.frame0, 3), _pyr(omt, p.frame1, 3)
+    pts = torch.tensor([[100.0, 100.0], [200.0, 300.0], [400.0, 50.0]], device="cuda")
+    o = torch.full((3, 2), -1.0, device="cuda")
+    s = torch.full((3,), 255, dtype=torch.uint8, device="cuda")
+    n_dev = torch.tensor([2], dtype=torch.int32, device="cuda")
+    omt.lk_track(P0, P1, pts, params, o, s, None, n_max=3, n_dev=n_dev)
+    torch.cuda.synchronize()
+    assert s[2].item() == 255 and o[2, 0].item() == -1.0
+    assert (s[:2].cpu().numpy() & OK).all()
+
+
+def test_lk_batch_independence(omt):
+    # a point's result does not depend on the launch shape or batch mates
+    p = synth.sd_pair()
+    rng = np.random.default_rng(9)
+    pts = np.stack([rng.uniform(0, 719, 3000), rng.uniform(0, 575, 3000)], 1).astype(np.float32)
+    full = gpu_lk(omt, p.frame0, p.frame1, pts)
+    for sl in [slice(0, 1), slice(17, 400), slice(2999, 3000)]:
+        part = gpu_lk(omt, p.frame0, p.frame1, pts[sl])
+        for a, b in zip(full, part):
+            np.testing.assert_array_equal(a[sl], b)
+
+
+def test_lk_f16_storage_within_002(omt, oracle):
+    p = synth.sd_pair()
+    pts, cnt = oracle.select_corners(p.frame0, p.boxes, 50)
+    allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+    compare(omt, oracle, p.frame0, p.frame1, allp, storage=1, tol=F16_TOL)
+
+
+def test_lk_4k_large_motion_sample(omt, oracle):
+    pr = synth.rigid_pair()
+    pts, cnt = oracle.select_corners(pr.frame0, pr.boxes, 250)
+    allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+    rng = np.random.default_rng(1)
+    sample = allp[rng.choice(len(allp), 3000, replace=False)]
+    kw = dict(levels=5, win=31, max_iter=30, eps=0.01)
+    compare(omt, oracle, pr.frame0, pr.frame1, sample, min_ok=0.5, **kw)
+    compare(omt, oracle, pr.frame0, pr.frame1, sample, storage=1, tol=F16_TOL, min_ok=0.5, **kw)
+
+
+# ------------------------------------------------------------------ boxes
+
+def _gpu_update(omt, boxes, off, pts, out, st, agg):
+    params = omt.default_params(aggregator=agg)
+    nb = len(boxes)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).cuda()
+    bo = torch.empty((nb, 4), device="cuda")
+    nv = torch.empty(nb, dtype=torch.int32, device="cuda")
+    omt.update_boxes(t(boxes, np.float32), t(off, np.int32), t(pts.reshape(-1, 2), np.float32),
+                     t(out.reshape(-1, 2), np.float32), t(st, np.uint8), params, bo, nv)
+    torch.cuda.synchronize()
+    return bo.cpu().numpy(), nv.cpu().numpy()
+
+
+@pytest.mark.parametrize("agg", [0, 1])
+def test_update_boxes_matches_oracle(omt, oracle, agg):
+    rng = np.random.default_rng(5 + agg)
+    nb = 300
+    counts = rng.integers(0, 400, nb)
+    counts[:3] = [0, 1, 2]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    n = int(off[-1])
+    pts = rng.uniform(0, 3800, (n, 2)).astype(np.float32)
+    out = (pts + rng.normal(0, 5, (n, 2))).astype(np.float32)
+    st = rng.choice([OK, OK | NONCONV, LOST_EIG, LOST_OOB], n, p=[0.6, 0.1, 0.15, 0.15]).astype(np.uint8)
+    boxes = rng.uniform(0, 3000, (nb, 4)).astype(np.float32)
+    g, gn = _gpu_update(omt, boxes, off, pts, out, st, agg)
+    o, on = oracle.update_boxes(boxes, off, pts, out, st, aggregator=agg)
+    np.testing.assert_array_equal(gn, on)
+    np.testing.assert_allclose(g, o, rtol=0, atol=1e-3 if agg else 5e-4)
+
+
+def test_update_boxes_hand_vectors(omt):
+    boxes = np.array([[10, 20, 50, 70], [0, 0, 5, 5], [1, 1, 2, 2]], np.float32)
+    pts = np.zeros((7, 2), np.float32) + 100
+    d = np.array([[3, 5], [-1, 0], [2, -7], [1, 0], [4, 1], [2, 2], [10, 3]], np.float32)
+    st = np.array([OK, OK, OK, OK, OK | NONCONV, LOST_EIG, OK], np.uint8)
+    off = np.array([0, 3, 7, 7], np.int32)
+    g, gn = _gpu_update(omt, boxes, off, pts, pts + d, st, 0)
+    np.testing.assert_array_equal(gn, [3, 3, 0])
+    np.testing.assert_array_equal(g[0], [12, 20, 52, 70])
+    np.testing.assert_array_equal(g[1], [4, 1, 9, 6])
+    np.testing.assert_array_equal(g[2], boxes[2])
+
+
+# ------------------------------------------------------------ end to end
+
+def test_stream_tracker_sd_step(omt, oracle):
+    p = synth.sd_pair()
+    params = omt.default_params()
+    T = omt.StreamTracker(720, 576, params, max_boxes=16)
+    T.prime(torch.from_numpy(p.frame0).cuda())
+    boxes = torch.from_numpy(p.boxes).cuda()
+    bo = T.step(torch.from_numpy(p.frame1).cuda(), boxes)
+    torch.cuda.synchronize()
+    # oracle pipeline on the same frames
+    pts, cnt = oracle.select_corners(p.frame0, p.boxes, 50)
+    allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+    O0, O1 = oracle.Pyramid(p.frame0, 3), oracle.Pyramid(p.frame1, 3)
+    o_out, o_st = oracle.lk_track(O0, O1, allp)
+    off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+    o_b, o_nv = oracle.update_boxes(p.boxes, off, allp, o_out.astype(np.float32), o_st)
+    np.testing.assert_array_equal(T.offsets[:len(p.boxes) + 1].cpu().numpy(), off)
+    np.testing.assert_array_equal(T.pts[:off[-1]].cpu().numpy(), allp)
+    np.testing.assert_array_equal(T.nvalid[:len(p.boxes)].cpu().numpy(), o_nv)
+    np.testing.assert_allclose(bo.cpu().numpy(), o_b, rtol=0, atol=2e-3)
+    assert np.abs(bo.cpu().numpy() - p.boxes - [1.37, -0.62, 1.37, -0.62]).max() <= 0.02
+
+
+def test_1080p_clip_trajectory_matches_oracle(omt, oracle):
+    # Section V-A loop on the 1080p affine clip: detections every 5th frame,
+    # prediction in between; GPU and oracle box trajectories must agree.
+    n = 8
+    clip = synth.affine_clip(n_frames=n)
+    params = omt.default_params(levels=4, max_corners=100)
+    T = omt.StreamTracker(1920, 1080, params, max_boxes=16)
+    T.prime(torch.from_numpy(clip.frames[0]).cuda())
+    gb = clip.gt_boxes[0].astype(np.float32)
+    ob = gb.copy()
+    for t in range(1, n):
+        if (t - 1) % 5 == 0:
+            gb = clip.gt_boxes[t - 1].astype(np.float32)
+            ob = gb.copy()
+        g = T.step(torch.from_numpy(clip.frames[t]).cuda(), torch.from_numpy(gb).cuda())
+        torch.cuda.synchronize()
+        gb = g.cpu().numpy().copy()
+        pts, cnt = oracle.select_corners(clip.frames[t - 1], ob, 100)
+        allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+        O0, O1 = oracle.Pyramid(clip.frames[t - 1], 4), oracle.Pyramid(clip.frames[t], 4)
+        o_out, o_st = oracle.lk_track(O0, O1, allp)
+        off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+        ob, _ = oracle.update_boxes(ob, off, allp, o_out.astype(np.float32), o_st)
+        ob = ob.astype(np.float32)
+        assert np.abs(gb - ob).max() <= 0.05, (t, np.abs(gb - ob).max())
