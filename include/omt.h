@@ -172,6 +172,36 @@ int omt_select_corners(const omt_pyramid *pyr, const float *boxes, int32_t nboxe
                        const omt_params *prm, void *scratch, size_t scratch_bytes,
                        float *pts, int32_t *offsets, void *stream);
 
+/* Bytes of the device array that omt_select_corners_static uses as scratch.
+ * Every GPU that loads this library holds this much memory until the
+ * process exits. */
+#define OMT_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* omt_select_corners for callers that cannot allocate device memory.  The
+ * paper has no counterpart; it exists for callers that only own their
+ * inputs and outputs: a plugin inside an application that controls the CUDA
+ * allocator, or a real-time loop that must not call cudaMalloc (which can
+ * synchronise the whole device).  Same arguments and result as
+ * omt_select_corners, minus the scratch: the scratch is one fixed array
+ * (OMT_STATIC_SCRATCH_BYTES) inside the library.
+ *   - Returns OMT_ENOMEM when omt_corner_scratch_bytes(w, h, nboxes,
+ *     max_corners) exceeds OMT_STATIC_SCRATCH_BYTES (16 MiB: a 1920x1080
+ *     frame with up to about 160,000 box-corner slots); the caller must then
+ *     use omt_select_corners with its own scratch.
+ *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *     routine.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, and it keeps whatever the last call
+ *     left in it; nothing in it needs to start at zero, because a call
+ *     writes every scratch value before reading it.  Calls whose work
+ *     overlaps on the GPU (different streams, or different host threads)
+ *     race on the array and corrupt each other's results: serialise them. */
+int omt_select_corners_static(const omt_pyramid *pyr, const float *boxes, int32_t nboxes,
+                              const omt_params *prm, float *pts, int32_t *offsets,
+                              void *stream);
+
 /* --------------------------------------------------------------------- LK */
 
 /* Pyramidal iterative Lucas-Kanade (Bouguet), standing in for the dense

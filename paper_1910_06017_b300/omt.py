@@ -24,8 +24,9 @@ EXPORTED = [
     "omt_default_params", "omt_validate_params", "omt_pyramid_bytes", "omt_pyramid_init",
     "omt_build_pyramid", "omt_corner_response", "omt_corner_scratch_bytes",
     "omt_select_corners", "omt_lk_track", "omt_update_boxes", "omt_error_string",
-    "omt_version",
+    "omt_version", "omt_select_corners_static",
 ]
+STATIC_SCRATCH_BYTES = 16 << 20
 
 
 class OmtError(RuntimeError):
@@ -194,6 +195,19 @@ def select_corners(pyr: Pyramid, boxes, params: Params, scratch, pts, offsets, s
     _check(lib().omt_select_corners(ctypes.byref(pyr.desc), _ptr(boxes), nb, ctypes.byref(params),
                                     _ptr(scratch), scratch.numel() * scratch.element_size(),
                                     _ptr(pts), _ptr(offsets), _stream(stream)), "omt_select_corners")
+
+
+def select_corners_static(pyr: Pyramid, boxes, params: Params, pts, offsets, stream=None):
+    """select_corners without a scratch argument: the library's own fixed
+    device array is used instead (for callers that cannot allocate).  Calls
+    share that array, so they must not overlap on the GPU."""
+    L = lib()
+    fn = L.omt_select_corners_static
+    fn.argtypes = [POINTER(PyramidDesc), c_void_p, c_int32, POINTER(Params), c_void_p, c_void_p,
+                   c_void_p]
+    nb = boxes.shape[0] if boxes is not None else 0
+    _check(fn(ctypes.byref(pyr.desc), _ptr(boxes), nb, ctypes.byref(params), _ptr(pts),
+              _ptr(offsets), _stream(stream)), "omt_select_corners_static")
 
 
 def lk_track(prev: Pyramid, nxt: Pyramid, pts, params: Params, pts_out, status, iters=None,
