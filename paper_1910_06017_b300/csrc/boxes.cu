@@ -1,10 +1,11 @@
 // boxes.cu -- K4: per-box displacement update (Section V-A, prediction).
 //
 // One CTA per box.  The median of dx (and of dy) over the box's OK points is
-// found by an exact MSD radix select on order-preserving 32-bit keys of the
-// FP32 displacements (four 8-bit digits, shared-memory histograms), so it
-// needs no sort, no scratch and works for any number of points per box; an
-// even count averages the two middle order statistics.  The mean flag sums
+// an exact order statistic: for up to 2048 OK points the displacements are
+// gathered in shared memory and the element of rank k is found by counting;
+// larger boxes use an MSD radix select on order-preserving 32-bit keys of the
+// FP32 displacements (four 8-bit digits, shared-memory histograms).  Neither
+// needs a sort or scratch; an even count averages the two middle values.  The mean flag sums
 // with a fixed per-thread stride and a fixed tree, so it is deterministic.
 #include "omt_internal.cuh"
 
@@ -35,7 +36,9 @@ __device__ __forceinline__ float disp(const BoxArgs &a, int i, int axis) {
     return axis == 0 ? a.pts_out[i].x - a.pts[i].x : a.pts_out[i].y - a.pts[i].y;
 }
 
-// Value of rank k (0-based, ascending) among the OK displacements of [lo, hi).
+// Value of rank k (0-based, ascending) among the OK displacements of [lo, hi),
+// for boxes too large for the shared-memory path: MSD radix select, with
+// the digit's bin found by a warp scan over the 256-bin histogram.
 __device__ float select_rank(const BoxArgs &a, int lo, int hi, int axis, int k, unsigned *hist,
                              int *s_sel, int *s_k) {
     uint32_t prefix = 0, pmask = 0;
@@ -48,18 +51,32 @@ __device__ float select_rank(const BoxArgs &a, int lo, int hi, int axis, int k, 
             if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned cum = 0;
-            int sel = 255;
-            for (int b = 0; b < 256; ++b) {
-                if (cum + hist[b] > (unsigned)k) {
-                    sel = b;
-                    break;
-                }
-                cum += hist[b];
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            unsigned c[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j] = hist[lane * 8 + j];
+                sum += c[j];
             }
-            *s_sel = sel;
-            *s_k = k - (int)cum;
+            unsigned inc = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(FULL_MASK, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const unsigned exc = inc - sum;
+            if (exc <= (unsigned)k && (unsigned)k < inc) {
+                unsigned cum = exc;
+                for (int j = 0; j < 8; ++j) {
+                    if (cum + c[j] > (unsigned)k) {
+                        *s_sel = lane * 8 + j;
+                        *s_k = k - (int)cum;
+                        break;
+                    }
+                    cum += c[j];
+                }
+            }
         }
         __syncthreads();
         prefix |= (uint32_t)*s_sel << shift;
@@ -70,11 +87,34 @@ __device__ float select_rank(const BoxArgs &a, int lo, int hi, int axis, int k, 
     return fval(prefix);
 }
 
+// Shared-memory path for boxes with at most SMALL OK points: gather the
+// displacements, then the element of rank k is the one with exactly k
+// elements before it in the order (value, gather position).
+constexpr int SMALL = 2048;
+
+__device__ float rank_pick(const float *v, int m, int k, float *s_out) {
+    for (int i = threadIdx.x; i < m; i += BNT) {
+        const float x = v[i];
+        int r = 0;
+        for (int j = 0; j < m; ++j) {
+            const float y = v[j];
+            r += (y < x) || (y == x && j < i);
+        }
+        if (r == k) *s_out = x;
+    }
+    __syncthreads();
+    const float out = *s_out;
+    __syncthreads();
+    return out;
+}
+
 __global__ void __launch_bounds__(BNT) box_update_kernel(BoxArgs a) {
     __shared__ unsigned hist[256];
     __shared__ float red[2][BNT / 32];
     __shared__ int cnt[BNT / 32];
-    __shared__ int s_sel, s_k;
+    __shared__ int s_sel, s_k, s_n;
+    __shared__ float s_val;
+    __shared__ float vx[SMALL], vy[SMALL];
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int lo = a.offsets[b], hi = a.offsets[b + 1];
 
@@ -112,6 +152,28 @@ __global__ void __launch_bounds__(BNT) box_update_kernel(BoxArgs a) {
         if (a.aggregator == 1) {
             mx = tx / (float)total;
             my = ty / (float)total;
+        } else if (total <= SMALL) {
+            if (tid == 0) s_n = 0;
+            __syncthreads();
+            for (int i = lo + tid; i < hi; i += BNT) {
+                if (!(a.status[i] & OMT_PT_OK)) continue;
+                const int p = atomicAdd(&s_n, 1);
+                vx[p] = disp(a, i, 0);
+                vy[p] = disp(a, i, 1);
+            }
+            __syncthreads();
+            const int k1 = (total - 1) / 2, k2 = total / 2;
+            const float x1 = rank_pick(vx, total, k1, &s_val);
+            const float y1 = rank_pick(vy, total, k1, &s_val);
+            if (k2 != k1) {
+                const float x2 = rank_pick(vx, total, k2, &s_val);
+                const float y2 = rank_pick(vy, total, k2, &s_val);
+                mx = 0.5f * (x1 + x2);
+                my = 0.5f * (y1 + y2);
+            } else {
+                mx = x1;
+                my = y1;
+            }
         } else {
             const int k1 = (total - 1) / 2, k2 = total / 2;
             const float x1 = select_rank(a, lo, hi, 0, k1, hist, &s_sel, &s_k);

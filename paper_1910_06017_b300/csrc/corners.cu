@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(RNT) response_kernel(RespArgs a) {
 
 // ------------------------------------------------------------ select kernel
 constexpr int SNT = 512;
-constexpr int SCAP = 8192;  // keys sorted at once in shared memory
+constexpr int SCAP = 8192;   // keys sorted at once in shared memory
+constexpr int GCAP = 32768;  // cells of the accepted-point grid in shared memory
 
 struct SelectArgs {
     const uint32_t *rmap;
@@ -147,6 +148,8 @@ struct SelectArgs {
     int maxc;
     int qnum, qden;
     int64_t md2c;   // reject when dx^2 + dy^2 < md2c (= ceil(fl32(min_dist^2)))
+    int dmax;       // largest |dx| with dx^2 < md2c
+    int cell;       // side of the accepted-point grid cells, max(1, floor(sqrt(md2c / 2)))
     float2 *pad_pts;
     int32_t *pad_counts;
 };
@@ -175,10 +178,18 @@ __device__ void bitonic_sort(uint64_t *keys, int N) {
     }
 }
 
+// Grid of accepted points over a box's eligible pixels: cells of side
+// `cell` with 2 (cell-1)^2 < md2c hold at most one accepted point each, so a
+// candidate only checks the cells within dmax pixels of itself.
+struct AccGrid {
+    int16_t *cells;  // nullptr: no grid (too many cells), check the whole list
+    int gx, gy, xlo, ylo;
+};
+
 // Greedy minimum-distance acceptance over the n largest keys of the sorted
 // array (descending order from index N-1), by warp 0.  nacc is shared.
 __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N, int n,
-                       int2 *acc, int *s_nacc) {
+                       int2 *acc, int *s_nacc, const AccGrid &g) {
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     int nacc = *s_nacc;
@@ -189,10 +200,31 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
         const uint32_t idx = 0xFFFFFFFFu - (uint32_t)key;
         const int y = (int)(idx / (uint32_t)a.w), x = (int)(idx - (uint32_t)y * (uint32_t)a.w);
         bool ok = valid;
-        for (int t = 0; t < nacc && ok; ++t) {
-            const int2 q = acc[t];
-            const int64_t dx = x - q.x, dy = y - q.y;
-            if (dx * dx + dy * dy < a.md2c) ok = false;
+        if (ok && a.md2c > 0) {
+            if (g.cells) {
+                const int cx0 = max(x - a.dmax - g.xlo, 0) / a.cell;
+                const int cx1 = min((x + a.dmax - g.xlo) / a.cell, g.gx - 1);
+                const int cy0 = max(y - a.dmax - g.ylo, 0) / a.cell;
+                const int cy1 = min((y + a.dmax - g.ylo) / a.cell, g.gy - 1);
+                for (int cy = cy0; cy <= cy1 && ok; ++cy)
+                    for (int cx = cx0; cx <= cx1; ++cx) {
+                        const int t = g.cells[cy * g.gx + cx];
+                        if (t >= 0) {
+                            const int2 q = acc[t];
+                            const int64_t dx = x - q.x, dy = y - q.y;
+                            if (dx * dx + dy * dy < a.md2c) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                    }
+            } else {
+                for (int t = 0; t < nacc && ok; ++t) {
+                    const int2 q = acc[t];
+                    const int64_t dx = x - q.x, dy = y - q.y;
+                    if (dx * dx + dy * dy < a.md2c) ok = false;
+                }
+            }
         }
         unsigned m = __ballot_sync(FULL_MASK, ok);
         while (m && nacc < a.maxc) {
@@ -200,6 +232,8 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
             const int xs = __shfl_sync(FULL_MASK, x, src), ys = __shfl_sync(FULL_MASK, y, src);
             if (lane == 0) {
                 acc[nacc] = make_int2(xs, ys);
+                if (g.cells)
+                    g.cells[((ys - g.ylo) / a.cell) * g.gx + (xs - g.xlo) / a.cell] = (int16_t)nacc;
                 a.pad_pts[(int64_t)box * a.maxc + nacc] = make_float2((float)xs, (float)ys);
             }
             ++nacc;
@@ -218,6 +252,7 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *keys = (uint64_t *)smem;
     int2 *acc = (int2 *)(keys + SCAP);
+    int16_t *cells = (int16_t *)(acc + a.maxc);
     __shared__ unsigned hist[256];
     __shared__ int s_count, s_nacc, s_sel, s_k;
     __shared__ uint32_t s_rmax;
@@ -230,6 +265,14 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
     }
     const int nx = xhi - xlo + 1;
     const int E = nx * (yhi - ylo + 1);
+    AccGrid g;
+    g.xlo = xlo;
+    g.ylo = ylo;
+    g.gx = (nx + a.cell - 1) / a.cell;
+    g.gy = (yhi - ylo + a.cell) / a.cell;
+    g.cells = (a.md2c > 0 && (int64_t)g.gx * g.gy <= GCAP) ? cells : nullptr;
+    if (g.cells)
+        for (int i = tid; i < g.gx * g.gy; i += SNT) g.cells[i] = -1;
 
     // Pass 1: R_max over the eligible pixels.
     uint32_t m = 0;
@@ -268,7 +311,7 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
         for (int i = total + tid; i < N; i += SNT) keys[i] = 0ull;
         __syncthreads();
         bitonic_sort(keys, N);
-        greedy(a, box, keys, N, total, acc, &s_nacc);
+        greedy(a, box, keys, N, total, acc, &s_nacc, g);
         __syncthreads();
     } else {
         // Descending chunks of SCAP keys: lo = the SCAP-th largest key below hi.
@@ -344,7 +387,7 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
             for (int i = n + tid; i < N; i += SNT) keys[i] = 0ull;
             __syncthreads();
             bitonic_sort(keys, N);
-            greedy(a, box, keys, N, n, acc, &s_nacc);
+            greedy(a, box, keys, N, n, acc, &s_nacc, g);
             __syncthreads();
             if (take_all || s_nacc >= a.maxc || lo == 0ull || lo >= hi) break;
             hi = lo;
@@ -449,9 +492,13 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
         a.qden = prm.quality_den;
         const float md2 = prm.min_dist * prm.min_dist;
         a.md2c = (int64_t)ceil((double)md2);
+        a.dmax = 0;
+        while ((int64_t)(a.dmax + 1) * (a.dmax + 1) < a.md2c) ++a.dmax;
+        a.cell = 1;
+        while (2 * (int64_t)(a.cell + 1) * (a.cell + 1) <= a.md2c) ++a.cell;
         a.pad_pts = pad_pts;
         a.pad_counts = pad_counts;
-        const size_t smem = (size_t)SCAP * 8 + (size_t)prm.max_corners * 8;
+        const size_t smem = (size_t)SCAP * 8 + (size_t)prm.max_corners * 8 + (size_t)GCAP * 2;
         e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;

@@ -2,12 +2,14 @@
 // stand-in for the dense motion field of Section V-A (feature calculation).
 //
 // One warp per point, lane c owning window column c.  Per level the warp
-// walks the (win+1) texel rows of the window once: each lane loads the texel
-// of its column, takes the right neighbour from lane c+1 with a shuffle, and
-// interpolates horizontally; the vertical interpolation reuses the previous
-// row.  The frame-t window (I, Ix, Iy) stays in registers for all
-// iterations, so an iteration reads one frame-(t+1) texel per lane and row,
-// and the two sums of b (and the three of G) are warp butterfly reductions.
+// walks the (win+1) texel rows of its window: each lane loads the texel of
+// its column, takes the right neighbour from lane c+1 with a shuffle, and
+// interpolates horizontally, then vertically reusing the previous row.  The
+// frame-t window keeps only (Ix, Iy) per tap in registers (its rows are
+// loaded in batches of 8); b = sum (I - J) grad I is formed as
+// c - sum J grad I with the level constant c = sum I grad I, so an iteration
+// reads one frame-(t+1) texel per lane and row.  The sums of b (and of G, c)
+// are warp butterfly reductions.
 // All lanes end with identical sums, so the control flow stays uniform, and
 // the reduction order is fixed: a point's result does not depend on the
 // launch shape or on its neighbours in the batch.
@@ -19,7 +21,7 @@
 namespace omt {
 namespace {
 
-constexpr int LK_NT = 256;
+constexpr int LK_NT = 128;
 constexpr int LK_WARPS = LK_NT / 32;
 
 struct LKArgs {
@@ -45,12 +47,166 @@ __device__ __forceinline__ float det2(float a, float d, float b) {
     return f + e;
 }
 
+// Image value at an in-range pixel: u8 for level 0, else float or
+// half(I - 128).  One code path for all levels keeps the register budget
+// of a single inlined copy; the branch is uniform across the warp.
+template <int ST>
+__device__ __forceinline__ float texel(const uint8_t *row, int x, bool u8) {
+    if (u8) return (float)__ldg(row + x);
+    if (ST == OMT_F32) return __ldg((const float *)row + x);
+    return __half2float(__ldg((const __half *)row + x)) + 128.0f;
+}
+
+// Frame-t window of one level: (Ix, Iy) per tap row in registers, and the
+// level constants G (three sums) and c = sum I (Ix, Iy).
+template <int ST, int WIN>
+__device__ __forceinline__ void template_window(const LevelView &P, int ipx, int ipy, float ax,
+                                                float ay, int lane, bool u8, float (&Xw)[WIN],
+                                                float (&Yw)[WIN], float &sxx, float &sxy,
+                                                float &syy, float &cx, float &cy) {
+    constexpr int R = WIN / 2;
+    constexpr int CH = 8;  // texel rows loaded per batch (bounds live registers)
+    const bool loader = lane <= WIN, tapcol = lane < WIN;
+    const int tx = clampi(ipx + lane - R, 0, P.w - 1);
+    float pI = 0.f, pX = 0.f, pY = 0.f;
+    sxx = sxy = syy = cx = cy = 0.f;
+#pragma unroll
+    for (int t0 = 0; t0 <= WIN; t0 += CH) {
+        float v[CH];
+        float2 g[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int tr = t0 + c;
+            v[c] = 0.f;
+            g[c] = make_float2(0.f, 0.f);
+            if (tr <= WIN && loader) {
+                const int ty = clampi(ipy + tr - R, 0, P.h - 1);
+                v[c] = texel<ST>(P.img + (int64_t)ty * P.img_pitch, tx, u8);
+                g[c] = load_grad<ST>(P, tx, ty);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int tr = t0 + c;
+            if (tr > WIN) break;
+            const float v1 = __shfl_down_sync(FULL_MASK, v[c], 1);
+            const float g1x = __shfl_down_sync(FULL_MASK, g[c].x, 1);
+            const float g1y = __shfl_down_sync(FULL_MASK, g[c].y, 1);
+            const float hI = fmaf(ax, v1 - v[c], v[c]);
+            const float hX = fmaf(ax, g1x - g[c].x, g[c].x);
+            const float hY = fmaf(ax, g1y - g[c].y, g[c].y);
+            if (tr > 0) {
+                const float I = fmaf(ay, hI - pI, pI);
+                const float X = fmaf(ay, hX - pX, pX);
+                const float Y = fmaf(ay, hY - pY, pY);
+                Xw[tr - 1] = X;
+                Yw[tr - 1] = Y;
+                if (tapcol) {
+                    sxx = fmaf(X, X, sxx);
+                    sxy = fmaf(X, Y, sxy);
+                    syy = fmaf(Y, Y, syy);
+                    cx = fmaf(I, X, cx);
+                    cy = fmaf(I, Y, cy);
+                }
+            }
+            pI = hI;
+            pX = hX;
+            pY = hY;
+        }
+    }
+}
+
+// sum over the window of J(c + (i, j)) (Ix, Iy), J bilinear at fractional
+// offset (bx, by) from the integer centre (jx, jy); per-lane partial sums.
+template <int ST, int WIN>
+__device__ __forceinline__ void correlate_window(const LevelView &J, int jx, int jy, float bx,
+                                                 float by, int lane, bool u8, const float (&Xw)[WIN],
+                                                 const float (&Yw)[WIN], float &sx, float &sy) {
+    constexpr int R = WIN / 2;
+    const bool loader = lane <= WIN;
+    const int tx = clampi(jx + lane - R, 0, J.w - 1);
+    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ph = 0.f;
+#pragma unroll
+    for (int tr = 0; tr <= WIN; ++tr) {
+        const int ty = clampi(jy + tr - R, 0, J.h - 1);
+        const float vt = loader ? texel<ST>(J.img + (int64_t)ty * J.img_pitch, tx, u8) : 0.f;
+        const float v1 = __shfl_down_sync(FULL_MASK, vt, 1);
+        const float h = fmaf(bx, v1 - vt, vt);
+        if (tr > 0) {
+            const float jv = fmaf(by, h - ph, ph);
+            if (tr & 1) {
+                ax0 = fmaf(jv, Xw[tr - 1], ax0);
+                ay0 = fmaf(jv, Yw[tr - 1], ay0);
+            } else {
+                ax1 = fmaf(jv, Xw[tr - 1], ax1);
+                ay1 = fmaf(jv, Yw[tr - 1], ay1);
+            }
+        }
+        ph = h;
+    }
+    const bool tapcol = lane < WIN;
+    sx = tapcol ? ax0 + ax1 : 0.f;
+    sy = tapcol ? ay0 + ay1 : 0.f;
+}
+
+// One level of the pyramidal iteration for one point (the whole warp).
+// Returns the status after this level; nu is the level's increment.
+template <int ST, int WIN>
+__device__ __forceinline__ int track_level(const LevelView &P, const LevelView &J, float px,
+                                           float py, float gx, float gy, int max_iter,
+                                           float eps2, float tau_n, int lane, bool u8, float &nux,
+                                           float &nuy, int &k, bool &conv) {
+    constexpr int R = WIN / 2;
+    const float fpx = floorf(px), fpy = floorf(py);
+    const int ipx = (int)fpx, ipy = (int)fpy;
+    const float ax = px - fpx, ay = py - fpy;
+    float Xw[WIN], Yw[WIN];
+    float sxx, sxy, syy, cx, cy;
+    template_window<ST, WIN>(P, ipx, ipy, ax, ay, lane, u8, Xw, Yw, sxx, sxy, syy, cx, cy);
+    sxx = warp_sum(sxx);
+    sxy = warp_sum(sxy);
+    syy = warp_sum(syy);
+    cx = warp_sum(cx);
+    cy = warp_sum(cy);
+    const float det = det2(sxx, syy, sxy);
+    const float dd = sxx - syy;
+    const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
+    const float lmin = det / lmax;
+    nux = nuy = 0.f;
+    k = 0;
+    conv = false;
+    if (!(lmin >= tau_n) || !(lmin > 0.f)) return OMT_PT_LOST_EIG;
+    while (k < max_iter) {
+        // Centre c = p + g + nu, held as (ipx, ipy) + (ccx, ccy).
+        const float ccx = ax + gx + nux, ccy = ay + gy + nuy;
+        if (!(fabsf(ccx) < 1.0e8f) || !(fabsf(ccy) < 1.0e8f)) return OMT_PT_LOST_OOB;
+        const float fcx = floorf(ccx), fcy = floorf(ccy);
+        const int jx = ipx + (int)fcx, jy = ipy + (int)fcy;
+        const float bx = ccx - fcx, by = ccy - fcy;
+        if (jx < -R || jx > J.w - 1 + R || (jx == J.w - 1 + R && bx > 0.f) || jy < -R ||
+            jy > J.h - 1 + R || (jy == J.h - 1 + R && by > 0.f))
+            return OMT_PT_LOST_OOB;
+        float sx, sy;
+        correlate_window<ST, WIN>(J, jx, jy, bx, by, lane, u8, Xw, Yw, sx, sy);
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
+        const float ex = (syy * bbx - sxy * bby) / det;
+        const float ey = (sxx * bby - sxy * bbx) / det;
+        nux += ex;
+        nuy += ey;
+        ++k;
+        if (ex * ex + ey * ey < eps2) {
+            conv = true;
+            break;
+        }
+    }
+    return OMT_PT_OK;
+}
+
 template <int ST, int WIN>
 __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArgs a) {
-    constexpr int R = WIN / 2;
     const int lane = threadIdx.x & 31;
-    const bool loader = lane <= WIN;  // texel columns 0..WIN
-    const bool tapcol = lane < WIN;   // window columns 0..WIN-1
     int n = a.n_max;
     if (a.n_dev) {
         const int m = *a.n_dev;
@@ -65,115 +221,13 @@ __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArg
         unsigned long long itp = 0ull;  // iterations per level, 8 bits each
 
         for (int L = a.levels - 1; L >= 0; --L) {
-            const LevelView &P = a.P[L];
-            const LevelView &J = a.J[L];
             const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact
-            const float px = u.x * sc, py = u.y * sc;
-            const float fpx = floorf(px), fpy = floorf(py);
-            const int ipx = (int)fpx, ipy = (int)fpy;
-            const float ax = px - fpx, ay = py - fpy;
-
-            // Frame-t window: I, Ix, Iy at p + (i, j), bilinear.
-            float Iw[WIN], Xw[WIN], Yw[WIN];
-            {
-                const int tx = clampi(ipx + lane - R, 0, P.w - 1);
-                float pI = 0.f, pX = 0.f, pY = 0.f;
-#pragma unroll
-                for (int tr = 0; tr <= WIN; ++tr) {
-                    const int ty = clampi(ipy + tr - R, 0, P.h - 1);
-                    float v = 0.f;
-                    float2 g = make_float2(0.f, 0.f);
-                    if (loader) {
-                        v = load_level<ST>(P, L, tx, ty);
-                        g = load_grad<ST>(P, tx, ty);
-                    }
-                    const float v1 = __shfl_down_sync(FULL_MASK, v, 1);
-                    const float g1x = __shfl_down_sync(FULL_MASK, g.x, 1);
-                    const float g1y = __shfl_down_sync(FULL_MASK, g.y, 1);
-                    const float hI = fmaf(ax, v1 - v, v);
-                    const float hX = fmaf(ax, g1x - g.x, g.x);
-                    const float hY = fmaf(ax, g1y - g.y, g.y);
-                    if (tr > 0) {
-                        Iw[tr - 1] = fmaf(ay, hI - pI, pI);
-                        Xw[tr - 1] = fmaf(ay, hX - pX, pX);
-                        Yw[tr - 1] = fmaf(ay, hY - pY, pY);
-                    }
-                    pI = hI;
-                    pX = hX;
-                    pY = hY;
-                }
-            }
-            float sxx = 0.f, sxy = 0.f, syy = 0.f;
-            if (tapcol) {
-#pragma unroll
-                for (int r = 0; r < WIN; ++r) {
-                    sxx = fmaf(Xw[r], Xw[r], sxx);
-                    sxy = fmaf(Xw[r], Yw[r], sxy);
-                    syy = fmaf(Yw[r], Yw[r], syy);
-                }
-            }
-            sxx = warp_sum(sxx);
-            sxy = warp_sum(sxy);
-            syy = warp_sum(syy);
-            const float det = det2(sxx, syy, sxy);
-            const float dd = sxx - syy;
-            const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
-            const float lmin = det / lmax;
-            if (!(lmin >= a.tau_n) || !(lmin > 0.f)) {
-                st = OMT_PT_LOST_EIG;
-                break;
-            }
-
-            float nux = 0.f, nuy = 0.f;
-            int k = 0;
-            bool conv = false;
-            while (k < a.max_iter) {
-                // Centre c = p + g + nu, held as (ipx, ipy) + (cx, cy).
-                const float cx = ax + gx + nux, cy = ay + gy + nuy;
-                if (!(fabsf(cx) < 1.0e8f) || !(fabsf(cy) < 1.0e8f)) {
-                    st = OMT_PT_LOST_OOB;
-                    break;
-                }
-                const float fcx = floorf(cx), fcy = floorf(cy);
-                const int jx = ipx + (int)fcx, jy = ipy + (int)fcy;
-                const float bx = cx - fcx, by = cy - fcy;
-                if (jx < -R || jx > J.w - 1 + R || (jx == J.w - 1 + R && bx > 0.f) ||
-                    jy < -R || jy > J.h - 1 + R || (jy == J.h - 1 + R && by > 0.f)) {
-                    st = OMT_PT_LOST_OOB;
-                    break;
-                }
-                const int txj = clampi(jx + lane - R, 0, J.w - 1);
-                float sbx = 0.f, sby = 0.f, ph = 0.f;
-#pragma unroll
-                for (int tr = 0; tr <= WIN; ++tr) {
-                    const int ty = clampi(jy + tr - R, 0, J.h - 1);
-                    const float v = loader ? load_level<ST>(J, L, txj, ty) : 0.f;
-                    const float v1 = __shfl_down_sync(FULL_MASK, v, 1);
-                    const float hv = fmaf(bx, v1 - v, v);
-                    if (tr > 0) {
-                        const float jv = fmaf(by, hv - ph, ph);
-                        const float dI = Iw[tr - 1] - jv;
-                        sbx = fmaf(dI, Xw[tr - 1], sbx);
-                        sby = fmaf(dI, Yw[tr - 1], sby);
-                    }
-                    ph = hv;
-                }
-                if (!tapcol) {
-                    sbx = 0.f;
-                    sby = 0.f;
-                }
-                sbx = warp_sum(sbx);
-                sby = warp_sum(sby);
-                const float ex = (syy * sbx - sxy * sby) / det;
-                const float ey = (sxx * sby - sxy * sbx) / det;
-                nux += ex;
-                nuy += ey;
-                ++k;
-                if (ex * ex + ey * ey < a.eps2) {
-                    conv = true;
-                    break;
-                }
-            }
+            float nux, nuy;
+            int k;
+            bool conv;
+            st = track_level<ST, WIN>(a.P[L], a.J[L], u.x * sc, u.y * sc, gx, gy,
+                                             a.max_iter, a.eps2, a.tau_n, lane, L == 0, nux, nuy, k,
+                                             conv);
             itp |= (unsigned long long)k << (8 * L);
             if (st != OMT_PT_OK) break;
             if (!conv) nonconv = true;
@@ -248,7 +302,7 @@ cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const fl
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int need = (n_max + LK_WARPS - 1) / LK_WARPS;
-    const int cap = sms * 16;
+    const int cap = sms * 32;
     const int grid = need < cap ? need : cap;
     if (prev.storage == OMT_F32) return launch_st<OMT_F32>(a, prm.win, grid, s);
     return launch_st<OMT_F16>(a, prm.win, grid, s);
