@@ -252,6 +252,66 @@ int omt_update_boxes(const float *boxes, const int32_t *offsets, const float *pt
                      const float *pts_out, const uint8_t *status, int32_t nboxes,
                      const omt_params *prm, float *boxes_out, int32_t *nvalid, void *stream);
 
+/* ---------------------------------------------------------------- batched */
+
+/* Section V-B runs the phases of consecutive frames and of several models
+ * concurrently; the batched form carries that to many independent video
+ * streams: one step moves every stream's boxes from frame t to frame t+1
+ * with one launch per kernel for all streams (a1-a8 in 4 + levels launches).
+ * Each stream keeps its own pyramids, points and boxes resident on the
+ * device; the step is described by a table packed on the host. */
+#define OMT_BATCH_MAX_STREAMS 256
+
+typedef struct omt_batch_stream {
+    const uint8_t *frame;  /* device, frame t+1: h rows of frame_pitch bytes        */
+    size_t frame_pitch;    /* >= w                                                  */
+    omt_pyramid prev;      /* frame t's pyramid (built by an earlier step)          */
+    omt_pyramid next;      /* receives frame t+1's pyramid (same shape as prev)     */
+    const float *boxes;    /* device float4[nboxes], boxes on frame t               */
+    int32_t nboxes;        /* >= 0                                                  */
+    int32_t max_corners;   /* per-box corner cap of this stream, <= caps max        */
+    void *scratch;         /* device, 256-aligned, omt_corner_scratch_bytes(...)    */
+    size_t scratch_bytes;
+    float *pts;            /* device float2[nboxes * max_corners]                   */
+    float *pts_out;        /* device float2[nboxes * max_corners]                   */
+    uint8_t *status;       /* device uint8[nboxes * max_corners]                    */
+    uint8_t *iters;        /* device uint8[nboxes * max_corners * levels] or NULL   */
+    int32_t *offsets;      /* device int32[nboxes + 1] (CSR of pts per box)         */
+    float *boxes_out;      /* device float4[nboxes], must not alias boxes           */
+    int32_t *nvalid;       /* device int32[nboxes] or NULL                          */
+} omt_batch_stream;
+
+/* Capacities a packed table must fit; the launch grids depend on these
+ * only, so one captured CUDA graph serves any membership within them. */
+typedef struct omt_batch_caps {
+    int32_t max_streams;  /* 1..OMT_BATCH_MAX_STREAMS                 */
+    int32_t max_boxes;    /* boxes summed over the streams, >= 0      */
+    int32_t max_w, max_h; /* largest frame                            */
+    int32_t max_corners;  /* largest per-box cap, <= OMT_MAX_CORNERS   */
+} omt_batch_caps;
+
+/* Bytes of a packed table (host) and of its device copy (0 on bad caps). */
+size_t omt_batch_table_bytes(const omt_batch_caps *caps);
+
+/* Host only: validate nstreams stream descriptions against prm and caps and
+ * pack them into `table` (host memory, >= omt_batch_table_bytes).  Every
+ * check of omt_build_pyramid / omt_select_corners / omt_lk_track /
+ * omt_update_boxes applies per stream; the first failure returns OMT_EINVAL
+ * (or OMT_ENOMEM for a short scratch) and leaves `table` unusable. */
+int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_params *prm,
+                   const omt_batch_caps *caps, void *table, size_t table_bytes);
+
+/* One step for every stream of a packed table: copies the table to
+ * dev_table (device, 256-aligned, >= omt_batch_table_bytes) with one
+ * cudaMemcpyAsync on `stream`, then builds every frame t+1 pyramid, selects
+ * every stream's corners on frame t, tracks all points in one persistent
+ * LK launch and updates every box.  Results per stream equal the plain
+ * calls' bit for bit.  `table` is read when the copy executes: keep it
+ * unchanged until then; under stream capture it must be page-locked host
+ * memory, and a replay copies its contents at replay time. */
+int omt_batch_step(const void *table, const omt_batch_caps *caps, const omt_params *prm,
+                   void *dev_table, size_t dev_table_bytes, void *stream);
+
 /* ---------------------------------------------------------------- misc */
 
 const char *omt_error_string(int32_t code);

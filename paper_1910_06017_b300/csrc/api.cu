@@ -176,6 +176,150 @@ int omt_update_boxes(const float *boxes, const int32_t *offsets, const float *pt
                                          (cudaStream_t)stream));
 }
 
+namespace {
+
+bool caps_ok(const omt_batch_caps *c) {
+    return c && c->max_streams >= 1 && c->max_streams <= OMT_BATCH_MAX_STREAMS &&
+           c->max_boxes >= 0 && c->max_w >= 1 && c->max_h >= 1 && c->max_w <= (1 << 16) &&
+           c->max_h <= (1 << 16) && c->max_corners >= 0 && c->max_corners <= OMT_MAX_CORNERS;
+}
+
+void fill_levels(const omt_pyramid &p, LevelView *out) {
+    for (int L = 0; L < OMT_MAX_LEVELS; ++L) out[L] = level_view(p, L < p.levels ? L : 0);
+}
+
+}  // namespace
+
+size_t omt_batch_table_bytes(const omt_batch_caps *caps) {
+    if (!caps_ok(caps)) return 0;
+    return batch_table_bytes(caps->max_streams);
+}
+
+int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_params *prm,
+                   const omt_batch_caps *caps, void *table, size_t table_bytes) {
+    if (omt_validate_params(prm) != OMT_OK || !caps_ok(caps) || !table) return OMT_EINVAL;
+    if (nstreams < 0 || nstreams > caps->max_streams || (nstreams > 0 && !streams))
+        return OMT_EINVAL;
+    if (prm->max_corners > caps->max_corners) return OMT_EINVAL;
+    const size_t need = batch_table_bytes(caps->max_streams);
+    if (table_bytes < need) return OMT_ENOMEM;
+    uint8_t *base = (uint8_t *)table;
+    memset(base, 0, need);
+    BatchHeader &h = *(BatchHeader *)base;
+    h.nstreams = nstreams;
+    h.max_streams = caps->max_streams;
+    h.levels = prm->levels;
+    h.storage = prm->storage;
+    h.win = prm->win;
+    h.max_iter = prm->max_iter;
+    h.qnum = prm->quality_num;
+    h.qden = prm->quality_den;
+    h.aggregator = prm->aggregator;
+    h.eps2 = prm->eps * prm->eps;
+    h.tau_n = prm->min_eig * (float)(prm->win * prm->win);
+    const float md2 = prm->min_dist * prm->min_dist;
+    h.md2c = (int64_t)ceil((double)md2);
+    h.dmax = 0;
+    while ((int64_t)(h.dmax + 1) * (h.dmax + 1) < h.md2c) ++h.dmax;
+    h.cell = 1;
+    while (2 * (int64_t)(h.cell + 1) * (h.cell + 1) <= h.md2c) ++h.cell;
+    h.bytes = (int64_t)need;
+    BatchView v(base);
+    int32_t *pyr_pre[OMT_MAX_LEVELS];
+    for (int L = 0; L < OMT_MAX_LEVELS; ++L) pyr_pre[L] = const_cast<int32_t *>(v.pyr_prefix(L));
+    int32_t *resp_pre = const_cast<int32_t *>(v.resp_prefix());
+    int32_t *box_pre = const_cast<int32_t *>(v.box_prefix());
+    StreamEntry *ent = (StreamEntry *)(base + batch_entries_offset(caps->max_streams));
+    int64_t boxes_total = 0;
+    for (int i = 0; i < nstreams; ++i) {
+        const omt_batch_stream &b = streams[i];
+        const omt_pyramid &P = b.prev, &N = b.next;
+        if (!pyr_ok(&P) || !pyr_ok(&N)) return OMT_EINVAL;
+        if (P.w != N.w || P.h != N.h || P.levels != prm->levels || N.levels != prm->levels ||
+            P.storage != prm->storage || N.storage != prm->storage)
+            return OMT_EINVAL;
+        if (P.base == N.base) return OMT_EINVAL;
+        if (P.w > caps->max_w || P.h > caps->max_h) return OMT_EINVAL;
+        if (!b.frame || b.frame_pitch < (size_t)P.w) return OMT_EINVAL;
+        if (b.nboxes < 0 || b.max_corners < 0 || b.max_corners > caps->max_corners) return OMT_EINVAL;
+        if ((int64_t)b.nboxes * b.max_corners > ((int64_t)1 << 31) - 1) return OMT_EINVAL;
+        if (b.nboxes > 0) {
+            if (!b.boxes || !aligned(b.boxes, 16) || !b.boxes_out || !aligned(b.boxes_out, 16) ||
+                b.boxes == b.boxes_out)
+                return OMT_EINVAL;
+            if (!b.pts || !b.pts_out || !b.status || !aligned(b.pts, 8) || !aligned(b.pts_out, 8))
+                return OMT_EINVAL;
+        }
+        if (!b.offsets || !b.scratch || !aligned(b.scratch, 256)) return OMT_EINVAL;
+        if (b.scratch_bytes < select_scratch_bytes(P.w, P.h, b.nboxes, b.max_corners))
+            return OMT_ENOMEM;
+        StreamEntry &e = ent[i];
+        fill_levels(P, e.P);
+        fill_levels(N, e.P_next);
+        e.frame = b.frame;
+        e.frame_pitch = (int64_t)b.frame_pitch;
+        e.boxes = (const float4 *)b.boxes;
+        e.boxes_out = (float4 *)b.boxes_out;
+        e.nvalid = b.nvalid;
+        e.pts = (float2 *)b.pts;
+        e.pts_out = (float2 *)b.pts_out;
+        e.status = b.status;
+        e.iters = b.iters;
+        e.offsets = b.offsets;
+        uint8_t *sp = (uint8_t *)b.scratch;
+        e.rmap = (uint32_t *)sp;
+        sp += align_up((size_t)P.w * P.h * 4, 256);
+        e.pad_pts = (float2 *)sp;
+        sp += align_up((size_t)b.nboxes * b.max_corners * 8, 256);
+        e.pad_counts = (int32_t *)sp;
+        e.w = P.w;
+        e.h = P.h;
+        e.nboxes = b.nboxes;
+        e.maxc = b.max_corners;
+        for (int L = 0; L < prm->levels; ++L)
+            pyr_pre[L][i + 1] = pyr_pre[L][i] + pyramid_tiles(P.lv[L].w, P.lv[L].h);
+        resp_pre[i + 1] = resp_pre[i] + response_tiles(P.w, P.h);
+        boxes_total += b.nboxes;
+        if (boxes_total > caps->max_boxes) return OMT_EINVAL;
+        box_pre[i + 1] = (int32_t)boxes_total;
+    }
+    h.total_boxes = (int32_t)boxes_total;
+    return OMT_OK;
+}
+
+int omt_batch_step(const void *table, const omt_batch_caps *caps, const omt_params *prm,
+                   void *dev_table, size_t dev_table_bytes, void *stream) {
+    if (omt_validate_params(prm) != OMT_OK || !caps_ok(caps) || !table || !dev_table)
+        return OMT_EINVAL;
+    if (!aligned(dev_table, 256)) return OMT_EINVAL;
+    const size_t need = batch_table_bytes(caps->max_streams);
+    if (dev_table_bytes < need) return OMT_ENOMEM;
+    const BatchHeader &h = *(const BatchHeader *)table;
+    if (h.max_streams != caps->max_streams || h.bytes != (int64_t)need || h.levels != prm->levels ||
+        h.storage != prm->storage || h.win != prm->win || h.max_iter != prm->max_iter ||
+        h.nstreams < 0 || h.nstreams > caps->max_streams || h.total_boxes > caps->max_boxes)
+        return OMT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(dev_table, table, need, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return OMT_ECUDA;
+    const uint8_t *dt = (const uint8_t *)dev_table;
+    int max_tiles[OMT_MAX_LEVELS];
+    int lw = caps->max_w, lh = caps->max_h;
+    for (int L = 0; L < prm->levels; ++L) {
+        max_tiles[L] = caps->max_streams * pyramid_tiles(lw, lh);
+        lw = (lw + 1) >> 1;
+        lh = (lh + 1) >> 1;
+    }
+    e = launch_pyramid_batch(dt, prm->levels, prm->storage, max_tiles, s);
+    if (e != cudaSuccess) return OMT_ECUDA;
+    e = launch_corners_batch(dt, caps->max_streams, caps->max_streams * response_tiles(caps->max_w, caps->max_h),
+                             caps->max_boxes, caps->max_corners, s);
+    if (e != cudaSuccess) return OMT_ECUDA;
+    e = launch_lk_batch(dt, prm->storage, prm->win, s);
+    if (e != cudaSuccess) return OMT_ECUDA;
+    return from_cuda(launch_update_boxes_batch(dt, caps->max_boxes, s));
+}
+
 const char *omt_error_string(int32_t code) {
     switch (code) {
         case OMT_OK: return "success";

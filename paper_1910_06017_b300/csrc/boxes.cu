@@ -108,15 +108,17 @@ __device__ float rank_pick(const float *v, int m, int k, float *s_out) {
     return out;
 }
 
-__global__ void __launch_bounds__(BNT) box_update_kernel(BoxArgs a) {
+// Box b of one stream, whole CTA.
+__device__ void box_update_one(const BoxArgs &a, int b) {
     __shared__ unsigned hist[256];
     __shared__ float red[2][BNT / 32];
     __shared__ int cnt[BNT / 32];
     __shared__ int s_sel, s_k, s_n;
     __shared__ float s_val;
     __shared__ float vx[SMALL], vy[SMALL];
-    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int lo = a.offsets[b], hi = a.offsets[b + 1];
+    __syncthreads();
 
     int m = 0;
     float sx = 0.f, sy = 0.f;
@@ -196,6 +198,21 @@ __global__ void __launch_bounds__(BNT) box_update_kernel(BoxArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(BNT) box_update_kernel(BoxArgs a) { box_update_one(a, blockIdx.x); }
+
+__global__ void __launch_bounds__(BNT) box_update_batch_kernel(const uint8_t *table) {
+    const BatchView t(table);
+    const int32_t *pre = t.box_prefix();
+    const int total = pre[t.nstreams()];
+    for (int gb = blockIdx.x; gb < total; gb += gridDim.x) {
+        const int si = find_segment(pre, t.nstreams(), gb);
+        const StreamEntry &e = t.stream(si);
+        BoxArgs a{e.boxes, e.offsets, e.pts, e.pts_out, e.status, t.hdr().aggregator,
+                  e.boxes_out, e.nvalid};
+        box_update_one(a, gb - pre[si]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_update_boxes(const float4 *boxes, const int32_t *offsets, const float2 *pts,
@@ -205,6 +222,16 @@ cudaError_t launch_update_boxes(const float4 *boxes, const int32_t *offsets, con
     if (nboxes <= 0) return cudaSuccess;
     BoxArgs a{boxes, offsets, pts, pts_out, status, aggregator, boxes_out, nvalid};
     box_update_kernel<<<nboxes, BNT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, cudaStream_t s) {
+    if (max_boxes <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = max_boxes < sms * 8 ? max_boxes : sms * 8;
+    box_update_batch_kernel<<<grid, BNT, 0, s>>>(table);
     return cudaGetLastError();
 }
 

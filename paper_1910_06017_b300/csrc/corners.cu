@@ -61,11 +61,12 @@ __device__ __forceinline__ int px(const RespArgs &a, int x, int y) {
     return (int)__ldg(a.img + (int64_t)y * a.pitch + x);
 }
 
-__global__ void __launch_bounds__(RNT) response_kernel(RespArgs a) {
+// One 32x16 tile of the response map at (ox, oy), whole CTA.
+__device__ __forceinline__ void response_tile(const RespArgs &a, int ox, int oy) {
     __shared__ int2 g[RTY + 4][RTX + 4];
     __shared__ uint32_t R[RTY + 2][RTX + 2];
-    const int ox = blockIdx.x * RTX, oy = blockIdx.y * RTY;
     const int tid = threadIdx.x;
+    __syncthreads();
 
     if (a.boxes) {
         // Skip tiles that hold no eligible pixel of any box.
@@ -133,6 +134,32 @@ __global__ void __launch_bounds__(RNT) response_kernel(RespArgs a) {
             flag = m ? MAX_FLAG : 0u;
         }
         a.out[(int64_t)y * a.w + x] = v | flag;
+    }
+}
+
+__global__ void __launch_bounds__(RNT) response_kernel(RespArgs a) {
+    response_tile(a, blockIdx.x * RTX, blockIdx.y * RTY);
+}
+
+__global__ void __launch_bounds__(RNT) response_batch_kernel(const uint8_t *table) {
+    const BatchView t(table);
+    const int32_t *pre = t.resp_prefix();
+    const int total = pre[t.nstreams()];
+    for (int gi = blockIdx.x; gi < total; gi += gridDim.x) {
+        const int si = find_segment(pre, t.nstreams(), gi);
+        const StreamEntry &e = t.stream(si);
+        RespArgs a;
+        a.img = e.P[0].img;
+        a.pitch = e.P[0].img_pitch;
+        a.w = e.w;
+        a.h = e.h;
+        a.out = e.rmap;
+        a.boxes = e.boxes;
+        a.nboxes = e.nboxes;
+        const int tiles_x = (e.w + RTX - 1) / RTX;
+        const int local = gi - pre[si];
+        const int ty = local / tiles_x, tx = local - ty * tiles_x;
+        response_tile(a, tx * RTX, ty * RTY);
     }
 }
 
@@ -248,15 +275,18 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
     if (lane == 0) *s_nacc = nacc;
 }
 
-__global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
+// Corners of one box, whole CTA.  Shared memory: keys[SCAP] | acc[acc_cap]
+// | cells[GCAP] in the dynamic area.
+__device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *keys = (uint64_t *)smem;
     int2 *acc = (int2 *)(keys + SCAP);
-    int16_t *cells = (int16_t *)(acc + a.maxc);
+    int16_t *cells = (int16_t *)(acc + acc_cap);
     __shared__ unsigned hist[256];
     __shared__ int s_count, s_nacc, s_sel, s_k;
     __shared__ uint32_t s_rmax;
-    const int box = blockIdx.x, tid = threadIdx.x;
+    const int tid = threadIdx.x;
+    __syncthreads();
 
     int xlo, xhi, ylo, yhi;
     if (!box_pixel_range(a.boxes[box], a.w, a.h, xlo, xhi, ylo, yhi) || a.maxc == 0) {
@@ -397,12 +427,41 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
     if (tid == 0) a.pad_counts[box] = s_nacc;
 }
 
+__global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
+    select_box(a, blockIdx.x, a.maxc);
+}
+
+__global__ void __launch_bounds__(SNT) select_batch_kernel(const uint8_t *table, int acc_cap) {
+    const BatchView t(table);
+    const BatchHeader &h = t.hdr();
+    const int32_t *pre = t.box_prefix();
+    const int total = pre[t.nstreams()];
+    for (int gb = blockIdx.x; gb < total; gb += gridDim.x) {
+        const int si = find_segment(pre, t.nstreams(), gb);
+        const StreamEntry &e = t.stream(si);
+        SelectArgs a;
+        a.rmap = e.rmap;
+        a.w = e.w;
+        a.h = e.h;
+        a.boxes = e.boxes;
+        a.maxc = e.maxc;
+        a.qnum = h.qnum;
+        a.qden = h.qden;
+        a.md2c = h.md2c;
+        a.dmax = h.dmax;
+        a.cell = h.cell;
+        a.pad_pts = e.pad_pts;
+        a.pad_counts = e.pad_counts;
+        select_box(a, gb - pre[si], acc_cap);
+    }
+}
+
 // ----------------------------------------------------------- compact kernel
 constexpr int CNT = 1024;
 
-__global__ void __launch_bounds__(CNT) compact_kernel(const int32_t *pad_counts,
-                                                      const float2 *pad_pts, int nboxes,
-                                                      int maxc, float2 *pts, int32_t *offsets) {
+__device__ __forceinline__ void compact_stream(const int32_t *pad_counts, const float2 *pad_pts,
+                                               int nboxes, int maxc, float2 *pts,
+                                               int32_t *offsets) {
     __shared__ int warp_tot[CNT / 32];
     __shared__ int s_carry;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -442,6 +501,20 @@ __global__ void __launch_bounds__(CNT) compact_kernel(const int32_t *pad_counts,
         const int c = pad_counts[b], o = offsets[b];
         for (int i = lane; i < c; i += 32) pts[o + i] = pad_pts[(int64_t)b * maxc + i];
     }
+}
+
+__global__ void __launch_bounds__(CNT) compact_kernel(const int32_t *pad_counts,
+                                                      const float2 *pad_pts, int nboxes,
+                                                      int maxc, float2 *pts, int32_t *offsets) {
+    compact_stream(pad_counts, pad_pts, nboxes, maxc, pts, offsets);
+}
+
+__global__ void __launch_bounds__(CNT) compact_batch_kernel(const uint8_t *table) {
+    const BatchView t(table);
+    const int si = blockIdx.x;
+    if (si >= t.nstreams()) return;
+    const StreamEntry &e = t.stream(si);
+    compact_stream(e.pad_counts, e.pad_pts, e.nboxes, e.maxc, e.pts, e.offsets);
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -507,6 +580,34 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
         if (e != cudaSuccess) return e;
     }
     compact_kernel<<<1, CNT, 0, s>>>(pad_counts, pad_pts, nboxes, prm.max_corners, pts, offsets);
+    return cudaGetLastError();
+}
+
+int response_tiles(int w, int h) { return ((w + RTX - 1) / RTX) * ((h + RTY - 1) / RTY); }
+
+cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_resp_tiles,
+                                 int max_boxes, int max_corners, cudaStream_t s) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = max_resp_tiles < sms * 8 ? max_resp_tiles : sms * 8;
+    response_batch_kernel<<<grid > 0 ? grid : 1, RNT, 0, s>>>(table);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (max_boxes > 0) {
+        const size_t smem = (size_t)SCAP * 8 + (size_t)max_corners * 8 + (size_t)GCAP * 2;
+        e = cudaFuncSetAttribute(select_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_batch_kernel, SNT, smem);
+        if (per_sm < 1) per_sm = 1;
+        grid = max_boxes < sms * per_sm ? max_boxes : sms * per_sm;
+        select_batch_kernel<<<grid, SNT, smem, s>>>(table, max_corners);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    compact_batch_kernel<<<max_streams > 0 ? max_streams : 1, CNT, 0, s>>>(table);
     return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ __device__ __forceinline__ void template_window(const LevelView &P, int ipx, int
     const bool loader = lane <= WIN, tapcol = lane < WIN;
     const int tx = clampi(ipx + lane - R, 0, P.w - 1);
     float pI = 0.f, pX = 0.f, pY = 0.f;
-    sxx = sxy = syy = cx = cy = 0.f;
+    float cx0 = 0.f, cy0 = 0.f, cx1 = 0.f, cy1 = 0.f;
+    sxx = sxy = syy = 0.f;
 #pragma unroll
     for (int t0 = 0; t0 <= WIN; t0 += CH) {
         float v[CH];
@@ -101,12 +102,17 @@ __device__ __forceinline__ void template_window(const LevelView &P, int ipx, int
                 const float Y = fmaf(ay, hY - pY, pY);
                 Xw[tr - 1] = X;
                 Yw[tr - 1] = Y;
-                if (tapcol) {
-                    sxx = fmaf(X, X, sxx);
-                    sxy = fmaf(X, Y, sxy);
-                    syy = fmaf(Y, Y, syy);
-                    cx = fmaf(I, X, cx);
-                    cy = fmaf(I, Y, cy);
+                sxx = fmaf(X, X, sxx);
+                sxy = fmaf(X, Y, sxy);
+                syy = fmaf(Y, Y, syy);
+                // Same two chains as correlate_window, so that J == I gives
+                // c - sum J grad I == 0 exactly (zero flow on equal frames).
+                if (tr & 1) {
+                    cx0 = fmaf(I, X, cx0);
+                    cy0 = fmaf(I, Y, cy0);
+                } else {
+                    cx1 = fmaf(I, X, cx1);
+                    cy1 = fmaf(I, Y, cy1);
                 }
             }
             pI = hI;
@@ -114,6 +120,9 @@ __device__ __forceinline__ void template_window(const LevelView &P, int ipx, int
             pY = hY;
         }
     }
+    if (!tapcol) sxx = sxy = syy = 0.f;
+    cx = tapcol ? cx0 + cx1 : 0.f;
+    cy = tapcol ? cy0 + cy1 : 0.f;
 }
 
 // sum over the window of J(c + (i, j)) (Ix, Iy), J bilinear at fractional
@@ -204,57 +213,94 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     return OMT_PT_OK;
 }
 
+// The whole pyramidal iteration for one point u (the whole warp); P, J are
+// the frame-t and frame-(t+1) level views.  Writes pts_out / status / iters
+// entry i.
+template <int ST, int WIN>
+__device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
+                                         int max_iter, float eps2, float tau_n, float2 u,
+                                         int i, float2 *out, uint8_t *status, uint8_t *iters) {
+    const int lane = threadIdx.x & 31;
+    float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
+    int st = OMT_PT_OK;
+    bool nonconv = false;
+    unsigned long long itp = 0ull;  // iterations per level, 8 bits each
+
+    for (int L = levels - 1; L >= 0; --L) {
+        const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact
+        float nux, nuy;
+        int k;
+        bool conv;
+        st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
+                                  lane, L == 0, nux, nuy, k, conv);
+        itp |= (unsigned long long)k << (8 * L);
+        if (st != OMT_PT_OK) break;
+        if (!conv) nonconv = true;
+        if (L > 0) {
+            gx = 2.0f * (gx + nux);
+            gy = 2.0f * (gy + nuy);
+        } else {
+            dx = gx + nux;
+            dy = gy + nuy;
+        }
+    }
+
+    float2 v = u;
+    if (st == OMT_PT_OK) {
+        const float ox = u.x + dx, oy = u.y + dy;
+        if (!(ox >= 0.f && ox <= (float)(P[0].w - 1) && oy >= 0.f && oy <= (float)(P[0].h - 1)))
+            st = OMT_PT_LOST_OOB;
+        else
+            v = make_float2(ox, oy);
+    }
+    if (st == OMT_PT_OK && nonconv) st |= OMT_PT_NONCONV;
+    if (lane == 0) {
+        out[i] = v;
+        status[i] = (uint8_t)st;
+    }
+    if (iters && lane < levels) iters[(int64_t)i * levels + lane] = (uint8_t)(itp >> (8 * lane));
+}
+
 template <int ST, int WIN>
 __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArgs a) {
-    const int lane = threadIdx.x & 31;
     int n = a.n_max;
     if (a.n_dev) {
         const int m = *a.n_dev;
         n = m < n ? m : n;
     }
     const int nwarps = gridDim.x * LK_WARPS;
-    for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
-        const float2 u = a.pts[i];
-        float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
-        int st = OMT_PT_OK;
-        bool nonconv = false;
-        unsigned long long itp = 0ull;  // iterations per level, 8 bits each
+    for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps)
+        lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
+                          a.status, a.iters);
+}
 
-        for (int L = a.levels - 1; L >= 0; --L) {
-            const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact
-            float nux, nuy;
-            int k;
-            bool conv;
-            st = track_level<ST, WIN>(a.P[L], a.J[L], u.x * sc, u.y * sc, gx, gy,
-                                             a.max_iter, a.eps2, a.tau_n, lane, L == 0, nux, nuy, k,
-                                             conv);
-            itp |= (unsigned long long)k << (8 * L);
-            if (st != OMT_PT_OK) break;
-            if (!conv) nonconv = true;
-            if (L > 0) {
-                gx = 2.0f * (gx + nux);
-                gy = 2.0f * (gy + nuy);
-            } else {
-                dx = gx + nux;
-                dy = gy + nuy;
-            }
+// All points of all streams of a batch: the per-stream counts come from the
+// CSR offsets written by the corner step; each CTA forms their prefix in
+// shared memory and its warps stride over the concatenated index space.
+template <int ST, int WIN>
+__global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
+    __shared__ int32_t pre[OMT_BATCH_MAX_STREAMS + 1];
+    const BatchView t(table);
+    const BatchHeader &h = t.hdr();
+    const int ns = h.nstreams;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        pre[0] = 0;
+        for (int s = 0; s < ns; ++s) {
+            const StreamEntry &e = t.stream(s);
+            acc += e.offsets[e.nboxes];
+            pre[s + 1] = acc;
         }
-
-        float2 v = u;
-        if (st == OMT_PT_OK) {
-            const float ox = u.x + dx, oy = u.y + dy;
-            if (!(ox >= 0.f && ox <= (float)(a.P[0].w - 1) && oy >= 0.f && oy <= (float)(a.P[0].h - 1)))
-                st = OMT_PT_LOST_OOB;
-            else
-                v = make_float2(ox, oy);
-        }
-        if (st == OMT_PT_OK && nonconv) st |= OMT_PT_NONCONV;
-        if (lane == 0) {
-            a.out[i] = v;
-            a.status[i] = (uint8_t)st;
-        }
-        if (a.iters && lane < a.levels)
-            a.iters[(int64_t)i * a.levels + lane] = (uint8_t)(itp >> (8 * lane));
+    }
+    __syncthreads();
+    const int total = pre[ns];
+    const int nwarps = gridDim.x * LK_WARPS;
+    for (int g = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); g < total; g += nwarps) {
+        const int s = find_segment(pre, ns, g);
+        const StreamEntry &e = t.stream(s);
+        const int i = g - pre[s];
+        lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
+                          e.pts_out, e.status, e.iters);
     }
 }
 
@@ -272,7 +318,37 @@ cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int ST, int WIN>
+cudaError_t launch_batch_win(const uint8_t *table, int sms, cudaStream_t s) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lk_batch_kernel<ST, WIN>, LK_NT, 0);
+    if (per_sm < 1) per_sm = 1;
+    lk_batch_kernel<ST, WIN><<<sms * per_sm, LK_NT, 0, s>>>(table);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t launch_batch_st(const uint8_t *table, int win, int sms, cudaStream_t s) {
+    switch (win) {
+#define OMT_LK_CASE(W) \
+    case W: return launch_batch_win<ST, W>(table, sms, s);
+        OMT_LK_CASE(3) OMT_LK_CASE(5) OMT_LK_CASE(7) OMT_LK_CASE(9) OMT_LK_CASE(11)
+        OMT_LK_CASE(13) OMT_LK_CASE(15) OMT_LK_CASE(17) OMT_LK_CASE(19) OMT_LK_CASE(21)
+        OMT_LK_CASE(23) OMT_LK_CASE(25) OMT_LK_CASE(27) OMT_LK_CASE(29) OMT_LK_CASE(31)
+#undef OMT_LK_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, cudaStream_t s) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (storage == OMT_F32) return launch_batch_st<OMT_F32>(table, win, sms, s);
+    return launch_batch_st<OMT_F16>(table, win, sms, s);
+}
 
 cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const float2 *pts,
                       int n_max, const int32_t *n_dev, const omt_params &prm, float2 *out,

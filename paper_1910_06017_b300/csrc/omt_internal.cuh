@@ -89,6 +89,73 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// ------------------------------------------------------------ batch table
+// Device-side description of a batched step (one entry per stream), packed
+// on the host by omt_batch_pack and copied to the device by omt_batch_step.
+// Layout: BatchHeader | int32 pyr_prefix[OMT_MAX_LEVELS][S+1] |
+// int32 resp_prefix[S+1] | int32 box_prefix[S+1] | StreamEntry[S], with S =
+// the capacity in streams; prefixes count tiles or boxes per stream.
+struct StreamEntry {
+    LevelView P[OMT_MAX_LEVELS];       // frame t's pyramid (read)
+    LevelView P_next[OMT_MAX_LEVELS];  // frame t+1's pyramid (K1 writes, K3 reads)
+    const uint8_t *frame;              // frame t+1 (u8)
+    int64_t frame_pitch;
+    const float4 *boxes;
+    float4 *boxes_out;
+    int32_t *nvalid;
+    float2 *pts, *pts_out;
+    uint8_t *status, *iters;
+    int32_t *offsets;
+    uint32_t *rmap;                    // scratch: response map
+    float2 *pad_pts;                   // scratch: per-box corner lists
+    int32_t *pad_counts;               // scratch: per-box counts
+    int32_t w, h, nboxes, maxc;
+};
+
+struct BatchHeader {
+    int32_t nstreams, max_streams, total_boxes, levels, storage, win, max_iter;
+    int32_t qnum, qden, aggregator, dmax, cell;
+    float eps2, tau_n;
+    int64_t md2c;
+    int64_t bytes;  // size of the packed table
+};
+
+__host__ __device__ inline size_t batch_entries_offset(int max_streams) {
+    size_t off = sizeof(BatchHeader) + sizeof(int32_t) * (size_t)(OMT_MAX_LEVELS + 2) * (max_streams + 1);
+    return (off + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t batch_table_bytes(int max_streams) {
+    return batch_entries_offset(max_streams) + sizeof(StreamEntry) * (size_t)max_streams;
+}
+
+struct BatchView {
+    const uint8_t *base;
+    __host__ __device__ explicit BatchView(const uint8_t *b) : base(b) {}
+    __host__ __device__ const BatchHeader &hdr() const { return *(const BatchHeader *)base; }
+    __host__ __device__ int nstreams() const { return hdr().nstreams; }
+    __host__ __device__ int levels() const { return hdr().levels; }
+    __host__ __device__ const int32_t *pyr_prefix(int L) const {
+        return (const int32_t *)(base + sizeof(BatchHeader)) + (size_t)L * (hdr().max_streams + 1);
+    }
+    __host__ __device__ const int32_t *resp_prefix() const { return pyr_prefix(OMT_MAX_LEVELS); }
+    __host__ __device__ const int32_t *box_prefix() const { return pyr_prefix(OMT_MAX_LEVELS + 1); }
+    __host__ __device__ const StreamEntry &stream(int s) const {
+        return ((const StreamEntry *)(base + batch_entries_offset(hdr().max_streams)))[s];
+    }
+};
+
+// Segment s of a prefix array (pre[0] = 0, non-decreasing, n segments) that
+// holds item g < pre[n]: the last s with pre[s] <= g (empty segments skipped).
+__host__ __device__ __forceinline__ int find_segment(const int32_t *pre, int n, int g) {
+    int lo = 0, hi = n;  // pre[lo] <= g < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------- launchers
 // Each returns the cudaError_t of cudaGetLastError() after its launches.
 
@@ -103,6 +170,17 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
                                   int32_t *offsets, cudaStream_t s);
 
 size_t select_scratch_bytes(int w, int h, int nboxes, int max_corners);
+
+// Batched forms: every launch covers all streams of the table in `table`
+// (device memory); grids depend only on the capacities.
+int pyramid_tiles(int w, int h);   // K1 tiles of a level of this size
+int response_tiles(int w, int h);  // K2 response tiles of a frame of this size
+cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
+                                 cudaStream_t s);
+cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_resp_tiles,
+                                 int max_boxes, int max_corners, cudaStream_t s);
+cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, cudaStream_t s);
+cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, cudaStream_t s);
 
 cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const float2 *pts,
                       int n_max, const int32_t *n_dev, const omt_params &prm, float2 *out,

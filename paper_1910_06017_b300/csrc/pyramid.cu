@@ -40,12 +40,49 @@ __device__ __forceinline__ float load_src(const LevelArgs &a, int x, int y) {
     return __half2float(((const __half *)row)[x]) + 128.0f;
 }
 
+// Arguments of level L of the pyramid a batch entry builds (frame t+1).
+__device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int L, int levels,
+                                                      LevelArgs &a) {
+    const LevelView &v = e.P_next[L];
+    a.level = L;
+    a.w = v.w;
+    a.h = v.h;
+    if (L == 0) {
+        a.src = e.frame;
+        a.src_pitch = e.frame_pitch;
+        a.copy = const_cast<uint8_t *>(v.img);
+        a.copy_pitch = v.img_pitch;
+    } else {
+        a.src = v.img;
+        a.src_pitch = v.img_pitch;
+        a.copy = nullptr;
+        a.copy_pitch = 0;
+    }
+    a.grad = const_cast<uint8_t *>(v.grad);
+    a.grad_pitch = v.grad_pitch;
+    if (L + 1 < levels) {
+        const LevelView &n = e.P_next[L + 1];
+        a.next = const_cast<uint8_t *>(n.img);
+        a.next_pitch = n.img_pitch;
+        a.nw = n.w;
+        a.nh = n.h;
+    } else {
+        a.next = nullptr;
+        a.next_pitch = 0;
+        a.nw = a.nh = 0;
+    }
+}
+
+// One 64x16 tile of level L at (ox, oy): gradients of the tile and the
+// 32x8 tile of level L+1 that decimates it.  Callers loop over tiles with
+// the whole CTA; the leading barrier keeps tiles from overlapping in the
+// shared arrays.
 template <int ST>
-__global__ void __launch_bounds__(NT) pyramid_level_kernel(LevelArgs a) {
+__device__ __forceinline__ void pyramid_tile(const LevelArgs &a, int ox, int oy) {
     __shared__ float s[SY][SX];
     __shared__ float hs[SY][TX / 2];
-    const int ox = blockIdx.x * TX, oy = blockIdx.y * TY;
     const int tid = threadIdx.x;
+    __syncthreads();
 
     // Stage level L with a reflect-101 halo of 2.
     for (int i = tid; i < SX * SY; i += NT) {
@@ -80,26 +117,50 @@ __global__ void __launch_bounds__(NT) pyramid_level_kernel(LevelArgs a) {
         if (ST == OMT_F32) ((float2 *)row)[x] = make_float2(gx, gy);
         else ((__half2 *)row)[x] = __floats2half2_rn(gx, gy);
     }
-    if (!a.next) return;
-
-    // Binomial reduce to level L+1: horizontal pass at the even columns...
-    for (int i = tid; i < SY * (TX / 2); i += NT) {
-        const int r = i / (TX / 2), X = i - r * (TX / 2);
-        const int c = 2 * X + 2;
-        hs[r][X] = (s[r][c - 2] + s[r][c + 2]) + 4.0f * (s[r][c - 1] + s[r][c + 1]) + 6.0f * s[r][c];
+    if (a.next) {
+        // Binomial reduce to level L+1: horizontal pass at the even columns...
+        for (int i = tid; i < SY * (TX / 2); i += NT) {
+            const int r = i / (TX / 2), X = i - r * (TX / 2);
+            const int c = 2 * X + 2;
+            hs[r][X] = (s[r][c - 2] + s[r][c + 2]) + 4.0f * (s[r][c - 1] + s[r][c + 1]) + 6.0f * s[r][c];
+        }
+        __syncthreads();
+        // ...then vertical at the even rows, scaled by 1/256.
+        for (int i = tid; i < (TX / 2) * (TY / 2); i += NT) {
+            const int Y = i / (TX / 2), X = i - Y * (TX / 2);
+            const int gXo = ox / 2 + X, gYo = oy / 2 + Y;
+            if (gXo >= a.nw || gYo >= a.nh) continue;
+            const int r = 2 * Y + 2;
+            float v = (hs[r - 2][X] + hs[r + 2][X]) + 4.0f * (hs[r - 1][X] + hs[r + 1][X]) + 6.0f * hs[r][X];
+            v *= (1.0f / 256.0f);
+            uint8_t *row = a.next + (int64_t)gYo * a.next_pitch;
+            if (ST == OMT_F32) ((float *)row)[gXo] = v;
+            else ((__half *)row)[gXo] = __float2half_rn(v - 128.0f);
+        }
     }
-    __syncthreads();
-    // ...then vertical at the even rows, scaled by 1/256.
-    for (int i = tid; i < (TX / 2) * (TY / 2); i += NT) {
-        const int Y = i / (TX / 2), X = i - Y * (TX / 2);
-        const int gXo = ox / 2 + X, gYo = oy / 2 + Y;
-        if (gXo >= a.nw || gYo >= a.nh) continue;
-        const int r = 2 * Y + 2;
-        float v = (hs[r - 2][X] + hs[r + 2][X]) + 4.0f * (hs[r - 1][X] + hs[r + 1][X]) + 6.0f * hs[r][X];
-        v *= (1.0f / 256.0f);
-        uint8_t *row = a.next + (int64_t)gYo * a.next_pitch;
-        if (ST == OMT_F32) ((float *)row)[gXo] = v;
-        else ((__half *)row)[gXo] = __float2half_rn(v - 128.0f);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(NT) pyramid_level_kernel(LevelArgs a) {
+    pyramid_tile<ST>(a, blockIdx.x * TX, blockIdx.y * TY);
+}
+
+// Level L of every stream of a batch: a grid-stride loop over the batch's
+// tiles (tile prefix per stream in the table).
+template <int ST>
+__global__ void __launch_bounds__(NT) pyramid_batch_kernel(const uint8_t *table, int L) {
+    const BatchView t(table);
+    const int *pre = t.pyr_prefix(L);
+    const int total = pre[t.nstreams()];
+    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+        const int si = find_segment(pre, t.nstreams(), g);
+        const StreamEntry &e = t.stream(si);
+        const int tiles_x = (e.P_next[L].w + TX - 1) / TX;
+        const int local = g - pre[si];
+        const int ty = local / tiles_x, tx = local - ty * tiles_x;
+        LevelArgs a;
+        level_args_from_entry(e, L, t.levels(), a);
+        pyramid_tile<ST>(a, tx * TX, ty * TY);
     }
 }
 
@@ -145,5 +206,23 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
     }
     return cudaSuccess;
 }
+
+cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
+                                 cudaStream_t s) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int L = 0; L < levels; ++L) {
+        const int cap = sms * 8;
+        const int grid = max_tiles[L] < cap ? (max_tiles[L] > 0 ? max_tiles[L] : 1) : cap;
+        if (storage == OMT_F32) pyramid_batch_kernel<OMT_F32><<<grid, NT, 0, s>>>(table, L);
+        else pyramid_batch_kernel<OMT_F16><<<grid, NT, 0, s>>>(table, L);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int pyramid_tiles(int w, int h) { return ((w + TX - 1) / TX) * ((h + TY - 1) / TY); }
 
 }  // namespace omt

@@ -24,8 +24,10 @@ EXPORTED = [
     "omt_default_params", "omt_validate_params", "omt_pyramid_bytes", "omt_pyramid_init",
     "omt_build_pyramid", "omt_corner_response", "omt_corner_scratch_bytes",
     "omt_select_corners", "omt_lk_track", "omt_update_boxes", "omt_error_string",
-    "omt_version", "omt_select_corners_static",
+    "omt_version", "omt_select_corners_static", "omt_batch_table_bytes", "omt_batch_pack",
+    "omt_batch_step",
 ]
+BATCH_MAX_STREAMS = 256
 STATIC_SCRATCH_BYTES = 16 << 20
 
 
@@ -62,6 +64,20 @@ class PyramidDesc(Structure):
                 ("base", c_void_p), ("bytes", c_size_t), ("lv", Level * MAX_LEVELS)]
 
 
+class BatchStream(Structure):
+    _fields_ = [("frame", c_void_p), ("frame_pitch", c_size_t), ("prev", PyramidDesc),
+                ("next", PyramidDesc), ("boxes", c_void_p), ("nboxes", c_int32),
+                ("max_corners", c_int32), ("scratch", c_void_p), ("scratch_bytes", c_size_t),
+                ("pts", c_void_p), ("pts_out", c_void_p), ("status", c_void_p),
+                ("iters", c_void_p), ("offsets", c_void_p), ("boxes_out", c_void_p),
+                ("nvalid", c_void_p)]
+
+
+class BatchCaps(Structure):
+    _fields_ = [("max_streams", c_int32), ("max_boxes", c_int32), ("max_w", c_int32),
+                ("max_h", c_int32), ("max_corners", c_int32)]
+
+
 _lib = None
 
 
@@ -92,6 +108,12 @@ def lib():
         L.omt_error_string.argtypes = [c_int32]
         L.omt_error_string.restype = ctypes.c_char_p
         L.omt_version.restype = c_int32
+        L.omt_batch_table_bytes.argtypes = [POINTER(BatchCaps)]
+        L.omt_batch_table_bytes.restype = c_size_t
+        L.omt_batch_pack.argtypes = [POINTER(BatchStream), c_int32, POINTER(Params),
+                                     POINTER(BatchCaps), c_void_p, c_size_t]
+        L.omt_batch_step.argtypes = [c_void_p, POINTER(BatchCaps), POINTER(Params), c_void_p,
+                                     c_size_t, c_void_p]
         _lib = L
     return _lib
 
@@ -268,3 +290,133 @@ class StreamTracker:
                      self.boxes_out[:nb], self.nvalid[:nb], stream)
         self.cur = 1 - self.cur
         return self.boxes_out[:nb]
+
+
+# ------------------------------------------------------------------ batched
+
+def batch_table_bytes(caps: BatchCaps) -> int:
+    return int(lib().omt_batch_table_bytes(ctypes.byref(caps)))
+
+
+def batch_pack(streams, params: Params, caps: BatchCaps, table):
+    """streams: sequence of BatchStream; table: host uint8 tensor (pinned for graphs)."""
+    arr = (BatchStream * max(1, len(streams)))(*streams)
+    _check(lib().omt_batch_pack(arr, len(streams), ctypes.byref(params), ctypes.byref(caps),
+                                ctypes.c_void_p(table.data_ptr()), table.numel()), "omt_batch_pack")
+
+
+def batch_step(table, caps: BatchCaps, params: Params, dev_table, stream=None):
+    _check(lib().omt_batch_step(ctypes.c_void_p(table.data_ptr()), ctypes.byref(caps),
+                                ctypes.byref(params), _ptr(dev_table), dev_table.numel(),
+                                _stream(stream)), "omt_batch_step")
+
+
+class BatchTracker:
+    """Many independent streams advanced by one omt_batch_step per step.
+
+    Every stream keeps, resident on the device, two pyramids that swap roles
+    (frame t, frame t+1), a frame slot for the next frame, its input and
+    output boxes, point buffers and corner scratch.  Two tables (one per
+    pyramid parity) are packed once into page-locked host memory; a step
+    copies the right one to the device and runs 4 + levels launches for all
+    streams.  With graph=True each parity's step is captured once in a CUDA
+    graph and replayed (the table copy is a node of the graph).
+    """
+
+    def __init__(self, sizes, params: Params, max_boxes, max_corners=None, device="cuda",
+                 with_iters: bool = True):
+        import torch
+        self.params = params
+        self.device = torch.device(device)
+        n = len(sizes)
+        if isinstance(max_boxes, int):
+            max_boxes = [max_boxes] * n
+        if max_corners is None:
+            max_corners = [params.max_corners] * n
+        elif isinstance(max_corners, int):
+            max_corners = [max_corners] * n
+        self.sizes, self.max_boxes, self.max_corners = list(sizes), list(max_boxes), list(max_corners)
+        self.caps = BatchCaps(n, int(sum(max_boxes)), max(w for w, _ in sizes),
+                              max(h for _, h in sizes), max(max(max_corners), params.max_corners))
+        dev = self.device
+        self.pyr, self.frame, self.boxes, self.boxes_out = [], [], [], []
+        self.pts, self.pts_out, self.status, self.iters, self.offsets, self.nvalid = [], [], [], [], [], []
+        self.scratch, self.nboxes = [], [0] * n
+        for (w, h), nb, mc in zip(sizes, max_boxes, max_corners):
+            self.pyr.append([Pyramid(w, h, params.levels, params.storage, dev),
+                             Pyramid(w, h, params.levels, params.storage, dev)])
+            self.frame.append(torch.zeros((h, w), dtype=torch.uint8, device=dev))
+            cap = max(1, nb * mc)
+            self.boxes.append(torch.zeros((max(1, nb), 4), dtype=torch.float32, device=dev))
+            self.boxes_out.append(torch.zeros((max(1, nb), 4), dtype=torch.float32, device=dev))
+            self.pts.append(torch.zeros((cap, 2), dtype=torch.float32, device=dev))
+            self.pts_out.append(torch.zeros((cap, 2), dtype=torch.float32, device=dev))
+            self.status.append(torch.zeros(cap, dtype=torch.uint8, device=dev))
+            self.iters.append(torch.zeros((cap, params.levels), dtype=torch.uint8, device=dev)
+                              if with_iters else None)
+            self.offsets.append(torch.zeros(nb + 1, dtype=torch.int32, device=dev))
+            self.nvalid.append(torch.zeros(max(1, nb), dtype=torch.int32, device=dev))
+            self.scratch.append(torch.empty(corner_scratch_bytes(w, h, nb, mc), dtype=torch.uint8,
+                                            device=dev))
+        nbytes = batch_table_bytes(self.caps)
+        self.tables = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+        self.dev_table = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.cur = 0
+        self.graphs = [None, None]
+
+    def _desc(self, s: int, parity: int) -> BatchStream:
+        d = BatchStream()
+        f = self.frame[s]
+        d.frame, d.frame_pitch = f.data_ptr(), f.stride(0)
+        d.prev = self.pyr[s][parity].desc
+        d.next = self.pyr[s][1 - parity].desc
+        d.boxes = self.boxes[s].data_ptr()
+        d.nboxes = self.nboxes[s]
+        d.max_corners = self.max_corners[s]
+        d.scratch, d.scratch_bytes = self.scratch[s].data_ptr(), self.scratch[s].numel()
+        d.pts, d.pts_out = self.pts[s].data_ptr(), self.pts_out[s].data_ptr()
+        d.status = self.status[s].data_ptr()
+        d.iters = self.iters[s].data_ptr() if self.iters[s] is not None else None
+        d.offsets = self.offsets[s].data_ptr()
+        d.boxes_out, d.nvalid = self.boxes_out[s].data_ptr(), self.nvalid[s].data_ptr()
+        return d
+
+    def set_boxes(self, s: int, boxes):
+        """Boxes of stream s on frame t (device or host tensor (nb, 4))."""
+        nb = boxes.shape[0]
+        assert nb <= self.max_boxes[s]
+        if nb:
+            self.boxes[s][:nb].copy_(boxes, non_blocking=True)
+        self.nboxes[s] = nb
+        self.graphs = [None, None]
+
+    def pack(self):
+        for parity in range(2):
+            batch_pack([self._desc(s, parity) for s in range(len(self.sizes))], self.params,
+                       self.caps, self.tables[parity])
+
+    def prime(self, s: int, frame, stream=None):
+        """Build stream s's frame-t pyramid from a u8 device frame."""
+        build_pyramid(frame, self.pyr[s][self.cur], self.params, stream)
+
+    def capture(self):
+        """Capture each parity's step in a CUDA graph (after one eager step)."""
+        import torch
+        self.pack()
+        self.graphs = [None, None]
+        for parity in range(2):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                batch_step(self.tables[parity], self.caps, self.params, self.dev_table)
+            self.graphs[parity] = g
+
+    def step(self, stream=None):
+        """Advance every stream: frame slots hold frame t+1, boxes frame t's."""
+        if self.graphs[self.cur] is not None:
+            self.graphs[self.cur].replay()
+        else:
+            batch_step(self.tables[self.cur], self.caps, self.params, self.dev_table, stream)
+        self.cur = 1 - self.cur
+
+    def count(self, s: int) -> int:
+        return int(self.offsets[s][self.nboxes[s]].item())

@@ -123,3 +123,82 @@ def test_error_strings():
     assert omt.error_string(omt.OK) == "success"
     assert "invalid" in omt.error_string(omt.EINVAL)
     assert omt.error_string(12345) == "unknown error"
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors have the C structs' sizes and field offsets."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "omt.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(omt_params), sizeof(omt_pyramid),
+         sizeof(omt_batch_stream), sizeof(omt_batch_caps), sizeof(omt_level));
+  printf("%zu %zu %zu %zu\n", offsetof(omt_batch_stream, prev), offsetof(omt_batch_stream, boxes),
+         offsetof(omt_batch_stream, scratch), offsetof(omt_batch_stream, nvalid));
+  printf("%zu %zu\n", offsetof(omt_pyramid, base), offsetof(omt_pyramid, lv));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()
+    got = list(map(int, out))
+    want = [ctypes.sizeof(omt.Params), ctypes.sizeof(omt.PyramidDesc), ctypes.sizeof(omt.BatchStream),
+            ctypes.sizeof(omt.BatchCaps), ctypes.sizeof(omt.Level),
+            omt.BatchStream.prev.offset, omt.BatchStream.boxes.offset, omt.BatchStream.scratch.offset,
+            omt.BatchStream.nvalid.offset, omt.PyramidDesc.base.offset, omt.PyramidDesc.lv.offset]
+    assert got == want
+
+
+def _fake_stream(w, h, nb, mc, base, levels=3, storage=0):
+    """A batch stream description over made-up, well-aligned addresses (the
+    pack step only reads the description, never the memory)."""
+    d = omt.BatchStream()
+    n = omt.pyramid_bytes(w, h, levels, storage)
+    lib = omt.lib()
+    assert lib.omt_pyramid_init(ctypes.byref(d.prev), w, h, levels, storage, ctypes.c_void_p(base), n) == 0
+    assert lib.omt_pyramid_init(ctypes.byref(d.next), w, h, levels, storage,
+                                ctypes.c_void_p(base + (1 << 28)), n) == 0
+    p = base + (1 << 29)
+    d.frame, d.frame_pitch = p, w
+    d.boxes, d.nboxes, d.max_corners = p + (1 << 24), nb, mc
+    d.scratch = p + (2 << 24)
+    d.scratch_bytes = omt.corner_scratch_bytes(w, h, nb, mc)
+    d.pts, d.pts_out, d.status = p + (3 << 24), p + (4 << 24), p + (5 << 24)
+    d.iters, d.offsets = None, p + (6 << 24)
+    d.boxes_out, d.nvalid = p + (7 << 24), None
+    return d
+
+
+def test_batch_pack_validation():
+    import numpy as np
+    prm = omt.default_params(levels=3, max_corners=50)
+    caps = omt.BatchCaps(4, 100, 1920, 1080, 64)
+    n = omt.batch_table_bytes(caps)
+    assert n > 0
+    table = np.zeros(n, np.uint8)
+    tp = ctypes.c_void_p(table.ctypes.data)
+    lib = omt.lib()
+    ok = [_fake_stream(720, 576, 10, 50, 1 << 32), _fake_stream(1920, 1080, 64, 64, 2 << 32)]
+    arr = (omt.BatchStream * 2)(*ok)
+    assert lib.omt_batch_pack(arr, 2, ctypes.byref(prm), ctypes.byref(caps), tp, n) == omt.OK
+    # header: two streams, 74 boxes
+    hdr = np.frombuffer(table[:12].tobytes(), np.int32)
+    assert hdr.tolist() == [2, 4, 74]
+    bad = []
+    s = _fake_stream(720, 576, 101, 50, 1 << 32); bad.append(("boxes over caps", s, omt.EINVAL))
+    s = _fake_stream(3840, 2160, 1, 50, 1 << 32); bad.append(("frame over caps", s, omt.EINVAL))
+    s = _fake_stream(720, 576, 10, 65, 1 << 32); bad.append(("corners over caps", s, omt.EINVAL))
+    s = _fake_stream(720, 576, 10, 50, 1 << 32); s.scratch_bytes -= 1; bad.append(("short scratch", s, omt.ENOMEM))
+    s = _fake_stream(720, 576, 10, 50, 1 << 32); s.boxes_out = s.boxes; bad.append(("aliased boxes", s, omt.EINVAL))
+    s = _fake_stream(720, 576, 10, 50, 1 << 32, levels=4); bad.append(("levels differ", s, omt.EINVAL))
+    s = _fake_stream(720, 576, 10, 50, 1 << 32); s.frame_pitch = 700; bad.append(("pitch", s, omt.EINVAL))
+    for what, s, code in bad:
+        arr = (omt.BatchStream * 1)(s)
+        assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n) == code, what
+    arr = (omt.BatchStream * 5)(*([ok[0]] * 5))
+    assert lib.omt_batch_pack(arr, 5, ctypes.byref(prm), ctypes.byref(caps), tp, n) == omt.EINVAL
+    assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n - 1) == omt.ENOMEM

@@ -1,0 +1,206 @@
+"""The batched path (omt_batch_step) against the plain per-stream calls.
+
+Both run the same per-tile / per-box / per-point device code, so every
+result must agree bit for bit: the new pyramids, the corner lists and
+offsets, the tracked points, statuses and iteration counts, the boxes.
+Also: a stream gives the same result alone as in a mix of streams, a CUDA
+graph replay equals the eager step, and membership below the capacities
+works.  The plain path is itself held to the oracle by the other tests.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1910_06017_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def omt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_06017_b300 import omt as m
+    m.lib()
+    return m
+
+
+def _streams(n, first=0):
+    out = []
+    for s in range(first, first + n):
+        sp = synth.stream_pair(s, workload=13, n_range=(300, 3000))
+        out.append(sp)
+    # a stream with an empty box list and one with boxes off the frame
+    return out
+
+
+def _cap(sp):
+    return int(math.ceil(sp.n_target / 64))
+
+
+def _run_plain(omt, sps, params, boxes_list):
+    res = []
+    for sp, boxes in zip(sps, boxes_list):
+        w, h = sp.size
+        prm = params.replace(max_corners=_cap(sp))
+        T = omt.StreamTracker(w, h, prm, max_boxes=max(1, len(boxes)))
+        T.prime(torch.from_numpy(sp.frame0).cuda())
+        b = torch.from_numpy(np.ascontiguousarray(boxes, np.float32)).cuda()
+        nb = len(boxes)
+        if nb:
+            bo = T.step(torch.from_numpy(sp.frame1).cuda(), b)
+        else:
+            omt.build_pyramid(torch.from_numpy(sp.frame1).cuda(), T.pyr[1], prm)
+            T.offsets.zero_()
+            T.cur = 1
+            bo = T.boxes_out[:0]
+        torch.cuda.synchronize()
+        n = int(T.offsets[nb].item()) if nb else 0
+        res.append(dict(
+            offsets=T.offsets[:nb + 1].cpu().numpy(), pts=T.pts[:n].cpu().numpy(),
+            out=T.pts_out[:n].cpu().numpy(), st=T.status[:n].cpu().numpy(),
+            it=T.iters[:n].cpu().numpy(), boxes=bo.cpu().numpy(),
+            nvalid=T.nvalid[:nb].cpu().numpy(), pyr=T.pyr[1].buffer.cpu().numpy()))
+    return res
+
+
+def _make_batch(omt, sps, params, boxes_list, graph=False):
+    sizes = [sp.size for sp in sps]
+    B = omt.BatchTracker(sizes, params, max_boxes=[max(1, len(b)) for b in boxes_list],
+                         max_corners=[_cap(sp) for sp in sps])
+    for s, (sp, boxes) in enumerate(zip(sps, boxes_list)):
+        B.prime(s, torch.from_numpy(sp.frame0).cuda())
+        B.frame[s].copy_(torch.from_numpy(sp.frame1))
+        B.set_boxes(s, torch.from_numpy(np.ascontiguousarray(boxes, np.float32)))
+    B.pack()
+    return B
+
+
+def _batch_results(B, sps):
+    res = []
+    for s in range(len(sps)):
+        nb = B.nboxes[s]
+        n = B.count(s)
+        res.append(dict(
+            offsets=B.offsets[s][:nb + 1].cpu().numpy(), pts=B.pts[s][:n].cpu().numpy(),
+            out=B.pts_out[s][:n].cpu().numpy(), st=B.status[s][:n].cpu().numpy(),
+            it=B.iters[s][:n].cpu().numpy(), boxes=B.boxes_out[s][:nb].cpu().numpy(),
+            nvalid=B.nvalid[s][:nb].cpu().numpy(),
+            pyr=B.pyr[s][1 - B.cur].buffer.cpu().numpy()))
+    return res
+
+
+def _assert_same(a, b, pyramids=True):
+    for k in a:
+        if k == "pyr" and not pyramids:
+            continue
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def _pyr_planes(omt, buf, w, h, levels, storage):
+    """The payload of every plane of a pyramid buffer (pitch padding is
+    never written, so only the planes are compared)."""
+    import ctypes
+    d = omt.PyramidDesc()
+    n = omt.pyramid_bytes(w, h, levels, storage)
+    assert omt.lib().omt_pyramid_init(ctypes.byref(d), w, h, levels, storage,
+                                      ctypes.c_void_p(1 << 20), n) == 0  # layout only
+    out = []
+    for L in range(levels):
+        lv = d.lv[L]
+        esz = 1 if L == 0 else (4 if storage == 0 else 2)
+        gsz = 8 if storage == 0 else 4
+        out.append(buf[lv.img_off:lv.img_off + lv.img_pitch * lv.h].reshape(lv.h, lv.img_pitch)[:, :lv.w * esz])
+        out.append(buf[lv.grad_off:lv.grad_off + lv.grad_pitch * lv.h].reshape(lv.h, lv.grad_pitch)[:, :lv.w * gsz])
+    return out
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_batch_equals_plain_bitwise(omt, storage):
+    sps = _streams(6)
+    boxes_list = [sp.boxes for sp in sps]
+    boxes_list[2] = np.zeros((0, 4), np.float32)  # a stream with no boxes
+    boxes_list[3] = np.concatenate([sps[3].boxes, [[5000, 5000, 5100, 5100], [-40, -40, -10, -10]]]).astype(np.float32)
+    params = omt.default_params(levels=4, win=21, min_dist=3.0, storage=storage,
+                                max_corners=max(_cap(sp) for sp in sps))
+    plain = _run_plain(omt, sps, params, boxes_list)
+    B = _make_batch(omt, sps, params, boxes_list)
+    B.step()
+    torch.cuda.synchronize()
+    got = _batch_results(B, sps)
+    for s, (a, b) in enumerate(zip(plain, got)):
+        w, h = sps[s].size
+        _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
+        for x, y in zip(_pyr_planes(omt, a["pyr"], w, h, 4, storage), _pyr_planes(omt, b["pyr"], w, h, 4, storage)):
+            np.testing.assert_array_equal(x, y)
+    assert sum(len(r["st"]) for r in got) > 1000
+
+
+def test_alone_equals_in_the_mix(omt):
+    sps = _streams(5, first=20)
+    params = omt.default_params(levels=4, win=21, min_dist=3.0,
+                                max_corners=max(_cap(sp) for sp in sps))
+    boxes_list = [sp.boxes for sp in sps]
+    B = _make_batch(omt, sps, params, boxes_list)
+    B.step()
+    torch.cuda.synchronize()
+    mix = _batch_results(B, sps)
+    for s in (0, 3):
+        A = _make_batch(omt, [sps[s]], params, [boxes_list[s]])
+        A.step()
+        torch.cuda.synchronize()
+        alone = _batch_results(A, [sps[s]])[0]
+        _assert_same({k: v for k, v in alone.items() if k != "pyr"},
+                     {k: v for k, v in mix[s].items() if k != "pyr"})
+
+
+def test_graph_replay_equals_eager(omt):
+    sps = _streams(4, first=40)
+    params = omt.default_params(levels=4, win=21, min_dist=3.0, storage=1,
+                                max_corners=max(_cap(sp) for sp in sps))
+    boxes_list = [sp.boxes for sp in sps]
+    E = _make_batch(omt, sps, params, boxes_list)
+    G = _make_batch(omt, sps, params, boxes_list)
+    G.step()             # one eager step before capture (library one-time setup)
+    for s, sp in enumerate(sps):      # rewind G to frame 0 -> 1
+        G.cur = 0
+        G.prime(s, torch.from_numpy(sp.frame0).cuda())
+    torch.cuda.synchronize()
+    G.capture()
+    for k in range(3):
+        for s, sp in enumerate(sps):
+            f = sp.frame1 if k % 2 == 0 else sp.frame0
+            E.frame[s].copy_(torch.from_numpy(f))
+            G.frame[s].copy_(torch.from_numpy(f))
+        E.step()
+        G.step()
+        torch.cuda.synchronize()
+        for a, b in zip(_batch_results(E, sps), _batch_results(G, sps)):
+            _assert_same({k2: v for k2, v in a.items() if k2 != "pyr"},
+                         {k2: v for k2, v in b.items() if k2 != "pyr"})
+
+
+def test_membership_below_capacity(omt):
+    sps = _streams(3, first=60)
+    params = omt.default_params(levels=3, win=15, min_dist=3.0,
+                                max_corners=max(_cap(sp) for sp in sps))
+    boxes_list = [sp.boxes for sp in sps]
+    plain = _run_plain(omt, sps, params, boxes_list)
+    sizes = [sp.size for sp in sps] + [(1920, 1080)]
+    B = omt.BatchTracker(sizes, params, max_boxes=[64, 64, 64, 64],
+                         max_corners=[_cap(sp) for sp in sps] + [10])
+    for s, sp in enumerate(sps):
+        B.prime(s, torch.from_numpy(sp.frame0).cuda())
+        B.frame[s].copy_(torch.from_numpy(sp.frame1))
+        B.set_boxes(s, torch.from_numpy(sp.boxes))
+    # the fourth stream exists in the capacities but has nothing to track
+    B.set_boxes(3, torch.zeros((0, 4)))
+    B.prime(3, B.frame[3])
+    B.pack()
+    B.step()
+    torch.cuda.synchronize()
+    got = _batch_results(B, sps)
+    for a, b in zip(plain, got):
+        _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
