@@ -312,6 +312,24 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
 int omt_batch_step(const void *table, const omt_batch_caps *caps, const omt_params *prm,
                    void *dev_table, size_t dev_table_bytes, void *stream);
 
+/* The same step in pieces, for callers that interleave the phases of
+ * consecutive steps (e.g. the next frames' pyramids while this step's
+ * points are tracked, Section V-B) or time them separately:
+ * omt_batch_upload copies `table` to dev_table; omt_batch_phase runs one
+ * phase on an uploaded table.  Phases must run in order on the table's data
+ * (the corners read frame t's pyramid, LK reads both pyramids and the
+ * corners, the box update reads LK's results). */
+enum omt_batch_phase_id {
+    OMT_PHASE_PYRAMID = 0, /* frame t+1 pyramids of every stream          */
+    OMT_PHASE_CORNERS = 1, /* response maps, selection, CSR compaction    */
+    OMT_PHASE_LK = 2,      /* one persistent launch over all points       */
+    OMT_PHASE_BOXES = 3    /* per-box median / mean update                */
+};
+int omt_batch_upload(const void *table, const omt_batch_caps *caps, void *dev_table,
+                     size_t dev_table_bytes, void *stream);
+int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt_params *prm,
+                    int32_t phase, void *stream);
+
 /* ---------------------------------------------------------------- misc */
 
 const char *omt_error_string(int32_t code);

@@ -287,37 +287,62 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
     return OMT_OK;
 }
 
+int omt_batch_upload(const void *table, const omt_batch_caps *caps, void *dev_table,
+                     size_t dev_table_bytes, void *stream) {
+    if (!caps_ok(caps) || !table || !dev_table || !aligned(dev_table, 256)) return OMT_EINVAL;
+    const size_t need = batch_table_bytes(caps->max_streams);
+    if (dev_table_bytes < need) return OMT_ENOMEM;
+    const BatchHeader &h = *(const BatchHeader *)table;
+    if (h.max_streams != caps->max_streams || h.bytes != (int64_t)need || h.nstreams < 0 ||
+        h.nstreams > caps->max_streams || h.total_boxes > caps->max_boxes)
+        return OMT_EINVAL;
+    return from_cuda(cudaMemcpyAsync(dev_table, table, need, cudaMemcpyHostToDevice,
+                                     (cudaStream_t)stream));
+}
+
+int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt_params *prm,
+                    int32_t phase, void *stream) {
+    if (omt_validate_params(prm) != OMT_OK || !caps_ok(caps) || !dev_table ||
+        !aligned(dev_table, 256))
+        return OMT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint8_t *dt = (const uint8_t *)dev_table;
+    switch (phase) {
+        case OMT_PHASE_PYRAMID: {
+            int max_tiles[OMT_MAX_LEVELS];
+            int lw = caps->max_w, lh = caps->max_h;
+            for (int L = 0; L < prm->levels; ++L) {
+                max_tiles[L] = caps->max_streams * pyramid_tiles(lw, lh);
+                lw = (lw + 1) >> 1;
+                lh = (lh + 1) >> 1;
+            }
+            return from_cuda(launch_pyramid_batch(dt, prm->levels, prm->storage, max_tiles, s));
+        }
+        case OMT_PHASE_CORNERS:
+            return from_cuda(launch_corners_batch(
+                dt, caps->max_streams, caps->max_streams * response_tiles(caps->max_w, caps->max_h),
+                caps->max_boxes, caps->max_corners, s));
+        case OMT_PHASE_LK:
+            return from_cuda(launch_lk_batch(dt, prm->storage, prm->win, s));
+        case OMT_PHASE_BOXES:
+            return from_cuda(launch_update_boxes_batch(dt, caps->max_boxes, s));
+        default:
+            return OMT_EINVAL;
+    }
+}
+
 int omt_batch_step(const void *table, const omt_batch_caps *caps, const omt_params *prm,
                    void *dev_table, size_t dev_table_bytes, void *stream) {
     if (omt_validate_params(prm) != OMT_OK || !caps_ok(caps) || !table || !dev_table)
         return OMT_EINVAL;
-    if (!aligned(dev_table, 256)) return OMT_EINVAL;
-    const size_t need = batch_table_bytes(caps->max_streams);
-    if (dev_table_bytes < need) return OMT_ENOMEM;
     const BatchHeader &h = *(const BatchHeader *)table;
-    if (h.max_streams != caps->max_streams || h.bytes != (int64_t)need || h.levels != prm->levels ||
-        h.storage != prm->storage || h.win != prm->win || h.max_iter != prm->max_iter ||
-        h.nstreams < 0 || h.nstreams > caps->max_streams || h.total_boxes > caps->max_boxes)
+    if (h.levels != prm->levels || h.storage != prm->storage || h.win != prm->win ||
+        h.max_iter != prm->max_iter)
         return OMT_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(dev_table, table, need, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return OMT_ECUDA;
-    const uint8_t *dt = (const uint8_t *)dev_table;
-    int max_tiles[OMT_MAX_LEVELS];
-    int lw = caps->max_w, lh = caps->max_h;
-    for (int L = 0; L < prm->levels; ++L) {
-        max_tiles[L] = caps->max_streams * pyramid_tiles(lw, lh);
-        lw = (lw + 1) >> 1;
-        lh = (lh + 1) >> 1;
-    }
-    e = launch_pyramid_batch(dt, prm->levels, prm->storage, max_tiles, s);
-    if (e != cudaSuccess) return OMT_ECUDA;
-    e = launch_corners_batch(dt, caps->max_streams, caps->max_streams * response_tiles(caps->max_w, caps->max_h),
-                             caps->max_boxes, caps->max_corners, s);
-    if (e != cudaSuccess) return OMT_ECUDA;
-    e = launch_lk_batch(dt, prm->storage, prm->win, s);
-    if (e != cudaSuccess) return OMT_ECUDA;
-    return from_cuda(launch_update_boxes_batch(dt, caps->max_boxes, s));
+    int rc = omt_batch_upload(table, caps, dev_table, dev_table_bytes, stream);
+    for (int phase = OMT_PHASE_PYRAMID; rc == OMT_OK && phase <= OMT_PHASE_BOXES; ++phase)
+        rc = omt_batch_phase(dev_table, caps, prm, phase, stream);
+    return rc;
 }
 
 const char *omt_error_string(int32_t code) {

@@ -25,8 +25,9 @@ EXPORTED = [
     "omt_build_pyramid", "omt_corner_response", "omt_corner_scratch_bytes",
     "omt_select_corners", "omt_lk_track", "omt_update_boxes", "omt_error_string",
     "omt_version", "omt_select_corners_static", "omt_batch_table_bytes", "omt_batch_pack",
-    "omt_batch_step",
+    "omt_batch_step", "omt_batch_upload", "omt_batch_phase",
 ]
+PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES = 0, 1, 2, 3
 BATCH_MAX_STREAMS = 256
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -114,6 +115,9 @@ def lib():
                                      POINTER(BatchCaps), c_void_p, c_size_t]
         L.omt_batch_step.argtypes = [c_void_p, POINTER(BatchCaps), POINTER(Params), c_void_p,
                                      c_size_t, c_void_p]
+        L.omt_batch_upload.argtypes = [c_void_p, POINTER(BatchCaps), c_void_p, c_size_t, c_void_p]
+        L.omt_batch_phase.argtypes = [c_void_p, POINTER(BatchCaps), POINTER(Params), c_int32,
+                                      c_void_p]
         _lib = L
     return _lib
 
@@ -311,12 +315,24 @@ def batch_step(table, caps: BatchCaps, params: Params, dev_table, stream=None):
                                 _stream(stream)), "omt_batch_step")
 
 
+def batch_upload(table, caps: BatchCaps, dev_table, stream=None):
+    _check(lib().omt_batch_upload(ctypes.c_void_p(table.data_ptr()), ctypes.byref(caps),
+                                  _ptr(dev_table), dev_table.numel(), _stream(stream)),
+           "omt_batch_upload")
+
+
+def batch_phase(dev_table, caps: BatchCaps, params: Params, phase: int, stream=None):
+    _check(lib().omt_batch_phase(_ptr(dev_table), ctypes.byref(caps), ctypes.byref(params),
+                                 phase, _stream(stream)), "omt_batch_phase")
+
+
 class BatchTracker:
     """Many independent streams advanced by one omt_batch_step per step.
 
     Every stream keeps, resident on the device, two pyramids that swap roles
-    (frame t, frame t+1), a frame slot for the next frame, its input and
-    output boxes, point buffers and corner scratch.  Two tables (one per
+    (frame t, frame t+1), two frame slots (the step with parity p reads
+    frame t+1 from slot p), its input and output boxes, point buffers and
+    corner scratch.  Two tables (one per
     pyramid parity) are packed once into page-locked host memory; a step
     copies the right one to the device and runs 4 + levels launches for all
     streams.  With graph=True each parity's step is captured once in a CUDA
@@ -345,7 +361,7 @@ class BatchTracker:
         for (w, h), nb, mc in zip(sizes, max_boxes, max_corners):
             self.pyr.append([Pyramid(w, h, params.levels, params.storage, dev),
                              Pyramid(w, h, params.levels, params.storage, dev)])
-            self.frame.append(torch.zeros((h, w), dtype=torch.uint8, device=dev))
+            self.frame.append([torch.zeros((h, w), dtype=torch.uint8, device=dev) for _ in range(2)])
             cap = max(1, nb * mc)
             self.boxes.append(torch.zeros((max(1, nb), 4), dtype=torch.float32, device=dev))
             self.boxes_out.append(torch.zeros((max(1, nb), 4), dtype=torch.float32, device=dev))
@@ -366,7 +382,7 @@ class BatchTracker:
 
     def _desc(self, s: int, parity: int) -> BatchStream:
         d = BatchStream()
-        f = self.frame[s]
+        f = self.frame[s][parity]
         d.frame, d.frame_pitch = f.data_ptr(), f.stride(0)
         d.prev = self.pyr[s][parity].desc
         d.next = self.pyr[s][1 - parity].desc
@@ -380,6 +396,10 @@ class BatchTracker:
         d.offsets = self.offsets[s].data_ptr()
         d.boxes_out, d.nvalid = self.boxes_out[s].data_ptr(), self.nvalid[s].data_ptr()
         return d
+
+    def slot(self, s: int):
+        """Device frame slot the next step reads frame t+1 of stream s from."""
+        return self.frame[s][self.cur]
 
     def set_boxes(self, s: int, boxes):
         """Boxes of stream s on frame t (device or host tensor (nb, 4))."""
@@ -416,6 +436,20 @@ class BatchTracker:
             self.graphs[self.cur].replay()
         else:
             batch_step(self.tables[self.cur], self.caps, self.params, self.dev_table, stream)
+        self.cur = 1 - self.cur
+
+    def step_phases(self, lk_events=None, stream=None):
+        """The step as upload + four phases; with lk_events=(start, end)
+        CUDA events, they bracket the LK phase."""
+        batch_upload(self.tables[self.cur], self.caps, self.dev_table, stream)
+        batch_phase(self.dev_table, self.caps, self.params, PHASE_PYRAMID, stream)
+        batch_phase(self.dev_table, self.caps, self.params, PHASE_CORNERS, stream)
+        if lk_events:
+            lk_events[0].record()
+        batch_phase(self.dev_table, self.caps, self.params, PHASE_LK, stream)
+        if lk_events:
+            lk_events[1].record()
+        batch_phase(self.dev_table, self.caps, self.params, PHASE_BOXES, stream)
         self.cur = 1 - self.cur
 
     def count(self, s: int) -> int:

@@ -72,7 +72,7 @@ def _make_batch(omt, sps, params, boxes_list, graph=False):
                          max_corners=[_cap(sp) for sp in sps])
     for s, (sp, boxes) in enumerate(zip(sps, boxes_list)):
         B.prime(s, torch.from_numpy(sp.frame0).cuda())
-        B.frame[s].copy_(torch.from_numpy(sp.frame1))
+        B.slot(s).copy_(torch.from_numpy(sp.frame1))
         B.set_boxes(s, torch.from_numpy(np.ascontiguousarray(boxes, np.float32)))
     B.pack()
     return B
@@ -88,7 +88,7 @@ def _batch_results(B, sps):
             out=B.pts_out[s][:n].cpu().numpy(), st=B.status[s][:n].cpu().numpy(),
             it=B.iters[s][:n].cpu().numpy(), boxes=B.boxes_out[s][:nb].cpu().numpy(),
             nvalid=B.nvalid[s][:nb].cpu().numpy(),
-            pyr=B.pyr[s][1 - B.cur].buffer.cpu().numpy()))
+            pyr=B.pyr[s][B.cur].buffer.cpu().numpy()))
     return res
 
 
@@ -172,8 +172,8 @@ def test_graph_replay_equals_eager(omt):
     for k in range(3):
         for s, sp in enumerate(sps):
             f = sp.frame1 if k % 2 == 0 else sp.frame0
-            E.frame[s].copy_(torch.from_numpy(f))
-            G.frame[s].copy_(torch.from_numpy(f))
+            E.slot(s).copy_(torch.from_numpy(f))
+            G.slot(s).copy_(torch.from_numpy(f))
         E.step()
         G.step()
         torch.cuda.synchronize()
@@ -193,11 +193,11 @@ def test_membership_below_capacity(omt):
                          max_corners=[_cap(sp) for sp in sps] + [10])
     for s, sp in enumerate(sps):
         B.prime(s, torch.from_numpy(sp.frame0).cuda())
-        B.frame[s].copy_(torch.from_numpy(sp.frame1))
+        B.slot(s).copy_(torch.from_numpy(sp.frame1))
         B.set_boxes(s, torch.from_numpy(sp.boxes))
     # the fourth stream exists in the capacities but has nothing to track
     B.set_boxes(3, torch.zeros((0, 4)))
-    B.prime(3, B.frame[3])
+    B.prime(3, B.slot(3))
     B.pack()
     B.step()
     torch.cuda.synchronize()
