@@ -125,22 +125,71 @@ __device__ __forceinline__ void template_window(const LevelView &P, int ipx, int
     cy = tapcol ? cy0 + cy1 : 0.f;
 }
 
-// sum over the window of J(c + (i, j)) (Ix, Iy), J bilinear at fractional
-// offset (bx, by) from the integer centre (jx, jy); per-lane partial sums.
+// ------------------------------------------------------------ J staging
+// Each warp stages frame t+1's search region of one level in shared memory:
+// SH texel rows around the window with MARGIN texels of slack on every
+// side, stored as (J(x), J(x+1)) pairs so that a tap row of an iteration is
+// one 8-byte shared load per lane.  Texels are clamped to the level and
+// converted to float once, at staging; the region is restaged only when the
+// iteration centre moves more than MARGIN texels from where it was staged.
+constexpr int MARGIN = 4;
+
+template <int WIN>
+struct StageDims {
+    static constexpr int R = WIN / 2;
+    static constexpr int SH = WIN + 1 + 2 * MARGIN;  // texel rows
+    static constexpr int SP = WIN + 2 * MARGIN;      // pairs per row
+    static constexpr int PAIRS = SH * SP;            // float2 per warp
+};
+
 template <int ST, int WIN>
-__device__ __forceinline__ void correlate_window(const LevelView &J, int jx, int jy, float bx,
-                                                 float by, int lane, bool u8, const float (&Xw)[WIN],
+__device__ __forceinline__ void stage_region(const LevelView &J, bool u8, int jx, int jy, int lane,
+                                             float *S) {
+    using D = StageDims<WIN>;
+    const int sx0 = jx - D::R - MARGIN, sy0 = jy - D::R - MARGIN;
+    __syncwarp();
+#pragma unroll 2
+    for (int r = 0; r < D::SH; ++r) {
+        const int y = clampi(sy0 + r, 0, J.h - 1);
+        const uint8_t *row = J.img + (int64_t)y * J.img_pitch;
+        for (int c = lane; c <= D::SP; c += 32) {
+            const float v = texel<ST>(row, clampi(sx0 + c, 0, J.w - 1), u8);
+            if (c < D::SP) S[2 * (r * D::SP + c)] = v;
+            if (c >= 1) S[2 * (r * D::SP + c - 1) + 1] = v;
+        }
+    }
+    __syncwarp();
+}
+
+// Two warp sums at once: lanes 0-15 end with the total of a, lanes 16-31
+// with the total of b (one exchange, then butterflies within each half);
+// returns both totals in every lane.  Fixed order: every lane gets the same
+// bits, and equal inputs give equal outputs whatever they are paired with.
+__device__ __forceinline__ void warp_sum2(float &a, float &b, int lane) {
+    const bool hi = (lane & 16) != 0;
+    float keep = hi ? b : a;
+    const float give = hi ? a : b;
+    keep += __shfl_xor_sync(FULL_MASK, give, 16);
+#pragma unroll
+    for (int m = 8; m > 0; m >>= 1) keep += __shfl_xor_sync(FULL_MASK, keep, m);
+    a = __shfl_sync(FULL_MASK, keep, 0);
+    b = __shfl_sync(FULL_MASK, keep, 16);
+}
+
+// sum over the window of J(c + (i, j)) (Ix, Iy) from the staged region; the
+// window's top-left tap sits at pair (oy, ox) of the region.
+template <int WIN>
+__device__ __forceinline__ void correlate_staged(const float2 *S, int ox, int oy, float bx, float by,
+                                                 int lane, const float (&Xw)[WIN],
                                                  const float (&Yw)[WIN], float &sx, float &sy) {
-    constexpr int R = WIN / 2;
-    const bool loader = lane <= WIN;
-    const int tx = clampi(jx + lane - R, 0, J.w - 1);
+    using D = StageDims<WIN>;
+    const bool tapcol = lane < WIN;
+    const float2 *base = S + oy * D::SP + ox + (tapcol ? lane : 0);
     float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ph = 0.f;
 #pragma unroll
     for (int tr = 0; tr <= WIN; ++tr) {
-        const int ty = clampi(jy + tr - R, 0, J.h - 1);
-        const float vt = loader ? texel<ST>(J.img + (int64_t)ty * J.img_pitch, tx, u8) : 0.f;
-        const float v1 = __shfl_down_sync(FULL_MASK, vt, 1);
-        const float h = fmaf(bx, v1 - vt, vt);
+        const float2 pv = base[tr * D::SP];
+        const float h = fmaf(bx, pv.y - pv.x, pv.x);
         if (tr > 0) {
             const float jv = fmaf(by, h - ph, ph);
             if (tr & 1) {
@@ -153,7 +202,6 @@ __device__ __forceinline__ void correlate_window(const LevelView &J, int jx, int
         }
         ph = h;
     }
-    const bool tapcol = lane < WIN;
     sx = tapcol ? ax0 + ax1 : 0.f;
     sy = tapcol ? ay0 + ay1 : 0.f;
 }
@@ -163,8 +211,8 @@ __device__ __forceinline__ void correlate_window(const LevelView &J, int jx, int
 template <int ST, int WIN>
 __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &J, float px,
                                            float py, float gx, float gy, int max_iter,
-                                           float eps2, float tau_n, int lane, bool u8, float &nux,
-                                           float &nuy, int &k, bool &conv) {
+                                           float eps2, float tau_n, int lane, bool u8, float *Sw,
+                                           float &nux, float &nuy, int &k, bool &conv) {
     constexpr int R = WIN / 2;
     const float fpx = floorf(px), fpy = floorf(py);
     const int ipx = (int)fpx, ipy = (int)fpy;
@@ -175,8 +223,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     sxx = warp_sum(sxx);
     sxy = warp_sum(sxy);
     syy = warp_sum(syy);
-    cx = warp_sum(cx);
-    cy = warp_sum(cy);
+    warp_sum2(cx, cy, lane);
     const float det = det2(sxx, syy, sxy);
     const float dd = sxx - syy;
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
@@ -185,6 +232,9 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     k = 0;
     conv = false;
     if (!(lmin >= tau_n) || !(lmin > 0.f)) return OMT_PT_LOST_EIG;
+    const float2 *S = (const float2 *)Sw;
+    int sjx = 0, sjy = 0;
+    bool staged = false;
     while (k < max_iter) {
         // Centre c = p + g + nu, held as (ipx, ipy) + (ccx, ccy).
         const float ccx = ax + gx + nux, ccy = ay + gy + nuy;
@@ -195,10 +245,16 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         if (jx < -R || jx > J.w - 1 + R || (jx == J.w - 1 + R && bx > 0.f) || jy < -R ||
             jy > J.h - 1 + R || (jy == J.h - 1 + R && by > 0.f))
             return OMT_PT_LOST_OOB;
+        if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
+            stage_region<ST, WIN>(J, u8, jx, jy, lane, Sw);
+            sjx = jx;
+            sjy = jy;
+            staged = true;
+        }
         float sx, sy;
-        correlate_window<ST, WIN>(J, jx, jy, bx, by, lane, u8, Xw, Yw, sx, sy);
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
+        correlate_staged<WIN>(S, jx - sjx + MARGIN, jy - sjy + MARGIN, bx, by, lane, Xw, Yw, sx,
+                              sy);
+        warp_sum2(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
         const float ex = (syy * bbx - sxy * bby) / det;
         const float ey = (sxx * bby - sxy * bbx) / det;
@@ -219,7 +275,8 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
 template <int ST, int WIN>
 __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
                                          int max_iter, float eps2, float tau_n, float2 u,
-                                         int i, float2 *out, uint8_t *status, uint8_t *iters) {
+                                         int i, float2 *out, uint8_t *status, uint8_t *iters,
+                                         float *Sw) {
     const int lane = threadIdx.x & 31;
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     int st = OMT_PT_OK;
@@ -232,7 +289,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         int k;
         bool conv;
         st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
-                                  lane, L == 0, nux, nuy, k, conv);
+                                  lane, L == 0, Sw, nux, nuy, k, conv);
         itp |= (unsigned long long)k << (8 * L);
         if (st != OMT_PT_OK) break;
         if (!conv) nonconv = true;
@@ -261,8 +318,21 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
     if (iters && lane < levels) iters[(int64_t)i * levels + lane] = (uint8_t)(itp >> (8 * lane));
 }
 
+// Staging buffer of this warp in the block's dynamic shared memory.
+template <int WIN>
+__device__ __forceinline__ float *warp_stage() {
+    extern __shared__ __align__(16) float lk_smem[];
+    return lk_smem + (size_t)(threadIdx.x >> 5) * StageDims<WIN>::PAIRS * 2;
+}
+
+template <int WIN>
+constexpr size_t stage_bytes() {
+    return (size_t)LK_WARPS * StageDims<WIN>::PAIRS * sizeof(float2);
+}
+
 template <int ST, int WIN>
 __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArgs a) {
+    float *Sw = warp_stage<WIN>();
     int n = a.n_max;
     if (a.n_dev) {
         const int m = *a.n_dev;
@@ -271,7 +341,7 @@ __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArg
     const int nwarps = gridDim.x * LK_WARPS;
     for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps)
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters);
+                          a.status, a.iters, Sw);
 }
 
 // All points of all streams of a batch: the per-stream counts come from the
@@ -280,6 +350,7 @@ __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArg
 template <int ST, int WIN>
 __global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
     __shared__ int32_t pre[OMT_BATCH_MAX_STREAMS + 1];
+    float *Sw = warp_stage<WIN>();
     const BatchView t(table);
     const BatchHeader &h = t.hdr();
     const int ns = h.nstreams;
@@ -300,15 +371,20 @@ __global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
         const StreamEntry &e = t.stream(s);
         const int i = g - pre[s];
         lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
-                          e.pts_out, e.status, e.iters);
+                          e.pts_out, e.status, e.iters, Sw);
     }
 }
 
 template <int ST>
 cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
     switch (win) {
-#define OMT_LK_CASE(W) \
-    case W: lk_kernel<ST, W><<<grid, LK_NT, 0, s>>>(a); break;
+#define OMT_LK_CASE(W)                                                                    \
+    case W:                                                                               \
+        if (cudaFuncSetAttribute(lk_kernel<ST, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)stage_bytes<W>()) != cudaSuccess)                  \
+            return cudaGetLastError();                                                    \
+        lk_kernel<ST, W><<<grid, LK_NT, stage_bytes<W>(), s>>>(a);                        \
+        break;
         OMT_LK_CASE(3) OMT_LK_CASE(5) OMT_LK_CASE(7) OMT_LK_CASE(9) OMT_LK_CASE(11)
         OMT_LK_CASE(13) OMT_LK_CASE(15) OMT_LK_CASE(17) OMT_LK_CASE(19) OMT_LK_CASE(21)
         OMT_LK_CASE(23) OMT_LK_CASE(25) OMT_LK_CASE(27) OMT_LK_CASE(29) OMT_LK_CASE(31)
@@ -320,10 +396,14 @@ cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
 
 template <int ST, int WIN>
 cudaError_t launch_batch_win(const uint8_t *table, int sms, cudaStream_t s) {
+    const size_t smem = stage_bytes<WIN>();
+    cudaError_t e = cudaFuncSetAttribute(lk_batch_kernel<ST, WIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lk_batch_kernel<ST, WIN>, LK_NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lk_batch_kernel<ST, WIN>, LK_NT, smem);
     if (per_sm < 1) per_sm = 1;
-    lk_batch_kernel<ST, WIN><<<sms * per_sm, LK_NT, 0, s>>>(table);
+    lk_batch_kernel<ST, WIN><<<sms * per_sm, LK_NT, smem, s>>>(table);
     return cudaGetLastError();
 }
 
