@@ -47,118 +47,111 @@ __device__ __forceinline__ float det2(float a, float d, float b) {
     return f + e;
 }
 
-// Image value at an in-range pixel: u8 for level 0, else float or
-// half(I - 128).  One code path for all levels keeps the register budget
-// of a single inlined copy; the branch is uniform across the warp.
-template <int ST>
-__device__ __forceinline__ float texel(const uint8_t *row, int x, bool u8) {
-    if (u8) return (float)__ldg(row + x);
-    if (ST == OMT_F32) return __ldg((const float *)row + x);
-    return __half2float(__ldg((const __half *)row + x)) + 128.0f;
-}
-
-// Frame-t window of one level: (Ix, Iy) per tap row in registers, and the
-// level constants G (three sums) and c = sum I (Ix, Iy).
-template <int ST, int WIN>
-__device__ __forceinline__ void template_window(const LevelView &P, int ipx, int ipy, float ax,
-                                                float ay, int lane, bool u8, float (&Xw)[WIN],
-                                                float (&Yw)[WIN], float &sxx, float &sxy,
-                                                float &syy, float &cx, float &cy) {
-    constexpr int R = WIN / 2;
-    constexpr int CH = 8;  // texel rows loaded per batch (bounds live registers)
-    const bool loader = lane <= WIN, tapcol = lane < WIN;
-    const int tx = clampi(ipx + lane - R, 0, P.w - 1);
-    float pI = 0.f, pX = 0.f, pY = 0.f;
-    float cx0 = 0.f, cy0 = 0.f, cx1 = 0.f, cy1 = 0.f;
-    sxx = sxy = syy = 0.f;
-#pragma unroll
-    for (int t0 = 0; t0 <= WIN; t0 += CH) {
-        float v[CH];
-        float2 g[CH];
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int tr = t0 + c;
-            v[c] = 0.f;
-            g[c] = make_float2(0.f, 0.f);
-            if (tr <= WIN && loader) {
-                const int ty = clampi(ipy + tr - R, 0, P.h - 1);
-                v[c] = texel<ST>(P.img + (int64_t)ty * P.img_pitch, tx, u8);
-                g[c] = load_grad<ST>(P, tx, ty);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int tr = t0 + c;
-            if (tr > WIN) break;
-            const float v1 = __shfl_down_sync(FULL_MASK, v[c], 1);
-            const float g1x = __shfl_down_sync(FULL_MASK, g[c].x, 1);
-            const float g1y = __shfl_down_sync(FULL_MASK, g[c].y, 1);
-            const float hI = fmaf(ax, v1 - v[c], v[c]);
-            const float hX = fmaf(ax, g1x - g[c].x, g[c].x);
-            const float hY = fmaf(ax, g1y - g[c].y, g[c].y);
-            if (tr > 0) {
-                const float I = fmaf(ay, hI - pI, pI);
-                const float X = fmaf(ay, hX - pX, pX);
-                const float Y = fmaf(ay, hY - pY, pY);
-                Xw[tr - 1] = X;
-                Yw[tr - 1] = Y;
-                sxx = fmaf(X, X, sxx);
-                sxy = fmaf(X, Y, sxy);
-                syy = fmaf(Y, Y, syy);
-                // Same two chains as correlate_window, so that J == I gives
-                // c - sum J grad I == 0 exactly (zero flow on equal frames).
-                if (tr & 1) {
-                    cx0 = fmaf(I, X, cx0);
-                    cy0 = fmaf(I, Y, cy0);
-                } else {
-                    cx1 = fmaf(I, X, cx1);
-                    cy1 = fmaf(I, Y, cy1);
-                }
-            }
-            pI = hI;
-            pX = hX;
-            pY = hY;
-        }
-    }
-    if (!tapcol) sxx = sxy = syy = 0.f;
-    cx = tapcol ? cx0 + cx1 : 0.f;
-    cy = tapcol ? cy0 + cy1 : 0.f;
-}
-
-// ------------------------------------------------------------ J staging
-// Each warp stages frame t+1's search region of one level in shared memory:
-// SH texel rows around the window with MARGIN texels of slack on every
-// side, stored as (J(x), J(x+1)) pairs so that a tap row of an iteration is
-// one 8-byte shared load per lane.  Texels are clamped to the level and
-// converted to float once, at staging; the region is restaged only when the
-// iteration centre moves more than MARGIN texels from where it was staged.
+// ------------------------------------------------------------ staging
+// Per warp and level, the texels the level needs are copied global ->
+// shared with cp.async (no registers held, all rows in flight at once): the
+// (win+1)^2 window of frame t under the template (I and (Ix, Iy)) and frame
+// t+1's search region around the initial centre, MARGIN texels wider than
+// the window on every side.  Rows are clamped to the level when copied; a
+// row is copied as the 4-byte words covering its column range clamped to
+// the level, and columns are clamped when the raw rows are read back.  The
+// search region is then converted once to (J(x), J(x+1)) float pairs, so an
+// iteration's tap row is one 8-byte shared load per lane.  The region is
+// copied again only if the centre moves more than MARGIN texels away.
 constexpr int MARGIN = 4;
 
-template <int WIN>
-struct StageDims {
+template <int ST, int WIN>
+struct Dims {
     static constexpr int R = WIN / 2;
-    static constexpr int SH = WIN + 1 + 2 * MARGIN;  // texel rows
-    static constexpr int SP = WIN + 2 * MARGIN;      // pairs per row
-    static constexpr int PAIRS = SH * SP;            // float2 per warp
+    static constexpr int T = WIN + 1;                 // template texels per side
+    static constexpr int SH = WIN + 1 + 2 * MARGIN;   // search rows
+    static constexpr int SP = WIN + 2 * MARGIN;       // search pairs per row
+    static constexpr int ESZ = ST == OMT_F32 ? 4 : 2; // bytes of a level >= 1 texel
+    static constexpr int GSZ = 2 * ESZ;               // bytes of a gradient texel
+    static constexpr int RWJ = ((SP + 1) * ESZ + 3) / 4 + 1;  // words per raw search row
+    static constexpr int RWI = (T * ESZ + 3) / 4 + 1;         // words per raw template I row
+    static constexpr int RWG = (T * GSZ) / 4;                 // words per raw gradient row
+    static constexpr int TRAW = T * (RWI + RWG);              // raw template words
+    static constexpr int PAIRW = 2 * SH * SP;                 // pair area words
+    static constexpr int UNION = TRAW > PAIRW ? TRAW : PAIRW; // template raw aliases pairs
+    static constexpr int WORDS = UNION + SH * RWJ;            // per warp
+};
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Copy `rows` rows starting at level row y0 (each clamped), texel columns
+// [x0, x0 + ncols) clamped to the level, as raw words into dst (rw words per
+// row).  Returns the level column of the first texel held by each raw row.
+__device__ __forceinline__ int copy_rows(const uint8_t *plane, int64_t pitch, int w, int h,
+                                         int esz, int x0, int ncols, int y0, int rows, int rw,
+                                         unsigned *dst, int lane) {
+    const int xa = clampi(x0, 0, w - 1), xb = clampi(x0 + ncols - 1, 0, w - 1);
+    const int b0 = (xa * esz) & ~3, b1 = (xb + 1) * esz;
+    const int nw = (b1 - b0 + 3) >> 2;
+    for (int r = 0; r < rows; ++r) {
+        const uint8_t *row = plane + (int64_t)clampi(y0 + r, 0, h - 1) * pitch + b0;
+        for (int k = lane; k < nw; k += 32) cp_async4(dst + r * rw + k, row + 4 * k);
+    }
+    return b0 / esz;
+}
+
+// Texel x (level column, clamped) of a raw row whose first byte is level
+// column `base`: u8, float or half(I - 128).  Level >= 1 values stay in the
+// stored domain (I - 128 for half): only differences and products with the
+// template, stored the same way, enter the solve.
+template <int ST>
+__device__ __forceinline__ float raw_texel(const unsigned *row, int col, bool u8) {
+    if (u8) return (float)((const uint8_t *)row)[col];
+    if (ST == OMT_F32) return ((const float *)row)[col];
+    return __half2float(((const __half *)row)[col]);
+}
+
+template <int ST>
+__device__ __forceinline__ float2 raw_grad(const unsigned *row, int col) {
+    if (ST == OMT_F32) return ((const float2 *)row)[col];
+    return __half22float2(((const __half2 *)row)[col]);
+}
+
+// Level layout the copies need.
+struct LevelCopy {
+    int tcol_i, tcol_g;  // level column of the first raw template texel (I, gradients)
+    int scol;            // level column of the first raw search texel
+    int sx0, sy0;        // search region origin (texels)
 };
 
 template <int ST, int WIN>
-__device__ __forceinline__ void stage_region(const LevelView &J, bool u8, int jx, int jy, int lane,
-                                             float *S) {
-    using D = StageDims<WIN>;
-    const int sx0 = jx - D::R - MARGIN, sy0 = jy - D::R - MARGIN;
-    __syncwarp();
-#pragma unroll 2
-    for (int r = 0; r < D::SH; ++r) {
-        const int y = clampi(sy0 + r, 0, J.h - 1);
-        const uint8_t *row = J.img + (int64_t)y * J.img_pitch;
-        for (int c = lane; c <= D::SP; c += 32) {
-            const float v = texel<ST>(row, clampi(sx0 + c, 0, J.w - 1), u8);
-            if (c < D::SP) S[2 * (r * D::SP + c)] = v;
-            if (c >= 1) S[2 * (r * D::SP + c - 1) + 1] = v;
+__device__ __forceinline__ void copy_search(const LevelView &J, bool u8, int jx, int jy, int lane,
+                                            unsigned *W, LevelCopy &lc) {
+    using D = Dims<ST, WIN>;
+    lc.sx0 = jx - D::R - MARGIN;
+    lc.sy0 = jy - D::R - MARGIN;
+    lc.scol = copy_rows(J.img, J.img_pitch, J.w, J.h, u8 ? 1 : D::ESZ, lc.sx0, D::SP + 1, lc.sy0,
+                        D::SH, D::RWJ, W + D::UNION, lane);
+}
+
+// Raw search rows -> (J(x), J(x+1)) pairs.
+template <int ST, int WIN>
+__device__ __forceinline__ void make_pairs(const LevelView &J, bool u8, int lane, unsigned *W,
+                                           const LevelCopy &lc) {
+    using D = Dims<ST, WIN>;
+    float *P = (float *)W;
+    const unsigned *raw = W + D::UNION;
+    for (int c = lane; c <= D::SP; c += 32) {
+        const int col = clampi(lc.sx0 + c, 0, J.w - 1) - lc.scol;
+#pragma unroll 6
+        for (int r = 0; r < D::SH; ++r) {
+            const float v = raw_texel<ST>(raw + r * D::RWJ, col, u8);
+            if (c < D::SP) P[2 * (r * D::SP + c)] = v;
+            if (c >= 1) P[2 * (r * D::SP + c - 1) + 1] = v;
         }
     }
-    __syncwarp();
 }
 
 // Two warp sums at once: lanes 0-15 end with the total of a, lanes 16-31
@@ -176,15 +169,70 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b, int lane) {
     b = __shfl_sync(FULL_MASK, keep, 16);
 }
 
-// sum over the window of J(c + (i, j)) (Ix, Iy) from the staged region; the
-// window's top-left tap sits at pair (oy, ox) of the region.
-template <int WIN>
-__device__ __forceinline__ void correlate_staged(const float2 *S, int ox, int oy, float bx, float by,
+// Frame-t window from the raw template rows: (Ix, Iy) per tap row stay in
+// registers, with the level constants G (three sums) and c = sum I (Ix, Iy).
+template <int ST, int WIN>
+__device__ __forceinline__ void template_window(const LevelView &P, int tx0, float ax, float ay,
+                                                int lane, bool u8, const unsigned *W,
+                                                const LevelCopy &lc, float (&Xw)[WIN],
+                                                float (&Yw)[WIN], float &sxx, float &sxy,
+                                                float &syy, float &cx, float &cy) {
+    using D = Dims<ST, WIN>;
+    const unsigned *rawI = W;
+    const unsigned *rawG = W + D::T * D::RWI;
+    const bool tapcol = lane < WIN;
+    const int c = tapcol ? lane : 0;
+    const int ci0 = clampi(tx0 + c, 0, P.w - 1) - lc.tcol_i, ci1 = clampi(tx0 + c + 1, 0, P.w - 1) - lc.tcol_i;
+    const int cg0 = clampi(tx0 + c, 0, P.w - 1) - lc.tcol_g, cg1 = clampi(tx0 + c + 1, 0, P.w - 1) - lc.tcol_g;
+    float pI = 0.f, pX = 0.f, pY = 0.f;
+    float cx0 = 0.f, cy0 = 0.f, cx1 = 0.f, cy1 = 0.f;
+    sxx = sxy = syy = 0.f;
+#pragma unroll
+    for (int tr = 0; tr <= WIN; ++tr) {
+        const float i0 = raw_texel<ST>(rawI + tr * D::RWI, ci0, u8);
+        const float i1 = raw_texel<ST>(rawI + tr * D::RWI, ci1, u8);
+        const float2 g0 = raw_grad<ST>(rawG + tr * D::RWG, cg0);
+        const float2 g1 = raw_grad<ST>(rawG + tr * D::RWG, cg1);
+        const float hI = fmaf(ax, i1 - i0, i0);
+        const float hX = fmaf(ax, g1.x - g0.x, g0.x);
+        const float hY = fmaf(ax, g1.y - g0.y, g0.y);
+        if (tr > 0) {
+            const float I = fmaf(ay, hI - pI, pI);
+            const float X = fmaf(ay, hX - pX, pX);
+            const float Y = fmaf(ay, hY - pY, pY);
+            Xw[tr - 1] = X;
+            Yw[tr - 1] = Y;
+            sxx = fmaf(X, X, sxx);
+            sxy = fmaf(X, Y, sxy);
+            syy = fmaf(Y, Y, syy);
+            // Same two chains as the iteration's correlation, so that J == I
+            // gives c - sum J grad I == 0 exactly (zero flow on equal frames).
+            if (tr & 1) {
+                cx0 = fmaf(I, X, cx0);
+                cy0 = fmaf(I, Y, cy0);
+            } else {
+                cx1 = fmaf(I, X, cx1);
+                cy1 = fmaf(I, Y, cy1);
+            }
+        }
+        pI = hI;
+        pX = hX;
+        pY = hY;
+    }
+    if (!tapcol) sxx = sxy = syy = 0.f;
+    cx = tapcol ? cx0 + cx1 : 0.f;
+    cy = tapcol ? cy0 + cy1 : 0.f;
+}
+
+// sum over the window of J(c + (i, j)) (Ix, Iy) from the pairs; the window's
+// top-left tap sits at pair (oy, ox) of the search region.
+template <int ST, int WIN>
+__device__ __forceinline__ void correlate_staged(const unsigned *W, int ox, int oy, float bx, float by,
                                                  int lane, const float (&Xw)[WIN],
                                                  const float (&Yw)[WIN], float &sx, float &sy) {
-    using D = StageDims<WIN>;
+    using D = Dims<ST, WIN>;
     const bool tapcol = lane < WIN;
-    const float2 *base = S + oy * D::SP + ox + (tapcol ? lane : 0);
+    const float2 *base = (const float2 *)W + oy * D::SP + ox + (tapcol ? lane : 0);
     float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ph = 0.f;
 #pragma unroll
     for (int tr = 0; tr <= WIN; ++tr) {
@@ -211,15 +259,40 @@ __device__ __forceinline__ void correlate_staged(const float2 *S, int ox, int oy
 template <int ST, int WIN>
 __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &J, float px,
                                            float py, float gx, float gy, int max_iter,
-                                           float eps2, float tau_n, int lane, bool u8, float *Sw,
+                                           float eps2, float tau_n, int lane, bool u8, unsigned *W,
                                            float &nux, float &nuy, int &k, bool &conv) {
-    constexpr int R = WIN / 2;
+    using D = Dims<ST, WIN>;
+    constexpr int R = D::R;
     const float fpx = floorf(px), fpy = floorf(py);
     const int ipx = (int)fpx, ipy = (int)fpy;
     const float ax = px - fpx, ay = py - fpy;
+    nux = nuy = 0.f;
+    k = 0;
+    conv = false;
+
+    // One copy batch: the template window and the search region around the
+    // initial centre p + g.
+    LevelCopy lc;
+    const int esz = u8 ? 1 : D::ESZ;
+    __syncwarp();
+    lc.tcol_i = copy_rows(P.img, P.img_pitch, P.w, P.h, esz, ipx - R, D::T, ipy - R, D::T, D::RWI,
+                          W, lane);
+    lc.tcol_g = copy_rows(P.grad, P.grad_pitch, P.w, P.h, D::GSZ, ipx - R, D::T, ipy - R, D::T,
+                          D::RWG, W + D::T * D::RWI, lane);
+    const float c0x = ax + gx, c0y = ay + gy;
+    const bool c0_ok = fabsf(c0x) < 1.0e8f && fabsf(c0y) < 1.0e8f;
+    int sjx = 0, sjy = 0;
+    if (c0_ok) {
+        sjx = ipx + (int)floorf(c0x);
+        sjy = ipy + (int)floorf(c0y);
+        copy_search<ST, WIN>(J, u8, sjx, sjy, lane, W, lc);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+
     float Xw[WIN], Yw[WIN];
     float sxx, sxy, syy, cx, cy;
-    template_window<ST, WIN>(P, ipx, ipy, ax, ay, lane, u8, Xw, Yw, sxx, sxy, syy, cx, cy);
+    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, u8, W, lc, Xw, Yw, sxx, sxy, syy, cx, cy);
     sxx = warp_sum(sxx);
     sxy = warp_sum(sxy);
     syy = warp_sum(syy);
@@ -228,13 +301,14 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     const float dd = sxx - syy;
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
     const float lmin = det / lmax;
-    nux = nuy = 0.f;
-    k = 0;
-    conv = false;
     if (!(lmin >= tau_n) || !(lmin > 0.f)) return OMT_PT_LOST_EIG;
-    const float2 *S = (const float2 *)Sw;
-    int sjx = 0, sjy = 0;
     bool staged = false;
+    if (c0_ok) {
+        __syncwarp();  // the template is read: its raw rows may be overwritten
+        make_pairs<ST, WIN>(J, u8, lane, W, lc);
+        __syncwarp();
+        staged = true;
+    }
     while (k < max_iter) {
         // Centre c = p + g + nu, held as (ipx, ipy) + (ccx, ccy).
         const float ccx = ax + gx + nux, ccy = ay + gy + nuy;
@@ -246,14 +320,19 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
             jy > J.h - 1 + R || (jy == J.h - 1 + R && by > 0.f))
             return OMT_PT_LOST_OOB;
         if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
-            stage_region<ST, WIN>(J, u8, jx, jy, lane, Sw);
+            __syncwarp();
+            copy_search<ST, WIN>(J, u8, jx, jy, lane, W, lc);
+            cp_async_wait_all();
+            __syncwarp();
+            make_pairs<ST, WIN>(J, u8, lane, W, lc);
+            __syncwarp();
             sjx = jx;
             sjy = jy;
             staged = true;
         }
         float sx, sy;
-        correlate_staged<WIN>(S, jx - sjx + MARGIN, jy - sjy + MARGIN, bx, by, lane, Xw, Yw, sx,
-                              sy);
+        correlate_staged<ST, WIN>(W, jx - sjx + MARGIN, jy - sjy + MARGIN, bx, by, lane, Xw, Yw,
+                                  sx, sy);
         warp_sum2(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
         const float ex = (syy * bbx - sxy * bby) / det;
@@ -276,7 +355,7 @@ template <int ST, int WIN>
 __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
                                          int max_iter, float eps2, float tau_n, float2 u,
                                          int i, float2 *out, uint8_t *status, uint8_t *iters,
-                                         float *Sw) {
+                                         unsigned *W) {
     const int lane = threadIdx.x & 31;
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     int st = OMT_PT_OK;
@@ -289,7 +368,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         int k;
         bool conv;
         st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
-                                  lane, L == 0, Sw, nux, nuy, k, conv);
+                                  lane, L == 0, W, nux, nuy, k, conv);
         itp |= (unsigned long long)k << (8 * L);
         if (st != OMT_PT_OK) break;
         if (!conv) nonconv = true;
@@ -318,21 +397,21 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
     if (iters && lane < levels) iters[(int64_t)i * levels + lane] = (uint8_t)(itp >> (8 * lane));
 }
 
-// Staging buffer of this warp in the block's dynamic shared memory.
-template <int WIN>
-__device__ __forceinline__ float *warp_stage() {
-    extern __shared__ __align__(16) float lk_smem[];
-    return lk_smem + (size_t)(threadIdx.x >> 5) * StageDims<WIN>::PAIRS * 2;
+// This warp's staging words in the block's dynamic shared memory.
+template <int ST, int WIN>
+__device__ __forceinline__ unsigned *warp_words() {
+    extern __shared__ __align__(16) unsigned lk_smem[];
+    return lk_smem + (size_t)(threadIdx.x >> 5) * Dims<ST, WIN>::WORDS;
 }
 
-template <int WIN>
+template <int ST, int WIN>
 constexpr size_t stage_bytes() {
-    return (size_t)LK_WARPS * StageDims<WIN>::PAIRS * sizeof(float2);
+    return (size_t)LK_WARPS * Dims<ST, WIN>::WORDS * 4;
 }
 
 template <int ST, int WIN>
 __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArgs a) {
-    float *Sw = warp_stage<WIN>();
+    unsigned *W = warp_words<ST, WIN>();
     int n = a.n_max;
     if (a.n_dev) {
         const int m = *a.n_dev;
@@ -341,7 +420,7 @@ __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArg
     const int nwarps = gridDim.x * LK_WARPS;
     for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps)
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters, Sw);
+                          a.status, a.iters, W);
 }
 
 // All points of all streams of a batch: the per-stream counts come from the
@@ -350,7 +429,7 @@ __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArg
 template <int ST, int WIN>
 __global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
     __shared__ int32_t pre[OMT_BATCH_MAX_STREAMS + 1];
-    float *Sw = warp_stage<WIN>();
+    unsigned *W = warp_words<ST, WIN>();
     const BatchView t(table);
     const BatchHeader &h = t.hdr();
     const int ns = h.nstreams;
@@ -371,7 +450,7 @@ __global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
         const StreamEntry &e = t.stream(s);
         const int i = g - pre[s];
         lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
-                          e.pts_out, e.status, e.iters, Sw);
+                          e.pts_out, e.status, e.iters, W);
     }
 }
 
@@ -381,9 +460,9 @@ cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
 #define OMT_LK_CASE(W)                                                                    \
     case W:                                                                               \
         if (cudaFuncSetAttribute(lk_kernel<ST, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)stage_bytes<W>()) != cudaSuccess)                  \
+                                 (int)stage_bytes<ST, W>()) != cudaSuccess)                  \
             return cudaGetLastError();                                                    \
-        lk_kernel<ST, W><<<grid, LK_NT, stage_bytes<W>(), s>>>(a);                        \
+        lk_kernel<ST, W><<<grid, LK_NT, stage_bytes<ST, W>(), s>>>(a);                        \
         break;
         OMT_LK_CASE(3) OMT_LK_CASE(5) OMT_LK_CASE(7) OMT_LK_CASE(9) OMT_LK_CASE(11)
         OMT_LK_CASE(13) OMT_LK_CASE(15) OMT_LK_CASE(17) OMT_LK_CASE(19) OMT_LK_CASE(21)
@@ -396,7 +475,7 @@ cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
 
 template <int ST, int WIN>
 cudaError_t launch_batch_win(const uint8_t *table, int sms, cudaStream_t s) {
-    const size_t smem = stage_bytes<WIN>();
+    const size_t smem = stage_bytes<ST, WIN>();
     cudaError_t e = cudaFuncSetAttribute(lk_batch_kernel<ST, WIN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -653,3 +653,78 @@ class PlainGpuBackend(GpuBackend):
             ev = torch.cuda.Event()
             ev.record(self.stream)
         return _Handle(ev, list(items), stepped)
+
+
+# ---------------------------------------------------------------- workload
+
+def build_workload(n_streams: int, duration: float, workload: int = 5, sizes=None, boxes=(20, 300),
+                   max_corners: int = 50):
+    """Stream specs (Poisson arrivals at 25-60 fps, mixed resolutions, 20-300
+    boxes refreshed every 5-15 frames), two rendered frames per resolution
+    (shared by the streams of that size, page-locked) and detection boxes."""
+    import torch
+    from . import synth
+    sizes = sizes or (synth.SD, synth.FHD, synth.UHD)
+    ss = synth.serve_streams(n_streams, duration, workload=workload, sizes=sizes, boxes=boxes)
+    renders = {}
+    for sz in sorted({s.size for s in ss}):
+        rng = np.random.default_rng(synth.seed_for(workload) + sz[0])
+        w, h = sz
+        tex = synth.Texture.draw(rng, w + 40, h + 40, ox=-20, oy=-20, n_blobs=max(64, w * h // 6000))
+        f0 = synth.render_shift(tex, w, h, 0.0, 0.0)
+        f1 = synth.render_shift(tex, w, h, 3.3, -2.1)
+        renders[sz] = [torch.from_numpy(f0).pin_memory(), torch.from_numpy(f1).pin_memory()]
+    specs, frames, det = [], {}, {}
+    for s in ss:
+        rng = np.random.default_rng(synth.seed_for(workload, s.stream) + 7)
+        w, h = s.size
+        specs.append(StreamSpec(s.stream, s.size, s.n_boxes, s.refresh, s.arrivals, max_corners))
+        frames[s.stream] = renders[s.size]
+        det[s.stream] = synth.uniform_boxes(rng, w, h, s.n_boxes, side=(40.0, 150.0))
+    return specs, frames, det
+
+
+def serve(specs, frames, det, params, budget_bytes: int, plain: bool = False, deadline=None,
+          keep_boxes: bool = False, device="cuda", max_in_flight: int = 2):
+    """Run the loop on the GPU; returns (Stats, backend)."""
+    max_w = max(s.size[0] for s in specs)
+    max_h = max(s.size[1] for s in specs)
+    caps_boxes = sum(max(1, s.n_boxes) for s in specs)
+    cls = PlainGpuBackend if plain else GpuBackend
+    be = cls(params, len(specs), caps_boxes, max_w, max_h, max(s.max_corners for s in specs),
+             frames, det, device=device, keep_boxes=keep_boxes)
+    sch = Scheduler(be, budget_bytes, max_in_flight=max_in_flight)
+    last = max(float(s.arrivals[-1]) for s in specs if len(s.arrivals))
+    stats = sch.run(specs, deadline=deadline if deadline is not None else last + 30.0)
+    return stats, be
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import torch
+    from . import omt
+    ap = argparse.ArgumentParser(description="serve many synthetic video streams")
+    ap.add_argument("--streams", type=int, default=64)
+    ap.add_argument("--duration", type=float, default=10.0, help="seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=40.0)
+    ap.add_argument("--storage", default="f16", choices=["f16", "f32"])
+    ap.add_argument("--plain", action="store_true", help="baseline: plain FP32 calls, one frame at a time")
+    args = ap.parse_args(argv)
+    specs, frames, det = build_workload(args.streams, args.duration)
+    storage = omt.F16 if (args.storage == "f16" and not args.plain) else omt.F32
+    params = omt.default_params(levels=4, win=21, max_corners=50, storage=storage)
+    # warm-up: one short run so one-time setup is outside the measurement
+    serve(specs[:2], frames, det, params, int(args.budget_gb * 2 ** 30), plain=args.plain,
+          deadline=0.5)
+    torch.cuda.synchronize()
+    stats, _ = serve(specs, frames, det, params, int(args.budget_gb * 2 ** 30), plain=args.plain,
+                     deadline=args.duration + 5.0)
+    out = stats.summary()
+    out.update({"streams": args.streams, "duration_s": args.duration, "budget_gb": args.budget_gb,
+                "path": "plain FP32 per frame" if args.plain else f"batched {args.storage}"})
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
