@@ -137,6 +137,15 @@ def lk_flops(iters: np.ndarray, status: np.ndarray, levels: int, win: int) -> fl
     return float(27 * N * reached.sum() + 12 * N * it.sum())
 
 
+def pyramid_bytes_per_px(storage: str, levels: int) -> float:
+    """Compulsory DRAM bytes of the pyramid per level-0 pixel: read the u8
+    frame, write its u8 copy, write every level >= 1 once and every level's
+    gradient pair once (level L holds 4^-L of the pixels)."""
+    esz = 2.0 if storage == "f16" else 4.0
+    frac = [4.0 ** -L for L in range(levels)]
+    return 1.0 + 1.0 + esz * sum(frac[1:]) + 2 * esz * sum(frac)
+
+
 def params_for(omt, storage, max_corners):
     return omt.default_params(levels=LEVELS, win=WIN, max_iter=MAX_ITER, eps=EPS,
                               max_corners=max_corners, storage=storage, min_dist=MIN_DIST)
@@ -236,14 +245,19 @@ def run_omt(args, ws, rank, local):
         n_pts += n
         flops += lk_flops(it, st, LEVELS, WIN)
 
-    # ---- LK kernel alone: events around the LK phase, eager, same steps
-    lk_ev = []
+    # ---- per-phase kernel time: events around the LK and pyramid phases,
+    # eager, same steps and stream
+    ph_ev = []
     for k in range(args.steps):
-        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        B.step_phases(lk_events=e)
-        lk_ev.append(e)
+        e = {p: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for p in (omt.PHASE_PYRAMID, omt.PHASE_LK)}
+        B.step_phases(events=e)
+        ph_ev.append(e)
     torch.cuda.synchronize()
-    lk_ms = float(np.mean([a.elapsed_time(b) for a, b in lk_ev]))
+    lk_ms = float(np.mean([e[omt.PHASE_LK][0].elapsed_time(e[omt.PHASE_LK][1]) for e in ph_ev]))
+    pyr_ms = float(np.mean([e[omt.PHASE_PYRAMID][0].elapsed_time(e[omt.PHASE_PYRAMID][1]) for e in ph_ev]))
+    px0 = sum(sp.size[0] * sp.size[1] for sp in streams)
+    pyr_bytes = px0 * pyramid_bytes_per_px(args.storage, LEVELS)
 
     # ---- end to end: pinned frames H2D, step, boxes D2H, every step
     outs_h = [torch.empty((len(sp.boxes), 4), dtype=torch.float32).pin_memory() for sp in streams]
@@ -300,6 +314,12 @@ def run_omt(args, ws, rank, local):
                      "traffic": None,
                      "peak_source": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({pk_src} max clock)",
                      "lk_ms_per_step": lk_ms, "lk_share": lk_ms / ms_step},
+        "roofline_pyramid": {"kernel": "pyramid_batch_kernel (all levels)", "bound": "hbm",
+                             "achieved": pyr_bytes / (pyr_ms * 1e-3) / 1e9,
+                             "peak": pk.get("hbm_gbs", 6400.0), "unit": "GB/s",
+                             "frac": pyr_bytes / (pyr_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6400.0),
+                             "traffic": None, "bytes_per_level0_px": pyramid_bytes_per_px(args.storage, LEVELS),
+                             "ms_per_step": pyr_ms},
         "clocks": clk,
         "gpu_launches": (LEVELS + 5) * args.steps,
     }

@@ -438,18 +438,18 @@ class BatchTracker:
             batch_step(self.tables[self.cur], self.caps, self.params, self.dev_table, stream)
         self.cur = 1 - self.cur
 
-    def step_phases(self, lk_events=None, stream=None):
-        """The step as upload + four phases; with lk_events=(start, end)
-        CUDA events, they bracket the LK phase."""
+    def step_phases(self, events=None, stream=None):
+        """The step as upload + four phases.  events: optional dict phase ->
+        (start, end) CUDA events recorded around that phase."""
+        events = events or {}
         batch_upload(self.tables[self.cur], self.caps, self.dev_table, stream)
-        batch_phase(self.dev_table, self.caps, self.params, PHASE_PYRAMID, stream)
-        batch_phase(self.dev_table, self.caps, self.params, PHASE_CORNERS, stream)
-        if lk_events:
-            lk_events[0].record()
-        batch_phase(self.dev_table, self.caps, self.params, PHASE_LK, stream)
-        if lk_events:
-            lk_events[1].record()
-        batch_phase(self.dev_table, self.caps, self.params, PHASE_BOXES, stream)
+        for phase in (PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES):
+            ev = events.get(phase)
+            if ev:
+                ev[0].record()
+            batch_phase(self.dev_table, self.caps, self.params, phase, stream)
+            if ev:
+                ev[1].record()
         self.cur = 1 - self.cur
 
     def count(self, s: int) -> int:
