@@ -49,11 +49,11 @@ __device__ __forceinline__ float det2(float a, float d, float b) {
 
 // ------------------------------------------------------------ staging
 // Per warp and level, the texels the level needs are copied global ->
-// shared with cp.async (no registers held, all rows in flight at once): the
+// shared with 16-byte cp.async (no registers held, all rows in flight): the
 // (win+1)^2 window of frame t under the template (I and (Ix, Iy)) and frame
 // t+1's search region around the initial centre, MARGIN texels wider than
 // the window on every side.  Rows are clamped to the level when copied; a
-// row is copied as the 4-byte words covering its column range clamped to
+// row is copied as the 16-byte chunks covering its column range clamped to
 // the level, and columns are clamped when the raw rows are read back.  The
 // search region is then converted once to (J(x), J(x+1)) float pairs, so an
 // iteration's tap row is one 8-byte shared load per lane.  The region is
@@ -68,18 +68,22 @@ struct Dims {
     static constexpr int SP = WIN + 2 * MARGIN;       // search pairs per row
     static constexpr int ESZ = ST == OMT_F32 ? 4 : 2; // bytes of a level >= 1 texel
     static constexpr int GSZ = 2 * ESZ;               // bytes of a gradient texel
-    static constexpr int RWJ = ((SP + 1) * ESZ + 3) / 4 + 1;  // words per raw search row
-    static constexpr int RWI = (T * ESZ + 3) / 4 + 1;         // words per raw template I row
-    static constexpr int RWG = (T * GSZ) / 4;                 // words per raw gradient row
+    // 4-byte words per raw row: the 16-byte chunks covering the row's bytes
+    // from a 16-byte aligned start (at most 15 bytes of lead-in), rounded to
+    // whole chunks.
+    static constexpr int chunks(int bytes) { return (bytes + 15 + 15) / 16; }
+    static constexpr int RWJ = 4 * chunks((SP + 1) * ESZ);
+    static constexpr int RWI = 4 * chunks(T * ESZ);
+    static constexpr int RWG = 4 * chunks(T * GSZ);
     static constexpr int TRAW = T * (RWI + RWG);              // raw template words
     static constexpr int PAIRW = 2 * SH * SP;                 // pair area words
-    static constexpr int UNION = TRAW > PAIRW ? TRAW : PAIRW; // template raw aliases pairs
-    static constexpr int WORDS = UNION + SH * RWJ;            // per warp
+    static constexpr int UNION = (TRAW > PAIRW ? TRAW : PAIRW + 3) & ~3;  // 16-byte multiple
+    static constexpr int WORDS = UNION + SH * RWJ;            // per warp, 16-byte multiple
 };
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -87,17 +91,22 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Copy `rows` rows starting at level row y0 (each clamped), texel columns
-// [x0, x0 + ncols) clamped to the level, as raw words into dst (rw words per
-// row).  Returns the level column of the first texel held by each raw row.
+// [x0, x0 + ncols) clamped to the level, as 16-byte chunks into dst (rw
+// 4-byte words per row, a multiple of 4).  A chunk is 16-byte aligned in the
+// row and every row is 128-byte aligned with its pitch a multiple of 128, so
+// a chunk never leaves its row's pitch.  Returns the level column of the
+// first texel held by each raw row.
 __device__ __forceinline__ int copy_rows(const uint8_t *plane, int64_t pitch, int w, int h,
                                          int esz, int x0, int ncols, int y0, int rows, int rw,
                                          unsigned *dst, int lane) {
     const int xa = clampi(x0, 0, w - 1), xb = clampi(x0 + ncols - 1, 0, w - 1);
-    const int b0 = (xa * esz) & ~3, b1 = (xb + 1) * esz;
-    const int nw = (b1 - b0 + 3) >> 2;
-    for (int r = 0; r < rows; ++r) {
+    const int b0 = (xa * esz) & ~15, b1 = (xb + 1) * esz;
+    const int nc = (b1 - b0 + 15) >> 4;  // chunks per row
+    const int total = rows * nc;
+    for (int k = lane; k < total; k += 32) {
+        const int r = k / nc, c = k - r * nc;
         const uint8_t *row = plane + (int64_t)clampi(y0 + r, 0, h - 1) * pitch + b0;
-        for (int k = lane; k < nw; k += 32) cp_async4(dst + r * rw + k, row + 4 * k);
+        cp_async16(dst + r * rw + 4 * c, row + 16 * c);
     }
     return b0 / esz;
 }
@@ -271,7 +280,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     conv = false;
 
     // One copy batch: the template window and the search region around the
-    // initial centre p + g.
+    // initial centre p + g (16-byte chunks, all in flight together).
     LevelCopy lc;
     const int esz = u8 ? 1 : D::ESZ;
     __syncwarp();
