@@ -54,10 +54,10 @@ __device__ __forceinline__ float det2(float a, float d, float b) {
 // t+1's search region around the initial centre, MARGIN texels wider than
 // the window on every side.  Rows are clamped to the level when copied; a
 // row is copied as the 16-byte chunks covering its column range clamped to
-// the level, and columns are clamped when the raw rows are read back.  The
-// search region is then converted once to (J(x), J(x+1)) float pairs, so an
-// iteration's tap row is one 8-byte shared load per lane.  The region is
-// copied again only if the centre moves more than MARGIN texels away.
+// the level, and columns are clamped when the raw rows are read back: an
+// iteration's tap row is two shared loads per lane (its texel and the right
+// neighbour).  The region is copied again only if the centre moves more
+// than MARGIN texels away.
 constexpr int MARGIN = 4;
 
 template <int ST, int WIN>
@@ -76,8 +76,7 @@ struct Dims {
     static constexpr int RWI = 4 * chunks(T * ESZ);
     static constexpr int RWG = 4 * chunks(T * GSZ);
     static constexpr int TRAW = T * (RWI + RWG);              // raw template words
-    static constexpr int PAIRW = 2 * SH * SP;                 // pair area words
-    static constexpr int UNION = (TRAW > PAIRW ? TRAW : PAIRW + 3) & ~3;  // 16-byte multiple
+    static constexpr int UNION = TRAW;                        // template area (16-byte multiple)
     static constexpr int WORDS = UNION + SH * RWJ;            // per warp, 16-byte multiple
 };
 
@@ -143,24 +142,6 @@ __device__ __forceinline__ void copy_search(const LevelView &J, bool u8, int jx,
     lc.sy0 = jy - D::R - MARGIN;
     lc.scol = copy_rows(J.img, J.img_pitch, J.w, J.h, u8 ? 1 : D::ESZ, lc.sx0, D::SP + 1, lc.sy0,
                         D::SH, D::RWJ, W + D::UNION, lane);
-}
-
-// Raw search rows -> (J(x), J(x+1)) pairs.
-template <int ST, int WIN>
-__device__ __forceinline__ void make_pairs(const LevelView &J, bool u8, int lane, unsigned *W,
-                                           const LevelCopy &lc) {
-    using D = Dims<ST, WIN>;
-    float *P = (float *)W;
-    const unsigned *raw = W + D::UNION;
-    for (int c = lane; c <= D::SP; c += 32) {
-        const int col = clampi(lc.sx0 + c, 0, J.w - 1) - lc.scol;
-#pragma unroll 6
-        for (int r = 0; r < D::SH; ++r) {
-            const float v = raw_texel<ST>(raw + r * D::RWJ, col, u8);
-            if (c < D::SP) P[2 * (r * D::SP + c)] = v;
-            if (c >= 1) P[2 * (r * D::SP + c - 1) + 1] = v;
-        }
-    }
 }
 
 // Two warp sums at once: lanes 0-15 end with the total of a, lanes 16-31
@@ -233,20 +214,23 @@ __device__ __forceinline__ void template_window(const LevelView &P, int tx0, flo
     cy = tapcol ? cy0 + cy1 : 0.f;
 }
 
-// sum over the window of J(c + (i, j)) (Ix, Iy) from the pairs; the window's
-// top-left tap sits at pair (oy, ox) of the search region.
-template <int ST, int WIN>
-__device__ __forceinline__ void correlate_staged(const unsigned *W, int ox, int oy, float bx, float by,
-                                                 int lane, const float (&Xw)[WIN],
-                                                 const float (&Yw)[WIN], float &sx, float &sy) {
+// sum over the window of J(c + (i, j)) (Ix, Iy), read straight from the raw
+// search rows: tap row tr is raw row oy + tr (rows were clamped when
+// copied), its two texels sit at raw columns col0 and col1 (clamped level
+// columns of the lane's tap and its right neighbour).
+template <int ST, bool U8, int WIN>
+__device__ __forceinline__ void correlate_raw(const unsigned *rawJ, int oy, int col0, int col1,
+                                              float bx, float by, int lane, const float (&Xw)[WIN],
+                                              const float (&Yw)[WIN], float &sx, float &sy) {
     using D = Dims<ST, WIN>;
     const bool tapcol = lane < WIN;
-    const float2 *base = (const float2 *)W + oy * D::SP + ox + (tapcol ? lane : 0);
+    const unsigned *base = rawJ + oy * D::RWJ;
     float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ph = 0.f;
 #pragma unroll
     for (int tr = 0; tr <= WIN; ++tr) {
-        const float2 pv = base[tr * D::SP];
-        const float h = fmaf(bx, pv.y - pv.x, pv.x);
+        const unsigned *row = base + tr * D::RWJ;
+        const float v0 = raw_texel<ST>(row, col0, U8), v1 = raw_texel<ST>(row, col1, U8);
+        const float h = fmaf(bx, v1 - v0, v0);
         if (tr > 0) {
             const float jv = fmaf(by, h - ph, ph);
             if (tr & 1) {
@@ -311,13 +295,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
     const float lmin = det / lmax;
     if (!(lmin >= tau_n) || !(lmin > 0.f)) return OMT_PT_LOST_EIG;
-    bool staged = false;
-    if (c0_ok) {
-        __syncwarp();  // the template is read: its raw rows may be overwritten
-        make_pairs<ST, WIN>(J, u8, lane, W, lc);
-        __syncwarp();
-        staged = true;
-    }
+    bool staged = c0_ok;
     while (k < max_iter) {
         // Centre c = p + g + nu, held as (ipx, ipy) + (ccx, ccy).
         const float ccx = ax + gx + nux, ccy = ay + gy + nuy;
@@ -333,15 +311,16 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
             copy_search<ST, WIN>(J, u8, jx, jy, lane, W, lc);
             cp_async_wait_all();
             __syncwarp();
-            make_pairs<ST, WIN>(J, u8, lane, W, lc);
-            __syncwarp();
             sjx = jx;
             sjy = jy;
             staged = true;
         }
+        const int tx = jx - R + (lane < WIN ? lane : 0);
+        const int col0 = clampi(tx, 0, J.w - 1) - lc.scol, col1 = clampi(tx + 1, 0, J.w - 1) - lc.scol;
+        const int oy = jy - sjy + MARGIN;
         float sx, sy;
-        correlate_staged<ST, WIN>(W, jx - sjx + MARGIN, jy - sjy + MARGIN, bx, by, lane, Xw, Yw,
-                                  sx, sy);
+        if (u8) correlate_raw<ST, true, WIN>(W + D::UNION, oy, col0, col1, bx, by, lane, Xw, Yw, sx, sy);
+        else correlate_raw<ST, false, WIN>(W + D::UNION, oy, col0, col1, bx, by, lane, Xw, Yw, sx, sy);
         warp_sum2(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
         const float ex = (syy * bbx - sxy * bby) / det;
