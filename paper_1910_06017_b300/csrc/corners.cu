@@ -65,6 +65,7 @@ __device__ __forceinline__ int px(const RespArgs &a, int x, int y) {
 __device__ __forceinline__ void response_tile(const RespArgs &a, int ox, int oy) {
     __shared__ int2 g[RTY + 4][RTX + 4];
     __shared__ uint32_t R[RTY + 2][RTX + 2];
+    __shared__ uint8_t px8[RTY + 6][RTX + 8];  // u8 texels of r101(q), q in the tile +- 3
     const int tid = threadIdx.x;
     __syncthreads();
 
@@ -80,15 +81,36 @@ __device__ __forceinline__ void response_tile(const RespArgs &a, int ox, int oy)
         if (!__syncthreads_or(hit)) return;
     }
 
+    // Stage the u8 texels the gradients read.  Position (r, c) holds the
+    // texel at (r101(ox-3+c), r101(oy-3+r)); a gradient at the pixel r101(q)
+    // reads r101(r101(q) +- 1), which equals the texel staged at q +- 1
+    // except where q itself lies outside the frame: those positions are
+    // re-read through the map below.
+    for (int i = tid; i < (RTY + 6) * (RTX + 6); i += RNT) {
+        const int r = i / (RTX + 6), c = i - r * (RTX + 6);
+        px8[r][c] = __ldg(a.img + (int64_t)reflect101(oy - 3 + r, a.h) * a.pitch +
+                          reflect101(ox - 3 + c, a.w));
+    }
+    __syncthreads();
+
     // Raw Scharr at the pixels r101(q) for q in the tile +- 2.
     for (int i = tid; i < (RTY + 4) * (RTX + 4); i += RNT) {
         const int r = i / (RTX + 4), c = i - r * (RTX + 4);
-        const int x = reflect101(ox - 2 + c, a.w), y = reflect101(oy - 2 + r, a.h);
-        const int xm = reflect101(x - 1, a.w), xp = reflect101(x + 1, a.w);
-        const int ym = reflect101(y - 1, a.h), yp = reflect101(y + 1, a.h);
-        const int i00 = px(a, xm, ym), i01 = px(a, x, ym), i02 = px(a, xp, ym);
-        const int i10 = px(a, xm, y), i12 = px(a, xp, y);
-        const int i20 = px(a, xm, yp), i21 = px(a, x, yp), i22 = px(a, xp, yp);
+        const int qx = ox - 2 + c, qy = oy - 2 + r;
+        int i00, i01, i02, i10, i12, i20, i21, i22;
+        if (qx >= 0 && qx < a.w && qy >= 0 && qy < a.h) {
+            // in-frame: neighbours are the staged positions around (r+1, c+1)
+            i00 = px8[r][c];     i01 = px8[r][c + 1];     i02 = px8[r][c + 2];
+            i10 = px8[r + 1][c];                          i12 = px8[r + 1][c + 2];
+            i20 = px8[r + 2][c]; i21 = px8[r + 2][c + 1]; i22 = px8[r + 2][c + 2];
+        } else {
+            const int x = reflect101(qx, a.w), y = reflect101(qy, a.h);
+            const int xm = reflect101(x - 1, a.w), xp = reflect101(x + 1, a.w);
+            const int ym = reflect101(y - 1, a.h), yp = reflect101(y + 1, a.h);
+            i00 = px(a, xm, ym); i01 = px(a, x, ym); i02 = px(a, xp, ym);
+            i10 = px(a, xm, y);                      i12 = px(a, xp, y);
+            i20 = px(a, xm, yp); i21 = px(a, x, yp); i22 = px(a, xp, yp);
+        }
         const int gx = 3 * (i02 - i00) + 10 * (i12 - i10) + 3 * (i22 - i20);
         const int gy = 3 * (i20 - i00) + 10 * (i21 - i01) + 3 * (i22 - i02);
         g[r][c] = make_int2(gx, gy);

@@ -1,28 +1,32 @@
 // pyramid.cu -- K1: Gaussian pyramid and Scharr gradients (Section V-A,
 // preprocessing).
 //
-// One launch per level L.  A CTA owns a 64x16 tile of level L: it stages
-// the tile plus a 2-pixel reflect-101 halo in shared memory (coalesced
-// loads), writes the tile's gradients (Ix, Iy), and writes the 32x8 tile of
-// level L+1 that decimates it.  Level 0 also copies the u8 frame into the
-// pyramid buffer.  Sums use the integer binomial weights and scale by a power
-// of two at the end, so every value that is dyadic-exact in FP32 (levels 0-2)
-// comes out bit-identical to the definition.
+// One launch per level L.  A 256-thread CTA owns a 128x32 tile of level L:
+// it stages the tile plus a 2-pixel reflect-101 halo in shared memory
+// (interior tiles with aligned 4-byte or 16-byte row loads, border tiles
+// element by element through the reflect-101 map), writes the tile's
+// gradients (Ix, Iy) with conflict-free shared reads and coalesced stores,
+// and writes the 64x16 tile of level L+1 that decimates it.  Level 0 also copies the u8
+// frame into the pyramid buffer.  Sums use the integer binomial weights and
+// scale by a power of two at the end, so every value that is dyadic-exact in
+// FP32 (levels 0-2) comes out bit-identical to the definition.
 #include "omt_internal.cuh"
 
 namespace omt {
 namespace {
 
-constexpr int TX = 64;  // level-L tile width
-constexpr int TY = 16;  // level-L tile height
-constexpr int NT = 256; // threads per CTA
+constexpr int TX = 128;  // level-L tile width
+constexpr int TY = 32;   // level-L tile height
+constexpr int NT = 256;  // threads per CTA
 constexpr int SX = TX + 4, SY = TY + 4;
+constexpr int HX = TX / 2;  // level L+1 tile width
 
 struct LevelArgs {
     const uint8_t *src;   // level L: u8 frame (L = 0) or the pyramid's level plane
     int64_t src_pitch;
     int w, h;             // level L size
     int level;
+    bool vec_ok;          // src rows are 4-byte aligned (pointer and pitch)
     uint8_t *copy;        // level-0 u8 copy (L = 0 only)
     int64_t copy_pitch;
     uint8_t *grad;        // level-L gradient plane
@@ -40,6 +44,55 @@ __device__ __forceinline__ float load_src(const LevelArgs &a, int x, int y) {
     return __half2float(((const __half *)row)[x]) + 128.0f;
 }
 
+// Stage level L over [ox-2, ox+TX+2) x [oy-2, oy+TY+2) into s.
+template <int ST>
+__device__ __forceinline__ void stage_tile(const LevelArgs &a, int ox, int oy, float (*s)[SX]) {
+    const int tid = threadIdx.x;
+    const bool interior = ox - 4 >= 0 && oy - 2 >= 0 && ox + TX + 4 <= a.w && oy + TY + 2 <= a.h;
+    if (interior && a.vec_ok) {
+        if (a.level == 0 || ST == OMT_F16) {
+            // 4-byte words from column ox-4 (4-aligned): 4 u8 or 2 half texels each
+            const int per = a.level == 0 ? 4 : 2;
+            const int nwords = (TX + 8) / per;
+            for (int i = tid; i < SY * nwords; i += NT) {
+                const int r = i / nwords, k = i - r * nwords;
+                const uint8_t *row = a.src + (int64_t)(oy - 2 + r) * a.src_pitch;
+                const int x = ox - 4 + k * per;  // first texel of the word
+                const unsigned wv = __ldg((const unsigned *)(row + (int64_t)x * (per == 4 ? 1 : 2)));
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q >= per) break;
+                    const int c = x + q - (ox - 2);
+                    if (c < 0 || c >= SX) continue;
+                    float v;
+                    if (per == 4) v = (float)((wv >> (8 * q)) & 0xFFu);
+                    else v = __half2float(__ushort_as_half((unsigned short)(wv >> (16 * q)))) + 128.0f;
+                    s[r][c] = v;
+                }
+            }
+        } else {
+            // float4 from column ox-4 (16-byte aligned)
+            const int nq = (TX + 8) / 4;
+            for (int i = tid; i < SY * nq; i += NT) {
+                const int r = i / nq, k = i - r * nq;
+                const float4 v = __ldg((const float4 *)(a.src + (int64_t)(oy - 2 + r) * a.src_pitch) +
+                                       (ox - 4) / 4 + k);
+                const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = 4 * k + q - 2;
+                    if (c >= 0 && c < SX) s[r][c] = e[q];
+                }
+            }
+        }
+    } else {
+        for (int i = tid; i < SX * SY; i += NT) {
+            const int r = i / SX, c = i - r * SX;
+            s[r][c] = load_src<ST>(a, reflect101(ox - 2 + c, a.w), reflect101(oy - 2 + r, a.h));
+        }
+    }
+}
+
 // Arguments of level L of the pyramid a batch entry builds (frame t+1).
 __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int L, int levels,
                                                       LevelArgs &a) {
@@ -50,11 +103,13 @@ __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int 
     if (L == 0) {
         a.src = e.frame;
         a.src_pitch = e.frame_pitch;
+        a.vec_ok = (((uintptr_t)e.frame | (uintptr_t)e.frame_pitch) & 3) == 0;
         a.copy = const_cast<uint8_t *>(v.img);
         a.copy_pitch = v.img_pitch;
     } else {
         a.src = v.img;
         a.src_pitch = v.img_pitch;
+        a.vec_ok = true;
         a.copy = nullptr;
         a.copy_pitch = 0;
     }
@@ -73,69 +128,89 @@ __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int 
     }
 }
 
-// One 64x16 tile of level L at (ox, oy): gradients of the tile and the
-// 32x8 tile of level L+1 that decimates it.  Callers loop over tiles with
+// One 128x32 tile of level L at (ox, oy): gradients of the tile and the
+// 64x16 tile of level L+1 that decimates it.  Callers loop over tiles with
 // the whole CTA; the leading barrier keeps tiles from overlapping in the
 // shared arrays.
 template <int ST>
 __device__ __forceinline__ void pyramid_tile(const LevelArgs &a, int ox, int oy) {
     __shared__ float s[SY][SX];
-    __shared__ float hs[SY][TX / 2];
+    __shared__ float hs[SY][HX];
     const int tid = threadIdx.x;
     __syncthreads();
-
-    // Stage level L with a reflect-101 halo of 2.
-    for (int i = tid; i < SX * SY; i += NT) {
-        const int r = i / SX, c = i - r * SX;
-        const int x = reflect101(ox - 2 + c, a.w), y = reflect101(oy - 2 + r, a.h);
-        s[r][c] = load_src<ST>(a, x, y);
-    }
+    stage_tile<ST>(a, ox, oy, s);
     if (a.copy) {
-        for (int i = tid; i < TX * TY; i += NT) {
-            const int r = i / TX, c = i - r * TX;
-            const int x = ox + c, y = oy + r;
-            if (x < a.w && y < a.h) a.copy[(int64_t)y * a.copy_pitch + x] = a.src[(int64_t)y * a.src_pitch + x];
+        // u8 copy of the tile, 4 bytes per thread where the row allows
+        for (int i = tid; i < TY * (TX / 4); i += NT) {
+            const int r = i / (TX / 4), k = i - r * (TX / 4);
+            const int x = ox + 4 * k, y = oy + r;
+            if (y >= a.h || x >= a.w) continue;
+            uint8_t *dst = a.copy + (int64_t)y * a.copy_pitch + x;
+            const uint8_t *src = a.src + (int64_t)y * a.src_pitch + x;
+            if (x + 3 < a.w && a.vec_ok) {
+                *(unsigned *)dst = __ldg((const unsigned *)src);
+            } else {
+                for (int q = 0; q < 4 && x + q < a.w; ++q) dst[q] = src[q];
+            }
         }
     }
     __syncthreads();
 
-    // Scharr gradients of the tile, intensity per level pixel.
-    for (int i = tid; i < TX * TY; i += NT) {
-        const int r = i / TX, c = i - r * TX;
-        const int x = ox + c, y = oy + r;
-        if (x >= a.w || y >= a.h) continue;
-        const int R = r + 2, C = c + 2;
-        float gx = 3.0f * (s[R - 1][C + 1] - s[R - 1][C - 1]);
-        gx += 10.0f * (s[R][C + 1] - s[R][C - 1]);
-        gx += 3.0f * (s[R + 1][C + 1] - s[R + 1][C - 1]);
-        float gy = 3.0f * (s[R + 1][C - 1] - s[R - 1][C - 1]);
-        gy += 10.0f * (s[R + 1][C] - s[R - 1][C]);
-        gy += 3.0f * (s[R + 1][C + 1] - s[R - 1][C + 1]);
-        gx *= (1.0f / 32.0f);
-        gy *= (1.0f / 32.0f);
-        uint8_t *row = a.grad + (int64_t)y * a.grad_pitch;
-        if (ST == OMT_F32) ((float2 *)row)[x] = make_float2(gx, gy);
-        else ((__half2 *)row)[x] = __floats2half2_rn(gx, gy);
+    // Scharr gradients, intensity per level pixel.  Thread (tx, ty) takes
+    // columns tx + 32 q and rows 4 ty + rr: conflict-free shared reads, and a
+    // warp stores 32 consecutive pixels of a row.
+    {
+        const int tx = tid & 31, ty = tid >> 5;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int r = 4 * ty + rr;
+            const int y = oy + r;
+            if (y >= a.h) break;
+            const int R = r + 2;
+            uint8_t *row = a.grad + (int64_t)y * a.grad_pitch;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = tx + 32 * q, x = ox + c;
+                if (x >= a.w) break;
+                const int C = c + 2;
+                float gx = 3.0f * (s[R - 1][C + 1] - s[R - 1][C - 1]);
+                gx += 10.0f * (s[R][C + 1] - s[R][C - 1]);
+                gx += 3.0f * (s[R + 1][C + 1] - s[R + 1][C - 1]);
+                float gy = 3.0f * (s[R + 1][C - 1] - s[R - 1][C - 1]);
+                gy += 10.0f * (s[R + 1][C] - s[R - 1][C]);
+                gy += 3.0f * (s[R + 1][C + 1] - s[R - 1][C + 1]);
+                gx *= (1.0f / 32.0f);
+                gy *= (1.0f / 32.0f);
+                if (ST == OMT_F32) ((float2 *)row)[x] = make_float2(gx, gy);
+                else ((__half2 *)row)[x] = __floats2half2_rn(gx, gy);
+            }
+        }
     }
     if (a.next) {
         // Binomial reduce to level L+1: horizontal pass at the even columns...
-        for (int i = tid; i < SY * (TX / 2); i += NT) {
-            const int r = i / (TX / 2), X = i - r * (TX / 2);
+        for (int i = tid; i < SY * HX; i += NT) {
+            const int r = i / HX, X = i - r * HX;
             const int c = 2 * X + 2;
             hs[r][X] = (s[r][c - 2] + s[r][c + 2]) + 4.0f * (s[r][c - 1] + s[r][c + 1]) + 6.0f * s[r][c];
         }
         __syncthreads();
-        // ...then vertical at the even rows, scaled by 1/256.
-        for (int i = tid; i < (TX / 2) * (TY / 2); i += NT) {
-            const int Y = i / (TX / 2), X = i - Y * (TX / 2);
-            const int gXo = ox / 2 + X, gYo = oy / 2 + Y;
-            if (gXo >= a.nw || gYo >= a.nh) continue;
-            const int r = 2 * Y + 2;
-            float v = (hs[r - 2][X] + hs[r + 2][X]) + 4.0f * (hs[r - 1][X] + hs[r + 1][X]) + 6.0f * hs[r][X];
-            v *= (1.0f / 256.0f);
-            uint8_t *row = a.next + (int64_t)gYo * a.next_pitch;
-            if (ST == OMT_F32) ((float *)row)[gXo] = v;
-            else ((__half *)row)[gXo] = __float2half_rn(v - 128.0f);
+        // ...then vertical at the even rows, scaled by 1/256: thread (X, Y0)
+        // takes rows Y0 + 4 q of column X.
+        const int X = tid & (HX - 1), Y0 = tid / HX;
+        const int gX = ox / 2 + X;
+        if (gX < a.nw) {
+#pragma unroll
+            for (int q = 0; q < (TY / 2) / (NT / HX); ++q) {
+                const int Y = Y0 + (NT / HX) * q;
+                const int gY = oy / 2 + Y;
+                if (gY >= a.nh) break;
+                const int r = 2 * Y + 2;
+                const float v = ((hs[r - 2][X] + hs[r + 2][X]) + 4.0f * (hs[r - 1][X] + hs[r + 1][X]) +
+                                 6.0f * hs[r][X]) * (1.0f / 256.0f);
+                uint8_t *row = a.next + (int64_t)gY * a.next_pitch;
+                if (ST == OMT_F32) ((float *)row)[gX] = v;
+                else ((__half *)row)[gX] = __float2half_rn(v - 128.0f);
+            }
         }
     }
 }
@@ -178,11 +253,13 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
         if (L == 0) {
             a.src = frame;
             a.src_pitch = (int64_t)pitch;
+            a.vec_ok = (((uintptr_t)frame | (uintptr_t)pitch) & 3) == 0;
             a.copy = base + lv.img_off;
             a.copy_pitch = lv.img_pitch;
         } else {
             a.src = base + lv.img_off;
             a.src_pitch = lv.img_pitch;
+            a.vec_ok = true;
             a.copy = nullptr;
             a.copy_pitch = 0;
         }
