@@ -186,9 +186,9 @@ __global__ void __launch_bounds__(RNT) response_batch_kernel(const uint8_t *tabl
 }
 
 // ------------------------------------------------------------ select kernel
-constexpr int SNT = 512;
-constexpr int SCAP = 8192;   // keys sorted at once in shared memory
-constexpr int GCAP = 32768;  // cells of the accepted-point grid in shared memory
+constexpr int SNT = 256;
+constexpr int SCAP = 4096;   // keys sorted at once in shared memory
+constexpr int GCAP = 16384;  // cells of the accepted-point grid in shared memory
 
 struct SelectArgs {
     const uint32_t *rmap;

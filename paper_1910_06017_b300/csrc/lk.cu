@@ -75,8 +75,8 @@ struct Dims {
     static constexpr int RWJ = 4 * chunks((SP + 1) * ESZ);
     static constexpr int RWI = 4 * chunks(T * ESZ);
     static constexpr int RWG = 4 * chunks(T * GSZ);
-    static constexpr int TRAW = T * (RWI + RWG);              // raw template words
-    static constexpr int UNION = TRAW;                        // template area (16-byte multiple)
+    static constexpr int TRAW = T * (RWI + RWG);              // raw template words (16-byte multiple)
+    static constexpr int UNION = 2 * TRAW;                    // two template buffers
     static constexpr int WORDS = UNION + SH * RWJ;            // per warp, 16-byte multiple
 };
 
@@ -84,9 +84,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most N of this thread's most recent copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    cp_async_commit();
+    cp_async_wait<0>();
 }
 
 // Copy `rows` rows starting at level row y0 (each clamped), texel columns
@@ -134,6 +138,36 @@ struct LevelCopy {
     int sx0, sy0;        // search region origin (texels)
 };
 
+// The template window to prefetch after this level's template compute.
+struct NextTemplate {
+    bool has;
+    const LevelView *P;
+    bool u8;
+    int ipx, ipy;
+};
+
+// A template window copied (or being copied) ahead of its level.
+struct Prefetch {
+    bool valid;
+    int buf;             // template buffer 0 or 1
+    int tcol_i, tcol_g;  // as in LevelCopy
+};
+
+// Start copying the template window of the level at (ipx, ipy) into buffer
+// `buf`, as one copy group; returns its column origins.
+template <int ST, int WIN>
+__device__ __forceinline__ void issue_template(const LevelView &P, bool u8, int ipx, int ipy,
+                                               int buf, int lane, unsigned *W, int &tcol_i,
+                                               int &tcol_g) {
+    using D = Dims<ST, WIN>;
+    unsigned *T = W + buf * D::TRAW;
+    tcol_i = copy_rows(P.img, P.img_pitch, P.w, P.h, u8 ? 1 : D::ESZ, ipx - D::R, D::T,
+                       ipy - D::R, D::T, D::RWI, T, lane);
+    tcol_g = copy_rows(P.grad, P.grad_pitch, P.w, P.h, D::GSZ, ipx - D::R, D::T, ipy - D::R,
+                       D::T, D::RWG, T + D::T * D::RWI, lane);
+    cp_async_commit();
+}
+
 template <int ST, int WIN>
 __device__ __forceinline__ void copy_search(const LevelView &J, bool u8, int jx, int jy, int lane,
                                             unsigned *W, LevelCopy &lc) {
@@ -168,7 +202,7 @@ __device__ __forceinline__ void template_window(const LevelView &P, int tx0, flo
                                                 float (&Yw)[WIN], float &sxx, float &sxy,
                                                 float &syy, float &cx, float &cy) {
     using D = Dims<ST, WIN>;
-    const unsigned *rawI = W;
+    const unsigned *rawI = W;  // the level's template buffer
     const unsigned *rawG = W + D::T * D::RWI;
     const bool tapcol = lane < WIN;
     const int c = tapcol ? lane : 0;
@@ -253,7 +287,8 @@ template <int ST, int WIN>
 __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &J, float px,
                                            float py, float gx, float gy, int max_iter,
                                            float eps2, float tau_n, int lane, bool u8, unsigned *W,
-                                           float &nux, float &nuy, int &k, bool &conv) {
+                                           Prefetch &pf, const NextTemplate &nx, float &nux,
+                                           float &nuy, int &k, bool &conv) {
     using D = Dims<ST, WIN>;
     constexpr int R = D::R;
     const float fpx = floorf(px), fpy = floorf(py);
@@ -263,15 +298,22 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     k = 0;
     conv = false;
 
-    // One copy batch: the template window and the search region around the
-    // initial centre p + g (16-byte chunks, all in flight together).
+    // The template window was prefetched while the previous level (or the
+    // previous point) iterated, unless this is the warp's first level; the
+    // search region around the initial centre p + g is copied now, and only
+    // the template has to land before the template compute starts.
     LevelCopy lc;
-    const int esz = u8 ? 1 : D::ESZ;
-    __syncwarp();
-    lc.tcol_i = copy_rows(P.img, P.img_pitch, P.w, P.h, esz, ipx - R, D::T, ipy - R, D::T, D::RWI,
-                          W, lane);
-    lc.tcol_g = copy_rows(P.grad, P.grad_pitch, P.w, P.h, D::GSZ, ipx - R, D::T, ipy - R, D::T,
-                          D::RWG, W + D::T * D::RWI, lane);
+    int buf;
+    if (pf.valid) {
+        buf = pf.buf;
+        lc.tcol_i = pf.tcol_i;
+        lc.tcol_g = pf.tcol_g;
+    } else {
+        buf = 0;
+        __syncwarp();
+        issue_template<ST, WIN>(P, u8, ipx, ipy, buf, lane, W, lc.tcol_i, lc.tcol_g);
+    }
+    pf.valid = false;
     const float c0x = ax + gx, c0y = ay + gy;
     const bool c0_ok = fabsf(c0x) < 1.0e8f && fabsf(c0y) < 1.0e8f;
     int sjx = 0, sjy = 0;
@@ -279,13 +321,17 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         sjx = ipx + (int)floorf(c0x);
         sjy = ipy + (int)floorf(c0y);
         copy_search<ST, WIN>(J, u8, sjx, sjy, lane, W, lc);
+        cp_async_commit();
+        cp_async_wait<1>();   // the template group is done; the search may still run
+    } else {
+        cp_async_wait<0>();
     }
-    cp_async_wait_all();
     __syncwarp();
 
     float Xw[WIN], Yw[WIN];
     float sxx, sxy, syy, cx, cy;
-    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, u8, W, lc, Xw, Yw, sxx, sxy, syy, cx, cy);
+    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, u8, W + buf * D::TRAW, lc, Xw, Yw, sxx, sxy,
+                             syy, cx, cy);
     sxx = warp_sum(sxx);
     sxy = warp_sum(sxy);
     syy = warp_sum(syy);
@@ -295,6 +341,18 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
     const float lmin = det / lmax;
     if (!(lmin >= tau_n) || !(lmin > 0.f)) return OMT_PT_LOST_EIG;
+    // Prefetch the next template (next level, or the next point's top level)
+    // into the other buffer while this level iterates.
+    if (nx.has) {
+        __syncwarp();
+        issue_template<ST, WIN>(*nx.P, nx.u8, nx.ipx, nx.ipy, 1 - buf, lane, W, pf.tcol_i, pf.tcol_g);
+        pf.valid = true;
+        pf.buf = 1 - buf;
+        if (c0_ok) cp_async_wait<1>();  // the search group is done; the prefetch may still run
+    } else if (c0_ok) {
+        cp_async_wait<0>();
+    }
+    __syncwarp();
     bool staged = c0_ok;
     while (k < max_iter) {
         // Centre c = p + g + nu, held as (ipx, ipy) + (ccx, ccy).
@@ -309,7 +367,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
             __syncwarp();
             copy_search<ST, WIN>(J, u8, jx, jy, lane, W, lc);
-            cp_async_wait_all();
+            cp_async_wait_all();   // also lands a pending prefetch
             __syncwarp();
             sjx = jx;
             sjy = jy;
@@ -343,7 +401,8 @@ template <int ST, int WIN>
 __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
                                          int max_iter, float eps2, float tau_n, float2 u,
                                          int i, float2 *out, uint8_t *status, uint8_t *iters,
-                                         unsigned *W) {
+                                         unsigned *W, Prefetch &pf, bool has_next, float2 u_next,
+                                         const LevelView *P_next_point) {
     const int lane = threadIdx.x & 31;
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     int st = OMT_PT_OK;
@@ -352,11 +411,27 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
 
     for (int L = levels - 1; L >= 0; --L) {
         const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact
+        NextTemplate nx;
+        if (L > 0) {
+            const float s1 = __int_as_float((127 - (L - 1)) << 23);
+            nx.has = true;
+            nx.P = &P[L - 1];
+            nx.u8 = L - 1 == 0;
+            nx.ipx = (int)floorf(u.x * s1);
+            nx.ipy = (int)floorf(u.y * s1);
+        } else {
+            const float st0 = __int_as_float((127 - (levels - 1)) << 23);
+            nx.has = has_next;
+            nx.P = &P_next_point[levels - 1];
+            nx.u8 = levels - 1 == 0;
+            nx.ipx = (int)floorf(u_next.x * st0);
+            nx.ipy = (int)floorf(u_next.y * st0);
+        }
         float nux, nuy;
         int k;
         bool conv;
         st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
-                                  lane, L == 0, W, nux, nuy, k, conv);
+                                  lane, L == 0, W, pf, nx, nux, nuy, k, conv);
         itp |= (unsigned long long)k << (8 * L);
         if (st != OMT_PT_OK) break;
         if (!conv) nonconv = true;
@@ -367,6 +442,12 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
             dx = gx + nux;
             dy = gy + nuy;
         }
+    }
+    if (st != OMT_PT_OK) {
+        // a lost point leaves its prefetch (for a level it will not reach)
+        // unused: land it and forget it
+        cp_async_wait<0>();
+        pf.valid = false;
     }
 
     float2 v = u;
@@ -406,9 +487,16 @@ __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArg
         n = m < n ? m : n;
     }
     const int nwarps = gridDim.x * LK_WARPS;
-    for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps)
+    Prefetch pf;
+    pf.valid = false;
+    for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
+        const int nxt = i + nwarps;
+        const bool has_next = nxt < n;
+        const float2 un = has_next ? a.pts[nxt] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters, W);
+                          a.status, a.iters, W, pf, has_next, un, a.P);
+    }
+    cp_async_wait<0>();
 }
 
 // All points of all streams of a batch: the per-stream counts come from the
@@ -433,13 +521,25 @@ __global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
     __syncthreads();
     const int total = pre[ns];
     const int nwarps = gridDim.x * LK_WARPS;
-    for (int g = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); g < total; g += nwarps) {
-        const int s = find_segment(pre, ns, g);
+    Prefetch pf;
+    pf.valid = false;
+    int g = blockIdx.x * LK_WARPS + (threadIdx.x >> 5);
+    int s = g < total ? find_segment(pre, ns, g) : 0;
+    for (; g < total; g += nwarps) {
         const StreamEntry &e = t.stream(s);
         const int i = g - pre[s];
+        // the warp's next point, whose top-level template is prefetched
+        // while this point's finest level iterates
+        const int gn = g + nwarps;
+        const bool has_next = gn < total;
+        const int sn = has_next ? find_segment(pre, ns, gn) : s;
+        const StreamEntry &en = t.stream(sn);
+        const float2 un = has_next ? en.pts[gn - pre[sn]] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
-                          e.pts_out, e.status, e.iters, W);
+                          e.pts_out, e.status, e.iters, W, pf, has_next, un, en.P);
+        s = sn;
     }
+    cp_async_wait<0>();
 }
 
 template <int ST>
