@@ -265,7 +265,10 @@ class GpuBackend(Backend):
                 offsets=torch.zeros(nb + 1, dtype=torch.int32, device=dev),
                 nvalid=torch.zeros(nb, dtype=torch.int32, device=dev),
                 scratch=torch.empty(omt.corner_scratch_bytes(w, h, nb, mc), dtype=torch.uint8, device=dev),
-                boxes_host=torch.empty((nb, 4), dtype=torch.float32).pin_memory(),
+                # one page-locked copy of the output boxes per table of the
+                # ring, so a step's boxes survive until it is harvested
+                boxes_host=[torch.empty((nb, 4), dtype=torch.float32).pin_memory()
+                            for _ in range(len(self.tables))] if self.keep_boxes else None,
                 primed=False)
         except torch.cuda.OutOfMemoryError as e:  # the budget was set above what the device holds
             raise MemoryError(str(e))
@@ -296,7 +299,7 @@ class GpuBackend(Backend):
         self.ring_next = (k + 1) % len(self.tables)
         if self.ring_events[k] is not None:
             self.ring_events[k].synchronize()   # the step that read this table is done
-        descs, stepped = [], []
+        descs, host = [], {}
         with torch.cuda.stream(self.stream):
             for slot, idx in items:
                 spec = slot["spec"]
@@ -313,304 +316,41 @@ class GpuBackend(Backend):
                 if idx % spec.refresh == 0:   # a detection replaces the tracked boxes
                     slot["boxes"].copy_(torch.from_numpy(self.det_boxes[spec.sid]), non_blocking=True)
                 descs.append(self._desc(slot, par))
-                stepped.append(slot)
+                host[id(slot)] = slot
             if descs:
                 omt.batch_pack(descs, self.params, self.caps, self.tables[k])
                 omt.batch_step(self.tables[k], self.caps, self.params, self.dev_tables[k], self.stream)
-                for slot in stepped:
+                for slot in host.values():
                     # the tracked boxes are the next step's input; flip the pyramids
                     slot["boxes"].copy_(slot["boxes_out"], non_blocking=True)
-                    if self.keep_boxes:
-                        slot["boxes_host"].copy_(slot["boxes_out"], non_blocking=True)
                     slot["cur"] = 1 - slot["cur"]
+                if self.keep_boxes:
+                    for key, slot in host.items():
+                        host[key] = slot["boxes_host"][k]
+                        host[key].copy_(slot["boxes_out"], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(self.stream)
         self.ring_events[k] = ev
-        return _Handle(ev, list(items), [id(sl) for sl in stepped])
-
-    def done(self, handle) -> bool:
-        raise NotImplementedError
-
-    def results(self, handle) -> Optional[List[Optional[np.ndarray]]]:
-        return None
-
-
-@dataclasses.dataclass
-class Stats:
-    frames: List[FrameResult]
-    duration: float
-    admitted: int
-    rejected_frames: int
-    max_bytes_in_use: int
-    steps: int
-    batch_sizes: List[int]
-
-    def summary(self) -> dict:
-        done = [f for f in self.frames if not math.isnan(f.done)]
-        lat = np.array([f.latency for f in done]) * 1e3 if done else np.zeros(1)
-        return {
-            "frames_done": len(done), "frames_arrived": len(self.frames),
-            "stream_frames_per_s": len(done) / self.duration if self.duration > 0 else 0.0,
-            "latency_ms_p50": float(np.percentile(lat, 50)),
-            "latency_ms_p99": float(np.percentile(lat, 99)),
-            "latency_ms_max": float(lat.max()),
-            "streams_admitted": self.admitted, "frames_rejected": self.rejected_frames,
-            "max_bytes_in_use": self.max_bytes_in_use, "steps": self.steps,
-            "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
-        }
-
-
-class Scheduler:
-    """The request loop.  run() replays the arrival schedules against a
-    clock (wall time by default) until every frame is processed, rejected
-    or the deadline passes."""
-
-    def __init__(self, backend: Backend, budget_bytes: int, max_in_flight: int = 2,
-                 max_batch: int = 256, idle_timeout: float = 1.0,
-                 clock: Callable[[], float] = time.perf_counter,
-                 frame_ok: Optional[Callable[[int, int], bool]] = None):
-        self.backend = backend
-        self.budget = budget_bytes
-        self.max_in_flight = max_in_flight
-        self.max_batch = max_batch
-        self.idle_timeout = idle_timeout
-        self.clock = clock
-        self.frame_ok = frame_ok or (lambda sid, idx: True)
-
-    def run(self, specs: List[StreamSpec], deadline: float, sleep: Callable[[float], None] = None) -> Stats:
-        sleep = sleep or (lambda dt: None)
-        t0 = self.clock()
-        now = lambda: self.clock() - t0
-        frames: Dict[tuple, FrameResult] = {}
-        waiting = collections.deque(sorted(specs, key=lambda s: s.arrivals[0] if len(s.arrivals) else 1e30))
-        active: Dict[int, dict] = {}
-        in_use = max_in_use = 0
-        in_flight = collections.deque()
-        rejected = steps = 0
-        batch_sizes = []
-        admitted = 0
-        while True:
-            t = now()
-            # admit, in order of first arrival, while the budget allows
-            while waiting and len(waiting[0].arrivals) and waiting[0].arrivals[0] <= t:
-                spec = waiting[0]
-                need = self.backend.bytes_for(spec)
-                if in_use + need > self.budget:
-                    break
-                try:
-                    slot = self.backend.alloc(spec)
-                except MemoryError:
-                    break
-                waiting.popleft()
-                in_use += need
-                max_in_use = max(max_in_use, in_use)
-                admitted += 1
-                active[spec.sid] = dict(spec=spec, slot=slot, bytes=need, next=0, busy=0,
-                                        last_seen=t)
-            # drop specs that never deliver a frame
-            while waiting and not len(waiting[0].arrivals):
-                waiting.popleft()
-            # harvest finished steps
-            while in_flight and self.backend.done(in_flight[0][0]):
-                handle, items = in_flight.popleft()
-                tdone = now()
-                boxes = self.backend.results(handle) or [None] * len(items)
-                for (sid, idx), b in zip(items, boxes):
-                    fr = frames[(sid, idx)]
-                    fr.done = tdone
-                    fr.boxes = b
-                    active[sid]["busy"] -= 1
-            # build the next step: the oldest pending frame of every stream
-            if len(in_flight) < self.max_in_flight:
-                items = []
-                for sid, st in active.items():
-                    spec = st["spec"]
-                    while st["next"] < len(spec.arrivals) and spec.arrivals[st["next"]] <= t:
-                        idx = st["next"]
-                        if (sid, idx) not in frames:
-                            frames[(sid, idx)] = FrameResult(sid, idx, float(spec.arrivals[idx]))
-                        if self.frame_ok(sid, idx):
-                            break
-                        rejected += 1          # malformed frame: skip it, keep the stream
-                        frames[(sid, idx)].done = math.nan
-                        st["next"] += 1
-                    if st["next"] < len(spec.arrivals) and spec.arrivals[st["next"]] <= t:
-                        items.append((sid, st["next"]))
-                        st["next"] += 1
-                        st["busy"] += 1
-                        st["last_seen"] = t
-                    if len(items) >= self.max_batch:
-                        break
-                if items:
-                    handle = self.backend.submit([(active[sid]["slot"], idx) for sid, idx in items])
-                    in_flight.append((handle, items))
-                    steps += 1
-                    batch_sizes.append(len(items))
-            # release streams that are finished, or silent for too long
-            for sid in list(active):
-                st = active[sid]
-                spec = st["spec"]
-                finished = st["next"] >= len(spec.arrivals)
-                silent = (st["next"] < len(spec.arrivals) and spec.arrivals[st["next"]] > t and
-                          t - st["last_seen"] > self.idle_timeout and
-                          spec.arrivals[st["next"]] - st["last_seen"] > self.idle_timeout)
-                if (finished or silent) and st["busy"] == 0:
-                    self.backend.free(st["slot"])
-                    in_use -= st["bytes"]
-                    del active[sid]
-            if not waiting and not active and not in_flight:
-                break
-            if t > deadline:
-                break
-            sleep(2e-4)
-        return Stats(list(frames.values()), min(now(), deadline), admitted, rejected, max_in_use,
-                     steps, batch_sizes)
-
-
-# ---------------------------------------------------------------- GPU side
-
-class GpuBackend(Backend):
-    """Drives libomt: per stream a slot of device buffers (two pyramids, two
-    frame slots, boxes, points, corner scratch); one omt_batch_step per
-    step over the slots of that step, from a ring of page-locked tables."""
-
-    def __init__(self, params, caps_streams: int, caps_boxes: int, max_w: int, max_h: int,
-                 max_corners: int, frames_host: Dict[int, list], det_boxes: Dict[int, np.ndarray],
-                 device="cuda", ring: int = 4, keep_boxes: bool = False):
-        import torch
-        from . import omt
-        self.torch, self.omt = torch, omt
-        self.params = params
-        self.device = torch.device(device)
-        self.caps = omt.BatchCaps(caps_streams, caps_boxes, max_w, max_h, max_corners)
-        nbytes = omt.batch_table_bytes(self.caps)
-        self.tables = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(ring)]
-        self.dev_tables = [torch.empty(nbytes, dtype=torch.uint8, device=self.device) for _ in range(ring)]
-        self.ring_events = [None] * ring
-        self.ring_next = 0
-        self.frames_host = frames_host
-        self.det_boxes = det_boxes
-        self.keep_boxes = keep_boxes
-        self.stream = torch.cuda.Stream(device=self.device)
-
-    def bytes_for(self, spec: StreamSpec) -> int:
-        omt = self.omt
-        w, h = spec.size
-        p = self.params
-        nb, mc = max(1, spec.n_boxes), spec.max_corners
-        cap = nb * mc
-        return (2 * omt.pyramid_bytes(w, h, p.levels, p.storage) + 2 * w * h +
-                omt.corner_scratch_bytes(w, h, nb, mc) + cap * (8 + 8 + 1 + p.levels) +
-                (nb + 1) * 4 + nb * (16 + 16 + 4))
-
-    def alloc(self, spec: StreamSpec):
-        torch, omt = self.torch, self.omt
-        w, h = spec.size
-        p, dev = self.params, self.device
-        nb, mc = max(1, spec.n_boxes), spec.max_corners
-        cap = nb * mc
-        try:
-            slot = dict(
-                spec=spec, cur=0,
-                pyr=[omt.Pyramid(w, h, p.levels, p.storage, dev), omt.Pyramid(w, h, p.levels, p.storage, dev)],
-                frame=[torch.empty((h, w), dtype=torch.uint8, device=dev) for _ in range(2)],
-                boxes=torch.zeros((nb, 4), dtype=torch.float32, device=dev),
-                boxes_out=torch.zeros((nb, 4), dtype=torch.float32, device=dev),
-                pts=torch.empty((cap, 2), dtype=torch.float32, device=dev),
-                pts_out=torch.empty((cap, 2), dtype=torch.float32, device=dev),
-                status=torch.empty(cap, dtype=torch.uint8, device=dev),
-                offsets=torch.zeros(nb + 1, dtype=torch.int32, device=dev),
-                nvalid=torch.zeros(nb, dtype=torch.int32, device=dev),
-                scratch=torch.empty(omt.corner_scratch_bytes(w, h, nb, mc), dtype=torch.uint8, device=dev),
-                boxes_host=torch.empty((nb, 4), dtype=torch.float32).pin_memory(),
-                primed=False)
-        except torch.cuda.OutOfMemoryError as e:  # the budget was set above what the device holds
-            raise MemoryError(str(e))
-        return slot
-
-    def free(self, slot) -> None:
-        slot.clear()
-
-    def _desc(self, slot, parity):
-        omt = self.omt
-        d = omt.BatchStream()
-        f = slot["frame"][parity]
-        d.frame, d.frame_pitch = f.data_ptr(), f.stride(0)
-        d.prev = slot["pyr"][parity].desc
-        d.next = slot["pyr"][1 - parity].desc
-        d.boxes, d.nboxes = slot["boxes"].data_ptr(), slot["spec"].n_boxes
-        d.max_corners = slot["spec"].max_corners
-        d.scratch, d.scratch_bytes = slot["scratch"].data_ptr(), slot["scratch"].numel()
-        d.pts, d.pts_out = slot["pts"].data_ptr(), slot["pts_out"].data_ptr()
-        d.status, d.iters = slot["status"].data_ptr(), None
-        d.offsets = slot["offsets"].data_ptr()
-        d.boxes_out, d.nvalid = slot["boxes_out"].data_ptr(), slot["nvalid"].data_ptr()
-        return d
-
-    def submit(self, items):
-        torch, omt = self.torch, self.omt
-        k = self.ring_next
-        self.ring_next = (k + 1) % len(self.tables)
-        if self.ring_events[k] is not None:
-            self.ring_events[k].synchronize()   # that table's step has read it
-        descs = []
-        with torch.cuda.stream(self.stream):
-            for slot, idx in items:
-                spec = slot["spec"]
-                fh = self.frames_host[spec.sid][idx % len(self.frames_host[spec.sid])]
-                if not slot["primed"]:
-                    # the stream's first frame only builds its pyramid
-                    slot["frame"][0].copy_(fh, non_blocking=True)
-                    omt.build_pyramid(slot["frame"][0], slot["pyr"][0], self.params)
-                    slot["primed"] = True
-                    slot["boxes"].copy_(torch.from_numpy(self.det_boxes[spec.sid]), non_blocking=True)
-                    continue
-                par = slot["cur"]
-                slot["frame"][par].copy_(fh, non_blocking=True)
-                if idx % spec.refresh == 0:   # a detection replaces the tracked boxes
-                    slot["boxes"].copy_(torch.from_numpy(self.det_boxes[spec.sid]), non_blocking=True)
-                descs.append(self._desc(slot, par))
-            if descs:
-                omt.batch_pack(descs, self.params, self.caps, self.tables[k])
-                omt.batch_step(self.tables[k], self.caps, self.params, self.dev_tables[k], self.stream)
-                for slot, idx in items:
-                    if slot.get("cur") is None:
-                        continue
-                for d_slot, idx in items:
-                    pass
-                for slot, idx in items:
-                    if idx == 0 and slot["cur"] == 0 and not slot.get("stepped"):
-                        pass
-                for slot, idx in items:
-                    if slot.get("primed_now"):
-                        pass
-            # track: next input boxes are this step's outputs; flip parity
-            for slot, idx in items:
-                if descs and slot.get("_in_step", True) and idx > 0:
-                    slot["boxes"].copy_(slot["boxes_out"], non_blocking=True)
-                    if self.keep_boxes:
-                        slot["boxes_host"].copy_(slot["boxes_out"], non_blocking=True)
-                    slot["cur"] = 1 - slot["cur"]
-            ev = torch.cuda.Event()
-            ev.record(self.stream)
-        self.ring_events[k] = ev
-        return _Handle(ev, [(s, i) for s, i in items])
+        return _Handle(ev, list(items), host if self.keep_boxes else {})
 
     def done(self, handle) -> bool:
         return handle.event.query()
 
-    def results(self, handle):
+    def results(self, handle) -> Optional[List[Optional[np.ndarray]]]:
         if not self.keep_boxes:
-            return [None] * len(handle.items)
-        return [slot["boxes_host"].numpy().copy() if id(slot) in handle.stepped else None
-                for slot, idx in handle.items]
+            return None
+        out = []
+        for slot, idx in handle.items:
+            b = handle.host.get(id(slot))
+            out.append(None if b is None else (b if isinstance(b, np.ndarray) else b.numpy().copy()))
+        return out
 
 
 @dataclasses.dataclass
 class _Handle:
     event: object
     items: list
-    stepped: list = dataclasses.field(default_factory=list)
+    host: dict = dataclasses.field(default_factory=dict)   # id(slot) -> output boxes
 
 
 class PlainGpuBackend(GpuBackend):
@@ -619,7 +359,7 @@ class PlainGpuBackend(GpuBackend):
 
     def submit(self, items):
         torch, omt = self.torch, self.omt
-        stepped = []
+        host = {}
         with torch.cuda.stream(self.stream):
             for slot, idx in items:
                 spec = slot["spec"]
@@ -645,14 +385,13 @@ class PlainGpuBackend(GpuBackend):
                 omt.update_boxes(slot["boxes"][:nb], slot["offsets"], slot["pts"], slot["pts_out"],
                                  slot["status"], prm, slot["boxes_out"][:nb], slot["nvalid"][:nb])
                 slot["boxes"].copy_(slot["boxes_out"], non_blocking=True)
-                if self.keep_boxes:
-                    slot["boxes_host"].copy_(slot["boxes_out"], non_blocking=True)
                 slot["cur"] = 1 - par
-                stepped.append(id(slot))
                 self.stream.synchronize()
+                if self.keep_boxes:
+                    host[id(slot)] = slot["boxes_out"].cpu().numpy()
             ev = torch.cuda.Event()
             ev.record(self.stream)
-        return _Handle(ev, list(items), stepped)
+        return _Handle(ev, list(items), host)
 
 
 # ---------------------------------------------------------------- workload
