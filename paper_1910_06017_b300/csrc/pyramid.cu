@@ -1,32 +1,51 @@
 // pyramid.cu -- K1: Gaussian pyramid and Scharr gradients (Section V-A,
 // preprocessing).
 //
-// One launch per level L.  A 256-thread CTA owns a 128x32 tile of level L:
-// it stages the tile plus a 2-pixel reflect-101 halo in shared memory
-// (interior tiles with aligned 4-byte or 16-byte row loads, border tiles
-// element by element through the reflect-101 map), writes the tile's
-// gradients (Ix, Iy) with conflict-free shared reads and coalesced stores,
-// and writes the 64x16 tile of level L+1 that decimates it.  Level 0 also copies the u8
-// frame into the pyramid buffer.  Sums use the integer binomial weights and
-// scale by a power of two at the end, so every value that is dyadic-exact in
-// FP32 (levels 0-2) comes out bit-identical to the definition.
+// One launch per level L; CTAs stride over 128x32 tiles of level L (of every
+// stream, in the batched form), two tiles in flight per CTA.  A tile is staged in shared memory with
+// 16-byte cp.async copies of its rows plus a 2-texel reflect-101 halo
+// (rounded out to 16-byte chunks; chunks that cross the frame edge are
+// filled texel by texel through the reflect-101 map) in its stored format:
+// u8, half or float.  Each thread then owns 4 adjacent columns and 4
+// consecutive rows of the tile: it reads the 7 staged rows it needs (3-4
+// 32-bit, 64-bit or 128-bit shared loads per row, conflict-free), forms the
+// horizontal Scharr difference and smoothing and the horizontal binomial sums
+// in registers, combines them vertically, and stores 4 gradient pairs per
+// row with one 16-byte (F16) or two (F32) stores, 2 texels of level L+1 at
+// each of its two even rows, and at level 0 the u8 copy of its 4x4 texels.
+//
+// Exactness: the Scharr weights 3/32 and 10/32 and the integer binomial
+// weights with a final 1/256 keep every value that is dyadic-exact in FP32
+// (pyramid levels 0-2, gradients of levels 0-1) bit-identical to the
+// definition.
 #include "omt_internal.cuh"
 
 namespace omt {
 namespace {
 
-constexpr int TX = 128;  // level-L tile width
-constexpr int TY = 32;   // level-L tile height
-constexpr int NT = 256;  // threads per CTA
-constexpr int SX = TX + 4, SY = TY + 4;
-constexpr int HX = TX / 2;  // level L+1 tile width
+constexpr int TX = 128;        // tile width
+constexpr int TY = 32;         // tile height (even: level L+1 rows align)
+constexpr int RPT = 4;         // rows per thread
+constexpr int SROWS = TY + 4;  // staged rows: the tile and 2 halo rows each side
+constexpr int NT = 256;        // threads per CTA: 32 column groups x 8 row groups
+static_assert(TY == RPT * (NT / 32), "tile rows");
+
+enum Fmt { FMT_U8 = 0, FMT_H16 = 1, FMT_F32 = 2 };  // storage of level L's texels
+
+template <int FMT>
+struct Stage {
+    static constexpr int ESZ = FMT == FMT_U8 ? 1 : (FMT == FMT_H16 ? 2 : 4);
+    // staged columns start at the 16-byte boundary at or below column ox-4
+    static constexpr int LEAD = FMT == FMT_U8 ? 16 : (FMT == FMT_H16 ? 8 : 4);  // texels before ox
+    static constexpr int RB = ((LEAD + TX + 4) * ESZ + 15) / 16 * 16;            // bytes per staged row
+    static constexpr int BYTES = SROWS * RB;
+};
 
 struct LevelArgs {
     const uint8_t *src;   // level L: u8 frame (L = 0) or the pyramid's level plane
     int64_t src_pitch;
     int w, h;             // level L size
-    int level;
-    bool vec_ok;          // src rows are 4-byte aligned (pointer and pitch)
+    bool vec_ok;          // src base and pitch are 16-byte aligned
     uint8_t *copy;        // level-0 u8 copy (L = 0 only)
     int64_t copy_pitch;
     uint8_t *grad;        // level-L gradient plane
@@ -36,74 +55,248 @@ struct LevelArgs {
     int nw, nh;           // level L+1 size
 };
 
-template <int ST>
-__device__ __forceinline__ float load_src(const LevelArgs &a, int x, int y) {
-    const uint8_t *row = a.src + (int64_t)y * a.src_pitch;
-    if (a.level == 0) return (float)row[x];
-    if (ST == OMT_F32) return ((const float *)row)[x];
-    return __half2float(((const __half *)row)[x]) + 128.0f;
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// Stage level L over [ox-2, ox+TX+2) x [oy-2, oy+TY+2) into s.
-template <int ST>
-__device__ __forceinline__ void stage_tile(const LevelArgs &a, int ox, int oy, float (*s)[SX]) {
-    const int tid = threadIdx.x;
-    const bool interior = ox - 4 >= 0 && oy - 2 >= 0 && ox + TX + 4 <= a.w && oy + TY + 2 <= a.h;
-    if (interior && a.vec_ok) {
-        if (a.level == 0 || ST == OMT_F16) {
-            // 4-byte words from column ox-4 (4-aligned): 4 u8 or 2 half texels each
-            const int per = a.level == 0 ? 4 : 2;
-            const int nwords = (TX + 8) / per;
-            for (int i = tid; i < SY * nwords; i += NT) {
-                const int r = i / nwords, k = i - r * nwords;
-                const uint8_t *row = a.src + (int64_t)(oy - 2 + r) * a.src_pitch;
-                const int x = ox - 4 + k * per;  // first texel of the word
-                const unsigned wv = __ldg((const unsigned *)(row + (int64_t)x * (per == 4 ? 1 : 2)));
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (q >= per) break;
-                    const int c = x + q - (ox - 2);
-                    if (c < 0 || c >= SX) continue;
-                    float v;
-                    if (per == 4) v = (float)((wv >> (8 * q)) & 0xFFu);
-                    else v = __half2float(__ushort_as_half((unsigned short)(wv >> (16 * q)))) + 128.0f;
-                    s[r][c] = v;
-                }
-            }
+template <int FMT>
+__device__ __forceinline__ float texel_value(unsigned bits) {
+    if (FMT == FMT_U8) return (float)bits;
+    if (FMT == FMT_H16) return __half2float(__ushort_as_half((unsigned short)bits)) + 128.0f;
+    return __uint_as_float(bits);
+}
+
+// Start staging level rows oy-2 .. oy+TY+1, columns from ox-LEAD, into st
+// (one cp.async group per thread; chunks crossing the frame edge are
+// written directly).
+template <int FMT>
+__device__ __forceinline__ void stage_tile(const LevelArgs &a, int ox, int oy, uint8_t *st) {
+    using S = Stage<FMT>;
+    constexpr int NCH = S::RB / 16, PER = 16 / S::ESZ;  // chunks per row, texels per chunk
+    const int c_first = ox - S::LEAD;
+    for (int k = threadIdx.x; k < SROWS * NCH; k += NT) {
+        const int r = k / NCH, c = k - r * NCH;
+        const uint8_t *row = a.src + (int64_t)reflect101(oy - 2 + r, a.h) * a.src_pitch;
+        const int col0 = c_first + c * PER;
+        uint8_t *dst = st + r * S::RB + 16 * c;
+        if (a.vec_ok && col0 >= 0 && col0 + PER <= a.w) {
+            cp_async16(dst, row + (int64_t)col0 * S::ESZ);
         } else {
-            // float4 from column ox-4 (16-byte aligned)
-            const int nq = (TX + 8) / 4;
-            for (int i = tid; i < SY * nq; i += NT) {
-                const int r = i / nq, k = i - r * nq;
-                const float4 v = __ldg((const float4 *)(a.src + (int64_t)(oy - 2 + r) * a.src_pitch) +
-                                       (ox - 4) / 4 + k);
-                const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int c = 4 * k + q - 2;
-                    if (c >= 0 && c < SX) s[r][c] = e[q];
-                }
+            for (int e = 0; e < PER; ++e) {
+                const int col = reflect101(col0 + e, a.w);
+                if (FMT == FMT_U8) dst[e] = row[col];
+                else if (FMT == FMT_H16) ((unsigned short *)dst)[e] = ((const unsigned short *)row)[col];
+                else ((unsigned *)dst)[e] = ((const unsigned *)row)[col];
             }
-        }
-    } else {
-        for (int i = tid; i < SX * SY; i += NT) {
-            const int r = i / SX, c = i - r * SX;
-            s[r][c] = load_src<ST>(a, reflect101(ox - 2 + c, a.w), reflect101(oy - 2 + r, a.h));
         }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Values of tile columns 4g-2 .. 4g+5 of staged row r.
+template <int FMT>
+__device__ __forceinline__ void staged_row(const uint8_t *st, int r, int g, float m[8]) {
+    using S = Stage<FMT>;
+    const uint8_t *row = st + r * S::RB;
+    if (FMT == FMT_U8) {
+        // texels 4g+14 .. 4g+21 of the staged row: words g+3 .. g+5
+        const unsigned *w = (const unsigned *)row + g + 3;
+        const unsigned w0 = w[0], w1 = w[1], w2 = w[2];
+        m[0] = (float)((w0 >> 16) & 0xFFu);
+        m[1] = (float)(w0 >> 24);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) m[2 + c] = (float)((w1 >> (8 * c)) & 0xFFu);
+        m[6] = (float)(w2 & 0xFFu);
+        m[7] = (float)((w2 >> 8) & 0xFFu);
+    } else if (FMT == FMT_H16) {
+        // halves 4g+6 .. 4g+13: words 2g+3 .. 2g+6
+        const unsigned *w = (const unsigned *)row + 2 * g + 3;
+        const unsigned w0 = w[0];
+        const uint2 w12 = *(const uint2 *)(w + 1);
+        const unsigned w3 = w[3];
+        const unsigned u[4] = {w0, w12.x, w12.y, w3};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) m[c] = texel_value<FMT>((u[c >> 1] >> (16 * (c & 1))) & 0xFFFFu);
+    } else {
+        // floats 4g+2 .. 4g+9
+        const float *f = (const float *)row + 4 * g + 2;
+        const float2 p0 = *(const float2 *)f;
+        const float4 p1 = *(const float4 *)(f + 2);
+        const float2 p2 = *(const float2 *)(f + 6);
+        m[0] = p0.x;
+        m[1] = p0.y;
+        m[2] = p1.x;
+        m[3] = p1.y;
+        m[4] = p1.z;
+        m[5] = p1.w;
+        m[6] = p2.x;
+        m[7] = p2.y;
+    }
+}
+
+template <int ST>
+__device__ __forceinline__ void store_grads(const LevelArgs &a, int y, int x, const float gx[4],
+                                            const float gy[4]) {
+    uint8_t *row = a.grad + (int64_t)y * a.grad_pitch;
+    const bool full = x + 3 < a.w;
+    if (ST == OMT_F32) {
+        if (full) {
+            float4 *p = (float4 *)(row + 8 * (int64_t)x);
+            p[0] = make_float4(gx[0], gy[0], gx[1], gy[1]);
+            p[1] = make_float4(gx[2], gy[2], gx[3], gy[3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (x + c < a.w) ((float2 *)row)[x + c] = make_float2(gx[c], gy[c]);
+        }
+    } else {
+        unsigned g[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const __half2 t = __floats2half2_rn(gx[c], gy[c]);
+            g[c] = *(const unsigned *)&t;
+        }
+        if (full) {
+            *(uint4 *)(row + 4 * (int64_t)x) = make_uint4(g[0], g[1], g[2], g[3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (x + c < a.w) ((unsigned *)row)[x + c] = g[c];
+        }
+    }
+}
+
+template <int ST>
+__device__ __forceinline__ void store_next(const LevelArgs &a, int Y, int X0, float v0, float v1) {
+    if (Y >= a.nh || X0 >= a.nw) return;
+    uint8_t *row = a.next + (int64_t)Y * a.next_pitch;
+    if (ST == OMT_F32) {
+        if (X0 + 1 < a.nw) ((float2 *)row)[X0 >> 1] = make_float2(v0, v1);
+        else ((float *)row)[X0] = v0;
+    } else {
+        if (X0 + 1 < a.nw) ((__half2 *)row)[X0 >> 1] = __floats2half2_rn(v0 - 128.0f, v1 - 128.0f);
+        else ((__half *)row)[X0] = __float2half_rn(v0 - 128.0f);
+    }
+}
+
+// This thread's share of the staged 128x32 tile of level L at (ox, oy).
+template <int ST, int FMT>
+__device__ __forceinline__ void compute_tile(const LevelArgs &a, int ox, int oy, const uint8_t *st) {
+    const int g = threadIdx.x & 31;   // columns 4g .. 4g+3 of the tile
+    const int q = threadIdx.x >> 5;   // rows RPT q .. RPT q + RPT-1 of the tile
+    const int x = ox + 4 * g;
+    if (x >= a.w) return;
+    const int y0 = oy + RPT * q;
+    // tile row t is staged row t + 2; this thread reads tile rows y0-oy-2 ..
+    // y0-oy+RPT (k = 0 .. RPT+2) and emits each output once its rows are in
+    float d[RPT + 3][4], hh[RPT + 3][4], hs[RPT + 3][2];
+#pragma unroll
+    for (int k = 0; k < RPT + 3; ++k) {
+        float m[8];
+        staged_row<FMT>(st, RPT * q + k, g, m);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            d[k][c] = m[c + 3] - m[c + 1];
+            hh[k][c] = fmaf(10.0f / 32.0f, m[c + 2], (3.0f / 32.0f) * (m[c + 1] + m[c + 3]));
+        }
+        hs[k][0] = (m[0] + m[4]) + 4.0f * (m[1] + m[3]) + 6.0f * m[2];
+        hs[k][1] = (m[2] + m[6]) + 4.0f * (m[3] + m[5]) + 6.0f * m[4];
+        if (FMT == FMT_U8 && a.copy && k >= 2 && k < RPT + 2 && y0 + k - 2 < a.h) {
+            uint8_t *dst = a.copy + (int64_t)(y0 + k - 2) * a.copy_pitch + x;
+            const uint8_t *srow = st + (RPT * q + k) * Stage<FMT>::RB;
+            if (x + 3 < a.w) {
+                *(unsigned *)dst = ((const unsigned *)srow)[g + 4];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (x + c < a.w) dst[c] = srow[16 + 4 * g + c];
+            }
+        }
+        // gradients of row y0 + k - 3 (rows k-2 .. k are in)
+        if (k >= 3 && k < RPT + 3 && y0 + k - 3 < a.h) {
+            float gx[4], gy[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                gx[c] = fmaf(10.0f / 32.0f, d[k - 1][c], (3.0f / 32.0f) * (d[k - 2][c] + d[k][c]));
+                gy[c] = hh[k][c] - hh[k - 2][c];
+            }
+            store_grads<ST>(a, y0 + k - 3, x, gx, gy);
+        }
+        // level L+1 row (y0 + k - 4) / 2 at even rows (rows k-4 .. k are in)
+        if (a.next && k >= 4 && ((k & 1) == 0)) {
+            float o[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                o[c] = ((hs[k - 4][c] + hs[k][c]) + 4.0f * (hs[k - 3][c] + hs[k - 1][c]) +
+                        6.0f * hs[k - 2][c]) * (1.0f / 256.0f);
+            store_next<ST>(a, (y0 >> 1) + (k - 4) / 2, x >> 1, o[0], o[1]);
+        }
+    }
+}
+
+// A tile to process: its level arguments and origin.
+struct Tile {
+    LevelArgs a;
+    int ox, oy;
+};
+
+// The CTA's tiles g = blockIdx.x, += gridDim.x, < total, two at a time in
+// flight: while the CTA computes tile g from one shared buffer, the copies
+// of the next tile land in the other.  resolve(g, Tile&) names a tile
+// (thread 0 only; the result is shared through a ring of three slots, so
+// the slot being written is never one that a thread may still read: slot
+// i % 3 serves the CTA's i-th tile, written at the top of trip i - 1 and
+// read until the end of trip i, and trip i + 1 writes slot (i + 2) % 3).
+template <int ST, int FMT, typename Resolve>
+__device__ __forceinline__ void tile_pipeline(int total, Resolve resolve) {
+    extern __shared__ __align__(16) uint8_t pyr_smem[];
+    uint8_t *st[2] = {pyr_smem, pyr_smem + Stage<FMT>::BYTES};
+    __shared__ Tile tl[3];
+    int g = blockIdx.x;
+    if (g >= total) return;
+    if (threadIdx.x == 0) resolve(g, tl[0]);
+    __syncthreads();
+    stage_tile<FMT>(tl[0].a, tl[0].ox, tl[0].oy, st[0]);
+    int i = 0;  // this CTA's tile count
+    for (; g < total; g += gridDim.x, ++i) {
+        const int gn = g + gridDim.x;
+        const int cur = i % 3, nxt = (i + 1) % 3, b = i & 1;
+        if (threadIdx.x == 0 && gn < total) resolve(gn, tl[nxt]);
+        __syncthreads();  // tl[nxt] is set; every thread is done with st[b ^ 1]
+        if (gn < total) {
+            stage_tile<FMT>(tl[nxt].a, tl[nxt].ox, tl[nxt].oy, st[b ^ 1]);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();  // tile g is staged by every thread
+        compute_tile<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
+    }
+}
+
+template <int ST, int FMT>
+__global__ void __launch_bounds__(NT) pyramid_level_kernel(const LevelArgs a, int tiles_x,
+                                                           int total) {
+    tile_pipeline<ST, FMT>(total, [&](int g, Tile &t) {
+        const int ty = g / tiles_x, tx = g - ty * tiles_x;
+        t.a = a;
+        t.ox = tx * TX;
+        t.oy = ty * TY;
+    });
 }
 
 // Arguments of level L of the pyramid a batch entry builds (frame t+1).
 __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int L, int levels,
                                                       LevelArgs &a) {
     const LevelView &v = e.P_next[L];
-    a.level = L;
     a.w = v.w;
     a.h = v.h;
     if (L == 0) {
         a.src = e.frame;
         a.src_pitch = e.frame_pitch;
-        a.vec_ok = (((uintptr_t)e.frame | (uintptr_t)e.frame_pitch) & 3) == 0;
+        a.vec_ok = (((uintptr_t)e.frame | (uintptr_t)e.frame_pitch) & 15) == 0;
         a.copy = const_cast<uint8_t *>(v.img);
         a.copy_pitch = v.img_pitch;
     } else {
@@ -128,115 +321,69 @@ __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int 
     }
 }
 
-// One 128x32 tile of level L at (ox, oy): gradients of the tile and the
-// 64x16 tile of level L+1 that decimates it.  Callers loop over tiles with
-// the whole CTA; the leading barrier keeps tiles from overlapping in the
-// shared arrays.
-template <int ST>
-__device__ __forceinline__ void pyramid_tile(const LevelArgs &a, int ox, int oy) {
-    __shared__ float s[SY][SX];
-    __shared__ float hs[SY][HX];
-    const int tid = threadIdx.x;
-    __syncthreads();
-    stage_tile<ST>(a, ox, oy, s);
-    if (a.copy) {
-        // u8 copy of the tile, 4 bytes per thread where the row allows
-        for (int i = tid; i < TY * (TX / 4); i += NT) {
-            const int r = i / (TX / 4), k = i - r * (TX / 4);
-            const int x = ox + 4 * k, y = oy + r;
-            if (y >= a.h || x >= a.w) continue;
-            uint8_t *dst = a.copy + (int64_t)y * a.copy_pitch + x;
-            const uint8_t *src = a.src + (int64_t)y * a.src_pitch + x;
-            if (x + 3 < a.w && a.vec_ok) {
-                *(unsigned *)dst = __ldg((const unsigned *)src);
-            } else {
-                for (int q = 0; q < 4 && x + q < a.w; ++q) dst[q] = src[q];
-            }
-        }
-    }
-    __syncthreads();
-
-    // Scharr gradients, intensity per level pixel.  Thread (tx, ty) takes
-    // columns tx + 32 q and rows 4 ty + rr: conflict-free shared reads, and a
-    // warp stores 32 consecutive pixels of a row.
-    {
-        const int tx = tid & 31, ty = tid >> 5;
-#pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-            const int r = 4 * ty + rr;
-            const int y = oy + r;
-            if (y >= a.h) break;
-            const int R = r + 2;
-            uint8_t *row = a.grad + (int64_t)y * a.grad_pitch;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int c = tx + 32 * q, x = ox + c;
-                if (x >= a.w) break;
-                const int C = c + 2;
-                float gx = 3.0f * (s[R - 1][C + 1] - s[R - 1][C - 1]);
-                gx += 10.0f * (s[R][C + 1] - s[R][C - 1]);
-                gx += 3.0f * (s[R + 1][C + 1] - s[R + 1][C - 1]);
-                float gy = 3.0f * (s[R + 1][C - 1] - s[R - 1][C - 1]);
-                gy += 10.0f * (s[R + 1][C] - s[R - 1][C]);
-                gy += 3.0f * (s[R + 1][C + 1] - s[R - 1][C + 1]);
-                gx *= (1.0f / 32.0f);
-                gy *= (1.0f / 32.0f);
-                if (ST == OMT_F32) ((float2 *)row)[x] = make_float2(gx, gy);
-                else ((__half2 *)row)[x] = __floats2half2_rn(gx, gy);
-            }
-        }
-    }
-    if (a.next) {
-        // Binomial reduce to level L+1: horizontal pass at the even columns...
-        for (int i = tid; i < SY * HX; i += NT) {
-            const int r = i / HX, X = i - r * HX;
-            const int c = 2 * X + 2;
-            hs[r][X] = (s[r][c - 2] + s[r][c + 2]) + 4.0f * (s[r][c - 1] + s[r][c + 1]) + 6.0f * s[r][c];
-        }
-        __syncthreads();
-        // ...then vertical at the even rows, scaled by 1/256: thread (X, Y0)
-        // takes rows Y0 + 4 q of column X.
-        const int X = tid & (HX - 1), Y0 = tid / HX;
-        const int gX = ox / 2 + X;
-        if (gX < a.nw) {
-#pragma unroll
-            for (int q = 0; q < (TY / 2) / (NT / HX); ++q) {
-                const int Y = Y0 + (NT / HX) * q;
-                const int gY = oy / 2 + Y;
-                if (gY >= a.nh) break;
-                const int r = 2 * Y + 2;
-                const float v = ((hs[r - 2][X] + hs[r + 2][X]) + 4.0f * (hs[r - 1][X] + hs[r + 1][X]) +
-                                 6.0f * hs[r][X]) * (1.0f / 256.0f);
-                uint8_t *row = a.next + (int64_t)gY * a.next_pitch;
-                if (ST == OMT_F32) ((float *)row)[gX] = v;
-                else ((__half *)row)[gX] = __float2half_rn(v - 128.0f);
-            }
-        }
-    }
-}
-
-template <int ST>
-__global__ void __launch_bounds__(NT) pyramid_level_kernel(LevelArgs a) {
-    pyramid_tile<ST>(a, blockIdx.x * TX, blockIdx.y * TY);
-}
-
-// Level L of every stream of a batch: a grid-stride loop over the batch's
+// Level L of every stream of a batch: the CTAs stride over the batch's
 // tiles (tile prefix per stream in the table).
-template <int ST>
+template <int ST, int FMT>
 __global__ void __launch_bounds__(NT) pyramid_batch_kernel(const uint8_t *table, int L) {
     const BatchView t(table);
     const int *pre = t.pyr_prefix(L);
     const int total = pre[t.nstreams()];
-    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+    tile_pipeline<ST, FMT>(total, [&](int g, Tile &tile) {
         const int si = find_segment(pre, t.nstreams(), g);
         const StreamEntry &e = t.stream(si);
         const int tiles_x = (e.P_next[L].w + TX - 1) / TX;
         const int local = g - pre[si];
         const int ty = local / tiles_x, tx = local - ty * tiles_x;
-        LevelArgs a;
-        level_args_from_entry(e, L, t.levels(), a);
-        pyramid_tile<ST>(a, tx * TX, ty * TY);
+        level_args_from_entry(e, L, t.levels(), tile.a);
+        tile.ox = tx * TX;
+        tile.oy = ty * TY;
+    });
+}
+
+// CTAs for `tiles` tiles: at most the number resident on the device at
+// once (the kernels stride over the rest).  Sets the kernel's dynamic shared
+// memory limit the first time per device; cap is the caller's per-kernel
+// cache of resident CTAs per device.
+template <typename K>
+cudaError_t grid_for(K kernel, int tiles, size_t smem, int *cap, int &grid) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (cap[dev] == 0) {
+        int sms = 0, per_sm = 0;
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
+        if (e != cudaSuccess) return e;
+        cap[dev] = sms * (per_sm < 1 ? 1 : per_sm);
     }
+    grid = tiles < 1 ? 1 : (tiles < cap[dev] ? tiles : cap[dev]);
+    return cudaSuccess;
+}
+
+template <int ST, int FMT>
+cudaError_t launch_level(const LevelArgs &a, cudaStream_t s) {
+    const int tiles_x = (a.w + TX - 1) / TX, total = tiles_x * ((a.h + TY - 1) / TY);
+    const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
+    static int cap[64] = {0};
+    int grid = 0;
+    cudaError_t e = grid_for(pyramid_level_kernel<ST, FMT>, total, smem, cap, grid);
+    if (e != cudaSuccess) return e;
+    pyramid_level_kernel<ST, FMT><<<grid, NT, smem, s>>>(a, tiles_x, total);
+    return cudaGetLastError();
+}
+
+template <int ST, int FMT>
+cudaError_t launch_batch_level(const uint8_t *table, int L, int max_tiles, cudaStream_t s) {
+    const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
+    static int cap[64] = {0};
+    int grid = 0;
+    cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT>, max_tiles, smem, cap, grid);
+    if (e != cudaSuccess) return e;
+    pyramid_batch_kernel<ST, FMT><<<grid, NT, smem, s>>>(table, L);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -247,13 +394,12 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
     for (int L = 0; L < pyr.levels; ++L) {
         LevelArgs a;
         const omt_level &lv = pyr.lv[L];
-        a.level = L;
         a.w = lv.w;
         a.h = lv.h;
         if (L == 0) {
             a.src = frame;
             a.src_pitch = (int64_t)pitch;
-            a.vec_ok = (((uintptr_t)frame | (uintptr_t)pitch) & 3) == 0;
+            a.vec_ok = (((uintptr_t)frame | (uintptr_t)pitch) & 15) == 0;
             a.copy = base + lv.img_off;
             a.copy_pitch = lv.img_pitch;
         } else {
@@ -275,10 +421,11 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
             a.next_pitch = 0;
             a.nw = a.nh = 0;
         }
-        dim3 grid((lv.w + TX - 1) / TX, (lv.h + TY - 1) / TY);
-        if (pyr.storage == OMT_F32) pyramid_level_kernel<OMT_F32><<<grid, NT, 0, s>>>(a);
-        else pyramid_level_kernel<OMT_F16><<<grid, NT, 0, s>>>(a);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e;
+        if (pyr.storage == OMT_F32)
+            e = L == 0 ? launch_level<OMT_F32, FMT_U8>(a, s) : launch_level<OMT_F32, FMT_F32>(a, s);
+        else
+            e = L == 0 ? launch_level<OMT_F16, FMT_U8>(a, s) : launch_level<OMT_F16, FMT_H16>(a, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -286,15 +433,15 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
 
 cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
                                  cudaStream_t s) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int L = 0; L < levels; ++L) {
-        const int cap = sms * 8;
-        const int grid = max_tiles[L] < cap ? (max_tiles[L] > 0 ? max_tiles[L] : 1) : cap;
-        if (storage == OMT_F32) pyramid_batch_kernel<OMT_F32><<<grid, NT, 0, s>>>(table, L);
-        else pyramid_batch_kernel<OMT_F16><<<grid, NT, 0, s>>>(table, L);
-        cudaError_t e = cudaGetLastError();
+        const int mt = max_tiles[L] > 0 ? max_tiles[L] : 1;
+        cudaError_t e;
+        if (storage == OMT_F32)
+            e = L == 0 ? launch_batch_level<OMT_F32, FMT_U8>(table, L, mt, s)
+                       : launch_batch_level<OMT_F32, FMT_F32>(table, L, mt, s);
+        else
+            e = L == 0 ? launch_batch_level<OMT_F16, FMT_U8>(table, L, mt, s)
+                       : launch_batch_level<OMT_F16, FMT_H16>(table, L, mt, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

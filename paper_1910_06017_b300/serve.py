@@ -396,23 +396,36 @@ class PlainGpuBackend(GpuBackend):
 
 # ---------------------------------------------------------------- workload
 
-def build_workload(n_streams: int, duration: float, workload: int = 5, sizes=None, boxes=(20, 300),
-                   max_corners: int = 50):
-    """Stream specs (Poisson arrivals at 25-60 fps, mixed resolutions, 20-300
-    boxes refreshed every 5-15 frames), two rendered frames per resolution
-    (shared by the streams of that size, page-locked) and detection boxes."""
+_RENDERS: Dict[tuple, list] = {}
+
+
+def _renders(workload: int, size: tuple) -> list:
+    """Two page-locked frames of one resolution (a texture and its shift by
+    (3.3, -2.1) px), rendered once per process and shared by its streams."""
     import torch
     from . import synth
-    sizes = sizes or (synth.SD, synth.FHD, synth.UHD)
-    ss = synth.serve_streams(n_streams, duration, workload=workload, sizes=sizes, boxes=boxes)
-    renders = {}
-    for sz in sorted({s.size for s in ss}):
-        rng = np.random.default_rng(synth.seed_for(workload) + sz[0])
-        w, h = sz
+    key = (workload, size)
+    if key not in _RENDERS:
+        rng = np.random.default_rng(synth.seed_for(workload) + size[0])
+        w, h = size
         tex = synth.Texture.draw(rng, w + 40, h + 40, ox=-20, oy=-20, n_blobs=max(64, w * h // 6000))
         f0 = synth.render_shift(tex, w, h, 0.0, 0.0)
         f1 = synth.render_shift(tex, w, h, 3.3, -2.1)
-        renders[sz] = [torch.from_numpy(f0).pin_memory(), torch.from_numpy(f1).pin_memory()]
+        _RENDERS[key] = [torch.from_numpy(f0).pin_memory(), torch.from_numpy(f1).pin_memory()]
+    return _RENDERS[key]
+
+
+def build_workload(n_streams: int, duration: float, workload: int = 5, sizes=None, boxes=(20, 300),
+                   max_corners: int = 50, fps_scale: float = 1.0):
+    """Stream specs (Poisson arrivals at 25-60 fps times fps_scale, mixed
+    resolutions, 20-300 boxes refreshed every 5-15 frames), two rendered
+    frames per resolution (shared by the streams of that size, page-locked)
+    and detection boxes."""
+    from . import synth
+    sizes = sizes or (synth.SD, synth.FHD, synth.UHD)
+    ss = synth.serve_streams(n_streams, duration, workload=workload, sizes=sizes, boxes=boxes,
+                             fps=(25.0 * fps_scale, 60.0 * fps_scale))
+    renders = {sz: _renders(workload, sz) for sz in sorted({s.size for s in ss})}
     specs, frames, det = [], {}, {}
     for s in ss:
         rng = np.random.default_rng(synth.seed_for(workload, s.stream) + 7)
@@ -438,6 +451,68 @@ def serve(specs, frames, det, params, budget_bytes: int, plain: bool = False, de
     return stats, be
 
 
+def capacity(n_streams: int, params, plain: bool, budget_bytes: int, p99_ms: float = 40.0,
+             duration: float = 3.0, min_frames: int = 3000, bisect: int = 3, workload: int = 5):
+    """The highest offered load (the 25-60 fps arrival rates times a common
+    scale) that the loop serves completely with p99 latency within p99_ms:
+    doubling or halving the scale from 1 until the outcome flips, then
+    bisecting geometrically.  Returns the summary of the best passing run
+    (its stream_frames_per_s is the capacity) and every probe."""
+    probes = []
+
+    def probe(scale):
+        dur = max(duration, min_frames / (n_streams * 42.5 * scale))
+        specs, frames, det = build_workload(n_streams, dur, workload=workload, fps_scale=scale)
+        st, _ = serve(specs, frames, det, params, budget_bytes, plain=plain, deadline=dur + 5.0)
+        s = st.summary()
+        ok = s["frames_done"] == s["frames_arrived"] and s["latency_ms_p99"] <= p99_ms
+        s["fps_scale"] = scale
+        probes.append({"fps_scale": scale, "ok": ok, "stream_frames_per_s": s["stream_frames_per_s"],
+                       "latency_ms_p99": s["latency_ms_p99"]})
+        return ok, s
+
+    best = search_scale(probe, bisect=bisect)
+    return best, probes
+
+
+def search_scale(probe: Callable[[float], tuple], bisect: int = 3, limit: float = 256.0):
+    """Largest scale with probe(scale)[0] true, for an outcome that holds
+    below some threshold and fails above it: double or halve from 1 until it
+    flips (within [1/limit, limit]), then bisect geometrically.  Returns the
+    second element of the best passing probe, or None if none passed."""
+    lo = hi = None
+    best = None
+    scale = 1.0
+    ok, s = probe(scale)
+    if ok:
+        lo, best = scale, s
+        while hi is None and scale < limit:
+            scale *= 2
+            ok, s = probe(scale)
+            if ok:
+                lo, best = scale, s
+            else:
+                hi = scale
+    else:
+        hi = scale
+        while lo is None and scale > 1.0 / limit:
+            scale /= 2
+            ok, s = probe(scale)
+            if ok:
+                lo, best = scale, s
+            else:
+                hi = scale
+    if lo is not None and hi is not None:
+        for _ in range(bisect):
+            mid = math.sqrt(lo * hi)
+            ok, s = probe(mid)
+            if ok:
+                lo, best = mid, s
+            else:
+                hi = mid
+    return best
+
+
 def main(argv=None):
     import argparse
     import json
@@ -449,19 +524,33 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--storage", default="f16", choices=["f16", "f32"])
     ap.add_argument("--plain", action="store_true", help="baseline: plain FP32 calls, one frame at a time")
+    ap.add_argument("--rate-scale", type=float, default=1.0, help="multiply every stream's frame rate")
+    ap.add_argument("--capacity", action="store_true",
+                    help="search the highest rate scale served with p99 latency within --p99-ms")
+    ap.add_argument("--p99-ms", type=float, default=40.0)
     args = ap.parse_args(argv)
-    specs, frames, det = build_workload(args.streams, args.duration)
+    specs, frames, det = build_workload(args.streams, args.duration, fps_scale=args.rate_scale)
     storage = omt.F16 if (args.storage == "f16" and not args.plain) else omt.F32
     params = omt.default_params(levels=4, win=21, max_corners=50, storage=storage)
+    budget = int(args.budget_gb * 2 ** 30)
     # warm-up: one short run so one-time setup is outside the measurement
-    serve(specs[:2], frames, det, params, int(args.budget_gb * 2 ** 30), plain=args.plain,
-          deadline=0.5)
+    serve(specs[:2], frames, det, params, budget, plain=args.plain, deadline=0.5)
     torch.cuda.synchronize()
-    stats, _ = serve(specs, frames, det, params, int(args.budget_gb * 2 ** 30), plain=args.plain,
+    path = "plain FP32 per frame" if args.plain else f"batched {args.storage}"
+    if args.capacity:
+        best, probes = capacity(args.streams, params, args.plain, budget, p99_ms=args.p99_ms,
+                                duration=args.duration)
+        out = dict(best or {})
+        out.update({"streams": args.streams, "budget_gb": args.budget_gb, "path": path,
+                    "p99_bound_ms": args.p99_ms, "capacity_stream_fps":
+                    best["stream_frames_per_s"] if best else 0.0, "probes": probes})
+        print(json.dumps(out))
+        return
+    stats, _ = serve(specs, frames, det, params, budget, plain=args.plain,
                      deadline=args.duration + 5.0)
     out = stats.summary()
     out.update({"streams": args.streams, "duration_s": args.duration, "budget_gb": args.budget_gb,
-                "path": "plain FP32 per frame" if args.plain else f"batched {args.storage}"})
+                "rate_scale": args.rate_scale, "path": path})
     print(json.dumps(out))
 
 

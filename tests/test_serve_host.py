@@ -171,3 +171,24 @@ def test_delayed_producer_latency_counts_from_arrival():
     assert all(f.done >= f.arrival for f in fr)
     # the burst is served one frame per step
     assert fr[-1].latency >= 4 * 0.004
+
+
+@pytest.mark.parametrize("threshold", [0.3, 1.0, 5.0, 40.0])
+def test_capacity_search_brackets_the_threshold(threshold):
+    from paper_1910_06017_b300.serve import search_scale
+    seen = []
+
+    def probe(scale):
+        seen.append(scale)
+        return scale <= threshold, scale
+
+    best = search_scale(probe, bisect=4)
+    assert best is not None and best <= threshold
+    # four geometric bisections of a factor-2 bracket leave < 2^(1/16) of slack
+    assert best > threshold / 2 ** (1 / 16) - 1e-12
+    assert len(seen) <= 2 + int(math.ceil(abs(math.log2(threshold)))) + 4
+
+
+def test_capacity_search_none_passes():
+    from paper_1910_06017_b300.serve import search_scale
+    assert search_scale(lambda s: (False, s), limit=8.0) is None
