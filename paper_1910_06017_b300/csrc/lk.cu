@@ -194,34 +194,28 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b, int lane) {
 }
 
 // Frame-t window from the raw template rows: (Ix, Iy) per tap row stay in
-// registers, with the level constants G (three sums) and c = sum I (Ix, Iy).
+// registers, with the level constants G (three sums).  Lane l < WIN owns tap
+// column l; lane WIN holds the column right of the window, so every lane's
+// right-hand texel comes from the next lane by a shuffle.
 template <int ST, int WIN>
 __device__ __forceinline__ void template_window(const LevelView &P, int tx0, float ax, float ay,
-                                                int lane, bool u8, const unsigned *W,
-                                                const LevelCopy &lc, float (&Xw)[WIN],
-                                                float (&Yw)[WIN], float &sxx, float &sxy,
-                                                float &syy, float &cx, float &cy) {
+                                                int lane, const unsigned *W, const LevelCopy &lc,
+                                                float (&Xw)[WIN], float (&Yw)[WIN], float &sxx,
+                                                float &sxy, float &syy) {
     using D = Dims<ST, WIN>;
-    const unsigned *rawI = W;  // the level's template buffer
     const unsigned *rawG = W + D::T * D::RWI;
     const bool tapcol = lane < WIN;
-    const int c = tapcol ? lane : 0;
-    const int ci0 = clampi(tx0 + c, 0, P.w - 1) - lc.tcol_i, ci1 = clampi(tx0 + c + 1, 0, P.w - 1) - lc.tcol_i;
-    const int cg0 = clampi(tx0 + c, 0, P.w - 1) - lc.tcol_g, cg1 = clampi(tx0 + c + 1, 0, P.w - 1) - lc.tcol_g;
-    float pI = 0.f, pX = 0.f, pY = 0.f;
-    float cx0 = 0.f, cy0 = 0.f, cx1 = 0.f, cy1 = 0.f;
+    const int cg0 = clampi(tx0 + (lane < WIN ? lane : WIN), 0, P.w - 1) - lc.tcol_g;
+    float pX = 0.f, pY = 0.f;
     sxx = sxy = syy = 0.f;
 #pragma unroll
     for (int tr = 0; tr <= WIN; ++tr) {
-        const float i0 = raw_texel<ST>(rawI + tr * D::RWI, ci0, u8);
-        const float i1 = raw_texel<ST>(rawI + tr * D::RWI, ci1, u8);
         const float2 g0 = raw_grad<ST>(rawG + tr * D::RWG, cg0);
-        const float2 g1 = raw_grad<ST>(rawG + tr * D::RWG, cg1);
-        const float hI = fmaf(ax, i1 - i0, i0);
-        const float hX = fmaf(ax, g1.x - g0.x, g0.x);
-        const float hY = fmaf(ax, g1.y - g0.y, g0.y);
+        const float g1x = __shfl_down_sync(FULL_MASK, g0.x, 1);
+        const float g1y = __shfl_down_sync(FULL_MASK, g0.y, 1);
+        const float hX = fmaf(ax, g1x - g0.x, g0.x);
+        const float hY = fmaf(ax, g1y - g0.y, g0.y);
         if (tr > 0) {
-            const float I = fmaf(ay, hI - pI, pI);
             const float X = fmaf(ay, hX - pX, pX);
             const float Y = fmaf(ay, hY - pY, pY);
             Xw[tr - 1] = X;
@@ -229,56 +223,62 @@ __device__ __forceinline__ void template_window(const LevelView &P, int tx0, flo
             sxx = fmaf(X, X, sxx);
             sxy = fmaf(X, Y, sxy);
             syy = fmaf(Y, Y, syy);
-            // Same two chains as the iteration's correlation, so that J == I
-            // gives c - sum J grad I == 0 exactly (zero flow on equal frames).
-            if (tr & 1) {
-                cx0 = fmaf(I, X, cx0);
-                cy0 = fmaf(I, Y, cy0);
-            } else {
-                cx1 = fmaf(I, X, cx1);
-                cy1 = fmaf(I, Y, cy1);
-            }
         }
-        pI = hI;
         pX = hX;
         pY = hY;
     }
     if (!tapcol) sxx = sxy = syy = 0.f;
-    cx = tapcol ? cx0 + cx1 : 0.f;
-    cy = tapcol ? cy0 + cy1 : 0.f;
 }
 
-// sum over the window of J(c + (i, j)) (Ix, Iy), read straight from the raw
-// search rows: tap row tr is raw row oy + tr (rows were clamped when
-// copied), its two texels sit at raw columns col0 and col1 (clamped level
-// columns of the lane's tap and its right neighbour).
+// The four integer-shift correlations of a raw image window with the
+// template gradients: S[2a+b] = sum over taps of V(tap + (b, a)) * Ix(tap)
+// and S[4 + 2a+b] the same with Iy, for the window whose top-left tap sits
+// at raw row oy, raw column col0 of this lane (lanes as in template_window).
+// Bilinear sampling at fraction (bx, by) is then the weighted sum
+// (1-bx)(1-by) S0 + bx(1-by) S1 + (1-bx)by S2 + bx by S3 (combine8), so a
+// window position is correlated once however many iterations revisit it.
+// The frame-t template and the frame-(t+1) search window go through this
+// same code, so equal frames give exactly equal sums.
 template <int ST, bool U8, int WIN>
-__device__ __forceinline__ void correlate_raw(const unsigned *rawJ, int oy, int col0, int col1,
-                                              float bx, float by, int lane, const float (&Xw)[WIN],
-                                              const float (&Yw)[WIN], float &sx, float &sy) {
-    using D = Dims<ST, WIN>;
-    const bool tapcol = lane < WIN;
-    const unsigned *base = rawJ + oy * D::RWJ;
-    float ax0 = 0.f, ay0 = 0.f, ax1 = 0.f, ay1 = 0.f, ph = 0.f;
+__device__ __forceinline__ void corr8(const unsigned *raw, int rw, int oy, int col0, int lane,
+                                      const float (&Xw)[WIN], const float (&Yw)[WIN],
+                                      float (&S)[8]) {
+    const unsigned *base = raw + oy * rw;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) S[q] = 0.f;
+    float p0 = 0.f, p1 = 0.f;
 #pragma unroll
     for (int tr = 0; tr <= WIN; ++tr) {
-        const unsigned *row = base + tr * D::RWJ;
-        const float v0 = raw_texel<ST>(row, col0, U8), v1 = raw_texel<ST>(row, col1, U8);
-        const float h = fmaf(bx, v1 - v0, v0);
+        const float v0 = raw_texel<ST>(base + tr * rw, col0, U8);
+        const float v1 = __shfl_down_sync(FULL_MASK, v0, 1);
         if (tr > 0) {
-            const float jv = fmaf(by, h - ph, ph);
-            if (tr & 1) {
-                ax0 = fmaf(jv, Xw[tr - 1], ax0);
-                ay0 = fmaf(jv, Yw[tr - 1], ay0);
-            } else {
-                ax1 = fmaf(jv, Xw[tr - 1], ax1);
-                ay1 = fmaf(jv, Yw[tr - 1], ay1);
-            }
+            const float X = Xw[tr - 1], Y = Yw[tr - 1];
+            S[0] = fmaf(p0, X, S[0]);
+            S[1] = fmaf(p1, X, S[1]);
+            S[2] = fmaf(v0, X, S[2]);
+            S[3] = fmaf(v1, X, S[3]);
+            S[4] = fmaf(p0, Y, S[4]);
+            S[5] = fmaf(p1, Y, S[5]);
+            S[6] = fmaf(v0, Y, S[6]);
+            S[7] = fmaf(v1, Y, S[7]);
         }
-        ph = h;
+        p0 = v0;
+        p1 = v1;
     }
-    sx = tapcol ? ax0 + ax1 : 0.f;
-    sy = tapcol ? ay0 + ay1 : 0.f;
+    if (lane >= WIN) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) S[q] = 0.f;
+    }
+}
+
+// This lane's share of sum over taps of V(tap + (fx, fy)) (Ix, Iy) for the
+// window of S, by bilinear weights.
+__device__ __forceinline__ void combine8(const float (&S)[8], float fx, float fy, float &sx,
+                                         float &sy) {
+    const float w0 = (1.0f - fx) * (1.0f - fy), w1 = fx * (1.0f - fy);
+    const float w2 = (1.0f - fx) * fy, w3 = fx * fy;
+    sx = fmaf(w3, S[3], fmaf(w2, S[2], fmaf(w1, S[1], w0 * S[0])));
+    sy = fmaf(w3, S[7], fmaf(w2, S[6], fmaf(w1, S[5], w0 * S[4])));
 }
 
 // One level of the pyramidal iteration for one point (the whole warp).
@@ -330,8 +330,16 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
 
     float Xw[WIN], Yw[WIN];
     float sxx, sxy, syy, cx, cy;
-    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, u8, W + buf * D::TRAW, lc, Xw, Yw, sxx, sxy,
-                             syy, cx, cy);
+    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, W + buf * D::TRAW, lc, Xw, Yw, sxx, sxy,
+                             syy);
+    float S[8];  // integer-shift correlations at the last position visited
+    {
+        // c = sum I(p + tap) (Ix, Iy), through the same path as J below
+        const int ci0 = clampi(ipx - R + (lane < WIN ? lane : WIN), 0, P.w - 1) - lc.tcol_i;
+        if (u8) corr8<ST, true, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, Xw, Yw, S);
+        else corr8<ST, false, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, Xw, Yw, S);
+        combine8(S, ax, ay, cx, cy);
+    }
     sxx = warp_sum(sxx);
     sxy = warp_sum(sxy);
     syy = warp_sum(syy);
@@ -354,6 +362,8 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     }
     __syncwarp();
     bool staged = c0_ok;
+    int cjx = 0, cjy = 0;
+    bool cached = false;  // S holds the correlations at (cjx, cjy)
     while (k < max_iter) {
         // Centre c = p + g + nu, held as (ipx, ipy) + (ccx, ccy).
         const float ccx = ax + gx + nux, ccy = ay + gy + nuy;
@@ -364,21 +374,26 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         if (jx < -R || jx > J.w - 1 + R || (jx == J.w - 1 + R && bx > 0.f) || jy < -R ||
             jy > J.h - 1 + R || (jy == J.h - 1 + R && by > 0.f))
             return OMT_PT_LOST_OOB;
-        if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
-            __syncwarp();
-            copy_search<ST, WIN>(J, u8, jx, jy, lane, W, lc);
-            cp_async_wait_all();   // also lands a pending prefetch
-            __syncwarp();
-            sjx = jx;
-            sjy = jy;
-            staged = true;
+        if (!cached || jx != cjx || jy != cjy) {
+            if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
+                __syncwarp();
+                copy_search<ST, WIN>(J, u8, jx, jy, lane, W, lc);
+                cp_async_wait_all();   // also lands a pending prefetch
+                __syncwarp();
+                sjx = jx;
+                sjy = jy;
+                staged = true;
+            }
+            const int col0 = clampi(jx - R + (lane < WIN ? lane : WIN), 0, J.w - 1) - lc.scol;
+            const int oy = jy - sjy + MARGIN;
+            if (u8) corr8<ST, true, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, Xw, Yw, S);
+            else corr8<ST, false, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, Xw, Yw, S);
+            cjx = jx;
+            cjy = jy;
+            cached = true;
         }
-        const int tx = jx - R + (lane < WIN ? lane : 0);
-        const int col0 = clampi(tx, 0, J.w - 1) - lc.scol, col1 = clampi(tx + 1, 0, J.w - 1) - lc.scol;
-        const int oy = jy - sjy + MARGIN;
         float sx, sy;
-        if (u8) correlate_raw<ST, true, WIN>(W + D::UNION, oy, col0, col1, bx, by, lane, Xw, Yw, sx, sy);
-        else correlate_raw<ST, false, WIN>(W + D::UNION, oy, col0, col1, bx, by, lane, Xw, Yw, sx, sy);
+        combine8(S, bx, by, sx, sy);
         warp_sum2(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
         const float ex = (syy * bbx - sxy * bby) / det;
