@@ -1,8 +1,9 @@
 // corners.cu -- K2: Shi-Tomasi response and per-box corner selection.
 //
 // Three launches per call:
-//   1. response_kernel   32x16 tiles of level 0 (only tiles that touch an
-//                        eligible pixel of some box when boxes are given):
+//   1. response_kernel   28x64 strips of level 0, one warp each (only
+//                        strips that touch an eligible pixel of some box
+//                        when boxes are given), all in registers:
 //                        integer Scharr -> 3x3 structure tensor -> exact
 //                        R = (a+c) - isqrt((a-c)^2 + 4b^2) -> non-strict 3x3
 //                        maximum flag, packed as R | flag << 30 into a
@@ -35,7 +36,7 @@ __device__ __forceinline__ uint32_t isqrt_u64(uint64_t D) {
     int64_t s = (int64_t)sqrtf(f);
     if (s > 0) {
         const int64_t r = (int64_t)D - s * s;
-        s += (int64_t)floorf((float)r / (2.0f * (float)s));
+        s += (int64_t)floorf(__fdividef((float)r, 2.0f * (float)s));
     }
     if (s < 0) s = 0;
 #pragma unroll 1
@@ -46,7 +47,20 @@ __device__ __forceinline__ uint32_t isqrt_u64(uint64_t D) {
 }
 
 // ------------------------------------------------------ response map kernel
-constexpr int RTX = 32, RTY = 16, RNT = 256;
+// A warp walks a strip of RW = 28 columns down RH = 64 rows of level 0, all
+// in registers.  Lane l holds column x = x0 - 2 + l; lanes 2..29 own the
+// strip's columns, the others supply the halo.  Per row step a lane loads
+// its column's three u8 texels (the rows around the step's gradient row),
+// takes the neighbouring columns from lanes l-1 and l+1 by shuffles (lanes
+// 0 and 31 load theirs), forms the raw Scharr gradient, and the structure
+// tensor products; their 3x1 sums come from the neighbouring lanes, the
+// 1x3 sums from the two previous rows kept in registers.  The response of
+// the row above follows (exact integer square root), and the non-strict 3x3
+// maximum flag of the row above that is decided from the 3-column maxima of
+// three response rows.  A gradient position outside the frame takes the
+// gradient of its reflect-101 image (a lane shuffle for columns; for rows the
+// three texel rows are reflected around the reflected row).
+constexpr int RW = 28, RH = 64, RNT = 256, RWARPS = RNT / 32;
 
 struct RespArgs {
     const uint8_t *img;
@@ -57,117 +71,125 @@ struct RespArgs {
     int nboxes;
 };
 
-__device__ __forceinline__ int px(const RespArgs &a, int x, int y) {
-    return (int)__ldg(a.img + (int64_t)y * a.pitch + x);
-}
-
-// One 32x16 tile of the response map at (ox, oy), whole CTA.
-__device__ __forceinline__ void response_tile(const RespArgs &a, int ox, int oy) {
-    __shared__ int2 g[RTY + 4][RTX + 4];
-    __shared__ uint32_t R[RTY + 2][RTX + 2];
-    __shared__ uint8_t px8[RTY + 6][RTX + 8];  // u8 texels of r101(q), q in the tile +- 3
-    const int tid = threadIdx.x;
-    __syncthreads();
-
-    if (a.boxes) {
-        // Skip tiles that hold no eligible pixel of any box.
-        int hit = 0;
-        const int tx1 = min(ox + RTX - 1, a.w - 1), ty1 = min(oy + RTY - 1, a.h - 1);
-        for (int b = tid; b < a.nboxes && !hit; b += RNT) {
+// Whether the strip tile at (x0, y0) holds an eligible pixel of some box
+// (always, without boxes).  Warp-uniform.
+__device__ __forceinline__ bool strip_needed(const RespArgs &a, int x0, int y0, int lane) {
+    if (!a.boxes) return true;
+    const int x1 = min(x0 + RW - 1, a.w - 1), y1 = min(y0 + RH - 1, a.h - 1);
+    for (int b0 = 0; b0 < a.nboxes; b0 += 32) {
+        const int b = b0 + lane;
+        bool hit = false;
+        if (b < a.nboxes) {
             int xlo, xhi, ylo, yhi;
             if (box_pixel_range(a.boxes[b], a.w, a.h, xlo, xhi, ylo, yhi))
-                hit = xlo <= tx1 && xhi >= ox && ylo <= ty1 && yhi >= oy;
+                hit = xlo <= x1 && xhi >= x0 && ylo <= y1 && yhi >= y0;
         }
-        if (!__syncthreads_or(hit)) return;
+        if (__any_sync(FULL_MASK, hit)) return true;
     }
+    return false;
+}
 
-    // Stage the u8 texels the gradients read.  Position (r, c) holds the
-    // texel at (r101(ox-3+c), r101(oy-3+r)); a gradient at the pixel r101(q)
-    // reads r101(r101(q) +- 1), which equals the texel staged at q +- 1
-    // except where q itself lies outside the frame: those positions are
-    // re-read through the map below.
-    for (int i = tid; i < (RTY + 6) * (RTX + 6); i += RNT) {
-        const int r = i / (RTX + 6), c = i - r * (RTX + 6);
-        px8[r][c] = __ldg(a.img + (int64_t)reflect101(oy - 3 + r, a.h) * a.pitch +
-                          reflect101(ox - 3 + c, a.w));
-    }
-    __syncthreads();
-
-    // Raw Scharr at the pixels r101(q) for q in the tile +- 2.
-    for (int i = tid; i < (RTY + 4) * (RTX + 4); i += RNT) {
-        const int r = i / (RTX + 4), c = i - r * (RTX + 4);
-        const int qx = ox - 2 + c, qy = oy - 2 + r;
-        int i00, i01, i02, i10, i12, i20, i21, i22;
-        if (qx >= 0 && qx < a.w && qy >= 0 && qy < a.h) {
-            // in-frame: neighbours are the staged positions around (r+1, c+1)
-            i00 = px8[r][c];     i01 = px8[r][c + 1];     i02 = px8[r][c + 2];
-            i10 = px8[r + 1][c];                          i12 = px8[r + 1][c + 2];
-            i20 = px8[r + 2][c]; i21 = px8[r + 2][c + 1]; i22 = px8[r + 2][c + 2];
-        } else {
-            const int x = reflect101(qx, a.w), y = reflect101(qy, a.h);
-            const int xm = reflect101(x - 1, a.w), xp = reflect101(x + 1, a.w);
-            const int ym = reflect101(y - 1, a.h), yp = reflect101(y + 1, a.h);
-            i00 = px(a, xm, ym); i01 = px(a, x, ym); i02 = px(a, xp, ym);
-            i10 = px(a, xm, y);                      i12 = px(a, xp, y);
-            i20 = px(a, xm, yp); i21 = px(a, x, yp); i22 = px(a, xp, yp);
+__device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy, int lane) {
+    const int x = x0 - 2 + lane;
+    const bool inx = x >= 0 && x < a.w;
+    const int cx = reflect101(x, a.w);
+    const bool edge = lane == 0 || lane == 31;
+    const int ex = reflect101(lane == 0 ? x - 1 : x + 1, a.w);  // edge lanes' outer column
+    // outside the frame a lane takes the gradient of its mirror column's lane
+    int src = lane;
+    if (!inx) src = min(max(reflect101(x, a.w) - (x0 - 2), 0), 31);
+    int Ha2 = 0, Hb2 = 0, Hc2 = 0, Ha1 = 0, Hb1 = 0, Hc1 = 0;  // 3x1 sums, rows g-2, g-1
+    uint32_t Rp = 0, M2 = 0, M1 = 0;  // R of row g-2; 3-column maxima of rows g-3, g-2
+#pragma unroll 1
+    for (int s = 0; s < RH + 4; ++s) {
+        const int g = oy - 2 + s;  // gradient row of this step
+        const int py = reflect101(g, a.h);
+        const uint8_t *r0 = a.img + (int64_t)reflect101(py - 1, a.h) * a.pitch;
+        const uint8_t *r1 = a.img + (int64_t)py * a.pitch;
+        const uint8_t *r2 = a.img + (int64_t)reflect101(py + 1, a.h) * a.pitch;
+        const int vm = __ldg(r0 + cx), v0 = __ldg(r1 + cx), vp = __ldg(r2 + cx);
+        int em = 0, e0 = 0, ep = 0;
+        if (edge) {
+            em = __ldg(r0 + ex);
+            e0 = __ldg(r1 + ex);
+            ep = __ldg(r2 + ex);
         }
-        const int gx = 3 * (i02 - i00) + 10 * (i12 - i10) + 3 * (i22 - i20);
-        const int gy = 3 * (i20 - i00) + 10 * (i21 - i01) + 3 * (i22 - i02);
-        g[r][c] = make_int2(gx, gy);
-    }
-    __syncthreads();
-
-    // Structure tensor and response at the tile +- 1 (in-image positions).
-    for (int i = tid; i < (RTY + 2) * (RTX + 2); i += RNT) {
-        const int r = i / (RTX + 2), c = i - r * (RTX + 2);
-        const int x = ox - 1 + c, y = oy - 1 + r;
-        uint32_t val = 0;
-        if (x >= 0 && x < a.w && y >= 0 && y < a.h) {
-            int sa = 0, sb = 0, sc = 0;
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    const int2 q = g[r + dy][c + dx];
-                    sa += q.x * q.x;
-                    sb += q.x * q.y;
-                    sc += q.y * q.y;
-                }
-            const int64_t amc = (int64_t)sa - sc;
-            const uint64_t D = (uint64_t)(amc * amc) + 4ull * (uint64_t)((int64_t)sb * sb);
-            val = (uint32_t)((int64_t)sa + sc - (int64_t)isqrt_u64(D));
+        int lm = __shfl_up_sync(FULL_MASK, vm, 1), l0 = __shfl_up_sync(FULL_MASK, v0, 1),
+            lp = __shfl_up_sync(FULL_MASK, vp, 1);
+        int qm = __shfl_down_sync(FULL_MASK, vm, 1), q0 = __shfl_down_sync(FULL_MASK, v0, 1),
+            qp = __shfl_down_sync(FULL_MASK, vp, 1);
+        if (lane == 0) {
+            lm = em;
+            l0 = e0;
+            lp = ep;
+        } else if (lane == 31) {
+            qm = em;
+            q0 = e0;
+            qp = ep;
         }
-        R[r][c] = val;
-    }
-    __syncthreads();
+        int gx = 3 * (qm - lm) + 10 * (q0 - l0) + 3 * (qp - lp);
+        int gy = 3 * (lp - lm) + 10 * (vp - vm) + 3 * (qp - qm);
+        gx = __shfl_sync(FULL_MASK, gx, src);
+        gy = __shfl_sync(FULL_MASK, gy, src);
+        const int pa = gx * gx, pb = gx * gy, pc = gy * gy;
+        const int Ha0 = pa + __shfl_up_sync(FULL_MASK, pa, 1) + __shfl_down_sync(FULL_MASK, pa, 1);
+        const int Hb0 = pb + __shfl_up_sync(FULL_MASK, pb, 1) + __shfl_down_sync(FULL_MASK, pb, 1);
+        const int Hc0 = pc + __shfl_up_sync(FULL_MASK, pc, 1) + __shfl_down_sync(FULL_MASK, pc, 1);
 
-    for (int i = tid; i < RTY * RTX; i += RNT) {
-        const int r = i / RTX, c = i - r * RTX;
-        const int x = ox + c, y = oy + r;
-        if (x >= a.w || y >= a.h) continue;
-        const uint32_t v = R[r + 1][c + 1];
-        uint32_t flag = 0;
-        if (x >= 1 && x <= a.w - 2 && y >= 1 && y <= a.h - 2) {
-            bool m = true;
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) m = m && (v >= R[r + dy][c + dx]);
-            flag = m ? MAX_FLAG : 0u;
+        // response of row g - 1 (its tensor is complete: rows g-2 .. g)
+        uint32_t Rn = 0;
+        if (inx && g - 1 >= 0 && g - 1 < a.h) {
+            const int ta = Ha2 + Ha1 + Ha0, tb = Hb2 + Hb1 + Hb0, tc = Hc2 + Hc1 + Hc0;
+            const int64_t amc = (int64_t)ta - tc;
+            const uint64_t D = (uint64_t)(amc * amc) + 4ull * (uint64_t)((int64_t)tb * tb);
+            Rn = (uint32_t)((int64_t)ta + tc - (int64_t)isqrt_u64(D));
         }
-        a.out[(int64_t)y * a.w + x] = v | flag;
+        const uint32_t Mn =
+            max(Rn, max(__shfl_up_sync(FULL_MASK, Rn, 1), __shfl_down_sync(FULL_MASK, Rn, 1)));
+
+        // row g - 2: its value and maximum flag
+        const int yf = g - 2;
+        if (s >= 4 && yf < a.h && lane >= 2 && lane <= 29 && inx) {
+            uint32_t flag = 0;
+            if (x >= 1 && x <= a.w - 2 && yf >= 1 && yf <= a.h - 2)
+                flag = Rp >= max(M2, max(M1, Mn)) ? MAX_FLAG : 0u;
+            a.out[(int64_t)yf * a.w + x] = Rp | flag;
+        }
+        Ha2 = Ha1;
+        Hb2 = Hb1;
+        Hc2 = Hc1;
+        Ha1 = Ha0;
+        Hb1 = Hb0;
+        Hc1 = Hc0;
+        M2 = M1;
+        M1 = Mn;
+        Rp = Rn;
     }
 }
 
-__global__ void __launch_bounds__(RNT) response_kernel(RespArgs a) {
-    response_tile(a, blockIdx.x * RTX, blockIdx.y * RTY);
+// Tile t of a w x h frame: strip column and row block.
+__device__ __forceinline__ void strip_origin(int t, int w, int &x0, int &y0) {
+    const int tx = (w + RW - 1) / RW;
+    const int ty = t / tx;
+    x0 = (t - ty * tx) * RW;
+    y0 = ty * RH;
+}
+
+__global__ void __launch_bounds__(RNT) response_kernel(RespArgs a, int total) {
+    const int lane = threadIdx.x & 31;
+    for (int t = blockIdx.x * RWARPS + (threadIdx.x >> 5); t < total; t += gridDim.x * RWARPS) {
+        int x0, y0;
+        strip_origin(t, a.w, x0, y0);
+        if (strip_needed(a, x0, y0, lane)) response_strip(a, x0, y0, lane);
+    }
 }
 
 __global__ void __launch_bounds__(RNT) response_batch_kernel(const uint8_t *table) {
     const BatchView t(table);
     const int32_t *pre = t.resp_prefix();
     const int total = pre[t.nstreams()];
-    for (int gi = blockIdx.x; gi < total; gi += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int gi = blockIdx.x * RWARPS + (threadIdx.x >> 5); gi < total; gi += gridDim.x * RWARPS) {
         const int si = find_segment(pre, t.nstreams(), gi);
         const StreamEntry &e = t.stream(si);
         RespArgs a;
@@ -178,10 +200,9 @@ __global__ void __launch_bounds__(RNT) response_batch_kernel(const uint8_t *tabl
         a.out = e.rmap;
         a.boxes = e.boxes;
         a.nboxes = e.nboxes;
-        const int tiles_x = (e.w + RTX - 1) / RTX;
-        const int local = gi - pre[si];
-        const int ty = local / tiles_x, tx = local - ty * tiles_x;
-        response_tile(a, tx * RTX, ty * RTY);
+        int x0, y0;
+        strip_origin(gi - pre[si], e.w, x0, y0);
+        if (strip_needed(a, x0, y0, lane)) response_strip(a, x0, y0, lane);
     }
 }
 
@@ -558,8 +579,8 @@ cudaError_t launch_corner_response(const omt_pyramid &pyr, uint32_t *out, const 
     a.out = out;
     a.boxes = boxes;
     a.nboxes = nboxes;
-    dim3 grid((pyr.w + RTX - 1) / RTX, (pyr.h + RTY - 1) / RTY);
-    response_kernel<<<grid, RNT, 0, s>>>(a);
+    const int total = response_tiles(pyr.w, pyr.h);
+    response_kernel<<<(total + RWARPS - 1) / RWARPS, RNT, 0, s>>>(a, total);
     return cudaGetLastError();
 }
 
@@ -605,14 +626,15 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
     return cudaGetLastError();
 }
 
-int response_tiles(int w, int h) { return ((w + RTX - 1) / RTX) * ((h + RTY - 1) / RTY); }
+int response_tiles(int w, int h) { return ((w + RW - 1) / RW) * ((h + RH - 1) / RH); }
 
 cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_resp_tiles,
                                  int max_boxes, int max_corners, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = max_resp_tiles < sms * 8 ? max_resp_tiles : sms * 8;
+    int grid = (max_resp_tiles + RWARPS - 1) / RWARPS;
+    grid = grid < sms * 8 ? grid : sms * 8;
     response_batch_kernel<<<grid > 0 ? grid : 1, RNT, 0, s>>>(table);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
