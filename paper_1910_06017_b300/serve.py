@@ -215,7 +215,13 @@ class Scheduler:
 class GpuBackend(Backend):
     """Drives libomt: per stream a slot of device buffers (two pyramids, two
     frame slots, boxes, points, corner scratch); one omt_batch_step per
-    step over the slots of that step, from a ring of page-locked tables."""
+    step over the slots of that step, from a ring of page-locked tables.
+
+    The frames of a step are copied to the device on a copy stream, so the
+    copies of step k overlap the compute of step k-1; the compute stream
+    waits for them.  A stream's frame slots alternate, so the slot a copy
+    overwrites was last read by step k-2 or earlier, which the copy stream
+    waits for."""
 
     def __init__(self, params, caps_streams: int, caps_boxes: int, max_w: int, max_h: int,
                  max_corners: int, frames_host: Dict[int, list], det_boxes: Dict[int, np.ndarray],
@@ -235,6 +241,15 @@ class GpuBackend(Backend):
         self.det_boxes = det_boxes
         self.keep_boxes = keep_boxes
         self.stream = torch.cuda.Stream(device=self.device)
+        self.copy_stream = torch.cuda.Stream(device=self.device)
+        self.step_events = collections.deque(maxlen=2)   # steps k-2, k-1
+        self._det = {}
+
+    def _det_boxes(self, sid):
+        """Detection boxes of a stream, page-locked once."""
+        if sid not in self._det:
+            self._det[sid] = self.torch.from_numpy(np.ascontiguousarray(self.det_boxes[sid])).pin_memory()
+        return self._det[sid]
 
     def bytes_for(self, spec: StreamSpec) -> int:
         omt = self.omt
@@ -300,21 +315,30 @@ class GpuBackend(Backend):
         if self.ring_events[k] is not None:
             self.ring_events[k].synchronize()   # the step that read this table is done
         descs, host = [], {}
-        with torch.cuda.stream(self.stream):
+        with torch.cuda.stream(self.copy_stream):
+            if len(self.step_events) == 2:
+                self.copy_stream.wait_event(self.step_events[0])
             for slot, idx in items:
                 spec = slot["spec"]
                 fh = self.frames_host[spec.sid][idx % len(self.frames_host[spec.sid])]
+                # a stream's first frame goes to slot 1, so that its first
+                # step's copy (slot 0) has no earlier reader
+                slot["frame"][1 if not slot["primed"] else slot["cur"]].copy_(fh, non_blocking=True)
+            copied = torch.cuda.Event()
+            copied.record(self.copy_stream)
+        with torch.cuda.stream(self.stream):
+            self.stream.wait_event(copied)
+            for slot, idx in items:
+                spec = slot["spec"]
                 if not slot["primed"]:
                     # a stream's first frame only builds its pyramid
-                    slot["frame"][0].copy_(fh, non_blocking=True)
-                    omt.build_pyramid(slot["frame"][0], slot["pyr"][0], self.params)
-                    slot["boxes"].copy_(torch.from_numpy(self.det_boxes[spec.sid]), non_blocking=True)
+                    omt.build_pyramid(slot["frame"][1], slot["pyr"][0], self.params)
+                    slot["boxes"].copy_(self._det_boxes(spec.sid), non_blocking=True)
                     slot["primed"] = True
                     continue
                 par = slot["cur"]
-                slot["frame"][par].copy_(fh, non_blocking=True)
                 if idx % spec.refresh == 0:   # a detection replaces the tracked boxes
-                    slot["boxes"].copy_(torch.from_numpy(self.det_boxes[spec.sid]), non_blocking=True)
+                    slot["boxes"].copy_(self._det_boxes(spec.sid), non_blocking=True)
                 descs.append(self._desc(slot, par))
                 host[id(slot)] = slot
             if descs:
@@ -331,6 +355,7 @@ class GpuBackend(Backend):
             ev = torch.cuda.Event()
             ev.record(self.stream)
         self.ring_events[k] = ev
+        self.step_events.append(ev)
         return _Handle(ev, list(items), host if self.keep_boxes else {})
 
     def done(self, handle) -> bool:
@@ -368,13 +393,13 @@ class PlainGpuBackend(GpuBackend):
                     slot["frame"][0].copy_(fh, non_blocking=True)
                     omt.build_pyramid(slot["frame"][0], slot["pyr"][0], self.params)
                     slot["primed"] = True
-                    slot["boxes"].copy_(torch.from_numpy(self.det_boxes[spec.sid]), non_blocking=True)
+                    slot["boxes"].copy_(self._det_boxes(spec.sid), non_blocking=True)
                     continue
                 par = slot["cur"]
                 f = slot["frame"][par]
                 f.copy_(fh, non_blocking=True)
                 if idx % spec.refresh == 0:
-                    slot["boxes"].copy_(torch.from_numpy(self.det_boxes[spec.sid]), non_blocking=True)
+                    slot["boxes"].copy_(self._det_boxes(spec.sid), non_blocking=True)
                 prm = self.params.replace(max_corners=spec.max_corners)
                 prev, nxt = slot["pyr"][par], slot["pyr"][1 - par]
                 nb = spec.n_boxes
