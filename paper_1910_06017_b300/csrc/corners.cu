@@ -46,15 +46,37 @@ __device__ __forceinline__ uint32_t isqrt_u64(uint64_t D) {
     return (uint32_t)s;
 }
 
+// The same for D < 2^58 given f, any float within a relative 2^-20 of D:
+// the hardware square-root approximation of f is within a relative 2^-19
+// of sqrt(D), i.e. within 2^10 for sqrt(D) < 2^29, and one Newton step on
+// the exact residual brings it within one unit (the unit steps finish).
+__device__ __forceinline__ uint32_t isqrt_est(uint64_t D, float f) {
+    if (D == 0) return 0;
+    float sf;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(sf) : "f"(f));
+    int64_t s = (int64_t)sf;
+    if (s > 0) {
+        const int64_t r = (int64_t)D - s * s;
+        s += (int64_t)floorf(__fdividef((float)r, 2.0f * (float)s));
+    }
+    if (s < 0) s = 0;
+#pragma unroll 1
+    for (int k = 0; k < 8 && (uint64_t)s * (uint64_t)s > D; ++k) --s;
+#pragma unroll 1
+    for (int k = 0; k < 8 && (uint64_t)(s + 1) * (uint64_t)(s + 1) <= D; ++k) ++s;
+    return (uint32_t)s;
+}
+
 // ------------------------------------------------------ response map kernel
 // A warp walks a strip of RW = 28 columns down RH = 64 rows of level 0, all
 // in registers.  Lane l holds column x = x0 - 2 + l; lanes 2..29 own the
 // strip's columns, the others supply the halo.  Per row step a lane loads
-// its column's three u8 texels (the rows around the step's gradient row),
-// takes the neighbouring columns from lanes l-1 and l+1 by shuffles (lanes
-// 0 and 31 load theirs), forms the raw Scharr gradient, and the structure
-// tensor products; their 3x1 sums come from the neighbouring lanes, the
-// 1x3 sums from the two previous rows kept in registers.  The response of
+// its column's texel of the new bottom row (the three rows around the step's
+// gradient row slide down; reflected rows at the frame's top and bottom are
+// read afresh), takes the neighbouring columns from lanes l-1 and l+1 by
+// shuffles (lanes 0 and 31 load theirs), forms the raw Scharr gradient, and
+// the 3x1 sums of the structure tensor products from its neighbours'
+// gradients; the 1x3 sums come from the two previous rows kept in registers.  The response of
 // the row above follows (exact integer square root), and the non-strict 3x3
 // maximum flag of the row above that is decided from the 3-column maxima of
 // three response rows.  A gradient position outside the frame takes the
@@ -95,54 +117,86 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
     const int cx = reflect101(x, a.w);
     const bool edge = lane == 0 || lane == 31;
     const int ex = reflect101(lane == 0 ? x - 1 : x + 1, a.w);  // edge lanes' outer column
-    // outside the frame a lane takes the gradient of its mirror column's lane
+    // Outside the frame a lane takes the gradient of its mirror column's
+    // lane; only strips that reach a frame edge need the exchange.
+    const bool mirror = x0 - 2 < 0 || x0 + 29 >= a.w;
     int src = lane;
     if (!inx) src = min(max(reflect101(x, a.w) - (x0 - 2), 0), 31);
+    // texels of the three rows around the gradient row: own column (v),
+    // left (l) and right (q) neighbours; m, 0, p = rows above, at, below
+    int vm = 0, v0 = 0, vp = 0, lm = 0, l0 = 0, lp = 0, qm = 0, q0 = 0, qp = 0;
     int Ha2 = 0, Hb2 = 0, Hc2 = 0, Ha1 = 0, Hb1 = 0, Hc1 = 0;  // 3x1 sums, rows g-2, g-1
     uint32_t Rp = 0, M2 = 0, M1 = 0;  // R of row g-2; 3-column maxima of rows g-3, g-2
 #pragma unroll 1
     for (int s = 0; s < RH + 4; ++s) {
         const int g = oy - 2 + s;  // gradient row of this step
-        const int py = reflect101(g, a.h);
-        const uint8_t *r0 = a.img + (int64_t)reflect101(py - 1, a.h) * a.pitch;
-        const uint8_t *r1 = a.img + (int64_t)py * a.pitch;
-        const uint8_t *r2 = a.img + (int64_t)reflect101(py + 1, a.h) * a.pitch;
-        const int vm = __ldg(r0 + cx), v0 = __ldg(r1 + cx), vp = __ldg(r2 + cx);
-        int em = 0, e0 = 0, ep = 0;
-        if (edge) {
-            em = __ldg(r0 + ex);
-            e0 = __ldg(r1 + ex);
-            ep = __ldg(r2 + ex);
-        }
-        int lm = __shfl_up_sync(FULL_MASK, vm, 1), l0 = __shfl_up_sync(FULL_MASK, v0, 1),
+        if (s > 0 && g >= 2 && g <= a.h - 2) {
+            // the previous step read rows g-2 .. g: slide and read row g+1
+            vm = v0;
+            v0 = vp;
+            lm = l0;
+            l0 = lp;
+            qm = q0;
+            q0 = qp;
+            const uint8_t *r2 = a.img + (int64_t)(g + 1) * a.pitch;
+            vp = __ldg(r2 + cx);
+            const int ep = edge ? (int)__ldg(r2 + ex) : 0;
             lp = __shfl_up_sync(FULL_MASK, vp, 1);
-        int qm = __shfl_down_sync(FULL_MASK, vm, 1), q0 = __shfl_down_sync(FULL_MASK, v0, 1),
             qp = __shfl_down_sync(FULL_MASK, vp, 1);
-        if (lane == 0) {
-            lm = em;
-            l0 = e0;
-            lp = ep;
-        } else if (lane == 31) {
-            qm = em;
-            q0 = e0;
-            qp = ep;
+            if (lane == 0) lp = ep;
+            else if (lane == 31) qp = ep;
+        } else {
+            const int py = reflect101(g, a.h);
+            const uint8_t *r0 = a.img + (int64_t)reflect101(py - 1, a.h) * a.pitch;
+            const uint8_t *r1 = a.img + (int64_t)py * a.pitch;
+            const uint8_t *r2 = a.img + (int64_t)reflect101(py + 1, a.h) * a.pitch;
+            vm = __ldg(r0 + cx);
+            v0 = __ldg(r1 + cx);
+            vp = __ldg(r2 + cx);
+            int em = 0, e0 = 0, ep = 0;
+            if (edge) {
+                em = __ldg(r0 + ex);
+                e0 = __ldg(r1 + ex);
+                ep = __ldg(r2 + ex);
+            }
+            lm = __shfl_up_sync(FULL_MASK, vm, 1);
+            l0 = __shfl_up_sync(FULL_MASK, v0, 1);
+            lp = __shfl_up_sync(FULL_MASK, vp, 1);
+            qm = __shfl_down_sync(FULL_MASK, vm, 1);
+            q0 = __shfl_down_sync(FULL_MASK, v0, 1);
+            qp = __shfl_down_sync(FULL_MASK, vp, 1);
+            if (lane == 0) {
+                lm = em;
+                l0 = e0;
+                lp = ep;
+            } else if (lane == 31) {
+                qm = em;
+                q0 = e0;
+                qp = ep;
+            }
         }
         int gx = 3 * (qm - lm) + 10 * (q0 - l0) + 3 * (qp - lp);
         int gy = 3 * (lp - lm) + 10 * (vp - vm) + 3 * (qp - qm);
-        gx = __shfl_sync(FULL_MASK, gx, src);
-        gy = __shfl_sync(FULL_MASK, gy, src);
-        const int pa = gx * gx, pb = gx * gy, pc = gy * gy;
-        const int Ha0 = pa + __shfl_up_sync(FULL_MASK, pa, 1) + __shfl_down_sync(FULL_MASK, pa, 1);
-        const int Hb0 = pb + __shfl_up_sync(FULL_MASK, pb, 1) + __shfl_down_sync(FULL_MASK, pb, 1);
-        const int Hc0 = pc + __shfl_up_sync(FULL_MASK, pc, 1) + __shfl_down_sync(FULL_MASK, pc, 1);
+        if (mirror) {
+            gx = __shfl_sync(FULL_MASK, gx, src);
+            gy = __shfl_sync(FULL_MASK, gy, src);
+        }
+        // 3x1 sums of the tensor products over columns x-1 .. x+1
+        const int gxl = __shfl_up_sync(FULL_MASK, gx, 1), gyl = __shfl_up_sync(FULL_MASK, gy, 1);
+        const int gxr = __shfl_down_sync(FULL_MASK, gx, 1), gyr = __shfl_down_sync(FULL_MASK, gy, 1);
+        const int Ha0 = gxl * gxl + gx * gx + gxr * gxr;
+        const int Hb0 = gxl * gyl + gx * gy + gxr * gyr;
+        const int Hc0 = gyl * gyl + gy * gy + gyr * gyr;
 
         // response of row g - 1 (its tensor is complete: rows g-2 .. g)
         uint32_t Rn = 0;
         if (inx && g - 1 >= 0 && g - 1 < a.h) {
             const int ta = Ha2 + Ha1 + Ha0, tb = Hb2 + Hb1 + Hb0, tc = Hc2 + Hc1 + Hc0;
-            const int64_t amc = (int64_t)ta - tc;
-            const uint64_t D = (uint64_t)(amc * amc) + 4ull * (uint64_t)((int64_t)tb * tb);
-            Rn = (uint32_t)((int64_t)ta + tc - (int64_t)isqrt_u64(D));
+            const int amc = ta - tc;  // |a - c| < 2^28
+            const uint64_t D = (uint64_t)((int64_t)amc * amc) + 4ull * (uint64_t)((int64_t)tb * tb);
+            const float fa = (float)amc, fb = (float)tb;
+            const float f = fmaf(fa, fa, 4.0f * fb * fb);
+            Rn = (uint32_t)((int64_t)ta + tc - (int64_t)isqrt_est(D, f));
         }
         const uint32_t Mn =
             max(Rn, max(__shfl_up_sync(FULL_MASK, Rn, 1), __shfl_down_sync(FULL_MASK, Rn, 1)));
