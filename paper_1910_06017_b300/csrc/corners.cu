@@ -262,8 +262,23 @@ __global__ void __launch_bounds__(RNT) response_batch_kernel(const uint8_t *tabl
 
 // ------------------------------------------------------------ select kernel
 constexpr int SNT = 256;
-constexpr int SCAP = 4096;   // keys sorted at once in shared memory
-constexpr int GCAP = 16384;  // cells of the accepted-point grid in shared memory
+constexpr int SCAP = 4096;   // candidate keys held in shared memory
+constexpr int GCAP = 8192;   // cells of the accepted-point grid in shared memory
+
+// Keys sorted per chunk for a box keeping up to maxc corners: enough for the
+// greedy pass to usually finish in one chunk (it rejects some candidates).
+__host__ __device__ __forceinline__ int chunk_keys(int maxc) {
+    int t = 64;
+    while (t < 4 * maxc && t < SCAP) t <<= 1;
+    return t;
+}
+
+// Dynamic shared memory of the select kernels for boxes of up to acc_cap
+// corners: keys[SCAP] | sorted chunk | accepted points | grid cells.
+__host__ __device__ __forceinline__ size_t select_smem_bytes(int acc_cap) {
+    return (size_t)SCAP * 8 + (size_t)chunk_keys(acc_cap) * 8 + (size_t)acc_cap * 8 +
+           (size_t)GCAP * 2;
+}
 
 struct SelectArgs {
     const uint32_t *rmap;
@@ -372,12 +387,67 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
     if (lane == 0) *s_nacc = nacc;
 }
 
-// Corners of one box, whole CTA.  Shared memory: keys[SCAP] | acc[acc_cap]
-// | cells[GCAP] in the dynamic area.
+// Find the k-th largest of the keys in [lo_bound, hi) among keys[0..n)
+// (1 <= k <= their count; keys are unique), by an 8-bit MSD radix select;
+// whole CTA, result in the return value of every thread.
+__device__ uint64_t kth_largest(const uint64_t *keys, int n, uint64_t lo_bound, uint64_t hi, int k,
+                                unsigned *hist, int *s_sel, int *s_k) {
+    const int tid = threadIdx.x;
+    uint64_t prefix = 0, pmask = 0;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int i = tid; i < 256; i += SNT) hist[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += SNT) {
+            const uint64_t key = keys[i];
+            if (key >= lo_bound && key < hi && (key & pmask) == prefix)
+                atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // lane l holds bins 255-8l .. 248-8l; scan from the top
+            unsigned c[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = hist[255 - 8 * tid - q];
+                sum += c[q];
+            }
+            unsigned incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(FULL_MASK, incl, o);
+                if (tid >= o) incl += v;
+            }
+            const unsigned excl = incl - sum;
+            const unsigned hit = __ballot_sync(FULL_MASK, incl >= (unsigned)k);
+            if (tid == __ffs(hit) - 1) {
+                unsigned cum = excl;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (cum + c[q] >= (unsigned)k) {
+                        *s_sel = 255 - 8 * tid - q;
+                        *s_k = k - (int)cum;
+                        break;
+                    }
+                    cum += c[q];
+                }
+            }
+        }
+        __syncthreads();
+        prefix |= (uint64_t)*s_sel << shift;
+        pmask |= 0xFFull << shift;
+        k = *s_k;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+// Corners of one box, whole CTA.  Shared memory: keys[SCAP] | chunk[T] |
+// acc[acc_cap] | cells[GCAP] in the dynamic area.
 __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *keys = (uint64_t *)smem;
-    int2 *acc = (int2 *)(keys + SCAP);
+    uint64_t *chunk = keys + SCAP;
+    int2 *acc = (int2 *)(chunk + chunk_keys(acc_cap));
     int16_t *cells = (int16_t *)(acc + acc_cap);
     __shared__ unsigned hist[256];
     __shared__ int s_count, s_nacc, s_sel, s_k;
@@ -401,45 +471,79 @@ __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
     if (g.cells)
         for (int i = tid; i < g.gx * g.gy; i += SNT) g.cells[i] = -1;
 
-    // Pass 1: R_max over the eligible pixels.
-    uint32_t m = 0;
-    for (int i = tid; i < E; i += SNT) {
-        const int y = ylo + i / nx, x = xlo + i % nx;
-        m = max(m, __ldg(a.rmap + (int64_t)y * a.w + x) & R_MASK);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
+    // One pass over the eligible pixels (a warp per row): R_max, and the keys
+    // of every local maximum with R > 0 while they fit.
+    const int warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         s_rmax = 0;
         s_count = 0;
         s_nacc = 0;
     }
     __syncthreads();
-    if ((tid & 31) == 0) atomicMax(&s_rmax, m);
-    __syncthreads();
-    const int64_t thr = (int64_t)a.qnum * (int64_t)s_rmax;
-
-    // Pass 2: gather the candidate keys (all of them if they fit).
-    for (int i = tid; i < E; i += SNT) {
-        const int y = ylo + i / nx, x = xlo + i % nx;
-        const uint32_t v = __ldg(a.rmap + (int64_t)y * a.w + x);
-        const uint32_t R = v & R_MASK;
-        if ((v & MAX_FLAG) && R > 0 && (int64_t)a.qden * R > thr) {
-            const int pos = atomicAdd(&s_count, 1);
-            if (pos < SCAP) keys[pos] = make_key(R, (uint32_t)(y * a.w + x));
+    uint32_t m = 0;
+    for (int y = ylo + warp; y <= yhi; y += SNT / 32) {
+        const uint32_t *row = a.rmap + (int64_t)y * a.w;
+        // four loads in flight per lane
+        for (int x = xlo + lane; x <= xhi; x += 128) {
+            uint32_t v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = x + 32 * q <= xhi ? __ldg(row + x + 32 * q) : 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t R = v[q] & R_MASK;
+                m = max(m, R);
+                if ((v[q] & MAX_FLAG) && R > 0) {
+                    const int pos = atomicAdd(&s_count, 1);
+                    if (pos < SCAP) keys[pos] = make_key(R, (uint32_t)(y * a.w + x + 32 * q));
+                }
+            }
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
+    if (lane == 0) atomicMax(&s_rmax, m);
     __syncthreads();
+    const int64_t thr = (int64_t)a.qnum * (int64_t)s_rmax;
     const int total = s_count;
 
     if (total <= SCAP) {
-        int N = 1;
-        while (N < total) N <<= 1;
-        for (int i = total + tid; i < N; i += SNT) keys[i] = 0ull;
-        __syncthreads();
-        bitonic_sort(keys, N);
-        greedy(a, box, keys, N, total, acc, &s_nacc, g);
-        __syncthreads();
+        // Candidates pass the quality test iff R > thr / qden, i.e. they are
+        // the keys >= vmin.  Take them in descending chunks of T keys: radix
+        // select the chunk's smallest key, gather, sort, greedy.
+        const int64_t rth = thr / a.qden;  // largest R that fails
+        const uint64_t vmin = rth >= (int64_t)R_MASK ? ~0ull : (uint64_t)(rth + 1) << 32;
+        const int T = chunk_keys(a.maxc);
+        uint64_t hi = ~0ull;
+        for (int round = 0; round <= total / T + 1; ++round) {
+            if (tid == 0) s_k = 0;
+            __syncthreads();
+            int cnt = 0;
+            for (int i = tid; i < total; i += SNT) cnt += keys[i] >= vmin && keys[i] < hi;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+            if (lane == 0 && cnt) atomicAdd(&s_k, cnt);
+            __syncthreads();
+            const int rem = s_k;
+            if (rem == 0) break;
+            const uint64_t lo = rem <= T ? vmin : kth_largest(keys, total, vmin, hi, T, hist, &s_sel, &s_k);
+            if (tid == 0) s_count = 0;
+            __syncthreads();
+            for (int i = tid; i < total; i += SNT) {
+                const uint64_t key = keys[i];
+                if (key >= lo && key < hi) chunk[atomicAdd(&s_count, 1)] = key;
+            }
+            __syncthreads();
+            const int n = s_count;  // = min(rem, T)
+            int N = 1;
+            while (N < n) N <<= 1;
+            for (int i = n + tid; i < N; i += SNT) chunk[i] = 0ull;
+            __syncthreads();
+            bitonic_sort(chunk, N);
+            greedy(a, box, chunk, N, n, acc, &s_nacc, g);
+            __syncthreads();
+            if (s_nacc >= a.maxc || rem <= T) break;
+            hi = lo;
+        }
     } else {
         // Descending chunks of SCAP keys: lo = the SCAP-th largest key below hi.
         // Each round consumes exactly SCAP keys below hi, so total / SCAP + 1
@@ -668,7 +772,7 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
         while (2 * (int64_t)(a.cell + 1) * (a.cell + 1) <= a.md2c) ++a.cell;
         a.pad_pts = pad_pts;
         a.pad_counts = pad_counts;
-        const size_t smem = (size_t)SCAP * 8 + (size_t)prm.max_corners * 8 + (size_t)GCAP * 2;
+        const size_t smem = select_smem_bytes(prm.max_corners);
         e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
@@ -693,7 +797,7 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (max_boxes > 0) {
-        const size_t smem = (size_t)SCAP * 8 + (size_t)max_corners * 8 + (size_t)GCAP * 2;
+        const size_t smem = select_smem_bytes(max_corners);
         e = cudaFuncSetAttribute(select_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
