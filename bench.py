@@ -52,6 +52,29 @@ def peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
+def source_digest(files) -> str:
+    """sha256 over kernel source files (paths relative to the repository)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in files:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def dram_traffic(kernel: str):
+    """DRAM bytes of one ncu capture of `kernel` (profiles/traffic.json), or
+    None when the kernel's sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(kernel)
+    if not rec or source_digest(rec["sources"]) != rec["sha256"]:
+        return None
+    return rec
+
+
 def dist_env():
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -292,6 +315,9 @@ def run_omt(args, ws, rank, local):
     sm_mhz = pk.get("sm_max_mhz", 2032.0)
     fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (lk_ms * 1e-3) / 1e12
+    lk_tr = dram_traffic("lk_batch_kernel")
+    pyr_tr = dram_traffic("pyramid_batch_kernel")
+    level0_px = sum(w * h for w, h in (sp.size for sp in streams))
     return {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -311,14 +337,19 @@ def run_omt(args, ws, rank, local):
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "roofline": {"kernel": "lk_batch_kernel", "bound": "alu", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None,
+                     # DRAM bytes of one launch on this workload (ncu capture of the
+                     # same kernel source; see profiles/traffic.json)
+                     "traffic": lk_tr["bytes_per_launch"] if lk_tr else None,
                      "peak_source": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({pk_src} max clock)",
                      "lk_ms_per_step": lk_ms, "lk_share": lk_ms / ms_step},
         "roofline_pyramid": {"kernel": "pyramid_batch_kernel (all levels)", "bound": "hbm",
                              "achieved": pyr_bytes / (pyr_ms * 1e-3) / 1e9,
                              "peak": pk.get("hbm_gbs", 6400.0), "unit": "GB/s",
                              "frac": pyr_bytes / (pyr_ms * 1e-3) / 1e9 / pk.get("hbm_gbs", 6400.0),
-                             "traffic": None, "bytes_per_level0_px": pyramid_bytes_per_px(args.storage, LEVELS),
+                             # captured on a larger case, scaled per level-0 pixel
+                             "traffic": (pyr_tr["bytes_per_level0_px"] * level0_px
+                                         if pyr_tr and args.storage == "f16" else None),
+                             "bytes_per_level0_px": pyramid_bytes_per_px(args.storage, LEVELS),
                              "ms_per_step": pyr_ms},
         "clocks": clk,
         "gpu_launches": (LEVELS + 5) * args.steps,
