@@ -106,12 +106,15 @@ __device__ __forceinline__ int copy_rows(const uint8_t *plane, int64_t pitch, in
     const int b0 = (xa * esz) & ~15, b1 = (xb + 1) * esz;
     const int nc = (b1 - b0 + 15) >> 4;  // chunks per row
     const int total = rows * nc;
+    // k / nc by a multiply-high with ceil(2^32 / nc), exact for k < 2^32 / nc
+    // (nc = 1, whose multiplier does not fit 32 bits, is the identity)
+    const unsigned magic = nc > 1 ? 0xFFFFFFFFu / (unsigned)nc + 1u : 0u;
     for (int k = lane; k < total; k += 32) {
-        const int r = k / nc, c = k - r * nc;
+        const int r = nc > 1 ? (int)__umulhi((unsigned)k, magic) : k, c = k - r * nc;
         const uint8_t *row = plane + (int64_t)clampi(y0 + r, 0, h - 1) * pitch + b0;
         cp_async16(dst + r * rw + 4 * c, row + 16 * c);
     }
-    return b0 / esz;
+    return b0 >> (__ffs(esz) - 1);  // esz is 1, 2, 4 or 8
 }
 
 // Texel x (level column, clamped) of a raw row whose first byte is level
@@ -348,6 +351,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     const float dd = sxx - syy;
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
     const float lmin = det / lmax;
+    const float inv_det = 1.0f / det;
     if (!(lmin >= tau_n) || !(lmin > 0.f)) return OMT_PT_LOST_EIG;
     // Prefetch the next template (next level, or the next point's top level)
     // into the other buffer while this level iterates.
@@ -396,8 +400,8 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         combine8(S, bx, by, sx, sy);
         warp_sum2(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
-        const float ex = (syy * bbx - sxy * bby) / det;
-        const float ey = (sxx * bby - sxy * bbx) / det;
+        const float ex = (syy * bbx - sxy * bby) * inv_det;
+        const float ey = (sxx * bby - sxy * bbx) * inv_det;
         nux += ex;
         nuy += ey;
         ++k;
