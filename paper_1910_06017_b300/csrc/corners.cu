@@ -269,7 +269,7 @@ constexpr int GCAP = 8192;   // cells of the accepted-point grid in shared memor
 // greedy pass to usually finish in one chunk (it rejects some candidates).
 __host__ __device__ __forceinline__ int chunk_keys(int maxc) {
     int t = 64;
-    while (t < 4 * maxc && t < SCAP) t <<= 1;
+    while (t < 2 * maxc && t < SCAP) t <<= 1;
     return t;
 }
 
@@ -484,12 +484,12 @@ __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
     for (int y = ylo + warp; y <= yhi; y += SNT / 32) {
         const uint32_t *row = a.rmap + (int64_t)y * a.w;
         // four loads in flight per lane
-        for (int x = xlo + lane; x <= xhi; x += 128) {
-            uint32_t v[4];
+        for (int x = xlo + lane; x <= xhi; x += 256) {
+            uint32_t v[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = x + 32 * q <= xhi ? __ldg(row + x + 32 * q) : 0u;
+            for (int q = 0; q < 8; ++q) v[q] = x + 32 * q <= xhi ? __ldg(row + x + 32 * q) : 0u;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 8; ++q) {
                 const uint32_t R = v[q] & R_MASK;
                 m = max(m, R);
                 if ((v[q] & MAX_FLAG) && R > 0) {
