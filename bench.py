@@ -282,21 +282,15 @@ def run_omt(args, ws, rank, local):
     px0 = sum(sp.size[0] * sp.size[1] for sp in streams)
     pyr_bytes = px0 * pyramid_bytes_per_px(args.storage, LEVELS)
 
-    # ---- end to end: pinned frames H2D, step, boxes D2H, every step
-    outs_h = [torch.empty((len(sp.boxes), 4), dtype=torch.float32).pin_memory() for sp in streams]
+    # ---- end to end: every step's frames copied from page-locked host memory
+    # and its boxes read back, through BatchTracker.run_pipelined (copies on a
+    # second stream overlap the previous step's compute)
     torch.cuda.synchronize()
-    h2d = d2h = 0
+    par0 = B.cur
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        par = B.cur
-        for s in range(len(streams)):
-            B.slot(s).copy_(fr_h[s][par], non_blocking=True)
-            h2d += fr_h[s][par].numel()
-        B.step()
-        for s, sp in enumerate(streams):
-            outs_h[s].copy_(B.boxes_out[s][:len(sp.boxes)], non_blocking=True)
-            d2h += outs_h[s].numel() * 4
-        torch.cuda.synchronize()
+    h2d, d2h = B.run_pipelined(lambda k: [fr_h[s][(par0 + k) & 1] for s in range(len(streams))],
+                               args.steps)
+    torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
 
     ms_step = ms_total / args.steps

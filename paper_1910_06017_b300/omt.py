@@ -333,10 +333,10 @@ class BatchTracker:
     (frame t, frame t+1), two frame slots (the step with parity p reads
     frame t+1 from slot p), its input and output boxes, point buffers and
     corner scratch.  Two tables (one per
-    pyramid parity) are packed once into page-locked host memory; a step
-    copies the right one to the device and runs 4 + levels launches for all
-    streams.  With graph=True each parity's step is captured once in a CUDA
-    graph and replayed (the table copy is a node of the graph).
+    pyramid parity) are packed into page-locked host memory and copied to two
+    device tables by pack(); a step runs 4 + levels launches for all streams
+    over the table of its parity.  capture() records each parity's step in a
+    CUDA graph, which step() then replays.
     """
 
     def __init__(self, sizes, params: Params, max_boxes, max_corners=None, device="cuda",
@@ -358,13 +358,18 @@ class BatchTracker:
         self.pyr, self.frame, self.boxes, self.boxes_out = [], [], [], []
         self.pts, self.pts_out, self.status, self.iters, self.offsets, self.nvalid = [], [], [], [], [], []
         self.scratch, self.nboxes = [], [0] * n
+        # every stream's output boxes in one buffer, so one copy reads them all
+        nbs = [max(1, nb) for nb in max_boxes]
+        self.boxes_out_all = torch.zeros((sum(nbs), 4), dtype=torch.float32, device=dev)
+        self.boxes_out_at = [sum(nbs[:i]) for i in range(n)]
         for (w, h), nb, mc in zip(sizes, max_boxes, max_corners):
             self.pyr.append([Pyramid(w, h, params.levels, params.storage, dev),
                              Pyramid(w, h, params.levels, params.storage, dev)])
             self.frame.append([torch.zeros((h, w), dtype=torch.uint8, device=dev) for _ in range(2)])
             cap = max(1, nb * mc)
             self.boxes.append(torch.zeros((max(1, nb), 4), dtype=torch.float32, device=dev))
-            self.boxes_out.append(torch.zeros((max(1, nb), 4), dtype=torch.float32, device=dev))
+            at = self.boxes_out_at[len(self.boxes_out)]
+            self.boxes_out.append(self.boxes_out_all[at:at + max(1, nb)])
             self.pts.append(torch.zeros((cap, 2), dtype=torch.float32, device=dev))
             self.pts_out.append(torch.zeros((cap, 2), dtype=torch.float32, device=dev))
             self.status.append(torch.zeros(cap, dtype=torch.uint8, device=dev))
@@ -376,7 +381,7 @@ class BatchTracker:
                                             device=dev))
         nbytes = batch_table_bytes(self.caps)
         self.tables = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
-        self.dev_table = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.dev_tables = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
         self.cur = 0
         self.graphs = [None, None]
 
@@ -410,10 +415,23 @@ class BatchTracker:
         self.nboxes[s] = nb
         self.graphs = [None, None]
 
-    def pack(self):
+    def pack(self, stream=None):
+        """Pack both parities' tables and copy them to the device (on
+        `stream`, ordered after the steps already queued there)."""
         for parity in range(2):
             batch_pack([self._desc(s, parity) for s in range(len(self.sizes))], self.params,
                        self.caps, self.tables[parity])
+            batch_upload(self.tables[parity], self.caps, self.dev_tables[parity], stream)
+
+    def _phases(self, parity, events=None, stream=None):
+        events = events or {}
+        for phase in (PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES):
+            ev = events.get(phase)
+            if ev:
+                ev[0].record()
+            batch_phase(self.dev_tables[parity], self.caps, self.params, phase, stream)
+            if ev:
+                ev[1].record()
 
     def prime(self, s: int, frame, stream=None):
         """Build stream s's frame-t pyramid from a u8 device frame."""
@@ -424,10 +442,11 @@ class BatchTracker:
         import torch
         self.pack()
         self.graphs = [None, None]
+        torch.cuda.synchronize()
         for parity in range(2):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, capture_error_mode="relaxed"):
-                batch_step(self.tables[parity], self.caps, self.params, self.dev_table)
+                self._phases(parity)
             self.graphs[parity] = g
 
     def step(self, stream=None):
@@ -435,22 +454,73 @@ class BatchTracker:
         if self.graphs[self.cur] is not None:
             self.graphs[self.cur].replay()
         else:
-            batch_step(self.tables[self.cur], self.caps, self.params, self.dev_table, stream)
+            self._phases(self.cur, stream=stream)
         self.cur = 1 - self.cur
 
     def step_phases(self, events=None, stream=None):
-        """The step as upload + four phases.  events: optional dict phase ->
+        """The step as its four phases, eagerly.  events: optional dict phase ->
         (start, end) CUDA events recorded around that phase."""
-        events = events or {}
-        batch_upload(self.tables[self.cur], self.caps, self.dev_table, stream)
-        for phase in (PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES):
-            ev = events.get(phase)
-            if ev:
-                ev[0].record()
-            batch_phase(self.dev_table, self.caps, self.params, phase, stream)
-            if ev:
-                ev[1].record()
+        self._phases(self.cur, events, stream)
         self.cur = 1 - self.cur
 
     def count(self, s: int) -> int:
         return int(self.offsets[s][self.nboxes[s]].item())
+
+    def run_pipelined(self, frames_for, steps: int, consume=None, copy_stream=None):
+        """Run `steps` steps with host frames in and boxes out, overlapping
+        the copies with compute.
+
+        frames_for(k) returns step k's frames (page-locked host u8 tensors,
+        one per stream, frame t+1 of every stream).  They are copied on a
+        copy stream while step k-1 computes; the compute stream waits for
+        them.  Step k reads the frame slots of its parity, which step k-2
+        read last, so the copy for step k waits for step k-2.  After each
+        step its output boxes are copied to page-locked host memory (two
+        alternating buffers) and consume(k, boxes) runs on the host once
+        they have arrived, while step k+1 computes.  Returns the bytes
+        copied host to device and device to host."""
+        import torch
+        comp = torch.cuda.current_stream(self.device)
+        up = copy_stream or torch.cuda.Stream(device=self.device)
+        n = len(self.sizes)
+        outs_all = [torch.empty(self.boxes_out_all.shape, dtype=torch.float32).pin_memory()
+                    for _ in range(2)]
+        at = self.boxes_out_at
+        outs = [[o[at[s]:at[s] + max(1, self.nboxes[s])] for s in range(n)] for o in outs_all]
+        h2d = d2h = 0
+        done_step = [None] * steps
+        done_d2h = [None] * steps
+
+        def upload(k, parity):
+            nonlocal h2d
+            with torch.cuda.stream(up):
+                if k >= 2:
+                    up.wait_event(done_step[k - 2])
+                for s, f in enumerate(frames_for(k)):
+                    self.frame[s][parity].copy_(f, non_blocking=True)
+                    h2d += f.numel() * f.element_size()
+                e = torch.cuda.Event()
+                e.record(up)
+            return e
+
+        ready = upload(0, self.cur)
+        for k in range(steps):
+            comp.wait_event(ready)
+            self.step()
+            done_step[k] = torch.cuda.Event()
+            done_step[k].record(comp)
+            outs_all[k & 1].copy_(self.boxes_out_all, non_blocking=True)
+            d2h += self.boxes_out_all.numel() * 4
+            done_d2h[k] = torch.cuda.Event()
+            done_d2h[k].record(comp)
+            if k + 1 < steps:
+                ready = upload(k + 1, self.cur)
+            if k >= 1:
+                done_d2h[k - 1].synchronize()
+                if consume:
+                    consume(k - 1, [outs[(k - 1) & 1][s][:self.nboxes[s]] for s in range(n)])
+        if steps:
+            done_d2h[steps - 1].synchronize()
+            if consume:
+                consume(steps - 1, [outs[(steps - 1) & 1][s][:self.nboxes[s]] for s in range(n)])
+        return h2d, d2h

@@ -204,3 +204,31 @@ def test_membership_below_capacity(omt):
     got = _batch_results(B, sps)
     for a, b in zip(plain, got):
         _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
+
+
+def test_run_pipelined_equals_stepwise(omt):
+    """Frames uploaded on a copy stream while the previous step computes give
+    the same boxes as copying each step's frames before it runs."""
+    sps = _streams(3, first=80)
+    params = omt.default_params(levels=4, win=21, min_dist=3.0, storage=1,
+                                max_corners=max(_cap(sp) for sp in sps))
+    boxes_list = [sp.boxes for sp in sps]
+    A = _make_batch(omt, sps, params, boxes_list)
+    P = _make_batch(omt, sps, params, boxes_list)
+    fr = [(torch.from_numpy(sp.frame1).pin_memory(), torch.from_numpy(sp.frame0).pin_memory())
+          for sp in sps]
+    want = []
+    for k in range(5):
+        for s in range(len(sps)):
+            A.slot(s).copy_(fr[s][k & 1])
+        A.step()
+        torch.cuda.synchronize()
+        want.append([A.boxes_out[s][:len(sps[s].boxes)].cpu().numpy() for s in range(len(sps))])
+    got = {}
+    h2d, d2h = P.run_pipelined(lambda k: [fr[s][k & 1] for s in range(len(sps))], 5,
+                               consume=lambda k, b: got.__setitem__(k, [x.numpy().copy() for x in b]))
+    assert sorted(got) == list(range(5))
+    for k in range(5):
+        for s in range(len(sps)):
+            np.testing.assert_array_equal(got[k][s], want[k][s])
+    assert h2d == 5 * sum(sp.size[0] * sp.size[1] for sp in sps)
