@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import math
 import time
 from typing import Callable, Dict, List, Optional
@@ -121,6 +122,18 @@ class Scheduler:
         self.frame_ok = frame_ok or (lambda sid, idx: True)
 
     def run(self, specs: List[StreamSpec], deadline: float, sleep: Callable[[float], None] = None) -> Stats:
+        # The cyclic garbage collector can pause the loop for tens of
+        # milliseconds; it is held off for the run (the loop's objects are
+        # freed by reference counting) and restored afterwards.
+        gc_was = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(specs, deadline, sleep)
+        finally:
+            if gc_was:
+                gc.enable()
+
+    def _run(self, specs, deadline, sleep):
         sleep = sleep or (lambda dt: None)
         t0 = self.clock()
         now = lambda: self.clock() - t0
@@ -217,11 +230,15 @@ class GpuBackend(Backend):
     frame slots, boxes, points, corner scratch); one omt_batch_step per
     step over the slots of that step, from a ring of page-locked tables.
 
-    The frames of a step are copied to the device on a copy stream, so the
-    copies of step k overlap the compute of step k-1; the compute stream
-    waits for them.  A stream's frame slots alternate, so the slot a copy
-    overwrites was last read by step k-2 or earlier, which the copy stream
-    waits for."""
+    Everything a step needs from the host (its frames, its table, fresh
+    detection boxes) is copied on a copy stream, so the copies of step k
+    overlap the compute of step k-1; the compute stream waits for them and
+    then only launches kernels.  A stream's frame slots and box buffers
+    alternate with its pyramid parity (a step reads boxes[p] and writes
+    boxes[1-p], the next step's input), so nothing is copied between steps,
+    and the slot a copy overwrites was last read by step k-2 or earlier,
+    which the copy stream waits for.  A detection goes to a staging buffer
+    that the step reads in place of its input boxes."""
 
     def __init__(self, params, caps_streams: int, caps_boxes: int, max_w: int, max_h: int,
                  max_corners: int, frames_host: Dict[int, list], det_boxes: Dict[int, np.ndarray],
@@ -259,7 +276,7 @@ class GpuBackend(Backend):
         cap = nb * mc
         return (2 * omt.pyramid_bytes(w, h, p.levels, p.storage) + 2 * w * h +
                 omt.corner_scratch_bytes(w, h, nb, mc) + cap * (8 + 8 + 1 + p.levels) +
-                (nb + 1) * 4 + nb * (16 + 16 + 4))
+                (nb + 1) * 4 + nb * (16 + 16 + 16 + 4))
 
     def alloc(self, spec: StreamSpec):
         torch, omt = self.torch, self.omt
@@ -274,6 +291,8 @@ class GpuBackend(Backend):
                 frame=[torch.empty((h, w), dtype=torch.uint8, device=dev) for _ in range(2)],
                 boxes=torch.zeros((nb, 4), dtype=torch.float32, device=dev),
                 boxes_out=torch.zeros((nb, 4), dtype=torch.float32, device=dev),
+                det=[torch.zeros((nb, 4), dtype=torch.float32, device=dev) for _ in range(2)],
+                use_det=False,
                 pts=torch.empty((cap, 2), dtype=torch.float32, device=dev),
                 pts_out=torch.empty((cap, 2), dtype=torch.float32, device=dev),
                 status=torch.empty(cap, dtype=torch.uint8, device=dev),
@@ -292,20 +311,25 @@ class GpuBackend(Backend):
     def free(self, slot) -> None:
         slot.clear()
 
-    def _desc(self, slot, parity):
+    def _desc(self, slot, parity, use_det=False):
+        """Batch entry of a slot for a step of pyramid parity `parity`: it
+        reads boxes[parity] (or the detection staged for that parity) and
+        writes boxes[1 - parity]."""
         omt = self.omt
         d = omt.BatchStream()
         f = slot["frame"][parity]
+        pair = (slot["boxes"], slot["boxes_out"])
         d.frame, d.frame_pitch = f.data_ptr(), f.stride(0)
         d.prev = slot["pyr"][parity].desc
         d.next = slot["pyr"][1 - parity].desc
-        d.boxes, d.nboxes = slot["boxes"].data_ptr(), slot["spec"].n_boxes
+        d.boxes = (slot["det"][parity] if use_det else pair[parity]).data_ptr()
+        d.nboxes = slot["spec"].n_boxes
         d.max_corners = slot["spec"].max_corners
         d.scratch, d.scratch_bytes = slot["scratch"].data_ptr(), slot["scratch"].numel()
         d.pts, d.pts_out = slot["pts"].data_ptr(), slot["pts_out"].data_ptr()
         d.status, d.iters = slot["status"].data_ptr(), None
         d.offsets = slot["offsets"].data_ptr()
-        d.boxes_out, d.nvalid = slot["boxes_out"].data_ptr(), slot["nvalid"].data_ptr()
+        d.boxes_out, d.nvalid = pair[1 - parity].data_ptr(), slot["nvalid"].data_ptr()
         return d
 
     def submit(self, items):
@@ -314,49 +338,61 @@ class GpuBackend(Backend):
         self.ring_next = (k + 1) % len(self.tables)
         if self.ring_events[k] is not None:
             self.ring_events[k].synchronize()   # the step that read this table is done
-        descs, host = [], {}
+        # host side first: which frames prime a stream, which step, the table
+        primes, steps = [], []
+        for slot, idx in items:
+            spec = slot["spec"]
+            if not slot["primed"]:
+                primes.append((slot, idx))
+            else:
+                steps.append((slot, idx, idx % spec.refresh == 0))   # a detection replaces the boxes
+        descs = [self._desc(slot, slot["cur"], det or slot["use_det"]) for slot, idx, det in steps]
+        if descs:
+            omt.batch_pack(descs, self.params, self.caps, self.tables[k])
         with torch.cuda.stream(self.copy_stream):
             if len(self.step_events) == 2:
                 self.copy_stream.wait_event(self.step_events[0])
-            for slot, idx in items:
-                spec = slot["spec"]
-                fh = self.frames_host[spec.sid][idx % len(self.frames_host[spec.sid])]
-                # a stream's first frame goes to slot 1, so that its first
-                # step's copy (slot 0) has no earlier reader
-                slot["frame"][1 if not slot["primed"] else slot["cur"]].copy_(fh, non_blocking=True)
+            for slot, idx in primes:
+                # a stream's first frame goes to slot 1 (its first step's
+                # frame goes to slot 0, which then has no earlier reader);
+                # its first boxes are the detection, staged for parity 0
+                sid = slot["spec"].sid
+                slot["frame"][1].copy_(self.frames_host[sid][idx % len(self.frames_host[sid])],
+                                       non_blocking=True)
+                slot["det"][0].copy_(self._det_boxes(sid), non_blocking=True)
+            for slot, idx, det in steps:
+                sid = slot["spec"].sid
+                slot["frame"][slot["cur"]].copy_(self.frames_host[sid][idx % len(self.frames_host[sid])],
+                                                 non_blocking=True)
+                if det:
+                    slot["det"][slot["cur"]].copy_(self._det_boxes(sid), non_blocking=True)
+            if descs:
+                omt.batch_upload(self.tables[k], self.caps, self.dev_tables[k], self.copy_stream)
             copied = torch.cuda.Event()
             copied.record(self.copy_stream)
+        host = {}
         with torch.cuda.stream(self.stream):
             self.stream.wait_event(copied)
-            for slot, idx in items:
-                spec = slot["spec"]
-                if not slot["primed"]:
-                    # a stream's first frame only builds its pyramid
-                    omt.build_pyramid(slot["frame"][1], slot["pyr"][0], self.params)
-                    slot["boxes"].copy_(self._det_boxes(spec.sid), non_blocking=True)
-                    slot["primed"] = True
-                    continue
-                par = slot["cur"]
-                if idx % spec.refresh == 0:   # a detection replaces the tracked boxes
-                    slot["boxes"].copy_(self._det_boxes(spec.sid), non_blocking=True)
-                descs.append(self._desc(slot, par))
-                host[id(slot)] = slot
+            for slot, idx in primes:
+                omt.build_pyramid(slot["frame"][1], slot["pyr"][0], self.params)
+                slot["primed"] = True
+                slot["use_det"] = True
             if descs:
-                omt.batch_pack(descs, self.params, self.caps, self.tables[k])
-                omt.batch_step(self.tables[k], self.caps, self.params, self.dev_tables[k], self.stream)
-                for slot in host.values():
-                    # the tracked boxes are the next step's input; flip the pyramids
-                    slot["boxes"].copy_(slot["boxes_out"], non_blocking=True)
-                    slot["cur"] = 1 - slot["cur"]
+                for phase in (omt.PHASE_PYRAMID, omt.PHASE_CORNERS, omt.PHASE_LK, omt.PHASE_BOXES):
+                    omt.batch_phase(self.dev_tables[k], self.caps, self.params, phase, self.stream)
+            for slot, idx, det in steps:
+                par = slot["cur"]
                 if self.keep_boxes:
-                    for key, slot in host.items():
-                        host[key] = slot["boxes_host"][k]
-                        host[key].copy_(slot["boxes_out"], non_blocking=True)
+                    out = (slot["boxes"], slot["boxes_out"])[1 - par]
+                    host[id(slot)] = slot["boxes_host"][k]
+                    host[id(slot)].copy_(out, non_blocking=True)
+                slot["cur"] = 1 - par
+                slot["use_det"] = False
             ev = torch.cuda.Event()
             ev.record(self.stream)
         self.ring_events[k] = ev
         self.step_events.append(ev)
-        return _Handle(ev, list(items), host if self.keep_boxes else {})
+        return _Handle(ev, list(items), host)
 
     def done(self, handle) -> bool:
         return handle.event.query()
