@@ -18,7 +18,7 @@ and per-step latency percentiles.  `e2e` copies every step's frames host ->
 device from pinned memory and reads every box back.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl omt|reference]
-                    [--storage f16|f32] [--streams S] [--no-graph]
+                    [--storage f16|f32] [--streams S] [--no-graph] [--no-tune]
 """
 from __future__ import annotations
 
@@ -234,6 +234,9 @@ def run_omt(args, ws, rank, local):
     for _ in range(args.warmup):
         B.step()
     torch.cuda.synchronize()
+    # launch shape of the LK kernel, timed on this batch (results do not depend on it)
+    tune_ms = B.autotune() if args.tune else {}
+    torch.cuda.synchronize()
     if args.graph:
         B.capture()
         for _ in range(2):
@@ -326,7 +329,10 @@ def run_omt(args, ws, rank, local):
             "latency_ms_p99": float(np.percentile(step_ms, 99)),
             "plain_f32_points_per_s": plain_value, "plain_f32_ms_per_step": plain_ms,
             "speedup_vs_plain_f32": value / plain_value,
-            "l2": "working set > L2 (126 MB): no flush", "parallelism": f"replicas x{ws}"},
+            "l2": "working set > L2 (126 MB): no flush", "parallelism": f"replicas x{ws}",
+            "lk_launch": {"warps_per_cta": B.caps.lk_warps or 4, "queue_chunk": B.caps.lk_chunk or 1,
+                          "autotuned": bool(tune_ms),
+                          "candidates_ms": {f"{w}x{c}": round(t, 4) for (w, c), t in tune_ms.items()}}},
         "e2e": {"value": ok_total / e2e_s, "unit": "points/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "roofline": {"kernel": "lk_batch_kernel", "bound": "alu", "achieved": achieved,
@@ -400,6 +406,8 @@ def main():
     ap.add_argument("--storage", default="f16", choices=["f32", "f16"])
     ap.add_argument("--streams", type=int, default=32)
     ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="keep the default LK launch shape instead of autotuning it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()

@@ -288,6 +288,14 @@ typedef struct omt_batch_caps {
     int32_t max_boxes;    /* boxes summed over the streams, >= 0      */
     int32_t max_w, max_h; /* largest frame                            */
     int32_t max_corners;  /* largest per-box cap, <= OMT_MAX_CORNERS   */
+    /* Launch shape of the batched LK kernel, 0 = the library default: warps
+     * per CTA (1..8; default 4), CTAs per SM (0..32; 0 = as many as fit),
+     * points a warp takes at a time from the launch's work queue (1..16;
+     * default 1).  No result depends on them (each point is computed by one
+     * warp in a fixed order), so a tuner may pick any; an autotuner in the
+     * Python binding times the candidates on the caller's own batch. */
+    int32_t lk_warps, lk_ctas_per_sm, lk_chunk;
+    int32_t reserved;     /* 0 */
 } omt_batch_caps;
 
 /* Bytes of a packed table (host) and of its device copy (0 on bad caps). */

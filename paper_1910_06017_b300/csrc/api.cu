@@ -181,7 +181,9 @@ namespace {
 bool caps_ok(const omt_batch_caps *c) {
     return c && c->max_streams >= 1 && c->max_streams <= OMT_BATCH_MAX_STREAMS &&
            c->max_boxes >= 0 && c->max_w >= 1 && c->max_h >= 1 && c->max_w <= (1 << 16) &&
-           c->max_h <= (1 << 16) && c->max_corners >= 0 && c->max_corners <= OMT_MAX_CORNERS;
+           c->max_h <= (1 << 16) && c->max_corners >= 0 && c->max_corners <= OMT_MAX_CORNERS &&
+           c->lk_warps >= 0 && c->lk_warps <= 8 && c->lk_ctas_per_sm >= 0 &&
+           c->lk_ctas_per_sm <= 32 && c->lk_chunk >= 0 && c->lk_chunk <= 16 && c->reserved == 0;
 }
 
 void fill_levels(const omt_pyramid &p, LevelView *out) {
@@ -323,7 +325,8 @@ int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt
                 dt, caps->max_streams, caps->max_streams * response_tiles(caps->max_w, caps->max_h),
                 caps->max_boxes, caps->max_corners, s));
         case OMT_PHASE_LK:
-            return from_cuda(launch_lk_batch(dt, prm->storage, prm->win, s));
+            return from_cuda(launch_lk_batch(dt, prm->storage, prm->win, caps->lk_warps,
+                                             caps->lk_ctas_per_sm, caps->lk_chunk, s));
         case OMT_PHASE_BOXES:
             return from_cuda(launch_update_boxes_batch(dt, caps->max_boxes, s));
         default:

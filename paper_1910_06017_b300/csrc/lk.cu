@@ -21,8 +21,9 @@
 namespace omt {
 namespace {
 
-constexpr int LK_NT = 128;
+constexpr int LK_NT = 128;               // CTA size of the plain launch (and the batched default)
 constexpr int LK_WARPS = LK_NT / 32;
+constexpr int LK_MAX_NT = 256;           // largest CTA a launch may use
 
 struct LKArgs {
     LevelView P[OMT_MAX_LEVELS];
@@ -493,12 +494,12 @@ __device__ __forceinline__ unsigned *warp_words() {
 }
 
 template <int ST, int WIN>
-constexpr size_t stage_bytes() {
-    return (size_t)LK_WARPS * Dims<ST, WIN>::WORDS * 4;
+constexpr size_t stage_bytes(int warps = LK_WARPS) {
+    return (size_t)warps * Dims<ST, WIN>::WORDS * 4;
 }
 
 template <int ST, int WIN>
-__global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArgs a) {
+__global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ LKArgs a) {
     unsigned *W = warp_words<ST, WIN>();
     int n = a.n_max;
     if (a.n_dev) {
@@ -520,14 +521,20 @@ __global__ void __launch_bounds__(LK_NT) lk_kernel(const __grid_constant__ LKArg
 
 // All points of all streams of a batch: the per-stream counts come from the
 // CSR offsets written by the corner step; each CTA forms their prefix in
-// shared memory and its warps stride over the concatenated index space.
+// shared memory.  Warps take `chunk` consecutive points at a time from a
+// work queue (a counter in the table's header, zeroed before the launch), so
+// points of uneven cost balance over the warps; a warp takes its next chunk
+// before the last point of the current one, whose finest level then
+// prefetches the next point's top-level template.
 template <int ST, int WIN>
-__global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
+__global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *table, int chunk) {
     __shared__ int32_t pre[OMT_BATCH_MAX_STREAMS + 1];
     unsigned *W = warp_words<ST, WIN>();
     const BatchView t(table);
     const BatchHeader &h = t.hdr();
+    unsigned *queue = const_cast<unsigned *>(&h.work[0]);
     const int ns = h.nstreams;
+    const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         int acc = 0;
         pre[0] = 0;
@@ -539,23 +546,31 @@ __global__ void __launch_bounds__(LK_NT) lk_batch_kernel(const uint8_t *table) {
     }
     __syncthreads();
     const int total = pre[ns];
-    const int nwarps = gridDim.x * LK_WARPS;
+    auto take = [&]() -> int {
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(queue, (unsigned)chunk);
+        b = __shfl_sync(FULL_MASK, b, 0);
+        return b < (unsigned)total ? (int)b : total;
+    };
     Prefetch pf;
     pf.valid = false;
-    int g = blockIdx.x * LK_WARPS + (threadIdx.x >> 5);
+    int g = take(), end = g + chunk;
     int s = g < total ? find_segment(pre, ns, g) : 0;
-    for (; g < total; g += nwarps) {
+    while (g < total) {
+        int gn = g + 1;
+        if (gn >= end || gn >= total) {
+            gn = take();
+            end = gn + chunk;
+        }
         const StreamEntry &e = t.stream(s);
         const int i = g - pre[s];
-        // the warp's next point, whose top-level template is prefetched
-        // while this point's finest level iterates
-        const int gn = g + nwarps;
         const bool has_next = gn < total;
         const int sn = has_next ? find_segment(pre, ns, gn) : s;
         const StreamEntry &en = t.stream(sn);
         const float2 un = has_next ? en.pts[gn - pre[sn]] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
                           e.pts_out, e.status, e.iters, W, pf, has_next, un, en.P);
+        g = gn;
         s = sn;
     }
     cp_async_wait<0>();
@@ -581,23 +596,39 @@ cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
 }
 
 template <int ST, int WIN>
-cudaError_t launch_batch_win(const uint8_t *table, int sms, cudaStream_t s) {
-    const size_t smem = stage_bytes<ST, WIN>();
-    cudaError_t e = cudaFuncSetAttribute(lk_batch_kernel<ST, WIN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_batch_win(const uint8_t *table, int sms, int warps, int ctas_per_sm, int chunk,
+                             cudaStream_t s) {
+    // no more warps per CTA than their staging areas fit in shared memory
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int fit = optin / (int)stage_bytes<ST, WIN>(1);
+    if (warps > fit) warps = fit > 0 ? fit : 1;
+    const size_t smem = stage_bytes<ST, WIN>(warps);
+    e = cudaFuncSetAttribute(lk_batch_kernel<ST, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lk_batch_kernel<ST, WIN>, LK_NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lk_batch_kernel<ST, WIN>, 32 * warps,
+                                                      smem);
+    if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    lk_batch_kernel<ST, WIN><<<sms * per_sm, LK_NT, smem, s>>>(table);
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    // the work queue starts at 0 for every launch
+    e = cudaMemsetAsync(const_cast<uint8_t *>(table) + offsetof(BatchHeader, work), 0,
+                        sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    lk_batch_kernel<ST, WIN><<<sms * per_sm, 32 * warps, smem, s>>>(table, chunk);
     return cudaGetLastError();
 }
 
 template <int ST>
-cudaError_t launch_batch_st(const uint8_t *table, int win, int sms, cudaStream_t s) {
+cudaError_t launch_batch_st(const uint8_t *table, int win, int sms, int warps, int ctas_per_sm,
+                            int chunk, cudaStream_t s) {
     switch (win) {
 #define OMT_LK_CASE(W) \
-    case W: return launch_batch_win<ST, W>(table, sms, s);
+    case W: return launch_batch_win<ST, W>(table, sms, warps, ctas_per_sm, chunk, s);
         OMT_LK_CASE(3) OMT_LK_CASE(5) OMT_LK_CASE(7) OMT_LK_CASE(9) OMT_LK_CASE(11)
         OMT_LK_CASE(13) OMT_LK_CASE(15) OMT_LK_CASE(17) OMT_LK_CASE(19) OMT_LK_CASE(21)
         OMT_LK_CASE(23) OMT_LK_CASE(25) OMT_LK_CASE(27) OMT_LK_CASE(29) OMT_LK_CASE(31)
@@ -608,12 +639,16 @@ cudaError_t launch_batch_st(const uint8_t *table, int win, int sms, cudaStream_t
 
 }  // namespace
 
-cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, cudaStream_t s) {
+cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
+                            int ctas_per_sm, int chunk, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (storage == OMT_F32) return launch_batch_st<OMT_F32>(table, win, sms, s);
-    return launch_batch_st<OMT_F16>(table, win, sms, s);
+    if (warps <= 0) warps = LK_WARPS;
+    if (chunk <= 0) chunk = 1;
+    if (storage == OMT_F32)
+        return launch_batch_st<OMT_F32>(table, win, sms, warps, ctas_per_sm, chunk, s);
+    return launch_batch_st<OMT_F16>(table, win, sms, warps, ctas_per_sm, chunk, s);
 }
 
 cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const float2 *pts,

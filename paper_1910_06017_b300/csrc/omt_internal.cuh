@@ -118,6 +118,9 @@ struct BatchHeader {
     float eps2, tau_n;
     int64_t md2c;
     int64_t bytes;  // size of the packed table
+    // work[0]: next point of the batched LK launch's work queue (reset to 0
+    // on the device before each LK launch; the only field a kernel writes)
+    uint32_t work[4];
 };
 
 __host__ __device__ inline size_t batch_entries_offset(int max_streams) {
@@ -179,7 +182,10 @@ cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, 
                                  cudaStream_t s);
 cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_resp_tiles,
                                  int max_boxes, int max_corners, cudaStream_t s);
-cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, cudaStream_t s);
+// LK over every point of a batch: warps per CTA, CTAs per SM and work-queue
+// chunk as in omt_batch_caps (0 = default).
+cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
+                            int ctas_per_sm, int chunk, cudaStream_t s);
 cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, cudaStream_t s);
 
 cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const float2 *pts,

@@ -76,7 +76,9 @@ class BatchStream(Structure):
 
 class BatchCaps(Structure):
     _fields_ = [("max_streams", c_int32), ("max_boxes", c_int32), ("max_w", c_int32),
-                ("max_h", c_int32), ("max_corners", c_int32)]
+                ("max_h", c_int32), ("max_corners", c_int32),
+                ("lk_warps", c_int32), ("lk_ctas_per_sm", c_int32), ("lk_chunk", c_int32),
+                ("reserved", c_int32)]
 
 
 _lib = None
@@ -462,6 +464,42 @@ class BatchTracker:
         (start, end) CUDA events recorded around that phase."""
         self._phases(self.cur, events, stream)
         self.cur = 1 - self.cur
+
+    # Launch shapes the autotuner tries: (warps per CTA, points per work-queue take).
+    TUNE_CANDIDATES = tuple((w, c) for w in (2, 4, 8) for c in (1, 2, 4))
+
+    def autotune(self, candidates=None, reps: int = 3, stream=None) -> dict:
+        """Pick the batched LK launch shape that is fastest on this batch.
+
+        Runs the pyramid and corner phases of the next step once (so the
+        points exist), then times the LK phase for every candidate (warps
+        per CTA, work-queue chunk) with CUDA events, the median of `reps`
+        runs after one untimed run, and keeps the fastest in self.caps.  No
+        result depends on the shape.  The state afterwards is as before the
+        call except for the rebuilt frame t+1 pyramids; captured graphs are
+        dropped (capture again).  Returns {(warps, chunk): ms}."""
+        import torch
+        cands = list(candidates or self.TUNE_CANDIDATES)
+        par = self.cur
+        for phase in (PHASE_PYRAMID, PHASE_CORNERS):
+            batch_phase(self.dev_tables[par], self.caps, self.params, phase, stream)
+        times = {}
+        for w, c in cands:
+            self.caps.lk_warps, self.caps.lk_chunk = int(w), int(c)
+            batch_phase(self.dev_tables[par], self.caps, self.params, PHASE_LK, stream)
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                batch_phase(self.dev_tables[par], self.caps, self.params, PHASE_LK, stream)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            times[(int(w), int(c))] = sorted(ms)[len(ms) // 2]
+        best = min(times, key=times.get)
+        self.caps.lk_warps, self.caps.lk_chunk = best
+        self.graphs = [None, None]
+        return times
 
     def count(self, s: int) -> int:
         return int(self.offsets[s][self.nboxes[s]].item())

@@ -201,4 +201,12 @@ def test_batch_pack_validation():
         assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n) == code, what
     arr = (omt.BatchStream * 5)(*([ok[0]] * 5))
     assert lib.omt_batch_pack(arr, 5, ctypes.byref(prm), ctypes.byref(caps), tp, n) == omt.EINVAL
+    # launch-shape fields out of range are rejected
+    for field, value in [("lk_warps", 9), ("lk_warps", -1), ("lk_ctas_per_sm", 33), ("lk_chunk", 17),
+                         ("reserved", 1)]:
+        bad_caps = omt.BatchCaps(4, 100, 1920, 1080, 64)
+        setattr(bad_caps, field, value)
+        assert omt.batch_table_bytes(bad_caps) == 0, field
+    good = omt.BatchCaps(4, 100, 1920, 1080, 64, 8, 2, 16)
+    assert omt.batch_table_bytes(good) == n
     assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n - 1) == omt.ENOMEM

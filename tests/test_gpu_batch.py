@@ -232,3 +232,32 @@ def test_run_pipelined_equals_stepwise(omt):
         for s in range(len(sps)):
             np.testing.assert_array_equal(got[k][s], want[k][s])
     assert h2d == 5 * sum(sp.size[0] * sp.size[1] for sp in sps)
+
+
+def test_lk_launch_shape_does_not_change_results(omt):
+    """Every launch shape the tuner may pick (warps per CTA, work-queue
+    chunk) gives the same points, statuses, iterations and boxes bit for bit,
+    and autotune keeps one of its candidates."""
+    sps = _streams(4, first=100)
+    params = omt.default_params(levels=4, win=21, min_dist=3.0, storage=1,
+                                max_corners=max(_cap(sp) for sp in sps))
+    boxes_list = [sp.boxes for sp in sps]
+    ref = None
+    for warps, chunk in [(4, 1), (2, 4), (8, 2), (1, 16)]:
+        B = _make_batch(omt, sps, params, boxes_list)
+        B.caps.lk_warps, B.caps.lk_chunk = warps, chunk
+        B.step()
+        torch.cuda.synchronize()
+        got = _batch_results(B, sps)
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                _assert_same(a, b, pyramids=False)
+    B = _make_batch(omt, sps, params, boxes_list)
+    times = B.autotune(reps=2)
+    assert (B.caps.lk_warps, B.caps.lk_chunk) in times and min(times.values()) > 0
+    B.step()
+    torch.cuda.synchronize()
+    for a, b in zip(ref, _batch_results(B, sps)):
+        _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
