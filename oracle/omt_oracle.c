@@ -333,6 +333,15 @@ static void lk_point(const level_t *P, const level_t *J, int levels, int win, in
         if (iters) iters[L] = 0;
         if (mineig) mineig[L] = NAN;
     }
+    /* Input domain (a reading: the method assumes points on the frame): a
+     * point with a non-finite coordinate or one beyond 2^24 px is lost
+     * outside the frame without being tracked. */
+    if (!(fabs(ux) <= 16777216.0) || !(fabs(uy) <= 16777216.0)) {
+        *vx = ux;
+        *vy = uy;
+        *status = ORC_LOST_OOB;
+        return;
+    }
     for (int L = levels - 1; L >= 0; --L) {
         const level_t *pl = &P[L], *jl = &J[L];
         double sc = ldexp(1.0, -L);

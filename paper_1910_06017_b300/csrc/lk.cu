@@ -428,6 +428,20 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
     int st = OMT_PT_OK;
     bool nonconv = false;
     unsigned long long itp = 0ull;  // iterations per level, 8 bits each
+    // A point with a non-finite coordinate or one beyond 2^24 px is lost
+    // outside the frame without a window (its integer positions would not
+    // fit); such a next point gets no prefetch either.
+    if (!(fabsf(u.x) <= 16777216.f) || !(fabsf(u.y) <= 16777216.f)) {
+        cp_async_wait<0>();
+        pf.valid = false;
+        if (lane == 0) {
+            out[i] = u;
+            status[i] = (uint8_t)OMT_PT_LOST_OOB;
+        }
+        if (iters && lane < levels) iters[(int64_t)i * levels + lane] = 0;
+        return;
+    }
+    has_next = has_next && fabsf(u_next.x) <= 16777216.f && fabsf(u_next.y) <= 16777216.f;
 
     for (int L = levels - 1; L >= 0; --L) {
         const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact

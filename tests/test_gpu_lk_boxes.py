@@ -214,6 +214,25 @@ def test_lk_empty_and_device_count(omt, oracle):
     assert (s[:2].cpu().numpy() & OK).all()
 
 
+def test_lk_points_outside_the_input_domain(omt, oracle):
+    # non-finite coordinates and coordinates beyond 2^24 px come back
+    # LOST_OOB and unchanged, as in the oracle; the other points are unaffected
+    p = synth.sd_pair()
+    far = np.array([[np.nan, 10.0], [10.0, np.inf], [3.0e9, 5.0], [-3.0e9, -7.0e9], [1.0e20, 1.0],
+                    [-16777300.0, 5.0]], np.float32)
+    good = np.array([[100.0, 100.0], [200.0, 300.0]], np.float32)
+    pts = np.concatenate([good[:1], far, good[1:]])
+    out, st, it = gpu_lk(omt, p.frame0, p.frame1, pts)
+    assert st[1:7].tolist() == [LOST_OOB] * 6
+    assert np.all(it[1:7] == 0)
+    np.testing.assert_array_equal(out[3:7], far[2:6])
+    ref_out, ref_st, _ = gpu_lk(omt, p.frame0, p.frame1, good)
+    np.testing.assert_array_equal(out[[0, 7]], ref_out)
+    np.testing.assert_array_equal(st[[0, 7]], ref_st)
+    o_out, o_st, _, _ = oracle_lk(oracle, p.frame0, p.frame1, far)
+    assert o_st.tolist() == [LOST_OOB] * 6
+
+
 def test_lk_batch_independence(omt):
     # a point's result does not depend on the launch shape or batch mates
     p = synth.sd_pair()

@@ -181,6 +181,21 @@ def test_out_of_image_is_lost(oracle):
     assert np.abs(out[1] - [276.0, 256.0]).max() <= 1e-9
 
 
+def test_points_outside_the_input_domain_are_lost(oracle):
+    # a non-finite coordinate or one beyond 2^24 px is lost outside the frame
+    # without tracking; the output is the input
+    w = h = 64
+    f0 = synth.render_bilinear(w, h)
+    P0, P1 = oracle.Pyramid(f0, 3), oracle.Pyramid(f0, 3)
+    pts = np.array([[np.nan, 10.0], [10.0, np.inf], [3.0e9, 5.0], [-16777300.0, 5.0], [30.0, 30.0]],
+                   np.float32)
+    out, st, it, me = oracle.lk_track(P0, P1, pts, win=7, diagnostics=True)
+    assert st[:4].tolist() == [LOST_OOB] * 4
+    assert np.all(it[:4] == 0)
+    np.testing.assert_array_equal(out[2:4], pts[2:4].astype(np.float64))
+    assert st[4] == OK and np.abs(out[4] - [30.0, 30.0]).max() == 0.0
+
+
 def test_status_is_consistent_near_borders(oracle):
     # Whatever the tracker does near the frame edge, an OK point ends inside
     # [0, W-1] x [0, H-1] and a lost point reports its input position.
