@@ -75,6 +75,18 @@ def dram_traffic(kernel: str):
     return rec
 
 
+def combine_ranks(times, counts, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's times (max)
+    and the points of all ranks (sum), over the initialised process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(list(counts), dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return [float(x) for x in t], [float(x) for x in c]
+
+
 def dist_env():
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -299,13 +311,8 @@ def run_omt(args, ws, rank, local):
     ms_step = ms_total / args.steps
     ok_total, plain_ok_total = float(ok_pts), float(plain_ok)
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step, e2e_s, plain_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, e2e_s, plain_ms = float(t[0]), float(t[1]), float(t[2])
-        c = torch.tensor([ok_pts, plain_ok], dtype=torch.float64, device=dev)
-        dist.all_reduce(c)
-        ok_total, plain_ok_total = float(c[0]), float(c[1])
+        (ms_step, e2e_s, plain_ms), (ok_total, plain_ok_total) = combine_ranks(
+            [ms_step, e2e_s, plain_ms], [ok_pts, plain_ok], dev)
     value = ok_total / (ms_step * 1e-3)
     plain_value = plain_ok_total / (plain_ms * 1e-3)
     pk, pk_src = peaks()
