@@ -28,43 +28,22 @@ constexpr uint32_t R_MASK = 0x3FFFFFFFu;
 constexpr uint32_t MAX_FLAG = 1u << 30;
 
 // ----------------------------------------------------------- exact isqrt
-// floor(sqrt(D)) for D < 2^62: a correctly rounded FP32 estimate, one Newton
-// correction of its residual, then at most a few unit steps.
-__device__ __forceinline__ uint32_t isqrt_u64(uint64_t D) {
-    if (D == 0) return 0;
-    const float f = __ull2float_rn(D);
-    int64_t s = (int64_t)sqrtf(f);
-    if (s > 0) {
-        const int64_t r = (int64_t)D - s * s;
-        s += (int64_t)floorf(__fdividef((float)r, 2.0f * (float)s));
-    }
-    if (s < 0) s = 0;
-#pragma unroll 1
-    for (int k = 0; k < 8 && (uint64_t)s * (uint64_t)s > D; ++k) --s;
-#pragma unroll 1
-    for (int k = 0; k < 8 && (uint64_t)(s + 1) * (uint64_t)(s + 1) <= D; ++k) ++s;
-    return (uint32_t)s;
-}
-
-// The same for D < 2^58 given f, any float within a relative 2^-20 of D:
-// the hardware square-root approximation of f is within a relative 2^-19
-// of sqrt(D), i.e. within 2^10 for sqrt(D) < 2^29, and one Newton step on
-// the exact residual brings it within one unit (the unit steps finish).
+// floor(sqrt(D)) for D < 2^58 given f, any float within a relative 2^-20 of
+// D, without branches: the hardware square-root approximation of f is within a
+// relative 2^-19 of sqrt(D) (within 2^10 for sqrt(D) < 2^29), and one
+// Newton step on the exact residual leaves it within one unit of
+// floor(sqrt(D)) (the step's overshoot e^2 / (2 s) stays below 0.1, its
+// float rounding below 1e-3), which one comparison each way settles.
 __device__ __forceinline__ uint32_t isqrt_est(uint64_t D, float f) {
-    if (D == 0) return 0;
     float sf;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(sf) : "f"(f));
-    int64_t s = (int64_t)sf;
-    if (s > 0) {
-        const int64_t r = (int64_t)D - s * s;
-        s += (int64_t)floorf(__fdividef((float)r, 2.0f * (float)s));
-    }
-    if (s < 0) s = 0;
-#pragma unroll 1
-    for (int k = 0; k < 8 && (uint64_t)s * (uint64_t)s > D; ++k) --s;
-#pragma unroll 1
-    for (int k = 0; k < 8 && (uint64_t)(s + 1) * (uint64_t)(s + 1) <= D; ++k) ++s;
-    return (uint32_t)s;
+    int s = (int)sf;  // < 2^30
+    const int64_t r = (int64_t)D - (int64_t)((uint64_t)(uint32_t)s * (uint32_t)s);
+    s += s > 0 ? (int)floorf(__fdividef((float)r, 2.0f * (float)s)) : 0;
+    s = s < 0 ? 0 : s;
+    const uint64_t sq = (uint64_t)(uint32_t)s * (uint32_t)s;
+    const uint64_t sq1 = sq + 2 * (uint64_t)(uint32_t)s + 1;  // (s + 1)^2
+    return (uint32_t)(s - (sq > D ? 1 : 0) + (sq1 <= D ? 1 : 0));
 }
 
 // ------------------------------------------------------ response map kernel
@@ -127,25 +106,42 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
     int vm = 0, v0 = 0, vp = 0, lm = 0, l0 = 0, lp = 0, qm = 0, q0 = 0, qp = 0;
     int Ha2 = 0, Hb2 = 0, Hc2 = 0, Ha1 = 0, Hb1 = 0, Hc1 = 0;  // 3x1 sums, rows g-2, g-1
     uint32_t Rp = 0, M2 = 0, M1 = 0;  // R of row g-2; 3-column maxima of rows g-3, g-2
+    // texels of row g+1 loaded one step early for sliding steps (nv, ne)
+    int nv = 0, ne = 0;
+    bool have_next = false;
 #pragma unroll 1
     for (int s = 0; s < RH + 4; ++s) {
         const int g = oy - 2 + s;  // gradient row of this step
         if (s > 0 && g >= 2 && g <= a.h - 2) {
-            // the previous step read rows g-2 .. g: slide and read row g+1
+            // the previous step read rows g-2 .. g: slide and take row g+1
             vm = v0;
             v0 = vp;
             lm = l0;
             l0 = lp;
             qm = q0;
             q0 = qp;
-            const uint8_t *r2 = a.img + (int64_t)(g + 1) * a.pitch;
-            vp = __ldg(r2 + cx);
-            const int ep = edge ? (int)__ldg(r2 + ex) : 0;
+            int ep;
+            if (have_next) {
+                vp = nv;
+                ep = ne;
+            } else {
+                const uint8_t *r2 = a.img + (int64_t)(g + 1) * a.pitch;
+                vp = __ldg(r2 + cx);
+                ep = edge ? (int)__ldg(r2 + ex) : 0;
+            }
+            // the next step slides too: load its row g+2 now
+            have_next = s + 1 < RH + 4 && g + 1 <= a.h - 2;
+            if (have_next) {
+                const uint8_t *r3 = a.img + (int64_t)(g + 2) * a.pitch;
+                nv = __ldg(r3 + cx);
+                ne = edge ? (int)__ldg(r3 + ex) : 0;
+            }
             lp = __shfl_up_sync(FULL_MASK, vp, 1);
             qp = __shfl_down_sync(FULL_MASK, vp, 1);
             if (lane == 0) lp = ep;
             else if (lane == 31) qp = ep;
         } else {
+            have_next = false;
             const int py = reflect101(g, a.h);
             const uint8_t *r0 = a.img + (int64_t)reflect101(py - 1, a.h) * a.pitch;
             const uint8_t *r1 = a.img + (int64_t)py * a.pitch;
@@ -188,16 +184,15 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
         const int Hb0 = gxl * gyl + gx * gy + gxr * gyr;
         const int Hc0 = gyl * gyl + gy * gy + gyr * gyr;
 
-        // response of row g - 1 (its tensor is complete: rows g-2 .. g)
-        uint32_t Rn = 0;
-        if (inx && g - 1 >= 0 && g - 1 < a.h) {
-            const int ta = Ha2 + Ha1 + Ha0, tb = Hb2 + Hb1 + Hb0, tc = Hc2 + Hc1 + Hc0;
-            const int amc = ta - tc;  // |a - c| < 2^28
-            const uint64_t D = (uint64_t)((int64_t)amc * amc) + 4ull * (uint64_t)((int64_t)tb * tb);
-            const float fa = (float)amc, fb = (float)tb;
-            const float f = fmaf(fa, fa, 4.0f * fb * fb);
-            Rn = (uint32_t)((int64_t)ta + tc - (int64_t)isqrt_est(D, f));
-        }
+        // response of row g - 1 (its tensor is complete: rows g-2 .. g);
+        // computed by every lane, kept where the pixel is in the frame
+        const int ta = Ha2 + Ha1 + Ha0, tb = Hb2 + Hb1 + Hb0, tc = Hc2 + Hc1 + Hc0;
+        const int amc = ta - tc;  // |a - c| < 2^28
+        const uint64_t D = (uint64_t)((int64_t)amc * amc) + 4ull * (uint64_t)((int64_t)tb * tb);
+        const float fa = (float)amc, fb = (float)tb;
+        const float f = fmaf(fa, fa, 4.0f * fb * fb);
+        const uint32_t Rv = (uint32_t)((int64_t)ta + tc - (int64_t)isqrt_est(D, f));
+        const uint32_t Rn = inx && g - 1 >= 0 && g - 1 < a.h ? Rv : 0u;
         const uint32_t Mn =
             max(Rn, max(__shfl_up_sync(FULL_MASK, Rn, 1), __shfl_down_sync(FULL_MASK, Rn, 1)));
 
