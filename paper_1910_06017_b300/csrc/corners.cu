@@ -292,10 +292,30 @@ __device__ __forceinline__ uint64_t make_key(uint32_t R, uint32_t idx) {
     return ((uint64_t)R << 32) | (uint64_t)(0xFFFFFFFFu - idx);
 }
 
-// Ascending bitonic sort of keys[0..N), N a power of two <= SCAP.
+// One compare-exchange of the bitonic network for the key at index i, held
+// by this lane, against index i ^ j in the same warp (j < 32).
+__device__ __forceinline__ uint64_t bitonic_step(uint64_t x, int i, int j, int k) {
+    const uint64_t y = __shfl_xor_sync(FULL_MASK, x, j);
+    const bool up = (i & k) == 0, lower = (i & j) == 0;
+    const bool take_min = lower == up;
+    return take_min ? (x < y ? x : y) : (x < y ? y : x);
+}
+
+// Ascending bitonic sort of keys[0..N), N a power of two, 32 <= N <= SCAP.
+// Exchanges between indices less than 32 apart run inside a warp with
+// shuffles (one key per lane); the wider ones through shared memory with a
+// barrier per stage.
 __device__ void bitonic_sort(uint64_t *keys, int N) {
-    for (int k = 2; k <= N; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b = warp * 32; b < N; b += SNT) {
+        uint64_t x = keys[b + lane];
+        for (int k = 2; k <= 32; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) x = bitonic_step(x, b + lane, j, k);
+        keys[b + lane] = x;
+    }
+    __syncthreads();
+    for (int k = 64; k <= N; k <<= 1) {
+        for (int j = k >> 1; j >= 32; j >>= 1) {
             for (int i = threadIdx.x; i < N; i += SNT) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
@@ -309,6 +329,12 @@ __device__ void bitonic_sort(uint64_t *keys, int N) {
             }
             __syncthreads();
         }
+        for (int b = warp * 32; b < N; b += SNT) {
+            uint64_t x = keys[b + lane];
+            for (int j = 16; j > 0; j >>= 1) x = bitonic_step(x, b + lane, j, k);
+            keys[b + lane] = x;
+        }
+        __syncthreads();
     }
 }
 
@@ -529,7 +555,7 @@ __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
             }
             __syncthreads();
             const int n = s_count;  // = min(rem, T)
-            int N = 1;
+            int N = 32;
             while (N < n) N <<= 1;
             for (int i = n + tid; i < N; i += SNT) chunk[i] = 0ull;
             __syncthreads();
@@ -608,7 +634,7 @@ __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
             }
             __syncthreads();
             const int n = min(s_count, SCAP);
-            int N = 1;
+            int N = 32;
             while (N < n) N <<= 1;
             for (int i = n + tid; i < N; i += SNT) keys[i] = 0ull;
             __syncthreads();
