@@ -408,8 +408,10 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
     if (lane == 0) *s_nacc = nacc;
 }
 
-// Find the k-th largest of the keys in [lo_bound, hi) among keys[0..n)
-// (1 <= k <= their count; keys are unique), by an 8-bit MSD radix select;
+// A lower bound `lo` such that exactly k of the keys in [lo_bound, hi)
+// among keys[0..n) are >= lo (1 <= k <= their count; keys are unique): the
+// k-th largest key, or the prefix of a digit bin that holds exactly the
+// keys still needed (then no lower digit matters).  8-bit MSD radix select;
 // whole CTA, result in the return value of every thread.
 __device__ uint64_t kth_largest(const uint64_t *keys, int n, uint64_t lo_bound, uint64_t hi, int k,
                                 unsigned *hist, int *s_sel, int *s_k) {
@@ -445,7 +447,8 @@ __device__ uint64_t kth_largest(const uint64_t *keys, int n, uint64_t lo_bound, 
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     if (cum + c[q] >= (unsigned)k) {
-                        *s_sel = 255 - 8 * tid - q;
+                        // a bin holding exactly the keys still needed ends the search
+                        *s_sel = (255 - 8 * tid - q) | (cum + c[q] == (unsigned)k ? 256 : 0);
                         *s_k = k - (int)cum;
                         break;
                     }
@@ -454,10 +457,12 @@ __device__ uint64_t kth_largest(const uint64_t *keys, int n, uint64_t lo_bound, 
             }
         }
         __syncthreads();
-        prefix |= (uint64_t)*s_sel << shift;
+        const int sel = *s_sel;
+        prefix |= (uint64_t)(sel & 255) << shift;
         pmask |= 0xFFull << shift;
         k = *s_k;
         __syncthreads();
+        if (sel & 256) break;
     }
     return prefix;
 }
