@@ -589,6 +589,7 @@ def main(argv=None):
     ap.add_argument("--capacity", action="store_true",
                     help="search the highest rate scale served with p99 latency within --p99-ms")
     ap.add_argument("--p99-ms", type=float, default=40.0)
+    ap.add_argument("--bisect", type=int, default=3, help="geometric bisection steps of the capacity search")
     args = ap.parse_args(argv)
     specs, frames, det = build_workload(args.streams, args.duration, fps_scale=args.rate_scale)
     storage = omt.F16 if (args.storage == "f16" and not args.plain) else omt.F32
@@ -600,7 +601,7 @@ def main(argv=None):
     path = "plain FP32 per frame" if args.plain else f"batched {args.storage}"
     if args.capacity:
         best, probes = capacity(args.streams, params, args.plain, budget, p99_ms=args.p99_ms,
-                                duration=args.duration)
+                                duration=args.duration, bisect=args.bisect)
         out = dict(best or {})
         out.update({"streams": args.streams, "budget_gb": args.budget_gb, "path": path,
                     "p99_bound_ms": args.p99_ms, "capacity_stream_fps":
