@@ -261,3 +261,22 @@ def test_lk_launch_shape_does_not_change_results(omt):
     torch.cuda.synchronize()
     for a, b in zip(ref, _batch_results(B, sps)):
         _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_batch_equals_plain_win31_five_levels(omt, storage):
+    """The largest window (31x31) and five levels, as for 3840x2160 frames,
+    through the batched path (whose launch clamps the warps per CTA to the
+    shared memory their staging areas need) equal the plain calls."""
+    sps = _streams(3, first=120)
+    boxes_list = [sp.boxes for sp in sps]
+    params = omt.default_params(levels=5, win=31, min_dist=3.0, storage=storage,
+                                max_corners=max(_cap(sp) for sp in sps))
+    plain = _run_plain(omt, sps, params, boxes_list)
+    for warps in (4, 8):
+        B = _make_batch(omt, sps, params, boxes_list)
+        B.caps.lk_warps, B.caps.lk_chunk = warps, 2
+        B.step()
+        torch.cuda.synchronize()
+        for a, b in zip(plain, _batch_results(B, sps)):
+            _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
