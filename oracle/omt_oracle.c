@@ -502,3 +502,122 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ================================================================ matching
+ * Matching and update phases (Section V-A): the predicted scene objects S_t
+ * are matched against the detections D_t by a globally optimal assignment
+ * (the Hungarian method, Kuhn 1955) of the IoU score; unmatched scene
+ * objects are flagged lost, unmatched detections become new scene objects.
+ * Boxes are half-open (x0, y0, x1, y1) floats. */
+
+/* IoU of one pair in double, in this order: areas from clipped extents, the
+ * intersection's extents clipped at 0, union = (area_a + area_b) - inter,
+ * iou = inter / union (0 when the union is empty). */
+static double orc_iou1(const float *a, const float *b)
+{
+    const double aw = fmax((double)a[2] - (double)a[0], 0.0), ah = fmax((double)a[3] - (double)a[1], 0.0);
+    const double bw = fmax((double)b[2] - (double)b[0], 0.0), bh = fmax((double)b[3] - (double)b[1], 0.0);
+    const double iw = fmax(fmin((double)a[2], (double)b[2]) - fmax((double)a[0], (double)b[0]), 0.0);
+    const double ih = fmax(fmin((double)a[3], (double)b[3]) - fmax((double)a[1], (double)b[1]), 0.0);
+    const double inter = iw * ih;
+    const double uni = (aw * ah + bw * bh) - inter;
+    return uni > 0.0 ? inter / uni : 0.0;
+}
+
+void orc_iou_matrix(const float *a, int na, const float *b, int nb, double *out)
+{
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) out[(size_t)i * nb + j] = orc_iou1(a + 4 * i, b + 4 * j);
+}
+
+/* Optimal assignment on an n x n cost matrix (minimum sum), by the
+ * Hungarian method with row and column potentials: rows enter one at a
+ * time, and each is joined by a shortest augmenting path over reduced costs
+ * (Dijkstra over the columns).  p[j] = row of column j (1-based, 0 free). */
+static void orc_hungarian(const double *c, int n, int *col_of_row)
+{
+    double *u = calloc(n + 1, sizeof(double)), *v = calloc(n + 1, sizeof(double));
+    double *minv = malloc((n + 1) * sizeof(double));
+    int *p = calloc(n + 1, sizeof(int)), *way = calloc(n + 1, sizeof(int));
+    char *used = malloc(n + 1);
+    for (int i = 1; i <= n; ++i) {
+        p[0] = i;
+        int j0 = 0;
+        for (int j = 0; j <= n; ++j) { minv[j] = INFINITY; used[j] = 0; }
+        do {
+            used[j0] = 1;
+            const int i0 = p[j0];
+            double delta = INFINITY;
+            int j1 = 0;
+            for (int j = 1; j <= n; ++j) {
+                if (used[j]) continue;
+                const double cur = c[(size_t)(i0 - 1) * n + (j - 1)] - u[i0] - v[j];
+                if (cur < minv[j]) { minv[j] = cur; way[j] = j0; }
+                if (minv[j] < delta) { delta = minv[j]; j1 = j; }
+            }
+            for (int j = 0; j <= n; ++j) {
+                if (used[j]) { u[p[j]] += delta; v[j] -= delta; }
+                else minv[j] -= delta;
+            }
+            j0 = j1;
+        } while (p[j0] != 0);
+        do {
+            const int j1 = way[j0];
+            p[j0] = p[j1];
+            j0 = j1;
+        } while (j0);
+    }
+    for (int j = 1; j <= n; ++j)
+        if (p[j]) col_of_row[p[j] - 1] = j - 1;
+    free(u); free(v); free(minv); free(p); free(way); free(used);
+}
+
+/* Maximum-total-IoU assignment of the active rows of an na x nb IoU matrix
+ * (the matrix is padded to a square with zero scores); a row and column
+ * count as matched only when their assigned IoU exceeds iou_min.
+ * match_a[i] = column or -1, match_b[j] = row or -1. */
+void orc_assign(const double *iou, int na, int nb, const uint8_t *active, double iou_min,
+                int32_t *match_a, int32_t *match_b)
+{
+    for (int i = 0; i < na; ++i) match_a[i] = -1;
+    for (int j = 0; j < nb; ++j) match_b[j] = -1;
+    const int n = na > nb ? na : nb;
+    if (n == 0) return;
+    double *c = calloc((size_t)n * n, sizeof(double));
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j)
+            c[(size_t)i * n + j] = (active && !active[i]) ? 0.0 : -iou[(size_t)i * nb + j];
+    int *col = malloc(n * sizeof(int));
+    orc_hungarian(c, n, col);
+    for (int i = 0; i < na; ++i) {
+        const int j = col[i];
+        if (j < nb && (!active || active[i]) && iou[(size_t)i * nb + j] > iou_min) {
+            match_a[i] = j;
+            match_b[j] = i;
+        }
+    }
+    free(c);
+    free(col);
+}
+
+/* Update phase: matched scene objects take their detection's box; active
+ * unmatched ones are flagged lost (kept, excluded from further
+ * processing); unmatched detections are appended as new scene objects.
+ * Outputs hold up to ns + nd entries; *n_out is the new count. */
+void orc_update_tracks(const float *boxes_s, const uint8_t *active_s, int ns, const float *boxes_d,
+                       int nd, const int32_t *match_s, const int32_t *match_d, float *boxes_out,
+                       uint8_t *active_out, int32_t *n_out)
+{
+    int n = 0;
+    for (int i = 0; i < ns; ++i, ++n) {
+        const float *src = (active_s[i] && match_s[i] >= 0) ? boxes_d + 4 * match_s[i] : boxes_s + 4 * i;
+        for (int k = 0; k < 4; ++k) boxes_out[4 * n + k] = src[k];
+        active_out[n] = (uint8_t)(active_s[i] && match_s[i] >= 0);
+    }
+    for (int j = 0; j < nd; ++j) {
+        if (match_d[j] >= 0) continue;
+        for (int k = 0; k < 4; ++k) boxes_out[4 * n + k] = boxes_d[4 * j + k];
+        active_out[n++] = 1;
+    }
+    *n_out = n;
+}

@@ -178,5 +178,42 @@ def update_boxes(boxes, offsets, pts, pts_out, status, aggregator: int = 0):
     return out, nv
 
 
+def iou_matrix(a, b):
+    """IoU of every pair (na, nb) float64, Section V-A matching score."""
+    A = np.ascontiguousarray(a, dtype=np.float32).reshape(-1, 4)
+    B = np.ascontiguousarray(b, dtype=np.float32).reshape(-1, 4)
+    out = np.zeros((A.shape[0], B.shape[0]), np.float64)
+    lib().orc_iou_matrix(_p(A, c_float), A.shape[0], _p(B, c_float), B.shape[0], _p(out, c_double))
+    return out
+
+
+def assign(iou, active=None, iou_min: float = 0.0):
+    """Maximum-total-IoU assignment (Hungarian method): (match_a, match_b)."""
+    m = np.ascontiguousarray(iou, dtype=np.float64)
+    na, nb = m.shape
+    act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+    ma = np.zeros(na, np.int32)
+    mb = np.zeros(nb, np.int32)
+    lib().orc_assign(_p(m, c_double), na, nb, None if act is None else _p(act, c_uint8),
+                     ctypes.c_double(iou_min), _p(ma, c_int32), _p(mb, c_int32))
+    return ma, mb
+
+
+def update_tracks(boxes_s, active_s, boxes_d, match_s, match_d):
+    """Update phase: (boxes (n, 4) float32, active (n,) uint8)."""
+    S = np.ascontiguousarray(boxes_s, dtype=np.float32).reshape(-1, 4)
+    D = np.ascontiguousarray(boxes_d, dtype=np.float32).reshape(-1, 4)
+    a = np.ascontiguousarray(active_s, dtype=np.uint8)
+    ms = np.ascontiguousarray(match_s, dtype=np.int32)
+    md = np.ascontiguousarray(match_d, dtype=np.int32)
+    out = np.zeros((S.shape[0] + D.shape[0], 4), np.float32)
+    act = np.zeros(S.shape[0] + D.shape[0], np.uint8)
+    n = np.zeros(1, np.int32)
+    lib().orc_update_tracks(_p(S, c_float), _p(a, c_uint8), S.shape[0], _p(D, c_float), D.shape[0],
+                            _p(ms, c_int32), _p(md, c_int32), _p(out, c_float), _p(act, c_uint8),
+                            _p(n, c_int32))
+    return out[:n[0]], act[:n[0]]
+
+
 def max_threads() -> int:
     return lib().orc_max_threads()
