@@ -338,6 +338,47 @@ int omt_batch_upload(const void *table, const omt_batch_caps *caps, void *dev_ta
 int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt_params *prm,
                     int32_t phase, void *stream);
 
+/* ------------------------------------------------- matching and update
+ * Section V-A, matching phase: the predicted scene objects S_t are matched
+ * against the detections D_t by a globally optimal assignment (the
+ * Hungarian method, Kuhn 1955) with the IoU as score; update phase: scene
+ * objects that find no match are flagged lost (kept, excluded from further
+ * processing), detections that find none become new scene objects.  Boxes
+ * are half-open (x0, y0, x1, y1) floats. */
+
+/* IoU of every pair (a[i], b[j]) into iou[i * nb + j] (device, row-major
+ * doubles): area = max(x1 - x0, 0) * max(y1 - y0, 0) per box, the
+ * intersection's extents clipped at 0, union = (area_a + area_b) - inter,
+ * IoU = inter / union (0 for an empty union), every operation a single
+ * rounded FP64 operation (no fused multiply-add), so the matrix is the
+ * same bit for bit on any IEEE machine that keeps that order.  a, b: device,
+ * 16-byte aligned; na, nb >= 0 (0 is a no-op).  Asynchronous on `stream`. */
+int omt_iou_matrix(const float *a, int32_t na, const float *b, int32_t nb, double *iou,
+                   void *stream);
+
+/* Host only.  Host workspace bytes for omt_assign on an na x nb matrix. */
+size_t omt_assign_workspace_bytes(int32_t na, int32_t nb);
+
+/* Host only.  Maximum-total-IoU assignment of the rows of `iou` (host,
+ * na x nb doubles) to its columns; rows with active[i] == 0 take no part
+ * (active may be NULL: all rows).  The matrix is padded to a square with
+ * zero scores; a row and a column count as matched only when their
+ * assigned IoU exceeds iou_min.  match_a[i] = column or -1, match_b[j] = row
+ * or -1.  Among several optimal assignments the one returned is a fixed
+ * function of the matrix.  OMT_ENOMEM if workspace_bytes is short. */
+int omt_assign(const double *iou, int32_t na, int32_t nb, const uint8_t *active, double iou_min,
+               void *workspace, size_t workspace_bytes, int32_t *match_a, int32_t *match_b);
+
+/* Host only.  Update phase: entry i < ns of the output is scene object i,
+ * with its detection's box and active = 1 when it is active and matched,
+ * else its own box and active = 0 (lost, or lost before); the detections
+ * that match no scene object follow, active.  boxes_out holds ns + nd
+ * boxes, active_out ns + nd flags; *n_out receives the new count. */
+int omt_update_tracks(const float *boxes_s, const uint8_t *active_s, int32_t ns,
+                      const float *boxes_d, int32_t nd, const int32_t *match_s,
+                      const int32_t *match_d, float *boxes_out, uint8_t *active_out,
+                      int32_t *n_out);
+
 /* ---------------------------------------------------------------- misc */
 
 const char *omt_error_string(int32_t code);

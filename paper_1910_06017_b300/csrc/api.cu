@@ -348,6 +348,53 @@ int omt_batch_step(const void *table, const omt_batch_caps *caps, const omt_para
     return rc;
 }
 
+int omt_iou_matrix(const float *a, int32_t na, const float *b, int32_t nb, double *iou,
+                   void *stream) {
+    if (na < 0 || nb < 0) return OMT_EINVAL;
+    if (na == 0 || nb == 0) return OMT_OK;
+    if (!a || !b || !iou || !aligned(a, 16) || !aligned(b, 16) || !aligned(iou, 8)) return OMT_EINVAL;
+    return from_cuda(launch_iou_matrix(a, na, b, nb, iou, (cudaStream_t)stream));
+}
+
+size_t omt_assign_workspace_bytes(int32_t na, int32_t nb) {
+    if (na < 0 || nb < 0) return 0;
+    return assign_workspace(na > nb ? na : nb);
+}
+
+int omt_assign(const double *iou, int32_t na, int32_t nb, const uint8_t *active, double iou_min,
+               void *workspace, size_t workspace_bytes, int32_t *match_a, int32_t *match_b) {
+    if (na < 0 || nb < 0 || iou_min != iou_min) return OMT_EINVAL;
+    if ((na > 0 && !match_a) || (nb > 0 && !match_b) || (na > 0 && nb > 0 && !iou))
+        return OMT_EINVAL;
+    if (workspace_bytes < omt_assign_workspace_bytes(na, nb) || (!workspace && (na || nb)))
+        return OMT_ENOMEM;
+    assign_max_iou(iou, na, nb, active, iou_min, workspace, match_a, match_b);
+    return OMT_OK;
+}
+
+int omt_update_tracks(const float *boxes_s, const uint8_t *active_s, int32_t ns,
+                      const float *boxes_d, int32_t nd, const int32_t *match_s,
+                      const int32_t *match_d, float *boxes_out, uint8_t *active_out,
+                      int32_t *n_out) {
+    if (ns < 0 || nd < 0 || !n_out) return OMT_EINVAL;
+    if ((ns > 0 && (!boxes_s || !active_s || !match_s)) || (nd > 0 && (!boxes_d || !match_d)) ||
+        (ns + nd > 0 && (!boxes_out || !active_out)))
+        return OMT_EINVAL;
+    int n = 0;
+    for (int i = 0; i < ns; ++i, ++n) {
+        const bool keep = active_s[i] && match_s[i] >= 0 && match_s[i] < nd;
+        memcpy(boxes_out + 4 * n, keep ? boxes_d + 4 * match_s[i] : boxes_s + 4 * i, 4 * sizeof(float));
+        active_out[n] = keep ? 1 : 0;
+    }
+    for (int j = 0; j < nd; ++j) {
+        if (match_d[j] >= 0) continue;
+        memcpy(boxes_out + 4 * n, boxes_d + 4 * j, 4 * sizeof(float));
+        active_out[n++] = 1;
+    }
+    *n_out = n;
+    return OMT_OK;
+}
+
 const char *omt_error_string(int32_t code) {
     switch (code) {
         case OMT_OK: return "success";

@@ -176,7 +176,12 @@ size_t select_scratch_bytes(int w, int h, int nboxes, int max_corners);
 
 // Batched forms: every launch covers all streams of the table in `table`
 // (device memory); grids depend only on the capacities.
-int pyramid_tiles(int w, int h);   // K1 tiles of a level of this size
+int pyramid_tiles(int w, int h);
+cudaError_t launch_iou_matrix(const float *a, int na, const float *b, int nb, double *out,
+                              cudaStream_t s);
+size_t assign_workspace(int n);   // host bytes of the assignment's work arrays
+void assign_max_iou(const double *iou, int na, int nb, const uint8_t *active, double iou_min,
+                    void *ws, int32_t *match_a, int32_t *match_b);   // K1 tiles of a level of this size
 int response_tiles(int w, int h);  // K2 response tiles of a frame of this size
 cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
                                  cudaStream_t s);

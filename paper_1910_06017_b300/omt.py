@@ -25,7 +25,8 @@ EXPORTED = [
     "omt_build_pyramid", "omt_corner_response", "omt_corner_scratch_bytes",
     "omt_select_corners", "omt_lk_track", "omt_update_boxes", "omt_error_string",
     "omt_version", "omt_select_corners_static", "omt_batch_table_bytes", "omt_batch_pack",
-    "omt_batch_step", "omt_batch_upload", "omt_batch_phase",
+    "omt_batch_step", "omt_batch_upload", "omt_batch_phase", "omt_iou_matrix",
+    "omt_assign_workspace_bytes", "omt_assign", "omt_update_tracks",
 ]
 PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES = 0, 1, 2, 3
 BATCH_MAX_STREAMS = 256
@@ -111,6 +112,13 @@ def lib():
         L.omt_error_string.argtypes = [c_int32]
         L.omt_error_string.restype = ctypes.c_char_p
         L.omt_version.restype = c_int32
+        L.omt_iou_matrix.argtypes = [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p]
+        L.omt_assign_workspace_bytes.argtypes = [c_int32, c_int32]
+        L.omt_assign_workspace_bytes.restype = c_size_t
+        L.omt_assign.argtypes = [c_void_p, c_int32, c_int32, c_void_p, ctypes.c_double, c_void_p,
+                                 c_size_t, c_void_p, c_void_p]
+        L.omt_update_tracks.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p]
         L.omt_batch_table_bytes.argtypes = [POINTER(BatchCaps)]
         L.omt_batch_table_bytes.restype = c_size_t
         L.omt_batch_pack.argtypes = [POINTER(BatchStream), c_int32, POINTER(Params),
@@ -252,6 +260,64 @@ def update_boxes(boxes, offsets, pts, pts_out, status, params: Params, boxes_out
     _check(lib().omt_update_boxes(_ptr(boxes), _ptr(offsets), _ptr(pts), _ptr(pts_out),
                                   _ptr(status), nb, ctypes.byref(params), _ptr(boxes_out),
                                   _ptr(nvalid), _stream(stream)), "omt_update_boxes")
+
+
+def iou_matrix(a, b, out, stream=None):
+    """IoU of every pair of boxes (device tensors (na, 4), (nb, 4) float32)
+    into out (device (na, nb) float64), Section V-A matching score."""
+    _check(lib().omt_iou_matrix(_ptr(a), a.shape[0], _ptr(b), b.shape[0], _ptr(out), _stream(stream)),
+           "omt_iou_matrix")
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
+
+
+def assign(iou, active=None, iou_min: float = 0.0):
+    """Maximum-total-IoU assignment (host numpy (na, nb) float64): returns
+    (match_a, match_b) int32, -1 where unmatched."""
+    import numpy as np
+    m = np.ascontiguousarray(iou, dtype=np.float64)
+    na, nb = m.shape
+    act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+    ws = np.empty(max(1, lib().omt_assign_workspace_bytes(na, nb)), np.uint8)
+    ma, mb = np.empty(na, np.int32), np.empty(nb, np.int32)
+    _check(lib().omt_assign(_np_ptr(m), na, nb, _np_ptr(act), float(iou_min), _np_ptr(ws), ws.size,
+                            _np_ptr(ma), _np_ptr(mb)), "omt_assign")
+    return ma, mb
+
+
+def update_tracks(boxes_s, active_s, boxes_d, match_s, match_d):
+    """Update phase on host arrays: returns (boxes (n, 4) float32, active (n,) uint8)."""
+    import numpy as np
+    S = np.ascontiguousarray(boxes_s, dtype=np.float32).reshape(-1, 4)
+    D = np.ascontiguousarray(boxes_d, dtype=np.float32).reshape(-1, 4)
+    a = np.ascontiguousarray(active_s, dtype=np.uint8)
+    ms, md = np.ascontiguousarray(match_s, dtype=np.int32), np.ascontiguousarray(match_d, dtype=np.int32)
+    out = np.zeros((S.shape[0] + D.shape[0], 4), np.float32)
+    act = np.zeros(S.shape[0] + D.shape[0], np.uint8)
+    n = np.zeros(1, np.int32)
+    _check(lib().omt_update_tracks(_np_ptr(S), _np_ptr(a), S.shape[0], _np_ptr(D), D.shape[0],
+                                   _np_ptr(ms), _np_ptr(md), _np_ptr(out), _np_ptr(act),
+                                   ctypes.c_void_p(n.ctypes.data)), "omt_update_tracks")
+    return out[:n[0]], act[:n[0]]
+
+
+def match_and_update(pred, active, dets, iou_min: float = 0.0, stream=None):
+    """Matching and update phases for one stream: pred (device (ns, 4)
+    float32, the predicted scene objects), active (host (ns,) uint8), dets
+    (device (nd, 4) float32).  The IoU matrix is computed on the device and
+    read back; the assignment and update run on the host.  Returns
+    (boxes (n, 4) float32, active (n,) uint8, match_s, match_d) on the host."""
+    import numpy as np
+    import torch
+    ns, nd = pred.shape[0], dets.shape[0]
+    iou = torch.empty((ns, nd), dtype=torch.float64, device=pred.device)
+    iou_matrix(pred, dets, iou, stream)
+    m = iou.cpu().numpy()
+    ms, md = assign(m, active, iou_min)
+    boxes, act = update_tracks(pred.cpu().numpy(), active, dets.cpu().numpy(), ms, md)
+    return boxes, act, ms, md
 
 
 class StreamTracker:
