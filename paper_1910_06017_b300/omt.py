@@ -314,7 +314,9 @@ def match_and_update(pred, active, dets, iou_min: float = 0.0, stream=None):
     ns, nd = pred.shape[0], dets.shape[0]
     iou = torch.empty((ns, nd), dtype=torch.float64, device=pred.device)
     iou_matrix(pred, dets, iou, stream)
-    m = iou.cpu().numpy()
+    host = torch.empty((ns, nd), dtype=torch.float64).pin_memory()
+    host.copy_(iou)
+    m = host.numpy()
     ms, md = assign(m, active, iou_min)
     boxes, act = update_tracks(pred.cpu().numpy(), active, dets.cpu().numpy(), ms, md)
     return boxes, act, ms, md
