@@ -359,7 +359,10 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
         const uint64_t key = valid ? keys[N - 1 - j] : 0ull;
         const uint32_t idx = 0xFFFFFFFFu - (uint32_t)key;
         const int y = (int)(idx / (uint32_t)a.w), x = (int)(idx - (uint32_t)y * (uint32_t)a.w);
-        bool ok = valid;
+        // a key always names a pixel of the box; anything else (a corrupted
+        // input) is refused rather than indexing the grid out of range
+        bool ok = valid && x >= g.xlo && y >= g.ylo && x < g.xlo + g.gx * a.cell &&
+                  y < g.ylo + g.gy * a.cell;
         if (ok && a.md2c > 0) {
             if (g.cells) {
                 const int cx0 = max(x - a.dmax - g.xlo, 0) / a.cell;
