@@ -256,9 +256,9 @@ __global__ void __launch_bounds__(RNT) response_batch_kernel(const uint8_t *tabl
 }
 
 // ------------------------------------------------------------ select kernel
-constexpr int SNT = 256;
-constexpr int SCAP = 4096;   // candidate keys held in shared memory
-constexpr int GCAP = 8192;   // cells of the accepted-point grid in shared memory
+constexpr int SNT = 128;
+constexpr int SCAP = 1024;   // candidate keys held in shared memory
+constexpr int GCAP = 4096;   // cells of the accepted-point grid in shared memory
 
 // Keys sorted per chunk for a box keeping up to maxc corners: enough for the
 // greedy pass to usually finish in one chunk (it rejects some candidates).
@@ -470,6 +470,34 @@ __device__ uint64_t kth_largest(const uint64_t *keys, int n, uint64_t lo_bound, 
     return prefix;
 }
 
+// Gathers into keys[] (up to SCAP of them, counted in *count) the keys of
+// the box's local maxima with R > 0 and, with QUALITY, qden * R > thr; a warp
+// per row, eight loads in flight per lane.  Returns this lane's R_max.
+template <bool QUALITY>
+__device__ __forceinline__ uint32_t gather_keys(const SelectArgs &a, int xlo, int xhi, int ylo,
+                                                int yhi, int64_t thr, uint64_t *keys, int *count) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t m = 0;
+    for (int y = ylo + warp; y <= yhi; y += SNT / 32) {
+        const uint32_t *row = a.rmap + (int64_t)y * a.w;
+        for (int x = xlo + lane; x <= xhi; x += 256) {
+            uint32_t v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = x + 32 * q <= xhi ? __ldg(row + x + 32 * q) : 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t R = v[q] & R_MASK;
+                m = max(m, R);
+                if ((v[q] & MAX_FLAG) && R > 0 && (!QUALITY || (int64_t)a.qden * R > thr)) {
+                    const int pos = atomicAdd(count, 1);
+                    if (pos < SCAP) keys[pos] = make_key(R, (uint32_t)(y * a.w + x + 32 * q));
+                }
+            }
+        }
+    }
+    return m;
+}
+
 // Corners of one box, whole CTA.  Shared memory: keys[SCAP] | chunk[T] |
 // acc[acc_cap] | cells[GCAP] in the dynamic area.
 __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
@@ -502,38 +530,30 @@ __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
 
     // One pass over the eligible pixels (a warp per row): R_max, and the keys
     // of every local maximum with R > 0 while they fit.
-    const int warp = tid >> 5, lane = tid & 31;
+    const int lane = tid & 31;
     if (tid == 0) {
         s_rmax = 0;
         s_count = 0;
         s_nacc = 0;
     }
     __syncthreads();
-    uint32_t m = 0;
-    for (int y = ylo + warp; y <= yhi; y += SNT / 32) {
-        const uint32_t *row = a.rmap + (int64_t)y * a.w;
-        // four loads in flight per lane
-        for (int x = xlo + lane; x <= xhi; x += 256) {
-            uint32_t v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = x + 32 * q <= xhi ? __ldg(row + x + 32 * q) : 0u;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const uint32_t R = v[q] & R_MASK;
-                m = max(m, R);
-                if ((v[q] & MAX_FLAG) && R > 0) {
-                    const int pos = atomicAdd(&s_count, 1);
-                    if (pos < SCAP) keys[pos] = make_key(R, (uint32_t)(y * a.w + x + 32 * q));
-                }
-            }
-        }
-    }
+    uint32_t m = gather_keys<false>(a, xlo, xhi, ylo, yhi, 0, keys, &s_count);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
     if (lane == 0) atomicMax(&s_rmax, m);
     __syncthreads();
     const int64_t thr = (int64_t)a.qnum * (int64_t)s_rmax;
-    const int total = s_count;
+    int total = s_count;
+    if (total > SCAP) {
+        // Overflow: gather again, keeping only the keys that pass the
+        // quality test (R > thr / qden); they usually fit.
+        __syncthreads();
+        if (tid == 0) s_count = 0;
+        __syncthreads();
+        gather_keys<true>(a, xlo, xhi, ylo, yhi, thr, keys, &s_count);
+        __syncthreads();
+        total = s_count;
+    }
 
     if (total <= SCAP) {
         // Candidates pass the quality test iff R > thr / qden, i.e. they are

@@ -208,3 +208,23 @@ def test_select_4k_workload(omt, oracle):
     pr = synth.rigid_pair(n_regions=200)
     cnt = _check_select(omt, oracle, pr.frame0, pr.boxes, 250)
     assert cnt.sum() > 20000
+
+
+def test_select_weak_maxima_overflow_quality_fits(omt, oracle):
+    # faint noise makes thousands of weak local maxima in the box; a few
+    # strong squares set R_max so that the quality test keeps only their
+    # corners: the box overflows the first gather but not the second
+    rng = np.random.default_rng(23)
+    w, h = 640, 480
+    f = (128 + rng.integers(-2, 3, size=(h, w))).astype(np.uint8)
+    for k in range(12):
+        x0, y0 = 40 + 48 * (k % 6) * 2, 60 + 150 * (k // 6)
+        f[y0:y0 + 30, x0:x0 + 30] = 250 if k % 2 else 5
+    R = oracle.corner_response(f)
+    lm = _local_max(R) & (R > 0)
+    box = (slice(10, 470), slice(5, 635))
+    assert lm[box].sum() > 4096
+    assert (lm[box] & (R[box] * 100 > R[box].max())).sum() < 1024
+    boxes = np.array([[5, 10, 635, 470], [0, 0, w, h]], np.float32)
+    _check_select(omt, oracle, f, boxes, 200)
+    _check_select(omt, oracle, f, boxes, 20, (1, 100), 12.0)
