@@ -197,92 +197,92 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b, int lane) {
     b = __shfl_sync(FULL_MASK, keep, 16);
 }
 
+// Packed FP32 arithmetic: two lanes of one instruction, each rounded as
+// the scalar fmaf / add.
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+
 // Frame-t window from the raw template rows: (Ix, Iy) per tap row stay in
-// registers, with the level constants G (three sums).  Lane l < WIN owns tap
-// column l; lane WIN holds the column right of the window, so every lane's
-// right-hand texel comes from the next lane by a shuffle.
+// registers as one pair, with the level constants G (three sums).  Lane
+// l < WIN owns tap column l; lane WIN holds the column right of the window,
+// so every lane's right-hand texel comes from the next lane by a shuffle.
 template <int ST, int WIN>
 __device__ __forceinline__ void template_window(const LevelView &P, int tx0, float ax, float ay,
                                                 int lane, const unsigned *W, const LevelCopy &lc,
-                                                float (&Xw)[WIN], float (&Yw)[WIN], float &sxx,
-                                                float &sxy, float &syy) {
+                                                float2 (&XY)[WIN], float &sxx, float &sxy,
+                                                float &syy) {
     using D = Dims<ST, WIN>;
     const unsigned *rawG = W + D::T * D::RWI;
     const bool tapcol = lane < WIN;
     const int cg0 = clampi(tx0 + (lane < WIN ? lane : WIN), 0, P.w - 1) - lc.tcol_g;
-    float pX = 0.f, pY = 0.f;
-    sxx = sxy = syy = 0.f;
+    const float2 ax2 = f2(ax, ax), ay2 = f2(ay, ay);
+    float2 prev = f2(0.f, 0.f), sq = f2(0.f, 0.f);  // sq = (sxx, syy)
+    sxy = 0.f;
 #pragma unroll
     for (int tr = 0; tr <= WIN; ++tr) {
         const float2 g0 = raw_grad<ST>(rawG + tr * D::RWG, cg0);
-        const float g1x = __shfl_down_sync(FULL_MASK, g0.x, 1);
-        const float g1y = __shfl_down_sync(FULL_MASK, g0.y, 1);
-        const float hX = fmaf(ax, g1x - g0.x, g0.x);
-        const float hY = fmaf(ax, g1y - g0.y, g0.y);
+        const float2 g1 = f2(__shfl_down_sync(FULL_MASK, g0.x, 1),
+                             __shfl_down_sync(FULL_MASK, g0.y, 1));
+        const float2 h = __ffma2_rn(ax2, f2sub(g1, g0), g0);   // horizontal
         if (tr > 0) {
-            const float X = fmaf(ay, hX - pX, pX);
-            const float Y = fmaf(ay, hY - pY, pY);
-            Xw[tr - 1] = X;
-            Yw[tr - 1] = Y;
-            sxx = fmaf(X, X, sxx);
-            sxy = fmaf(X, Y, sxy);
-            syy = fmaf(Y, Y, syy);
+            const float2 v = __ffma2_rn(ay2, f2sub(h, prev), prev);  // vertical
+            XY[tr - 1] = v;
+            sq = __ffma2_rn(v, v, sq);
+            sxy = fmaf(v.x, v.y, sxy);
         }
-        pX = hX;
-        pY = hY;
+        prev = h;
     }
+    sxx = sq.x;
+    syy = sq.y;
     if (!tapcol) sxx = sxy = syy = 0.f;
 }
 
 // The four integer-shift correlations of a raw image window with the
-// template gradients: S[2a+b] = sum over taps of V(tap + (b, a)) * Ix(tap)
-// and S[4 + 2a+b] the same with Iy, for the window whose top-left tap sits
-// at raw row oy, raw column col0 of this lane (lanes as in template_window).
-// Bilinear sampling at fraction (bx, by) is then the weighted sum
-// (1-bx)(1-by) S0 + bx(1-by) S1 + (1-bx)by S2 + bx by S3 (combine8), so a
-// window position is correlated once however many iterations revisit it.
-// The frame-t template and the frame-(t+1) search window go through this
-// same code, so equal frames give exactly equal sums.
+// template gradients: S[s] = sum over taps of V(tap + (b, a)) (Ix, Iy)(tap),
+// s = 2a + b, for the window whose top-left tap sits at raw row oy, raw
+// column col0 of this lane (lanes as in template_window).  Bilinear
+// sampling at fraction (bx, by) is then the weighted sum (1-bx)(1-by) S0 +
+// bx(1-by) S1 + (1-bx)by S2 + bx by S3 (combine4), so a window position is
+// correlated once however many iterations revisit it.  The frame-t template
+// and the frame-(t+1) search window go through this same code, so equal
+// frames give exactly equal sums.
 template <int ST, bool U8, int WIN>
-__device__ __forceinline__ void corr8(const unsigned *raw, int rw, int oy, int col0, int lane,
-                                      const float (&Xw)[WIN], const float (&Yw)[WIN],
-                                      float (&S)[8]) {
+__device__ __forceinline__ void corr4(const unsigned *raw, int rw, int oy, int col0, int lane,
+                                      const float2 (&XY)[WIN], float2 (&S)[4]) {
     const unsigned *base = raw + oy * rw;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) S[q] = 0.f;
+    for (int q = 0; q < 4; ++q) S[q] = f2(0.f, 0.f);
     float p0 = 0.f, p1 = 0.f;
 #pragma unroll
     for (int tr = 0; tr <= WIN; ++tr) {
         const float v0 = raw_texel<ST>(base + tr * rw, col0, U8);
         const float v1 = __shfl_down_sync(FULL_MASK, v0, 1);
         if (tr > 0) {
-            const float X = Xw[tr - 1], Y = Yw[tr - 1];
-            S[0] = fmaf(p0, X, S[0]);
-            S[1] = fmaf(p1, X, S[1]);
-            S[2] = fmaf(v0, X, S[2]);
-            S[3] = fmaf(v1, X, S[3]);
-            S[4] = fmaf(p0, Y, S[4]);
-            S[5] = fmaf(p1, Y, S[5]);
-            S[6] = fmaf(v0, Y, S[6]);
-            S[7] = fmaf(v1, Y, S[7]);
+            const float2 g = XY[tr - 1];
+            S[0] = __ffma2_rn(f2(p0, p0), g, S[0]);
+            S[1] = __ffma2_rn(f2(p1, p1), g, S[1]);
+            S[2] = __ffma2_rn(f2(v0, v0), g, S[2]);
+            S[3] = __ffma2_rn(f2(v1, v1), g, S[3]);
         }
         p0 = v0;
         p1 = v1;
     }
     if (lane >= WIN) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) S[q] = 0.f;
+        for (int q = 0; q < 4; ++q) S[q] = f2(0.f, 0.f);
     }
 }
 
 // This lane's share of sum over taps of V(tap + (fx, fy)) (Ix, Iy) for the
 // window of S, by bilinear weights.
-__device__ __forceinline__ void combine8(const float (&S)[8], float fx, float fy, float &sx,
+__device__ __forceinline__ void combine4(const float2 (&S)[4], float fx, float fy, float &sx,
                                          float &sy) {
     const float w0 = (1.0f - fx) * (1.0f - fy), w1 = fx * (1.0f - fy);
     const float w2 = (1.0f - fx) * fy, w3 = fx * fy;
-    sx = fmaf(w3, S[3], fmaf(w2, S[2], fmaf(w1, S[1], w0 * S[0])));
-    sy = fmaf(w3, S[7], fmaf(w2, S[6], fmaf(w1, S[5], w0 * S[4])));
+    sx = fmaf(w3, S[3].x, fmaf(w2, S[2].x, fmaf(w1, S[1].x, w0 * S[0].x)));
+    sy = fmaf(w3, S[3].y, fmaf(w2, S[2].y, fmaf(w1, S[1].y, w0 * S[0].y)));
 }
 
 // One level of the pyramidal iteration for one point (the whole warp).
@@ -332,17 +332,16 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     }
     __syncwarp();
 
-    float Xw[WIN], Yw[WIN];
+    float2 XY[WIN];
     float sxx, sxy, syy, cx, cy;
-    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, W + buf * D::TRAW, lc, Xw, Yw, sxx, sxy,
-                             syy);
-    float S[8];  // integer-shift correlations at the last position visited
+    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, W + buf * D::TRAW, lc, XY, sxx, sxy, syy);
+    float2 S[4];  // integer-shift correlations at the last position visited
     {
         // c = sum I(p + tap) (Ix, Iy), through the same path as J below
         const int ci0 = clampi(ipx - R + (lane < WIN ? lane : WIN), 0, P.w - 1) - lc.tcol_i;
-        if (u8) corr8<ST, true, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, Xw, Yw, S);
-        else corr8<ST, false, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, Xw, Yw, S);
-        combine8(S, ax, ay, cx, cy);
+        if (u8) corr4<ST, true, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, XY, S);
+        else corr4<ST, false, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, XY, S);
+        combine4(S, ax, ay, cx, cy);
     }
     sxx = warp_sum(sxx);
     sxy = warp_sum(sxy);
@@ -391,14 +390,14 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
             }
             const int col0 = clampi(jx - R + (lane < WIN ? lane : WIN), 0, J.w - 1) - lc.scol;
             const int oy = jy - sjy + MARGIN;
-            if (u8) corr8<ST, true, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, Xw, Yw, S);
-            else corr8<ST, false, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, Xw, Yw, S);
+            if (u8) corr4<ST, true, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, XY, S);
+            else corr4<ST, false, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, XY, S);
             cjx = jx;
             cjy = jy;
             cached = true;
         }
         float sx, sy;
-        combine8(S, bx, by, sx, sy);
+        combine4(S, bx, by, sx, sy);
         warp_sum2(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
         const float ex = (syy * bbx - sxy * bby) * inv_det;
