@@ -381,6 +381,15 @@ int omt_update_tracks(const float *boxes_s, const uint8_t *active_s, int32_t ns,
 
 /* ---------------------------------------------------------------- misc */
 
+/* Synchronous (waits for the device).  *count receives the number of LK
+ * window copies (omt_lk_track and the batched LK phase) whose completion
+ * wait reached its time limit (one second) since the previous call, and the
+ * count restarts at 0.  A copy lands in microseconds, so a non-zero count
+ * means the copy engine stalled and the points tracked meanwhile may be
+ * wrong.  OMT_EINVAL if count is NULL; OMT_ECUDA on a CUDA error. */
+int omt_lk_wait_timeouts(uint32_t *count);
+
+
 const char *omt_error_string(int32_t code);
 
 /* Library version as major * 10000 + minor * 100 + patch. */

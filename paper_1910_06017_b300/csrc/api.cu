@@ -278,6 +278,14 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
         e.h = P.h;
         e.nboxes = b.nboxes;
         e.maxc = b.max_corners;
+        {
+            // the host table may be only 16-byte aligned: encode aside, then copy
+            alignas(64) CUtensorMap tm[OMT_MAX_LEVELS * LK_MAPS];
+            e.tm_ok = encode_lk_maps(P, N, prm->win, tm);
+            memcpy(base + batch_maps_offset(caps->max_streams) +
+                       sizeof(CUtensorMap) * (size_t)i * OMT_MAX_LEVELS * LK_MAPS,
+                   tm, sizeof(tm));
+        }
         for (int L = 0; L < prm->levels; ++L)
             pyr_pre[L][i + 1] = pyr_pre[L][i] + pyramid_tiles(P.lv[L].w, P.lv[L].h);
         resp_pre[i + 1] = resp_pre[i] + response_tiles(P.w, P.h);
@@ -354,6 +362,14 @@ int omt_iou_matrix(const float *a, int32_t na, const float *b, int32_t nb, doubl
     if (na == 0 || nb == 0) return OMT_OK;
     if (!a || !b || !iou || !aligned(a, 16) || !aligned(b, 16) || !aligned(iou, 8)) return OMT_EINVAL;
     return from_cuda(launch_iou_matrix(a, na, b, nb, iou, (cudaStream_t)stream));
+}
+
+int omt_lk_wait_timeouts(uint32_t *count) {
+    if (!count) return OMT_EINVAL;
+    unsigned c = 0;
+    const int r = from_cuda(lk_wait_timeouts_take(&c));
+    *count = c;
+    return r;
 }
 
 size_t omt_assign_workspace_bytes(int32_t na, int32_t nb) {

@@ -16,6 +16,11 @@
 //
 // Solve: det = Gxx Gyy - Gxy^2 by Kahan's fused form, lambda_min =
 // det / lambda_max (no cancellation), eta = G^-1 b by the 2x2 adjugate.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <unordered_map>
+
 #include "omt_internal.cuh"
 
 namespace omt {
@@ -26,6 +31,8 @@ constexpr int LK_WARPS = LK_NT / 32;
 constexpr int LK_MAX_NT = 256;           // largest CTA a launch may use
 
 struct LKArgs {
+    CUtensorMap tm[OMT_MAX_LEVELS * LK_MAPS];  // window maps (encode_lk_maps)
+    uint32_t tm_ok;                              // valid maps, bit 3L + m
     LevelView P[OMT_MAX_LEVELS];
     LevelView J[OMT_MAX_LEVELS];
     const float2 *pts;
@@ -50,15 +57,20 @@ __device__ __forceinline__ float det2(float a, float d, float b) {
 
 // ------------------------------------------------------------ staging
 // Per warp and level, the texels the level needs are copied global ->
-// shared with 16-byte cp.async (no registers held, all rows in flight): the
-// (win+1)^2 window of frame t under the template (I and (Ix, Iy)) and frame
-// t+1's search region around the initial centre, MARGIN texels wider than
-// the window on every side.  Rows are clamped to the level when copied; a
-// row is copied as the 16-byte chunks covering its column range clamped to
-// the level, and columns are clamped when the raw rows are read back: an
-// iteration's tap row is two shared loads per lane (its texel and the right
-// neighbour).  The region is copied again only if the centre moves more
-// than MARGIN texels away.
+// shared by the tensor memory accelerator: the (win+1)^2 window of frame t
+// under the template (I and (Ix, Iy)) and frame t+1's search region around
+// the initial centre, MARGIN texels wider than the window on every side.
+// A window whose rows lie inside the level is one 2D tensor copy per plane
+// (cp.async.bulk.tensor, issued by lane 0): a box of whole 16-byte chunks
+// from the 16-byte aligned column at or before its first column; columns
+// past the level's right edge arrive as zeros and are never read, because
+// columns are clamped to the level when the raw rows are read back.  A
+// window that crosses the top or bottom edge is copied row by row instead
+// (cp.async.bulk, one row per lane, each row clamped to the level), and so
+// is every window of a level whose map could not be encoded.  Each of the
+// warp's three buffers (two templates, one search region) has an mbarrier
+// whose phase completes when its fill's bytes have landed.  The region is
+// copied again only if the centre moves more than MARGIN texels away.
 constexpr int MARGIN = 4;
 
 template <int ST, int WIN>
@@ -71,52 +83,142 @@ struct Dims {
     static constexpr int GSZ = 2 * ESZ;               // bytes of a gradient texel
     // 4-byte words per raw row: the 16-byte chunks covering the row's bytes
     // from a 16-byte aligned start (at most 15 bytes of lead-in), rounded to
-    // whole chunks.
+    // whole chunks; a tensor copy's box is one raw row wide.
     static constexpr int chunks(int bytes) { return (bytes + 15 + 15) / 16; }
     static constexpr int RWJ = 4 * chunks((SP + 1) * ESZ);
     static constexpr int RWI = 4 * chunks(T * ESZ);
     static constexpr int RWG = 4 * chunks(T * GSZ);
-    static constexpr int TRAW = T * (RWI + RWG);              // raw template words (16-byte multiple)
+    // tensor copies land on 128-byte boundaries (32 words)
+    static constexpr int a128(int words) { return (words + 31) & ~31; }
+    static constexpr int TG = a128(T * RWI);                  // gradient rows in a template buffer
+    static constexpr int TRAW = TG + a128(T * RWG);           // one template buffer
     static constexpr int UNION = 2 * TRAW;                    // two template buffers
-    static constexpr int WORDS = UNION + SH * RWJ;            // per warp, 16-byte multiple
+    static constexpr int BAR = UNION + a128(SH * RWJ);        // the three mbarriers
+    static constexpr int WORDS = BAR + 32;                    // per warp, 128-byte multiple
 };
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// Wait until at most N of this thread's most recent copy groups are pending.
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() {
-    cp_async_commit();
-    cp_async_wait<0>();
+constexpr int BUF_SEARCH = 2;
+// A fill lands in microseconds; a wait gives up after this long (globaltimer
+// nanoseconds) so that a stalled copy cannot hold the warp forever.
+constexpr unsigned long long FILL_WAIT_NS = 1000000000ull;
+
+// Fills that were not seen complete within FILL_WAIT_NS (read by
+// omt_lk_wait_timeouts; zero unless the copy engine stalls).
+__device__ unsigned lk_wait_timeouts;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// Copy `rows` rows starting at level row y0 (each clamped), texel columns
-// [x0, x0 + ncols) clamped to the level, as 16-byte chunks into dst (rw
-// 4-byte words per row, a multiple of 4).  A chunk is 16-byte aligned in the
-// row and every row is 128-byte aligned with its pitch a multiple of 128, so
-// a chunk never leaves its row's pitch.  Returns the level column of the
-// first texel held by each raw row.
-__device__ __forceinline__ int copy_rows(const uint8_t *plane, int64_t pitch, int w, int h,
-                                         int esz, int x0, int ncols, int y0, int rows, int rw,
-                                         unsigned *dst, int lane) {
-    const int xa = clampi(x0, 0, w - 1), xb = clampi(x0 + ncols - 1, 0, w - 1);
-    const int b0 = (xa * esz) & ~15, b1 = (xb + 1) * esz;
-    const int nc = (b1 - b0 + 15) >> 4;  // chunks per row
-    const int total = rows * nc;
-    // k / nc by a multiply-high with ceil(2^32 / nc), exact for k < 2^32 / nc
-    // (nc = 1, whose multiplier does not fit 32 bits, is the identity)
-    const unsigned magic = nc > 1 ? 0xFFFFFFFFu / (unsigned)nc + 1u : 0u;
-    for (int k = lane; k < total; k += 32) {
-        const int r = nc > 1 ? (int)__umulhi((unsigned)k, magic) : k, c = k - r * nc;
-        const uint8_t *row = plane + (int64_t)clampi(y0 + r, 0, h - 1) * pitch + b0;
-        cp_async16(dst + r * rw + 4 * c, row + 16 * c);
+// Completion state of a warp's three staging buffers.
+struct Fills {
+    uint64_t *bar;   // bar[b]: mbarrier of buffer b
+    unsigned pend;   // bit b: a fill of buffer b is in flight
+    unsigned phase;  // bit b: parity of buffer b's current phase
+};
+
+__device__ __forceinline__ void fills_init(Fills &f, unsigned *W_bar, int lane) {
+    f.bar = (uint64_t *)W_bar;
+    f.pend = 0;
+    f.phase = 0;
+    if (lane == 0) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(f.bar + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    return b0 >> (__ffs(esz) - 1);  // esz is 1, 2, 4 or 8
+    __syncwarp();
 }
+
+// Open a fill of buffer b that will land `bytes` bytes: lane 0 arrives and
+// sets the expected count; the copies follow after the warp syncs.
+__device__ __forceinline__ void fill_begin(Fills &f, int b, unsigned bytes, int lane) {
+    if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(f.bar + b)),
+                     "r"(bytes)
+                     : "memory");
+    f.pend |= 1u << b;
+    __syncwarp();
+}
+
+// One row (bytes a multiple of 16, both ends 16-byte aligned).
+__device__ __forceinline__ void bulk_row(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One box of a 2D tensor map at element (x, y); x times the element size is
+// a multiple of 16 bytes and dst is 128-byte aligned.
+__device__ __forceinline__ void tensor_box(void *dst, const CUtensorMap *map, int x, int y,
+                                           uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Wait (bounded) until buffer b's fill in flight, if any, has landed.
+__device__ __forceinline__ void fill_wait(Fills &f, int b) {
+    if (!((f.pend >> b) & 1u)) return;
+    const unsigned a = smem_u32(f.bar + b), par = (f.phase >> b) & 1u;
+    if (!mbar_try_wait(a, par)) {
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(a, par)) {
+            if (global_ns() - t0 > FILL_WAIT_NS) {
+                atomicAdd(&lk_wait_timeouts, 1u);
+                break;
+            }
+        }
+    }
+    f.phase ^= 1u << b;
+    f.pend &= ~(1u << b);
+}
+
+__device__ __forceinline__ void fill_drain(Fills &f) {
+    fill_wait(f, 0);
+    fill_wait(f, 1);
+    fill_wait(f, BUF_SEARCH);
+}
+
+// The bytes of a row to copy for texel columns [x0, x0 + ncols) clamped to
+// the level: from the 16-byte aligned byte b0 at or before the first column,
+// whole 16-byte chunks through the last.  Rows are 128-byte aligned with
+// pitches a multiple of 128, so the chunks never leave the row's pitch.
+struct Span {
+    int b0;
+    unsigned bytes;
+};
+__device__ __forceinline__ Span row_span(int w, int esz, int x0, int ncols) {
+    const int xa = clampi(x0, 0, w - 1), xb = clampi(x0 + ncols - 1, 0, w - 1);
+    Span s;
+    s.b0 = (xa * esz) & ~15;
+    s.bytes = (unsigned)(((xb + 1) * esz - s.b0 + 15) & ~15);
+    return s;
+}
+
+// log2 of an element size of 1, 2, 4 or 8 bytes.
+__device__ __forceinline__ int esz_shift(int esz) { return __ffs(esz) - 1; }
 
 // Texel x (level column, clamped) of a raw row whose first byte is level
 // column `base`: u8, float or half(I - 128).  Level >= 1 values stay in the
@@ -146,6 +248,7 @@ struct LevelCopy {
 struct NextTemplate {
     bool has;
     const LevelView *P;
+    const CUtensorMap *tm;  // the level's maps, or null
     bool u8;
     int ipx, ipy;
 };
@@ -158,28 +261,58 @@ struct Prefetch {
 };
 
 // Start copying the template window of the level at (ipx, ipy) into buffer
-// `buf`, as one copy group; returns its column origins.
+// `buf` (I and gradient rows, one fill); returns its column origins.  tm
+// points at the level's maps when they are valid, else null.
 template <int ST, int WIN>
-__device__ __forceinline__ void issue_template(const LevelView &P, bool u8, int ipx, int ipy,
-                                               int buf, int lane, unsigned *W, int &tcol_i,
-                                               int &tcol_g) {
+__device__ __forceinline__ void issue_template(const LevelView &P, const CUtensorMap *tm, bool u8,
+                                               int ipx, int ipy, int buf, int lane, unsigned *W,
+                                               Fills &f, int &tcol_i, int &tcol_g) {
     using D = Dims<ST, WIN>;
-    unsigned *T = W + buf * D::TRAW;
-    tcol_i = copy_rows(P.img, P.img_pitch, P.w, P.h, u8 ? 1 : D::ESZ, ipx - D::R, D::T,
-                       ipy - D::R, D::T, D::RWI, T, lane);
-    tcol_g = copy_rows(P.grad, P.grad_pitch, P.w, P.h, D::GSZ, ipx - D::R, D::T, ipy - D::R,
-                       D::T, D::RWG, T + D::T * D::RWI, lane);
-    cp_async_commit();
+    unsigned *TI = W + buf * D::TRAW, *TGr = TI + D::TG;
+    const int esz = u8 ? 1 : D::ESZ;
+    const Span si = row_span(P.w, esz, ipx - D::R, D::T);
+    const Span sg = row_span(P.w, D::GSZ, ipx - D::R, D::T);
+    const int y0 = ipy - D::R;
+    tcol_i = si.b0 >> esz_shift(esz);
+    tcol_g = sg.b0 >> esz_shift(D::GSZ);
+    if (tm && y0 >= 0 && y0 + D::T <= P.h) {
+        fill_begin(f, buf, D::T * 4 * (D::RWI + D::RWG), lane);
+        if (lane == 0) {
+            tensor_box(TI, tm + LK_MAP_TI, tcol_i, y0, f.bar + buf);
+            tensor_box(TGr, tm + LK_MAP_TG, tcol_g, y0, f.bar + buf);
+        }
+    } else {
+        fill_begin(f, buf, D::T * (si.bytes + sg.bytes), lane);
+        if (lane < D::T) {
+            const int64_t y = clampi(y0 + lane, 0, P.h - 1);
+            bulk_row(TI + lane * D::RWI, P.img + y * P.img_pitch + si.b0, si.bytes, f.bar + buf);
+            bulk_row(TGr + lane * D::RWG, P.grad + y * P.grad_pitch + sg.b0, sg.bytes, f.bar + buf);
+        }
+    }
 }
 
+// Start copying frame t+1's search region around (jx, jy); tm as above.
 template <int ST, int WIN>
-__device__ __forceinline__ void copy_search(const LevelView &J, bool u8, int jx, int jy, int lane,
-                                            unsigned *W, LevelCopy &lc) {
+__device__ __forceinline__ void copy_search(const LevelView &J, const CUtensorMap *tm, bool u8,
+                                            int jx, int jy, int lane, unsigned *W, Fills &f,
+                                            LevelCopy &lc) {
     using D = Dims<ST, WIN>;
+    const int esz = u8 ? 1 : D::ESZ;
     lc.sx0 = jx - D::R - MARGIN;
     lc.sy0 = jy - D::R - MARGIN;
-    lc.scol = copy_rows(J.img, J.img_pitch, J.w, J.h, u8 ? 1 : D::ESZ, lc.sx0, D::SP + 1, lc.sy0,
-                        D::SH, D::RWJ, W + D::UNION, lane);
+    const Span ss = row_span(J.w, esz, lc.sx0, D::SP + 1);
+    lc.scol = ss.b0 >> esz_shift(esz);
+    unsigned *S = W + D::UNION;
+    if (tm && lc.sy0 >= 0 && lc.sy0 + D::SH <= J.h) {
+        fill_begin(f, BUF_SEARCH, D::SH * 4 * D::RWJ, lane);
+        if (lane == 0) tensor_box(S, tm, lc.scol, lc.sy0, f.bar + BUF_SEARCH);
+    } else {
+        fill_begin(f, BUF_SEARCH, D::SH * ss.bytes, lane);
+        for (int r = lane; r < D::SH; r += 32) {
+            const int64_t y = clampi(lc.sy0 + r, 0, J.h - 1);
+            bulk_row(S + r * D::RWJ, J.img + y * J.img_pitch + ss.b0, ss.bytes, f.bar + BUF_SEARCH);
+        }
+    }
 }
 
 // Two warp sums at once: lanes 0-15 end with the total of a, lanes 16-31
@@ -214,7 +347,7 @@ __device__ __forceinline__ void template_window(const LevelView &P, int tx0, flo
                                                 float2 (&XY)[WIN], float &sxx, float &sxy,
                                                 float &syy) {
     using D = Dims<ST, WIN>;
-    const unsigned *rawG = W + D::T * D::RWI;
+    const unsigned *rawG = W + D::TG;
     const bool tapcol = lane < WIN;
     const int cg0 = clampi(tx0 + (lane < WIN ? lane : WIN), 0, P.w - 1) - lc.tcol_g;
     const float2 ax2 = f2(ax, ax), ay2 = f2(ay, ay);
@@ -285,12 +418,18 @@ __device__ __forceinline__ void combine4(const float2 (&S)[4], float fx, float f
     sy = fmaf(w3, S[3].y, fmaf(w2, S[2].y, fmaf(w1, S[1].y, w0 * S[0].y)));
 }
 
+// Level L's maps when all three are valid, else null (row copies).
+__device__ __forceinline__ const CUtensorMap *level_maps(const CUtensorMap *tm, uint32_t ok, int L) {
+    return tm && ((ok >> (LK_MAPS * L)) & 7u) == 7u ? tm + LK_MAPS * L : nullptr;
+}
+
 // One level of the pyramidal iteration for one point (the whole warp).
 // Returns the status after this level; nu is the level's increment.
 template <int ST, int WIN>
 __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &J, float px,
                                            float py, float gx, float gy, int max_iter,
-                                           float eps2, float tau_n, int lane, bool u8, unsigned *W,
+                                           float eps2, float tau_n, int lane, bool u8,
+                                           const CUtensorMap *tm, unsigned *W, Fills &f,
                                            Prefetch &pf, const NextTemplate &nx, float &nux,
                                            float &nuy, int &k, bool &conv) {
     using D = Dims<ST, WIN>;
@@ -315,7 +454,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     } else {
         buf = 0;
         __syncwarp();
-        issue_template<ST, WIN>(P, u8, ipx, ipy, buf, lane, W, lc.tcol_i, lc.tcol_g);
+        issue_template<ST, WIN>(P, tm, u8, ipx, ipy, buf, lane, W, f, lc.tcol_i, lc.tcol_g);
     }
     pf.valid = false;
     const float c0x = ax + gx, c0y = ay + gy;
@@ -324,12 +463,9 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     if (c0_ok) {
         sjx = ipx + (int)floorf(c0x);
         sjy = ipy + (int)floorf(c0y);
-        copy_search<ST, WIN>(J, u8, sjx, sjy, lane, W, lc);
-        cp_async_commit();
-        cp_async_wait<1>();   // the template group is done; the search may still run
-    } else {
-        cp_async_wait<0>();
+        copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, sjx, sjy, lane, W, f, lc);
     }
+    fill_wait(f, buf);   // the template has landed; the search may still run
     __syncwarp();
 
     float2 XY[WIN];
@@ -357,13 +493,12 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     // into the other buffer while this level iterates.
     if (nx.has) {
         __syncwarp();
-        issue_template<ST, WIN>(*nx.P, nx.u8, nx.ipx, nx.ipy, 1 - buf, lane, W, pf.tcol_i, pf.tcol_g);
+        issue_template<ST, WIN>(*nx.P, nx.tm, nx.u8, nx.ipx, nx.ipy, 1 - buf, lane, W, f,
+                                pf.tcol_i, pf.tcol_g);
         pf.valid = true;
         pf.buf = 1 - buf;
-        if (c0_ok) cp_async_wait<1>();  // the search group is done; the prefetch may still run
-    } else if (c0_ok) {
-        cp_async_wait<0>();
     }
+    fill_wait(f, BUF_SEARCH);  // the search region has landed; the prefetch may still run
     __syncwarp();
     bool staged = c0_ok;
     int cjx = 0, cjy = 0;
@@ -381,8 +516,8 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         if (!cached || jx != cjx || jy != cjy) {
             if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
                 __syncwarp();
-                copy_search<ST, WIN>(J, u8, jx, jy, lane, W, lc);
-                cp_async_wait_all();   // also lands a pending prefetch
+                copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, jx, jy, lane, W, f, lc);
+                fill_wait(f, BUF_SEARCH);
                 __syncwarp();
                 sjx = jx;
                 sjy = jy;
@@ -420,8 +555,10 @@ template <int ST, int WIN>
 __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
                                          int max_iter, float eps2, float tau_n, float2 u,
                                          int i, float2 *out, uint8_t *status, uint8_t *iters,
-                                         unsigned *W, Prefetch &pf, bool has_next, float2 u_next,
-                                         const LevelView *P_next_point) {
+                                         const CUtensorMap *tm, uint32_t tm_ok, unsigned *W,
+                                         Fills &f, Prefetch &pf, bool has_next, float2 u_next,
+                                         const LevelView *P_next_point, const CUtensorMap *tm_next,
+                                         uint32_t tm_ok_next) {
     const int lane = threadIdx.x & 31;
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     int st = OMT_PT_OK;
@@ -431,7 +568,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
     // outside the frame without a window (its integer positions would not
     // fit); such a next point gets no prefetch either.
     if (!(fabsf(u.x) <= 16777216.f) || !(fabsf(u.y) <= 16777216.f)) {
-        cp_async_wait<0>();
+        fill_drain(f);
         pf.valid = false;
         if (lane == 0) {
             out[i] = u;
@@ -449,6 +586,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
             const float s1 = __int_as_float((127 - (L - 1)) << 23);
             nx.has = true;
             nx.P = &P[L - 1];
+            nx.tm = level_maps(tm, tm_ok, L - 1);
             nx.u8 = L - 1 == 0;
             nx.ipx = (int)floorf(u.x * s1);
             nx.ipy = (int)floorf(u.y * s1);
@@ -456,6 +594,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
             const float st0 = __int_as_float((127 - (levels - 1)) << 23);
             nx.has = has_next;
             nx.P = &P_next_point[levels - 1];
+            nx.tm = level_maps(tm_next, tm_ok_next, levels - 1);
             nx.u8 = levels - 1 == 0;
             nx.ipx = (int)floorf(u_next.x * st0);
             nx.ipy = (int)floorf(u_next.y * st0);
@@ -464,7 +603,8 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         int k;
         bool conv;
         st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
-                                  lane, L == 0, W, pf, nx, nux, nuy, k, conv);
+                                  lane, L == 0, level_maps(tm, tm_ok, L), W, f, pf, nx, nux, nuy,
+                                  k, conv);
         itp |= (unsigned long long)k << (8 * L);
         if (st != OMT_PT_OK) break;
         if (!conv) nonconv = true;
@@ -478,8 +618,9 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
     }
     if (st != OMT_PT_OK) {
         // a lost point leaves its prefetch (for a level it will not reach)
-        // unused: land it and forget it
-        cp_async_wait<0>();
+        // unused, and maybe its search region in flight: land them and
+        // forget them
+        fill_drain(f);
         pf.valid = false;
     }
 
@@ -499,16 +640,18 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
     if (iters && lane < levels) iters[(int64_t)i * levels + lane] = (uint8_t)(itp >> (8 * lane));
 }
 
-// This warp's staging words in the block's dynamic shared memory.
+// This warp's staging words in the block's dynamic shared memory, from its
+// first 128-byte boundary (tensor copies land on 128-byte boundaries).
 template <int ST, int WIN>
 __device__ __forceinline__ unsigned *warp_words() {
-    extern __shared__ __align__(16) unsigned lk_smem[];
-    return lk_smem + (size_t)(threadIdx.x >> 5) * Dims<ST, WIN>::WORDS;
+    extern __shared__ __align__(128) unsigned lk_smem[];
+    const unsigned lead = (128u - (smem_u32(lk_smem) & 127u)) & 127u;
+    return lk_smem + lead / 4 + (size_t)(threadIdx.x >> 5) * Dims<ST, WIN>::WORDS;
 }
 
 template <int ST, int WIN>
 constexpr size_t stage_bytes(int warps = LK_WARPS) {
-    return (size_t)warps * Dims<ST, WIN>::WORDS * 4;
+    return (size_t)warps * Dims<ST, WIN>::WORDS * 4 + 128;
 }
 
 template <int ST, int WIN>
@@ -520,6 +663,8 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
         n = m < n ? m : n;
     }
     const int nwarps = gridDim.x * LK_WARPS;
+    Fills f;
+    fills_init(f, W + Dims<ST, WIN>::BAR, threadIdx.x & 31);
     Prefetch pf;
     pf.valid = false;
     for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
@@ -527,9 +672,10 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
         const bool has_next = nxt < n;
         const float2 un = has_next ? a.pts[nxt] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters, W, pf, has_next, un, a.P);
+                          a.status, a.iters, a.tm, a.tm_ok, W, f, pf, has_next, un, a.P, a.tm,
+                          a.tm_ok);
     }
-    cp_async_wait<0>();
+    fill_drain(f);
 }
 
 // All points of all streams of a batch: the per-stream counts come from the
@@ -565,6 +711,8 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *tabl
         b = __shfl_sync(FULL_MASK, b, 0);
         return b < (unsigned)total ? (int)b : total;
     };
+    Fills f;
+    fills_init(f, W + Dims<ST, WIN>::BAR, lane);
     Prefetch pf;
     pf.valid = false;
     int g = take(), end = g + chunk;
@@ -582,11 +730,12 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *tabl
         const StreamEntry &en = t.stream(sn);
         const float2 un = has_next ? en.pts[gn - pre[sn]] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
-                          e.pts_out, e.status, e.iters, W, pf, has_next, un, en.P);
+                          e.pts_out, e.status, e.iters, t.maps(s), e.tm_ok, W, f, pf, has_next, un,
+                          en.P, t.maps(sn), en.tm_ok);
         g = gn;
         s = sn;
     }
-    cp_async_wait<0>();
+    fill_drain(f);
 }
 
 template <int ST>
@@ -652,6 +801,124 @@ cudaError_t launch_batch_st(const uint8_t *table, int win, int sms, int warps, i
 
 }  // namespace
 
+// ------------------------------------------------------------ tensor maps
+namespace {
+
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeTiled tensor_map_encoder() {
+    static const EncodeTiled fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiled) nullptr;
+        }
+        return (EncodeTiled)p;
+    }();
+    return fn;
+}
+
+// Encoded maps are kept by their parameters: a caller that re-packs the
+// same pyramid buffers every step pays for each map once.
+struct MapKey {
+    const void *base;
+    int64_t pitch;
+    int w, h, dtype, box_w, box_h;
+    bool operator==(const MapKey &o) const {
+        return base == o.base && pitch == o.pitch && w == o.w && h == o.h && dtype == o.dtype &&
+               box_w == o.box_w && box_h == o.box_h;
+    }
+};
+struct MapKeyHash {
+    size_t operator()(const MapKey &k) const {
+        uint64_t x = (uint64_t)(uintptr_t)k.base ^ ((uint64_t)k.pitch << 17);
+        x ^= ((uint64_t)k.w << 32) ^ ((uint64_t)k.h << 8) ^ ((uint64_t)k.dtype << 56);
+        x ^= ((uint64_t)k.box_w << 40) ^ ((uint64_t)k.box_h << 24);
+        x *= 0x9E3779B97F4A7C15ull;
+        return (size_t)(x ^ (x >> 29));
+    }
+};
+constexpr size_t MAP_CACHE_MAX = 8192;
+
+// A 2D map of a plane of h rows of w elements (pitch bytes apart) read in
+// boxes of box_w x box_h elements, zero-filled outside the plane.
+bool encode_2d(CUtensorMap *m, CUtensorMapDataType dt, const void *base, int w, int h,
+               int64_t pitch, int box_w, int box_h) {
+    static std::mutex mu;
+    static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> cache;
+    const MapKey key{base, pitch, w, h, (int)dt, box_w, box_h};
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) {
+        *m = it->second;
+        return true;
+    }
+    const EncodeTiled enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t elem[2] = {1, 1};
+    if (enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, elem,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (cache.size() >= MAP_CACHE_MAX) cache.clear();
+    cache.emplace(key, *m);
+    return true;
+}
+
+template <int ST, int WIN>
+uint32_t encode_win(const omt_pyramid &P, const omt_pyramid &J, CUtensorMap *out) {
+    using D = Dims<ST, WIN>;
+    const CUtensorMapDataType dg = D::GSZ == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_INT64;
+    uint32_t ok = 0;
+    for (int L = 0; L < P.levels && L < OMT_MAX_LEVELS; ++L) {
+        const int esz = L == 0 ? 1 : D::ESZ;
+        const CUtensorMapDataType di = esz == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                       : esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+        const LevelView p = level_view(P, L), j = level_view(J, L);
+        CUtensorMap *m = out + LK_MAPS * L;
+        if (encode_2d(m + LK_MAP_TI, di, p.img, p.w, p.h, p.img_pitch, D::RWI * 4 / esz, D::T) &&
+            encode_2d(m + LK_MAP_TG, dg, p.grad, p.w, p.h, p.grad_pitch, D::RWG * 4 / D::GSZ, D::T) &&
+            encode_2d(m + LK_MAP_S, di, j.img, j.w, j.h, j.img_pitch, D::RWJ * 4 / esz, D::SH))
+            ok |= 7u << (LK_MAPS * L);
+    }
+    return ok;
+}
+
+template <int ST>
+uint32_t encode_st(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensorMap *out) {
+    switch (win) {
+#define OMT_LK_CASE(W) \
+    case W: return encode_win<ST, W>(P, J, out);
+        OMT_LK_CASE(3) OMT_LK_CASE(5) OMT_LK_CASE(7) OMT_LK_CASE(9) OMT_LK_CASE(11)
+        OMT_LK_CASE(13) OMT_LK_CASE(15) OMT_LK_CASE(17) OMT_LK_CASE(19) OMT_LK_CASE(21)
+        OMT_LK_CASE(23) OMT_LK_CASE(25) OMT_LK_CASE(27) OMT_LK_CASE(29) OMT_LK_CASE(31)
+#undef OMT_LK_CASE
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensorMap *out) {
+    if (P.storage == OMT_F32) return encode_st<OMT_F32>(P, J, win, out);
+    return encode_st<OMT_F16>(P, J, win, out);
+}
+
+cudaError_t lk_wait_timeouts_take(unsigned *count) {
+    unsigned zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(count, lk_wait_timeouts, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(lk_wait_timeouts, &zero, sizeof(unsigned));
+    return e;
+}
+
 cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
                             int ctas_per_sm, int chunk, cudaStream_t s) {
     int dev = 0, sms = 148;
@@ -669,6 +936,7 @@ cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const fl
                       uint8_t *status, uint8_t *iters, cudaStream_t s) {
     if (n_max <= 0) return cudaSuccess;
     LKArgs a;
+    a.tm_ok = encode_lk_maps(prev, next, prm.win, a.tm);
     for (int L = 0; L < OMT_MAX_LEVELS; ++L) {
         if (L < prev.levels) {
             a.P[L] = level_view(prev, L);

@@ -2,6 +2,7 @@
 // kernels of libomt.  Not part of the public C-ABI (see include/omt.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -110,7 +111,13 @@ struct StreamEntry {
     float2 *pad_pts;                   // scratch: per-box corner lists
     int32_t *pad_counts;               // scratch: per-box counts
     int32_t w, h, nboxes, maxc;
+    uint32_t tm_ok;                    // bit 3L + m: the table's LK map m of level L is valid
 };
+
+// Tensor maps of the LK window copies, per level: frame t's image and
+// gradient planes under the template box, frame t+1's image plane under the
+// search box.
+constexpr int LK_MAP_TI = 0, LK_MAP_TG = 1, LK_MAP_S = 2, LK_MAPS = 3;
 
 struct BatchHeader {
     int32_t nstreams, max_streams, total_boxes, levels, storage, win, max_iter;
@@ -128,8 +135,16 @@ __host__ __device__ inline size_t batch_entries_offset(int max_streams) {
     return (off + 15) & ~(size_t)15;
 }
 
+// The LK tensor maps follow the stream entries: stream s, level L, map m
+// at index (s * OMT_MAX_LEVELS + L) * LK_MAPS + m.
+__host__ __device__ inline size_t batch_maps_offset(int max_streams) {
+    const size_t off = batch_entries_offset(max_streams) + sizeof(StreamEntry) * (size_t)max_streams;
+    return (off + 127) & ~(size_t)127;
+}
+
 __host__ __device__ inline size_t batch_table_bytes(int max_streams) {
-    return batch_entries_offset(max_streams) + sizeof(StreamEntry) * (size_t)max_streams;
+    return batch_maps_offset(max_streams) +
+           sizeof(CUtensorMap) * (size_t)max_streams * OMT_MAX_LEVELS * LK_MAPS;
 }
 
 struct BatchView {
@@ -145,6 +160,11 @@ struct BatchView {
     __host__ __device__ const int32_t *box_prefix() const { return pyr_prefix(OMT_MAX_LEVELS + 1); }
     __host__ __device__ const StreamEntry &stream(int s) const {
         return ((const StreamEntry *)(base + batch_entries_offset(hdr().max_streams)))[s];
+    }
+    // stream s's LK maps, LK_MAPS per level
+    __host__ __device__ const CUtensorMap *maps(int s) const {
+        return (const CUtensorMap *)(base + batch_maps_offset(hdr().max_streams)) +
+               (size_t)s * OMT_MAX_LEVELS * LK_MAPS;
     }
 };
 
@@ -189,6 +209,15 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
                                  int max_boxes, int max_corners, cudaStream_t s);
 // LK over every point of a batch: warps per CTA, CTAs per SM and work-queue
 // chunk as in omt_batch_caps (0 = default).
+// Encodes the LK window maps of every level of P (frame t) and J (frame
+// t+1) for window side win into out[L * LK_MAPS + m]; returns the mask of
+// valid maps (bit 3L + m).  Host only; a map that cannot be encoded (or no
+// driver) leaves its bit clear and the kernels copy that level row by row.
+uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensorMap *out);
+
+// Reads and clears the count of LK staging waits that hit their limit.
+cudaError_t lk_wait_timeouts_take(unsigned *count);
+
 cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
                             int ctas_per_sm, int chunk, cudaStream_t s);
 cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, cudaStream_t s);

@@ -26,7 +26,7 @@ EXPORTED = [
     "omt_select_corners", "omt_lk_track", "omt_update_boxes", "omt_error_string",
     "omt_version", "omt_select_corners_static", "omt_batch_table_bytes", "omt_batch_pack",
     "omt_batch_step", "omt_batch_upload", "omt_batch_phase", "omt_iou_matrix",
-    "omt_assign_workspace_bytes", "omt_assign", "omt_update_tracks",
+    "omt_assign_workspace_bytes", "omt_assign", "omt_update_tracks", "omt_lk_wait_timeouts",
 ]
 PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES = 0, 1, 2, 3
 BATCH_MAX_STREAMS = 256
@@ -119,6 +119,7 @@ def lib():
                                  c_size_t, c_void_p, c_void_p]
         L.omt_update_tracks.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p]
+        L.omt_lk_wait_timeouts.argtypes = [c_void_p]
         L.omt_batch_table_bytes.argtypes = [POINTER(BatchCaps)]
         L.omt_batch_table_bytes.restype = c_size_t
         L.omt_batch_pack.argtypes = [POINTER(BatchStream), c_int32, POINTER(Params),
@@ -301,6 +302,14 @@ def update_tracks(boxes_s, active_s, boxes_d, match_s, match_d):
                                    _np_ptr(ms), _np_ptr(md), _np_ptr(out), _np_ptr(act),
                                    ctypes.c_void_p(n.ctypes.data)), "omt_update_tracks")
     return out[:n[0]], act[:n[0]]
+
+
+def lk_wait_timeouts() -> int:
+    """LK window copies whose completion wait reached its time limit since
+    the previous call (0 unless the copy engine stalled)."""
+    c = ctypes.c_uint32(0)
+    _check(lib().omt_lk_wait_timeouts(ctypes.byref(c)), "omt_lk_wait_timeouts")
+    return int(c.value)
 
 
 def match_and_update(pred, active, dets, iou_min: float = 0.0, stream=None):

@@ -280,3 +280,10 @@ def test_batch_equals_plain_win31_five_levels(omt, storage):
         torch.cuda.synchronize()
         for a, b in zip(plain, _batch_results(B, sps)):
             _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
+
+
+def test_lk_staging_waits_never_time_out(omt):
+    # every window copy of the LK kernels above landed within its wait limit
+    torch.cuda.synchronize()
+    assert omt.lk_wait_timeouts() == 0
+    assert omt.lk_wait_timeouts() == 0  # the read restarts the count
