@@ -418,9 +418,18 @@ __device__ __forceinline__ void combine4(const float2 (&S)[4], float fx, float f
     sy = fmaf(w3, S[3].y, fmaf(w2, S[2].y, fmaf(w1, S[1].y, w0 * S[0].y)));
 }
 
-// Level L's maps when all three are valid, else null (row copies).
-__device__ __forceinline__ const CUtensorMap *level_maps(const CUtensorMap *tm, uint32_t ok, int L) {
-    return tm && ((ok >> (LK_MAPS * L)) & 7u) == 7u ? tm + LK_MAPS * L : nullptr;
+// Level L's maps, or null (row copies).  A pyramid pair's maps are used
+// only when every level's encoded.
+__device__ __forceinline__ const CUtensorMap *level_maps(const CUtensorMap *tm, int L) {
+    return tm ? tm + LK_MAPS * L : nullptr;
+}
+
+__device__ __forceinline__ bool all_maps(uint32_t ok, int levels) {
+    return ok == (levels >= 32 / LK_MAPS ? ~0u : (1u << (LK_MAPS * levels)) - 1u);
+}
+
+__device__ __forceinline__ const CUtensorMap *stream_maps(const BatchView &t, int s, int levels) {
+    return all_maps(t.stream(s).tm_ok, levels) ? t.maps(s) : nullptr;
 }
 
 // One level of the pyramidal iteration for one point (the whole warp).
@@ -555,10 +564,10 @@ template <int ST, int WIN>
 __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
                                          int max_iter, float eps2, float tau_n, float2 u,
                                          int i, float2 *out, uint8_t *status, uint8_t *iters,
-                                         const CUtensorMap *tm, uint32_t tm_ok, unsigned *W,
-                                         Fills &f, Prefetch &pf, bool has_next, float2 u_next,
-                                         const LevelView *P_next_point, const CUtensorMap *tm_next,
-                                         uint32_t tm_ok_next) {
+                                         const CUtensorMap *tm, unsigned *W, Fills &f,
+                                         Prefetch &pf, bool has_next, float2 u_next,
+                                         const LevelView *P_next_point,
+                                         const CUtensorMap *tm_next) {
     const int lane = threadIdx.x & 31;
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     int st = OMT_PT_OK;
@@ -586,7 +595,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
             const float s1 = __int_as_float((127 - (L - 1)) << 23);
             nx.has = true;
             nx.P = &P[L - 1];
-            nx.tm = level_maps(tm, tm_ok, L - 1);
+            nx.tm = level_maps(tm, L - 1);
             nx.u8 = L - 1 == 0;
             nx.ipx = (int)floorf(u.x * s1);
             nx.ipy = (int)floorf(u.y * s1);
@@ -594,7 +603,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
             const float st0 = __int_as_float((127 - (levels - 1)) << 23);
             nx.has = has_next;
             nx.P = &P_next_point[levels - 1];
-            nx.tm = level_maps(tm_next, tm_ok_next, levels - 1);
+            nx.tm = level_maps(tm_next, levels - 1);
             nx.u8 = levels - 1 == 0;
             nx.ipx = (int)floorf(u_next.x * st0);
             nx.ipy = (int)floorf(u_next.y * st0);
@@ -603,7 +612,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         int k;
         bool conv;
         st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
-                                  lane, L == 0, level_maps(tm, tm_ok, L), W, f, pf, nx, nux, nuy,
+                                  lane, L == 0, level_maps(tm, L), W, f, pf, nx, nux, nuy,
                                   k, conv);
         itp |= (unsigned long long)k << (8 * L);
         if (st != OMT_PT_OK) break;
@@ -665,6 +674,7 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
     const int nwarps = gridDim.x * LK_WARPS;
     Fills f;
     fills_init(f, W + Dims<ST, WIN>::BAR, threadIdx.x & 31);
+    const CUtensorMap *tm = all_maps(a.tm_ok, a.levels) ? a.tm : nullptr;
     Prefetch pf;
     pf.valid = false;
     for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
@@ -672,8 +682,7 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
         const bool has_next = nxt < n;
         const float2 un = has_next ? a.pts[nxt] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters, a.tm, a.tm_ok, W, f, pf, has_next, un, a.P, a.tm,
-                          a.tm_ok);
+                          a.status, a.iters, tm, W, f, pf, has_next, un, a.P, tm);
     }
     fill_drain(f);
 }
@@ -730,8 +739,8 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *tabl
         const StreamEntry &en = t.stream(sn);
         const float2 un = has_next ? en.pts[gn - pre[sn]] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
-                          e.pts_out, e.status, e.iters, t.maps(s), e.tm_ok, W, f, pf, has_next, un,
-                          en.P, t.maps(sn), en.tm_ok);
+                          e.pts_out, e.status, e.iters, stream_maps(t, s, h.levels), W, f, pf,
+                          has_next, un, en.P, stream_maps(t, sn, h.levels));
         g = gn;
         s = sn;
     }
