@@ -220,6 +220,32 @@ __device__ __forceinline__ Span row_span(int w, int esz, int x0, int ncols) {
 // log2 of an element size of 1, 2, 4 or 8 bytes.
 __device__ __forceinline__ int esz_shift(int esz) { return __ffs(esz) - 1; }
 
+// How a block of `rows` raw rows from level row y0 is filled: one tensor
+// copy when it lies inside the level; one tensor copy and then the edge rows
+// replicated into the rows outside (fix_rows) when it only overlaps the
+// level; row by row (each row clamped) without a map or overlap.
+enum FillMode { VIA_TMA, VIA_TMA_EDGE, VIA_ROWS };
+__device__ __forceinline__ FillMode fill_mode(const CUtensorMap *tm, int y0, int rows, int h) {
+    if (!tm || y0 >= h || y0 + rows <= 0) return VIA_ROWS;
+    return y0 >= 0 && y0 + rows <= h ? VIA_TMA : VIA_TMA_EDGE;
+}
+
+// After a tensor copy of rows [y0, y0 + rows) that overlaps a level of h
+// rows, the rows above the level (zero-filled) take the level's first row
+// and those below take its last, as a copy of clamped rows would hold.
+template <int RW>
+__device__ __forceinline__ void fix_rows(unsigned *blk, int y0, int rows, int h, int lane) {
+    const int top = y0 < 0 ? -y0 : 0;                   // rows above the level, < rows
+    const int below = h - y0 < rows ? h - y0 : rows;    // first row below the level, > top
+    const int n = (top + rows - below) * RW;
+    for (int k = lane; k < n; k += 32) {
+        const int j = k / RW, c = k - j * RW;
+        const int r = j < top ? j : below + (j - top);
+        const int src = j < top ? top : below - 1;
+        blk[r * RW + c] = blk[src * RW + c];
+    }
+}
+
 // Texel x (level column, clamped) of a raw row whose first byte is level
 // column `base`: u8, float or half(I - 128).  Level >= 1 values stay in the
 // stored domain (I - 128 for half): only differences and products with the
@@ -275,7 +301,7 @@ __device__ __forceinline__ void issue_template(const LevelView &P, const CUtenso
     const int y0 = ipy - D::R;
     tcol_i = si.b0 >> esz_shift(esz);
     tcol_g = sg.b0 >> esz_shift(D::GSZ);
-    if (tm && y0 >= 0 && y0 + D::T <= P.h) {
+    if (fill_mode(tm, y0, D::T, P.h) != VIA_ROWS) {
         fill_begin(f, buf, D::T * 4 * (D::RWI + D::RWG), lane);
         if (lane == 0) {
             tensor_box(TI, tm + LK_MAP_TI, tcol_i, y0, f.bar + buf);
@@ -303,7 +329,7 @@ __device__ __forceinline__ void copy_search(const LevelView &J, const CUtensorMa
     const Span ss = row_span(J.w, esz, lc.sx0, D::SP + 1);
     lc.scol = ss.b0 >> esz_shift(esz);
     unsigned *S = W + D::UNION;
-    if (tm && lc.sy0 >= 0 && lc.sy0 + D::SH <= J.h) {
+    if (fill_mode(tm, lc.sy0, D::SH, J.h) != VIA_ROWS) {
         fill_begin(f, BUF_SEARCH, D::SH * 4 * D::RWJ, lane);
         if (lane == 0) tensor_box(S, tm, lc.scol, lc.sy0, f.bar + BUF_SEARCH);
     } else {
@@ -312,6 +338,17 @@ __device__ __forceinline__ void copy_search(const LevelView &J, const CUtensorMa
             const int64_t y = clampi(lc.sy0 + r, 0, J.h - 1);
             bulk_row(S + r * D::RWJ, J.img + y * J.img_pitch + ss.b0, ss.bytes, f.bar + BUF_SEARCH);
         }
+    }
+}
+
+// Edge rows of a search region that a tensor copy only overlapped.
+template <int ST, int WIN>
+__device__ __forceinline__ void search_edges(const LevelView &J, const CUtensorMap *tm, unsigned *W,
+                                             const LevelCopy &lc, int lane) {
+    using D = Dims<ST, WIN>;
+    if (fill_mode(tm ? tm + LK_MAP_S : nullptr, lc.sy0, D::SH, J.h) == VIA_TMA_EDGE) {
+        __syncwarp();
+        fix_rows<D::RWJ>(W + D::UNION, lc.sy0, D::SH, J.h, lane);
     }
 }
 
@@ -334,7 +371,7 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b, int lane) {
 // the scalar fmaf / add.
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
-    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // a - b, one rounding
 }
 
 // Frame-t window from the raw template rows: (Ix, Iy) per tap row stay in
@@ -475,6 +512,11 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, sjx, sjy, lane, W, f, lc);
     }
     fill_wait(f, buf);   // the template has landed; the search may still run
+    if (fill_mode(tm, ipy - R, D::T, P.h) == VIA_TMA_EDGE) {
+        __syncwarp();
+        fix_rows<D::RWI>(W + buf * D::TRAW, ipy - R, D::T, P.h, lane);
+        fix_rows<D::RWG>(W + buf * D::TRAW + D::TG, ipy - R, D::T, P.h, lane);
+    }
     __syncwarp();
 
     float2 XY[WIN];
@@ -508,6 +550,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         pf.buf = 1 - buf;
     }
     fill_wait(f, BUF_SEARCH);  // the search region has landed; the prefetch may still run
+    if (c0_ok) search_edges<ST, WIN>(J, tm, W, lc, lane);
     __syncwarp();
     bool staged = c0_ok;
     int cjx = 0, cjy = 0;
@@ -527,6 +570,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
                 __syncwarp();
                 copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, jx, jy, lane, W, f, lc);
                 fill_wait(f, BUF_SEARCH);
+                search_edges<ST, WIN>(J, tm, W, lc, lane);
                 __syncwarp();
                 sjx = jx;
                 sjy = jy;
