@@ -133,10 +133,12 @@ __device__ __forceinline__ void fills_init(Fills &f, unsigned *W_bar, int lane) 
 // Open a fill of buffer b that will land `bytes` bytes: lane 0 arrives and
 // sets the expected count; the copies follow after the warp syncs.
 __device__ __forceinline__ void fill_begin(Fills &f, int b, unsigned bytes, int lane) {
-    if (lane == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(f.bar + b)),
-                     "r"(bytes)
-                     : "memory");
+    // predicated on lane 0 inside the asm: no divergent branch
+    asm volatile(
+        "{\n .reg .pred q;\n setp.eq.u32 q, %2, 0;\n"
+        " @q mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n}\n" ::"r"(smem_u32(f.bar + b)),
+        "r"(bytes), "r"(lane)
+        : "memory");
     f.pend |= 1u << b;
     __syncwarp();
 }
@@ -150,14 +152,16 @@ __device__ __forceinline__ void bulk_row(void *dst, const void *src, unsigned by
         : "memory");
 }
 
-// One box of a 2D tensor map at element (x, y); x times the element size is
-// a multiple of 16 bytes and dst is 128-byte aligned.
+// One box of a 2D tensor map at element (x, y), issued by lane 0 only
+// (predicated inside the asm); x times the element size is a multiple of
+// 16 bytes and dst is 128-byte aligned.
 __device__ __forceinline__ void tensor_box(void *dst, const CUtensorMap *map, int x, int y,
-                                           uint64_t *bar) {
+                                           uint64_t *bar, int lane) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "{\n .reg .pred q;\n setp.eq.u32 q, %5, 0;\n"
+        " @q cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n}\n" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "r"(lane)
         : "memory");
 }
 
@@ -303,10 +307,8 @@ __device__ __forceinline__ void issue_template(const LevelView &P, const CUtenso
     tcol_g = sg.b0 >> esz_shift(D::GSZ);
     if (fill_mode(tm, y0, D::T, P.h) != VIA_ROWS) {
         fill_begin(f, buf, D::T * 4 * (D::RWI + D::RWG), lane);
-        if (lane == 0) {
-            tensor_box(TI, tm + LK_MAP_TI, tcol_i, y0, f.bar + buf);
-            tensor_box(TGr, tm + LK_MAP_TG, tcol_g, y0, f.bar + buf);
-        }
+        tensor_box(TI, tm + LK_MAP_TI, tcol_i, y0, f.bar + buf, lane);
+        tensor_box(TGr, tm + LK_MAP_TG, tcol_g, y0, f.bar + buf, lane);
     } else {
         fill_begin(f, buf, D::T * (si.bytes + sg.bytes), lane);
         if (lane < D::T) {
@@ -331,7 +333,7 @@ __device__ __forceinline__ void copy_search(const LevelView &J, const CUtensorMa
     unsigned *S = W + D::UNION;
     if (fill_mode(tm, lc.sy0, D::SH, J.h) != VIA_ROWS) {
         fill_begin(f, BUF_SEARCH, D::SH * 4 * D::RWJ, lane);
-        if (lane == 0) tensor_box(S, tm, lc.scol, lc.sy0, f.bar + BUF_SEARCH);
+        tensor_box(S, tm, lc.scol, lc.sy0, f.bar + BUF_SEARCH, lane);
     } else {
         fill_begin(f, BUF_SEARCH, D::SH * ss.bytes, lane);
         for (int r = lane; r < D::SH; r += 32) {
@@ -372,6 +374,27 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b, int lane) {
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // a - b, one rounding
+}
+
+// Four warp sums at once: halving exchanges leave each quarter of the warp
+// (lane bits 4 and 3) with one of the four partial sums, butterflies within
+// the quarter finish it, and every lane reads the four totals back.  Fixed
+// order, as warp_sum2.
+__device__ __forceinline__ void warp_sum4(float &a, float &b, float &c, float &d, int lane) {
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
+    float k0 = h4 ? c : a, k1 = h4 ? d : b;
+    const float g0 = h4 ? a : c, g1 = h4 ? b : d;
+    k0 += __shfl_xor_sync(FULL_MASK, g0, 16);
+    k1 += __shfl_xor_sync(FULL_MASK, g1, 16);
+    float keep = h3 ? k1 : k0;
+    const float give = h3 ? k0 : k1;
+    keep += __shfl_xor_sync(FULL_MASK, give, 8);
+#pragma unroll
+    for (int m = 4; m > 0; m >>= 1) keep += __shfl_xor_sync(FULL_MASK, keep, m);
+    a = __shfl_sync(FULL_MASK, keep, 0);
+    b = __shfl_sync(FULL_MASK, keep, 8);
+    c = __shfl_sync(FULL_MASK, keep, 16);
+    d = __shfl_sync(FULL_MASK, keep, 24);
 }
 
 // Frame-t window from the raw template rows: (Ix, Iy) per tap row stay in
@@ -530,10 +553,8 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         else corr4<ST, false, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, XY, S);
         combine4(S, ax, ay, cx, cy);
     }
-    sxx = warp_sum(sxx);
+    warp_sum4(sxx, syy, cx, cy, lane);
     sxy = warp_sum(sxy);
-    syy = warp_sum(syy);
-    warp_sum2(cx, cy, lane);
     const float det = det2(sxx, syy, sxy);
     const float dd = sxx - syy;
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
