@@ -19,6 +19,8 @@
 // Everything is integer arithmetic, so the result equals the definition bit
 // for bit, and the atomics only change the order in which unique keys are
 // gathered, never the sorted order.
+#include <type_traits>
+
 #include "omt_internal.cuh"
 
 namespace omt {
@@ -106,42 +108,34 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
     int vm = 0, v0 = 0, vp = 0, lm = 0, l0 = 0, lp = 0, qm = 0, q0 = 0, qp = 0;
     int Ha2 = 0, Hb2 = 0, Hc2 = 0, Ha1 = 0, Hb1 = 0, Hc1 = 0;  // 3x1 sums, rows g-2, g-1
     uint32_t Rp = 0, M2 = 0, M1 = 0;  // R of row g-2; 3-column maxima of rows g-3, g-2
-    // texels of row g+1 loaded one step early for sliding steps (nv, ne)
+    // texels of row g+1 loaded one step early by the sliding steps (nv, ne)
     int nv = 0, ne = 0;
-    bool have_next = false;
-#pragma unroll 1
-    for (int s = 0; s < RH + 4; ++s) {
-        const int g = oy - 2 + s;  // gradient row of this step
-        if (s > 0 && g >= 2 && g <= a.h - 2) {
-            // the previous step read rows g-2 .. g: slide and take row g+1
+    // One step: gradient row g = oy - 2 + s.  SLIDE steps (rows g-1 .. g+1
+    // inside the frame, after the first step) shift the rows read by the
+    // previous step and take row g+1 from the prefetch; the others read the
+    // three (reflected) rows afresh.  The sliding steps are one contiguous
+    // range of s, so the loops below need no per-step branch between them.
+    auto step = [&](int s, auto slide) {
+        const int g = oy - 2 + s;
+        if constexpr (decltype(slide)::value) {
             vm = v0;
             v0 = vp;
             lm = l0;
             l0 = lp;
             qm = q0;
             q0 = qp;
-            int ep;
-            if (have_next) {
-                vp = nv;
-                ep = ne;
-            } else {
-                const uint8_t *r2 = a.img + (int64_t)(g + 1) * a.pitch;
-                vp = __ldg(r2 + cx);
-                ep = edge ? (int)__ldg(r2 + ex) : 0;
-            }
-            // the next step slides too: load its row g+2 now
-            have_next = s + 1 < RH + 4 && g + 1 <= a.h - 2;
-            if (have_next) {
-                const uint8_t *r3 = a.img + (int64_t)(g + 2) * a.pitch;
-                nv = __ldg(r3 + cx);
-                ne = edge ? (int)__ldg(r3 + ex) : 0;
-            }
+            vp = nv;
+            const int ep = ne;
+            // the next step's row g+2 (clamped: the last sliding step's
+            // prefetch is not used)
+            const uint8_t *r3 = a.img + (int64_t)min(g + 2, a.h - 1) * a.pitch;
+            nv = __ldg(r3 + cx);
+            ne = edge ? (int)__ldg(r3 + ex) : 0;
             lp = __shfl_up_sync(FULL_MASK, vp, 1);
             qp = __shfl_down_sync(FULL_MASK, vp, 1);
-            if (lane == 0) lp = ep;
-            else if (lane == 31) qp = ep;
+            lp = lane == 0 ? ep : lp;
+            qp = lane == 31 ? ep : qp;
         } else {
-            have_next = false;
             const int py = reflect101(g, a.h);
             const uint8_t *r0 = a.img + (int64_t)reflect101(py - 1, a.h) * a.pitch;
             const uint8_t *r1 = a.img + (int64_t)py * a.pitch;
@@ -161,15 +155,12 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
             qm = __shfl_down_sync(FULL_MASK, vm, 1);
             q0 = __shfl_down_sync(FULL_MASK, v0, 1);
             qp = __shfl_down_sync(FULL_MASK, vp, 1);
-            if (lane == 0) {
-                lm = em;
-                l0 = e0;
-                lp = ep;
-            } else if (lane == 31) {
-                qm = em;
-                q0 = e0;
-                qp = ep;
-            }
+            lm = lane == 0 ? em : lm;
+            l0 = lane == 0 ? e0 : l0;
+            lp = lane == 0 ? ep : lp;
+            qm = lane == 31 ? em : qm;
+            q0 = lane == 31 ? e0 : q0;
+            qp = lane == 31 ? ep : qp;
         }
         int gx = 3 * (qm - lm) + 10 * (q0 - l0) + 3 * (qp - lp);
         int gy = 3 * (lp - lm) + 10 * (vp - vm) + 3 * (qp - qm);
@@ -196,14 +187,12 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
         const uint32_t Mn =
             max(Rn, max(__shfl_up_sync(FULL_MASK, Rn, 1), __shfl_down_sync(FULL_MASK, Rn, 1)));
 
-        // row g - 2: its value and maximum flag
+        // row g - 2: its value and maximum flag (a predicated store)
         const int yf = g - 2;
-        if (s >= 4 && yf < a.h && lane >= 2 && lane <= 29 && inx) {
-            uint32_t flag = 0;
-            if (x >= 1 && x <= a.w - 2 && yf >= 1 && yf <= a.h - 2)
-                flag = Rp >= max(M2, max(M1, Mn)) ? MAX_FLAG : 0u;
+        const bool interior = x >= 1 && x <= a.w - 2 && yf >= 1 && yf <= a.h - 2;
+        const uint32_t flag = interior && Rp >= max(M2, max(M1, Mn)) ? MAX_FLAG : 0u;
+        if (s >= 4 && yf < a.h && lane >= 2 && lane <= 29 && inx)
             a.out[(int64_t)yf * a.w + x] = Rp | flag;
-        }
         Ha2 = Ha1;
         Hb2 = Hb1;
         Hc2 = Hc1;
@@ -213,7 +202,24 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
         M2 = M1;
         M1 = Mn;
         Rp = Rn;
+    };
+    using Fresh = std::integral_constant<bool, false>;
+    using Slide = std::integral_constant<bool, true>;
+    constexpr int STEPS = RH + 4;
+    // sliding steps: s >= 1 with 2 <= g <= h - 2, i.e. s in [s_a, s_b]
+    const int s_a = max(1, 4 - oy), s_b = min(STEPS - 1, a.h - oy);
+    int s = 0;
+#pragma unroll 1
+    for (; s < min(s_a, STEPS); ++s) step(s, Fresh{});
+    if (s_a <= s_b) {
+        const uint8_t *r = a.img + (int64_t)(oy - 2 + s_a + 1) * a.pitch;  // row g(s_a) + 1
+        nv = __ldg(r + cx);
+        ne = edge ? (int)__ldg(r + ex) : 0;
+#pragma unroll 1
+        for (s = s_a; s <= s_b; ++s) step(s, Slide{});
     }
+#pragma unroll 1
+    for (; s < STEPS; ++s) step(s, Fresh{});
 }
 
 // Tile t of a w x h frame: strip column and row block.
