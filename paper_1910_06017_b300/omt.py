@@ -419,9 +419,12 @@ class BatchTracker:
     """
 
     def __init__(self, sizes, params: Params, max_boxes, max_corners=None, device="cuda",
-                 with_iters: bool = True):
+                 with_iters: bool = True, overlap: bool = True):
         import torch
         self.params = params
+        # run the corner phase (frame t) on a second stream beside the
+        # pyramid phase (frame t+1): they touch disjoint buffers
+        self.overlap = overlap
         self.device = torch.device(device)
         n = len(sizes)
         if isinstance(max_boxes, int):
@@ -463,6 +466,7 @@ class BatchTracker:
         self.dev_tables = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
         self.cur = 0
         self.graphs = [None, None]
+        self.side = torch.cuda.Stream(device=dev)
 
     def _desc(self, s: int, parity: int) -> BatchStream:
         d = BatchStream()
@@ -503,6 +507,17 @@ class BatchTracker:
             batch_upload(self.tables[parity], self.caps, self.dev_tables[parity], stream)
 
     def _phases(self, parity, events=None, stream=None):
+        if self.overlap and not events:
+            import torch
+            main = stream if stream is not None else torch.cuda.current_stream(self.device)
+            dt = self.dev_tables[parity]
+            self.side.wait_stream(main)
+            batch_phase(dt, self.caps, self.params, PHASE_PYRAMID, main)
+            batch_phase(dt, self.caps, self.params, PHASE_CORNERS, self.side)
+            main.wait_stream(self.side)
+            batch_phase(dt, self.caps, self.params, PHASE_LK, main)
+            batch_phase(dt, self.caps, self.params, PHASE_BOXES, main)
+            return
         events = events or {}
         for phase in (PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES):
             ev = events.get(phase)

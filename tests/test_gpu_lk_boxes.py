@@ -259,8 +259,20 @@ def test_lk_4k_large_motion_sample(omt, oracle):
     rng = np.random.default_rng(1)
     sample = allp[rng.choice(len(allp), 3000, replace=False)]
     kw = dict(levels=5, win=31, max_iter=30, eps=0.01)
-    compare(omt, oracle, pr.frame0, pr.frame1, sample, min_ok=0.5, **kw)
-    compare(omt, oracle, pr.frame0, pr.frame1, sample, storage=1, tol=F16_TOL, min_ok=0.5, **kw)
+    stats = {}
+    for storage, tol in ((0, FLOW_TOL), (1, F16_TOL)):
+        g_out, g_st, o_out, o_st = compare(omt, oracle, pr.frame0, pr.frame1, sample,
+                                           storage=storage, tol=tol, min_ok=0.5, **kw)
+        # error report against the FP64 oracle: points OK with the same status
+        both = ((g_st & OK) > 0) & (g_st == o_st)
+        e = np.hypot(*(g_out[both] - o_out[both]).T)
+        stats[storage] = (e.max(), np.percentile(e, 99), e.mean(), both.sum())
+        print(f"4K 31x31 5 levels, {'F16' if storage else 'F32'} storage: |error| max "
+              f"{e.max():.2e} px, p99 {np.percentile(e, 99):.2e}, mean {e.mean():.2e} "
+              f"over {both.sum()} points")
+    # storing the pyramid in half precision costs accuracy, never more than
+    # the FP16 bar on average
+    assert stats[1][2] >= stats[0][2] and stats[1][2] <= F16_TOL
 
 
 # ------------------------------------------------------------------ boxes
