@@ -259,6 +259,9 @@ class GpuBackend(Backend):
         self.keep_boxes = keep_boxes
         self.stream = torch.cuda.Stream(device=self.device)
         self.copy_stream = torch.cuda.Stream(device=self.device)
+        # the corner phase (frame t) runs here beside the pyramid phase
+        # (frame t+1); they touch disjoint buffers
+        self.side_stream = torch.cuda.Stream(device=self.device)
         self.step_events = collections.deque(maxlen=2)   # steps k-2, k-1
         self._det = {}
 
@@ -378,8 +381,13 @@ class GpuBackend(Backend):
                 slot["primed"] = True
                 slot["use_det"] = True
             if descs:
-                for phase in (omt.PHASE_PYRAMID, omt.PHASE_CORNERS, omt.PHASE_LK, omt.PHASE_BOXES):
-                    omt.batch_phase(self.dev_tables[k], self.caps, self.params, phase, self.stream)
+                dt = self.dev_tables[k]
+                self.side_stream.wait_stream(self.stream)
+                omt.batch_phase(dt, self.caps, self.params, omt.PHASE_PYRAMID, self.stream)
+                omt.batch_phase(dt, self.caps, self.params, omt.PHASE_CORNERS, self.side_stream)
+                self.stream.wait_stream(self.side_stream)
+                omt.batch_phase(dt, self.caps, self.params, omt.PHASE_LK, self.stream)
+                omt.batch_phase(dt, self.caps, self.params, omt.PHASE_BOXES, self.stream)
             for slot, idx, det in steps:
                 par = slot["cur"]
                 if self.keep_boxes:
