@@ -38,6 +38,7 @@
 #define ORC_LOST_EIG 2
 #define ORC_LOST_OOB 4
 #define ORC_NONCONV 8
+#define ORC_LOST_FB 16
 
 /* ---------------------------------------------------------------- borders */
 
@@ -620,4 +621,24 @@ void orc_update_tracks(const float *boxes_s, const uint8_t *active_s, int ns, co
         active_out[n++] = 1;
     }
     *n_out = n;
+}
+
+/* Forward-backward consistency of the tracked points (the round-trip test of
+ * Kalal, Mikolajczyk and Matas, 2010), the consistency check that widens the
+ * prediction phase of Section V-A: a point tracked from u on frame t to v on
+ * frame t+1 is tracked back from v to u' on frame t; it keeps its forward
+ * status only if the backward run is OK too and the round trip closes,
+ * |u' - u| <= fb_max (Euclidean, level-0 pixels).  Otherwise its status
+ * becomes LOST_FB (its NONCONV bit is dropped with the OK bit).  Points whose
+ * forward run was lost are left as they are. */
+void orc_fb_check(const float *pts, const double *pts_back, const uint8_t *status_back, int n,
+                  double fb_max, uint8_t *status)
+{
+    for (int i = 0; i < n; ++i) {
+        if (!(status[i] & ORC_OK)) continue;
+        const double dx = pts_back[2 * i] - (double)pts[2 * i];
+        const double dy = pts_back[2 * i + 1] - (double)pts[2 * i + 1];
+        const int closes = (status_back[i] & ORC_OK) && sqrt(dx * dx + dy * dy) <= fb_max;
+        if (!closes) status[i] = ORC_LOST_FB;
+    }
 }

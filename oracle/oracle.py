@@ -61,6 +61,8 @@ def lib():
         L.orc_update_boxes.argtypes = [POINTER(c_float), POINTER(c_int32), POINTER(c_float),
                                        POINTER(c_float), POINTER(c_uint8), c_int, c_int,
                                        POINTER(c_double), POINTER(c_int32)]
+        L.orc_fb_check.argtypes = [POINTER(c_float), POINTER(c_double), POINTER(c_uint8), c_int,
+                                   c_double, POINTER(c_uint8)]
         L.orc_max_threads.restype = c_int
         _lib = L
     return _lib
@@ -176,6 +178,29 @@ def update_boxes(boxes, offsets, pts, pts_out, status, aggregator: int = 0):
     lib().orc_update_boxes(_p(b, c_float), _p(o, c_int32), _p(p, c_float), _p(q, c_float),
                            _p(s, c_uint8), nb, int(aggregator), _p(out, c_double), _p(nv, c_int32))
     return out, nv
+
+
+def fb_check(pts, pts_back, status_back, status, fb_max: float):
+    """Forward-backward check: the forward statuses with the points whose
+    round trip u -> v -> u' does not close within fb_max (or whose backward
+    run was lost) set to LOST_FB."""
+    p = np.ascontiguousarray(pts, dtype=np.float32).reshape(-1, 2)
+    q = np.ascontiguousarray(pts_back, dtype=np.float64).reshape(-1, 2)
+    sb = np.ascontiguousarray(status_back, dtype=np.uint8)
+    st = np.array(status, dtype=np.uint8, copy=True)
+    lib().orc_fb_check(_p(p, c_float), _p(q, c_double), _p(sb, c_uint8), p.shape[0],
+                       float(fb_max), _p(st, c_uint8))
+    return st
+
+
+def lk_track_fb(prev: Pyramid, nxt: Pyramid, pts, fb_max: float, **kw):
+    """Forward LK from prev to nxt, backward LK from the results, and the
+    forward-backward check: (pts_out, status, pts_back, status_back).  The
+    backward run starts from the forward results as float32, the precision
+    points are stored in."""
+    out, st = lk_track(prev, nxt, pts, **kw)
+    back, sb = lk_track(nxt, prev, out.astype(np.float32), **kw)
+    return out, fb_check(pts, back, sb, st, fb_max), back, sb
 
 
 def iou_matrix(a, b):
