@@ -233,6 +233,8 @@ def run_omt(args, ws, rank, local):
 
     caps = [cap_of(sp) for sp in streams]
     prm = params_for(omt, storage, max(caps))
+    if args.fb is not None:
+        prm = prm.replace(fb_max=args.fb)  # forward-backward check in every step
     B = omt.BatchTracker([sp.size for sp in streams], prm, max_boxes=[len(sp.boxes) for sp in streams],
                          max_corners=caps, device=dev)
     fr_h = []
@@ -273,11 +275,12 @@ def run_omt(args, ws, rank, local):
     step_ms = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
     ms_total = ev[0].elapsed_time(ev[-1])
 
-    ok_pts = n_pts = 0
+    ok_pts = n_pts = fb_lost = 0
     flops = 0.0
     for s in range(len(streams)):
         n = B.count(s)
         st = B.status[s][:n].cpu().numpy()
+        fb_lost += int((st == omt.PT_LOST_FB).sum())
         it = B.iters[s][:n].cpu().numpy()
         ok_pts += int(((st & 1) > 0).sum())
         n_pts += n
@@ -288,12 +291,14 @@ def run_omt(args, ws, rank, local):
     ph_ev = []
     for k in range(args.steps):
         e = {p: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-             for p in (omt.PHASE_PYRAMID, omt.PHASE_LK)}
+             for p in (omt.PHASE_PYRAMID, omt.PHASE_LK, omt.PHASE_FB)}
         B.step_phases(events=e)
         ph_ev.append(e)
     torch.cuda.synchronize()
     lk_ms = float(np.mean([e[omt.PHASE_LK][0].elapsed_time(e[omt.PHASE_LK][1]) for e in ph_ev]))
     pyr_ms = float(np.mean([e[omt.PHASE_PYRAMID][0].elapsed_time(e[omt.PHASE_PYRAMID][1]) for e in ph_ev]))
+    fb_ms = (float(np.mean([e[omt.PHASE_FB][0].elapsed_time(e[omt.PHASE_FB][1]) for e in ph_ev]))
+             if B.fb else None)
     px0 = sum(sp.size[0] * sp.size[1] for sp in streams)
     pyr_bytes = px0 * pyramid_bytes_per_px(args.storage, LEVELS)
 
@@ -331,6 +336,8 @@ def run_omt(args, ws, rank, local):
             "path": "batched: one omt_batch_step per step" + (", CUDA graph" if args.graph else ""),
             "storage": args.storage, "streams_per_gpu": args.streams,
             "points_per_step": n_pts, "ok_points_per_step": ok_pts,
+            **({"fb_max": args.fb, "fb_lost_points_per_step": fb_lost,
+                "fb_ms_per_step": fb_ms} if args.fb is not None else {}),
             "stream_frames_per_s": args.streams * ws / (ms_step * 1e-3),
             "latency_ms_p50": float(np.percentile(step_ms, 50)),
             "latency_ms_p99": float(np.percentile(step_ms, 99)),
@@ -416,6 +423,8 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="keep the default LK launch shape instead of autotuning it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fb", type=float, default=None, metavar="MAX",
+                    help="forward-backward check in every step, threshold MAX px (default off)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "omt":

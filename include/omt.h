@@ -9,6 +9,7 @@
  *   omt_select_corners  Shi-Tomasi corners inside each box of frame t
  *   omt_lk_track        pyramidal Lucas-Kanade from frame t to frame t+1
  *   omt_update_boxes    per-box median (or mean) displacement
+ *   omt_fb_check        forward-backward consistency of tracked points
  *
  * Conventions shared by every call
  *   - Pixel centres sit at integer coordinates; a level-L coordinate is the
@@ -54,13 +55,15 @@ enum omt_storage {
     OMT_F16 = 1  /* levels as half(I - 128), gradients as half2 (intensity/px) */
 };
 
-/* Per-point status bits written by omt_lk_track.  Exactly one of OK,
- * LOST_EIG, LOST_OOB is set; NONCONV may accompany OK. */
+/* Per-point status bits written by omt_lk_track (and LOST_FB by the
+ * forward-backward check).  Exactly one of OK, LOST_EIG, LOST_OOB, LOST_FB
+ * is set; NONCONV may accompany OK. */
 enum omt_point_status {
     OMT_PT_OK = 1,       /* tracked                                            */
     OMT_PT_LOST_EIG = 2, /* lambda_min(G)/win^2 < min_eig (or <= 0) at a level */
     OMT_PT_LOST_OOB = 4, /* left the frame (see omt_lk_track)                  */
-    OMT_PT_NONCONV = 8   /* some level hit max_iter without converging (info)  */
+    OMT_PT_NONCONV = 8,  /* some level hit max_iter without converging (info)  */
+    OMT_PT_LOST_FB = 16  /* tracked, but the round trip back did not close     */
 };
 
 #define OMT_MAX_LEVELS 8
@@ -82,10 +85,13 @@ typedef struct omt_params {
     int32_t max_corners; /* corners per box, 0..OMT_MAX_CORNERS                   */
     int32_t storage;     /* enum omt_storage                                      */
     int32_t aggregator;  /* 0 = median (default), 1 = mean (the paper's choice)   */
+    float fb_max;        /* batched steps: forward-backward check threshold in    */
+                         /*   level-0 px (omt_fb_check); < 0 = off (default)     */
 } omt_params;
 
 /* Defaults: 3 levels, 21x21 window, 30 iterations, eps 0.01, tau 1e-3,
- * quality 1/100, min distance 5, 50 corners, F32 storage, median. */
+ * quality 1/100, min distance 5, 50 corners, F32 storage, median, no
+ * forward-backward check (fb_max -1). */
 void omt_default_params(omt_params *p);
 
 /* OMT_OK if every field is in range, else OMT_EINVAL. */
@@ -252,6 +258,22 @@ int omt_update_boxes(const float *boxes, const int32_t *offsets, const float *pt
                      const float *pts_out, const uint8_t *status, int32_t nboxes,
                      const omt_params *prm, float *boxes_out, int32_t *nvalid, void *stream);
 
+/* Forward-backward consistency of tracked points (the round-trip test of
+ * Kalal, Mikolajczyk and Matas, 2010), a check on the prediction of Section
+ * V-A: after omt_lk_track from frame t to t+1 (pts -> pts_out, status) and
+ * back from t+1 to t (pts_out -> pts_back, status_back), every point whose
+ * status has OK keeps it only if status_back has OK and its round trip
+ * closes, sqrt(dx^2 + dy^2) <= fb_max with (dx, dy) = pts_back - pts (FP32,
+ * level-0 px); otherwise its status becomes OMT_PT_LOST_FB (NONCONV
+ * dropped).  Other statuses are left as they are.  pts, pts_back: device
+ * float2[n]; status_back: device uint8[n]; status: device uint8[n], read
+ * and written.  n = min(n_max, *n_dev) if n_dev (device int32) is given,
+ * else n_max.  OMT_EINVAL on a NaN fb_max, n_max < 0 or a missing array.
+ * Asynchronous on `stream`. */
+int omt_fb_check(const float *pts, const float *pts_back, const uint8_t *status_back,
+                 int32_t n_max, const int32_t *n_dev, float fb_max, uint8_t *status,
+                 void *stream);
+
 /* ---------------------------------------------------------------- batched */
 
 /* Section V-B runs the phases of consecutive frames and of several models
@@ -279,6 +301,9 @@ typedef struct omt_batch_stream {
     int32_t *offsets;      /* device int32[nboxes + 1] (CSR of pts per box)         */
     float *boxes_out;      /* device float4[nboxes], must not alias boxes           */
     int32_t *nvalid;       /* device int32[nboxes] or NULL                          */
+    float *pts_back;       /* device float2[nboxes * max_corners]: the backward    */
+    uint8_t *status_back;  /*   run of the forward-backward check (prm->fb_max >= 0;*/
+                           /*   else may be NULL)                                   */
 } omt_batch_stream;
 
 /* Capacities a packed table must fit; the launch grids depend on these
@@ -331,7 +356,10 @@ enum omt_batch_phase_id {
     OMT_PHASE_PYRAMID = 0, /* frame t+1 pyramids of every stream          */
     OMT_PHASE_CORNERS = 1, /* response maps, selection, CSR compaction    */
     OMT_PHASE_LK = 2,      /* one persistent launch over all points       */
-    OMT_PHASE_BOXES = 3    /* per-box median / mean update                */
+    OMT_PHASE_BOXES = 3,   /* per-box median / mean update                */
+    OMT_PHASE_FB = 4       /* backward LK from frame t+1 to t and the     */
+                           /*   forward-backward check (between LK and    */
+                           /*   BOXES; a no-op when prm->fb_max < 0)      */
 };
 int omt_batch_upload(const void *table, const omt_batch_caps *caps, void *dev_table,
                      size_t dev_table_bytes, void *stream);

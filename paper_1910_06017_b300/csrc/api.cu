@@ -71,6 +71,7 @@ void omt_default_params(omt_params *p) {
     p->max_corners = 50;
     p->storage = OMT_F32;
     p->aggregator = 0;
+    p->fb_max = -1.0f;
 }
 
 int omt_validate_params(const omt_params *p) {
@@ -87,6 +88,7 @@ int omt_validate_params(const omt_params *p) {
     if (p->max_corners < 0 || p->max_corners > OMT_MAX_CORNERS) return OMT_EINVAL;
     if (p->storage != OMT_F32 && p->storage != OMT_F16) return OMT_EINVAL;
     if (p->aggregator != 0 && p->aggregator != 1) return OMT_EINVAL;
+    if (p->fb_max != p->fb_max) return OMT_EINVAL;  // NaN
     return OMT_OK;
 }
 
@@ -219,6 +221,8 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
     h.aggregator = prm->aggregator;
     h.eps2 = prm->eps * prm->eps;
     h.tau_n = prm->min_eig * (float)(prm->win * prm->win);
+    h.fb_max = prm->fb_max;
+    h.fb_on = prm->fb_max >= 0.0f;
     const float md2 = prm->min_dist * prm->min_dist;
     h.md2c = (int64_t)ceil((double)md2);
     h.dmax = 0;
@@ -251,6 +255,8 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
                 return OMT_EINVAL;
             if (!b.pts || !b.pts_out || !b.status || !aligned(b.pts, 8) || !aligned(b.pts_out, 8))
                 return OMT_EINVAL;
+            if (h.fb_on && (!b.pts_back || !b.status_back || !aligned(b.pts_back, 8)))
+                return OMT_EINVAL;
         }
         if (!b.offsets || !b.scratch || !aligned(b.scratch, 256)) return OMT_EINVAL;
         if (b.scratch_bytes < select_scratch_bytes(P.w, P.h, b.nboxes, b.max_corners))
@@ -267,6 +273,8 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
         e.pts_out = (float2 *)b.pts_out;
         e.status = b.status;
         e.iters = b.iters;
+        e.pts_back = h.fb_on ? (float2 *)b.pts_back : nullptr;
+        e.status_back = h.fb_on ? b.status_back : nullptr;
         e.offsets = b.offsets;
         uint8_t *sp = (uint8_t *)b.scratch;
         e.rmap = (uint32_t *)sp;
@@ -279,11 +287,15 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
         e.nboxes = b.nboxes;
         e.maxc = b.max_corners;
         {
-            // the host table may be only 16-byte aligned: encode aside, then copy
-            alignas(64) CUtensorMap tm[OMT_MAX_LEVELS * LK_MAPS];
-            e.tm_ok = encode_lk_maps(P, N, prm->win, tm);
+            // the host table may be only 16-byte aligned: encode aside, then
+            // copy; backward maps (templates on frame t+1) only for the
+            // forward-backward check
+            alignas(64) CUtensorMap tm[2][OMT_MAX_LEVELS * LK_MAPS];
+            memset(tm, 0, sizeof(tm));
+            e.tm_ok = encode_lk_maps(P, N, prm->win, tm[0]);
+            e.tm_ok_back = h.fb_on ? encode_lk_maps(N, P, prm->win, tm[1]) : 0u;
             memcpy(base + batch_maps_offset(caps->max_streams) +
-                       sizeof(CUtensorMap) * (size_t)i * OMT_MAX_LEVELS * LK_MAPS,
+                       sizeof(CUtensorMap) * (size_t)i * 2 * OMT_MAX_LEVELS * LK_MAPS,
                    tm, sizeof(tm));
         }
         for (int L = 0; L < prm->levels; ++L)
@@ -332,9 +344,13 @@ int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt
             return from_cuda(launch_corners_batch(
                 dt, caps->max_streams, caps->max_streams * response_tiles(caps->max_w, caps->max_h),
                 caps->max_boxes, caps->max_corners, s));
+        case OMT_PHASE_FB:
+            if (!(prm->fb_max >= 0.0f)) return OMT_OK;
+            return from_cuda(launch_lk_batch(dt, prm->storage, prm->win, caps->lk_warps,
+                                             caps->lk_ctas_per_sm, caps->lk_chunk, 1, s));
         case OMT_PHASE_LK:
             return from_cuda(launch_lk_batch(dt, prm->storage, prm->win, caps->lk_warps,
-                                             caps->lk_ctas_per_sm, caps->lk_chunk, s));
+                                             caps->lk_ctas_per_sm, caps->lk_chunk, 0, s));
         case OMT_PHASE_BOXES:
             return from_cuda(launch_update_boxes_batch(dt, caps->max_boxes, s));
         default:
@@ -350,9 +366,12 @@ int omt_batch_step(const void *table, const omt_batch_caps *caps, const omt_para
     if (h.levels != prm->levels || h.storage != prm->storage || h.win != prm->win ||
         h.max_iter != prm->max_iter)
         return OMT_EINVAL;
+    if (h.fb_max != prm->fb_max) return OMT_EINVAL;
     int rc = omt_batch_upload(table, caps, dev_table, dev_table_bytes, stream);
-    for (int phase = OMT_PHASE_PYRAMID; rc == OMT_OK && phase <= OMT_PHASE_BOXES; ++phase)
-        rc = omt_batch_phase(dev_table, caps, prm, phase, stream);
+    static const int order[] = {OMT_PHASE_PYRAMID, OMT_PHASE_CORNERS, OMT_PHASE_LK, OMT_PHASE_FB,
+                                OMT_PHASE_BOXES};
+    for (int k = 0; rc == OMT_OK && k < 5; ++k)
+        rc = omt_batch_phase(dev_table, caps, prm, order[k], stream);
     return rc;
 }
 
@@ -362,6 +381,17 @@ int omt_iou_matrix(const float *a, int32_t na, const float *b, int32_t nb, doubl
     if (na == 0 || nb == 0) return OMT_OK;
     if (!a || !b || !iou || !aligned(a, 16) || !aligned(b, 16) || !aligned(iou, 8)) return OMT_EINVAL;
     return from_cuda(launch_iou_matrix(a, na, b, nb, iou, (cudaStream_t)stream));
+}
+
+int omt_fb_check(const float *pts, const float *pts_back, const uint8_t *status_back,
+                 int32_t n_max, const int32_t *n_dev, float fb_max, uint8_t *status,
+                 void *stream) {
+    if (fb_max != fb_max || n_max < 0) return OMT_EINVAL;
+    if (n_max == 0) return OMT_OK;
+    if (!pts || !pts_back || !status_back || !status || !aligned(pts, 8) || !aligned(pts_back, 8))
+        return OMT_EINVAL;
+    return from_cuda(launch_fb_check((const float2 *)pts, (const float2 *)pts_back, status_back,
+                                     n_max, n_dev, fb_max, status, (cudaStream_t)stream));
 }
 
 int omt_lk_wait_timeouts(uint32_t *count) {

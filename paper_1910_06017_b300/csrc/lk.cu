@@ -488,8 +488,10 @@ __device__ __forceinline__ bool all_maps(uint32_t ok, int levels) {
     return ok == (levels >= 32 / LK_MAPS ? ~0u : (1u << (LK_MAPS * levels)) - 1u);
 }
 
-__device__ __forceinline__ const CUtensorMap *stream_maps(const BatchView &t, int s, int levels) {
-    return all_maps(t.stream(s).tm_ok, levels) ? t.maps(s) : nullptr;
+__device__ __forceinline__ const CUtensorMap *stream_maps(const BatchView &t, int s, int levels,
+                                                          int backward) {
+    const StreamEntry &e = t.stream(s);
+    return all_maps(backward ? e.tm_ok_back : e.tm_ok, levels) ? t.maps(s, backward) : nullptr;
 }
 
 // One level of the pyramidal iteration for one point (the whole warp).
@@ -714,6 +716,30 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
     if (iters && lane < levels) iters[(int64_t)i * levels + lane] = (uint8_t)(itp >> (8 * lane));
 }
 
+// ------------------------------------------------------ forward-backward
+// A point tracked u -> v keeps its status only if the backward run v -> u'
+// is OK and the round trip closes: |u' - u| <= fb_max (FP32, level-0 px);
+// else it becomes LOST_FB.  Lost forward points are left as they are.
+__device__ __forceinline__ void fb_apply(float2 u, float2 u_back, uint8_t status_back,
+                                         float fb_max, uint8_t &status) {
+    if (!(status & OMT_PT_OK)) return;
+    const float dx = u_back.x - u.x, dy = u_back.y - u.y;
+    const bool closes = (status_back & OMT_PT_OK) && sqrtf(fmaf(dx, dx, dy * dy)) <= fb_max;
+    if (!closes) status = (uint8_t)OMT_PT_LOST_FB;
+}
+
+__global__ void fb_check_kernel(const float2 *pts, const float2 *pts_back,
+                                const uint8_t *status_back, int n_max, const int32_t *n_dev,
+                                float fb_max, uint8_t *status) {
+    int n = n_max;
+    if (n_dev) n = min(n, *n_dev);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint8_t st = status[i];
+        fb_apply(pts[i], pts_back[i], status_back[i], fb_max, st);
+        status[i] = st;
+    }
+}
+
 // This warp's staging words in the block's dynamic shared memory, from its
 // first 128-byte boundary (tensor copies land on 128-byte boundaries).
 template <int ST, int WIN>
@@ -759,12 +785,15 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
 // points of uneven cost balance over the warps; a warp takes its next chunk
 // before the last point of the current one, whose finest level then
 // prefetches the next point's top-level template.
-template <int ST, int WIN>
+template <int ST, int WIN, bool backward>
 __global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *table, int chunk) {
     __shared__ int32_t pre[OMT_BATCH_MAX_STREAMS + 1];
     unsigned *W = warp_words<ST, WIN>();
     const BatchView t(table);
     const BatchHeader &h = t.hdr();
+    if constexpr (backward) {
+        if (!h.fb_on) return;  // a table packed without the check
+    }
     unsigned *queue = const_cast<unsigned *>(&h.work[0]);
     const int ns = h.nstreams;
     const int lane = threadIdx.x & 31;
@@ -802,10 +831,20 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *tabl
         const bool has_next = gn < total;
         const int sn = has_next ? find_segment(pre, ns, gn) : s;
         const StreamEntry &en = t.stream(sn);
-        const float2 un = has_next ? en.pts[gn - pre[sn]] : make_float2(0.f, 0.f);
-        lk_point<ST, WIN>(e.P, e.P_next, h.levels, h.max_iter, h.eps2, h.tau_n, e.pts[i], i,
-                          e.pts_out, e.status, e.iters, stream_maps(t, s, h.levels), W, f, pf,
-                          has_next, un, en.P, stream_maps(t, sn, h.levels));
+        // forward: frame t -> t+1 from the corners; backward: frame t+1 -> t
+        // from the forward results
+        const float2 *in = backward ? e.pts_out : e.pts;
+        const float2 *in_next = backward ? en.pts_out : en.pts;
+        const float2 un = has_next ? in_next[gn - pre[sn]] : make_float2(0.f, 0.f);
+        lk_point<ST, WIN>(backward ? e.P_next : e.P, backward ? e.P : e.P_next, h.levels,
+                          h.max_iter, h.eps2, h.tau_n, in[i], i,
+                          backward ? e.pts_back : e.pts_out, backward ? e.status_back : e.status,
+                          backward ? nullptr : e.iters, stream_maps(t, s, h.levels, backward), W,
+                          f, pf, has_next, un, backward ? en.P_next : en.P,
+                          stream_maps(t, sn, h.levels, backward));
+        if constexpr (backward) {
+            if (lane == 0) fb_apply(e.pts[i], e.pts_back[i], e.status_back[i], h.fb_max, e.status[i]);
+        }
         g = gn;
         s = sn;
     }
@@ -831,8 +870,8 @@ cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int ST, int WIN>
-cudaError_t launch_batch_win(const uint8_t *table, int sms, int warps, int ctas_per_sm, int chunk,
+template <int ST, int WIN, bool backward>
+cudaError_t launch_batch_dir(const uint8_t *table, int sms, int warps, int ctas_per_sm, int chunk,
                              cudaStream_t s) {
     // no more warps per CTA than their staging areas fit in shared memory
     int dev = 0, optin = 0;
@@ -842,11 +881,11 @@ cudaError_t launch_batch_win(const uint8_t *table, int sms, int warps, int ctas_
     const int fit = optin / (int)stage_bytes<ST, WIN>(1);
     if (warps > fit) warps = fit > 0 ? fit : 1;
     const size_t smem = stage_bytes<ST, WIN>(warps);
-    e = cudaFuncSetAttribute(lk_batch_kernel<ST, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(lk_batch_kernel<ST, WIN, backward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lk_batch_kernel<ST, WIN>, 32 * warps,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lk_batch_kernel<ST, WIN, backward>, 32 * warps,
                                                       smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
@@ -855,16 +894,23 @@ cudaError_t launch_batch_win(const uint8_t *table, int sms, int warps, int ctas_
     e = cudaMemsetAsync(const_cast<uint8_t *>(table) + offsetof(BatchHeader, work), 0,
                         sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    lk_batch_kernel<ST, WIN><<<sms * per_sm, 32 * warps, smem, s>>>(table, chunk);
+    lk_batch_kernel<ST, WIN, backward><<<sms * per_sm, 32 * warps, smem, s>>>(table, chunk);
     return cudaGetLastError();
+}
+
+template <int ST, int WIN>
+cudaError_t launch_batch_win(const uint8_t *table, int sms, int warps, int ctas_per_sm, int chunk,
+                             int backward, cudaStream_t s) {
+    if (backward) return launch_batch_dir<ST, WIN, true>(table, sms, warps, ctas_per_sm, chunk, s);
+    return launch_batch_dir<ST, WIN, false>(table, sms, warps, ctas_per_sm, chunk, s);
 }
 
 template <int ST>
 cudaError_t launch_batch_st(const uint8_t *table, int win, int sms, int warps, int ctas_per_sm,
-                            int chunk, cudaStream_t s) {
+                            int chunk, int backward, cudaStream_t s) {
     switch (win) {
 #define OMT_LK_CASE(W) \
-    case W: return launch_batch_win<ST, W>(table, sms, warps, ctas_per_sm, chunk, s);
+    case W: return launch_batch_win<ST, W>(table, sms, warps, ctas_per_sm, chunk, backward, s);
         OMT_LK_CASE(3) OMT_LK_CASE(5) OMT_LK_CASE(7) OMT_LK_CASE(9) OMT_LK_CASE(11)
         OMT_LK_CASE(13) OMT_LK_CASE(15) OMT_LK_CASE(17) OMT_LK_CASE(19) OMT_LK_CASE(21)
         OMT_LK_CASE(23) OMT_LK_CASE(25) OMT_LK_CASE(27) OMT_LK_CASE(29) OMT_LK_CASE(31)
@@ -994,15 +1040,27 @@ cudaError_t lk_wait_timeouts_take(unsigned *count) {
 }
 
 cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
-                            int ctas_per_sm, int chunk, cudaStream_t s) {
+                            int ctas_per_sm, int chunk, int backward, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (warps <= 0) warps = LK_WARPS;
     if (chunk <= 0) chunk = 1;
     if (storage == OMT_F32)
-        return launch_batch_st<OMT_F32>(table, win, sms, warps, ctas_per_sm, chunk, s);
-    return launch_batch_st<OMT_F16>(table, win, sms, warps, ctas_per_sm, chunk, s);
+        return launch_batch_st<OMT_F32>(table, win, sms, warps, ctas_per_sm, chunk, backward, s);
+    return launch_batch_st<OMT_F16>(table, win, sms, warps, ctas_per_sm, chunk, backward, s);
+}
+
+cudaError_t launch_fb_check(const float2 *pts, const float2 *pts_back, const uint8_t *status_back,
+                            int n_max, const int32_t *n_dev, float fb_max, uint8_t *status,
+                            cudaStream_t s) {
+    if (n_max <= 0) return cudaSuccess;
+    const int nt = 256;
+    int blocks = (n_max + nt - 1) / nt;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    fb_check_kernel<<<blocks, nt, 0, s>>>(pts, pts_back, status_back, n_max, n_dev, fb_max,
+                                          status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const float2 *pts,

@@ -104,25 +104,28 @@ struct StreamEntry {
     const float4 *boxes;
     float4 *boxes_out;
     int32_t *nvalid;
-    float2 *pts, *pts_out;
-    uint8_t *status, *iters;
+    float2 *pts, *pts_out, *pts_back;
+    uint8_t *status, *iters, *status_back;
     int32_t *offsets;
     uint32_t *rmap;                    // scratch: response map
     float2 *pad_pts;                   // scratch: per-box corner lists
     int32_t *pad_counts;               // scratch: per-box counts
     int32_t w, h, nboxes, maxc;
-    uint32_t tm_ok;                    // bit 3L + m: the table's LK map m of level L is valid
+    uint32_t tm_ok, tm_ok_back;        // bit 3L + m: LK map m of level L (forward, backward) valid
 };
 
-// Tensor maps of the LK window copies, per level: frame t's image and
-// gradient planes under the template box, frame t+1's image plane under the
-// search box.
+// Tensor maps of the LK window copies, per level: the template frame's
+// image and gradient planes under the template box, the other frame's image
+// plane under the search box (forward: templates on frame t; backward, for
+// the forward-backward check: templates on frame t+1).
 constexpr int LK_MAP_TI = 0, LK_MAP_TG = 1, LK_MAP_S = 2, LK_MAPS = 3;
 
 struct BatchHeader {
     int32_t nstreams, max_streams, total_boxes, levels, storage, win, max_iter;
     int32_t qnum, qden, aggregator, dmax, cell;
     float eps2, tau_n;
+    float fb_max;   // forward-backward threshold (level-0 px)
+    int32_t fb_on;  // fb_max >= 0
     int64_t md2c;
     int64_t bytes;  // size of the packed table
     // work[0]: next point of the batched LK launch's work queue (reset to 0
@@ -135,8 +138,9 @@ __host__ __device__ inline size_t batch_entries_offset(int max_streams) {
     return (off + 15) & ~(size_t)15;
 }
 
-// The LK tensor maps follow the stream entries: stream s, level L, map m
-// at index (s * OMT_MAX_LEVELS + L) * LK_MAPS + m.
+// The LK tensor maps follow the stream entries: stream s, direction d
+// (0 forward, 1 backward), level L, map m at index
+// ((2 s + d) * OMT_MAX_LEVELS + L) * LK_MAPS + m.
 __host__ __device__ inline size_t batch_maps_offset(int max_streams) {
     const size_t off = batch_entries_offset(max_streams) + sizeof(StreamEntry) * (size_t)max_streams;
     return (off + 127) & ~(size_t)127;
@@ -144,7 +148,7 @@ __host__ __device__ inline size_t batch_maps_offset(int max_streams) {
 
 __host__ __device__ inline size_t batch_table_bytes(int max_streams) {
     return batch_maps_offset(max_streams) +
-           sizeof(CUtensorMap) * (size_t)max_streams * OMT_MAX_LEVELS * LK_MAPS;
+           sizeof(CUtensorMap) * (size_t)max_streams * 2 * OMT_MAX_LEVELS * LK_MAPS;
 }
 
 struct BatchView {
@@ -161,10 +165,10 @@ struct BatchView {
     __host__ __device__ const StreamEntry &stream(int s) const {
         return ((const StreamEntry *)(base + batch_entries_offset(hdr().max_streams)))[s];
     }
-    // stream s's LK maps, LK_MAPS per level
-    __host__ __device__ const CUtensorMap *maps(int s) const {
+    // stream s's LK maps of direction d (0 forward, 1 backward), LK_MAPS per level
+    __host__ __device__ const CUtensorMap *maps(int s, int d) const {
         return (const CUtensorMap *)(base + batch_maps_offset(hdr().max_streams)) +
-               (size_t)s * OMT_MAX_LEVELS * LK_MAPS;
+               (size_t)(2 * s + d) * OMT_MAX_LEVELS * LK_MAPS;
     }
 };
 
@@ -218,8 +222,15 @@ uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUt
 // Reads and clears the count of LK staging waits that hit their limit.
 cudaError_t lk_wait_timeouts_take(unsigned *count);
 
+// backward = 0: the LK phase (frame t -> t+1); 1: the backward run of the
+// forward-backward check (frame t+1 -> t from the forward results), each
+// point's check applied as it finishes.
 cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
-                            int ctas_per_sm, int chunk, cudaStream_t s);
+                            int ctas_per_sm, int chunk, int backward, cudaStream_t s);
+
+cudaError_t launch_fb_check(const float2 *pts, const float2 *pts_back, const uint8_t *status_back,
+                            int n_max, const int32_t *n_dev, float fb_max, uint8_t *status,
+                            cudaStream_t s);
 cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, cudaStream_t s);
 
 cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const float2 *pts,

@@ -27,8 +27,10 @@ EXPORTED = [
     "omt_version", "omt_select_corners_static", "omt_batch_table_bytes", "omt_batch_pack",
     "omt_batch_step", "omt_batch_upload", "omt_batch_phase", "omt_iou_matrix",
     "omt_assign_workspace_bytes", "omt_assign", "omt_update_tracks", "omt_lk_wait_timeouts",
+    "omt_fb_check",
 ]
-PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES = 0, 1, 2, 3
+PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES, PHASE_FB = 0, 1, 2, 3, 4
+PT_OK, PT_LOST_EIG, PT_LOST_OOB, PT_NONCONV, PT_LOST_FB = 1, 2, 4, 8, 16
 BATCH_MAX_STREAMS = 256
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -43,7 +45,7 @@ class Params(Structure):
     _fields_ = [("levels", c_int32), ("win", c_int32), ("max_iter", c_int32), ("eps", c_float),
                 ("min_eig", c_float), ("quality_num", c_int32), ("quality_den", c_int32),
                 ("min_dist", c_float), ("max_corners", c_int32), ("storage", c_int32),
-                ("aggregator", c_int32)]
+                ("aggregator", c_int32), ("fb_max", c_float)]
 
     def replace(self, **kw) -> "Params":
         p = Params()
@@ -72,7 +74,7 @@ class BatchStream(Structure):
                 ("max_corners", c_int32), ("scratch", c_void_p), ("scratch_bytes", c_size_t),
                 ("pts", c_void_p), ("pts_out", c_void_p), ("status", c_void_p),
                 ("iters", c_void_p), ("offsets", c_void_p), ("boxes_out", c_void_p),
-                ("nvalid", c_void_p)]
+                ("nvalid", c_void_p), ("pts_back", c_void_p), ("status_back", c_void_p)]
 
 
 class BatchCaps(Structure):
@@ -120,6 +122,8 @@ def lib():
         L.omt_update_tracks.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p]
         L.omt_lk_wait_timeouts.argtypes = [c_void_p]
+        L.omt_fb_check.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_float,
+                                   c_void_p, c_void_p]
         L.omt_batch_table_bytes.argtypes = [POINTER(BatchCaps)]
         L.omt_batch_table_bytes.restype = c_size_t
         L.omt_batch_pack.argtypes = [POINTER(BatchStream), c_int32, POINTER(Params),
@@ -253,6 +257,24 @@ def lk_track(prev: Pyramid, nxt: Pyramid, pts, params: Params, pts_out, status, 
     _check(lib().omt_lk_track(ctypes.byref(prev.desc), ctypes.byref(nxt.desc), _ptr(pts), n,
                               _ptr(n_dev), ctypes.byref(params), _ptr(pts_out), _ptr(status),
                               _ptr(iters), _stream(stream)), "omt_lk_track")
+
+
+def fb_check(pts, pts_back, status_back, fb_max: float, status, n_max=None, n_dev=None,
+             stream=None):
+    """Forward-backward check (device tensors): status[i] with OK becomes
+    LOST_FB unless status_back[i] has OK and |pts_back[i] - pts[i]| <= fb_max."""
+    n = pts.shape[0] if n_max is None else n_max
+    _check(lib().omt_fb_check(_ptr(pts), _ptr(pts_back), _ptr(status_back), n, _ptr(n_dev),
+                              float(fb_max), _ptr(status), _stream(stream)), "omt_fb_check")
+
+
+def lk_track_fb(prev: Pyramid, nxt: Pyramid, pts, params: Params, fb_max: float, pts_out, status,
+                pts_back, status_back, iters=None, n_max=None, n_dev=None, stream=None):
+    """Forward LK (prev -> nxt), backward LK from its results (nxt -> prev)
+    and the forward-backward check, as three calls on one stream."""
+    lk_track(prev, nxt, pts, params, pts_out, status, iters, n_max, n_dev, stream)
+    lk_track(nxt, prev, pts_out, params, pts_back, status_back, None, n_max, n_dev, stream)
+    fb_check(pts, pts_back, status_back, fb_max, status, n_max, n_dev, stream)
 
 
 def update_boxes(boxes, offsets, pts, pts_out, status, params: Params, boxes_out, nvalid=None,
@@ -439,6 +461,9 @@ class BatchTracker:
         dev = self.device
         self.pyr, self.frame, self.boxes, self.boxes_out = [], [], [], []
         self.pts, self.pts_out, self.status, self.iters, self.offsets, self.nvalid = [], [], [], [], [], []
+        # the backward run of the forward-backward check (params.fb_max >= 0)
+        self.fb = params.fb_max >= 0
+        self.pts_back, self.status_back = [], []
         self.scratch, self.nboxes = [], [0] * n
         # every stream's output boxes in one buffer, so one copy reads them all
         nbs = [max(1, nb) for nb in max_boxes]
@@ -455,6 +480,10 @@ class BatchTracker:
             self.pts.append(torch.zeros((cap, 2), dtype=torch.float32, device=dev))
             self.pts_out.append(torch.zeros((cap, 2), dtype=torch.float32, device=dev))
             self.status.append(torch.zeros(cap, dtype=torch.uint8, device=dev))
+            self.pts_back.append(torch.zeros((cap, 2), dtype=torch.float32, device=dev)
+                                 if self.fb else None)
+            self.status_back.append(torch.zeros(cap, dtype=torch.uint8, device=dev)
+                                    if self.fb else None)
             self.iters.append(torch.zeros((cap, params.levels), dtype=torch.uint8, device=dev)
                               if with_iters else None)
             self.offsets.append(torch.zeros(nb + 1, dtype=torch.int32, device=dev))
@@ -483,6 +512,8 @@ class BatchTracker:
         d.iters = self.iters[s].data_ptr() if self.iters[s] is not None else None
         d.offsets = self.offsets[s].data_ptr()
         d.boxes_out, d.nvalid = self.boxes_out[s].data_ptr(), self.nvalid[s].data_ptr()
+        if self.fb:
+            d.pts_back, d.status_back = self.pts_back[s].data_ptr(), self.status_back[s].data_ptr()
         return d
 
     def slot(self, s: int):
@@ -516,10 +547,14 @@ class BatchTracker:
             batch_phase(dt, self.caps, self.params, PHASE_CORNERS, self.side)
             main.wait_stream(self.side)
             batch_phase(dt, self.caps, self.params, PHASE_LK, main)
+            if self.fb:
+                batch_phase(dt, self.caps, self.params, PHASE_FB, main)
             batch_phase(dt, self.caps, self.params, PHASE_BOXES, main)
             return
         events = events or {}
-        for phase in (PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES):
+        phases = (PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK) + ((PHASE_FB,) if self.fb else ()) + \
+            (PHASE_BOXES,)
+        for phase in phases:
             ev = events.get(phase)
             if ev:
                 ev[0].record()
