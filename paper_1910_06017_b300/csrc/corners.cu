@@ -347,10 +347,36 @@ __device__ void bitonic_sort(uint64_t *keys, int N) {
 // Grid of accepted points over a box's eligible pixels: cells of side
 // `cell` with 2 (cell-1)^2 < md2c hold at most one accepted point each, so a
 // candidate only checks the cells within dmax pixels of itself.
+// The accepted points of a box, for the minimum-distance test: an
+// occupancy bitmap of the box's pixels when the test's disc is small and the
+// bitmap fits (bits), else a grid of cells holding an accepted point's index
+// (cells), else none (the whole list is checked).
 struct AccGrid {
-    int16_t *cells;  // nullptr: no grid (too many cells), check the whole list
+    uint32_t *bits;  // row r of the box: bits[r * wpr ...], bit c = column xlo + c
+    int16_t *cells;
     int gx, gy, xlo, ylo;
+    int nx, rows, wpr;
 };
+
+// Whether an accepted point lies within the minimum distance of (xr, yr)
+// (box-relative), from the occupancy bitmap: the rows |dy| <= dmax, in each
+// the columns with dx^2 + dy^2 < md2c.
+__device__ __forceinline__ bool bitmap_conflict(const AccGrid &g, int xr, int yr, int dmax,
+                                                int64_t md2c) {
+    for (int dy = -dmax; dy <= dmax; ++dy) {
+        const int r = yr + dy;
+        if (r < 0 || r >= g.rows) continue;
+        int dx = dmax;
+        while (dx > 0 && (int64_t)dx * dx + (int64_t)dy * dy >= md2c) --dx;
+        const int c0 = max(xr - dx, 0), c1 = min(xr + dx, g.nx - 1);
+        const uint32_t *row = g.bits + r * g.wpr;
+        const int w0 = c0 >> 5, w1 = c1 >> 5;  // c1 - c0 <= 14: at most two words
+        const uint64_t v = (uint64_t)row[w0] | (w1 != w0 ? (uint64_t)row[w1] << 32 : 0ull);
+        const uint64_t mask = ((1ull << (c1 - c0 + 1)) - 1ull) << (c0 & 31);
+        if (v & mask) return true;
+    }
+    return false;
+}
 
 // Greedy minimum-distance acceptance over the n largest keys of the sorted
 // array (descending order from index N-1), by warp 0.  nacc is shared.
@@ -367,10 +393,11 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
         const int y = (int)(idx / (uint32_t)a.w), x = (int)(idx - (uint32_t)y * (uint32_t)a.w);
         // a key always names a pixel of the box; anything else (a corrupted
         // input) is refused rather than indexing the grid out of range
-        bool ok = valid && x >= g.xlo && y >= g.ylo && x < g.xlo + g.gx * a.cell &&
-                  y < g.ylo + g.gy * a.cell;
+        bool ok = valid && x >= g.xlo && y >= g.ylo && x < g.xlo + g.nx && y < g.ylo + g.rows;
         if (ok && a.md2c > 0) {
-            if (g.cells) {
+            if (g.bits) {
+                ok = !bitmap_conflict(g, x - g.xlo, y - g.ylo, a.dmax, a.md2c);
+            } else if (g.cells) {
                 const int cx0 = max(x - a.dmax - g.xlo, 0) / a.cell;
                 const int cx1 = min((x + a.dmax - g.xlo) / a.cell, g.gx - 1);
                 const int cy0 = max(y - a.dmax - g.ylo, 0) / a.cell;
@@ -401,7 +428,9 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
             const int xs = __shfl_sync(FULL_MASK, x, src), ys = __shfl_sync(FULL_MASK, y, src);
             if (lane == 0) {
                 acc[nacc] = make_int2(xs, ys);
-                if (g.cells)
+                if (g.bits)
+                    g.bits[(ys - g.ylo) * g.wpr + ((xs - g.xlo) >> 5)] |= 1u << ((xs - g.xlo) & 31);
+                else if (g.cells)
                     g.cells[((ys - g.ylo) / a.cell) * g.gx + (xs - g.xlo) / a.cell] = (int16_t)nacc;
                 a.pad_pts[(int64_t)box * a.maxc + nacc] = make_float2((float)xs, (float)ys);
             }
@@ -530,8 +559,16 @@ __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
     g.ylo = ylo;
     g.gx = (nx + a.cell - 1) / a.cell;
     g.gy = (yhi - ylo + a.cell) / a.cell;
-    g.cells = (a.md2c > 0 && (int64_t)g.gx * g.gy <= GCAP) ? cells : nullptr;
-    if (g.cells)
+    g.nx = nx;
+    g.rows = yhi - ylo + 1;
+    g.wpr = (nx + 31) >> 5;
+    // the bitmap shares the grid's shared memory (GCAP int16 = GCAP / 2 words)
+    g.bits = (a.md2c > 0 && a.dmax <= 7 && (int64_t)g.wpr * g.rows <= GCAP / 2)
+                 ? (uint32_t *)cells : nullptr;
+    g.cells = (!g.bits && a.md2c > 0 && (int64_t)g.gx * g.gy <= GCAP) ? cells : nullptr;
+    if (g.bits)
+        for (int i = tid; i < g.wpr * g.rows; i += SNT) g.bits[i] = 0u;
+    else if (g.cells)
         for (int i = tid; i < g.gx * g.gy; i += SNT) g.cells[i] = -1;
 
     // One pass over the eligible pixels (a warp per row): R_max, and the keys
@@ -687,7 +724,7 @@ __global__ void __launch_bounds__(SNT) select_kernel(SelectArgs a) {
     select_box(a, blockIdx.x, a.maxc);
 }
 
-__global__ void __launch_bounds__(SNT) select_batch_kernel(const uint8_t *table, int acc_cap) {
+__global__ void __launch_bounds__(SNT, 8) select_batch_kernel(const uint8_t *table, int acc_cap) {
     const BatchView t(table);
     const BatchHeader &h = t.hdr();
     const int32_t *pre = t.box_prefix();
