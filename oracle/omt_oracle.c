@@ -451,11 +451,28 @@ static int dbl_cmp(const void *pa, const void *pb)
     return a < b ? -1 : (a > b);
 }
 
+/* Median of m doubles (sorted in place; even count: mean of the two middle
+ * values). */
+static double median_of(double *v, int m)
+{
+    qsort(v, m, sizeof(double), dbl_cmp);
+    return (m & 1) ? v[m / 2] : 0.5 * (v[m / 2 - 1] + v[m / 2]);
+}
+
+/* Points of the scale estimate: the first ORC_SCALE_POINTS OK points of a box
+ * in CSR order (the strongest corners come first). */
+#define ORC_SCALE_POINTS 64
+
 /* Section V-A prediction: each box moves by an aggregate of the displacements
- * of its tracked (OK) points; the size is kept.  aggregator 0 = median of dx
- * and of dy separately (even count: mean of the two middle values), 1 = mean
- * (the paper's choice).  offsets is the CSR of points per box (nboxes + 1).
- * A box with no OK point stays where it is and gets nvalid = 0. */
+ * of its tracked (OK) points.  aggregator 0 = median of dx and of dy
+ * separately (even count: mean of the two middle values), 1 = mean (the
+ * paper's choice); the size is kept.  aggregator 2 = the median displacement
+ * of 0 plus a scale (the median-flow estimate of Kalal, Mikolajczyk and
+ * Matas, 2010): the median over all pairs i < j of the box's first 64 OK
+ * points of |v_i - v_j| / |u_i - u_j| (pairs with u_i = u_j skipped; no pair:
+ * scale 1); the box is scaled by it about its centre, then moved.  offsets is
+ * the CSR of points per box (nboxes + 1).  A box with no OK point stays where
+ * it is and gets nvalid = 0. */
 void orc_update_boxes(const float *boxes, const int32_t *offsets, const float *pts,
                       const float *pts_out, const uint8_t *status, int nboxes, int aggregator,
                       double *boxes_out, int32_t *nvalid)
@@ -465,33 +482,62 @@ void orc_update_boxes(const float *boxes, const int32_t *offsets, const float *p
         int cap = hi > lo ? hi - lo : 1;
         double *dx = (double *)malloc(sizeof(double) * cap);
         double *dy = (double *)malloc(sizeof(double) * cap);
+        int *ok = (int *)malloc(sizeof(int) * cap);
         int m = 0;
         for (int i = lo; i < hi; ++i)
             if (status[i] & ORC_OK) {
                 dx[m] = (double)pts_out[2 * i] - (double)pts[2 * i];
                 dy[m] = (double)pts_out[2 * i + 1] - (double)pts[2 * i + 1];
+                ok[m] = i;
                 ++m;
             }
-        double mx = 0.0, my = 0.0;
+        double mx = 0.0, my = 0.0, scale = 1.0;
         if (m > 0) {
             if (aggregator == 1) {
                 for (int i = 0; i < m; ++i) { mx += dx[i]; my += dy[i]; }
                 mx /= m;
                 my /= m;
             } else {
-                qsort(dx, m, sizeof(double), dbl_cmp);
-                qsort(dy, m, sizeof(double), dbl_cmp);
-                if (m & 1) { mx = dx[m / 2]; my = dy[m / 2]; }
-                else { mx = 0.5 * (dx[m / 2 - 1] + dx[m / 2]); my = 0.5 * (dy[m / 2 - 1] + dy[m / 2]); }
+                mx = median_of(dx, m);
+                my = median_of(dy, m);
             }
         }
-        boxes_out[4 * bi + 0] = boxes[4 * bi + 0] + mx;
-        boxes_out[4 * bi + 1] = boxes[4 * bi + 1] + my;
-        boxes_out[4 * bi + 2] = boxes[4 * bi + 2] + mx;
-        boxes_out[4 * bi + 3] = boxes[4 * bi + 3] + my;
+        if (aggregator == 2) {
+            const int k = m < ORC_SCALE_POINTS ? m : ORC_SCALE_POINTS;
+            double *r = (double *)malloc(sizeof(double) * (k * (k - 1) / 2 + 1));
+            int nr = 0;
+            for (int a = 0; a < k; ++a)
+                for (int b = a + 1; b < k; ++b) {
+                    const int i = ok[a], j = ok[b];
+                    const double ux = (double)pts[2 * i] - pts[2 * j];
+                    const double uy = (double)pts[2 * i + 1] - pts[2 * j + 1];
+                    const double vx = (double)pts_out[2 * i] - pts_out[2 * j];
+                    const double vy = (double)pts_out[2 * i + 1] - pts_out[2 * j + 1];
+                    const double du = sqrt(ux * ux + uy * uy);
+                    if (du > 0.0) r[nr++] = sqrt(vx * vx + vy * vy) / du;
+                }
+            if (nr > 0) scale = median_of(r, nr);
+            free(r);
+        }
+        const double cx = 0.5 * ((double)boxes[4 * bi + 0] + boxes[4 * bi + 2]);
+        const double cy = 0.5 * ((double)boxes[4 * bi + 1] + boxes[4 * bi + 3]);
+        if (aggregator == 2) {
+            const double hw = 0.5 * ((double)boxes[4 * bi + 2] - boxes[4 * bi + 0]) * scale;
+            const double hh = 0.5 * ((double)boxes[4 * bi + 3] - boxes[4 * bi + 1]) * scale;
+            boxes_out[4 * bi + 0] = cx + mx - hw;
+            boxes_out[4 * bi + 1] = cy + my - hh;
+            boxes_out[4 * bi + 2] = cx + mx + hw;
+            boxes_out[4 * bi + 3] = cy + my + hh;
+        } else {
+            boxes_out[4 * bi + 0] = boxes[4 * bi + 0] + mx;
+            boxes_out[4 * bi + 1] = boxes[4 * bi + 1] + my;
+            boxes_out[4 * bi + 2] = boxes[4 * bi + 2] + mx;
+            boxes_out[4 * bi + 3] = boxes[4 * bi + 3] + my;
+        }
         nvalid[bi] = m;
         free(dx);
         free(dy);
+        free(ok);
     }
 }
 
