@@ -84,7 +84,8 @@ typedef struct omt_params {
     float min_dist;      /* corners keep dx^2 + dy^2 >= fl32(min_dist^2), >= 0    */
     int32_t max_corners; /* corners per box, 0..OMT_MAX_CORNERS                   */
     int32_t storage;     /* enum omt_storage                                      */
-    int32_t aggregator;  /* 0 = median (default), 1 = mean (the paper's choice)   */
+    int32_t aggregator;  /* 0 = median (default), 1 = mean (the paper's choice), */
+                         /*   2 = median + median-flow scale (omt_update_boxes)  */
     float fb_max;        /* batched steps: forward-backward check threshold in    */
                          /*   level-0 px (omt_fb_check); < 0 = off (default)     */
 } omt_params;
@@ -248,7 +249,12 @@ int omt_lk_track(const omt_pyramid *prev, const omt_pyramid *next, const float *
 /* Section V-A (prediction): every box moves by an aggregate of the
  * displacements pts_out - pts of its OK points; its size is kept.
  * prm->aggregator 0: per-axis median (even count: mean of the two middle
- * values); 1: mean.  A box without OK points keeps its place, nvalid = 0.
+ * values); 1: mean; 2: the median of 0 plus a scale, the median-flow
+ * estimate (Kalal, Mikolajczyk and Matas, 2010): the median over all pairs
+ * of the box's first 64 OK points (CSR order) of |v_i - v_j| / |u_i - u_j|
+ * (u = pts, v = pts_out; FP32; pairs with u_i = u_j skipped; no pair: 1),
+ * the box scaled by it about its centre, then moved.  A box without OK
+ * points keeps its place, nvalid = 0.
  *   boxes      device float4[nboxes]
  *   offsets    device int32[nboxes + 1] CSR into the point arrays
  *   pts, pts_out, status   device, as written by omt_lk_track

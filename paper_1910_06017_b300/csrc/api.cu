@@ -87,7 +87,7 @@ int omt_validate_params(const omt_params *p) {
     if (!(p->min_dist >= 0.0f) || !(p->min_dist <= 65536.0f)) return OMT_EINVAL;
     if (p->max_corners < 0 || p->max_corners > OMT_MAX_CORNERS) return OMT_EINVAL;
     if (p->storage != OMT_F32 && p->storage != OMT_F16) return OMT_EINVAL;
-    if (p->aggregator != 0 && p->aggregator != 1) return OMT_EINVAL;
+    if (p->aggregator < 0 || p->aggregator > 2) return OMT_EINVAL;
     if (p->fb_max != p->fb_max) return OMT_EINVAL;  // NaN
     return OMT_OK;
 }
@@ -352,7 +352,7 @@ int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt
             return from_cuda(launch_lk_batch(dt, prm->storage, prm->win, caps->lk_warps,
                                              caps->lk_ctas_per_sm, caps->lk_chunk, 0, s));
         case OMT_PHASE_BOXES:
-            return from_cuda(launch_update_boxes_batch(dt, caps->max_boxes, s));
+            return from_cuda(launch_update_boxes_batch(dt, caps->max_boxes, prm->aggregator, s));
         default:
             return OMT_EINVAL;
     }
@@ -366,7 +366,7 @@ int omt_batch_step(const void *table, const omt_batch_caps *caps, const omt_para
     if (h.levels != prm->levels || h.storage != prm->storage || h.win != prm->win ||
         h.max_iter != prm->max_iter)
         return OMT_EINVAL;
-    if (h.fb_max != prm->fb_max) return OMT_EINVAL;
+    if (h.fb_max != prm->fb_max || h.aggregator != prm->aggregator) return OMT_EINVAL;
     int rc = omt_batch_upload(table, caps, dev_table, dev_table_bytes, stream);
     static const int order[] = {OMT_PHASE_PYRAMID, OMT_PHASE_CORNERS, OMT_PHASE_LK, OMT_PHASE_FB,
                                 OMT_PHASE_BOXES};

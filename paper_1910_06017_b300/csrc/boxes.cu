@@ -7,6 +7,10 @@
 // FP32 displacements (four 8-bit digits, shared-memory histograms).  Neither
 // needs a sort or scratch; an even count averages the two middle values.  The mean flag sums
 // with a fixed per-thread stride and a fixed tree, so it is deterministic.
+// The median-flow scale (aggregator 2) takes the box's first 64 OK points in
+// CSR order (a block-wide ordered compaction), forms the ratios of their
+// pairwise distances after and before into shared memory, and picks their
+// median by the same radix select on the ratios' keys.
 #include "omt_internal.cuh"
 
 namespace omt {
@@ -36,6 +40,36 @@ __device__ __forceinline__ float disp(const BoxArgs &a, int i, int axis) {
     return axis == 0 ? a.pts_out[i].x - a.pts[i].x : a.pts_out[i].y - a.pts[i].y;
 }
 
+// Warp 0: the bin of a 256-bin histogram holding the element of rank k
+// (ascending), and k's rank inside it, by a warp scan.
+__device__ __forceinline__ void pick_bin(const unsigned *hist, int k, int *s_sel, int *s_k) {
+    const int lane = threadIdx.x;
+    unsigned c[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        c[j] = hist[lane * 8 + j];
+        sum += c[j];
+    }
+    unsigned inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL_MASK, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const unsigned exc = inc - sum;
+    if (exc <= (unsigned)k && (unsigned)k < inc) {
+        unsigned cum = exc;
+        for (int j = 0; j < 8; ++j) {
+            if (cum + c[j] > (unsigned)k) {
+                *s_sel = lane * 8 + j;
+                *s_k = k - (int)cum;
+                break;
+            }
+            cum += c[j];
+        }
+    }
+}
+
 // Value of rank k (0-based, ascending) among the OK displacements of [lo, hi),
 // for boxes too large for the shared-memory path: MSD radix select, with
 // the digit's bin found by a warp scan over the 256-bin histogram.
@@ -51,33 +85,7 @@ __device__ float select_rank(const BoxArgs &a, int lo, int hi, int axis, int k, 
             if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
         }
         __syncthreads();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            unsigned c[8], sum = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                c[j] = hist[lane * 8 + j];
-                sum += c[j];
-            }
-            unsigned inc = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned t = __shfl_up_sync(FULL_MASK, inc, o);
-                if (lane >= o) inc += t;
-            }
-            const unsigned exc = inc - sum;
-            if (exc <= (unsigned)k && (unsigned)k < inc) {
-                unsigned cum = exc;
-                for (int j = 0; j < 8; ++j) {
-                    if (cum + c[j] > (unsigned)k) {
-                        *s_sel = lane * 8 + j;
-                        *s_k = k - (int)cum;
-                        break;
-                    }
-                    cum += c[j];
-                }
-            }
-        }
+        if (threadIdx.x < 32) pick_bin(hist, k, s_sel, s_k);
         __syncthreads();
         prefix |= (uint32_t)*s_sel << shift;
         pmask |= 0xFFu << shift;
@@ -86,6 +94,33 @@ __device__ float select_rank(const BoxArgs &a, int lo, int hi, int axis, int k, 
     }
     return fval(prefix);
 }
+
+// Key of rank k (ascending) among n 32-bit keys in shared memory: MSD radix
+// select, four 8-bit digits.
+__device__ uint32_t smem_rank(const uint32_t *keys, int n, int k, unsigned *hist, int *s_sel,
+                              int *s_k) {
+    uint32_t prefix = 0, pmask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += BNT) hist[b] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += BNT) {
+            const uint32_t key = keys[i];
+            if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) pick_bin(hist, k, s_sel, s_k);
+        __syncthreads();
+        prefix |= (uint32_t)*s_sel << shift;
+        pmask |= 0xFFu << shift;
+        k = *s_k;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+// Points of the scale estimate: the box's first SCALE_POINTS OK points in CSR
+// order (the strongest corners come first).
+constexpr int SCALE_POINTS = 64;
 
 // Shared-memory path for boxes with at most SMALL OK points: gather the
 // displacements, then the element of rank k is the one with exactly k
@@ -108,7 +143,9 @@ __device__ float rank_pick(const float *v, int m, int k, float *s_out) {
     return out;
 }
 
-// Box b of one stream, whole CTA.
+// Box b of one stream, whole CTA.  SCALE: the median-flow scale of
+// aggregator 2 (compiled only into the kernels that launch for it).
+template <bool SCALE>
 __device__ void box_update_one(const BoxArgs &a, int b) {
     __shared__ unsigned hist[256];
     __shared__ float red[2][BNT / 32];
@@ -191,6 +228,65 @@ __device__ void box_update_one(const BoxArgs &a, int b) {
             }
         }
     }
+    if (SCALE && a.aggregator == 2) {
+        // median-flow scale: the median over all pairs of the first
+        // SCALE_POINTS OK points (in CSR order) of |v_i - v_j| / |u_i - u_j|
+        __shared__ int s_idx[SCALE_POINTS], wsum[BNT / 32], s_found;
+        __shared__ float2 su[SCALE_POINTS], sv[SCALE_POINTS];
+        if (tid == 0) s_found = 0;
+        __syncthreads();
+        for (int base = lo; base < hi; base += BNT) {
+            const int i = base + tid;
+            const bool ok = i < hi && (a.status[i] & OMT_PT_OK);
+            const unsigned bal = __ballot_sync(FULL_MASK, ok);
+            if (lane == 0) wsum[wid] = __popc(bal);
+            __syncthreads();
+            int before = s_found;
+            for (int w = 0; w < wid; ++w) before += wsum[w];
+            const int p = before + __popc(bal & ((1u << lane) - 1u));
+            if (ok && p < SCALE_POINTS) s_idx[p] = i;
+            __syncthreads();
+            if (tid == 0) {
+                int t = s_found;
+                for (int w = 0; w < BNT / 32; ++w) t += wsum[w];
+                s_found = t;
+            }
+            __syncthreads();
+            if (s_found >= SCALE_POINTS) break;
+        }
+        const int k = min(s_found, SCALE_POINTS);
+        for (int q = tid; q < k; q += BNT) {
+            su[q] = a.pts[s_idx[q]];
+            sv[q] = a.pts_out[s_idx[q]];
+        }
+        if (tid == 0) s_n = 0;
+        __syncthreads();
+        uint32_t *keys = (uint32_t *)vx;  // SCALE_POINTS^2 / 2 < SMALL ratios
+        for (int q = tid; q < SCALE_POINTS * SCALE_POINTS; q += BNT) {
+            const int i = q / SCALE_POINTS, j = q % SCALE_POINTS;
+            if (i >= j || j >= k) continue;
+            const float ux = su[i].x - su[j].x, uy = su[i].y - su[j].y;
+            const float vx2 = sv[i].x - sv[j].x, vy2 = sv[i].y - sv[j].y;
+            const float du = sqrtf(fmaf(ux, ux, uy * uy));
+            if (du > 0.f) keys[atomicAdd(&s_n, 1)] = fkey(sqrtf(fmaf(vx2, vx2, vy2 * vy2)) / du);
+        }
+        __syncthreads();
+        const int nr = s_n;
+        float scale = 1.f;
+        if (nr > 0) {
+            const int k1 = (nr - 1) / 2, k2 = nr / 2;
+            const float r1 = fval(smem_rank(keys, nr, k1, hist, &s_sel, &s_k));
+            scale = k2 != k1 ? 0.5f * (r1 + fval(smem_rank(keys, nr, k2, hist, &s_sel, &s_k))) : r1;
+        }
+        if (tid == 0) {
+            const float4 bx = a.boxes[b];
+            const float cx = 0.5f * (bx.x + bx.z) + mx, cy = 0.5f * (bx.y + bx.w) + my;
+            const float hw = 0.5f * (bx.z - bx.x) * scale, hh = 0.5f * (bx.w - bx.y) * scale;
+            a.boxes_out[b] = make_float4(cx - hw, cy - hh, cx + hw, cy + hh);
+            if (a.nvalid) a.nvalid[b] = total;
+        }
+        return;
+    }
     if (tid == 0) {
         const float4 bx = a.boxes[b];
         a.boxes_out[b] = make_float4(bx.x + mx, bx.y + my, bx.z + mx, bx.w + my);
@@ -198,8 +294,12 @@ __device__ void box_update_one(const BoxArgs &a, int b) {
     }
 }
 
-__global__ void __launch_bounds__(BNT) box_update_kernel(BoxArgs a) { box_update_one(a, blockIdx.x); }
+template <bool SCALE>
+__global__ void __launch_bounds__(BNT) box_update_kernel(BoxArgs a) {
+    box_update_one<SCALE>(a, blockIdx.x);
+}
 
+template <bool SCALE>
 __global__ void __launch_bounds__(BNT) box_update_batch_kernel(const uint8_t *table) {
     const BatchView t(table);
     const int32_t *pre = t.box_prefix();
@@ -209,7 +309,7 @@ __global__ void __launch_bounds__(BNT) box_update_batch_kernel(const uint8_t *ta
         const StreamEntry &e = t.stream(si);
         BoxArgs a{e.boxes, e.offsets, e.pts, e.pts_out, e.status, t.hdr().aggregator,
                   e.boxes_out, e.nvalid};
-        box_update_one(a, gb - pre[si]);
+        box_update_one<SCALE>(a, gb - pre[si]);
     }
 }
 
@@ -221,17 +321,20 @@ cudaError_t launch_update_boxes(const float4 *boxes, const int32_t *offsets, con
                                 cudaStream_t s) {
     if (nboxes <= 0) return cudaSuccess;
     BoxArgs a{boxes, offsets, pts, pts_out, status, aggregator, boxes_out, nvalid};
-    box_update_kernel<<<nboxes, BNT, 0, s>>>(a);
+    if (aggregator == 2) box_update_kernel<true><<<nboxes, BNT, 0, s>>>(a);
+    else box_update_kernel<false><<<nboxes, BNT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, cudaStream_t s) {
+cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, int aggregator,
+                                      cudaStream_t s) {
     if (max_boxes <= 0) return cudaSuccess;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = max_boxes < sms * 8 ? max_boxes : sms * 8;
-    box_update_batch_kernel<<<grid, BNT, 0, s>>>(table);
+    if (aggregator == 2) box_update_batch_kernel<true><<<grid, BNT, 0, s>>>(table);
+    else box_update_batch_kernel<false><<<grid, BNT, 0, s>>>(table);
     return cudaGetLastError();
 }
 

@@ -231,7 +231,8 @@ cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warp
 cudaError_t launch_fb_check(const float2 *pts, const float2 *pts_back, const uint8_t *status_back,
                             int n_max, const int32_t *n_dev, float fb_max, uint8_t *status,
                             cudaStream_t s);
-cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, cudaStream_t s);
+cudaError_t launch_update_boxes_batch(const uint8_t *table, int max_boxes, int aggregator,
+                                      cudaStream_t s);
 
 cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const float2 *pts,
                       int n_max, const int32_t *n_dev, const omt_params &prm, float2 *out,

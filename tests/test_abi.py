@@ -52,7 +52,8 @@ def test_default_params_are_valid():
                                          ("min_eig", -0.1), ("quality_den", 0),
                                          ("quality_num", -1), ("min_dist", -1.0),
                                          ("max_corners", -1), ("max_corners", 4097),
-                                         ("storage", 2), ("aggregator", 2)])
+                                         ("storage", 2), ("aggregator", 3), ("aggregator", -1),
+                                         ("fb_max", float("nan"))])
 def test_invalid_params_rejected(field, value):
     p = omt.default_params().replace(**{field: value})
     assert omt.validate_params(p) == omt.EINVAL
@@ -210,3 +211,37 @@ def test_batch_pack_validation():
     good = omt.BatchCaps(4, 100, 1920, 1080, 64, 8, 2, 16)
     assert omt.batch_table_bytes(good) == n
     assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n - 1) == omt.ENOMEM
+
+
+def test_batch_pack_forward_backward_arrays():
+    import numpy as np
+    caps = omt.BatchCaps(2, 100, 1920, 1080, 64)
+    n = omt.batch_table_bytes(caps)
+    table = np.zeros(n, np.uint8)
+    tp = ctypes.c_void_p(table.ctypes.data)
+    lib = omt.lib()
+    prm = omt.default_params(levels=3, max_corners=50, fb_max=0.5)
+    s = _fake_stream(720, 576, 10, 50, 1 << 32)
+    arr = (omt.BatchStream * 1)(s)
+    # the check needs its backward arrays
+    assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n) == omt.EINVAL
+    s.pts_back, s.status_back = (1 << 29) + (1 << 32) + (8 << 24), (1 << 29) + (1 << 32) + (9 << 24)
+    arr = (omt.BatchStream * 1)(s)
+    assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n) == omt.OK
+    s.pts_back += 4  # float2 array misaligned
+    arr = (omt.BatchStream * 1)(s)
+    assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n) == omt.EINVAL
+    # without the check they are not needed; a step must use the packed threshold
+    off = omt.default_params(levels=3, max_corners=50)
+    s = _fake_stream(720, 576, 10, 50, 1 << 32)
+    arr = (omt.BatchStream * 1)(s)
+    assert lib.omt_batch_pack(arr, 1, ctypes.byref(off), ctypes.byref(caps), tp, n) == omt.OK
+    assert lib.omt_batch_step(tp, ctypes.byref(caps), ctypes.byref(prm), ctypes.c_void_p(1 << 40),
+                              n, None) == omt.EINVAL
+    # omt_fb_check argument checks (host only)
+    fake = ctypes.c_void_p(1 << 30)
+    assert lib.omt_fb_check(fake, fake, fake, 10, None, ctypes.c_float(float("nan")), fake,
+                            None) == omt.EINVAL
+    assert lib.omt_fb_check(fake, fake, fake, -1, None, ctypes.c_float(1.0), fake, None) == omt.EINVAL
+    assert lib.omt_fb_check(None, None, None, 0, None, ctypes.c_float(1.0), None, None) == omt.OK
+    assert lib.omt_fb_check(None, fake, fake, 10, None, ctypes.c_float(1.0), fake, None) == omt.EINVAL
