@@ -688,3 +688,219 @@ void orc_fb_check(const float *pts, const double *pts_back, const uint8_t *statu
         if (!closes) status[i] = ORC_LOST_FB;
     }
 }
+
+/* ------------------------------------------------------ dense TV-L1 flow
+ * Section IV: the paper's flow engine is a dense TV-L1 motion field (L1 data
+ * term, total variation regularised with the Huber norm, solved by a
+ * projected (primal-dual) gradient scheme) on frames preprocessed by a
+ * structure-texture decomposition; Section V-A moves each box by the mean of
+ * the field inside it.  The paper gives no parameters; the readings are:
+ *   - structure S = the ROF denoising of I (min_S TV(S) + |S - I|^2 / (2 theta))
+ *     by Chambolle's dual projection, texture T = I - alpha S, stored as u8
+ *     clamp(floor(k T + 128 + 0.5), 0, 255);
+ *   - forward differences with zero at the last row / column for grad, the
+ *     negative adjoint (backward differences, zero outside) for div;
+ *   - per pyramid level, coarse to fine, the flow of the level above sampled
+ *     bilinearly at (x/2, y/2) and doubled (zero at the top), the duals
+ *     restarted at zero; per warp, I1 and its gradient sampled bilinearly at
+ *     x + u0 (taps clamped, as for LK), rho(u) = rho0 + grad I1w . u with
+ *     rho0 = I1w - grad I1w . u0 - I0, intensities scaled to [0, 1];
+ *   - per iteration (Chambolle-Pock, sigma = tau = 1/sqrt(8)):
+ *       p_d <- P(p_d + sigma grad ubar_d) / (1 + sigma eps), P the projection
+ *              onto the unit disc, for each flow component d separately;
+ *       u~ = u + tau div p;  u <- the pointwise prox of tau lambda |rho|:
+ *              u~ + tau lambda g if rho(u~) < -tau lambda |g|^2,
+ *              u~ - tau lambda g if rho(u~) > tau lambda |g|^2,
+ *              u~ - rho(u~) g / |g|^2 otherwise (u~ if g = 0), g = grad I1w;
+ *       ubar = 2 u - u_previous. */
+
+static void grad_fwd(const double *u, int w, int h, size_t x, size_t y, double *gx, double *gy)
+{
+    const size_t i = y * w + x;
+    *gx = (int)x + 1 < w ? u[i + 1] - u[i] : 0.0;
+    *gy = (int)y + 1 < h ? u[i + w] - u[i] : 0.0;
+}
+
+/* div of the dual field p (interleaved (px, py)) at (x, y). */
+static double div_bwd(const double *p, int w, int h, size_t x, size_t y)
+{
+    const size_t i = y * w + x;
+    double d = 0.0;
+    if ((int)x + 1 < w) d += p[2 * i];
+    if (x > 0) d -= p[2 * (i - 1)];
+    if ((int)y + 1 < h) d += p[2 * i + 1];
+    if (y > 0) d -= p[2 * (i - w) + 1];
+    return d;
+}
+
+/* ROF structure of I by Chambolle's projection (iters steps of 1/8), then
+ * the u8 texture.  I: the u8 frame (pitch bytes per row); structure: the
+ * w x h structure S (optional). */
+void orc_structure_texture(const uint8_t *frame, int w, int h, long pitch, double theta,
+                           double alpha, double k, int iters, uint8_t *texture, long tpitch,
+                           double *structure)
+{
+    const size_t n = (size_t)w * h;
+    double *I = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)calloc(2 * n, sizeof(double));
+    double *q = (double *)malloc(sizeof(double) * n);
+    double *pn = (double *)malloc(sizeof(double) * 2 * n);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) I[(size_t)y * w + x] = frame[(size_t)y * pitch + x];
+    const double step = 0.125;
+    for (int it = 0; it < iters; ++it) {
+        /* q = div p - I / theta, then p <- (p + step grad q) / (1 + step |grad q|) */
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) q[(size_t)y * w + x] = div_bwd(p, w, h, x, y) - I[(size_t)y * w + x] / theta;
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                double gx, gy;
+                grad_fwd(q, w, h, x, y, &gx, &gy);
+                const double m = 1.0 + step * sqrt(gx * gx + gy * gy);
+                const size_t i = (size_t)y * w + x;
+                pn[2 * i] = (p[2 * i] + step * gx) / m;
+                pn[2 * i + 1] = (p[2 * i + 1] + step * gy) / m;
+            }
+        memcpy(p, pn, sizeof(double) * 2 * n);
+    }
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            const size_t i = (size_t)y * w + x;
+            const double S = I[i] - theta * div_bwd(p, w, h, x, y);
+            if (structure) structure[i] = S;
+            const double T = floor(k * (I[i] - alpha * S) + 128.0 + 0.5);
+            texture[(size_t)y * tpitch + x] = (uint8_t)(T < 0.0 ? 0.0 : (T > 255.0 ? 255.0 : T));
+        }
+    free(I); free(p); free(q); free(pn);
+}
+
+/* Dense Huber-TV-L1 flow from frame t (P0) to t+1 (P1), packed pyramids as
+ * orc_pyramid writes them, into flow (w x h interleaved (u1, u2), level-0
+ * pixels). */
+void orc_tvl1(const double *img0, const double *img1, const double *grad1, int w, int h,
+              int levels, double lambda, double eps, int warps, int iters, double *flow)
+{
+    const double sigma = 1.0 / sqrt(8.0), tau = 1.0 / sqrt(8.0), s255 = 1.0 / 255.0;
+    size_t off[64];
+    int lw_[64], lh_[64];
+    size_t o = 0;
+    for (int l = 0; l < levels; ++l) {
+        orc_level_size(w, h, l, &lw_[l], &lh_[l]);
+        off[l] = o;
+        o += (size_t)lw_[l] * lh_[l];
+    }
+    double *u = NULL;  /* flow of the level above, interleaved */
+    for (int L = levels - 1; L >= 0; --L) {
+        const int lw = lw_[L], lh = lh_[L];
+        const size_t n = (size_t)lw * lh;
+        const double *I0 = img0 + off[L], *I1 = img1 + off[L], *G1 = grad1 + 2 * off[L];
+        double *uc = (double *)calloc(2 * n, sizeof(double));
+        if (u) {
+            const int cw = lw_[L + 1], ch = lh_[L + 1];
+            for (int y = 0; y < lh; ++y)
+                for (int x = 0; x < lw; ++x) {
+                    const double cx = 0.5 * x, cy = 0.5 * y;
+                    const int ix = (int)floor(cx), iy = (int)floor(cy);
+                    const double a = cx - ix, b = cy - iy;
+                    const size_t i = (size_t)y * lw + x;
+                    uc[2 * i] = 2.0 * bilin(u, 2, 0, cw, ch, ix, iy, a, b);
+                    uc[2 * i + 1] = 2.0 * bilin(u, 2, 1, cw, ch, ix, iy, a, b);
+                }
+            free(u);
+        }
+        u = uc;
+        double *p = (double *)malloc(sizeof(double) * 4 * n);   /* (p1x, p1y, p2x, p2y) */
+        double *ub = (double *)malloc(sizeof(double) * 2 * n);
+        double *uold = (double *)malloc(sizeof(double) * 2 * n);
+        double *gw = (double *)malloc(sizeof(double) * 2 * n);  /* grad I1 at x + u0, scaled */
+        double *r0 = (double *)malloc(sizeof(double) * n);
+        double *p1 = (double *)malloc(sizeof(double) * 2 * n), *p2 = (double *)malloc(sizeof(double) * 2 * n);
+        double *comp = (double *)malloc(sizeof(double) * n);
+        for (size_t i = 0; i < 4 * n; ++i) p[i] = 0.0;
+        for (int wp = 0; wp < warps; ++wp) {
+            for (int y = 0; y < lh; ++y)
+                for (int x = 0; x < lw; ++x) {
+                    const size_t i = (size_t)y * lw + x;
+                    const double sx = x + u[2 * i], sy = y + u[2 * i + 1];
+                    const int ix = (int)floor(sx), iy = (int)floor(sy);
+                    const double a = sx - ix, b = sy - iy;
+                    const double I1w = bilin(I1, 1, 0, lw, lh, ix, iy, a, b) * s255;
+                    const double gx = bilin(G1, 2, 0, lw, lh, ix, iy, a, b) * s255;
+                    const double gy = bilin(G1, 2, 1, lw, lh, ix, iy, a, b) * s255;
+                    gw[2 * i] = gx;
+                    gw[2 * i + 1] = gy;
+                    r0[i] = I1w - gx * u[2 * i] - gy * u[2 * i + 1] - I0[i] * s255;
+                }
+            memcpy(ub, u, sizeof(double) * 2 * n);
+            for (int it = 0; it < iters; ++it) {
+                /* dual step, each flow component on its own */
+                for (int d = 0; d < 2; ++d) {
+                    for (size_t i = 0; i < n; ++i) comp[i] = ub[2 * i + d];
+                    for (int y = 0; y < lh; ++y)
+                        for (int x = 0; x < lw; ++x) {
+                            const size_t i = (size_t)y * lw + x;
+                            double gx, gy;
+                            grad_fwd(comp, lw, lh, x, y, &gx, &gy);
+                            double qx = (p[4 * i + 2 * d] + sigma * gx) / (1.0 + sigma * eps);
+                            double qy = (p[4 * i + 2 * d + 1] + sigma * gy) / (1.0 + sigma * eps);
+                            const double m = sqrt(qx * qx + qy * qy);
+                            if (m > 1.0) { qx /= m; qy /= m; }
+                            p[4 * i + 2 * d] = qx;
+                            p[4 * i + 2 * d + 1] = qy;
+                        }
+                }
+                /* primal step: u~ = u + tau div p, then the data prox */
+                for (size_t i = 0; i < n; ++i) {
+                    p1[2 * i] = p[4 * i]; p1[2 * i + 1] = p[4 * i + 1];
+                    p2[2 * i] = p[4 * i + 2]; p2[2 * i + 1] = p[4 * i + 3];
+                }
+                memcpy(uold, u, sizeof(double) * 2 * n);
+                for (int y = 0; y < lh; ++y)
+                    for (int x = 0; x < lw; ++x) {
+                        const size_t i = (size_t)y * lw + x;
+                        const double t1 = u[2 * i] + tau * div_bwd(p1, lw, lh, x, y);
+                        const double t2 = u[2 * i + 1] + tau * div_bwd(p2, lw, lh, x, y);
+                        const double gx = gw[2 * i], gy = gw[2 * i + 1];
+                        const double g2 = gx * gx + gy * gy;
+                        const double rho = r0[i] + gx * t1 + gy * t2;
+                        const double th = tau * lambda * g2;
+                        double v1 = t1, v2 = t2;
+                        if (rho < -th) { v1 = t1 + tau * lambda * gx; v2 = t2 + tau * lambda * gy; }
+                        else if (rho > th) { v1 = t1 - tau * lambda * gx; v2 = t2 - tau * lambda * gy; }
+                        else if (g2 > 0.0) { v1 = t1 - rho * gx / g2; v2 = t2 - rho * gy / g2; }
+                        u[2 * i] = v1;
+                        u[2 * i + 1] = v2;
+                    }
+                for (size_t i = 0; i < 2 * n; ++i) ub[i] = 2.0 * u[i] - uold[i];
+            }
+        }
+        free(p); free(ub); free(uold); free(gw); free(r0); free(p1); free(p2); free(comp);
+    }
+    memcpy(flow, u, sizeof(double) * 2 * (size_t)w * h);
+    free(u);
+}
+
+/* Section V-A prediction with the dense field: each box moves by the mean
+ * flow over the pixels whose centres lie in it (x0 <= x < x1, y0 <= y < y1,
+ * inside the frame); a box without such pixels stays. */
+void orc_box_mean_flow(const double *flow, int w, int h, const float *boxes, int nboxes,
+                       double *boxes_out)
+{
+    for (int b = 0; b < nboxes; ++b) {
+        const double x0 = boxes[4 * b], y0 = boxes[4 * b + 1], x1 = boxes[4 * b + 2], y1 = boxes[4 * b + 3];
+        double sx = 0.0, sy = 0.0;
+        long cnt = 0;
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x)
+                if (x >= x0 && x < x1 && y >= y0 && y < y1) {
+                    sx += flow[2 * ((size_t)y * w + x)];
+                    sy += flow[2 * ((size_t)y * w + x) + 1];
+                    ++cnt;
+                }
+        const double mx = cnt ? sx / cnt : 0.0, my = cnt ? sy / cnt : 0.0;
+        boxes_out[4 * b] = x0 + mx;
+        boxes_out[4 * b + 1] = y0 + my;
+        boxes_out[4 * b + 2] = x1 + mx;
+        boxes_out[4 * b + 3] = y1 + my;
+    }
+}

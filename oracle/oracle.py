@@ -63,6 +63,13 @@ def lib():
                                        POINTER(c_double), POINTER(c_int32)]
         L.orc_fb_check.argtypes = [POINTER(c_float), POINTER(c_double), POINTER(c_uint8), c_int,
                                    c_double, POINTER(c_uint8)]
+        L.orc_structure_texture.argtypes = [POINTER(c_uint8), c_int, c_int, c_long, c_double,
+                                            c_double, c_double, c_int, POINTER(c_uint8), c_long,
+                                            POINTER(c_double)]
+        L.orc_tvl1.argtypes = [POINTER(c_double), POINTER(c_double), POINTER(c_double), c_int, c_int,
+                               c_int, c_double, c_double, c_int, c_int, POINTER(c_double)]
+        L.orc_box_mean_flow.argtypes = [POINTER(c_double), c_int, c_int, POINTER(c_float), c_int,
+                                        POINTER(c_double)]
         L.orc_max_threads.restype = c_int
         _lib = L
     return _lib
@@ -201,6 +208,44 @@ def lk_track_fb(prev: Pyramid, nxt: Pyramid, pts, fb_max: float, **kw):
     out, st = lk_track(prev, nxt, pts, **kw)
     back, sb = lk_track(nxt, prev, out.astype(np.float32), **kw)
     return out, fb_check(pts, back, sb, st, fb_max), back, sb
+
+
+# Section IV readings of the dense flow engine (see omt_oracle.c)
+ST_THETA, ST_ALPHA, ST_K, ST_ITERS = 0.125, 0.95, 2.0, 100
+TVL1_LAMBDA, TVL1_EPS, TVL1_WARPS, TVL1_ITERS = 10.0, 0.05, 3, 30
+
+
+def structure_texture(frame, theta=ST_THETA, alpha=ST_ALPHA, k=ST_K, iters=ST_ITERS,
+                      with_structure: bool = False):
+    """u8 texture image of a u8 frame (ROF structure removed)[, structure]."""
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    h, w = f.shape
+    out = np.zeros((h, w), np.uint8)
+    S = np.zeros((h, w), np.float64) if with_structure else None
+    lib().orc_structure_texture(_p(f, c_uint8), w, h, w, float(theta), float(alpha), float(k),
+                                int(iters), _p(out, c_uint8), w, _p(S, c_double))
+    return (out, S) if with_structure else out
+
+
+def tvl1(prev: Pyramid, nxt: Pyramid, lam=TVL1_LAMBDA, eps=TVL1_EPS, warps=TVL1_WARPS,
+         iters=TVL1_ITERS):
+    """Dense flow (h, w, 2) float64 from prev to nxt, level-0 pixels."""
+    assert prev.w == nxt.w and prev.h == nxt.h and prev.levels == nxt.levels
+    out = np.zeros((prev.h, prev.w, 2), np.float64)
+    lib().orc_tvl1(_p(prev.img_flat, c_double), _p(nxt.img_flat, c_double),
+                   _p(nxt.grad_flat, c_double), prev.w, prev.h, prev.levels, float(lam),
+                   float(eps), int(warps), int(iters), _p(out, c_double))
+    return out
+
+
+def box_mean_flow(flow, boxes):
+    """Boxes moved by the mean flow over their pixels: (nboxes, 4) float64."""
+    fl = np.ascontiguousarray(flow, dtype=np.float64)
+    h, w = fl.shape[:2]
+    b = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 4)
+    out = np.zeros((b.shape[0], 4), np.float64)
+    lib().orc_box_mean_flow(_p(fl, c_double), w, h, _p(b, c_float), b.shape[0], _p(out, c_double))
+    return out
 
 
 def iou_matrix(a, b):
