@@ -372,6 +372,62 @@ int omt_batch_upload(const void *table, const omt_batch_caps *caps, void *dev_ta
 int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt_params *prm,
                     int32_t phase, void *stream);
 
+/* ------------------------------------------------- dense flow engine
+ * Section IV: the paper's flow is a dense TV-L1 field (L1 data term, total
+ * variation with the Huber norm, a primal-dual projected gradient scheme)
+ * on frames preprocessed by a structure-texture decomposition; Section V-A
+ * moves each box by the mean of the field inside it.  The paper gives no
+ * parameters; omt_default_flow_params holds the readings used here. */
+typedef struct omt_flow_params {
+    float st_theta;   /* ROF weight of the structure (Chambolle's projection)   */
+    float st_alpha;   /* texture = I - st_alpha * structure                      */
+    float st_k;       /* u8 texture = clamp(floor(st_k * texture + 128.5))       */
+    int32_t st_iters; /* projection steps (step 1/8), >= 0                      */
+    float lambda;     /* weight of the L1 data term (intensities scaled to [0,1])*/
+    float eps;        /* Huber parameter of the total variation, >= 0           */
+    int32_t warps;    /* warps per pyramid level, >= 1                          */
+    int32_t iters;    /* primal-dual iterations per warp, >= 1                  */
+} omt_flow_params;
+
+/* Defaults: st_theta 1/8, st_alpha 0.95, st_k 2, 100 steps; lambda 10,
+ * eps 0.05, 3 warps, 30 iterations. */
+void omt_default_flow_params(omt_flow_params *p);
+
+/* Device scratch bytes of omt_structure_texture / omt_tvl1_flow. */
+size_t omt_structure_texture_scratch_bytes(int32_t w, int32_t h);
+size_t omt_tvl1_scratch_bytes(int32_t w, int32_t h);
+
+/* The u8 texture image of a u8 frame (device, h rows of pitch bytes) into
+ * texture (device, h rows of tpitch >= w bytes): the ROF structure S by
+ * st_iters steps of Chambolle's dual projection (forward differences, zero
+ * at the last row and column; the divergence their negative adjoint), then
+ * clamp(floor(st_k (I - st_alpha S) + 128.5), 0, 255), all in FP32.
+ * scratch: device, >= omt_structure_texture_scratch_bytes.  Asynchronous. */
+int omt_structure_texture(const uint8_t *frame, int32_t w, int32_t h, size_t pitch,
+                          const omt_flow_params *fp, uint8_t *texture, size_t tpitch,
+                          void *scratch, size_t scratch_bytes, void *stream);
+
+/* Dense Huber-TV-L1 flow from prev (frame t) to next (frame t+1), pyramids
+ * of the same shape in OMT_F32 storage (built by omt_build_pyramid, e.g. of
+ * texture images), into flow (device float2[w * h], level-0 px, row-major).
+ * Per level, coarse to fine: the flow of the level above sampled bilinearly
+ * at (x/2, y/2) and doubled (zero at the top), the duals restarted at zero;
+ * per warp, frame t+1 and its gradient sampled bilinearly at x + u0 (taps
+ * clamped); per iteration (sigma = tau = 1/sqrt(8)) the duals of each flow
+ * component p <- P((p + sigma grad ubar) / (1 + sigma eps)), P the
+ * projection onto the unit disc, then u <- the pointwise prox of
+ * tau lambda |rho| at u + tau div p, ubar = 2 u - u_previous.
+ * scratch: device, >= omt_tvl1_scratch_bytes.  Asynchronous. */
+int omt_tvl1_flow(const omt_pyramid *prev, const omt_pyramid *next, const omt_flow_params *fp,
+                  float *flow, void *scratch, size_t scratch_bytes, void *stream);
+
+/* Section V-A prediction from the dense field: box b moves by the mean flow
+ * over the pixels x0 <= x < x1, y0 <= y < y1 of the frame (a box without
+ * such pixels stays).  flow: device float2[w * h]; boxes, boxes_out: device
+ * float4[nboxes], 16-byte aligned.  Asynchronous. */
+int omt_box_mean_flow(const float *flow, int32_t w, int32_t h, const float *boxes,
+                      int32_t nboxes, float *boxes_out, void *stream);
+
 /* ------------------------------------------------- matching and update
  * Section V-A, matching phase: the predicted scene objects S_t are matched
  * against the detections D_t by a globally optimal assignment (the

@@ -394,6 +394,71 @@ int omt_fb_check(const float *pts, const float *pts_back, const uint8_t *status_
                                      n_max, n_dev, fb_max, status, (cudaStream_t)stream));
 }
 
+void omt_default_flow_params(omt_flow_params *p) {
+    if (!p) return;
+    p->st_theta = 0.125f;
+    p->st_alpha = 0.95f;
+    p->st_k = 2.0f;
+    p->st_iters = 100;
+    p->lambda = 10.0f;
+    p->eps = 0.05f;
+    p->warps = 3;
+    p->iters = 30;
+}
+
+namespace {
+bool flow_params_ok(const omt_flow_params *p) {
+    return p && p->st_theta > 0.0f && isfinite(p->st_theta) && isfinite(p->st_alpha) &&
+           isfinite(p->st_k) && p->st_iters >= 0 && p->st_iters <= 100000 && p->lambda >= 0.0f &&
+           isfinite(p->lambda) && p->eps >= 0.0f && isfinite(p->eps) && p->warps >= 1 &&
+           p->warps <= 100 && p->iters >= 1 && p->iters <= 100000;
+}
+}  // namespace
+
+size_t omt_structure_texture_scratch_bytes(int32_t w, int32_t h) {
+    if (w < 1 || h < 1 || w > (1 << 16) || h > (1 << 16)) return 0;
+    return st_scratch_bytes(w, h);
+}
+
+size_t omt_tvl1_scratch_bytes(int32_t w, int32_t h) {
+    if (w < 1 || h < 1 || w > (1 << 16) || h > (1 << 16)) return 0;
+    return tvl1_scratch_bytes(w, h);
+}
+
+int omt_structure_texture(const uint8_t *frame, int32_t w, int32_t h, size_t pitch,
+                          const omt_flow_params *fp, uint8_t *texture, size_t tpitch,
+                          void *scratch, size_t scratch_bytes, void *stream) {
+    if (!flow_params_ok(fp) || !frame || !texture || !scratch || w < 1 || h < 1 ||
+        w > (1 << 16) || h > (1 << 16) || pitch < (size_t)w || tpitch < (size_t)w)
+        return OMT_EINVAL;
+    if (scratch_bytes < st_scratch_bytes(w, h)) return OMT_ENOMEM;
+    return from_cuda(launch_structure_texture(frame, w, h, pitch, *fp, texture, tpitch, scratch,
+                                              (cudaStream_t)stream));
+}
+
+int omt_tvl1_flow(const omt_pyramid *prev, const omt_pyramid *next, const omt_flow_params *fp,
+                  float *flow, void *scratch, size_t scratch_bytes, void *stream) {
+    if (!flow_params_ok(fp) || !pyr_ok(prev) || !pyr_ok(next) || !flow || !scratch ||
+        !aligned(flow, 8))
+        return OMT_EINVAL;
+    if (prev->w != next->w || prev->h != next->h || prev->levels != next->levels ||
+        prev->storage != OMT_F32 || next->storage != OMT_F32 || prev->base == next->base)
+        return OMT_EINVAL;
+    if (scratch_bytes < tvl1_scratch_bytes(prev->w, prev->h)) return OMT_ENOMEM;
+    return from_cuda(launch_tvl1(*prev, *next, *fp, (float2 *)flow, scratch, (cudaStream_t)stream));
+}
+
+int omt_box_mean_flow(const float *flow, int32_t w, int32_t h, const float *boxes, int32_t nboxes,
+                      float *boxes_out, void *stream) {
+    if (nboxes < 0 || w < 1 || h < 1) return OMT_EINVAL;
+    if (nboxes == 0) return OMT_OK;
+    if (!flow || !boxes || !boxes_out || !aligned(flow, 8) || !aligned(boxes, 16) ||
+        !aligned(boxes_out, 16) || boxes == boxes_out)
+        return OMT_EINVAL;
+    return from_cuda(launch_box_mean_flow((const float2 *)flow, w, h, (const float4 *)boxes,
+                                          nboxes, (float4 *)boxes_out, (cudaStream_t)stream));
+}
+
 int omt_lk_wait_timeouts(uint32_t *count) {
     if (!count) return OMT_EINVAL;
     unsigned c = 0;

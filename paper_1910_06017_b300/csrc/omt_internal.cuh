@@ -228,6 +228,16 @@ cudaError_t lk_wait_timeouts_take(unsigned *count);
 cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
                             int ctas_per_sm, int chunk, int backward, cudaStream_t s);
 
+size_t st_scratch_bytes(int w, int h);
+size_t tvl1_scratch_bytes(int w, int h);
+cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t pitch,
+                                     const omt_flow_params &fp, uint8_t *tex, size_t tpitch,
+                                     void *scratch, cudaStream_t s);
+cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_flow_params &fp,
+                        float2 *flow, void *scratch, cudaStream_t s);
+cudaError_t launch_box_mean_flow(const float2 *flow, int w, int h, const float4 *boxes,
+                                 int nboxes, float4 *out, cudaStream_t s);
+
 cudaError_t launch_fb_check(const float2 *pts, const float2 *pts_back, const uint8_t *status_back,
                             int n_max, const int32_t *n_dev, float fb_max, uint8_t *status,
                             cudaStream_t s);

@@ -1,0 +1,375 @@
+// tvl1.cu -- the paper's dense flow engine (Section IV) and the mean-in-box
+// prediction (Section V-A).
+//
+// Structure-texture: the ROF structure S of the u8 frame by Chambolle's dual
+// projection (one launch per iteration, dual field ping-ponged in global
+// memory), then the u8 texture clamp(floor(k (I - alpha S) + 128.5)).
+// Huber-TV-L1: per pyramid level (FP32 storage, coarse to fine) the flow of
+// the level above is sampled bilinearly at (x/2, y/2) and doubled; per warp
+// one launch samples frame t+1 and its gradient at x + u0 (taps clamped) and
+// stores grad I1w and rho0, then every primal-dual iteration is two
+// launches: the duals from the extrapolated flow (forward differences, a
+// Huber shrink and the projection onto the unit disc, per flow component)
+// and the flow (backward-difference divergence, the pointwise prox of the
+// L1 data term, the extrapolation).  Every expression keeps the order of
+// the definition, in FP32.  Each iteration reads and writes every field
+// once: the iteration kernels are bound by HBM (or L2 for small levels).
+#include "omt_internal.cuh"
+
+namespace omt {
+namespace {
+
+constexpr int TBX = 32, TBY = 8;
+
+__device__ __forceinline__ float2 grad_fwd(const float *u, int stride, int w, int h, int x, int y) {
+    const int64_t i = (int64_t)y * stride + x;
+    return make_float2(x + 1 < w ? u[i + 1] - u[i] : 0.f, y + 1 < h ? u[i + stride] - u[i] : 0.f);
+}
+
+// div of an interleaved dual field (px, py), component c of cc, at (x, y).
+__device__ __forceinline__ float div_bwd(const float *p, int cc, int c, int w, int h, int x, int y) {
+    const int64_t i = (int64_t)y * w + x;
+    float d = 0.f;
+    if (x + 1 < w) d += p[i * cc + c];
+    if (x > 0) d -= p[(i - 1) * cc + c];
+    if (y + 1 < h) d += p[i * cc + c + 1];
+    if (y > 0) d -= p[(i - w) * cc + c + 1];
+    return d;
+}
+
+// ------------------------------------------------------ structure-texture
+struct StArgs {
+    const uint8_t *img;
+    int64_t pitch;
+    int w, h;
+    float theta, step;
+    const float *p;  // (px, py) interleaved, w x h
+    float *p_out;
+    float *q;        // w x h scratch: div p - I / theta
+};
+
+__global__ void st_q_kernel(StArgs a) {
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+    if (x >= a.w || y >= a.h) return;
+    a.q[(int64_t)y * a.w + x] =
+        div_bwd(a.p, 2, 0, a.w, a.h, x, y) - (float)a.img[(int64_t)y * a.pitch + x] / a.theta;
+}
+
+__global__ void st_p_kernel(StArgs a) {
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+    if (x >= a.w || y >= a.h) return;
+    const float2 g = grad_fwd(a.q, a.w, a.w, a.h, x, y);
+    const float m = 1.f + a.step * sqrtf(g.x * g.x + g.y * g.y);
+    const int64_t i = (int64_t)y * a.w + x;
+    a.p_out[2 * i] = (a.p[2 * i] + a.step * g.x) / m;
+    a.p_out[2 * i + 1] = (a.p[2 * i + 1] + a.step * g.y) / m;
+}
+
+__global__ void st_texture_kernel(StArgs a, float alpha, float k, uint8_t *tex, int64_t tpitch) {
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+    if (x >= a.w || y >= a.h) return;
+    const float I = (float)a.img[(int64_t)y * a.pitch + x];
+    const float S = I - a.theta * div_bwd(a.p, 2, 0, a.w, a.h, x, y);
+    const float T = floorf(k * (I - alpha * S) + 128.0f + 0.5f);
+    tex[(int64_t)y * tpitch + x] = (uint8_t)(T < 0.f ? 0.f : (T > 255.f ? 255.f : T));
+}
+
+// --------------------------------------------------------------- TV-L1
+// Bilinear sample of channel c of a cc-channel float plane at (ix + a, iy + b),
+// taps clamped to the plane.
+__device__ __forceinline__ float bilin(const float *P, int64_t stride, int cc, int c, int w, int h,
+                                       int ix, int iy, float a, float b) {
+    const int x0 = clampi(ix, 0, w - 1), x1 = clampi(ix + 1, 0, w - 1);
+    const int y0 = clampi(iy, 0, h - 1), y1 = clampi(iy + 1, 0, h - 1);
+    return (1.f - a) * (1.f - b) * P[y0 * stride + x0 * cc + c] +
+           a * (1.f - b) * P[y0 * stride + x1 * cc + c] +
+           (1.f - a) * b * P[y1 * stride + x0 * cc + c] + a * b * P[y1 * stride + x1 * cc + c];
+}
+
+// Level image texel as float (level 0: u8; F32 storage above).
+struct LevelF {
+    const uint8_t *img;
+    const float *grad;   // (Ix, Iy) interleaved
+    int64_t img_pitch, grad_pitch;  // bytes
+    int w, h;
+    bool u8;
+};
+
+__device__ __forceinline__ float level_texel(const LevelF &L, int x, int y) {
+    const uint8_t *row = L.img + (int64_t)y * L.img_pitch;
+    return L.u8 ? (float)row[x] : ((const float *)row)[x];
+}
+
+__device__ __forceinline__ float level_bilin(const LevelF &L, int ix, int iy, float a, float b) {
+    const int x0 = clampi(ix, 0, L.w - 1), x1 = clampi(ix + 1, 0, L.w - 1);
+    const int y0 = clampi(iy, 0, L.h - 1), y1 = clampi(iy + 1, 0, L.h - 1);
+    return (1.f - a) * (1.f - b) * level_texel(L, x0, y0) + a * (1.f - b) * level_texel(L, x1, y0) +
+           (1.f - a) * b * level_texel(L, x0, y1) + a * b * level_texel(L, x1, y1);
+}
+
+struct FlowLevel {
+    int w, h;
+    float2 *u, *ub, *uold;   // flow, extrapolated flow, previous flow
+    float4 *p;               // (p1x, p1y, p2x, p2y)
+    float2 *gw;              // grad I1 at x + u0, scaled to [0, 1] intensities
+    float *r0;
+};
+
+__global__ void upsample_kernel(const float2 *coarse, int cw, int ch, float2 *u, int w, int h) {
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+    if (x >= w || y >= h) return;
+    float2 v = make_float2(0.f, 0.f);
+    if (coarse) {
+        const float cx = 0.5f * x, cy = 0.5f * y;
+        const int ix = (int)floorf(cx), iy = (int)floorf(cy);
+        const float a = cx - ix, b = cy - iy;
+        const float *c = (const float *)coarse;
+        v.x = 2.0f * bilin(c, 2 * (int64_t)cw, 2, 0, cw, ch, ix, iy, a, b);
+        v.y = 2.0f * bilin(c, 2 * (int64_t)cw, 2, 1, cw, ch, ix, iy, a, b);
+    }
+    u[(int64_t)y * w + x] = v;
+}
+
+__global__ void warp_kernel(FlowLevel f, LevelF I0, LevelF I1) {
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+    if (x >= f.w || y >= f.h) return;
+    const int64_t i = (int64_t)y * f.w + x;
+    const float s255 = 1.0f / 255.0f;
+    const float2 u0 = f.u[i];
+    const float sx = x + u0.x, sy = y + u0.y;
+    const int ix = (int)floorf(sx), iy = (int)floorf(sy);
+    const float a = sx - ix, b = sy - iy;
+    // both scaled intensities rounded on their own (no fused multiply-add
+    // across them), so equal frames give rho0 = 0 exactly
+    const float I1w = __fmul_rn(level_bilin(I1, ix, iy, a, b), s255);
+    const float I0s = __fmul_rn(level_texel(I0, x, y), s255);
+    const int64_t gs = I1.grad_pitch / 4;
+    const float gx = bilin(I1.grad, gs, 2, 0, I1.w, I1.h, ix, iy, a, b) * s255;
+    const float gy = bilin(I1.grad, gs, 2, 1, I1.w, I1.h, ix, iy, a, b) * s255;
+    f.gw[i] = make_float2(gx, gy);
+    f.r0[i] = I1w - gx * u0.x - gy * u0.y - I0s;
+    f.ub[i] = u0;
+}
+
+__global__ void dual_kernel(FlowLevel f, float sigma, float eps) {
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+    if (x >= f.w || y >= f.h) return;
+    const int64_t i = (int64_t)y * f.w + x;
+    const float2 c = f.ub[i];
+    const float2 r = x + 1 < f.w ? f.ub[i + 1] : c, d = y + 1 < f.h ? f.ub[i + f.w] : c;
+    const float g1x = r.x - c.x, g1y = d.x - c.x, g2x = r.y - c.y, g2y = d.y - c.y;
+    float4 p = f.p[i];
+    const float den = 1.0f + sigma * eps;
+    float qx = (p.x + sigma * g1x) / den, qy = (p.y + sigma * g1y) / den;
+    float m = sqrtf(qx * qx + qy * qy);
+    if (m > 1.0f) {
+        qx /= m;
+        qy /= m;
+    }
+    p.x = qx;
+    p.y = qy;
+    qx = (p.z + sigma * g2x) / den;
+    qy = (p.w + sigma * g2y) / den;
+    m = sqrtf(qx * qx + qy * qy);
+    if (m > 1.0f) {
+        qx /= m;
+        qy /= m;
+    }
+    p.z = qx;
+    p.w = qy;
+    f.p[i] = p;
+}
+
+__global__ void primal_kernel(FlowLevel f, float tau, float lambda) {
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+    if (x >= f.w || y >= f.h) return;
+    const int64_t i = (int64_t)y * f.w + x;
+    const float *p = (const float *)f.p;
+    // div of p1 = (p.x, p.y) and of p2 = (p.z, p.w)
+    float d1 = 0.f, d2 = 0.f;
+    if (x + 1 < f.w) {
+        d1 += p[4 * i];
+        d2 += p[4 * i + 2];
+    }
+    if (x > 0) {
+        d1 -= p[4 * (i - 1)];
+        d2 -= p[4 * (i - 1) + 2];
+    }
+    if (y + 1 < f.h) {
+        d1 += p[4 * i + 1];
+        d2 += p[4 * i + 3];
+    }
+    if (y > 0) {
+        d1 -= p[4 * (i - f.w) + 1];
+        d2 -= p[4 * (i - f.w) + 3];
+    }
+    const float2 u = f.u[i];
+    const float t1 = u.x + tau * d1, t2 = u.y + tau * d2;
+    const float2 g = f.gw[i];
+    const float g2 = g.x * g.x + g.y * g.y;
+    const float rho = f.r0[i] + g.x * t1 + g.y * t2;
+    const float th = tau * lambda * g2;
+    float v1 = t1, v2 = t2;
+    if (rho < -th) {
+        v1 = t1 + tau * lambda * g.x;
+        v2 = t2 + tau * lambda * g.y;
+    } else if (rho > th) {
+        v1 = t1 - tau * lambda * g.x;
+        v2 = t2 - tau * lambda * g.y;
+    } else if (g2 > 0.f) {
+        v1 = t1 - rho * g.x / g2;
+        v2 = t2 - rho * g.y / g2;
+    }
+    f.u[i] = make_float2(v1, v2);
+    f.ub[i] = make_float2(2.0f * v1 - u.x, 2.0f * v2 - u.y);
+}
+
+// -------------------------------------------------------- mean in a box
+constexpr int MNT = 256;
+
+__global__ void box_mean_kernel(const float2 *flow, int w, int h, const float4 *boxes,
+                                float4 *out) {
+    const float4 b = boxes[blockIdx.x];
+    // pixels with x0 <= x < x1, y0 <= y < y1 inside the frame
+    int xlo = 0, xhi = -1, ylo = 0, yhi = -1;
+    if (b.x <= b.z && b.y <= b.w) {  // also rejects NaN
+        const float x0 = fminf(fmaxf(b.x, -1.0f), (float)w + 1.0f);
+        const float x1 = fminf(fmaxf(b.z, -1.0f), (float)w + 1.0f);
+        const float y0 = fminf(fmaxf(b.y, -1.0f), (float)h + 1.0f);
+        const float y1 = fminf(fmaxf(b.w, -1.0f), (float)h + 1.0f);
+        xlo = max((int)ceilf(x0), 0);
+        xhi = min((int)ceilf(x1) - 1, w - 1);
+        ylo = max((int)ceilf(y0), 0);
+        yhi = min((int)ceilf(y1) - 1, h - 1);
+    }
+    const bool any = xlo <= xhi && ylo <= yhi;
+    float sx = 0.f, sy = 0.f;
+    int n = 0;
+    if (any) {
+        const int nx = xhi - xlo + 1;
+        n = nx * (yhi - ylo + 1);
+        for (int k = threadIdx.x; k < n; k += MNT) {
+            const float2 v = flow[(int64_t)(ylo + k / nx) * w + xlo + k % nx];
+            sx += v.x;
+            sy += v.y;
+        }
+    }
+    __shared__ float rx[MNT / 32], ry[MNT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(FULL_MASK, sx, o);
+        sy += __shfl_xor_sync(FULL_MASK, sy, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rx[threadIdx.x >> 5] = sx;
+        ry[threadIdx.x >> 5] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tx = 0.f, ty = 0.f;
+        for (int k = 0; k < MNT / 32; ++k) {
+            tx += rx[k];
+            ty += ry[k];
+        }
+        const float mx = n ? tx / (float)n : 0.f, my = n ? ty / (float)n : 0.f;
+        out[blockIdx.x] = make_float4(b.x + mx, b.y + my, b.z + mx, b.w + my);
+    }
+}
+
+dim3 grid2(int w, int h) { return dim3((w + TBX - 1) / TBX, (h + TBY - 1) / TBY); }
+
+LevelF level_f(const omt_pyramid &p, int L) {
+    const LevelView v = level_view(p, L);
+    LevelF f;
+    f.img = v.img;
+    f.grad = (const float *)v.grad;
+    f.img_pitch = v.img_pitch;
+    f.grad_pitch = v.grad_pitch;
+    f.w = v.w;
+    f.h = v.h;
+    f.u8 = L == 0;
+    return f;
+}
+
+}  // namespace
+
+size_t st_scratch_bytes(int w, int h) { return (size_t)w * h * 4 * 5 + 512; }
+
+cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t pitch,
+                                     const omt_flow_params &fp, uint8_t *tex, size_t tpitch,
+                                     void *scratch, cudaStream_t s) {
+    const size_t n = (size_t)w * h;
+    float *base = (float *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+    float *p0 = base, *p1 = base + 2 * n, *q = base + 4 * n;
+    cudaError_t e = cudaMemsetAsync(p0, 0, sizeof(float) * 2 * n, s);
+    if (e != cudaSuccess) return e;
+    StArgs a{frame, (int64_t)pitch, w, h, fp.st_theta, 0.125f, p0, p1, q};
+    const dim3 g = grid2(w, h), b(TBX, TBY);
+    for (int it = 0; it < fp.st_iters; ++it) {
+        st_q_kernel<<<g, b, 0, s>>>(a);
+        st_p_kernel<<<g, b, 0, s>>>(a);
+        const float *t = a.p;
+        a.p = a.p_out;
+        a.p_out = const_cast<float *>(t);
+    }
+    st_texture_kernel<<<g, b, 0, s>>>(a, fp.st_alpha, fp.st_k, tex, (int64_t)tpitch);
+    return cudaGetLastError();
+}
+
+size_t tvl1_scratch_bytes(int w, int h) {
+    // per level-0 pixel: u, ub, uold (3 float2), p (float4), gw (float2),
+    // r0 (float), the coarse flow (float2) -- 60 bytes, plus alignment
+    return (size_t)w * h * 60 + 8 * 256;
+}
+
+cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_flow_params &fp,
+                        float2 *flow, void *scratch, cudaStream_t s) {
+    const size_t n0 = (size_t)P0.w * P0.h;
+    uint8_t *sp = (uint8_t *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+    auto take = [&](size_t bytes) {
+        uint8_t *r = sp;
+        sp += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    FlowLevel f;
+    float2 *ua = (float2 *)take(8 * n0), *ucoarse = (float2 *)take(8 * n0);
+    f.ub = (float2 *)take(8 * n0);
+    f.uold = (float2 *)take(8 * n0);
+    f.p = (float4 *)take(16 * n0);
+    f.gw = (float2 *)take(8 * n0);
+    f.r0 = (float *)take(4 * n0);
+    const float sigma = 1.0f / sqrtf(8.0f), tau = 1.0f / sqrtf(8.0f);
+    const float2 *coarse = nullptr;
+    int cw = 0, ch = 0;
+    cudaError_t e = cudaSuccess;
+    for (int L = P0.levels - 1; L >= 0; --L) {
+        const LevelF I0 = level_f(P0, L), I1 = level_f(P1, L);
+        f.w = I0.w;
+        f.h = I0.h;
+        f.u = L == 0 ? flow : (coarse == ua ? ucoarse : ua);
+        const dim3 g = grid2(f.w, f.h), b(TBX, TBY);
+        upsample_kernel<<<g, b, 0, s>>>(coarse, cw, ch, f.u, f.w, f.h);
+        e = cudaMemsetAsync(f.p, 0, sizeof(float4) * (size_t)f.w * f.h, s);
+        if (e != cudaSuccess) return e;
+        for (int wp = 0; wp < fp.warps; ++wp) {
+            warp_kernel<<<g, b, 0, s>>>(f, I0, I1);
+            for (int it = 0; it < fp.iters; ++it) {
+                dual_kernel<<<g, b, 0, s>>>(f, sigma, fp.eps);
+                primal_kernel<<<g, b, 0, s>>>(f, tau, fp.lambda);
+            }
+        }
+        coarse = f.u;
+        cw = f.w;
+        ch = f.h;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_mean_flow(const float2 *flow, int w, int h, const float4 *boxes,
+                                 int nboxes, float4 *out, cudaStream_t s) {
+    if (nboxes <= 0) return cudaSuccess;
+    box_mean_kernel<<<nboxes, MNT, 0, s>>>(flow, w, h, boxes, out);
+    return cudaGetLastError();
+}
+
+}  // namespace omt

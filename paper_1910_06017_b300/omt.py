@@ -27,7 +27,8 @@ EXPORTED = [
     "omt_version", "omt_select_corners_static", "omt_batch_table_bytes", "omt_batch_pack",
     "omt_batch_step", "omt_batch_upload", "omt_batch_phase", "omt_iou_matrix",
     "omt_assign_workspace_bytes", "omt_assign", "omt_update_tracks", "omt_lk_wait_timeouts",
-    "omt_fb_check",
+    "omt_fb_check", "omt_default_flow_params", "omt_structure_texture_scratch_bytes",
+    "omt_tvl1_scratch_bytes", "omt_structure_texture", "omt_tvl1_flow", "omt_box_mean_flow",
 ]
 PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES, PHASE_FB = 0, 1, 2, 3, 4
 PT_OK, PT_LOST_EIG, PT_LOST_OOB, PT_NONCONV, PT_LOST_FB = 1, 2, 4, 8, 16
@@ -77,6 +78,12 @@ class BatchStream(Structure):
                 ("nvalid", c_void_p), ("pts_back", c_void_p), ("status_back", c_void_p)]
 
 
+class FlowParams(Structure):
+    _fields_ = [("st_theta", c_float), ("st_alpha", c_float), ("st_k", c_float),
+                ("st_iters", c_int32), ("lambda_", c_float), ("eps", c_float), ("warps", c_int32),
+                ("iters", c_int32)]
+
+
 class BatchCaps(Structure):
     _fields_ = [("max_streams", c_int32), ("max_boxes", c_int32), ("max_w", c_int32),
                 ("max_h", c_int32), ("max_corners", c_int32),
@@ -122,6 +129,18 @@ def lib():
         L.omt_update_tracks.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p]
         L.omt_lk_wait_timeouts.argtypes = [c_void_p]
+        L.omt_default_flow_params.argtypes = [POINTER(FlowParams)]
+        L.omt_structure_texture_scratch_bytes.argtypes = [c_int32, c_int32]
+        L.omt_structure_texture_scratch_bytes.restype = c_size_t
+        L.omt_tvl1_scratch_bytes.argtypes = [c_int32, c_int32]
+        L.omt_tvl1_scratch_bytes.restype = c_size_t
+        L.omt_structure_texture.argtypes = [c_void_p, c_int32, c_int32, c_size_t,
+                                            POINTER(FlowParams), c_void_p, c_size_t, c_void_p,
+                                            c_size_t, c_void_p]
+        L.omt_tvl1_flow.argtypes = [POINTER(PyramidDesc), POINTER(PyramidDesc), POINTER(FlowParams),
+                                    c_void_p, c_void_p, c_size_t, c_void_p]
+        L.omt_box_mean_flow.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_int32, c_void_p,
+                                        c_void_p]
         L.omt_fb_check.argtypes = [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_float,
                                    c_void_p, c_void_p]
         L.omt_batch_table_bytes.argtypes = [POINTER(BatchCaps)]
@@ -275,6 +294,47 @@ def lk_track_fb(prev: Pyramid, nxt: Pyramid, pts, params: Params, fb_max: float,
     lk_track(prev, nxt, pts, params, pts_out, status, iters, n_max, n_dev, stream)
     lk_track(nxt, prev, pts_out, params, pts_back, status_back, None, n_max, n_dev, stream)
     fb_check(pts, pts_back, status_back, fb_max, status, n_max, n_dev, stream)
+
+
+def default_flow_params(**kw) -> FlowParams:
+    """Dense-flow parameters (the library's readings), with overrides;
+    `lambda_` is the data weight."""
+    p = FlowParams()
+    lib().omt_default_flow_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def structure_texture(frame, params: FlowParams, texture, scratch=None, stream=None):
+    """u8 texture image of a u8 device frame (h, w) into texture (h, w)."""
+    import torch
+    h, w = frame.shape
+    n = lib().omt_structure_texture_scratch_bytes(w, h)
+    if scratch is None:
+        scratch = torch.empty(n, dtype=torch.uint8, device=frame.device)
+    _check(lib().omt_structure_texture(_ptr(frame), w, h, frame.stride(0), ctypes.byref(params),
+                                       _ptr(texture), texture.stride(0), _ptr(scratch),
+                                       scratch.numel(), _stream(stream)), "omt_structure_texture")
+
+
+def tvl1_flow(prev: "Pyramid", nxt: "Pyramid", params: FlowParams, flow, scratch=None,
+              stream=None):
+    """Dense flow (device (h, w, 2) float32) from prev to nxt (F32 pyramids)."""
+    import torch
+    n = lib().omt_tvl1_scratch_bytes(prev.w, prev.h)
+    if scratch is None:
+        scratch = torch.empty(n, dtype=torch.uint8, device=flow.device)
+    _check(lib().omt_tvl1_flow(ctypes.byref(prev.desc), ctypes.byref(nxt.desc),
+                               ctypes.byref(params), _ptr(flow), _ptr(scratch), scratch.numel(),
+                               _stream(stream)), "omt_tvl1_flow")
+
+
+def box_mean_flow(flow, boxes, boxes_out, stream=None):
+    """Boxes moved by the mean flow inside them (device tensors)."""
+    h, w = flow.shape[:2]
+    _check(lib().omt_box_mean_flow(_ptr(flow), w, h, _ptr(boxes), boxes.shape[0], _ptr(boxes_out),
+                                   _stream(stream)), "omt_box_mean_flow")
 
 
 def update_boxes(boxes, offsets, pts, pts_out, status, params: Params, boxes_out, nvalid=None,

@@ -245,3 +245,39 @@ def test_batch_pack_forward_backward_arrays():
     assert lib.omt_fb_check(fake, fake, fake, -1, None, ctypes.c_float(1.0), fake, None) == omt.EINVAL
     assert lib.omt_fb_check(None, None, None, 0, None, ctypes.c_float(1.0), None, None) == omt.OK
     assert lib.omt_fb_check(None, fake, fake, 10, None, ctypes.c_float(1.0), fake, None) == omt.EINVAL
+
+
+def test_flow_engine_arguments_rejected_before_launch():
+    lib = omt.lib()
+    fp = omt.default_flow_params()
+    assert omt.validate_params(omt.default_params()) == omt.OK
+    fake = ctypes.c_void_p(1 << 24)
+    n = lib.omt_structure_texture_scratch_bytes(64, 48)
+    assert n > 0 and lib.omt_structure_texture_scratch_bytes(0, 48) == 0
+    # pitch below width, short scratch, bad parameters
+    assert lib.omt_structure_texture(fake, 64, 48, 63, ctypes.byref(fp), fake, 64, fake, n,
+                                     None) == omt.EINVAL
+    assert lib.omt_structure_texture(fake, 64, 48, 64, ctypes.byref(fp), fake, 64, fake, n - 1,
+                                     None) == omt.ENOMEM
+    bad = omt.default_flow_params(iters=0)
+    assert lib.omt_structure_texture(fake, 64, 48, 64, ctypes.byref(bad), fake, 64, fake, n,
+                                     None) == omt.EINVAL
+    # the flow needs F32 pyramids of one shape
+    d0, d1, d16 = omt.PyramidDesc(), omt.PyramidDesc(), omt.PyramidDesc()
+    m = omt.pyramid_bytes(64, 48, 3, 0)
+    assert lib.omt_pyramid_init(ctypes.byref(d0), 64, 48, 3, 0, ctypes.c_void_p(1 << 20), m) == 0
+    assert lib.omt_pyramid_init(ctypes.byref(d1), 64, 48, 3, 0, ctypes.c_void_p(1 << 22), m) == 0
+    m16 = omt.pyramid_bytes(64, 48, 3, 1)
+    assert lib.omt_pyramid_init(ctypes.byref(d16), 64, 48, 3, 1, ctypes.c_void_p(1 << 23), m16) == 0
+    t = lib.omt_tvl1_scratch_bytes(64, 48)
+    assert lib.omt_tvl1_flow(ctypes.byref(d0), ctypes.byref(d16), ctypes.byref(fp), fake, fake, t,
+                             None) == omt.EINVAL
+    assert lib.omt_tvl1_flow(ctypes.byref(d0), ctypes.byref(d0), ctypes.byref(fp), fake, fake, t,
+                             None) == omt.EINVAL
+    assert lib.omt_tvl1_flow(ctypes.byref(d0), ctypes.byref(d1), ctypes.byref(fp), fake, fake, t - 1,
+                             None) == omt.ENOMEM
+    # box means: in place and misaligned boxes are rejected; zero boxes is a no-op
+    assert lib.omt_box_mean_flow(fake, 64, 48, fake, 3, fake, None) == omt.EINVAL
+    assert lib.omt_box_mean_flow(fake, 64, 48, ctypes.c_void_p((1 << 24) + 8), 3,
+                                 ctypes.c_void_p(1 << 25), None) == omt.EINVAL
+    assert lib.omt_box_mean_flow(None, 64, 48, None, 0, None, None) == omt.OK
