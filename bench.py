@@ -405,6 +405,152 @@ def run_reference(args, ws, rank):
     }
 
 
+# ------------------------------------------------------------ dense flow
+FLOW_SIZE, FLOW_LEVELS, FLOW_BOXES = (1920, 1080), 4, 16
+FLOW_METRIC = "dense flow frames/s (1920x1080)"
+FLOW_WORKLOAD = ("1920x1080 frame pairs, texture shifted by (2.25, -1.5) px; per frame: "
+                 "structure-texture, 4-level F32 pyramid, Huber-TV-L1 (3 warps x 30 iterations "
+                 "per level), mean flow in 16 boxes")
+
+
+def flow_frames(seed: int = 0):
+    from paper_1910_06017_b300 import synth
+    w, h = FLOW_SIZE
+    rng = np.random.default_rng(synth.seed_for(6) + seed)
+    tex = synth.Texture.draw(rng, w, h)
+    f0 = synth.render_shift(tex, w, h, 0.0, 0.0)
+    f1 = synth.render_shift(tex, w, h, 2.25, -1.5)
+    boxes = synth.uniform_boxes(rng, w, h, FLOW_BOXES)
+    return f0, f1, boxes
+
+
+def flow_bytes_per_l0px(omt, fp) -> float:
+    """Algorithmic DRAM bytes of the TV-L1 iterations per level-0 pixel: per
+    iteration the dual kernel reads the extrapolated flow (8 B) and the duals
+    (16 B) and writes the duals (16 B); the primal kernel reads the duals,
+    the flow, the warped gradient (8 B) and rho0 (4 B) and writes the flow and
+    its extrapolation (16 B): 92 B per pixel and iteration; levels add 1/4 each."""
+    area = sum(4.0 ** -L for L in range(FLOW_LEVELS))
+    return 92.0 * fp.warps * fp.iters * area
+
+
+def run_flow(args):
+    """One step = one new frame: its texture, its F32 pyramid, the flow from
+    the previous frame's pyramid, the mean flow in every box."""
+    import torch
+    from paper_1910_06017_b300 import omt
+    dev = torch.device("cuda", 0)
+    w, h = FLOW_SIZE
+    f0, f1, boxes = flow_frames()
+    fp = omt.default_flow_params()
+    prm = omt.default_params(levels=FLOW_LEVELS)
+    frames = [torch.from_numpy(f).to(dev) for f in (f0, f1)]
+    host = [torch.from_numpy(f).pin_memory() for f in (f0, f1)]
+    tex = [torch.zeros((h, w), dtype=torch.uint8, device=dev) for _ in range(2)]
+    pyr = [omt.Pyramid(w, h, FLOW_LEVELS, omt.F32, dev) for _ in range(2)]
+    st_scr = torch.empty(omt.lib().omt_structure_texture_scratch_bytes(w, h), dtype=torch.uint8, device=dev)
+    tv_scr = torch.empty(omt.lib().omt_tvl1_scratch_bytes(w, h), dtype=torch.uint8, device=dev)
+    flow = torch.zeros((h, w, 2), device=dev)
+    bx = torch.from_numpy(np.ascontiguousarray(boxes, np.float32)).to(dev)
+    bo = torch.zeros_like(bx)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
+
+    def prime(k):
+        omt.structure_texture(frames[k & 1], fp, tex[k & 1], st_scr)
+        omt.build_pyramid(tex[k & 1], pyr[k & 1], prm)
+
+    def step(k, ev=None):
+        # frame k+1 arrives: its texture and pyramid, then the flow k -> k+1
+        cur, nxt = k & 1, (k + 1) & 1
+        omt.structure_texture(frames[nxt], fp, tex[nxt], st_scr)
+        omt.build_pyramid(tex[nxt], pyr[nxt], prm)
+        if ev:
+            ev[0].record()
+        omt.tvl1_flow(pyr[cur], pyr[nxt], fp, flow, tv_scr)
+        if ev:
+            ev[1].record()
+        omt.box_mean_flow(flow, bx, bo)
+
+    prime(0)
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ms, tv = [], []
+    for k in range(args.steps):
+        flush.fill_(k & 255)    # L2 flushed between timed steps, outside the timed region
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        step(args.warmup + k, (e[1], e[2]))
+        e[3].record()
+        torch.cuda.synchronize()
+        ms.append(e[0].elapsed_time(e[3]))
+        tv.append(e[1].elapsed_time(e[2]))
+    clk = clocks.stop()
+    step_ms, tv_ms = float(np.mean(ms)), float(np.mean(tv))
+    # end to end: the new frame copied from page-locked host memory, the boxes read back
+    bo_h = torch.empty(bo.shape, dtype=torch.float32).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(args.steps):
+        frames[(k + 1) & 1].copy_(host[(k + 1) & 1], non_blocking=True)
+        step(k)
+        bo_h.copy_(bo, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    byts = flow_bytes_per_l0px(omt, fp) * w * h
+    pk, pk_src = peaks()
+    hbm = pk.get("hbm_gbs", 6400.0)
+    moved = (bo.cpu().numpy() - boxes)[:, :2]
+    return {
+        "metric": FLOW_METRIC, "value": 1e3 / step_ms, "unit": "frames/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": FLOW_WORKLOAD, "path": "omt_structure_texture + omt_build_pyramid + "
+                   "omt_tvl1_flow + omt_box_mean_flow", "l2": "flushed between timed steps",
+                   "tvl1_ms": tv_ms,
+                   # steps alternate the pair's direction: +-(2.25, -1.5) px
+                   "median_box_motion_last_step": np.median(moved, 0).tolist()},
+        "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": w * h,
+                "d2h_bytes_per_step": int(bo.numel() * 4)},
+        "roofline": {"kernel": "tvl1 dual + primal iterations (all levels)", "bound": "hbm",
+                     "achieved": byts / (tv_ms * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": byts / (tv_ms * 1e-3) / 1e9 / hbm,
+                     "peak_source": pk_src, "traffic": None,
+                     "bytes_per_level0_px": flow_bytes_per_l0px(omt, fp)},
+        "clocks": clk,
+        "gpu_launches": (2 * fp.st_iters + 1 + 5 + FLOW_LEVELS * (2 + fp.warps * (1 + 2 * fp.iters))
+                         + 1) * args.steps,
+    }
+
+
+def run_flow_reference(args):
+    """The FP64 oracle's flow engine on the host cores, on a bounded sample:
+    a 480x270 crop of the workload's frame pair per step (1/16 of the area),
+    scaled to frames/s of the full frame by area."""
+    from oracle import oracle as O
+    f0, f1, boxes = flow_frames()
+    c0, c1 = f0[:270, :480], f1[:270, :480]
+    O.lib()
+    P0 = O.Pyramid(O.structure_texture(c0), FLOW_LEVELS)   # the previous frame's, as on the GPU
+    times = []
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        T1 = O.structure_texture(c1)
+        fl = O.tvl1(P0, O.Pyramid(T1, FLOW_LEVELS))
+        O.box_mean_flow(fl, boxes / 4.0)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    sec = float(np.mean(times)) * 16.0   # area of the full frame
+    return {"value": 1.0 / sec, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": "480x270 crop of the 1920x1080 pair (the new frame's texture and "
+                      "pyramid, 4-level flow, box means), time x16 by area"}
+
+
 def cpu_baseline_sample():
     class A:
         steps, warmup = 1, 0
@@ -423,12 +569,35 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="keep the default LK launch shape instead of autotuning it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flow", action="store_true",
+                    help="the dense flow engine (TV-L1) on 1920x1080 frames instead of the tracker")
     ap.add_argument("--fb", type=float, default=None, metavar="MAX",
                     help="forward-backward check in every step, threshold MAX px (default off)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "omt":
         args.warmup = max(args.warmup, 3)
+    if args.flow:
+        if rank != 0:
+            return
+        if args.impl == "reference":
+            a = argparse.Namespace(steps=max(1, args.steps // 10), warmup=0)
+            cb = run_flow_reference(a)
+            print(json.dumps({"impl": "reference", "metric": FLOW_METRIC, "value": cb["value"],
+                              "unit": "frames/s", "n_gpus": ws, "steps": a.steps, "warmup": 0,
+                              "ms_per_step": 1e3 / cb["value"], "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                              "data": "synthetic", "config": {"workload": FLOW_WORKLOAD,
+                                                              "path": "FP64 CPU oracle"},
+                              "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "frames/s",
+                                                          "h2d_bytes_per_step": 0,
+                                                          "d2h_bytes_per_step": 0}}))
+            return
+        res = run_flow(args)
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = run_flow_reference(argparse.Namespace(steps=1, warmup=0))
+        print(json.dumps(res))
+        return
     if args.impl == "reference":
         # the oracle runs on rank 0 only; other ranks have no work
         if rank == 0:
