@@ -425,13 +425,13 @@ def flow_frames(seed: int = 0):
 
 
 def flow_bytes_per_l0px(omt, fp) -> float:
-    """Algorithmic DRAM bytes of the TV-L1 iterations per level-0 pixel: per
-    iteration the dual kernel reads the extrapolated flow (8 B) and the duals
-    (16 B) and writes the duals (16 B); the primal kernel reads the duals,
-    the flow, the warped gradient (8 B) and rho0 (4 B) and writes the flow and
-    its extrapolation (16 B): 92 B per pixel and iteration; levels add 1/4 each."""
+    """Algorithmic DRAM bytes of the TV-L1 iterations per level-0 pixel: an
+    iteration reads the state once -- the extrapolated flow (8 B), the duals
+    (16 B), the flow (8 B), the warped gradient (8 B), rho0 (4 B) -- and
+    writes the duals, the flow and its extrapolation (32 B): 76 B per pixel
+    and iteration; each level adds a quarter of the one below."""
     area = sum(4.0 ** -L for L in range(FLOW_LEVELS))
-    return 92.0 * fp.warps * fp.iters * area
+    return 76.0 * fp.warps * fp.iters * area
 
 
 def run_flow(args):
@@ -517,7 +517,7 @@ def run_flow(args):
                    "median_box_motion_last_step": np.median(moved, 0).tolist()},
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": w * h,
                 "d2h_bytes_per_step": int(bo.numel() * 4)},
-        "roofline": {"kernel": "tvl1 dual + primal iterations (all levels)", "bound": "hbm",
+        "roofline": {"kernel": "pd_kernel, the TV-L1 iterations (all levels)", "bound": "hbm",
                      "achieved": byts / (tv_ms * 1e-3) / 1e9, "peak": hbm,
                      "unit": "GB/s", "frac": byts / (tv_ms * 1e-3) / 1e9 / hbm,
                      "peak_source": pk_src, "traffic": None,

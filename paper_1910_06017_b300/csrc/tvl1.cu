@@ -2,29 +2,26 @@
 // prediction (Section V-A).
 //
 // Structure-texture: the ROF structure S of the u8 frame by Chambolle's dual
-// projection (one launch per iteration, dual field ping-ponged in global
+// projection (one launch per step, q = div p - I / theta formed in shared
+// memory for a tile and its halo, the dual field ping-ponged in global
 // memory), then the u8 texture clamp(floor(k (I - alpha S) + 128.5)).
 // Huber-TV-L1: per pyramid level (FP32 storage, coarse to fine) the flow of
 // the level above is sampled bilinearly at (x/2, y/2) and doubled; per warp
 // one launch samples frame t+1 and its gradient at x + u0 (taps clamped) and
-// stores grad I1w and rho0, then every primal-dual iteration is two
-// launches: the duals from the extrapolated flow (forward differences, a
+// stores grad I1w and rho0, then every primal-dual iteration is one launch
+// (pd_kernel): the duals from the extrapolated flow (forward differences, a
 // Huber shrink and the projection onto the unit disc, per flow component)
-// and the flow (backward-difference divergence, the pointwise prox of the
-// L1 data term, the extrapolation).  Every expression keeps the order of
-// the definition, in FP32.  Each iteration reads and writes every field
-// once: the iteration kernels are bound by HBM (or L2 for small levels).
+// in shared memory for a tile and its halo, then the flow (backward-
+// difference divergence, the pointwise prox of the L1 data term, the
+// extrapolation).  Every expression keeps the order of the definition, in
+// FP32.  Each iteration reads and writes every field once: the kernel is
+// bound by HBM (or L2 for small levels).
 #include "omt_internal.cuh"
 
 namespace omt {
 namespace {
 
 constexpr int TBX = 32, TBY = 8;
-
-__device__ __forceinline__ float2 grad_fwd(const float *u, int stride, int w, int h, int x, int y) {
-    const int64_t i = (int64_t)y * stride + x;
-    return make_float2(x + 1 < w ? u[i + 1] - u[i] : 0.f, y + 1 < h ? u[i + stride] - u[i] : 0.f);
-}
 
 // div of an interleaved dual field (px, py), component c of cc, at (x, y).
 __device__ __forceinline__ float div_bwd(const float *p, int cc, int c, int w, int h, int x, int y) {
@@ -45,24 +42,52 @@ struct StArgs {
     float theta, step;
     const float *p;  // (px, py) interleaved, w x h
     float *p_out;
-    float *q;        // w x h scratch: div p - I / theta
 };
 
-__global__ void st_q_kernel(StArgs a) {
-    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+// One projection step for a TBX x TBY tile: q = div p - I / theta on the
+// tile plus its right column and bottom row in shared memory (from p on the
+// tile plus one pixel on every side), then the tile's new duals from the
+// forward differences of q.  Equal to forming q everywhere and then p.
+__global__ void __launch_bounds__(TBX * TBY) st_step_kernel(StArgs a) {
+    constexpr int QW = TBX + 1, QH = TBY + 1, RW = TBX + 2, RH = TBY + 2;
+    __shared__ float2 spp[RH][RW];
+    __shared__ float sq[QH][QW];
+    const int tid = threadIdx.y * TBX + threadIdx.x;
+    const int bx = blockIdx.x * TBX, by = blockIdx.y * TBY;
+    for (int k = tid; k < RW * RH; k += TBX * TBY) {
+        const int ry = k / RW, rx = k - ry * RW;
+        const int x = bx - 1 + rx, y = by - 1 + ry;
+        spp[ry][rx] = (x >= 0 && x < a.w && y >= 0 && y < a.h)
+                          ? make_float2(a.p[2 * ((int64_t)y * a.w + x)], a.p[2 * ((int64_t)y * a.w + x) + 1])
+                          : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int k = tid; k < QW * QH; k += TBX * TBY) {
+        const int ry = k / QW, rx = k - ry * QW;
+        const int x = bx + rx, y = by + ry;
+        float q = 0.f;
+        if (x < a.w && y < a.h) {
+            // div p at (x, y): spp holds (x, y) at [ry + 1][rx + 1]
+            float d = 0.f;
+            if (x + 1 < a.w) d += spp[ry + 1][rx + 1].x;
+            if (x > 0) d -= spp[ry + 1][rx].x;
+            if (y + 1 < a.h) d += spp[ry + 1][rx + 1].y;
+            if (y > 0) d -= spp[ry][rx + 1].y;
+            q = d - (float)a.img[(int64_t)y * a.pitch + x] / a.theta;
+        }
+        sq[ry][rx] = q;
+    }
+    __syncthreads();
+    const int x = bx + threadIdx.x, y = by + threadIdx.y;
     if (x >= a.w || y >= a.h) return;
-    a.q[(int64_t)y * a.w + x] =
-        div_bwd(a.p, 2, 0, a.w, a.h, x, y) - (float)a.img[(int64_t)y * a.pitch + x] / a.theta;
-}
-
-__global__ void st_p_kernel(StArgs a) {
-    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
-    if (x >= a.w || y >= a.h) return;
-    const float2 g = grad_fwd(a.q, a.w, a.w, a.h, x, y);
-    const float m = 1.f + a.step * sqrtf(g.x * g.x + g.y * g.y);
+    const float qc = sq[threadIdx.y][threadIdx.x];
+    const float gx = x + 1 < a.w ? sq[threadIdx.y][threadIdx.x + 1] - qc : 0.f;
+    const float gy = y + 1 < a.h ? sq[threadIdx.y + 1][threadIdx.x] - qc : 0.f;
+    const float m = 1.f + a.step * sqrtf(gx * gx + gy * gy);
     const int64_t i = (int64_t)y * a.w + x;
-    a.p_out[2 * i] = (a.p[2 * i] + a.step * g.x) / m;
-    a.p_out[2 * i + 1] = (a.p[2 * i + 1] + a.step * g.y) / m;
+    const float2 pc = spp[threadIdx.y + 1][threadIdx.x + 1];
+    a.p_out[2 * i] = (pc.x + a.step * gx) / m;
+    a.p_out[2 * i + 1] = (pc.y + a.step * gy) / m;
 }
 
 __global__ void st_texture_kernel(StArgs a, float alpha, float k, uint8_t *tex, int64_t tpitch) {
@@ -109,8 +134,9 @@ __device__ __forceinline__ float level_bilin(const LevelF &L, int ix, int iy, fl
 
 struct FlowLevel {
     int w, h;
-    float2 *u, *ub, *uold;   // flow, extrapolated flow, previous flow
-    float4 *p;               // (p1x, p1y, p2x, p2y)
+    float2 *u;               // flow
+    float2 *ub, *ub_out;     // extrapolated flow: read, written (ping-pong)
+    float4 *p, *p_out;       // duals (p1x, p1y, p2x, p2y): read, written (ping-pong)
     float2 *gw;              // grad I1 at x + u0, scaled to [0, 1] intensities
     float *r0;
 };
@@ -151,23 +177,29 @@ __global__ void warp_kernel(FlowLevel f, LevelF I0, LevelF I1) {
     f.ub[i] = u0;
 }
 
-__global__ void dual_kernel(FlowLevel f, float sigma, float eps) {
-    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
-    if (x >= f.w || y >= f.h) return;
-    const int64_t i = (int64_t)y * f.w + x;
-    const float2 c = f.ub[i];
-    const float2 r = x + 1 < f.w ? f.ub[i + 1] : c, d = y + 1 < f.h ? f.ub[i + f.w] : c;
+// One primal-dual iteration for a TBX x TBY tile, one pixel per thread.  The
+// duals of the tile and of its left column and top row (which the
+// divergence needs) are formed in shared memory from the extrapolated flow
+// of the tile plus one pixel on every side; the flow then follows.  The
+// halo duals are recomputed, not exchanged: a neighbouring tile forms the
+// same values from the same inputs, so the result equals a dual launch
+// followed by a primal launch.  Reads p and ub, writes p_out and ub_out
+// (ping-pong: neighbours read the old fields while this tile writes).
+constexpr int PW = TBX + 1, PH = TBY + 1;   // dual region
+constexpr int UW = TBX + 2, UH = TBY + 2;   // extrapolated-flow region
+
+__device__ __forceinline__ float4 dual_step(float4 p, float2 c, float2 r, float2 d, float sigma,
+                                            float den) {
     const float g1x = r.x - c.x, g1y = d.x - c.x, g2x = r.y - c.y, g2y = d.y - c.y;
-    float4 p = f.p[i];
-    const float den = 1.0f + sigma * eps;
     float qx = (p.x + sigma * g1x) / den, qy = (p.y + sigma * g1y) / den;
     float m = sqrtf(qx * qx + qy * qy);
     if (m > 1.0f) {
         qx /= m;
         qy /= m;
     }
-    p.x = qx;
-    p.y = qy;
+    float4 o;
+    o.x = qx;
+    o.y = qy;
     qx = (p.z + sigma * g2x) / den;
     qy = (p.w + sigma * g2y) / den;
     m = sqrtf(qx * qx + qy * qy);
@@ -175,33 +207,61 @@ __global__ void dual_kernel(FlowLevel f, float sigma, float eps) {
         qx /= m;
         qy /= m;
     }
-    p.z = qx;
-    p.w = qy;
-    f.p[i] = p;
+    o.z = qx;
+    o.w = qy;
+    return o;
 }
 
-__global__ void primal_kernel(FlowLevel f, float tau, float lambda) {
-    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
+__global__ void __launch_bounds__(TBX * TBY) pd_kernel(FlowLevel f, float sigma, float eps, float tau,
+                                                       float lambda) {
+    __shared__ float2 sub[UH][UW];
+    __shared__ float4 sp[PH][PW];
+    const int tid = threadIdx.y * TBX + threadIdx.x;
+    const int x0 = blockIdx.x * TBX - 1, y0 = blockIdx.y * TBY - 1;  // region origins
+    for (int k = tid; k < UW * UH; k += TBX * TBY) {
+        const int ry = k / UW, rx = k - ry * UW;
+        const int x = x0 + rx, y = y0 + ry;
+        sub[ry][rx] = (x >= 0 && x < f.w && y >= 0 && y < f.h) ? f.ub[(int64_t)y * f.w + x]
+                                                                  : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float den = 1.0f + sigma * eps;
+    for (int k = tid; k < PW * PH; k += TBX * TBY) {
+        const int ry = k / PW, rx = k - ry * PW;
+        const int x = x0 + rx, y = y0 + ry;
+        float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (x >= 0 && x < f.w && y >= 0 && y < f.h) {
+            const float2 c = sub[ry][rx];
+            const float2 r = x + 1 < f.w ? sub[ry][rx + 1] : c;
+            const float2 d = y + 1 < f.h ? sub[ry + 1][rx] : c;
+            pn = dual_step(f.p[(int64_t)y * f.w + x], c, r, d, sigma, den);
+        }
+        sp[ry][rx] = pn;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;   // this pixel in the regions
+    const int x = x0 + tx, y = y0 + ty;
     if (x >= f.w || y >= f.h) return;
     const int64_t i = (int64_t)y * f.w + x;
-    const float *p = (const float *)f.p;
-    // div of p1 = (p.x, p.y) and of p2 = (p.z, p.w)
+    const float4 pc = sp[ty][tx];
+    f.p_out[i] = pc;
+    // div of p1 = (p.x, p.y) and of p2 = (p.z, p.w), as the definition orders it
     float d1 = 0.f, d2 = 0.f;
     if (x + 1 < f.w) {
-        d1 += p[4 * i];
-        d2 += p[4 * i + 2];
+        d1 += pc.x;
+        d2 += pc.z;
     }
     if (x > 0) {
-        d1 -= p[4 * (i - 1)];
-        d2 -= p[4 * (i - 1) + 2];
+        d1 -= sp[ty][tx - 1].x;
+        d2 -= sp[ty][tx - 1].z;
     }
     if (y + 1 < f.h) {
-        d1 += p[4 * i + 1];
-        d2 += p[4 * i + 3];
+        d1 += pc.y;
+        d2 += pc.w;
     }
     if (y > 0) {
-        d1 -= p[4 * (i - f.w) + 1];
-        d2 -= p[4 * (i - f.w) + 3];
+        d1 -= sp[ty - 1][tx].y;
+        d2 -= sp[ty - 1][tx].w;
     }
     const float2 u = f.u[i];
     const float t1 = u.x + tau * d1, t2 = u.y + tau * d2;
@@ -221,7 +281,7 @@ __global__ void primal_kernel(FlowLevel f, float tau, float lambda) {
         v2 = t2 - rho * g.y / g2;
     }
     f.u[i] = make_float2(v1, v2);
-    f.ub[i] = make_float2(2.0f * v1 - u.x, 2.0f * v2 - u.y);
+    f.ub_out[i] = make_float2(2.0f * v1 - u.x, 2.0f * v2 - u.y);
 }
 
 // -------------------------------------------------------- mean in a box
@@ -300,14 +360,13 @@ cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t 
                                      void *scratch, cudaStream_t s) {
     const size_t n = (size_t)w * h;
     float *base = (float *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
-    float *p0 = base, *p1 = base + 2 * n, *q = base + 4 * n;
+    float *p0 = base, *p1 = base + 2 * n;
     cudaError_t e = cudaMemsetAsync(p0, 0, sizeof(float) * 2 * n, s);
     if (e != cudaSuccess) return e;
-    StArgs a{frame, (int64_t)pitch, w, h, fp.st_theta, 0.125f, p0, p1, q};
+    StArgs a{frame, (int64_t)pitch, w, h, fp.st_theta, 0.125f, p0, p1};
     const dim3 g = grid2(w, h), b(TBX, TBY);
     for (int it = 0; it < fp.st_iters; ++it) {
-        st_q_kernel<<<g, b, 0, s>>>(a);
-        st_p_kernel<<<g, b, 0, s>>>(a);
+        st_step_kernel<<<g, b, 0, s>>>(a);
         const float *t = a.p;
         a.p = a.p_out;
         a.p_out = const_cast<float *>(t);
@@ -317,9 +376,10 @@ cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t 
 }
 
 size_t tvl1_scratch_bytes(int w, int h) {
-    // per level-0 pixel: u, ub, uold (3 float2), p (float4), gw (float2),
-    // r0 (float), the coarse flow (float2) -- 60 bytes, plus alignment
-    return (size_t)w * h * 60 + 8 * 256;
+    // per level-0 pixel: two flow buffers for the levels above (float2 each),
+    // the extrapolated flow and the duals twice (ping-pong: float2, float4),
+    // the warped gradient (float2) and rho0 (float) -- 76 bytes, plus alignment
+    return (size_t)w * h * 76 + 8 * 256;
 }
 
 cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_flow_params &fp,
@@ -331,11 +391,10 @@ cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_
         sp += (bytes + 255) & ~(size_t)255;
         return r;
     };
-    FlowLevel f;
     float2 *ua = (float2 *)take(8 * n0), *ucoarse = (float2 *)take(8 * n0);
-    f.ub = (float2 *)take(8 * n0);
-    f.uold = (float2 *)take(8 * n0);
-    f.p = (float4 *)take(16 * n0);
+    float2 *ubuf[2] = {(float2 *)take(8 * n0), (float2 *)take(8 * n0)};
+    float4 *pbuf[2] = {(float4 *)take(16 * n0), (float4 *)take(16 * n0)};
+    FlowLevel f;
     f.gw = (float2 *)take(8 * n0);
     f.r0 = (float *)take(4 * n0);
     const float sigma = 1.0f / sqrtf(8.0f), tau = 1.0f / sqrtf(8.0f);
@@ -349,13 +408,19 @@ cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_
         f.u = L == 0 ? flow : (coarse == ua ? ucoarse : ua);
         const dim3 g = grid2(f.w, f.h), b(TBX, TBY);
         upsample_kernel<<<g, b, 0, s>>>(coarse, cw, ch, f.u, f.w, f.h);
-        e = cudaMemsetAsync(f.p, 0, sizeof(float4) * (size_t)f.w * f.h, s);
+        int cur = 0;  // the p / ub buffers holding the current fields
+        e = cudaMemsetAsync(pbuf[cur], 0, sizeof(float4) * (size_t)f.w * f.h, s);
         if (e != cudaSuccess) return e;
         for (int wp = 0; wp < fp.warps; ++wp) {
+            f.ub = ubuf[cur];
             warp_kernel<<<g, b, 0, s>>>(f, I0, I1);
             for (int it = 0; it < fp.iters; ++it) {
-                dual_kernel<<<g, b, 0, s>>>(f, sigma, fp.eps);
-                primal_kernel<<<g, b, 0, s>>>(f, tau, fp.lambda);
+                f.p = pbuf[cur];
+                f.ub = ubuf[cur];
+                f.p_out = pbuf[1 - cur];
+                f.ub_out = ubuf[1 - cur];
+                pd_kernel<<<g, b, 0, s>>>(f, sigma, fp.eps, tau, fp.lambda);
+                cur = 1 - cur;
             }
         }
         coarse = f.u;
