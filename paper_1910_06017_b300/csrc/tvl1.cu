@@ -90,6 +90,93 @@ __global__ void __launch_bounds__(TBX * TBY) st_step_kernel(StArgs a) {
     a.p_out[2 * i + 1] = (pc.y + a.step * gy) / m;
 }
 
+// Two projection steps for a TBX x TBY tile in one launch: the duals of the
+// intermediate step are formed in shared memory on the tile grown by the
+// pixels the second step reads (temporal blocking), so a launch reads p and
+// I once and writes p once for two steps.  Positions outside the frame are
+// formed as zero and never read by a position inside it.  Equal to two
+// st_step_kernel launches bit for bit.
+__global__ void __launch_bounds__(TBX * TBY) st_step2_kernel(StArgs a) {
+    // regions (origin offset, width, height) relative to the tile origin:
+    // P0 p^n [-2, TBX+1], Q0 q^n [-1, TBX+1], P1 p^n+1 [-1, TBX], Q1 q^n+1 [0, TBX]
+    constexpr int P0W = TBX + 4, P0H = TBY + 4, Q0W = TBX + 3, Q0H = TBY + 3;
+    constexpr int P1W = TBX + 2, P1H = TBY + 2, Q1W = TBX + 1, Q1H = TBY + 1;
+    __shared__ float2 p0[P0H][P0W];
+    __shared__ float q0[Q0H][Q0W];
+    __shared__ float i0[Q0H][Q0W];
+    __shared__ float2 p1[P1H][P1W];
+    __shared__ float q1[Q1H][Q1W];
+    const int tid = threadIdx.y * TBX + threadIdx.x;
+    const int bx = blockIdx.x * TBX, by = blockIdx.y * TBY;
+    auto inside = [&](int x, int y) { return x >= 0 && x < a.w && y >= 0 && y < a.h; };
+    for (int k = tid; k < P0W * P0H; k += TBX * TBY) {
+        const int ry = k / P0W, rx = k - ry * P0W, x = bx - 2 + rx, y = by - 2 + ry;
+        p0[ry][rx] = inside(x, y) ? make_float2(a.p[2 * ((int64_t)y * a.w + x)],
+                                                a.p[2 * ((int64_t)y * a.w + x) + 1])
+                                  : make_float2(0.f, 0.f);
+    }
+    for (int k = tid; k < Q0W * Q0H; k += TBX * TBY) {
+        const int ry = k / Q0W, rx = k - ry * Q0W, x = bx - 1 + rx, y = by - 1 + ry;
+        i0[ry][rx] = inside(x, y) ? (float)a.img[(int64_t)y * a.pitch + x] : 0.f;
+    }
+    __syncthreads();
+    // q^n on Q0: div p^n - I / theta; Q0 (rx, ry) is P0 (rx + 1, ry + 1)
+    for (int k = tid; k < Q0W * Q0H; k += TBX * TBY) {
+        const int ry = k / Q0W, rx = k - ry * Q0W, x = bx - 1 + rx, y = by - 1 + ry;
+        float q = 0.f;
+        if (inside(x, y)) {
+            float d = 0.f;
+            if (x + 1 < a.w) d += p0[ry + 1][rx + 1].x;
+            if (x > 0) d -= p0[ry + 1][rx].x;
+            if (y + 1 < a.h) d += p0[ry + 1][rx + 1].y;
+            if (y > 0) d -= p0[ry][rx + 1].y;
+            q = d - i0[ry][rx] / a.theta;
+        }
+        q0[ry][rx] = q;
+    }
+    __syncthreads();
+    // p^n+1 on P1; P1 (rx, ry) is Q0 (rx, ry) and P0 (rx + 1, ry + 1)
+    for (int k = tid; k < P1W * P1H; k += TBX * TBY) {
+        const int ry = k / P1W, rx = k - ry * P1W, x = bx - 1 + rx, y = by - 1 + ry;
+        float2 pn = make_float2(0.f, 0.f);
+        if (inside(x, y)) {
+            const float qc = q0[ry][rx];
+            const float gx = x + 1 < a.w ? q0[ry][rx + 1] - qc : 0.f;
+            const float gy = y + 1 < a.h ? q0[ry + 1][rx] - qc : 0.f;
+            const float m = 1.f + a.step * sqrtf(gx * gx + gy * gy);
+            const float2 pc = p0[ry + 1][rx + 1];
+            pn = make_float2((pc.x + a.step * gx) / m, (pc.y + a.step * gy) / m);
+        }
+        p1[ry][rx] = pn;
+    }
+    __syncthreads();
+    // q^n+1 on Q1; Q1 (rx, ry) is P1 (rx + 1, ry + 1) and Q0 (rx + 1, ry + 1)
+    for (int k = tid; k < Q1W * Q1H; k += TBX * TBY) {
+        const int ry = k / Q1W, rx = k - ry * Q1W, x = bx + rx, y = by + ry;
+        float q = 0.f;
+        if (inside(x, y)) {
+            float d = 0.f;
+            if (x + 1 < a.w) d += p1[ry + 1][rx + 1].x;
+            if (x > 0) d -= p1[ry + 1][rx].x;
+            if (y + 1 < a.h) d += p1[ry + 1][rx + 1].y;
+            if (y > 0) d -= p1[ry][rx + 1].y;
+            q = d - i0[ry + 1][rx + 1] / a.theta;
+        }
+        q1[ry][rx] = q;
+    }
+    __syncthreads();
+    const int x = bx + threadIdx.x, y = by + threadIdx.y;
+    if (x >= a.w || y >= a.h) return;
+    const float qc = q1[threadIdx.y][threadIdx.x];
+    const float gx = x + 1 < a.w ? q1[threadIdx.y][threadIdx.x + 1] - qc : 0.f;
+    const float gy = y + 1 < a.h ? q1[threadIdx.y + 1][threadIdx.x] - qc : 0.f;
+    const float m = 1.f + a.step * sqrtf(gx * gx + gy * gy);
+    const float2 pc = p1[threadIdx.y + 1][threadIdx.x + 1];
+    const int64_t i = (int64_t)y * a.w + x;
+    a.p_out[2 * i] = (pc.x + a.step * gx) / m;
+    a.p_out[2 * i + 1] = (pc.y + a.step * gy) / m;
+}
+
 __global__ void st_texture_kernel(StArgs a, float alpha, float k, uint8_t *tex, int64_t tpitch) {
     const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
     if (x >= a.w || y >= a.h) return;
@@ -365,8 +452,9 @@ cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t 
     if (e != cudaSuccess) return e;
     StArgs a{frame, (int64_t)pitch, w, h, fp.st_theta, 0.125f, p0, p1};
     const dim3 g = grid2(w, h), b(TBX, TBY);
-    for (int it = 0; it < fp.st_iters; ++it) {
-        st_step_kernel<<<g, b, 0, s>>>(a);
+    for (int it = 0; it < fp.st_iters; it += 2) {
+        if (it + 1 < fp.st_iters) st_step2_kernel<<<g, b, 0, s>>>(a);
+        else st_step_kernel<<<g, b, 0, s>>>(a);
         const float *t = a.p;
         a.p = a.p_out;
         a.p_out = const_cast<float *>(t);
