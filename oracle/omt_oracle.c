@@ -904,3 +904,37 @@ void orc_box_mean_flow(const double *flow, int w, int h, const float *boxes, int
         boxes_out[4 * b + 3] = y1 + my;
     }
 }
+
+/* ----------------------------------------------------------- working level
+ * Section V-A (preprocessing): the frame is downscaled by the Gaussian
+ * pyramid and a pyramid level chosen by the input resolution is processed.
+ * Reading: the working frame is level L of the frame's pyramid (as
+ * orc_pyramid builds it) rounded to u8, clamp(floor(v + 0.5), 0, 255); the
+ * level is 0 for frames up to 1280 px wide, 1 up to 2560, 2 above (SD, 2K,
+ * 4K).  Out: L's w_L x h_L texels, row-major. */
+int orc_working_level(int w, int h)
+{
+    (void)h;
+    return w <= 1280 ? 0 : (w <= 2560 ? 1 : 2);
+}
+
+void orc_level_u8(const uint8_t *frame, int w, int h, long pitch, int level, uint8_t *out)
+{
+    const size_t n = orc_pyramid_elems(w, h, level + 1);
+    double *img = (double *)malloc(sizeof(double) * n);
+    double *grad = (double *)malloc(sizeof(double) * 2 * n);
+    orc_pyramid(frame, w, h, pitch, level + 1, img, grad);
+    size_t off = 0;
+    int lw = w, lh = h;
+    for (int l = 0; l < level; ++l) {
+        off += (size_t)lw * lh;
+        lw = (lw + 1) >> 1;
+        lh = (lh + 1) >> 1;
+    }
+    for (size_t i = 0; i < (size_t)lw * lh; ++i) {
+        const double v = floor(img[off + i] + 0.5);
+        out[i] = (uint8_t)(v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v));
+    }
+    free(img);
+    free(grad);
+}

@@ -70,6 +70,9 @@ def lib():
                                c_int, c_double, c_double, c_int, c_int, POINTER(c_double)]
         L.orc_box_mean_flow.argtypes = [POINTER(c_double), c_int, c_int, POINTER(c_float), c_int,
                                         POINTER(c_double)]
+        L.orc_working_level.argtypes = [c_int, c_int]
+        L.orc_working_level.restype = c_int
+        L.orc_level_u8.argtypes = [POINTER(c_uint8), c_int, c_int, c_long, c_int, POINTER(c_uint8)]
         L.orc_max_threads.restype = c_int
         _lib = L
     return _lib
@@ -208,6 +211,21 @@ def lk_track_fb(prev: Pyramid, nxt: Pyramid, pts, fb_max: float, **kw):
     out, st = lk_track(prev, nxt, pts, **kw)
     back, sb = lk_track(nxt, prev, out.astype(np.float32), **kw)
     return out, fb_check(pts, back, sb, st, fb_max), back, sb
+
+
+def working_level(w: int, h: int) -> int:
+    """Pyramid level processed for a w x h frame (Section V-A preprocessing)."""
+    return int(lib().orc_working_level(w, h))
+
+
+def level_u8(frame, level: int):
+    """Level `level` of the frame's pyramid rounded to u8: the working frame."""
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    h, w = f.shape
+    lw, lh = level_size(w, h, level)
+    out = np.zeros((lh, lw), np.uint8)
+    lib().orc_level_u8(_p(f, c_uint8), w, h, w, int(level), _p(out, c_uint8))
+    return out
 
 
 # Section IV readings of the dense flow engine (see omt_oracle.c)
