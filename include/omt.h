@@ -10,6 +10,7 @@
  *   omt_lk_track        pyramidal Lucas-Kanade from frame t to frame t+1
  *   omt_update_boxes    per-box median (or mean) displacement
  *   omt_fb_check        forward-backward consistency of tracked points
+ *   omt_level_u8        the working frame: a pyramid level chosen by resolution
  *
  * Conventions shared by every call
  *   - Pixel centres sit at integer coordinates; a level-L coordinate is the
@@ -263,6 +264,31 @@ int omt_lk_track(const omt_pyramid *prev, const omt_pyramid *next, const float *
 int omt_update_boxes(const float *boxes, const int32_t *offsets, const float *pts,
                      const float *pts_out, const uint8_t *status, int32_t nboxes,
                      const omt_params *prm, float *boxes_out, int32_t *nvalid, void *stream);
+
+/* ------------------------------------------------------- working level
+ * Section V-A (preprocessing): the frame is downscaled by the Gaussian
+ * pyramid and a level chosen by its resolution is processed.  The working
+ * frame of level L is the pyramid's level L rounded to u8; the whole path
+ * (omt_build_pyramid, omt_select_corners, omt_lk_track, omt_update_boxes)
+ * then runs on the working frames, with boxes in level-L pixels. */
+
+/* Working level of a w x h frame: 0 up to 1280 px wide (SD, HD), 1 up to
+ * 2560 (2K), 2 above (4K).  Host only. */
+int32_t omt_working_level(int32_t w, int32_t h);
+
+/* The working frame: level `level` of pyr rounded to u8,
+ * clamp(floor(v + 0.5), 0, 255) (level 0: the frame itself), into out
+ * (device, h_L rows of pitch >= w_L bytes).  pyr must use OMT_F32 storage,
+ * whose levels 0-2 are exact, so the working frames of levels 0-2 are the
+ * definition's bit for bit.  OMT_EINVAL on a bad pyramid or level.
+ * Asynchronous on `stream`. */
+int omt_level_u8(const omt_pyramid *pyr, int32_t level, uint8_t *out, size_t pitch,
+                 void *stream);
+
+/* boxes_out[i] = boxes[i] * scale (every coordinate); device float4[n],
+ * 16-byte aligned (in place allowed).  For scale 2^-L and 2^L (exact),
+ * boxes go to and from level-L pixels.  Asynchronous on `stream`. */
+int omt_scale_boxes(const float *boxes, int32_t n, float scale, float *boxes_out, void *stream);
 
 /* Forward-backward consistency of tracked points (the round-trip test of
  * Kalal, Mikolajczyk and Matas, 2010), a check on the prediction of Section

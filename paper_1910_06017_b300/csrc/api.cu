@@ -459,6 +459,27 @@ int omt_box_mean_flow(const float *flow, int32_t w, int32_t h, const float *boxe
                                           nboxes, (float4 *)boxes_out, (cudaStream_t)stream));
 }
 
+int32_t omt_working_level(int32_t w, int32_t h) {
+    (void)h;
+    return w <= 1280 ? 0 : (w <= 2560 ? 1 : 2);
+}
+
+int omt_level_u8(const omt_pyramid *pyr, int32_t level, uint8_t *out, size_t pitch,
+                 void *stream) {
+    if (!pyr_ok(pyr) || pyr->storage != OMT_F32 || level < 0 || level >= pyr->levels || !out ||
+        pitch < (size_t)pyr->lv[level].w)
+        return OMT_EINVAL;
+    return from_cuda(launch_level_u8(*pyr, level, out, pitch, (cudaStream_t)stream));
+}
+
+int omt_scale_boxes(const float *boxes, int32_t n, float scale, float *boxes_out, void *stream) {
+    if (n < 0 || scale != scale) return OMT_EINVAL;
+    if (n == 0) return OMT_OK;
+    if (!boxes || !boxes_out || !aligned(boxes, 16) || !aligned(boxes_out, 16)) return OMT_EINVAL;
+    return from_cuda(launch_scale_boxes((const float4 *)boxes, n, scale, (float4 *)boxes_out,
+                                        (cudaStream_t)stream));
+}
+
 int omt_lk_wait_timeouts(uint32_t *count) {
     if (!count) return OMT_EINVAL;
     unsigned c = 0;

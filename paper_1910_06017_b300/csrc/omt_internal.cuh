@@ -228,6 +228,10 @@ cudaError_t lk_wait_timeouts_take(unsigned *count);
 cudaError_t launch_lk_batch(const uint8_t *table, int storage, int win, int warps,
                             int ctas_per_sm, int chunk, int backward, cudaStream_t s);
 
+cudaError_t launch_level_u8(const omt_pyramid &p, int level, uint8_t *out, size_t pitch,
+                            cudaStream_t s);
+cudaError_t launch_scale_boxes(const float4 *in, int n, float scale, float4 *out, cudaStream_t s);
+
 size_t st_scratch_bytes(int w, int h);
 size_t tvl1_scratch_bytes(int w, int h);
 cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t pitch,

@@ -29,6 +29,7 @@ EXPORTED = [
     "omt_assign_workspace_bytes", "omt_assign", "omt_update_tracks", "omt_lk_wait_timeouts",
     "omt_fb_check", "omt_default_flow_params", "omt_structure_texture_scratch_bytes",
     "omt_tvl1_scratch_bytes", "omt_structure_texture", "omt_tvl1_flow", "omt_box_mean_flow",
+    "omt_working_level", "omt_level_u8", "omt_scale_boxes",
 ]
 PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES, PHASE_FB = 0, 1, 2, 3, 4
 PT_OK, PT_LOST_EIG, PT_LOST_OOB, PT_NONCONV, PT_LOST_FB = 1, 2, 4, 8, 16
@@ -130,6 +131,10 @@ def lib():
                                         c_void_p, c_void_p, c_void_p, c_void_p]
         L.omt_lk_wait_timeouts.argtypes = [c_void_p]
         L.omt_default_flow_params.argtypes = [POINTER(FlowParams)]
+        L.omt_working_level.argtypes = [c_int32, c_int32]
+        L.omt_working_level.restype = c_int32
+        L.omt_level_u8.argtypes = [POINTER(PyramidDesc), c_int32, c_void_p, c_size_t, c_void_p]
+        L.omt_scale_boxes.argtypes = [c_void_p, c_int32, c_float, c_void_p, c_void_p]
         L.omt_structure_texture_scratch_bytes.argtypes = [c_int32, c_int32]
         L.omt_structure_texture_scratch_bytes.restype = c_size_t
         L.omt_tvl1_scratch_bytes.argtypes = [c_int32, c_int32]
@@ -296,6 +301,23 @@ def lk_track_fb(prev: Pyramid, nxt: Pyramid, pts, params: Params, fb_max: float,
     fb_check(pts, pts_back, status_back, fb_max, status, n_max, n_dev, stream)
 
 
+def working_level(w: int, h: int) -> int:
+    """Pyramid level processed for a w x h frame: 0 SD/HD, 1 2K, 2 4K."""
+    return int(lib().omt_working_level(w, h))
+
+
+def level_u8(pyr: "Pyramid", level: int, out, stream=None):
+    """Level `level` of an F32 pyramid rounded to u8 into out (device (h_L, w_L))."""
+    _check(lib().omt_level_u8(ctypes.byref(pyr.desc), int(level), _ptr(out), out.stride(0),
+                              _stream(stream)), "omt_level_u8")
+
+
+def scale_boxes(boxes, scale: float, out, stream=None):
+    """out = boxes * scale (device (n, 4) float32)."""
+    _check(lib().omt_scale_boxes(_ptr(boxes), boxes.shape[0], float(scale), _ptr(out),
+                                 _stream(stream)), "omt_scale_boxes")
+
+
 def default_flow_params(**kw) -> FlowParams:
     """Dense-flow parameters (the library's readings), with overrides;
     `lambda_` is the data weight."""
@@ -454,6 +476,44 @@ class StreamTracker:
         update_boxes(boxes, self.offsets, self.pts, self.pts_out, self.status, self.params,
                      self.boxes_out[:nb], self.nvalid[:nb], stream)
         self.cur = 1 - self.cur
+        return self.boxes_out[:nb]
+
+
+class WorkingLevelTracker:
+    """The plain path on a frame's working level (Section V-A preprocessing:
+    a pyramid level chosen by resolution).  Each incoming frame is reduced
+    to its working frame (an F32 pyramid of level+1 levels, its last level
+    rounded to u8), and a StreamTracker of the working size tracks the boxes
+    scaled into level-L pixels; boxes come back in level-0 pixels.  Every
+    step is C-ABI calls on one stream."""
+
+    def __init__(self, w: int, h: int, params: Params, max_boxes: int, level=None,
+                 device="cuda"):
+        import torch
+        self.level = working_level(w, h) if level is None else int(level)
+        self.reduce = default_params(levels=self.level + 1, storage=F32)
+        self.full = Pyramid(w, h, self.level + 1, F32, device)
+        self.lw, self.lh = self.full.level_size(self.level)
+        self.work = torch.empty((self.lh, self.lw), dtype=torch.uint8, device=device)
+        self.inner = StreamTracker(self.lw, self.lh, params, max_boxes, device)
+        self.boxes_work = torch.empty((max(1, max_boxes), 4), dtype=torch.float32, device=device)
+        self.boxes_out = torch.empty((max(1, max_boxes), 4), dtype=torch.float32, device=device)
+
+    def _working_frame(self, frame, stream=None):
+        build_pyramid(frame, self.full, self.reduce, stream)
+        level_u8(self.full, self.level, self.work, stream)
+
+    def prime(self, frame, stream=None):
+        self._working_frame(frame, stream)
+        self.inner.prime(self.work, stream)
+
+    def step(self, frame_next, boxes, stream=None):
+        """Track boxes (nb, 4, level-0 px) of frame t into frame t+1."""
+        nb = boxes.shape[0]
+        self._working_frame(frame_next, stream)
+        scale_boxes(boxes, 2.0 ** -self.level, self.boxes_work[:nb], stream)
+        out = self.inner.step(self.work, self.boxes_work[:nb], stream)
+        scale_boxes(out, 2.0 ** self.level, self.boxes_out[:nb], stream)
         return self.boxes_out[:nb]
 
 
