@@ -281,3 +281,20 @@ def test_flow_engine_arguments_rejected_before_launch():
     assert lib.omt_box_mean_flow(fake, 64, 48, ctypes.c_void_p((1 << 24) + 8), 3,
                                  ctypes.c_void_p(1 << 25), None) == omt.EINVAL
     assert lib.omt_box_mean_flow(None, 64, 48, None, 0, None, None) == omt.OK
+
+
+def test_working_level_arguments_rejected_before_launch():
+    lib = omt.lib()
+    assert [lib.omt_working_level(w, h) for w, h in ((720, 576), (1920, 1080), (3840, 2160))] == [0, 1, 2]
+    d32, d16 = omt.PyramidDesc(), omt.PyramidDesc()
+    assert lib.omt_pyramid_init(ctypes.byref(d32), 64, 48, 3, 0, ctypes.c_void_p(1 << 20),
+                                omt.pyramid_bytes(64, 48, 3, 0)) == 0
+    assert lib.omt_pyramid_init(ctypes.byref(d16), 64, 48, 3, 1, ctypes.c_void_p(1 << 22),
+                                omt.pyramid_bytes(64, 48, 3, 1)) == 0
+    fake = ctypes.c_void_p(1 << 24)
+    assert lib.omt_level_u8(ctypes.byref(d16), 1, fake, 64, None) == omt.EINVAL   # F16 storage
+    assert lib.omt_level_u8(ctypes.byref(d32), 3, fake, 64, None) == omt.EINVAL   # no such level
+    assert lib.omt_level_u8(ctypes.byref(d32), 1, fake, 31, None) == omt.EINVAL   # pitch < 32
+    assert lib.omt_scale_boxes(None, 0, ctypes.c_float(0.5), None, None) == omt.OK
+    assert lib.omt_scale_boxes(ctypes.c_void_p((1 << 24) + 4), 2, ctypes.c_float(0.5), fake,
+                               None) == omt.EINVAL
