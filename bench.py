@@ -425,13 +425,27 @@ def flow_frames(seed: int = 0):
 
 
 def flow_bytes_per_l0px(omt, fp) -> float:
-    """Algorithmic DRAM bytes of the TV-L1 iterations per level-0 pixel: an
-    iteration reads the state once -- the extrapolated flow (8 B), the duals
-    (16 B), the flow (8 B), the warped gradient (8 B), rho0 (4 B) -- and
-    writes the duals, the flow and its extrapolation (32 B): 76 B per pixel
-    and iteration; each level adds a quarter of the one below."""
+    """Algorithmic DRAM bytes of the TV-L1 iteration launches per level-0
+    pixel: a launch (one iteration, or two when fp.block is 2) reads the
+    state once -- the extrapolated flow (8 B), the duals (16 B), the flow
+    (8 B), the warped gradient (8 B), rho0 (4 B) -- and writes the duals,
+    the flow and its extrapolation (32 B): 76 B per pixel and launch; each
+    level adds a quarter of the one below."""
     area = sum(4.0 ** -L for L in range(FLOW_LEVELS))
-    return 76.0 * fp.warps * fp.iters * area
+    per = 2 if fp.block == 2 else 1
+    launches = fp.iters // per + fp.iters % per
+    return 76.0 * fp.warps * launches * area
+
+
+def flow_launches_per_step(fp):
+    """Kernels one flow step launches: the projection steps (two per launch
+    when fp.block is 2) and the texture; one pyramid kernel per level; per
+    level the upsampling and, per warp, the warp kernel and the primal-dual
+    launches (pairs, then a single one for an odd count); the box means."""
+    per = 2 if fp.block == 2 else 1
+    st = fp.st_iters // per + fp.st_iters % per
+    pd = fp.iters // per + fp.iters % per
+    return st + 1 + FLOW_LEVELS + FLOW_LEVELS * (1 + fp.warps * (1 + pd)) + 1
 
 
 def run_flow(args):
@@ -517,14 +531,13 @@ def run_flow(args):
                    "median_box_motion_last_step": np.median(moved, 0).tolist()},
         "e2e": {"value": 1e3 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": w * h,
                 "d2h_bytes_per_step": int(bo.numel() * 4)},
-        "roofline": {"kernel": "pd_kernel, the TV-L1 iterations (all levels)", "bound": "hbm",
+        "roofline": {"kernel": "pd2_kernel, the TV-L1 iterations (all levels)", "bound": "hbm",
                      "achieved": byts / (tv_ms * 1e-3) / 1e9, "peak": hbm,
                      "unit": "GB/s", "frac": byts / (tv_ms * 1e-3) / 1e9 / hbm,
                      "peak_source": pk_src, "traffic": None,
                      "bytes_per_level0_px": flow_bytes_per_l0px(omt, fp)},
         "clocks": clk,
-        "gpu_launches": (2 * fp.st_iters + 1 + 5 + FLOW_LEVELS * (2 + fp.warps * (1 + 2 * fp.iters))
-                         + 1) * args.steps,
+        "gpu_launches": flow_launches_per_step(fp) * args.steps,
     }
 
 

@@ -413,10 +413,14 @@ typedef struct omt_flow_params {
     float eps;        /* Huber parameter of the total variation, >= 0           */
     int32_t warps;    /* warps per pyramid level, >= 1                          */
     int32_t iters;    /* primal-dual iterations per warp, >= 1                  */
+    int32_t block;    /* projection steps and primal-dual iterations carried  *
+                       * out per kernel launch: 1 or 2.  The results are the  *
+                       * same bit for bit; 2 reads and writes the state once  *
+                       * per two steps (temporal blocking).                   */
 } omt_flow_params;
 
 /* Defaults: st_theta 1/8, st_alpha 0.95, st_k 2, 100 steps; lambda 10,
- * eps 0.05, 3 warps, 30 iterations. */
+ * eps 0.05, 3 warps, 30 iterations; 2 per launch. */
 void omt_default_flow_params(omt_flow_params *p);
 
 /* Device scratch bytes of omt_structure_texture / omt_tvl1_flow. */

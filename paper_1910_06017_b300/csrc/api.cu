@@ -404,6 +404,7 @@ void omt_default_flow_params(omt_flow_params *p) {
     p->eps = 0.05f;
     p->warps = 3;
     p->iters = 30;
+    p->block = 2;
 }
 
 namespace {
@@ -411,7 +412,8 @@ bool flow_params_ok(const omt_flow_params *p) {
     return p && p->st_theta > 0.0f && isfinite(p->st_theta) && isfinite(p->st_alpha) &&
            isfinite(p->st_k) && p->st_iters >= 0 && p->st_iters <= 100000 && p->lambda >= 0.0f &&
            isfinite(p->lambda) && p->eps >= 0.0f && isfinite(p->eps) && p->warps >= 1 &&
-           p->warps <= 100 && p->iters >= 1 && p->iters <= 100000;
+           p->warps <= 100 && p->iters >= 1 && p->iters <= 100000 &&
+           (p->block == 1 || p->block == 2);
 }
 }  // namespace
 

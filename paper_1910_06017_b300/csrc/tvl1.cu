@@ -2,26 +2,34 @@
 // prediction (Section V-A).
 //
 // Structure-texture: the ROF structure S of the u8 frame by Chambolle's dual
-// projection (one launch per step, q = div p - I / theta formed in shared
-// memory for a tile and its halo, the dual field ping-ponged in global
-// memory), then the u8 texture clamp(floor(k (I - alpha S) + 128.5)).
+// projection (one or two steps per launch, q = div p - I / theta formed in
+// shared memory for a tile and its halo, the dual field ping-ponged in
+// global memory), then the u8 texture clamp(floor(k (I - alpha S) + 128.5)).
 // Huber-TV-L1: per pyramid level (FP32 storage, coarse to fine) the flow of
 // the level above is sampled bilinearly at (x/2, y/2) and doubled; per warp
 // one launch samples frame t+1 and its gradient at x + u0 (taps clamped) and
-// stores grad I1w and rho0, then every primal-dual iteration is one launch
-// (pd_kernel): the duals from the extrapolated flow (forward differences, a
-// Huber shrink and the projection onto the unit disc, per flow component)
-// in shared memory for a tile and its halo, then the flow (backward-
-// difference divergence, the pointwise prox of the L1 data term, the
-// extrapolation).  Every expression keeps the order of the definition, in
-// FP32.  Each iteration reads and writes every field once: the kernel is
-// bound by HBM (or L2 for small levels).
+// stores grad I1w and rho0, then the primal-dual iterations run one
+// (pd_kernel) or two (pd2_kernel) per launch: the duals from the
+// extrapolated flow (forward differences, a Huber shrink and the projection
+// onto the unit disc, per flow component) in shared memory for a tile and
+// its halo, then the flow (backward-difference divergence, the pointwise
+// prox of the L1 data term, the extrapolation).  Every expression keeps the
+// order of the definition, in FP32, and both launch forms give the same bits.
+// A launch reads and writes every field once: the kernels are bound by HBM
+// (or L2 for small levels).
 #include "omt_internal.cuh"
 
 namespace omt {
 namespace {
 
-constexpr int TBX = 32, TBY = 8;
+constexpr int TBX = 32, TBY = 8;   // threads of a CTA
+#ifndef OMT_ST_TH
+#define OMT_ST_TH 32
+#endif
+#ifndef OMT_PD_TH
+#define OMT_PD_TH 16
+#endif
+constexpr int ST_TH = OMT_ST_TH, PD_TH = OMT_PD_TH;  // tile rows of the blocked kernels
 
 // div of an interleaved dual field (px, py), component c of cc, at (x, y).
 __device__ __forceinline__ float div_bwd(const float *p, int cc, int c, int w, int h, int x, int y) {
@@ -34,150 +42,200 @@ __device__ __forceinline__ float div_bwd(const float *p, int cc, int c, int w, i
     return d;
 }
 
+// Asynchronous copy of N (4, 8 or 16) bytes from global into shared memory,
+// or N zero bytes when !valid (nothing is read then; gmem must still be a
+// valid address).  The copies of a region are issued back to back and
+// awaited once, so a thread keeps all of its loads in flight together.
+template <int N>
+__device__ __forceinline__ void cp_zfill(void *smem, const void *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int src = valid ? N : 0;
+    if constexpr (N == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(N),
+                     "r"(src)
+                     : "memory");
+}
+
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Calls fn(rx, ry) for every position of an RW x RH region, RW in
+// (TBX, 2 TBX]: the TBX x TBY threads sweep it by rows, a thread taking
+// column tx and, for the last RW - TBX columns, tx + TBX.
+template <int RW, int RH, class F>
+__device__ __forceinline__ void sweep(F &&fn) {
+    static_assert(RW > TBX && RW <= 2 * TBX, "region width");
+    for (int ry = threadIdx.y; ry < RH; ry += TBY) {
+        fn((int)threadIdx.x, ry);
+        if (threadIdx.x < RW - TBX) fn((int)threadIdx.x + TBX, ry);
+    }
+}
+
+// Programmatic dependent launch: every kernel of the chain below is launched
+// so that it may be scheduled while its predecessor in the stream drains;
+// it waits for that grid to complete (and its writes to be visible) before
+// touching global memory, then lets its own successor be scheduled.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------ structure-texture
 struct StArgs {
     const uint8_t *img;
     int64_t pitch;
     int w, h;
-    float theta, step;
+    float theta, rtheta, step;  // rtheta = 1 / theta
     const float *p;  // (px, py) interleaved, w x h
     float *p_out;
 };
 
-// One projection step for a TBX x TBY tile: q = div p - I / theta on the
-// tile plus its right column and bottom row in shared memory (from p on the
-// tile plus one pixel on every side), then the tile's new duals from the
-// forward differences of q.  Equal to forming q everywhere and then p.
-__global__ void __launch_bounds__(TBX * TBY) st_step_kernel(StArgs a) {
-    constexpr int QW = TBX + 1, QH = TBY + 1, RW = TBX + 2, RH = TBY + 2;
-    __shared__ float2 spp[RH][RW];
-    __shared__ float sq[QH][QW];
-    const int tid = threadIdx.y * TBX + threadIdx.x;
-    const int bx = blockIdx.x * TBX, by = blockIdx.y * TBY;
-    for (int k = tid; k < RW * RH; k += TBX * TBY) {
-        const int ry = k / RW, rx = k - ry * RW;
-        const int x = bx - 1 + rx, y = by - 1 + ry;
-        spp[ry][rx] = (x >= 0 && x < a.w && y >= 0 && y < a.h)
-                          ? make_float2(a.p[2 * ((int64_t)y * a.w + x)], a.p[2 * ((int64_t)y * a.w + x) + 1])
-                          : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    for (int k = tid; k < QW * QH; k += TBX * TBY) {
-        const int ry = k / QW, rx = k - ry * QW;
-        const int x = bx + rx, y = by + ry;
-        float q = 0.f;
-        if (x < a.w && y < a.h) {
-            // div p at (x, y): spp holds (x, y) at [ry + 1][rx + 1]
-            float d = 0.f;
-            if (x + 1 < a.w) d += spp[ry + 1][rx + 1].x;
-            if (x > 0) d -= spp[ry + 1][rx].x;
-            if (y + 1 < a.h) d += spp[ry + 1][rx + 1].y;
-            if (y > 0) d -= spp[ry][rx + 1].y;
-            q = d - (float)a.img[(int64_t)y * a.pitch + x] / a.theta;
-        }
-        sq[ry][rx] = q;
-    }
-    __syncthreads();
-    const int x = bx + threadIdx.x, y = by + threadIdx.y;
-    if (x >= a.w || y >= a.h) return;
-    const float qc = sq[threadIdx.y][threadIdx.x];
-    const float gx = x + 1 < a.w ? sq[threadIdx.y][threadIdx.x + 1] - qc : 0.f;
-    const float gy = y + 1 < a.h ? sq[threadIdx.y + 1][threadIdx.x] - qc : 0.f;
-    const float m = 1.f + a.step * sqrtf(gx * gx + gy * gy);
-    const int64_t i = (int64_t)y * a.w + x;
-    const float2 pc = spp[threadIdx.y + 1][threadIdx.x + 1];
-    a.p_out[2 * i] = (pc.x + a.step * gx) / m;
-    a.p_out[2 * i + 1] = (pc.y + a.step * gy) / m;
+// Chambolle's projection update of the dual at a position from the forward
+// differences (gx, gy) of q = div p - I / theta there.
+__device__ __forceinline__ float2 st_dual(float2 pc, float gx, float gy, float step) {
+    const float rm = 1.0f / (1.f + step * sqrtf(gx * gx + gy * gy));
+    return make_float2((pc.x + step * gx) * rm, (pc.y + step * gy) * rm);
 }
 
-// Two projection steps for a TBX x TBY tile in one launch: the duals of the
+// div p - I / theta at an inside position (x, y) from the duals there (c)
+// and at the left (l) and upper (u) neighbours.
+__device__ __forceinline__ float st_q(float2 c, float2 l, float2 u, int x, int y, int w, int h,
+                                      float img, float rtheta) {
+    float d = 0.f;
+    if (x + 1 < w) d += c.x;
+    if (x > 0) d -= l.x;
+    if (y + 1 < h) d += c.y;
+    if (y > 0) d -= u.y;
+    return d - img * rtheta;
+}
+
+// One projection step for a TBX x TH tile: q on the tile plus its right
+// column and bottom row in shared memory (from p on the tile plus one pixel
+// on every side), then the tile's new duals from the forward differences
+// of q.  Equal to forming q everywhere and then p.
+template <int TH>
+__global__ void __launch_bounds__(TBX * TBY) st_step_kernel(StArgs a) {
+    pdl_begin();
+    constexpr int QW = TBX + 1, QH = TH + 1, RW = TBX + 2, RH = TH + 2;
+    __shared__ float2 spp[RH][RW];
+    __shared__ float sq[QH][QW];
+    const int bx = blockIdx.x * TBX, by = blockIdx.y * TH;
+    auto inside = [&](int x, int y) { return x >= 0 && x < a.w && y >= 0 && y < a.h; };
+    sweep<RW, RH>([&](int rx, int ry) {
+        const int x = bx - 1 + rx, y = by - 1 + ry;
+        const bool in = inside(x, y);
+        cp_zfill<8>(&spp[ry][rx], in ? a.p + 2 * ((int64_t)y * a.w + x) : a.p, in);
+    });
+    cp_wait_all();
+    __syncthreads();
+    // q on [0, TBX] x [0, TH]; spp holds (x, y) at [ry + 1][rx + 1]
+    sweep<QW, QH>([&](int rx, int ry) {
+        const int x = bx + rx, y = by + ry;
+        if (inside(x, y))
+            sq[ry][rx] = st_q(spp[ry + 1][rx + 1], spp[ry + 1][rx], spp[ry][rx + 1], x, y, a.w, a.h,
+                              (float)a.img[(int64_t)y * a.pitch + x], a.rtheta);
+    });
+    __syncthreads();
+    for (int ty = threadIdx.y; ty < TH; ty += TBY) {
+        const int tx = threadIdx.x, x = bx + tx, y = by + ty;
+        if (x >= a.w || y >= a.h) continue;
+        const float qc = sq[ty][tx];
+        const float gx = x + 1 < a.w ? sq[ty][tx + 1] - qc : 0.f;
+        const float gy = y + 1 < a.h ? sq[ty + 1][tx] - qc : 0.f;
+        const float2 pn = st_dual(spp[ty + 1][tx + 1], gx, gy, a.step);
+        reinterpret_cast<float2 *>(a.p_out)[(int64_t)y * a.w + x] = pn;
+    }
+}
+
+// Two projection steps for a TBX x TH tile in one launch: the duals of the
 // intermediate step are formed in shared memory on the tile grown by the
 // pixels the second step reads (temporal blocking), so a launch reads p and
-// I once and writes p once for two steps.  Positions outside the frame are
-// formed as zero and never read by a position inside it.  Equal to two
-// st_step_kernel launches bit for bit.
+// I once and writes p once for two steps.  Each stage updates the inside
+// positions of its region from the previous stage's values, by the same
+// expressions as st_step_kernel, so the result equals two st_step_kernel
+// launches bit for bit; positions outside the frame are never read by a
+// position inside it.
+template <int TH>
 __global__ void __launch_bounds__(TBX * TBY) st_step2_kernel(StArgs a) {
-    // regions (origin offset, width, height) relative to the tile origin:
-    // P0 p^n [-2, TBX+1], Q0 q^n [-1, TBX+1], P1 p^n+1 [-1, TBX], Q1 q^n+1 [0, TBX]
-    constexpr int P0W = TBX + 4, P0H = TBY + 4, Q0W = TBX + 3, Q0H = TBY + 3;
-    constexpr int P1W = TBX + 2, P1H = TBY + 2, Q1W = TBX + 1, Q1H = TBY + 1;
-    __shared__ float2 p0[P0H][P0W];
-    __shared__ float q0[Q0H][Q0W];
-    __shared__ float i0[Q0H][Q0W];
-    __shared__ float2 p1[P1H][P1W];
-    __shared__ float q1[Q1H][Q1W];
-    const int tid = threadIdx.y * TBX + threadIdx.x;
-    const int bx = blockIdx.x * TBX, by = blockIdx.y * TBY;
+    pdl_begin();
+    // regions (origin offset, extent) relative to the tile origin:
+    // P p^n, then p^n+1 on [-1, TBX]: [-2, TBX + 1]; Q q^n: [-1, TBX + 1], then
+    // q^n+1 on [0, TBX]; I the frame on Q's region
+    constexpr int PW = TBX + 4, PH = TH + 4, QW = TBX + 3, QH = TH + 3;
+    constexpr int P1W = TBX + 2, P1H = TH + 2, Q1W = TBX + 1, Q1H = TH + 1;
+    __shared__ float2 sp[PH][PW];
+    __shared__ float sq[QH][QW];
+    __shared__ float si[QH][QW];
+    const int bx = blockIdx.x * TBX, by = blockIdx.y * TH;
     auto inside = [&](int x, int y) { return x >= 0 && x < a.w && y >= 0 && y < a.h; };
-    for (int k = tid; k < P0W * P0H; k += TBX * TBY) {
-        const int ry = k / P0W, rx = k - ry * P0W, x = bx - 2 + rx, y = by - 2 + ry;
-        p0[ry][rx] = inside(x, y) ? make_float2(a.p[2 * ((int64_t)y * a.w + x)],
-                                                a.p[2 * ((int64_t)y * a.w + x) + 1])
-                                  : make_float2(0.f, 0.f);
-    }
-    for (int k = tid; k < Q0W * Q0H; k += TBX * TBY) {
-        const int ry = k / Q0W, rx = k - ry * Q0W, x = bx - 1 + rx, y = by - 1 + ry;
-        i0[ry][rx] = inside(x, y) ? (float)a.img[(int64_t)y * a.pitch + x] : 0.f;
-    }
+    sweep<PW, PH>([&](int rx, int ry) {
+        const int x = bx - 2 + rx, y = by - 2 + ry;
+        const bool in = inside(x, y);
+        cp_zfill<8>(&sp[ry][rx], in ? a.p + 2 * ((int64_t)y * a.w + x) : a.p, in);
+    });
+    sweep<QW, QH>([&](int rx, int ry) {
+        const int x = bx - 1 + rx, y = by - 1 + ry;
+        if (inside(x, y)) si[ry][rx] = (float)a.img[(int64_t)y * a.pitch + x];
+    });
+    cp_wait_all();
     __syncthreads();
-    // q^n on Q0: div p^n - I / theta; Q0 (rx, ry) is P0 (rx + 1, ry + 1)
-    for (int k = tid; k < Q0W * Q0H; k += TBX * TBY) {
-        const int ry = k / Q0W, rx = k - ry * Q0W, x = bx - 1 + rx, y = by - 1 + ry;
-        float q = 0.f;
+    // q^n on Q; Q (rx, ry) is P (rx + 1, ry + 1)
+    sweep<QW, QH>([&](int rx, int ry) {
+        const int x = bx - 1 + rx, y = by - 1 + ry;
+        if (inside(x, y))
+            sq[ry][rx] = st_q(sp[ry + 1][rx + 1], sp[ry + 1][rx], sp[ry][rx + 1], x, y, a.w, a.h,
+                              si[ry][rx], a.rtheta);
+    });
+    __syncthreads();
+    // p^n+1 on [-1, TBX] x [-1, TH]: Q (rx, ry), P (rx + 1, ry + 1)
+    sweep<P1W, P1H>([&](int rx, int ry) {
+        const int x = bx - 1 + rx, y = by - 1 + ry;
         if (inside(x, y)) {
-            float d = 0.f;
-            if (x + 1 < a.w) d += p0[ry + 1][rx + 1].x;
-            if (x > 0) d -= p0[ry + 1][rx].x;
-            if (y + 1 < a.h) d += p0[ry + 1][rx + 1].y;
-            if (y > 0) d -= p0[ry][rx + 1].y;
-            q = d - i0[ry][rx] / a.theta;
+            const float qc = sq[ry][rx];
+            const float gx = x + 1 < a.w ? sq[ry][rx + 1] - qc : 0.f;
+            const float gy = y + 1 < a.h ? sq[ry + 1][rx] - qc : 0.f;
+            sp[ry + 1][rx + 1] = st_dual(sp[ry + 1][rx + 1], gx, gy, a.step);
         }
-        q0[ry][rx] = q;
-    }
+    });
     __syncthreads();
-    // p^n+1 on P1; P1 (rx, ry) is Q0 (rx, ry) and P0 (rx + 1, ry + 1)
-    for (int k = tid; k < P1W * P1H; k += TBX * TBY) {
-        const int ry = k / P1W, rx = k - ry * P1W, x = bx - 1 + rx, y = by - 1 + ry;
-        float2 pn = make_float2(0.f, 0.f);
-        if (inside(x, y)) {
-            const float qc = q0[ry][rx];
-            const float gx = x + 1 < a.w ? q0[ry][rx + 1] - qc : 0.f;
-            const float gy = y + 1 < a.h ? q0[ry + 1][rx] - qc : 0.f;
-            const float m = 1.f + a.step * sqrtf(gx * gx + gy * gy);
-            const float2 pc = p0[ry + 1][rx + 1];
-            pn = make_float2((pc.x + a.step * gx) / m, (pc.y + a.step * gy) / m);
-        }
-        p1[ry][rx] = pn;
-    }
+    // q^n+1 on [0, TBX] x [0, TH]: Q (rx + 1, ry + 1), P (rx + 2, ry + 2)
+    sweep<Q1W, Q1H>([&](int rx, int ry) {
+        const int x = bx + rx, y = by + ry;
+        if (inside(x, y))
+            sq[ry + 1][rx + 1] = st_q(sp[ry + 2][rx + 2], sp[ry + 2][rx + 1], sp[ry + 1][rx + 2], x,
+                                      y, a.w, a.h, si[ry + 1][rx + 1], a.rtheta);
+    });
     __syncthreads();
-    // q^n+1 on Q1; Q1 (rx, ry) is P1 (rx + 1, ry + 1) and Q0 (rx + 1, ry + 1)
-    for (int k = tid; k < Q1W * Q1H; k += TBX * TBY) {
-        const int ry = k / Q1W, rx = k - ry * Q1W, x = bx + rx, y = by + ry;
-        float q = 0.f;
-        if (inside(x, y)) {
-            float d = 0.f;
-            if (x + 1 < a.w) d += p1[ry + 1][rx + 1].x;
-            if (x > 0) d -= p1[ry + 1][rx].x;
-            if (y + 1 < a.h) d += p1[ry + 1][rx + 1].y;
-            if (y > 0) d -= p1[ry][rx + 1].y;
-            q = d - i0[ry + 1][rx + 1] / a.theta;
-        }
-        q1[ry][rx] = q;
+    for (int ty = threadIdx.y; ty < TH; ty += TBY) {
+        const int tx = threadIdx.x, x = bx + tx, y = by + ty;
+        if (x >= a.w || y >= a.h) continue;
+        const float qc = sq[ty + 1][tx + 1];
+        const float gx = x + 1 < a.w ? sq[ty + 1][tx + 2] - qc : 0.f;
+        const float gy = y + 1 < a.h ? sq[ty + 2][tx + 1] - qc : 0.f;
+        const float2 pn = st_dual(sp[ty + 2][tx + 2], gx, gy, a.step);
+        reinterpret_cast<float2 *>(a.p_out)[(int64_t)y * a.w + x] = pn;
     }
-    __syncthreads();
-    const int x = bx + threadIdx.x, y = by + threadIdx.y;
-    if (x >= a.w || y >= a.h) return;
-    const float qc = q1[threadIdx.y][threadIdx.x];
-    const float gx = x + 1 < a.w ? q1[threadIdx.y][threadIdx.x + 1] - qc : 0.f;
-    const float gy = y + 1 < a.h ? q1[threadIdx.y + 1][threadIdx.x] - qc : 0.f;
-    const float m = 1.f + a.step * sqrtf(gx * gx + gy * gy);
-    const float2 pc = p1[threadIdx.y + 1][threadIdx.x + 1];
-    const int64_t i = (int64_t)y * a.w + x;
-    a.p_out[2 * i] = (pc.x + a.step * gx) / m;
-    a.p_out[2 * i + 1] = (pc.y + a.step * gy) / m;
 }
 
 __global__ void st_texture_kernel(StArgs a, float alpha, float k, uint8_t *tex, int64_t tpitch) {
+    pdl_begin();
     const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
     if (x >= a.w || y >= a.h) return;
     const float I = (float)a.img[(int64_t)y * a.pitch + x];
@@ -221,7 +279,8 @@ __device__ __forceinline__ float level_bilin(const LevelF &L, int ix, int iy, fl
 
 struct FlowLevel {
     int w, h;
-    float2 *u;               // flow
+    float2 *u;               // flow (updated in place by pd_kernel)
+    float2 *u_out;           // flow written by pd2_kernel (ping-pong with u)
     float2 *ub, *ub_out;     // extrapolated flow: read, written (ping-pong)
     float4 *p, *p_out;       // duals (p1x, p1y, p2x, p2y): read, written (ping-pong)
     float2 *gw;              // grad I1 at x + u0, scaled to [0, 1] intensities
@@ -229,6 +288,7 @@ struct FlowLevel {
 };
 
 __global__ void upsample_kernel(const float2 *coarse, int cw, int ch, float2 *u, int w, int h) {
+    pdl_begin();
     const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
     if (x >= w || y >= h) return;
     float2 v = make_float2(0.f, 0.f);
@@ -244,6 +304,7 @@ __global__ void upsample_kernel(const float2 *coarse, int cw, int ch, float2 *u,
 }
 
 __global__ void warp_kernel(FlowLevel f, LevelF I0, LevelF I1) {
+    pdl_begin();
     const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;
     if (x >= f.w || y >= f.h) return;
     const int64_t i = (int64_t)y * f.w + x;
@@ -275,32 +336,79 @@ __global__ void warp_kernel(FlowLevel f, LevelF I0, LevelF I1) {
 constexpr int PW = TBX + 1, PH = TBY + 1;   // dual region
 constexpr int UW = TBX + 2, UH = TBY + 2;   // extrapolated-flow region
 
-__device__ __forceinline__ float4 dual_step(float4 p, float2 c, float2 r, float2 d, float sigma,
-                                            float den) {
-    const float g1x = r.x - c.x, g1y = d.x - c.x, g2x = r.y - c.y, g2y = d.y - c.y;
-    float qx = (p.x + sigma * g1x) / den, qy = (p.y + sigma * g1y) / den;
-    float m = sqrtf(qx * qx + qy * qy);
-    if (m > 1.0f) {
-        qx /= m;
-        qy /= m;
+__device__ __forceinline__ float2 project_unit(float qx, float qy) {
+    const float m2 = qx * qx + qy * qy;
+    if (m2 > 1.0f) {
+        const float r = rsqrtf(m2);
+        qx *= r;
+        qy *= r;
     }
-    float4 o;
-    o.x = qx;
-    o.y = qy;
-    qx = (p.z + sigma * g2x) / den;
-    qy = (p.w + sigma * g2y) / den;
-    m = sqrtf(qx * qx + qy * qy);
-    if (m > 1.0f) {
-        qx /= m;
-        qy /= m;
-    }
-    o.z = qx;
-    o.w = qy;
-    return o;
+    return make_float2(qx, qy);
 }
 
-__global__ void __launch_bounds__(TBX * TBY) pd_kernel(FlowLevel f, float sigma, float eps, float tau,
+// The dual update of both flow components at a position from the
+// extrapolated flow there (c) and at the right (r) and lower (d)
+// neighbours: (p + sigma grad ubar) / (1 + sigma eps), then the projection
+// onto the unit disc.  rden = 1 / (1 + sigma eps).
+__device__ __forceinline__ float4 dual_step(float4 p, float2 c, float2 r, float2 d, float sigma,
+                                            float rden) {
+    const float g1x = r.x - c.x, g1y = d.x - c.x, g2x = r.y - c.y, g2y = d.y - c.y;
+    const float2 q1 = project_unit((p.x + sigma * g1x) * rden, (p.y + sigma * g1y) * rden);
+    const float2 q2 = project_unit((p.z + sigma * g2x) * rden, (p.w + sigma * g2y) * rden);
+    return make_float4(q1.x, q1.y, q2.x, q2.y);
+}
+
+// The primal update at (x, y) from the new duals there (pc) and at the left
+// (pl) and upper (pu) neighbours: the backward-difference divergence of each
+// dual field in the order the definition writes it, then the pointwise prox
+// of tau lambda |rho| at u + tau div p.
+__device__ __forceinline__ float2 primal_step(float4 pc, float4 pl, float4 pu, int x, int y, int w,
+                                              int h, float2 u, float2 g, float r0, float tau,
+                                              float lambda) {
+    float d1 = 0.f, d2 = 0.f;
+    if (x + 1 < w) {
+        d1 += pc.x;
+        d2 += pc.z;
+    }
+    if (x > 0) {
+        d1 -= pl.x;
+        d2 -= pl.z;
+    }
+    if (y + 1 < h) {
+        d1 += pc.y;
+        d2 += pc.w;
+    }
+    if (y > 0) {
+        d1 -= pu.y;
+        d2 -= pu.w;
+    }
+    const float t1 = u.x + tau * d1, t2 = u.y + tau * d2;
+    const float g2 = g.x * g.x + g.y * g.y;
+    const float rho = r0 + g.x * t1 + g.y * t2;
+    const float th = tau * lambda * g2;
+    float v1 = t1, v2 = t2;
+    if (rho < -th) {
+        v1 = t1 + tau * lambda * g.x;
+        v2 = t2 + tau * lambda * g.y;
+    } else if (rho > th) {
+        v1 = t1 - tau * lambda * g.x;
+        v2 = t2 - tau * lambda * g.y;
+    } else if (g2 > 0.f) {
+        const float sr = rho / g2;
+        v1 = t1 - sr * g.x;
+        v2 = t2 - sr * g.y;
+    }
+    return make_float2(v1, v2);
+}
+
+// The extrapolation ubar = 2 u - u_previous.
+__device__ __forceinline__ float2 extrapolate(float2 v, float2 u) {
+    return make_float2(2.0f * v.x - u.x, 2.0f * v.y - u.y);
+}
+
+__global__ void __launch_bounds__(TBX * TBY) pd_kernel(FlowLevel f, float sigma, float rden, float tau,
                                                        float lambda) {
+    pdl_begin();
     __shared__ float2 sub[UH][UW];
     __shared__ float4 sp[PH][PW];
     const int tid = threadIdx.y * TBX + threadIdx.x;
@@ -312,7 +420,6 @@ __global__ void __launch_bounds__(TBX * TBY) pd_kernel(FlowLevel f, float sigma,
                                                                   : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const float den = 1.0f + sigma * eps;
     for (int k = tid; k < PW * PH; k += TBX * TBY) {
         const int ry = k / PW, rx = k - ry * PW;
         const int x = x0 + rx, y = y0 + ry;
@@ -321,7 +428,7 @@ __global__ void __launch_bounds__(TBX * TBY) pd_kernel(FlowLevel f, float sigma,
             const float2 c = sub[ry][rx];
             const float2 r = x + 1 < f.w ? sub[ry][rx + 1] : c;
             const float2 d = y + 1 < f.h ? sub[ry + 1][rx] : c;
-            pn = dual_step(f.p[(int64_t)y * f.w + x], c, r, d, sigma, den);
+            pn = dual_step(f.p[(int64_t)y * f.w + x], c, r, d, sigma, rden);
         }
         sp[ry][rx] = pn;
     }
@@ -332,43 +439,106 @@ __global__ void __launch_bounds__(TBX * TBY) pd_kernel(FlowLevel f, float sigma,
     const int64_t i = (int64_t)y * f.w + x;
     const float4 pc = sp[ty][tx];
     f.p_out[i] = pc;
-    // div of p1 = (p.x, p.y) and of p2 = (p.z, p.w), as the definition orders it
-    float d1 = 0.f, d2 = 0.f;
-    if (x + 1 < f.w) {
-        d1 += pc.x;
-        d2 += pc.z;
-    }
-    if (x > 0) {
-        d1 -= sp[ty][tx - 1].x;
-        d2 -= sp[ty][tx - 1].z;
-    }
-    if (y + 1 < f.h) {
-        d1 += pc.y;
-        d2 += pc.w;
-    }
-    if (y > 0) {
-        d1 -= sp[ty - 1][tx].y;
-        d2 -= sp[ty - 1][tx].w;
-    }
     const float2 u = f.u[i];
-    const float t1 = u.x + tau * d1, t2 = u.y + tau * d2;
-    const float2 g = f.gw[i];
-    const float g2 = g.x * g.x + g.y * g.y;
-    const float rho = f.r0[i] + g.x * t1 + g.y * t2;
-    const float th = tau * lambda * g2;
-    float v1 = t1, v2 = t2;
-    if (rho < -th) {
-        v1 = t1 + tau * lambda * g.x;
-        v2 = t2 + tau * lambda * g.y;
-    } else if (rho > th) {
-        v1 = t1 - tau * lambda * g.x;
-        v2 = t2 - tau * lambda * g.y;
-    } else if (g2 > 0.f) {
-        v1 = t1 - rho * g.x / g2;
-        v2 = t2 - rho * g.y / g2;
+    const float2 v = primal_step(pc, sp[ty][tx - 1], sp[ty - 1][tx], x, y, f.w, f.h, u, f.gw[i],
+                                 f.r0[i], tau, lambda);
+    f.u[i] = v;
+    f.ub_out[i] = extrapolate(v, u);
+}
+
+// Two primal-dual iterations for a TBX x TH tile (temporal blocking): the
+// first on the tile grown by the reach of the second, in shared memory, so a
+// launch reads the state once and writes it once for two iterations.
+// Regions relative to the tile origin: B [-2, TBX + 1] holds ub^n (and
+// later ub^n+1 on [-1, TBX]); Q [-2, TBX] holds p^n, then p^n+1, then p^n+2
+// on [-1, TBX - 1]; V [-1, TBX] holds u^n, then u^n+1, and the warped
+// gradient and rho0.  Each stage updates the inside positions of its region
+// from the previous stage's values there and at their neighbours, by the
+// same expressions as pd_kernel, so the result equals two pd_kernel launches
+// bit for bit.  Positions outside the level hold zeros and are never read
+// by a position inside it.  u is ping-ponged (u -> u_out), as are p and ub:
+// the halos read a neighbouring tile's old state.
+template <int TH>
+__global__ void __launch_bounds__(TBX * TBY) pd2_kernel(FlowLevel f, float sigma, float rden,
+                                                        float tau, float lambda) {
+    pdl_begin();
+    constexpr int BW = TBX + 4, BH = TH + 4, QW = TBX + 3, QH = TH + 3;
+    constexpr int VW = TBX + 2, VH = TH + 2, RW = TBX + 1, RH = TH + 1;
+    __shared__ float2 sb[BH][BW];
+    __shared__ float4 sq[QH][QW];
+    __shared__ float2 su[VH][VW];
+    __shared__ float2 sg[VH][VW];
+    __shared__ float sr[VH][VW];
+    const int bx = blockIdx.x * TBX, by = blockIdx.y * TH;
+    auto inside = [&](int x, int y) { return x >= 0 && x < f.w && y >= 0 && y < f.h; };
+    // the state on the grown regions, zero outside the level
+    sweep<QW, QH>([&](int rx, int ry) {
+        const int x = bx - 2 + rx, y = by - 2 + ry;
+        const bool in = inside(x, y);
+        cp_zfill<16>(&sq[ry][rx], in ? f.p + (int64_t)y * f.w + x : f.p, in);
+    });
+    sweep<BW, BH>([&](int rx, int ry) {
+        const int x = bx - 2 + rx, y = by - 2 + ry;
+        const bool in = inside(x, y);
+        cp_zfill<8>(&sb[ry][rx], in ? f.ub + (int64_t)y * f.w + x : f.ub, in);
+    });
+    sweep<VW, VH>([&](int rx, int ry) {
+        const int x = bx - 1 + rx, y = by - 1 + ry;
+        const bool in = inside(x, y);
+        const int64_t i = in ? (int64_t)y * f.w + x : 0;
+        cp_zfill<8>(&su[ry][rx], f.u + i, in);
+        cp_zfill<8>(&sg[ry][rx], f.gw + i, in);
+        cp_zfill<4>(&sr[ry][rx], f.r0 + i, in);
+    });
+    cp_wait_all();
+    __syncthreads();
+    // p^n+1 on Q; Q (rx, ry) is B (rx, ry)
+    sweep<QW, QH>([&](int rx, int ry) {
+        const int x = bx - 2 + rx, y = by - 2 + ry;
+        if (inside(x, y)) {
+            const float2 c = sb[ry][rx];
+            const float2 r = x + 1 < f.w ? sb[ry][rx + 1] : c;
+            const float2 d = y + 1 < f.h ? sb[ry + 1][rx] : c;
+            sq[ry][rx] = dual_step(sq[ry][rx], c, r, d, sigma, rden);
+        }
+    });
+    __syncthreads();
+    // u^n+1 and ub^n+1 on V; V (rx, ry) is Q (rx + 1, ry + 1) and B (rx + 1, ry + 1)
+    sweep<VW, VH>([&](int rx, int ry) {
+        const int x = bx - 1 + rx, y = by - 1 + ry;
+        if (inside(x, y)) {
+            const float2 u = su[ry][rx];
+            const float2 v = primal_step(sq[ry + 1][rx + 1], sq[ry + 1][rx], sq[ry][rx + 1], x, y,
+                                         f.w, f.h, u, sg[ry][rx], sr[ry][rx], tau, lambda);
+            su[ry][rx] = v;
+            sb[ry + 1][rx + 1] = extrapolate(v, u);
+        }
+    });
+    __syncthreads();
+    // p^n+2 on [-1, TBX - 1] x [-1, TH - 1]; (rx, ry) there is Q and B (rx + 1, ry + 1)
+    sweep<RW, RH>([&](int rx, int ry) {
+        const int x = bx - 1 + rx, y = by - 1 + ry;
+        if (inside(x, y)) {
+            const float2 c = sb[ry + 1][rx + 1];
+            const float2 r = x + 1 < f.w ? sb[ry + 1][rx + 2] : c;
+            const float2 d = y + 1 < f.h ? sb[ry + 2][rx + 1] : c;
+            sq[ry + 1][rx + 1] = dual_step(sq[ry + 1][rx + 1], c, r, d, sigma, rden);
+        }
+    });
+    __syncthreads();
+    // u^n+2 on the tile; a tile pixel is Q (tx + 2, ty + 2) and V (tx + 1, ty + 1)
+    for (int ty = threadIdx.y; ty < TH; ty += TBY) {
+        const int tx = threadIdx.x, x = bx + tx, y = by + ty;
+        if (x >= f.w || y >= f.h) continue;
+        const int64_t i = (int64_t)y * f.w + x;
+        const float4 pc = sq[ty + 2][tx + 2];
+        const float2 u = su[ty + 1][tx + 1];
+        const float2 v = primal_step(pc, sq[ty + 2][tx + 1], sq[ty + 1][tx + 2], x, y, f.w, f.h, u,
+                                     sg[ty + 1][tx + 1], sr[ty + 1][tx + 1], tau, lambda);
+        f.p_out[i] = pc;
+        f.u_out[i] = v;
+        f.ub_out[i] = extrapolate(v, u);
     }
-    f.u[i] = make_float2(v1, v2);
-    f.ub_out[i] = make_float2(2.0f * v1 - u.x, 2.0f * v2 - u.y);
 }
 
 // -------------------------------------------------------- mean in a box
@@ -424,6 +594,7 @@ __global__ void box_mean_kernel(const float2 *flow, int w, int h, const float4 *
 }
 
 dim3 grid2(int w, int h) { return dim3((w + TBX - 1) / TBX, (h + TBY - 1) / TBY); }
+dim3 grid_th(int w, int h, int th) { return dim3((w + TBX - 1) / TBX, (h + th - 1) / th); }
 
 LevelF level_f(const omt_pyramid &p, int L) {
     const LevelView v = level_view(p, L);
@@ -450,17 +621,23 @@ cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t 
     float *p0 = base, *p1 = base + 2 * n;
     cudaError_t e = cudaMemsetAsync(p0, 0, sizeof(float) * 2 * n, s);
     if (e != cudaSuccess) return e;
-    StArgs a{frame, (int64_t)pitch, w, h, fp.st_theta, 0.125f, p0, p1};
-    const dim3 g = grid2(w, h), b(TBX, TBY);
-    for (int it = 0; it < fp.st_iters; it += 2) {
-        if (it + 1 < fp.st_iters) st_step2_kernel<<<g, b, 0, s>>>(a);
-        else st_step_kernel<<<g, b, 0, s>>>(a);
+    StArgs a{frame, (int64_t)pitch, w, h, fp.st_theta, 1.0f / fp.st_theta, 0.125f, p0, p1};
+    const dim3 g = grid2(w, h), gs = grid_th(w, h, ST_TH), b(TBX, TBY);
+    for (int it = 0; it < fp.st_iters;) {
+        if (fp.block == 2 && it + 1 < fp.st_iters) {
+            e = launch_pdl(st_step2_kernel<ST_TH>, gs, b, s, a);
+            it += 2;
+        } else {
+            e = launch_pdl(st_step_kernel<ST_TH>, gs, b, s, a);
+            it += 1;
+        }
+        if (e != cudaSuccess) return e;
         const float *t = a.p;
         a.p = a.p_out;
         a.p_out = const_cast<float *>(t);
     }
-    st_texture_kernel<<<g, b, 0, s>>>(a, fp.st_alpha, fp.st_k, tex, (int64_t)tpitch);
-    return cudaGetLastError();
+    e = launch_pdl(st_texture_kernel, g, b, s, a, fp.st_alpha, fp.st_k, tex, (int64_t)tpitch);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 size_t tvl1_scratch_bytes(int w, int h) {
@@ -486,6 +663,11 @@ cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_
     f.gw = (float2 *)take(8 * n0);
     f.r0 = (float *)take(4 * n0);
     const float sigma = 1.0f / sqrtf(8.0f), tau = 1.0f / sqrtf(8.0f);
+    const float rden = 1.0f / (1.0f + sigma * fp.eps);
+    // launches per warp: pairs of iterations (pd2_kernel, u ping-ponged)
+    // and single ones (pd_kernel, u in place)
+    const int pairs = fp.block == 2 ? fp.iters / 2 : 0, singles = fp.iters - 2 * pairs;
+    const bool odd_flips = (fp.warps * pairs) % 2 == 1;
     const float2 *coarse = nullptr;
     int cw = 0, ch = 0;
     cudaError_t e = cudaSuccess;
@@ -493,25 +675,45 @@ cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_
         const LevelF I0 = level_f(P0, L), I1 = level_f(P1, L);
         f.w = I0.w;
         f.h = I0.h;
-        f.u = L == 0 ? flow : (coarse == ua ? ucoarse : ua);
-        const dim3 g = grid2(f.w, f.h), b(TBX, TBY);
-        upsample_kernel<<<g, b, 0, s>>>(coarse, cw, ch, f.u, f.w, f.h);
+        // the level's flow ends in dst; its ping-pong partner is a buffer
+        // that holds neither the level above nor dst (the output buffer is
+        // free until level 0).  The start buffer is chosen so that an odd
+        // number of u swaps ends in dst.
+        float2 *other_flow = coarse == ua ? ucoarse : ua;
+        float2 *dst = L == 0 ? flow : other_flow;
+        float2 *partner = L == 0 ? other_flow : flow;
+        float2 *ucur = odd_flips ? partner : dst, *unext = odd_flips ? dst : partner;
+        const dim3 g = grid2(f.w, f.h), gp = grid_th(f.w, f.h, PD_TH), b(TBX, TBY);
+        e = launch_pdl(upsample_kernel, g, b, s, coarse, cw, ch, ucur, f.w, f.h);
+        if (e != cudaSuccess) return e;
         int cur = 0;  // the p / ub buffers holding the current fields
         e = cudaMemsetAsync(pbuf[cur], 0, sizeof(float4) * (size_t)f.w * f.h, s);
         if (e != cudaSuccess) return e;
         for (int wp = 0; wp < fp.warps; ++wp) {
+            f.u = ucur;
             f.ub = ubuf[cur];
-            warp_kernel<<<g, b, 0, s>>>(f, I0, I1);
-            for (int it = 0; it < fp.iters; ++it) {
+            e = launch_pdl(warp_kernel, g, b, s, f, I0, I1);
+            if (e != cudaSuccess) return e;
+            for (int it = 0; it < pairs + singles; ++it) {
                 f.p = pbuf[cur];
                 f.ub = ubuf[cur];
                 f.p_out = pbuf[1 - cur];
                 f.ub_out = ubuf[1 - cur];
-                pd_kernel<<<g, b, 0, s>>>(f, sigma, fp.eps, tau, fp.lambda);
+                f.u = ucur;
+                if (it < pairs) {
+                    f.u_out = unext;
+                    e = launch_pdl(pd2_kernel<PD_TH>, gp, b, s, f, sigma, rden, tau, fp.lambda);
+                    float2 *t = ucur;
+                    ucur = unext;
+                    unext = t;
+                } else {
+                    e = launch_pdl(pd_kernel, g, b, s, f, sigma, rden, tau, fp.lambda);
+                }
+                if (e != cudaSuccess) return e;
                 cur = 1 - cur;
             }
         }
-        coarse = f.u;
+        coarse = ucur;
         cw = f.w;
         ch = f.h;
     }

@@ -82,7 +82,7 @@ class BatchStream(Structure):
 class FlowParams(Structure):
     _fields_ = [("st_theta", c_float), ("st_alpha", c_float), ("st_k", c_float),
                 ("st_iters", c_int32), ("lambda_", c_float), ("eps", c_float), ("warps", c_int32),
-                ("iters", c_int32)]
+                ("iters", c_int32), ("block", c_int32)]
 
 
 class BatchCaps(Structure):

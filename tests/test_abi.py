@@ -259,9 +259,11 @@ def test_flow_engine_arguments_rejected_before_launch():
                                      None) == omt.EINVAL
     assert lib.omt_structure_texture(fake, 64, 48, 64, ctypes.byref(fp), fake, 64, fake, n - 1,
                                      None) == omt.ENOMEM
-    bad = omt.default_flow_params(iters=0)
-    assert lib.omt_structure_texture(fake, 64, 48, 64, ctypes.byref(bad), fake, 64, fake, n,
-                                     None) == omt.EINVAL
+    assert fp.block == 2
+    for bad in (omt.default_flow_params(iters=0), omt.default_flow_params(block=0),
+                omt.default_flow_params(block=3)):
+        assert lib.omt_structure_texture(fake, 64, 48, 64, ctypes.byref(bad), fake, 64, fake, n,
+                                         None) == omt.EINVAL
     # the flow needs F32 pyramids of one shape
     d0, d1, d16 = omt.PyramidDesc(), omt.PyramidDesc(), omt.PyramidDesc()
     m = omt.pyramid_bytes(64, 48, 3, 0)
@@ -276,6 +278,9 @@ def test_flow_engine_arguments_rejected_before_launch():
                              None) == omt.EINVAL
     assert lib.omt_tvl1_flow(ctypes.byref(d0), ctypes.byref(d1), ctypes.byref(fp), fake, fake, t - 1,
                              None) == omt.ENOMEM
+    bad = omt.default_flow_params(block=3)
+    assert lib.omt_tvl1_flow(ctypes.byref(d0), ctypes.byref(d1), ctypes.byref(bad), fake, fake, t,
+                             None) == omt.EINVAL
     # box means: in place and misaligned boxes are rejected; zero boxes is a no-op
     assert lib.omt_box_mean_flow(fake, 64, 48, fake, 3, fake, None) == omt.EINVAL
     assert lib.omt_box_mean_flow(fake, 64, 48, ctypes.c_void_p((1 << 24) + 8), 3,

@@ -90,6 +90,43 @@ def test_tvl1_matches_oracle(omt, oracle, size, shift, levels):
         assert np.allclose(np.median(inner, 0), shift, atol=0.05)
 
 
+@pytest.mark.parametrize("size,st_iters", [((37, 23), 7), ((333, 250), 100), ((1, 1), 3)])
+def test_structure_texture_two_steps_per_launch_same_bits(omt, size, st_iters):
+    # one projection step per launch and two per launch (the last one alone
+    # when the count is odd) give the same texture bit for bit
+    w, h = size
+    f0, _ = _scene(w, h, (0, 0), seed=w * 3)
+    outs = []
+    for block in (1, 2):
+        fp = omt.default_flow_params(st_iters=st_iters, block=block)
+        out = torch.zeros((h, w), dtype=torch.uint8, device="cuda")
+        omt.structure_texture(_t(f0, np.uint8), fp, out)
+        outs.append(out.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("size,shift,levels,warps,iters", [((333, 250), (3.3, -1.7), 3, 3, 5),
+                                                           ((97, 61), (1.25, 0.5), 1, 1, 30),
+                                                           ((160, 120), (0.6, 2.2), 2, 2, 1),
+                                                           ((65, 33), (-1.0, 1.0), 2, 3, 4)])
+def test_tvl1_two_iterations_per_launch_same_bits(omt, oracle, size, shift, levels, warps, iters):
+    # pairs of iterations per launch (with the flow ping-ponged, an odd count
+    # of swaps per level, a single iteration left over) equal one iteration
+    # per launch bit for bit, on ragged tiles
+    w, h = size
+    f0, f1 = _scene(w, h, shift, seed=w + 2 * h)
+    T0, T1 = oracle.structure_texture(f0), oracle.structure_texture(f1)
+    P0, P1 = _pyr(omt, T0, levels), _pyr(omt, T1, levels)
+    flows = []
+    for block in (1, 2):
+        fp = omt.default_flow_params(warps=warps, iters=iters, block=block)
+        flow = torch.full((h, w, 2), float("nan"), device="cuda")
+        omt.tvl1_flow(P0, P1, fp, flow)
+        flows.append(flow.cpu().numpy())
+    assert np.all(np.isfinite(flows[1]))
+    np.testing.assert_array_equal(flows[0], flows[1])
+
+
 def test_tvl1_identical_frames_zero(omt, oracle):
     f0, _ = _scene(96, 80, (0, 0), seed=9)
     T = oracle.structure_texture(f0)
