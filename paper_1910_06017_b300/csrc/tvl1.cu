@@ -62,14 +62,18 @@ __device__ __forceinline__ void cp_zfill(void *smem, const void *gmem, bool vali
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Calls fn(rx, ry) for every position of an RW x RH region, RW in
-// (TBX, 2 TBX]: the TBX x TBY threads sweep it by rows, a thread taking
-// column tx and, for the last RW - TBX columns, tx + TBX.
+// (TBX, 2 TBX]: the TBX x TBY threads sweep its first TBX columns by rows
+// (a warp per row), then the last RW - TBX columns of all rows together,
+// numbered row-major across the CTA, so that no warp issues a pass for a
+// few lanes per row.
 template <int RW, int RH, class F>
 __device__ __forceinline__ void sweep(F &&fn) {
     static_assert(RW > TBX && RW <= 2 * TBX, "region width");
-    for (int ry = threadIdx.y; ry < RH; ry += TBY) {
-        fn((int)threadIdx.x, ry);
-        if (threadIdx.x < RW - TBX) fn((int)threadIdx.x + TBX, ry);
+    constexpr int XW = RW - TBX;
+    for (int ry = threadIdx.y; ry < RH; ry += TBY) fn((int)threadIdx.x, ry);
+    for (int e = threadIdx.y * TBX + threadIdx.x; e < XW * RH; e += TBX * TBY) {
+        const int ry = e / XW;
+        fn(TBX + e - ry * XW, ry);
     }
 }
 
