@@ -17,6 +17,8 @@
 // order of the definition, in FP32, and both launch forms give the same bits.
 // A launch reads and writes every field once: the kernels are bound by HBM
 // (or L2 for small levels).
+#include <type_traits>
+
 #include "omt_internal.cuh"
 
 namespace omt {
@@ -118,15 +120,16 @@ __device__ __forceinline__ float2 st_dual(float2 pc, float gx, float gy, float s
     return make_float2((pc.x + step * gx) * rm, (pc.y + step * gy) * rm);
 }
 
-// div p - I / theta at an inside position (x, y) from the duals there (c)
-// and at the left (l) and upper (u) neighbours.
-__device__ __forceinline__ float st_q(float2 c, float2 l, float2 u, int x, int y, int w, int h,
-                                      float img, float rtheta) {
+// div p - I / theta at an inside position from the duals there (c) and at
+// the left (l) and upper (u) neighbours (xr, xl, yd, yu: a right, left,
+// lower, upper neighbour inside the frame).
+__device__ __forceinline__ float st_q(float2 c, float2 l, float2 u, bool xr, bool xl, bool yd,
+                                      bool yu, float img, float rtheta) {
     float d = 0.f;
-    if (x + 1 < w) d += c.x;
-    if (x > 0) d -= l.x;
-    if (y + 1 < h) d += c.y;
-    if (y > 0) d -= u.y;
+    if (xr) d += c.x;
+    if (xl) d -= l.x;
+    if (yd) d += c.y;
+    if (yu) d -= u.y;
     return d - img * rtheta;
 }
 
@@ -153,8 +156,9 @@ __global__ void __launch_bounds__(TBX * TBY) st_step_kernel(StArgs a) {
     sweep<QW, QH>([&](int rx, int ry) {
         const int x = bx + rx, y = by + ry;
         if (inside(x, y))
-            sq[ry][rx] = st_q(spp[ry + 1][rx + 1], spp[ry + 1][rx], spp[ry][rx + 1], x, y, a.w, a.h,
-                              (float)a.img[(int64_t)y * a.pitch + x], a.rtheta);
+            sq[ry][rx] = st_q(spp[ry + 1][rx + 1], spp[ry + 1][rx], spp[ry][rx + 1], x + 1 < a.w,
+                              x > 0, y + 1 < a.h, y > 0, (float)a.img[(int64_t)y * a.pitch + x],
+                              a.rtheta);
     });
     __syncthreads();
     for (int ty = threadIdx.y; ty < TH; ty += TBY) {
@@ -187,55 +191,71 @@ __global__ void __launch_bounds__(TBX * TBY) st_step2_kernel(StArgs a) {
     __shared__ float2 sp[PH][PW];
     __shared__ float sq[QH][QW];
     __shared__ float si[QH][QW];
+    const int w = a.w, h = a.h;
+    const float *p_in = a.p;
+    const uint8_t *img = a.img;
+    const int64_t pitch = a.pitch;
+    const float rtheta = a.rtheta, step = a.step;
     const int bx = blockIdx.x * TBX, by = blockIdx.y * TH;
-    auto inside = [&](int x, int y) { return x >= 0 && x < a.w && y >= 0 && y < a.h; };
-    sweep<PW, PH>([&](int rx, int ry) {
-        const int x = bx - 2 + rx, y = by - 2 + ry;
-        const bool in = inside(x, y);
-        cp_zfill<8>(&sp[ry][rx], in ? a.p + 2 * ((int64_t)y * a.w + x) : a.p, in);
-    });
-    sweep<QW, QH>([&](int rx, int ry) {
-        const int x = bx - 1 + rx, y = by - 1 + ry;
-        if (inside(x, y)) si[ry][rx] = (float)a.img[(int64_t)y * a.pitch + x];
-    });
-    cp_wait_all();
-    __syncthreads();
-    // q^n on Q; Q (rx, ry) is P (rx + 1, ry + 1)
-    sweep<QW, QH>([&](int rx, int ry) {
-        const int x = bx - 1 + rx, y = by - 1 + ry;
-        if (inside(x, y))
-            sq[ry][rx] = st_q(sp[ry + 1][rx + 1], sp[ry + 1][rx], sp[ry][rx + 1], x, y, a.w, a.h,
-                              si[ry][rx], a.rtheta);
-    });
-    __syncthreads();
-    // p^n+1 on [-1, TBX] x [-1, TH]: Q (rx, ry), P (rx + 1, ry + 1)
-    sweep<P1W, P1H>([&](int rx, int ry) {
-        const int x = bx - 1 + rx, y = by - 1 + ry;
-        if (inside(x, y)) {
-            const float qc = sq[ry][rx];
-            const float gx = x + 1 < a.w ? sq[ry][rx + 1] - qc : 0.f;
-            const float gy = y + 1 < a.h ? sq[ry + 1][rx] - qc : 0.f;
-            sp[ry + 1][rx + 1] = st_dual(sp[ry + 1][rx + 1], gx, gy, a.step);
+    // IN: every position of the regions and its right / lower neighbour lie
+    // inside the frame, so no position needs an edge test
+    auto body = [&](auto in_c) {
+        constexpr bool IN = decltype(in_c)::value;
+        auto inside = [&](int x, int y) { return IN || (x >= 0 && x < w && y >= 0 && y < h); };
+        sweep<PW, PH>([&](int rx, int ry) {
+            const int x = bx - 2 + rx, y = by - 2 + ry;
+            const bool in = inside(x, y);
+            cp_zfill<8>(&sp[ry][rx], in ? p_in + 2 * ((int64_t)y * w + x) : p_in, in);
+        });
+        sweep<QW, QH>([&](int rx, int ry) {
+            const int x = bx - 1 + rx, y = by - 1 + ry;
+            if (inside(x, y)) si[ry][rx] = (float)img[(int64_t)y * pitch + x];
+        });
+        cp_wait_all();
+        __syncthreads();
+        // q^n on Q; Q (rx, ry) is P (rx + 1, ry + 1)
+        sweep<QW, QH>([&](int rx, int ry) {
+            const int x = bx - 1 + rx, y = by - 1 + ry;
+            if (inside(x, y))
+                sq[ry][rx] = st_q(sp[ry + 1][rx + 1], sp[ry + 1][rx], sp[ry][rx + 1],
+                                  IN || x + 1 < w, IN || x > 0, IN || y + 1 < h, IN || y > 0,
+                                  si[ry][rx], rtheta);
+        });
+        __syncthreads();
+        // p^n+1 on [-1, TBX] x [-1, TH]: Q (rx, ry), P (rx + 1, ry + 1)
+        sweep<P1W, P1H>([&](int rx, int ry) {
+            const int x = bx - 1 + rx, y = by - 1 + ry;
+            if (inside(x, y)) {
+                const float qc = sq[ry][rx];
+                const float gx = IN || x + 1 < w ? sq[ry][rx + 1] - qc : 0.f;
+                const float gy = IN || y + 1 < h ? sq[ry + 1][rx] - qc : 0.f;
+                sp[ry + 1][rx + 1] = st_dual(sp[ry + 1][rx + 1], gx, gy, step);
+            }
+        });
+        __syncthreads();
+        // q^n+1 on [0, TBX] x [0, TH]: Q (rx + 1, ry + 1), P (rx + 2, ry + 2)
+        sweep<Q1W, Q1H>([&](int rx, int ry) {
+            const int x = bx + rx, y = by + ry;
+            if (inside(x, y))
+                sq[ry + 1][rx + 1] = st_q(sp[ry + 2][rx + 2], sp[ry + 2][rx + 1], sp[ry + 1][rx + 2],
+                                          IN || x + 1 < w, IN || x > 0, IN || y + 1 < h,
+                                          IN || y > 0, si[ry + 1][rx + 1], rtheta);
+        });
+        __syncthreads();
+        for (int ty = threadIdx.y; ty < TH; ty += TBY) {
+            const int tx = threadIdx.x, x = bx + tx, y = by + ty;
+            if (!IN && (x >= w || y >= h)) continue;
+            const float qc = sq[ty + 1][tx + 1];
+            const float gx = IN || x + 1 < w ? sq[ty + 1][tx + 2] - qc : 0.f;
+            const float gy = IN || y + 1 < h ? sq[ty + 2][tx + 1] - qc : 0.f;
+            const float2 pn = st_dual(sp[ty + 2][tx + 2], gx, gy, step);
+            reinterpret_cast<float2 *>(a.p_out)[(int64_t)y * w + x] = pn;
         }
-    });
-    __syncthreads();
-    // q^n+1 on [0, TBX] x [0, TH]: Q (rx + 1, ry + 1), P (rx + 2, ry + 2)
-    sweep<Q1W, Q1H>([&](int rx, int ry) {
-        const int x = bx + rx, y = by + ry;
-        if (inside(x, y))
-            sq[ry + 1][rx + 1] = st_q(sp[ry + 2][rx + 2], sp[ry + 2][rx + 1], sp[ry + 1][rx + 2], x,
-                                      y, a.w, a.h, si[ry + 1][rx + 1], a.rtheta);
-    });
-    __syncthreads();
-    for (int ty = threadIdx.y; ty < TH; ty += TBY) {
-        const int tx = threadIdx.x, x = bx + tx, y = by + ty;
-        if (x >= a.w || y >= a.h) continue;
-        const float qc = sq[ty + 1][tx + 1];
-        const float gx = x + 1 < a.w ? sq[ty + 1][tx + 2] - qc : 0.f;
-        const float gy = y + 1 < a.h ? sq[ty + 2][tx + 1] - qc : 0.f;
-        const float2 pn = st_dual(sp[ty + 2][tx + 2], gx, gy, a.step);
-        reinterpret_cast<float2 *>(a.p_out)[(int64_t)y * a.w + x] = pn;
-    }
+    };
+    if (blockIdx.x > 0 && blockIdx.y > 0 && bx + TBX + 3 <= w && by + TH + 3 <= h)
+        body(std::true_type{});
+    else
+        body(std::false_type{});
 }
 
 __global__ void st_texture_kernel(StArgs a, float alpha, float k, uint8_t *tex, int64_t tpitch) {
@@ -342,12 +362,8 @@ constexpr int UW = TBX + 2, UH = TBY + 2;   // extrapolated-flow region
 
 __device__ __forceinline__ float2 project_unit(float qx, float qy) {
     const float m2 = qx * qx + qy * qy;
-    if (m2 > 1.0f) {
-        const float r = rsqrtf(m2);
-        qx *= r;
-        qy *= r;
-    }
-    return make_float2(qx, qy);
+    const float r = m2 > 1.0f ? rsqrtf(m2) : 1.0f;   // x 1 leaves the value as it is
+    return make_float2(qx * r, qy * r);
 }
 
 // The dual update of both flow components at a position from the
@@ -362,47 +378,39 @@ __device__ __forceinline__ float4 dual_step(float4 p, float2 c, float2 r, float2
     return make_float4(q1.x, q1.y, q2.x, q2.y);
 }
 
-// The primal update at (x, y) from the new duals there (pc) and at the left
-// (pl) and upper (pu) neighbours: the backward-difference divergence of each
-// dual field in the order the definition writes it, then the pointwise prox
-// of tau lambda |rho| at u + tau div p.
-__device__ __forceinline__ float2 primal_step(float4 pc, float4 pl, float4 pu, int x, int y, int w,
-                                              int h, float2 u, float2 g, float r0, float tau,
-                                              float lambda) {
+// The primal update at a position from the new duals there (pc) and at the
+// left (pl) and upper (pu) neighbours: the backward-difference divergence of
+// each dual field in the order the definition writes it (xr, xl, yd, yu: a
+// right, left, lower, upper neighbour inside the level), then the pointwise
+// prox of tau lambda |rho| at t = u + tau div p, written t - s g with
+// s = -tau lambda, tau lambda or rho / |g|^2 (g = 0 leaves t).  tl = tau lambda.
+__device__ __forceinline__ float2 primal_step(float4 pc, float4 pl, float4 pu, bool xr, bool xl,
+                                              bool yd, bool yu, float2 u, float2 g, float r0,
+                                              float tau, float tl) {
     float d1 = 0.f, d2 = 0.f;
-    if (x + 1 < w) {
+    if (xr) {
         d1 += pc.x;
         d2 += pc.z;
     }
-    if (x > 0) {
+    if (xl) {
         d1 -= pl.x;
         d2 -= pl.z;
     }
-    if (y + 1 < h) {
+    if (yd) {
         d1 += pc.y;
         d2 += pc.w;
     }
-    if (y > 0) {
+    if (yu) {
         d1 -= pu.y;
         d2 -= pu.w;
     }
     const float t1 = u.x + tau * d1, t2 = u.y + tau * d2;
     const float g2 = g.x * g.x + g.y * g.y;
     const float rho = r0 + g.x * t1 + g.y * t2;
-    const float th = tau * lambda * g2;
-    float v1 = t1, v2 = t2;
-    if (rho < -th) {
-        v1 = t1 + tau * lambda * g.x;
-        v2 = t2 + tau * lambda * g.y;
-    } else if (rho > th) {
-        v1 = t1 - tau * lambda * g.x;
-        v2 = t2 - tau * lambda * g.y;
-    } else if (g2 > 0.f) {
-        const float sr = rho / g2;
-        v1 = t1 - sr * g.x;
-        v2 = t2 - sr * g.y;
-    }
-    return make_float2(v1, v2);
+    const float th = tl * g2;
+    const float q = rho / g2;
+    const float sc = rho < -th ? -tl : (rho > th ? tl : (g2 > 0.f ? q : 0.f));
+    return make_float2(t1 - sc * g.x, t2 - sc * g.y);
 }
 
 // The extrapolation ubar = 2 u - u_previous.
@@ -444,8 +452,8 @@ __global__ void __launch_bounds__(TBX * TBY) pd_kernel(FlowLevel f, float sigma,
     const float4 pc = sp[ty][tx];
     f.p_out[i] = pc;
     const float2 u = f.u[i];
-    const float2 v = primal_step(pc, sp[ty][tx - 1], sp[ty - 1][tx], x, y, f.w, f.h, u, f.gw[i],
-                                 f.r0[i], tau, lambda);
+    const float2 v = primal_step(pc, sp[ty][tx - 1], sp[ty - 1][tx], x + 1 < f.w, x > 0, y + 1 < f.h,
+                                 y > 0, u, f.gw[i], f.r0[i], tau, tau * lambda);
     f.u[i] = v;
     f.ub_out[i] = extrapolate(v, u);
 }
@@ -473,76 +481,92 @@ __global__ void __launch_bounds__(TBX * TBY) pd2_kernel(FlowLevel f, float sigma
     __shared__ float2 su[VH][VW];
     __shared__ float2 sg[VH][VW];
     __shared__ float sr[VH][VW];
+    const int w = f.w, h = f.h;
+    const float2 *ub = f.ub, *u_in = f.u, *gw = f.gw;
+    const float4 *p_in = f.p;
+    const float *r0 = f.r0;
+    const float tl = tau * lambda;
     const int bx = blockIdx.x * TBX, by = blockIdx.y * TH;
-    auto inside = [&](int x, int y) { return x >= 0 && x < f.w && y >= 0 && y < f.h; };
-    // the state on the grown regions, zero outside the level
-    sweep<QW, QH>([&](int rx, int ry) {
-        const int x = bx - 2 + rx, y = by - 2 + ry;
-        const bool in = inside(x, y);
-        cp_zfill<16>(&sq[ry][rx], in ? f.p + (int64_t)y * f.w + x : f.p, in);
-    });
-    sweep<BW, BH>([&](int rx, int ry) {
-        const int x = bx - 2 + rx, y = by - 2 + ry;
-        const bool in = inside(x, y);
-        cp_zfill<8>(&sb[ry][rx], in ? f.ub + (int64_t)y * f.w + x : f.ub, in);
-    });
-    sweep<VW, VH>([&](int rx, int ry) {
-        const int x = bx - 1 + rx, y = by - 1 + ry;
-        const bool in = inside(x, y);
-        const int64_t i = in ? (int64_t)y * f.w + x : 0;
-        cp_zfill<8>(&su[ry][rx], f.u + i, in);
-        cp_zfill<8>(&sg[ry][rx], f.gw + i, in);
-        cp_zfill<4>(&sr[ry][rx], f.r0 + i, in);
-    });
-    cp_wait_all();
-    __syncthreads();
-    // p^n+1 on Q; Q (rx, ry) is B (rx, ry)
-    sweep<QW, QH>([&](int rx, int ry) {
-        const int x = bx - 2 + rx, y = by - 2 + ry;
-        if (inside(x, y)) {
-            const float2 c = sb[ry][rx];
-            const float2 r = x + 1 < f.w ? sb[ry][rx + 1] : c;
-            const float2 d = y + 1 < f.h ? sb[ry + 1][rx] : c;
-            sq[ry][rx] = dual_step(sq[ry][rx], c, r, d, sigma, rden);
+    // IN: the tile and its whole halo (and their right / lower neighbours)
+    // lie inside the level, so no position needs an edge test
+    auto body = [&](auto in_c) {
+        constexpr bool IN = decltype(in_c)::value;
+        auto inside = [&](int x, int y) { return IN || (x >= 0 && x < w && y >= 0 && y < h); };
+        // the state on the grown regions, zero outside the level
+        sweep<QW, QH>([&](int rx, int ry) {
+            const int x = bx - 2 + rx, y = by - 2 + ry;
+            const bool in = inside(x, y);
+            cp_zfill<16>(&sq[ry][rx], in ? p_in + (int64_t)y * w + x : p_in, in);
+        });
+        sweep<BW, BH>([&](int rx, int ry) {
+            const int x = bx - 2 + rx, y = by - 2 + ry;
+            const bool in = inside(x, y);
+            cp_zfill<8>(&sb[ry][rx], in ? ub + (int64_t)y * w + x : ub, in);
+        });
+        sweep<VW, VH>([&](int rx, int ry) {
+            const int x = bx - 1 + rx, y = by - 1 + ry;
+            const bool in = inside(x, y);
+            const int64_t i = in ? (int64_t)y * w + x : 0;
+            cp_zfill<8>(&su[ry][rx], u_in + i, in);
+            cp_zfill<8>(&sg[ry][rx], gw + i, in);
+            cp_zfill<4>(&sr[ry][rx], r0 + i, in);
+        });
+        cp_wait_all();
+        __syncthreads();
+        // p^n+1 on Q; Q (rx, ry) is B (rx, ry)
+        sweep<QW, QH>([&](int rx, int ry) {
+            const int x = bx - 2 + rx, y = by - 2 + ry;
+            if (inside(x, y)) {
+                const float2 c = sb[ry][rx];
+                const float2 r = IN || x + 1 < w ? sb[ry][rx + 1] : c;
+                const float2 d = IN || y + 1 < h ? sb[ry + 1][rx] : c;
+                sq[ry][rx] = dual_step(sq[ry][rx], c, r, d, sigma, rden);
+            }
+        });
+        __syncthreads();
+        // u^n+1 and ub^n+1 on V; V (rx, ry) is Q (rx + 1, ry + 1) and B (rx + 1, ry + 1)
+        sweep<VW, VH>([&](int rx, int ry) {
+            const int x = bx - 1 + rx, y = by - 1 + ry;
+            if (inside(x, y)) {
+                const float2 u = su[ry][rx];
+                const float2 v = primal_step(sq[ry + 1][rx + 1], sq[ry + 1][rx], sq[ry][rx + 1],
+                                             IN || x + 1 < w, IN || x > 0, IN || y + 1 < h,
+                                             IN || y > 0, u, sg[ry][rx], sr[ry][rx], tau, tl);
+                su[ry][rx] = v;
+                sb[ry + 1][rx + 1] = extrapolate(v, u);
+            }
+        });
+        __syncthreads();
+        // p^n+2 on [-1, TBX - 1] x [-1, TH - 1]; (rx, ry) there is Q and B (rx + 1, ry + 1)
+        sweep<RW, RH>([&](int rx, int ry) {
+            const int x = bx - 1 + rx, y = by - 1 + ry;
+            if (inside(x, y)) {
+                const float2 c = sb[ry + 1][rx + 1];
+                const float2 r = IN || x + 1 < w ? sb[ry + 1][rx + 2] : c;
+                const float2 d = IN || y + 1 < h ? sb[ry + 2][rx + 1] : c;
+                sq[ry + 1][rx + 1] = dual_step(sq[ry + 1][rx + 1], c, r, d, sigma, rden);
+            }
+        });
+        __syncthreads();
+        // u^n+2 on the tile; a tile pixel is Q (tx + 2, ty + 2) and V (tx + 1, ty + 1)
+        for (int ty = threadIdx.y; ty < TH; ty += TBY) {
+            const int tx = threadIdx.x, x = bx + tx, y = by + ty;
+            if (!IN && (x >= w || y >= h)) continue;
+            const int64_t i = (int64_t)y * w + x;
+            const float4 pc = sq[ty + 2][tx + 2];
+            const float2 u = su[ty + 1][tx + 1];
+            const float2 v = primal_step(pc, sq[ty + 2][tx + 1], sq[ty + 1][tx + 2], IN || x + 1 < w,
+                                         IN || x > 0, IN || y + 1 < h, IN || y > 0, u,
+                                         sg[ty + 1][tx + 1], sr[ty + 1][tx + 1], tau, tl);
+            f.p_out[i] = pc;
+            f.u_out[i] = v;
+            f.ub_out[i] = extrapolate(v, u);
         }
-    });
-    __syncthreads();
-    // u^n+1 and ub^n+1 on V; V (rx, ry) is Q (rx + 1, ry + 1) and B (rx + 1, ry + 1)
-    sweep<VW, VH>([&](int rx, int ry) {
-        const int x = bx - 1 + rx, y = by - 1 + ry;
-        if (inside(x, y)) {
-            const float2 u = su[ry][rx];
-            const float2 v = primal_step(sq[ry + 1][rx + 1], sq[ry + 1][rx], sq[ry][rx + 1], x, y,
-                                         f.w, f.h, u, sg[ry][rx], sr[ry][rx], tau, lambda);
-            su[ry][rx] = v;
-            sb[ry + 1][rx + 1] = extrapolate(v, u);
-        }
-    });
-    __syncthreads();
-    // p^n+2 on [-1, TBX - 1] x [-1, TH - 1]; (rx, ry) there is Q and B (rx + 1, ry + 1)
-    sweep<RW, RH>([&](int rx, int ry) {
-        const int x = bx - 1 + rx, y = by - 1 + ry;
-        if (inside(x, y)) {
-            const float2 c = sb[ry + 1][rx + 1];
-            const float2 r = x + 1 < f.w ? sb[ry + 1][rx + 2] : c;
-            const float2 d = y + 1 < f.h ? sb[ry + 2][rx + 1] : c;
-            sq[ry + 1][rx + 1] = dual_step(sq[ry + 1][rx + 1], c, r, d, sigma, rden);
-        }
-    });
-    __syncthreads();
-    // u^n+2 on the tile; a tile pixel is Q (tx + 2, ty + 2) and V (tx + 1, ty + 1)
-    for (int ty = threadIdx.y; ty < TH; ty += TBY) {
-        const int tx = threadIdx.x, x = bx + tx, y = by + ty;
-        if (x >= f.w || y >= f.h) continue;
-        const int64_t i = (int64_t)y * f.w + x;
-        const float4 pc = sq[ty + 2][tx + 2];
-        const float2 u = su[ty + 1][tx + 1];
-        const float2 v = primal_step(pc, sq[ty + 2][tx + 1], sq[ty + 1][tx + 2], x, y, f.w, f.h, u,
-                                     sg[ty + 1][tx + 1], sr[ty + 1][tx + 1], tau, lambda);
-        f.p_out[i] = pc;
-        f.u_out[i] = v;
-        f.ub_out[i] = extrapolate(v, u);
-    }
+    };
+    if (blockIdx.x > 0 && blockIdx.y > 0 && bx + TBX + 2 <= w && by + TH + 2 <= h)
+        body(std::true_type{});
+    else
+        body(std::false_type{});
 }
 
 // -------------------------------------------------------- mean in a box
