@@ -108,7 +108,8 @@ def test_structure_texture_two_steps_per_launch_same_bits(omt, size, st_iters):
 @pytest.mark.parametrize("size,shift,levels,warps,iters", [((333, 250), (3.3, -1.7), 3, 3, 5),
                                                            ((97, 61), (1.25, 0.5), 1, 1, 30),
                                                            ((160, 120), (0.6, 2.2), 2, 2, 1),
-                                                           ((65, 33), (-1.0, 1.0), 2, 3, 4)])
+                                                           ((65, 33), (-1.0, 1.0), 2, 3, 4),
+                                                           ((200, 150), (1.5, -2.0), 3, 3, 2)])
 def test_tvl1_two_iterations_per_launch_same_bits(omt, oracle, size, shift, levels, warps, iters):
     # pairs of iterations per launch (with the flow ping-ponged, an odd count
     # of swaps per level, a single iteration left over) equal one iteration
