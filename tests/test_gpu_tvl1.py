@@ -171,3 +171,57 @@ def test_end_to_end_translation(omt, oracle):
     torch.cuda.synchronize()
     moved = out.cpu().numpy() - boxes.cpu().numpy()
     np.testing.assert_allclose(moved[:, :2], [[2.25, -1.5]] * 2, atol=0.05)
+
+
+def test_flow_step_captured_in_a_cuda_graph(omt):
+    # the whole flow step (texture, pyramid, flow, box means; kernels chained
+    # by programmatic dependent launch) captured once and replayed equals
+    # the eager calls bit for bit, and a replay reads the frame it is given
+    w, h = 160, 120
+    f0, f1 = _scene(w, h, (1.75, -0.5), seed=44)
+    fp = omt.default_flow_params()
+    prm = omt.default_params(levels=3)
+    frames = [_t(f, np.uint8) for f in (f0, f1)]
+    tex = [torch.zeros((h, w), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    pyr = [omt.Pyramid(w, h, 3, 0) for _ in range(2)]
+    st_scr = torch.empty(omt.lib().omt_structure_texture_scratch_bytes(w, h), dtype=torch.uint8,
+                         device="cuda")
+    tv_scr = torch.empty(omt.lib().omt_tvl1_scratch_bytes(w, h), dtype=torch.uint8, device="cuda")
+    flow = torch.zeros((h, w, 2), device="cuda")
+    boxes = _t(np.array([[20, 10, 120, 90], [50, 40, 70, 60]], np.float32))
+    out = torch.zeros((2, 4), device="cuda")
+    src = torch.zeros((h, w), dtype=torch.uint8, device="cuda")
+
+    def prime(k):
+        omt.structure_texture(frames[k], fp, tex[k], st_scr)
+        omt.build_pyramid(tex[k], pyr[k], prm)
+
+    def step():
+        # src holds frame 1 of the pair; its texture and pyramid, then the flow
+        omt.structure_texture(src, fp, tex[1], st_scr)
+        omt.build_pyramid(tex[1], pyr[1], prm)
+        omt.tvl1_flow(pyr[0], pyr[1], fp, flow, tv_scr)
+        omt.box_mean_flow(flow, boxes, out)
+
+    prime(0)
+    src.copy_(frames[1])
+    step()
+    torch.cuda.synchronize()
+    want_flow, want_out = flow.clone(), out.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            step()
+    torch.cuda.synchronize()
+    flow.zero_()
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(flow, want_flow) and torch.equal(out, want_out)
+    # the replay reads the new frame: frame 0 again gives exactly zero flow
+    src.copy_(frames[0])
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.all(flow == 0) and torch.equal(out, boxes)
