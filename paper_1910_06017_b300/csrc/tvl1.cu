@@ -116,7 +116,7 @@ struct StArgs {
 // Chambolle's projection update of the dual at a position from the forward
 // differences (gx, gy) of q = div p - I / theta there.
 __device__ __forceinline__ float2 st_dual(float2 pc, float gx, float gy, float step) {
-    const float rm = 1.0f / (1.f + step * sqrtf(gx * gx + gy * gy));
+    const float rm = 1.0f / (1.f + step * sqrtf(__fmaf_rn(gx, gx, __fmul_rn(gy, gy))));
     return make_float2((pc.x + step * gx) * rm, (pc.y + step * gy) * rm);
 }
 
@@ -361,7 +361,9 @@ constexpr int PW = TBX + 1, PH = TBY + 1;   // dual region
 constexpr int UW = TBX + 2, UH = TBY + 2;   // extrapolated-flow region
 
 __device__ __forceinline__ float2 project_unit(float qx, float qy) {
-    const float m2 = qx * qx + qy * qy;
+    // sums of two products are rounded in a fixed way (the second product
+    // rounded, the first fused), so every kernel forms the same bits
+    const float m2 = __fmaf_rn(qx, qx, __fmul_rn(qy, qy));
     const float r = m2 > 1.0f ? rsqrtf(m2) : 1.0f;   // x 1 leaves the value as it is
     return make_float2(qx * r, qy * r);
 }
@@ -405,7 +407,7 @@ __device__ __forceinline__ float2 primal_step(float4 pc, float4 pl, float4 pu, b
         d2 -= pu.w;
     }
     const float t1 = u.x + tau * d1, t2 = u.y + tau * d2;
-    const float g2 = g.x * g.x + g.y * g.y;
+    const float g2 = __fmaf_rn(g.x, g.x, __fmul_rn(g.y, g.y));
     const float rho = r0 + g.x * t1 + g.y * t2;
     const float th = tl * g2;
     const float q = rho / g2;
