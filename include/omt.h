@@ -446,7 +446,9 @@ int omt_structure_texture(const uint8_t *frame, int32_t w, int32_t h, size_t pit
  * clamped); per iteration (sigma = tau = 1/sqrt(8)) the duals of each flow
  * component p <- P((p + sigma grad ubar) / (1 + sigma eps)), P the
  * projection onto the unit disc, then u <- the pointwise prox of
- * tau lambda |rho| at u + tau div p, ubar = 2 u - u_previous.
+ * tau lambda |rho| at u + tau div p, ubar = 2 u - u_previous.  flow also
+ * serves as working storage of the coarser levels; when the call's work
+ * completes it holds the level-0 field.
  * scratch: device, >= omt_tvl1_scratch_bytes.  Asynchronous. */
 int omt_tvl1_flow(const omt_pyramid *prev, const omt_pyramid *next, const omt_flow_params *fp,
                   float *flow, void *scratch, size_t scratch_bytes, void *stream);
