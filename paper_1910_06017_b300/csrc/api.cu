@@ -9,7 +9,7 @@ using namespace omt;
 
 namespace {
 
-constexpr int32_t kVersion = 100;  // 0.1.0
+constexpr int32_t kVersion = 200;  // 0.2.0: omt_flow_params gained block
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

@@ -13,6 +13,7 @@ from ctypes import POINTER, Structure, c_float, c_int32, c_int64, c_size_t, c_ui
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libomt.so")
+ABI_VERSION = 200   # the library version whose structure layouts this binding mirrors
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECHECK = 0, -1, -2, -3, -4, -5
 F32, F16 = 0, 1
@@ -122,6 +123,9 @@ def lib():
         L.omt_error_string.argtypes = [c_int32]
         L.omt_error_string.restype = ctypes.c_char_p
         L.omt_version.restype = c_int32
+        if L.omt_version() != ABI_VERSION:
+            raise OSError(f"{LIB_PATH} is version {L.omt_version()}, the binding's structures are "
+                          f"those of version {ABI_VERSION}; rebuild the library")
         L.omt_iou_matrix.argtypes = [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_void_p]
         L.omt_assign_workspace_bytes.argtypes = [c_int32, c_int32]
         L.omt_assign_workspace_bytes.restype = c_size_t

@@ -303,3 +303,9 @@ def test_working_level_arguments_rejected_before_launch():
     assert lib.omt_scale_boxes(None, 0, ctypes.c_float(0.5), None, None) == omt.OK
     assert lib.omt_scale_boxes(ctypes.c_void_p((1 << 24) + 4), 2, ctypes.c_float(0.5), fake,
                                None) == omt.EINVAL
+
+
+def test_library_version_matches_the_binding():
+    # the binding's ctypes structures mirror one library version's layouts;
+    # loading another version raises instead of misreading a structure
+    assert omt.lib().omt_version() == omt.ABI_VERSION == 200
