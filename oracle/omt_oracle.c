@@ -774,13 +774,129 @@ void orc_structure_texture(const uint8_t *frame, int w, int h, long pitch, doubl
     free(I); free(p); free(q); free(pn);
 }
 
+/* grad (forward differences, zero at the last row / column) of a w x h
+ * field, interleaved (gx, gy) into g. */
+void orc_grad_fwd(const double *u, int w, int h, double *g)
+{
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            const size_t i = (size_t)y * w + x;
+            grad_fwd(u, w, h, x, y, &g[2 * i], &g[2 * i + 1]);
+        }
+}
+
+/* div of an interleaved dual field p (the negative adjoint of grad) into d. */
+void orc_div_bwd(const double *p, int w, int h, double *d)
+{
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) d[(size_t)y * w + x] = div_bwd(p, w, h, x, y);
+}
+
+/* The dual step of one pixel and one flow component: the resolvent of the
+ * conjugate of the Huber norm, p <- P((p + sigma g) / (1 + sigma eps)), g the
+ * forward gradient of ubar there, P the projection onto the unit disc. */
+void orc_tvl1_dual(double px, double py, double gx, double gy, double sigma, double eps,
+                   double *qx_out, double *qy_out)
+{
+    double qx = (px + sigma * gx) / (1.0 + sigma * eps);
+    double qy = (py + sigma * gy) / (1.0 + sigma * eps);
+    const double m = sqrt(qx * qx + qy * qy);
+    if (m > 1.0) { qx /= m; qy /= m; }
+    *qx_out = qx;
+    *qy_out = qy;
+}
+
+/* The primal step's data term at one pixel: the prox of tau lambda |rho|,
+ * rho(v) = r0 + g . v, evaluated at (t1, t2) = u + tau div p. */
+void orc_tvl1_prox(double t1, double t2, double r0, double gx, double gy, double tau,
+                   double lambda, double *v1_out, double *v2_out)
+{
+    const double g2 = gx * gx + gy * gy;
+    const double rho = r0 + gx * t1 + gy * t2;
+    const double th = tau * lambda * g2;
+    double v1 = t1, v2 = t2;
+    if (rho < -th) { v1 = t1 + tau * lambda * gx; v2 = t2 + tau * lambda * gy; }
+    else if (rho > th) { v1 = t1 - tau * lambda * gx; v2 = t2 - tau * lambda * gy; }
+    else if (g2 > 0.0) { v1 = t1 - rho * gx / g2; v2 = t2 - rho * gy / g2; }
+    *v1_out = v1;
+    *v2_out = v2;
+}
+
+/* iters primal-dual iterations (Chambolle-Pock, sigma = tau = 1/sqrt(8)) of
+ * one warp of one lw x lh level: the linearised data term rho(u) = r0 +
+ * gw . u (gw interleaved), the flow u (interleaved (u1, u2)) and the duals p
+ * ((p1x, p1y, p2x, p2y) per pixel) updated in place; the extrapolation ubar
+ * starts at u. */
+void orc_tvl1_iterations(const double *gw, const double *r0, int lw, int lh, double lambda,
+                         double eps, int iters, double *u, double *p)
+{
+    const double sigma = 1.0 / sqrt(8.0), tau = 1.0 / sqrt(8.0);
+    const size_t n = (size_t)lw * lh;
+    double *ub = (double *)malloc(sizeof(double) * 2 * n);
+    double *uold = (double *)malloc(sizeof(double) * 2 * n);
+    double *p1 = (double *)malloc(sizeof(double) * 2 * n), *p2 = (double *)malloc(sizeof(double) * 2 * n);
+    double *comp = (double *)malloc(sizeof(double) * n);
+    memcpy(ub, u, sizeof(double) * 2 * n);
+    for (int it = 0; it < iters; ++it) {
+        /* dual step, each flow component on its own */
+        for (int d = 0; d < 2; ++d) {
+            for (size_t i = 0; i < n; ++i) comp[i] = ub[2 * i + d];
+            for (int y = 0; y < lh; ++y)
+                for (int x = 0; x < lw; ++x) {
+                    const size_t i = (size_t)y * lw + x;
+                    double gx, gy;
+                    grad_fwd(comp, lw, lh, x, y, &gx, &gy);
+                    orc_tvl1_dual(p[4 * i + 2 * d], p[4 * i + 2 * d + 1], gx, gy, sigma, eps,
+                                  &p[4 * i + 2 * d], &p[4 * i + 2 * d + 1]);
+                }
+        }
+        /* primal step: u~ = u + tau div p, then the data prox */
+        for (size_t i = 0; i < n; ++i) {
+            p1[2 * i] = p[4 * i]; p1[2 * i + 1] = p[4 * i + 1];
+            p2[2 * i] = p[4 * i + 2]; p2[2 * i + 1] = p[4 * i + 3];
+        }
+        memcpy(uold, u, sizeof(double) * 2 * n);
+        for (int y = 0; y < lh; ++y)
+            for (int x = 0; x < lw; ++x) {
+                const size_t i = (size_t)y * lw + x;
+                const double t1 = u[2 * i] + tau * div_bwd(p1, lw, lh, x, y);
+                const double t2 = u[2 * i + 1] + tau * div_bwd(p2, lw, lh, x, y);
+                orc_tvl1_prox(t1, t2, r0[i], gw[2 * i], gw[2 * i + 1], tau, lambda, &u[2 * i],
+                              &u[2 * i + 1]);
+            }
+        for (size_t i = 0; i < 2 * n; ++i) ub[i] = 2.0 * u[i] - uold[i];
+    }
+    free(ub); free(uold); free(p1); free(p2); free(comp);
+}
+
+/* The linearisation of a warp: frame t+1 and its gradient sampled
+ * bilinearly at x + u0 (taps clamped), intensities scaled to [0, 1]: gw =
+ * grad I1w, r0 = I1w - gw . u0 - I0 (I0, I1: lw x lh; G1 interleaved). */
+void orc_tvl1_warp(const double *I0, const double *I1, const double *G1, int lw, int lh,
+                   const double *u, double *gw, double *r0)
+{
+    const double s255 = 1.0 / 255.0;
+    for (int y = 0; y < lh; ++y)
+        for (int x = 0; x < lw; ++x) {
+            const size_t i = (size_t)y * lw + x;
+            const double sx = x + u[2 * i], sy = y + u[2 * i + 1];
+            const int ix = (int)floor(sx), iy = (int)floor(sy);
+            const double a = sx - ix, b = sy - iy;
+            const double I1w = bilin(I1, 1, 0, lw, lh, ix, iy, a, b) * s255;
+            const double gx = bilin(G1, 2, 0, lw, lh, ix, iy, a, b) * s255;
+            const double gy = bilin(G1, 2, 1, lw, lh, ix, iy, a, b) * s255;
+            gw[2 * i] = gx;
+            gw[2 * i + 1] = gy;
+            r0[i] = I1w - gx * u[2 * i] - gy * u[2 * i + 1] - I0[i] * s255;
+        }
+}
+
 /* Dense Huber-TV-L1 flow from frame t (P0) to t+1 (P1), packed pyramids as
  * orc_pyramid writes them, into flow (w x h interleaved (u1, u2), level-0
  * pixels). */
 void orc_tvl1(const double *img0, const double *img1, const double *grad1, int w, int h,
               int levels, double lambda, double eps, int warps, int iters, double *flow)
 {
-    const double sigma = 1.0 / sqrt(8.0), tau = 1.0 / sqrt(8.0), s255 = 1.0 / 255.0;
     size_t off[64];
     int lw_[64], lh_[64];
     size_t o = 0;
@@ -809,72 +925,14 @@ void orc_tvl1(const double *img0, const double *img1, const double *grad1, int w
             free(u);
         }
         u = uc;
-        double *p = (double *)malloc(sizeof(double) * 4 * n);   /* (p1x, p1y, p2x, p2y) */
-        double *ub = (double *)malloc(sizeof(double) * 2 * n);
-        double *uold = (double *)malloc(sizeof(double) * 2 * n);
+        double *p = (double *)calloc(4 * n, sizeof(double));   /* (p1x, p1y, p2x, p2y) */
         double *gw = (double *)malloc(sizeof(double) * 2 * n);  /* grad I1 at x + u0, scaled */
         double *r0 = (double *)malloc(sizeof(double) * n);
-        double *p1 = (double *)malloc(sizeof(double) * 2 * n), *p2 = (double *)malloc(sizeof(double) * 2 * n);
-        double *comp = (double *)malloc(sizeof(double) * n);
-        for (size_t i = 0; i < 4 * n; ++i) p[i] = 0.0;
         for (int wp = 0; wp < warps; ++wp) {
-            for (int y = 0; y < lh; ++y)
-                for (int x = 0; x < lw; ++x) {
-                    const size_t i = (size_t)y * lw + x;
-                    const double sx = x + u[2 * i], sy = y + u[2 * i + 1];
-                    const int ix = (int)floor(sx), iy = (int)floor(sy);
-                    const double a = sx - ix, b = sy - iy;
-                    const double I1w = bilin(I1, 1, 0, lw, lh, ix, iy, a, b) * s255;
-                    const double gx = bilin(G1, 2, 0, lw, lh, ix, iy, a, b) * s255;
-                    const double gy = bilin(G1, 2, 1, lw, lh, ix, iy, a, b) * s255;
-                    gw[2 * i] = gx;
-                    gw[2 * i + 1] = gy;
-                    r0[i] = I1w - gx * u[2 * i] - gy * u[2 * i + 1] - I0[i] * s255;
-                }
-            memcpy(ub, u, sizeof(double) * 2 * n);
-            for (int it = 0; it < iters; ++it) {
-                /* dual step, each flow component on its own */
-                for (int d = 0; d < 2; ++d) {
-                    for (size_t i = 0; i < n; ++i) comp[i] = ub[2 * i + d];
-                    for (int y = 0; y < lh; ++y)
-                        for (int x = 0; x < lw; ++x) {
-                            const size_t i = (size_t)y * lw + x;
-                            double gx, gy;
-                            grad_fwd(comp, lw, lh, x, y, &gx, &gy);
-                            double qx = (p[4 * i + 2 * d] + sigma * gx) / (1.0 + sigma * eps);
-                            double qy = (p[4 * i + 2 * d + 1] + sigma * gy) / (1.0 + sigma * eps);
-                            const double m = sqrt(qx * qx + qy * qy);
-                            if (m > 1.0) { qx /= m; qy /= m; }
-                            p[4 * i + 2 * d] = qx;
-                            p[4 * i + 2 * d + 1] = qy;
-                        }
-                }
-                /* primal step: u~ = u + tau div p, then the data prox */
-                for (size_t i = 0; i < n; ++i) {
-                    p1[2 * i] = p[4 * i]; p1[2 * i + 1] = p[4 * i + 1];
-                    p2[2 * i] = p[4 * i + 2]; p2[2 * i + 1] = p[4 * i + 3];
-                }
-                memcpy(uold, u, sizeof(double) * 2 * n);
-                for (int y = 0; y < lh; ++y)
-                    for (int x = 0; x < lw; ++x) {
-                        const size_t i = (size_t)y * lw + x;
-                        const double t1 = u[2 * i] + tau * div_bwd(p1, lw, lh, x, y);
-                        const double t2 = u[2 * i + 1] + tau * div_bwd(p2, lw, lh, x, y);
-                        const double gx = gw[2 * i], gy = gw[2 * i + 1];
-                        const double g2 = gx * gx + gy * gy;
-                        const double rho = r0[i] + gx * t1 + gy * t2;
-                        const double th = tau * lambda * g2;
-                        double v1 = t1, v2 = t2;
-                        if (rho < -th) { v1 = t1 + tau * lambda * gx; v2 = t2 + tau * lambda * gy; }
-                        else if (rho > th) { v1 = t1 - tau * lambda * gx; v2 = t2 - tau * lambda * gy; }
-                        else if (g2 > 0.0) { v1 = t1 - rho * gx / g2; v2 = t2 - rho * gy / g2; }
-                        u[2 * i] = v1;
-                        u[2 * i + 1] = v2;
-                    }
-                for (size_t i = 0; i < 2 * n; ++i) ub[i] = 2.0 * u[i] - uold[i];
-            }
+            orc_tvl1_warp(I0, I1, G1, lw, lh, u, gw, r0);
+            orc_tvl1_iterations(gw, r0, lw, lh, lambda, eps, iters, u, p);
         }
-        free(p); free(ub); free(uold); free(gw); free(r0); free(p1); free(p2); free(comp);
+        free(p); free(gw); free(r0);
     }
     memcpy(flow, u, sizeof(double) * 2 * (size_t)w * h);
     free(u);

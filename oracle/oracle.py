@@ -68,6 +68,14 @@ def lib():
                                             POINTER(c_double)]
         L.orc_tvl1.argtypes = [POINTER(c_double), POINTER(c_double), POINTER(c_double), c_int, c_int,
                                c_int, c_double, c_double, c_int, c_int, POINTER(c_double)]
+        L.orc_grad_fwd.argtypes = [POINTER(c_double), c_int, c_int, POINTER(c_double)]
+        L.orc_div_bwd.argtypes = [POINTER(c_double), c_int, c_int, POINTER(c_double)]
+        L.orc_tvl1_dual.argtypes = [c_double] * 6 + [POINTER(c_double)] * 2
+        L.orc_tvl1_prox.argtypes = [c_double] * 7 + [POINTER(c_double)] * 2
+        L.orc_tvl1_iterations.argtypes = [POINTER(c_double), POINTER(c_double), c_int, c_int,
+                                          c_double, c_double, c_int, POINTER(c_double),
+                                          POINTER(c_double)]
+        L.orc_tvl1_warp.argtypes = [POINTER(c_double)] * 3 + [c_int, c_int] + [POINTER(c_double)] * 3
         L.orc_box_mean_flow.argtypes = [POINTER(c_double), c_int, c_int, POINTER(c_float), c_int,
                                         POINTER(c_double)]
         L.orc_working_level.argtypes = [c_int, c_int]
@@ -254,6 +262,67 @@ def tvl1(prev: Pyramid, nxt: Pyramid, lam=TVL1_LAMBDA, eps=TVL1_EPS, warps=TVL1_
                    _p(nxt.grad_flat, c_double), prev.w, prev.h, prev.levels, float(lam),
                    float(eps), int(warps), int(iters), _p(out, c_double))
     return out
+
+
+def grad_fwd(u):
+    """Forward differences of a (h, w) field, zero at the last row/column: (h, w, 2)."""
+    f = np.ascontiguousarray(u, dtype=np.float64)
+    h, w = f.shape
+    g = np.zeros((h, w, 2), np.float64)
+    lib().orc_grad_fwd(_p(f, c_double), w, h, _p(g, c_double))
+    return g
+
+
+def div_bwd(p):
+    """Divergence of a (h, w, 2) dual field, the negative adjoint of grad_fwd: (h, w)."""
+    q = np.ascontiguousarray(p, dtype=np.float64)
+    h, w = q.shape[:2]
+    d = np.zeros((h, w), np.float64)
+    lib().orc_div_bwd(_p(q, c_double), w, h, _p(d, c_double))
+    return d
+
+
+def tvl1_dual(p, g, sigma, eps):
+    """One pixel's Huber-TV dual step of one flow component: (qx, qy)."""
+    qx, qy = c_double(), c_double()
+    lib().orc_tvl1_dual(float(p[0]), float(p[1]), float(g[0]), float(g[1]), float(sigma),
+                        float(eps), ctypes.byref(qx), ctypes.byref(qy))
+    return qx.value, qy.value
+
+
+def tvl1_prox(t, r0, g, tau, lam):
+    """One pixel's prox of tau lam |r0 + g . v| at v = t: (v1, v2)."""
+    v1, v2 = c_double(), c_double()
+    lib().orc_tvl1_prox(float(t[0]), float(t[1]), float(r0), float(g[0]), float(g[1]),
+                        float(tau), float(lam), ctypes.byref(v1), ctypes.byref(v2))
+    return v1.value, v2.value
+
+
+def tvl1_iterations(gw, r0, u, p, iters, lam=TVL1_LAMBDA, eps=TVL1_EPS):
+    """iters primal-dual iterations of one warp on one level: (u, p) after
+    them; gw (h, w, 2), r0 (h, w), u (h, w, 2), p (h, w, 4)."""
+    G = np.ascontiguousarray(gw, dtype=np.float64)
+    R = np.ascontiguousarray(r0, dtype=np.float64)
+    h, w = R.shape
+    U = np.array(u, dtype=np.float64, copy=True, order="C")
+    P = np.array(p, dtype=np.float64, copy=True, order="C")
+    lib().orc_tvl1_iterations(_p(G, c_double), _p(R, c_double), w, h, float(lam), float(eps),
+                              int(iters), _p(U, c_double), _p(P, c_double))
+    return U, P
+
+
+def tvl1_warp(I0, I1, G1, u):
+    """Linearisation of one warp: (gw (h, w, 2), r0 (h, w))."""
+    a = np.ascontiguousarray(I0, dtype=np.float64)
+    b = np.ascontiguousarray(I1, dtype=np.float64)
+    g = np.ascontiguousarray(G1, dtype=np.float64)
+    U = np.ascontiguousarray(u, dtype=np.float64)
+    h, w = a.shape
+    gw = np.zeros((h, w, 2), np.float64)
+    r0 = np.zeros((h, w), np.float64)
+    lib().orc_tvl1_warp(_p(a, c_double), _p(b, c_double), _p(g, c_double), w, h, _p(U, c_double),
+                        _p(gw, c_double), _p(r0, c_double))
+    return gw, r0
 
 
 def box_mean_flow(flow, boxes):
