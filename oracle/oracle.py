@@ -97,16 +97,27 @@ def level_size(w: int, h: int, level: int):
 
 
 class Pyramid:
-    """Oracle pyramid of one frame: img[L] (h_L, w_L) and grad[L] (h_L, w_L, 2)."""
+    """Oracle pyramid of one frame: img[L] (h_L, w_L) and grad[L] (h_L, w_L, 2).
 
-    def __init__(self, frame: np.ndarray, levels: int):
+    storage "f64" (default): every level and gradient plane in FP64, from
+    the definitions (Section V-A preprocessing; binomial reduction, Scharr).
+    storage "f16": the values a pyramid stored in half precision holds --
+    level 0 is the u8 frame; each level L >= 1 is the binomial reduction of
+    level L-1 *as stored*, rounded to half(I - 128) (the value kept is that
+    half plus 128); each gradient plane is the Scharr gradient of its level
+    as stored, rounded to half.  The reduction and the gradient are the FP64
+    ones of the "f64" pyramid, applied level by level to the stored values."""
+
+    def __init__(self, frame: np.ndarray, levels: int, storage: str = "f64"):
         """frame: uint8 (a video frame) or float64 (an unquantised render)."""
         h, w = frame.shape
-        self.w, self.h, self.levels = w, h, levels
+        self.w, self.h, self.levels, self.storage = w, h, levels, storage
         n = lib().orc_pyramid_elems(w, h, levels)
         self.img_flat = np.zeros(n, np.float64)
         self.grad_flat = np.zeros(2 * n, np.float64)
-        if frame.dtype == np.uint8:
+        if storage == "f16":
+            self._build_f16(frame, levels)
+        elif frame.dtype == np.uint8:
             f = np.ascontiguousarray(frame)
             lib().orc_pyramid(_p(f, c_uint8), w, h, w, levels, _p(self.img_flat, c_double),
                               _p(self.grad_flat, c_double))
@@ -121,6 +132,29 @@ class Pyramid:
             self.img.append(self.img_flat[off:off + lw * lh].reshape(lh, lw))
             self.grad.append(self.grad_flat[2 * off:2 * (off + lw * lh)].reshape(lh, lw, 2))
             off += lw * lh
+
+    def _build_f16(self, frame, levels):
+        assert frame.dtype == np.uint8, "half storage starts from a u8 frame"
+        h, w = frame.shape
+        cur = np.ascontiguousarray(frame, dtype=np.float64)   # level L as stored
+        off = 0
+        for L in range(levels):
+            lw, lh = level_size(w, h, L)
+            # the FP64 gradient of the stored level and the FP64 reduction of it
+            two = min(2, levels - L)
+            n2 = lib().orc_pyramid_elems(lw, lh, two)
+            img2 = np.zeros(n2, np.float64)
+            grad2 = np.zeros(2 * n2, np.float64)
+            lib().orc_pyramid_f64(_p(cur, c_double), lw, lh, two, _p(img2, c_double),
+                                  _p(grad2, c_double))
+            self.img_flat[off:off + lw * lh] = cur.reshape(-1)
+            self.grad_flat[2 * off:2 * (off + lw * lh)] = \
+                grad2[:2 * lw * lh].astype(np.float16).astype(np.float64)
+            off += lw * lh
+            if two == 2:
+                nw, nh = level_size(w, h, L + 1)
+                nxt = img2[lw * lh:lw * lh + nw * nh].reshape(nh, nw)
+                cur = np.ascontiguousarray((nxt - 128.0).astype(np.float16).astype(np.float64) + 128.0)
 
 
 def isqrt(d: int) -> int:

@@ -17,7 +17,13 @@
 // Exactness: the Scharr weights 3/32 and 10/32 and the integer binomial
 // weights with a final 1/256 keep every value that is dyadic-exact in FP32
 // (pyramid levels 0-2, gradients of levels 0-1) bit-identical to the
-// definition.
+// definition.  From level 2 on, a level's values need more bits than FP32
+// sums keep, so those launches form the sums exactly in 64-bit fixed point
+// (a level-L value, stored or not, is a multiple of 2^-8L: each reduction
+// divides by 2^8 and rounding only coarsens) and round once: the stored
+// value is the correctly rounded result of the definition applied to the
+// level above as stored, in both storages (half outputs go through a
+// round-to-odd FP32 value, which makes the second rounding exact).
 #include "omt_internal.cuh"
 
 namespace omt {
@@ -31,6 +37,7 @@ constexpr int NT = 256;        // threads per CTA: 32 column groups x 8 row grou
 static_assert(TY == RPT * (NT / 32), "tile rows");
 
 enum Fmt { FMT_U8 = 0, FMT_H16 = 1, FMT_F32 = 2 };  // storage of level L's texels
+enum Path { PATH_FLOAT = 0, PATH_SPLIT = 1, PATH_INT64 = 2 };  // how a level's sums stay exact
 
 template <int FMT>
 struct Stage {
@@ -53,7 +60,12 @@ struct LevelArgs {
     uint8_t *next;        // level L+1 image plane or nullptr
     int64_t next_pitch;
     int nw, nh;           // level L+1 size
+    int frac;             // 0: FP32 sums (exact for levels 0, 1); else the fixed-point
+                          // fraction bits of level L's values (8 L, at most 40)
 };
+
+// Fixed-point fraction bits for the sums over level L (see the header).
+__host__ __device__ __forceinline__ int level_frac(int L) { return L < 2 ? 0 : (L > 5 ? 40 : 8 * L); }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -181,6 +193,21 @@ __device__ __forceinline__ void store_next(const LevelArgs &a, int Y, int X0, fl
     }
 }
 
+// store_next for values already in the stored domain (half storage: I - 128).
+template <int ST>
+__device__ __forceinline__ void store_next_stored(const LevelArgs &a, int Y, int X0, float v0,
+                                                  float v1) {
+    if (Y >= a.nh || X0 >= a.nw) return;
+    uint8_t *row = a.next + (int64_t)Y * a.next_pitch;
+    if (ST == OMT_F32) {
+        if (X0 + 1 < a.nw) ((float2 *)row)[X0 >> 1] = make_float2(v0, v1);
+        else ((float *)row)[X0] = v0;
+    } else {
+        if (X0 + 1 < a.nw) ((__half2 *)row)[X0 >> 1] = __floats2half2_rn(v0, v1);
+        else ((__half *)row)[X0] = __float2half_rn(v0);
+    }
+}
+
 // This thread's share of the staged 128x32 tile of level L at (ox, oy).
 template <int ST, int FMT>
 __device__ __forceinline__ void compute_tile(const LevelArgs &a, int ox, int oy, const uint8_t *st) {
@@ -236,6 +263,210 @@ __device__ __forceinline__ void compute_tile(const LevelArgs &a, int ox, int oy,
     }
 }
 
+// ------------------------------------------------------------ exact sums
+// 2^e as a float, e in [-126, 127].
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// s as a float rounded to odd (truncate, then set the last bit if inexact):
+// rounding that to half precision gives the correctly rounded half of s.
+__device__ __forceinline__ float ll2float_odd(long long s) {
+    const float f = __ll2float_rz(s);
+    return __float2ll_rz(f) == s ? f : __int_as_float(__float_as_int(f) | 1);
+}
+
+// Values of tile columns 4g-2 .. 4g+5 of staged row r as integers v 2^frac.
+template <int FMT>
+__device__ __forceinline__ void staged_row_fixed(const uint8_t *st, int r, int g, float scale,
+                                                 long long off, long long q[8]) {
+    using S = Stage<FMT>;
+    const uint8_t *row = st + r * S::RB;
+    if (FMT == FMT_H16) {
+        const unsigned *w = (const unsigned *)row + 2 * g + 3;
+        const unsigned u[4] = {w[0], w[1], w[2], w[3]};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float h = __half2float(__ushort_as_half((unsigned short)((u[c >> 1] >> (16 * (c & 1))) & 0xFFFFu)));
+            q[c] = __float2ll_rn(h * scale) + off;   // half(I - 128) 2^frac + 128 2^frac
+        }
+    } else {
+        const float *f = (const float *)row + 4 * g + 2;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) q[c] = __float2ll_rn(f[c] * scale);
+    }
+}
+
+// The stored value of the integer s times 2^-e (correctly rounded).
+template <int ST>
+__device__ __forceinline__ float fixed_out(long long s, int e) {
+    if (ST == OMT_F32) return __ll2float_rn(s) * pow2f(-e);
+    return ll2float_odd(s) * pow2f(-e);   // the half store rounds it once more, exactly
+}
+
+template <int ST>
+__device__ __forceinline__ void store_grads_fixed(const LevelArgs &a, int y, int x,
+                                                  const long long gx[4], const long long gy[4]) {
+    float fx[4], fy[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        fx[c] = fixed_out<ST>(gx[c], a.frac + 5);
+        fy[c] = fixed_out<ST>(gy[c], a.frac + 5);
+    }
+    store_grads<ST>(a, y, x, fx, fy);
+}
+
+// compute_tile with the sums in 64-bit fixed point (levels >= 2).
+template <int ST, int FMT>
+__device__ __forceinline__ void compute_tile_fixed(const LevelArgs &a, int ox, int oy,
+                                                   const uint8_t *st) {
+    const int g = threadIdx.x & 31;
+    const int q = threadIdx.x >> 5;
+    const int x = ox + 4 * g;
+    if (x >= a.w) return;
+    const int y0 = oy + RPT * q;
+    const float scale = pow2f(a.frac);
+    const long long off = 128ll << a.frac;
+    long long d[RPT + 3][4], hh[RPT + 3][4], hs[RPT + 3][2];
+#pragma unroll
+    for (int k = 0; k < RPT + 3; ++k) {
+        long long m[8];
+        staged_row_fixed<FMT>(st, RPT * q + k, g, scale, off, m);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            d[k][c] = m[c + 3] - m[c + 1];
+            hh[k][c] = 10 * m[c + 2] + 3 * (m[c + 1] + m[c + 3]);
+        }
+        hs[k][0] = (m[0] + m[4]) + 4 * (m[1] + m[3]) + 6 * m[2];
+        hs[k][1] = (m[2] + m[6]) + 4 * (m[3] + m[5]) + 6 * m[4];
+        if (k >= 3 && k < RPT + 3 && y0 + k - 3 < a.h) {
+            long long gx[4], gy[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                gx[c] = 10 * d[k - 1][c] + 3 * (d[k - 2][c] + d[k][c]);
+                gy[c] = hh[k][c] - hh[k - 2][c];
+            }
+            store_grads_fixed<ST>(a, y0 + k - 3, x, gx, gy);
+        }
+        if (a.next && k >= 4 && ((k & 1) == 0)) {
+            float o[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                long long v = (hs[k - 4][c] + hs[k][c]) + 4 * (hs[k - 3][c] + hs[k - 1][c]) +
+                              6 * hs[k - 2][c];
+                // half storage keeps I - 128: subtract before the one rounding
+                if (ST == OMT_F16) v -= 128ll << (a.frac + 8);
+                o[c] = fixed_out<ST>(v, a.frac + 8);
+            }
+            store_next_stored<ST>(a, (y0 >> 1) + (k - 4) / 2, x >> 1, o[0], o[1]);
+        }
+    }
+}
+
+// ------------------------------------------------------ split FP32 sums
+// A level-2 or level-3 value v (a multiple of 2^-16 or 2^-24 below 256) is
+// split into hi = v rounded to a multiple of 2^-8 and lo = v - hi (|lo| <=
+// 2^-9): every FP32 sum compute_tile forms is then exact for hi and for lo
+// separately (at most 24 significant bits each), and the output is their
+// sum rounded once -- to nearest for FP32 storage, to odd for half storage,
+// whose store then rounds once more, exactly.
+__device__ __forceinline__ void split_hi_lo(float v, float &hi, float &lo) {
+    const float C = 49152.0f;   // 1.5 * 2^15: v + C has a 2^-8 ulp
+    hi = (v + C) - C;
+    lo = v - hi;
+}
+
+// a + b rounded to nearest (ST F32) or to odd (ST F16), a and b exact.
+template <int ST>
+__device__ __forceinline__ float sum_out(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    if (ST == OMT_F32) return s;
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));  // a + b = s + e
+    if (e == 0.0f || (__float_as_int(s) & 1)) return s;
+    // s is even and inexact: the odd neighbour on e's side
+    const int away = (e > 0.0f) == (s > 0.0f) ? 1 : -1;   // magnitude up or down
+    return s == 0.0f ? e : __int_as_float(__float_as_int(s) + away);
+}
+
+// Tile columns 4g-2 .. 4g+5 of staged row r, split (values I, not I - 128).
+template <int FMT>
+__device__ __forceinline__ void staged_row_split(const uint8_t *st, int r, int g, float hi[8],
+                                                 float lo[8]) {
+    using S = Stage<FMT>;
+    const uint8_t *row = st + r * S::RB;
+    if (FMT == FMT_H16) {
+        const unsigned *w = (const unsigned *)row + 2 * g + 3;
+        const unsigned u[4] = {w[0], w[1], w[2], w[3]};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float h = __half2float(__ushort_as_half((unsigned short)((u[c >> 1] >> (16 * (c & 1))) & 0xFFFFu)));
+            float hh;
+            split_hi_lo(h, hh, lo[c]);   // |h| <= 128: the same 2^-8 grid
+            hi[c] = hh + 128.0f;
+        }
+    } else {
+        const float *f = (const float *)row + 4 * g + 2;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) split_hi_lo(f[c], hi[c], lo[c]);
+    }
+}
+
+// compute_tile with every sum formed on the hi and lo parts (levels 2-3).
+template <int ST, int FMT>
+__device__ __forceinline__ void compute_tile_split(const LevelArgs &a, int ox, int oy,
+                                                   const uint8_t *st) {
+    const int g = threadIdx.x & 31;
+    const int q = threadIdx.x >> 5;
+    const int x = ox + 4 * g;
+    if (x >= a.w) return;
+    const int y0 = oy + RPT * q;
+    float d[2][RPT + 3][4], hh[2][RPT + 3][4], hs[2][RPT + 3][2];
+#pragma unroll
+    for (int k = 0; k < RPT + 3; ++k) {
+        float m[2][8];
+        staged_row_split<FMT>(st, RPT * q + k, g, m[0], m[1]);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                d[p][k][c] = m[p][c + 3] - m[p][c + 1];
+                hh[p][k][c] = fmaf(10.0f / 32.0f, m[p][c + 2], (3.0f / 32.0f) * (m[p][c + 1] + m[p][c + 3]));
+            }
+            hs[p][k][0] = (m[p][0] + m[p][4]) + 4.0f * (m[p][1] + m[p][3]) + 6.0f * m[p][2];
+            hs[p][k][1] = (m[p][2] + m[p][6]) + 4.0f * (m[p][3] + m[p][5]) + 6.0f * m[p][4];
+        }
+        if (k >= 3 && k < RPT + 3 && y0 + k - 3 < a.h) {
+            float gx[4], gy[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float px[2], py[2];
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    px[p] = fmaf(10.0f / 32.0f, d[p][k - 1][c], (3.0f / 32.0f) * (d[p][k - 2][c] + d[p][k][c]));
+                    py[p] = hh[p][k][c] - hh[p][k - 2][c];
+                }
+                gx[c] = sum_out<ST>(px[0], px[1]);
+                gy[c] = sum_out<ST>(py[0], py[1]);
+            }
+            store_grads<ST>(a, y0 + k - 3, x, gx, gy);
+        }
+        if (a.next && k >= 4 && ((k & 1) == 0)) {
+            float o[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                float n[2];
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+                    n[p] = (hs[p][k - 4][c] + hs[p][k][c]) + 4.0f * (hs[p][k - 3][c] + hs[p][k - 1][c]) +
+                           6.0f * hs[p][k - 2][c];
+                // 256 (I - 128) for half storage: exact on the hi part
+                if (ST == OMT_F16) n[0] -= 32768.0f;
+                o[c] = sum_out<ST>(n[0], n[1]) * (1.0f / 256.0f);
+            }
+            store_next_stored<ST>(a, (y0 >> 1) + (k - 4) / 2, x >> 1, o[0], o[1]);
+        }
+    }
+}
+
 // A tile to process: its level arguments and origin.
 struct Tile {
     LevelArgs a;
@@ -249,7 +480,7 @@ struct Tile {
 // the slot being written is never one that a thread may still read: slot
 // i % 3 serves the CTA's i-th tile, written at the top of trip i - 1 and
 // read until the end of trip i, and trip i + 1 writes slot (i + 2) % 3).
-template <int ST, int FMT, typename Resolve>
+template <int ST, int FMT, int PATH, typename Resolve>
 __device__ __forceinline__ void tile_pipeline(int total, Resolve resolve) {
     extern __shared__ __align__(16) uint8_t pyr_smem[];
     uint8_t *st[2] = {pyr_smem, pyr_smem + Stage<FMT>::BYTES};
@@ -272,14 +503,16 @@ __device__ __forceinline__ void tile_pipeline(int total, Resolve resolve) {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();  // tile g is staged by every thread
-        compute_tile<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
+        if constexpr (PATH == PATH_INT64) compute_tile_fixed<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
+        else if constexpr (PATH == PATH_SPLIT) compute_tile_split<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
+        else compute_tile<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
     }
 }
 
-template <int ST, int FMT>
+template <int ST, int FMT, int PATH>
 __global__ void __launch_bounds__(NT) pyramid_level_kernel(const LevelArgs a, int tiles_x,
                                                            int total) {
-    tile_pipeline<ST, FMT>(total, [&](int g, Tile &t) {
+    tile_pipeline<ST, FMT, PATH>(total, [&](int g, Tile &t) {
         const int ty = g / tiles_x, tx = g - ty * tiles_x;
         t.a = a;
         t.ox = tx * TX;
@@ -308,6 +541,7 @@ __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int 
     }
     a.grad = const_cast<uint8_t *>(v.grad);
     a.grad_pitch = v.grad_pitch;
+    a.frac = level_frac(L);
     if (L + 1 < levels) {
         const LevelView &n = e.P_next[L + 1];
         a.next = const_cast<uint8_t *>(n.img);
@@ -323,12 +557,12 @@ __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int 
 
 // Level L of every stream of a batch: the CTAs stride over the batch's
 // tiles (tile prefix per stream in the table).
-template <int ST, int FMT>
+template <int ST, int FMT, int PATH>
 __global__ void __launch_bounds__(NT) pyramid_batch_kernel(const uint8_t *table, int L) {
     const BatchView t(table);
     const int *pre = t.pyr_prefix(L);
     const int total = pre[t.nstreams()];
-    tile_pipeline<ST, FMT>(total, [&](int g, Tile &tile) {
+    tile_pipeline<ST, FMT, PATH>(total, [&](int g, Tile &tile) {
         const int si = find_segment(pre, t.nstreams(), g);
         const StreamEntry &e = t.stream(si);
         const int tiles_x = (e.P_next[L].w + TX - 1) / TX;
@@ -363,27 +597,60 @@ cudaError_t grid_for(K kernel, int tiles, size_t smem, int *cap, int &grid) {
     return cudaSuccess;
 }
 
-template <int ST, int FMT>
-cudaError_t launch_level(const LevelArgs &a, cudaStream_t s) {
+template <int ST, int FMT, int PATH>
+cudaError_t launch_level_k(const LevelArgs &a, cudaStream_t s) {
     const int tiles_x = (a.w + TX - 1) / TX, total = tiles_x * ((a.h + TY - 1) / TY);
     const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
     static int cap[64] = {0};
     int grid = 0;
-    cudaError_t e = grid_for(pyramid_level_kernel<ST, FMT>, total, smem, cap, grid);
+    cudaError_t e = grid_for(pyramid_level_kernel<ST, FMT, PATH>, total, smem, cap, grid);
     if (e != cudaSuccess) return e;
-    pyramid_level_kernel<ST, FMT><<<grid, NT, smem, s>>>(a, tiles_x, total);
+    pyramid_level_kernel<ST, FMT, PATH><<<grid, NT, smem, s>>>(a, tiles_x, total);
+    return cudaGetLastError();
+}
+
+// Level 0 reads the u8 frame; level 1 sums in FP32 (exact); levels 2-3
+// split their values in two FP32 parts (exact); deeper levels sum in 64-bit
+// fixed point.
+__host__ __device__ __forceinline__ int level_path(int frac) {
+    return frac == 0 ? PATH_FLOAT : (frac <= 24 ? PATH_SPLIT : PATH_INT64);
+}
+
+template <int ST, int FMT>
+cudaError_t launch_level(const LevelArgs &a, cudaStream_t s) {
+    if constexpr (FMT == FMT_U8) {
+        return launch_level_k<ST, FMT, PATH_FLOAT>(a, s);
+    } else {
+        switch (level_path(a.frac)) {
+            case PATH_SPLIT: return launch_level_k<ST, FMT, PATH_SPLIT>(a, s);
+            case PATH_INT64: return launch_level_k<ST, FMT, PATH_INT64>(a, s);
+            default: return launch_level_k<ST, FMT, PATH_FLOAT>(a, s);
+        }
+    }
+}
+
+template <int ST, int FMT, int PATH>
+cudaError_t launch_batch_level_k(const uint8_t *table, int L, int max_tiles, cudaStream_t s) {
+    const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
+    static int cap[64] = {0};
+    int grid = 0;
+    cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT, PATH>, max_tiles, smem, cap, grid);
+    if (e != cudaSuccess) return e;
+    pyramid_batch_kernel<ST, FMT, PATH><<<grid, NT, smem, s>>>(table, L);
     return cudaGetLastError();
 }
 
 template <int ST, int FMT>
 cudaError_t launch_batch_level(const uint8_t *table, int L, int max_tiles, cudaStream_t s) {
-    const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
-    static int cap[64] = {0};
-    int grid = 0;
-    cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT>, max_tiles, smem, cap, grid);
-    if (e != cudaSuccess) return e;
-    pyramid_batch_kernel<ST, FMT><<<grid, NT, smem, s>>>(table, L);
-    return cudaGetLastError();
+    if constexpr (FMT == FMT_U8) {
+        return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, s);
+    } else {
+        switch (level_path(level_frac(L))) {
+            case PATH_SPLIT: return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, s);
+            case PATH_INT64: return launch_batch_level_k<ST, FMT, PATH_INT64>(table, L, max_tiles, s);
+            default: return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, s);
+        }
+    }
 }
 
 }  // namespace
@@ -411,6 +678,7 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
         }
         a.grad = base + lv.grad_off;
         a.grad_pitch = lv.grad_pitch;
+        a.frac = level_frac(L);
         if (L + 1 < pyr.levels) {
             a.next = base + pyr.lv[L + 1].img_off;
             a.next_pitch = pyr.lv[L + 1].img_pitch;

@@ -282,6 +282,65 @@ def test_batch_equals_plain_win31_five_levels(omt, storage):
             _assert_same({k: v for k, v in a.items() if k != "pyr"}, {k: v for k, v in b.items() if k != "pyr"})
 
 
+@pytest.mark.slow
+def test_bench_workload_f16_step_against_oracle(omt, oracle):
+    """The benchmark's step itself (workload 3: 32 streams, 221 k corners,
+    4 levels, 21x21, F16-stored pyramids, one CUDA-graph replay of
+    omt_batch_step) against the oracle: every stream's corner list bit for
+    bit, then a seeded 5 % sample of the points tracked -- against the
+    oracle on half-precision storage at the FP32 bar, and against the FP64
+    oracle on unquantised pyramids as the error of the storage."""
+    from lk_parity import check, error_vs_fp64, oracle_lk
+    sps = [synth.stream_pair(s) for s in range(32)]
+    caps = [_cap(sp) for sp in sps]
+    params = omt.default_params(levels=4, win=21, max_iter=30, eps=0.01, min_dist=3.0,
+                                storage=1, max_corners=max(caps))
+    B = omt.BatchTracker([sp.size for sp in sps], params, max_boxes=[len(sp.boxes) for sp in sps],
+                         max_corners=caps)
+    for s, sp in enumerate(sps):
+        B.prime(s, torch.from_numpy(sp.frame0).cuda())
+        B.slot(s).copy_(torch.from_numpy(sp.frame1))
+        B.set_boxes(s, torch.from_numpy(sp.boxes))
+    B.pack()
+    B.capture()
+    B.step()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(synth.seed_for(3))
+    cols = {k: [] for k in ("g_out", "g_st", "g_it", "pts", "o_out", "o_st", "o_it", "o_me",
+                            "unstable", "d_out", "d_st")}
+    total = 0
+    for s, sp in enumerate(sps):
+        n = B.count(s)
+        total += n
+        g_pts = B.pts[s][:n].cpu().numpy()
+        pts, cnt = oracle.select_corners(sp.frame0, sp.boxes, caps[s], min_dist=3.0)
+        np.testing.assert_array_equal(B.offsets[s][:len(sp.boxes) + 1].cpu().numpy(),
+                                      np.concatenate([[0], np.cumsum(cnt)]))
+        allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+        np.testing.assert_array_equal(g_pts, allp)
+        pick = np.sort(rng.choice(n, int(round(0.05 * n)), replace=False))
+        sample = allp[pick]
+        kw = dict(levels=4, win=21, max_iter=30, eps=0.01)
+        (o_out, o_st, o_it, o_me), unstable = oracle_lk(oracle, sp.frame0, sp.frame1, sample,
+                                                        probe=True, storage=1, **kw)
+        d_out, d_st = oracle_lk(oracle, sp.frame0, sp.frame1, sample, **kw)[:2]
+        for k, v in (("g_out", B.pts_out[s][:n].cpu().numpy()[pick]),
+                     ("g_st", B.status[s][:n].cpu().numpy()[pick]),
+                     ("g_it", B.iters[s][:n].cpu().numpy()[pick]), ("pts", sample),
+                     ("o_out", o_out), ("o_st", o_st), ("o_it", o_it), ("o_me", o_me),
+                     ("unstable", unstable), ("d_out", d_out), ("d_st", d_st)):
+            cols[k].append(v)
+    c = {k: np.concatenate(v) for k, v in cols.items()}
+    assert total == 221227, total
+    # every stream's points lie in its own frame: validity per stream is
+    # covered by check() with the largest frame's bounds
+    check(f"32-stream batched F16 step, 5 % sample ({len(c['pts'])} of {total})", c["g_out"],
+          c["g_st"], c["g_it"], c["pts"], (1080, 1920), c["o_out"], c["o_st"], c["o_it"],
+          c["o_me"], c["unstable"], 1e-3, 0.01)
+    error_vs_fp64("32-stream batched F16 step, 5 % sample", c["g_out"], c["g_st"], c["d_out"],
+                  c["d_st"], max_nonconv=0.2)
+
+
 def test_lk_staging_waits_never_time_out(omt):
     # every window copy of the LK kernels above landed within its wait limit
     torch.cuda.synchronize()

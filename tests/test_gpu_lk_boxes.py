@@ -1,32 +1,26 @@
 """GPU parity of K3 (pyramidal LK) and K4 (box update) against the FP64
 oracle, through the C-ABI, and end-to-end steps of the whole path.
 
-Bar for FP32 flow: within 1e-3 px of the oracle on every point whose per-
-level iteration counts agree (a differing stopping iteration near eps moves
-the result by up to about eps and is counted and bounded separately);
-statuses identical outside the guard band lambda_min/N in [0.9 tau, 1.1 tau].
-FP16-stored pyramids: within 0.02 px on converged points.
-
-Conditioning probe: the oracle is run twice more with every pyramid value
-multiplied by (1 + 2^-20 z), z ~ N(0, 1): perturbations of about 16 FP32
-ulps, the size of the rounding the GPU's deeper pyramid levels carry.  A
-point whose oracle status, iteration counts or position (by more than
-1e-4 px) changes under that noise sits on a decision no FP32 computation can
-reproduce (oscillating or divergent iterations, stops right at eps, centres
-at the window bound); such points are counted, must stay a small minority,
-and are only checked for validity.
+Bar for flow, both storages: within 1e-3 px of the oracle run on the
+pyramid the GPU stores (F32: the FP64 definition; F16: the oracle's
+half-precision storage, which the F16 kernels produce bit for bit) on every
+point whose per-level iteration counts agree; a stopping iteration that
+differs stays within eps and is counted; statuses identical outside the
+guard band lambda_min/N in [0.9 tau, 1.1 tau] and the points the
+conditioning probe marks (tests/lk_parity.py).  Half-precision storage
+itself is stated per workload against the FP64 oracle on unquantised
+pyramids: within 0.02 px on every converged point, p99 and mean within
+0.02 px on all OK points, the NONCONV share counted and bounded.
 """
 import numpy as np
 import pytest
 
 from paper_1910_06017_b300 import synth
+from lk_parity import (FLOW_TOL, F16_TOL, LOST_EIG, LOST_OOB, NONCONV, OK, compare, error_vs_fp64,
+                       gpu_lk, gpu_pyramid, oracle_lk)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-OK, LOST_EIG, LOST_OOB, NONCONV = 1, 2, 4, 8
-FLOW_TOL = 1e-3
-F16_TOL = 0.02
 
 
 @pytest.fixture(scope="module")
@@ -39,102 +33,14 @@ def omt():
 
 
 def _pyr(omt, frame, levels, storage=0):
-    h, w = frame.shape
-    P = omt.Pyramid(w, h, levels, storage)
-    omt.build_pyramid(torch.from_numpy(np.ascontiguousarray(frame)).cuda(), P,
-                      omt.default_params(levels=levels, storage=storage))
-    return P
-
-
-def gpu_lk(omt, f0, f1, pts, storage=0, **kw):
-    params = omt.default_params(storage=storage, **kw)
-    P0, P1 = _pyr(omt, f0, params.levels, storage), _pyr(omt, f1, params.levels, storage)
-    n = len(pts)
-    p = torch.from_numpy(np.ascontiguousarray(pts, np.float32).reshape(-1, 2)).cuda()
-    out = torch.full((max(n, 1), 2), np.nan, device="cuda")
-    st = torch.full((max(n, 1),), 255, dtype=torch.uint8, device="cuda")
-    it = torch.full((max(n, 1), params.levels), 255, dtype=torch.uint8, device="cuda")
-    omt.lk_track(P0, P1, p, params, out, st, it, n_max=n)
-    torch.cuda.synchronize()
-    return out.cpu().numpy()[:n], st.cpu().numpy()[:n], it.cpu().numpy()[:n]
-
-
-def oracle_lk(oracle, f0, f1, pts, levels=3, win=21, max_iter=30, eps=0.01, min_eig=1e-3,
-              probe=False):
-    O0, O1 = oracle.Pyramid(f0, levels), oracle.Pyramid(f1, levels)
-    kw = dict(win=win, max_iter=max_iter, eps=eps, min_eig=min_eig, diagnostics=True)
-    res = oracle.lk_track(O0, O1, pts, **kw)
-    if not probe:
-        return res
-    unstable = np.zeros(len(res[1]), bool)
-    base = [(P.img_flat.copy(), P.grad_flat.copy()) for P in (O0, O1)]
-    for seed in (12345, 54321):
-        rng = np.random.default_rng(seed)
-        for P, (img, grad) in zip((O0, O1), base):
-            P.img_flat[:] = img * (1.0 + 2.0 ** -20 * rng.standard_normal(img.shape))
-            P.grad_flat[:] = grad * (1.0 + 2.0 ** -20 * rng.standard_normal(grad.shape))
-        res2 = oracle.lk_track(O0, O1, pts, **kw)
-        unstable |= ((res[1] != res2[1]) | np.any(res[2] != res2[2], axis=1) |
-                     (np.abs(res[0] - res2[0]).max(axis=1) > 1e-4))
-    return res, unstable
-
-
-def compare(omt, oracle, f0, f1, pts, storage=0, tol=FLOW_TOL, min_ok=0.9, max_unstable=0.05,
-            **kw):
-    params = dict(levels=3, win=21, max_iter=30, eps=0.01, min_eig=1e-3)
-    params.update(kw)
-    g_out, g_st, g_it = gpu_lk(omt, f0, f1, pts, storage, **params)
-    (o_out, o_st, o_it, o_me), unstable = oracle_lk(oracle, f0, f1, pts, probe=True, **params)
-    assert unstable.mean() <= max_unstable, unstable.mean()
-    tau = params["min_eig"]
-    band = np.any((o_me >= 0.9 * tau) & (o_me <= 1.1 * tau), axis=1)
-    stable = ~unstable & ~band
-    same_status = g_st == o_st
-    if storage == 0:
-        bad = np.nonzero(stable & ~same_status)[0]
-        assert len(bad) == 0, (bad[:10], g_st[bad[:10]], o_st[bad[:10]])
-    else:
-        # FP16 storage moves lambda_min and the stopping test slightly
-        assert np.mean(same_status[stable]) >= 0.98
-    ok = (g_st & OK) > 0
-    assert ok.mean() >= min_ok, ok.mean()
-    agree = np.all(g_it == o_it, axis=1) & same_status & stable
-    if storage == 0:
-        both = agree & ok
-        err = np.abs(g_out[both] - o_out[both]).max(initial=0.0)
-        assert err <= tol, err
-        # stable points whose stopping iteration differs stay within ~eps
-        differ = stable & ~agree & ok & ((o_st & OK) > 0)
-        if differ.any():
-            assert np.abs(g_out[differ] - o_out[differ]).max() <= 2 * params["eps"] + tol
-        assert differ.mean() <= 0.05
-    else:
-        # FP16 storage perturbs every sample by up to 2^-11 relative, far
-        # above the probe's noise; points that never converge (NONCONV: the
-        # iteration still oscillates at max_iter) carry that into their
-        # final position, so the 0.02 px bar applies to converged points and
-        # the others are only required to stay within the window's reach.
-        conv = (o_st == OK) & stable
-        both = ok & conv
-        err = np.abs(g_out[both] - o_out[both]).max(initial=0.0)
-        assert err <= tol, err
-        osc = ok & (o_st == (OK | NONCONV)) & stable
-        if osc.any():
-            assert np.abs(g_out[osc] - o_out[osc]).max() <= 0.5
-    # validity everywhere: lost points report their input, OK points stay inside
-    lost = ~ok
-    np.testing.assert_array_equal(g_out[lost], np.asarray(pts, np.float32)[lost])
-    h, w = f0.shape
-    assert np.all(g_out[ok] >= 0) and np.all(g_out[ok, 0] <= w - 1) and np.all(g_out[ok, 1] <= h - 1)
-    assert set(np.unique(g_st)) <= {OK, OK | NONCONV, LOST_EIG, LOST_OOB}
-    return g_out, g_st, o_out, o_st
+    return gpu_pyramid(omt, frame, levels, storage)
 
 
 def test_lk_sd_pair_corners(omt, oracle):
     p = synth.sd_pair()
     pts, cnt = oracle.select_corners(p.frame0, p.boxes, 50)
     allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
-    compare(omt, oracle, p.frame0, p.frame1, allp)
+    compare(omt, oracle, p.frame0, p.frame1, allp, label="SD pair corners")
 
 
 def test_lk_fixed_iterations_all_points(omt, oracle):
@@ -146,6 +52,8 @@ def test_lk_fixed_iterations_all_points(omt, oracle):
                                                     eps=0.0, probe=True)
     band = np.any((o_me >= 0.9e-3) & (o_me <= 1.1e-3), axis=1)
     stable = ~unstable & ~band
+    print(f"fixed 10 iterations, 2000 random points: excluded by the conditioning probe "
+          f"{unstable.sum()}, in the tau guard band {band.sum()}")
     assert unstable.mean() <= 0.05
     assert np.all(g_st[stable] == o_st[stable])
     both = ((g_st & OK) > 0) & stable
@@ -172,7 +80,8 @@ def test_lk_window_and_level_sweep(omt, oracle, win, levels):
     f0 = synth.render_shift(tex, w, h)
     f1 = synth.render_shift(tex, w, h, 2.3, -1.7)
     pts = np.stack([rng.uniform(0, w - 1, 600), rng.uniform(0, h - 1, 600)], 1).astype(np.float32)
-    compare(omt, oracle, f0, f1, pts, win=win, levels=levels, min_ok=0.5, max_unstable=0.12)
+    compare(omt, oracle, f0, f1, pts, win=win, levels=levels, min_ok=0.5, max_unstable=0.12,
+            label=f"random points, win {win}, {levels} levels")
 
 
 def test_lk_borders_and_oob(omt, oracle):
@@ -183,7 +92,8 @@ def test_lk_borders_and_oob(omt, oracle):
     f1 = synth.render_shift(tex, w, h, 6.0, -5.0)
     pts = np.concatenate([np.stack([rng.uniform(0, w - 1, 300), rng.uniform(0, h - 1, 300)], 1),
                           np.array([[w - 1, 3], [w - 2.5, h - 1], [0, 0], [95, 79]])]).astype(np.float32)
-    compare(omt, oracle, f0, f1, pts, levels=2, win=11, min_ok=0.3, max_unstable=0.12)
+    compare(omt, oracle, f0, f1, pts, levels=2, win=11, min_ok=0.3, max_unstable=0.12,
+            label="borders")
 
 
 def test_lk_one_dimensional_texture_lost(omt):
@@ -245,34 +155,40 @@ def test_lk_batch_independence(omt):
             np.testing.assert_array_equal(a[sl], b)
 
 
-def test_lk_f16_storage_within_002(omt, oracle):
+def test_lk_f16_storage_sd_pair(omt, oracle):
+    # workload 1 (the SD pair, 3 levels, 21x21): the F16 path against the
+    # oracle on half-precision storage at the FP32 bar, and the cost of the
+    # storage against the FP64 oracle
     p = synth.sd_pair()
     pts, cnt = oracle.select_corners(p.frame0, p.boxes, 50)
     allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
-    compare(omt, oracle, p.frame0, p.frame1, allp, storage=1, tol=F16_TOL)
+    g_out, g_st, _, _ = compare(omt, oracle, p.frame0, p.frame1, allp, storage=1,
+                                label="SD pair corners")
+    o_out, o_st = oracle_lk(oracle, p.frame0, p.frame1, allp)[:2]
+    error_vs_fp64("SD pair, F16 storage", g_out, g_st, o_out, o_st, max_nonconv=0.05)
 
 
 def test_lk_4k_large_motion_sample(omt, oracle):
+    # workload 4 (3840x2160, 200 rigid regions moving up to 40 px and 3
+    # degrees, 5 levels, 31x31): 3,000 sampled corners
     pr = synth.rigid_pair()
     pts, cnt = oracle.select_corners(pr.frame0, pr.boxes, 250)
     allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
     rng = np.random.default_rng(1)
     sample = allp[rng.choice(len(allp), 3000, replace=False)]
     kw = dict(levels=5, win=31, max_iter=30, eps=0.01)
+    o_out, o_st = oracle_lk(oracle, pr.frame0, pr.frame1, sample, **kw)[:2]
     stats = {}
-    for storage, tol in ((0, FLOW_TOL), (1, F16_TOL)):
-        g_out, g_st, o_out, o_st = compare(omt, oracle, pr.frame0, pr.frame1, sample,
-                                           storage=storage, tol=tol, min_ok=0.5, **kw)
-        # error report against the FP64 oracle: points OK with the same status
-        both = ((g_st & OK) > 0) & (g_st == o_st)
-        e = np.hypot(*(g_out[both] - o_out[both]).T)
-        stats[storage] = (e.max(), np.percentile(e, 99), e.mean(), both.sum())
-        print(f"4K 31x31 5 levels, {'F16' if storage else 'F32'} storage: |error| max "
-              f"{e.max():.2e} px, p99 {np.percentile(e, 99):.2e}, mean {e.mean():.2e} "
-              f"over {both.sum()} points")
-    # storing the pyramid in half precision costs accuracy, never more than
-    # the FP16 bar on average
-    assert stats[1][2] >= stats[0][2] and stats[1][2] <= F16_TOL
+    for storage in (0, 1):
+        g_out, g_st, _, _ = compare(omt, oracle, pr.frame0, pr.frame1, sample, storage=storage,
+                                    min_ok=0.5, label="4K sample", **kw)
+        # against the FP64 oracle on unquantised pyramids; most NONCONV
+        # points straddle two regions that move differently (their window's
+        # translation model does not fit, the iteration oscillates)
+        name = f"4K sample, {'F16' if storage else 'F32'} storage"
+        stats[storage] = error_vs_fp64(name, g_out, g_st, o_out, o_st)
+    # storing the pyramid in half precision costs accuracy
+    assert stats[1]["mean"] >= stats[0]["mean"]
 
 
 # ------------------------------------------------------------------ boxes
@@ -374,15 +290,17 @@ def test_stream_tracker_sd_step(omt, oracle):
 
 
 def test_1080p_clip_trajectory_matches_oracle(omt, oracle):
-    # Section V-A loop on the 1080p affine clip: detections every 5th frame,
-    # prediction in between; GPU and oracle box trajectories must agree.
-    n = 8
+    # Section V-A loop on the whole 64-frame 1080p affine clip (workload 2):
+    # detections every 5th frame, prediction in between; GPU and oracle box
+    # trajectories must agree on every frame.
+    n = 64
     clip = synth.affine_clip(n_frames=n)
     params = omt.default_params(levels=4, max_corners=100)
     T = omt.StreamTracker(1920, 1080, params, max_boxes=16)
     T.prime(torch.from_numpy(clip.frames[0]).cuda())
     gb = clip.gt_boxes[0].astype(np.float32)
     ob = gb.copy()
+    worst = []
     for t in range(1, n):
         if (t - 1) % 5 == 0:
             gb = clip.gt_boxes[t - 1].astype(np.float32)
@@ -397,4 +315,7 @@ def test_1080p_clip_trajectory_matches_oracle(omt, oracle):
         off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
         ob, _ = oracle.update_boxes(ob, off, allp, o_out.astype(np.float32), o_st)
         ob = ob.astype(np.float32)
-        assert np.abs(gb - ob).max() <= 0.05, (t, np.abs(gb - ob).max())
+        worst.append(float(np.abs(gb - ob).max()))
+        assert worst[-1] <= 0.05, (t, worst[-1])
+    print(f"1080p clip, {n} frames: max box corner difference per frame: median "
+          f"{np.median(worst):.2e} px, max {max(worst):.2e}")

@@ -116,3 +116,61 @@ def test_matches_library_convolution(oracle, shape):
         else:
             break
         cur = nxt
+
+
+# --------------------------------------------------- half-precision storage
+# A pyramid stored in half precision keeps level 0 as the u8 frame, every
+# level L >= 1 as half(I - 128) computed from level L-1 as stored, and every
+# gradient plane as the half of the gradient of its stored level.
+
+def _half(v):
+    return v.astype(np.float16).astype(np.float64)
+
+
+@pytest.mark.parametrize("shape", [(41, 53), (64, 64), (9, 6)])
+def test_f16_storage_matches_library_convolution(oracle, shape):
+    rng = np.random.default_rng(12)
+    f = rng.integers(0, 256, shape, dtype=np.uint8)
+    levels = 4
+    P = oracle.Pyramid(f, levels, storage="f16")
+    k2 = np.outer(K5, K5) / 256.0
+    cur = f.astype(np.float64)
+    for L in range(levels):
+        np.testing.assert_array_equal(P.img[L], cur)
+        if min(cur.shape) >= 2:
+            gx = ndi.correlate(cur, SCHARR_X / 32.0, mode="mirror")
+            gy = ndi.correlate(cur, SCHARR_X.T / 32.0, mode="mirror")
+            np.testing.assert_array_equal(P.grad[L][..., 0], _half(gx))
+            np.testing.assert_array_equal(P.grad[L][..., 1], _half(gy))
+        if min(cur.shape) < 3 or L + 1 == levels:
+            break
+        cur = _half(ndi.correlate(cur, k2, mode="mirror")[::2, ::2] - 128.0) + 128.0
+
+
+def test_f16_storage_values_and_error_bound(oracle):
+    rng = np.random.default_rng(13)
+    f = rng.integers(0, 256, (57, 71), dtype=np.uint8)
+    levels = 5
+    H = oracle.Pyramid(f, levels, storage="f16")
+    D = oracle.Pyramid(f, levels)
+    np.testing.assert_array_equal(H.img[0], D.img[0])
+    for L in range(levels):
+        # every stored value is a half (levels >= 1 offset by 128)
+        if L:
+            assert np.all(_half(H.img[L] - 128.0) == H.img[L] - 128.0)
+        assert np.all(_half(H.grad[L]) == H.grad[L])
+        # the binomial reduction averages (non-negative weights summing to
+        # one), so each level adds at most half a half-ulp of |I - 128| <=
+        # 128 (2^-5) to the error of the one above; the gradient moves by at
+        # most the level's error (|Scharr| sums to one per axis) plus its
+        # own rounding (|I_x| <= 128)
+        e_img = np.abs(H.img[L] - D.img[L]).max()
+        assert e_img <= L * 2.0 ** -5, (L, e_img)
+        e_grad = np.abs(H.grad[L] - D.grad[L]).max()
+        assert e_grad <= L * 2.0 ** -5 + 2.0 ** -5, (L, e_grad)
+    # frames whose level-1 values need no more than a half's precision
+    # (|I - 128| < 8: the half grid there is 2^-8 or finer, and level-1
+    # values are multiples of 2^-8) give level 1 exactly
+    g = rng.integers(121, 136, (40, 48), dtype=np.uint8)
+    np.testing.assert_array_equal(oracle.Pyramid(g, 2, storage="f16").img[1],
+                                  oracle.Pyramid(g, 2).img[1])
