@@ -19,14 +19,24 @@
  *   - Points are float2 (x, y) in level-0 pixels.
  *   - Every pointer argument marked "device" must point to device memory of
  *     the current CUDA device.  The caller owns every buffer; the library
- *     never allocates or frees device memory.
+ *     never allocates or frees device memory.  One exception: the scratch
+ *     of omt_select_corners_static is a fixed array inside the library
+ *     (OMT_STATIC_SCRATCH_BYTES on every device that loads it).
  *   - Every call is asynchronous on the given stream (a cudaStream_t passed
  *     as void*, NULL = legacy default stream) with no host synchronisation.
  *   - Arguments are validated on the host before anything is launched; an
  *     invalid call returns OMT_EINVAL and launches nothing.  A failed launch
- *     returns OMT_ECUDA.  Kernels contain no waits and cannot hang.
+ *     returns OMT_ECUDA.
+ *   - The only device-side waits are the LK kernels' waits for their window
+ *     copies (omt_lk_track and the batched LK phase).  Each gives up after
+ *     one second; the points it concerns come back OMT_PT_LOST_TIMEOUT and
+ *     omt_lk_wait_timeouts reports OMT_ETIMEOUT.  No kernel can hang.
  *   - Calls on different streams may run concurrently from different host
- *     threads; the library keeps no mutable global state.
+ *     threads.  Mutable global state, all of it named here: the count of LK
+ *     waits that ran out (omt_lk_wait_timeouts), the LK test hook
+ *     (omt_debug_fail_lk_wait), a host cache of encoded TMA descriptors
+ *     (thread-safe, keyed by buffer address and shape), and the array of
+ *     omt_select_corners_static (calls of it must not overlap on the GPU).
  */
 #ifndef OMT_H
 #define OMT_H
@@ -45,7 +55,7 @@ enum omt_status {
     OMT_EINVAL = -1,   /* bad argument (checked on the host, nothing launched) */
     OMT_ENOMEM = -2,   /* a caller buffer is smaller than the call needs     */
     OMT_ECUDA = -3,    /* a CUDA launch or runtime call failed               */
-    OMT_ETIMEOUT = -4, /* reserved for bounded device waits                  */
+    OMT_ETIMEOUT = -4, /* a bounded device wait ran out (omt_lk_wait_timeouts) */
     OMT_ECHECK = -5    /* a device-side consistency check failed             */
 };
 
@@ -57,14 +67,17 @@ enum omt_storage {
 };
 
 /* Per-point status bits written by omt_lk_track (and LOST_FB by the
- * forward-backward check).  Exactly one of OK, LOST_EIG, LOST_OOB, LOST_FB
- * is set; NONCONV may accompany OK. */
+ * forward-backward check).  Exactly one of OK, LOST_EIG, LOST_OOB, LOST_FB,
+ * LOST_TIMEOUT is set; NONCONV may accompany OK. */
 enum omt_point_status {
     OMT_PT_OK = 1,       /* tracked                                            */
     OMT_PT_LOST_EIG = 2, /* lambda_min(G)/win^2 < min_eig (or <= 0) at a level */
     OMT_PT_LOST_OOB = 4, /* left the frame (see omt_lk_track)                  */
     OMT_PT_NONCONV = 8,  /* some level hit max_iter without converging (info)  */
-    OMT_PT_LOST_FB = 16  /* tracked, but the round trip back did not close     */
+    OMT_PT_LOST_FB = 16, /* tracked, but the round trip back did not close    */
+    OMT_PT_LOST_TIMEOUT = 32 /* not tracked: a window copy the kernel waited  */
+                             /* for did not land within one second (never in  */
+                             /* normal operation); reported as its input      */
 };
 
 #define OMT_MAX_LEVELS 8
@@ -193,9 +206,12 @@ int omt_select_corners(const omt_pyramid *pyr, const float *boxes, int32_t nboxe
  * omt_select_corners, minus the scratch: the scratch is one fixed array
  * (OMT_STATIC_SCRATCH_BYTES) inside the library.
  *   - Returns OMT_ENOMEM when omt_corner_scratch_bytes(w, h, nboxes,
- *     max_corners) exceeds OMT_STATIC_SCRATCH_BYTES (16 MiB: a 1920x1080
- *     frame with up to about 160,000 box-corner slots); the caller must then
- *     use omt_select_corners with its own scratch.
+ *     max_corners) exceeds OMT_STATIC_SCRATCH_BYTES (16 MiB).  The frame's
+ *     response map takes 4 bytes per pixel and each box-corner slot
+ *     (nboxes x max_corners) 8 more: a 1920x1080 frame leaves room for about
+ *     1.05 million slots (for example 1,000 boxes of 1,000 corners), a
+ *     3840x2160 frame for none; the caller must then use omt_select_corners
+ *     with its own scratch.
  *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  *     routine.
  *   - The first call on each device looks up the array's device address
@@ -504,12 +520,30 @@ int omt_update_tracks(const float *boxes_s, const uint8_t *active_s, int32_t ns,
 /* ---------------------------------------------------------------- misc */
 
 /* Synchronous (waits for the device).  *count receives the number of LK
- * window copies (omt_lk_track and the batched LK phase) whose completion
- * wait reached its time limit (one second) since the previous call, and the
- * count restarts at 0.  A copy lands in microseconds, so a non-zero count
- * means the copy engine stalled and the points tracked meanwhile may be
- * wrong.  OMT_EINVAL if count is NULL; OMT_ECUDA on a CUDA error. */
+ * window-copy waits (omt_lk_track and the batched LK phase, one per warp
+ * and wait) that reached their time limit (one second) since the previous
+ * call, and the count restarts at 0; returns OMT_ETIMEOUT when it is not 0,
+ * else OMT_OK.  A copy lands in microseconds, so a non-zero count means the
+ * copy engine stalled.  No point is computed from a window that did not
+ * land: the warp whose wait ran out stops copying and reading windows,
+ * waits (again at most a second) for its other copies, and reports every
+ * point it held OMT_PT_LOST_TIMEOUT at its input position with zero
+ * iterations (in the plain call, all its later points too; in the batched
+ * step, the rest of its queue chunk, after which it takes no more work; a
+ * point whose backward run was lost so becomes OMT_PT_LOST_TIMEOUT in the
+ * forward-backward check).  The count is process-global.  OMT_EINVAL if
+ * count is NULL; OMT_ECUDA on a CUDA error. */
 int omt_lk_wait_timeouts(uint32_t *count);
+
+/* Test hook of the wait-failure path (synchronous, current device): from
+ * now on, the point with index `point` -- in omt_lk_track its index in pts,
+ * in the batched LK phase its position in the step's work queue (the
+ * streams' points back to back in stream order) -- declares its first
+ * search-window copy 16 bytes larger than the copy delivers, so that its
+ * wait runs out after one second with every copy landed and the failure
+ * path above runs.  point = -1 (the initial state) turns it off.  The paper
+ * has no counterpart.  OMT_ECUDA on a CUDA error. */
+int omt_debug_fail_lk_wait(int64_t point);
 
 
 const char *omt_error_string(int32_t code);

@@ -9,7 +9,7 @@ using namespace omt;
 
 namespace {
 
-constexpr int32_t kVersion = 200;  // 0.2.0: omt_flow_params gained block
+constexpr int32_t kVersion = 300;  // 0.3.0: OMT_PT_LOST_TIMEOUT, omt_debug_fail_lk_wait
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -487,7 +487,12 @@ int omt_lk_wait_timeouts(uint32_t *count) {
     unsigned c = 0;
     const int r = from_cuda(lk_wait_timeouts_take(&c));
     *count = c;
-    return r;
+    if (r != OMT_OK) return r;
+    return c ? OMT_ETIMEOUT : OMT_OK;
+}
+
+int omt_debug_fail_lk_wait(int64_t point) {
+    return from_cuda(lk_fail_point_set(point < 0 ? -1 : (long long)point));
 }
 
 size_t omt_assign_workspace_bytes(int32_t na, int32_t nb) {

@@ -102,25 +102,37 @@ constexpr int BUF_SEARCH = 2;
 // nanoseconds) so that a stalled copy cannot hold the warp forever.
 constexpr unsigned long long FILL_WAIT_NS = 1000000000ull;
 
-// Fills that were not seen complete within FILL_WAIT_NS (read by
+// Waits that ran out FILL_WAIT_NS, one per warp and wait (read and reset by
 // omt_lk_wait_timeouts; zero unless the copy engine stalls).
 __device__ unsigned lk_wait_timeouts;
+
+// Test hook (omt_debug_fail_lk_wait): the point with this index (the plain
+// call's point index, the batched step's position in the work queue) has
+// its first search-region fill declared 16 bytes larger than its copies,
+// so that the wait for it runs out with every copy landed; -1 = off.
+__device__ long long lk_fail_point = -1;
+constexpr unsigned FAIL_EXTRA_BYTES = 16;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// Completion state of a warp's three staging buffers.
+// Completion state of a warp's three staging buffers.  After a wait runs
+// out (failed), a late copy may still land in that buffer: the warp then
+// issues no copy and reads no staged texel again, marks the points it
+// holds OMT_PT_LOST_TIMEOUT and takes no more work.
 struct Fills {
     uint64_t *bar;   // bar[b]: mbarrier of buffer b
     unsigned pend;   // bit b: a fill of buffer b is in flight
     unsigned phase;  // bit b: parity of buffer b's current phase
+    bool failed;     // a wait ran out (warp-uniform)
 };
 
 __device__ __forceinline__ void fills_init(Fills &f, unsigned *W_bar, int lane) {
     f.bar = (uint64_t *)W_bar;
     f.pend = 0;
     f.phase = 0;
+    f.failed = false;
     if (lane == 0) {
 #pragma unroll
         for (int b = 0; b < 3; ++b)
@@ -183,26 +195,37 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Wait (bounded) until buffer b's fill in flight, if any, has landed.
-__device__ __forceinline__ void fill_wait(Fills &f, int b) {
-    if (!((f.pend >> b) & 1u)) return;
+// Returns false, for the whole warp, when the wait ran out its limit: the
+// warp is then failed (Fills) and the buffer is never waited on again.
+__device__ __forceinline__ bool fill_wait(Fills &f, int b) {
+    if (!((f.pend >> b) & 1u)) return true;
     const unsigned a = smem_u32(f.bar + b), par = (f.phase >> b) & 1u;
+    bool late = false;
     if (!mbar_try_wait(a, par)) {
         const unsigned long long t0 = global_ns();
         while (!mbar_try_wait(a, par)) {
             if (global_ns() - t0 > FILL_WAIT_NS) {
-                atomicAdd(&lk_wait_timeouts, 1u);
+                late = true;
                 break;
             }
         }
     }
-    f.phase ^= 1u << b;
     f.pend &= ~(1u << b);
+    if (__any_sync(FULL_MASK, late)) {
+        if ((threadIdx.x & 31) == 0) atomicAdd(&lk_wait_timeouts, 1u);
+        f.failed = true;
+        return false;
+    }
+    f.phase ^= 1u << b;
+    return true;
 }
 
-__device__ __forceinline__ void fill_drain(Fills &f) {
-    fill_wait(f, 0);
-    fill_wait(f, 1);
-    fill_wait(f, BUF_SEARCH);
+// Land every fill in flight (each wait bounded); false if one ran out.
+__device__ __forceinline__ bool fill_drain(Fills &f) {
+    const bool a = fill_wait(f, 0);
+    const bool b = fill_wait(f, 1);
+    const bool c = fill_wait(f, BUF_SEARCH);
+    return a && b && c;
 }
 
 // The bytes of a row to copy for texel columns [x0, x0 + ncols) clamped to
@@ -323,7 +346,7 @@ __device__ __forceinline__ void issue_template(const LevelView &P, const CUtenso
 template <int ST, int WIN>
 __device__ __forceinline__ void copy_search(const LevelView &J, const CUtensorMap *tm, bool u8,
                                             int jx, int jy, int lane, unsigned *W, Fills &f,
-                                            LevelCopy &lc) {
+                                            LevelCopy &lc, unsigned extra = 0) {
     using D = Dims<ST, WIN>;
     const int esz = u8 ? 1 : D::ESZ;
     lc.sx0 = jx - D::R - MARGIN;
@@ -332,10 +355,10 @@ __device__ __forceinline__ void copy_search(const LevelView &J, const CUtensorMa
     lc.scol = ss.b0 >> esz_shift(esz);
     unsigned *S = W + D::UNION;
     if (fill_mode(tm, lc.sy0, D::SH, J.h) != VIA_ROWS) {
-        fill_begin(f, BUF_SEARCH, D::SH * 4 * D::RWJ, lane);
+        fill_begin(f, BUF_SEARCH, D::SH * 4 * D::RWJ + extra, lane);
         tensor_box(S, tm, lc.scol, lc.sy0, f.bar + BUF_SEARCH, lane);
     } else {
-        fill_begin(f, BUF_SEARCH, D::SH * ss.bytes, lane);
+        fill_begin(f, BUF_SEARCH, D::SH * ss.bytes + extra, lane);
         for (int r = lane; r < D::SH; r += 32) {
             const int64_t y = clampi(lc.sy0 + r, 0, J.h - 1);
             bulk_row(S + r * D::RWJ, J.img + y * J.img_pitch + ss.b0, ss.bytes, f.bar + BUF_SEARCH);
@@ -502,7 +525,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
                                            float eps2, float tau_n, int lane, bool u8,
                                            const CUtensorMap *tm, unsigned *W, Fills &f,
                                            Prefetch &pf, const NextTemplate &nx, float &nux,
-                                           float &nuy, int &k, bool &conv) {
+                                           float &nuy, int &k, bool &conv, bool force_fail) {
     using D = Dims<ST, WIN>;
     constexpr int R = D::R;
     const float fpx = floorf(px), fpy = floorf(py);
@@ -534,9 +557,11 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     if (c0_ok) {
         sjx = ipx + (int)floorf(c0x);
         sjy = ipy + (int)floorf(c0y);
-        copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, sjx, sjy, lane, W, f, lc);
+        copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, sjx, sjy, lane, W, f, lc,
+                             force_fail ? FAIL_EXTRA_BYTES : 0u);
     }
-    fill_wait(f, buf);   // the template has landed; the search may still run
+    // the template has landed; the search may still run
+    if (!fill_wait(f, buf)) return OMT_PT_LOST_TIMEOUT;
     if (fill_mode(tm, ipy - R, D::T, P.h) == VIA_TMA_EDGE) {
         __syncwarp();
         fix_rows<D::RWI>(W + buf * D::TRAW, ipy - R, D::T, P.h, lane);
@@ -572,7 +597,8 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
         pf.valid = true;
         pf.buf = 1 - buf;
     }
-    fill_wait(f, BUF_SEARCH);  // the search region has landed; the prefetch may still run
+    // the search region has landed; the prefetch may still run
+    if (!fill_wait(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
     if (c0_ok) search_edges<ST, WIN>(J, tm, W, lc, lane);
     __syncwarp();
     bool staged = c0_ok;
@@ -592,7 +618,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
             if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
                 __syncwarp();
                 copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, jx, jy, lane, W, f, lc);
-                fill_wait(f, BUF_SEARCH);
+                if (!fill_wait(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
                 search_edges<ST, WIN>(J, tm, W, lc, lane);
                 __syncwarp();
                 sjx = jx;
@@ -627,6 +653,17 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
 // The whole pyramidal iteration for one point u (the whole warp); P, J are
 // the frame-t and frame-(t+1) level views.  Writes pts_out / status / iters
 // entry i.
+// A point the warp holds but cannot track because one of its waits ran out
+// (Fills): reported at its input position, no iterations.
+__device__ __forceinline__ void lost_timeout(float2 u, int i, float2 *out, uint8_t *status,
+                                             uint8_t *iters, int levels, int lane) {
+    if (lane == 0) {
+        out[i] = u;
+        status[i] = (uint8_t)OMT_PT_LOST_TIMEOUT;
+    }
+    if (iters && lane < levels) iters[(int64_t)i * levels + lane] = 0;
+}
+
 template <int ST, int WIN>
 __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
                                          int max_iter, float eps2, float tau_n, float2 u,
@@ -634,8 +671,12 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
                                          const CUtensorMap *tm, unsigned *W, Fills &f,
                                          Prefetch &pf, bool has_next, float2 u_next,
                                          const LevelView *P_next_point,
-                                         const CUtensorMap *tm_next) {
+                                         const CUtensorMap *tm_next, bool force_fail) {
     const int lane = threadIdx.x & 31;
+    if (f.failed) {
+        lost_timeout(u, i, out, status, iters, levels, lane);
+        return;
+    }
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     int st = OMT_PT_OK;
     bool nonconv = false;
@@ -680,7 +721,14 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         bool conv;
         st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
                                   lane, L == 0, level_maps(tm, L), W, f, pf, nx, nux, nuy,
-                                  k, conv);
+                                  k, conv, force_fail && L == levels - 1);
+        if (st == OMT_PT_LOST_TIMEOUT) {
+            // land what else is in flight (bounded), then give the point up
+            fill_drain(f);
+            pf.valid = false;
+            lost_timeout(u, i, out, status, iters, levels, lane);
+            return;
+        }
         itp |= (unsigned long long)k << (8 * L);
         if (st != OMT_PT_OK) break;
         if (!conv) nonconv = true;
@@ -723,6 +771,10 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
 __device__ __forceinline__ void fb_apply(float2 u, float2 u_back, uint8_t status_back,
                                          float fb_max, uint8_t &status) {
     if (!(status & OMT_PT_OK)) return;
+    if (status_back & OMT_PT_LOST_TIMEOUT) {   // the backward run was not made
+        status = (uint8_t)OMT_PT_LOST_TIMEOUT;
+        return;
+    }
     const float dx = u_back.x - u.x, dy = u_back.y - u.y;
     const bool closes = (status_back & OMT_PT_OK) && sqrtf(fmaf(dx, dx, dy * dy)) <= fb_max;
     if (!closes) status = (uint8_t)OMT_PT_LOST_FB;
@@ -755,7 +807,7 @@ constexpr size_t stage_bytes(int warps = LK_WARPS) {
 }
 
 template <int ST, int WIN>
-__global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ LKArgs a) {
+__global__ void __launch_bounds__(LK_MAX_NT, 2) lk_kernel(const __grid_constant__ LKArgs a) {
     unsigned *W = warp_words<ST, WIN>();
     int n = a.n_max;
     if (a.n_dev) {
@@ -766,14 +818,16 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
     Fills f;
     fills_init(f, W + Dims<ST, WIN>::BAR, threadIdx.x & 31);
     const CUtensorMap *tm = all_maps(a.tm_ok, a.levels) ? a.tm : nullptr;
+    const long long fail_at = lk_fail_point;
     Prefetch pf;
     pf.valid = false;
+    // a warp whose wait ran out marks its remaining points (lk_point)
     for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
         const int nxt = i + nwarps;
         const bool has_next = nxt < n;
         const float2 un = has_next ? a.pts[nxt] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters, tm, W, f, pf, has_next, un, a.P, tm);
+                          a.status, a.iters, tm, W, f, pf, has_next, un, a.P, tm, i == fail_at);
     }
     fill_drain(f);
 }
@@ -786,7 +840,7 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
 // before the last point of the current one, whose finest level then
 // prefetches the next point's top-level template.
 template <int ST, int WIN, bool backward>
-__global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *table, int chunk) {
+__global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *table, int chunk) {
     __shared__ int32_t pre[OMT_BATCH_MAX_STREAMS + 1];
     unsigned *W = warp_words<ST, WIN>();
     const BatchView t(table);
@@ -816,6 +870,7 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *tabl
     };
     Fills f;
     fills_init(f, W + Dims<ST, WIN>::BAR, lane);
+    const long long fail_at = lk_fail_point;
     Prefetch pf;
     pf.valid = false;
     int g = take(), end = g + chunk;
@@ -841,9 +896,30 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_batch_kernel(const uint8_t *tabl
                           backward ? e.pts_back : e.pts_out, backward ? e.status_back : e.status,
                           backward ? nullptr : e.iters, stream_maps(t, s, h.levels, backward), W,
                           f, pf, has_next, un, backward ? en.P_next : en.P,
-                          stream_maps(t, sn, h.levels, backward));
+                          stream_maps(t, sn, h.levels, backward), g == fail_at);
         if constexpr (backward) {
             if (lane == 0) fb_apply(e.pts[i], e.pts_back[i], e.status_back[i], h.fb_max, e.status[i]);
+        }
+        if (f.failed) {
+            // a wait ran out: the points this warp holds (the rest of its
+            // chunk, or the chunk it took next) are given up, and it takes
+            // no more work
+            const int stop = end < total ? end : total;
+            for (int q = gn; q < stop; ++q) {
+                const int sq = find_segment(pre, ns, q);
+                const StreamEntry &eq = t.stream(sq);
+                const int iq = q - pre[sq];
+                if constexpr (backward) {
+                    lost_timeout(eq.pts_out[iq], iq, eq.pts_back, eq.status_back, nullptr,
+                                 h.levels, lane);
+                    if (lane == 0)
+                        fb_apply(eq.pts[iq], eq.pts_back[iq], eq.status_back[iq], h.fb_max,
+                                 eq.status[iq]);
+                } else {
+                    lost_timeout(eq.pts[iq], iq, eq.pts_out, eq.status, eq.iters, h.levels, lane);
+                }
+            }
+            break;
         }
         g = gn;
         s = sn;
@@ -1030,6 +1106,10 @@ uint32_t encode_st(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensor
 uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensorMap *out) {
     if (P.storage == OMT_F32) return encode_st<OMT_F32>(P, J, win, out);
     return encode_st<OMT_F16>(P, J, win, out);
+}
+
+cudaError_t lk_fail_point_set(long long point) {
+    return cudaMemcpyToSymbol(lk_fail_point, &point, sizeof(point));
 }
 
 cudaError_t lk_wait_timeouts_take(unsigned *count) {

@@ -221,6 +221,7 @@ uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUt
 
 // Reads and clears the count of LK staging waits that hit their limit.
 cudaError_t lk_wait_timeouts_take(unsigned *count);
+cudaError_t lk_fail_point_set(long long point);
 
 // backward = 0: the LK phase (frame t -> t+1); 1: the backward run of the
 // forward-backward check (frame t+1 -> t from the forward results), each

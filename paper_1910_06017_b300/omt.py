@@ -13,7 +13,7 @@ from ctypes import POINTER, Structure, c_float, c_int32, c_int64, c_size_t, c_ui
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libomt.so")
-ABI_VERSION = 200   # the library version whose structure layouts this binding mirrors
+ABI_VERSION = 300   # the library version whose structure layouts this binding mirrors
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECHECK = 0, -1, -2, -3, -4, -5
 F32, F16 = 0, 1
@@ -30,10 +30,10 @@ EXPORTED = [
     "omt_assign_workspace_bytes", "omt_assign", "omt_update_tracks", "omt_lk_wait_timeouts",
     "omt_fb_check", "omt_default_flow_params", "omt_structure_texture_scratch_bytes",
     "omt_tvl1_scratch_bytes", "omt_structure_texture", "omt_tvl1_flow", "omt_box_mean_flow",
-    "omt_working_level", "omt_level_u8", "omt_scale_boxes",
+    "omt_working_level", "omt_level_u8", "omt_scale_boxes", "omt_debug_fail_lk_wait",
 ]
 PHASE_PYRAMID, PHASE_CORNERS, PHASE_LK, PHASE_BOXES, PHASE_FB = 0, 1, 2, 3, 4
-PT_OK, PT_LOST_EIG, PT_LOST_OOB, PT_NONCONV, PT_LOST_FB = 1, 2, 4, 8, 16
+PT_OK, PT_LOST_EIG, PT_LOST_OOB, PT_NONCONV, PT_LOST_FB, PT_LOST_TIMEOUT = 1, 2, 4, 8, 16, 32
 BATCH_MAX_STREAMS = 256
 STATIC_SCRATCH_BYTES = 16 << 20
 
@@ -134,6 +134,7 @@ def lib():
         L.omt_update_tracks.argtypes = [c_void_p, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p]
         L.omt_lk_wait_timeouts.argtypes = [c_void_p]
+        L.omt_debug_fail_lk_wait.argtypes = [c_int64]
         L.omt_default_flow_params.argtypes = [POINTER(FlowParams)]
         L.omt_working_level.argtypes = [c_int32, c_int32]
         L.omt_working_level.restype = c_int32
@@ -413,11 +414,21 @@ def update_tracks(boxes_s, active_s, boxes_d, match_s, match_d):
 
 
 def lk_wait_timeouts() -> int:
-    """LK window copies whose completion wait reached its time limit since
-    the previous call (0 unless the copy engine stalled)."""
+    """LK window-copy waits that reached their time limit since the previous
+    call (0 unless the copy engine stalled; the points concerned came back
+    PT_LOST_TIMEOUT).  The C call returns OMT_ETIMEOUT when the count is not
+    0; here the count is the answer."""
     c = ctypes.c_uint32(0)
-    _check(lib().omt_lk_wait_timeouts(ctypes.byref(c)), "omt_lk_wait_timeouts")
+    rc = lib().omt_lk_wait_timeouts(ctypes.byref(c))
+    if rc != ETIMEOUT:
+        _check(rc, "omt_lk_wait_timeouts")
     return int(c.value)
+
+
+def debug_fail_lk_wait(point: int) -> None:
+    """Test hook: make the wait for the first search window of LK point
+    `point` run out (omt_debug_fail_lk_wait); -1 turns it off."""
+    _check(lib().omt_debug_fail_lk_wait(int(point)), "omt_debug_fail_lk_wait")
 
 
 def match_and_update(pred, active, dets, iou_min: float = 0.0, stream=None):

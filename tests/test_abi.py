@@ -308,4 +308,4 @@ def test_working_level_arguments_rejected_before_launch():
 def test_library_version_matches_the_binding():
     # the binding's ctypes structures mirror one library version's layouts;
     # loading another version raises instead of misreading a structure
-    assert omt.lib().omt_version() == omt.ABI_VERSION == 200
+    assert omt.lib().omt_version() == omt.ABI_VERSION == 300

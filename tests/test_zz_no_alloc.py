@@ -111,3 +111,17 @@ def test_static_rejects_frames_beyond_its_array(omt):
     rc, pts, off = _static_abi(omt, P, prm, b)
     assert rc == omt.ENOMEM
     assert np.all(off == -1)  # nothing was launched
+
+
+def test_static_capacity_at_1080p(omt):
+    # a 1920x1080 frame leaves the array room for about 1.05 million
+    # box-corner slots: 1,000 boxes of 1,000 corners fit, 1,100 do not
+    assert omt.corner_scratch_bytes(1920, 1080, 1000, 1000) <= omt.STATIC_SCRATCH_BYTES
+    assert omt.corner_scratch_bytes(1920, 1080, 1100, 1000) > omt.STATIC_SCRATCH_BYTES
+    clip = synth.affine_clip(n_frames=1)
+    rng = np.random.default_rng(8)
+    boxes = synth.uniform_boxes(rng, 1920, 1080, 1000)
+    P, prm, b = _case(omt, clip.frames[0], boxes, 1000)
+    rc, pts, off = _static_abi(omt, P, prm, b)
+    assert rc == omt.OK
+    _same((pts, off), _with_scratch(omt, P, prm, b))
