@@ -17,8 +17,18 @@ stream and step) on the same streams, the ratio of the two, stream-frames/s
 and per-step latency percentiles.  `e2e` copies every step's frames host ->
 device from pinned memory and reads every box back.
 
+Beside the step: `served` runs the serving loop (workload 5: 64 streams of
+mixed resolution, Poisson arrivals, 40 GB admission budget) and searches the
+highest arrival rate each path serves with p99 frame latency <= 40 ms, for
+the batched FP16 path and the plain per-stream FP32 path; `roofline` divides
+the LK kernel's algorithmic flops by a measured FP32 multiply-add peak
+(probe/fma_peak.cu, timed in the same run); `cpu_baseline` times the FP64
+oracle on the host cores, one thread and all, on workloads 1-4.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl omt|reference]
                     [--storage f16|f32] [--streams S] [--no-graph] [--no-tune]
+                    [--no-serve] [--no-cpu-baseline]
+    python bench.py --flow | --match | --overlap | --working-level
 """
 from __future__ import annotations
 
@@ -100,13 +110,14 @@ class Clocks:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
+        import tempfile
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="omt_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -138,6 +149,10 @@ class Clocks:
             for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
@@ -217,6 +232,69 @@ def measure_plain(omt, torch, streams, dev, steps, warmup):
         ok += int(((T.status[:n].cpu().numpy() & 1) > 0).sum())
     del trackers
     return a.elapsed_time(b) / steps, ok
+
+
+def measure_fp32_peak(local: int):
+    """Measured FP32 multiply-add throughput of this GPU (TFLOP/s): the
+    faster of scalar and packed chains (probe/fma_peak.cu), each launch about
+    0.1 s, with the SM clock sampled meanwhile."""
+    import ctypes
+    import torch
+    from paper_1910_06017_b300 import build as bld
+    L = ctypes.CDLL(bld.build_probe())
+    L.omt_probe_fma_tflops.restype = ctypes.c_double
+    L.omt_probe_fma_tflops.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_float)]
+    sink = torch.empty(SMS * 8 * 256 * 4, dtype=torch.float32, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    res = {}
+    for packed in (0, 1):
+        ms = ctypes.c_float(0.0)
+        best = 0.0
+        for _ in range(3):
+            t = L.omt_probe_fma_tflops(packed, 30000, ctypes.c_void_p(sink.data_ptr()),
+                                       ctypes.byref(ms))
+            best = max(best, t)
+        res["packed" if packed else "scalar"] = {"tflops": best, "ms": float(ms.value)}
+    clk = clocks.stop()
+    peak = max(v["tflops"] for v in res.values())
+    return peak, {"probe": "probe/fma_peak.cu: 8 independent FMA chains per thread, 8 CTAs of 256 "
+                           "threads per SM, CUDA events, best of 3", **res, "clocks": clk}
+
+
+def served(args, local):
+    """Capacity of the serving loop (workload 5) for both paths: the highest
+    common scale of the 25-60 fps arrival rates served completely with p99
+    frame latency <= 40 ms (serve.capacity: doubling/halving, then three
+    geometric bisections; 2 s of arrivals per probe)."""
+    import torch
+    from paper_1910_06017_b300 import omt, serve
+    out = {"metric": "stream frames/s at p99 frame latency <= 40 ms",
+           "workload": "64 streams {720x576,1920x1080,3840x2160}, Poisson 25-60 fps x scale, "
+                       "20-300 boxes refreshed every 5-15 frames, <= 50 corners/box, 4 levels, "
+                       "21x21, 40 GB admission budget; latency = arrival -> boxes ready, "
+                       "frames copied from page-locked host memory inside it"}
+    budget = 40 << 30
+    for label, plain in (("batched_f16", False), ("plain_f32", True)):
+        storage = omt.F32 if plain else omt.F16
+        params = omt.default_params(levels=4, win=21, max_corners=50, storage=storage)
+        specs, frames, det = serve.build_workload(2, 0.5)
+        serve.serve(specs, frames, det, params, budget, plain=plain, deadline=0.5)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, probes = serve.capacity(64, params, plain, budget, p99_ms=40.0, duration=args.serve_s,
+                                      bisect=3)
+        out[label] = {"stream_frames_per_s": best["stream_frames_per_s"] if best else 0.0,
+                      "latency_ms_p50": best["latency_ms_p50"] if best else None,
+                      "latency_ms_p99": best["latency_ms_p99"] if best else None,
+                      "rate_scale": best["fps_scale"] if best else None,
+                      "probes": probes, "search_s": round(time.perf_counter() - t0, 1)}
+        torch.cuda.empty_cache()
+    b, p = out["batched_f16"]["stream_frames_per_s"], out["plain_f32"]["stream_frames_per_s"]
+    out["ratio_batched_over_plain"] = b / p if p else None
+    return out
 
 
 def run_omt(args, ws, rank, local):
@@ -321,9 +399,9 @@ def run_omt(args, ws, rank, local):
     value = ok_total / (ms_step * 1e-3)
     plain_value = plain_ok_total / (plain_ms * 1e-3)
     pk, pk_src = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2032.0)
-    fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    fp32_peak, fp32_probe = measure_fp32_peak(local)
     achieved = flops / (lk_ms * 1e-3) / 1e12
+    serve_res = served(args, local) if args.serve and rank == 0 else None
     lk_tr = dram_traffic("lk_batch_kernel")
     pyr_tr = dram_traffic("pyramid_batch_kernel")
     level0_px = sum(w * h for w, h in (sp.size for sp in streams))
@@ -354,7 +432,9 @@ def run_omt(args, ws, rank, local):
                      # DRAM bytes of one launch on this workload (ncu capture of the
                      # same kernel source; see profiles/traffic.json)
                      "traffic": lk_tr["bytes_per_launch"] if lk_tr else None,
-                     "peak_source": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz ({pk_src} max clock)",
+                     "peak_source": "measured in this run (FP32 multiply-add probe, of measured)",
+                     "peak_probe": fp32_probe,
+                     "nominal_tflops": SMS * FP32_LANES * 2 * pk.get("sm_max_mhz", 2032.0) / 1e6,
                      "lk_ms_per_step": lk_ms, "lk_share": lk_ms / ms_step},
         "roofline_pyramid": {"kernel": "pyramid_batch_kernel (all levels)", "bound": "hbm",
                              "achieved": pyr_bytes / (pyr_ms * 1e-3) / 1e9,
@@ -367,6 +447,7 @@ def run_omt(args, ws, rank, local):
                              "ms_per_step": pyr_ms},
         "clocks": clk,
         "gpu_launches": (LEVELS + 5) * args.steps,
+        **({"served": serve_res} if serve_res else {}),
     }
 
 
@@ -564,10 +645,228 @@ def run_flow_reference(args):
                       "pyramid, 4-level flow, box means), time x16 by area"}
 
 
+# ------------------------------------------------- beyond the hot path
+def run_match(args):
+    """The matching phase (Section V-A) at serving sizes: for n predicted
+    boxes of a 1920x1080 frame against n detections (the predictions
+    jittered, 10 % replaced), the device IoU matrix (CUDA events), its copy
+    to page-locked host memory, the host assignment and the update (wall
+    clock).  One JSON line per size."""
+    import torch
+    from paper_1910_06017_b300 import omt
+    rng = np.random.default_rng(20191006)
+    for n in (50, 300, 1000):
+        x0, y0 = rng.uniform(0, 1800, n), rng.uniform(0, 960, n)
+        w, h = rng.uniform(40, 150, n), rng.uniform(40, 150, n)
+        pred = np.stack([x0, y0, x0 + w, y0 + h], 1).astype(np.float32)
+        dets = pred + rng.normal(0, 4, pred.shape).astype(np.float32)
+        drop = rng.uniform(0, 1, n) < 0.1
+        dets[drop] = np.stack([x0[drop][::-1], y0[drop], x0[drop][::-1] + 60, y0[drop] + 60], 1)
+        active = np.ones(n, np.uint8)
+        pd, dd = torch.from_numpy(pred).cuda(), torch.from_numpy(dets).cuda()
+        iou = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            omt.iou_matrix(pd, dd, iou)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record()
+        for _ in range(reps):
+            omt.iou_matrix(pd, dd, iou)
+        e1.record()
+        torch.cuda.synchronize()
+        iou_ms = e0.elapsed_time(e1) / reps
+        host = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        t0 = time.perf_counter()
+        host.copy_(iou)
+        m = host.numpy()
+        t1 = time.perf_counter()
+        ma, mb = omt.assign(m, active)
+        t2 = time.perf_counter()
+        omt.update_tracks(pred, active, dets, ma, mb)
+        t3 = time.perf_counter()
+        print(json.dumps({"tracks": n, "detections": n, "iou_matrix_ms": round(iou_ms, 4),
+                          "copy_ms": round(1e3 * (t1 - t0), 3), "assign_ms": round(1e3 * (t2 - t1), 3),
+                          "update_ms": round(1e3 * (t3 - t2), 3), "matched": int((ma >= 0).sum())}))
+
+
+def run_overlap(args):
+    """Detection and tracking on one GPU at once (Section V-B runs the motion
+    field and the detector concurrently).  The detector is a stub (YoloV3 and
+    its weights are out of scope): per step, for every stream's frame, a
+    chain of bf16 GEMMs of 4096 x 1024 x 1024 through torch (cuBLAS) on a
+    CUDA stream of its own, 110 GFLOP per frame (about the two detector
+    models).  The tracker is the batched step of the 32-stream workload (CUDA
+    graph).  Median over the steps of CUDA events around tracking alone,
+    detection alone and both issued every step on their two streams, also
+    with the LK launch held to 2 CTAs per SM.  One JSON line."""
+    import torch
+    from paper_1910_06017_b300 import omt, synth
+    dev = torch.device("cuda", 0)
+    n_streams, gflop = args.streams, 110.0
+    streams = [synth.stream_pair(s) for s in range(n_streams)]
+    caps = [cap_of(sp) for sp in streams]
+    prm = params_for(omt, omt.F16, max(caps))
+    B = omt.BatchTracker([sp.size for sp in streams], prm, max_boxes=[len(sp.boxes) for sp in streams],
+                         max_corners=caps, device=dev)
+    for s, sp in enumerate(streams):
+        B.prime(s, torch.from_numpy(sp.frame0).to(dev))
+        B.frame[s][0].copy_(torch.from_numpy(sp.frame1))
+        B.frame[s][1].copy_(torch.from_numpy(sp.frame0))
+        B.set_boxes(s, torch.from_numpy(sp.boxes))
+    B.pack()
+    m, k, n = 4096, 1024, 1024
+    n_gemm = max(1, int(round(gflop * n_streams / (2.0 * m * k * n / 1e9))))
+    a = torch.randn(m, k, dtype=torch.bfloat16, device=dev)
+    w = [torch.randn(k, n, dtype=torch.bfloat16, device=dev) for _ in range(4)]
+    out = torch.empty(m, n, dtype=torch.bfloat16, device=dev)
+    det = torch.cuda.Stream(device=dev)
+    trk = torch.cuda.current_stream(dev)
+
+    def detect():
+        with torch.cuda.stream(det):
+            for i in range(n_gemm):
+                torch.matmul(a, w[i % 4], out=out)
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(trk)
+            det.wait_stream(trk)
+            fn()
+            trk.wait_stream(det)
+            e1.record(trk)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    res = {}
+    for label, ctas in (("default", 0), ("lk_2_ctas_per_sm", 2)):
+        B.caps.lk_ctas_per_sm = ctas
+        B.capture()
+        for _ in range(3):
+            B.step()
+            detect()
+        track_ms = timed(B.step, args.steps)
+        det_ms = timed(detect, args.steps)
+        both_ms = timed(lambda: (detect(), B.step()), args.steps)
+        res[label] = {"track_ms": track_ms, "detect_ms": det_ms, "both_ms": both_ms,
+                      "saved_ms": track_ms + det_ms - both_ms,
+                      "saved_frac_of_serial": (track_ms + det_ms - both_ms) / (track_ms + det_ms)}
+    print(json.dumps({"workload": f"{n_streams} streams (bench workload) + stub detector "
+                                  f"{gflop} GFLOP/frame ({n_gemm} bf16 GEMMs {m}x{k}x{n} per step)",
+                      **res}))
+
+
+def run_working_level(args):
+    """Tracking on the working level (Section V-A preprocessing: a pyramid
+    level chosen by resolution is processed).  For the 3840x2160 pair with
+    200 rigid regions and a 1920x1080 stream: the plain path's step time on
+    level 0 and on the working level (CUDA events, mean of 20 steps, frames
+    alternating) and, for the 4K pair, the median distance between each
+    box's move and its region's true translation.  One JSON line."""
+    import torch
+    from paper_1910_06017_b300 import omt, synth
+    dev = torch.device("cuda", 0)
+    res = {}
+    pr = synth.rigid_pair()
+    sp = synth.stream_pair(0, workload=13)
+    cases = [("3840x2160 rigid, 200 boxes", pr.frame0, pr.frame1, pr.boxes, pr.motions[:, :2], 250),
+             ("1920x1080 stream, 64 boxes", sp.frame0, sp.frame1, sp.boxes, None, 100)]
+    for name, f0, f1, boxes, truth, maxc in cases:
+        h, w = f0.shape
+        frames = [torch.from_numpy(f).to(dev) for f in (f0, f1)]
+        b = torch.from_numpy(np.ascontiguousarray(boxes, np.float32)).to(dev)
+        entry = {}
+        for label, level in (("level0", 0), ("working", None)):
+            params = omt.default_params(levels=4, win=21, max_corners=maxc, min_dist=3.0)
+            T = omt.WorkingLevelTracker(w, h, params, len(boxes), level=level, device=dev)
+            T.prime(frames[0])
+            moved = (T.step(frames[1], b).cpu().numpy() - boxes)[:, :2]
+            for k in range(3):
+                T.step(frames[k & 1], b)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            steps = 20
+            for k in range(steps):
+                T.step(frames[k & 1], b)
+            e1.record()
+            torch.cuda.synchronize()
+            entry[label] = {"level": T.level, "ms_per_step": e0.elapsed_time(e1) / steps}
+            if truth is not None:
+                entry[label]["median_box_error_px"] = float(np.median(np.hypot(*(moved - truth).T)))
+        res[name] = entry
+    print(json.dumps(res))
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def oracle_legs():
+    """The FP64 oracle, as it stands, on workloads 1, 2 and 4, with its LK
+    on one thread and on every core it may use (OpenMP over points; the
+    pyramids, corners and box update run on one thread in both): per leg the
+    seconds of the whole per-frame path over the sample and the OK points
+    per second of its LK step."""
+    from oracle import oracle as O
+    from paper_1910_06017_b300 import synth
+    O.lib()
+    cases = []
+    p = synth.sd_pair()
+    cases.append(("workload 1: 720x576 pair, 10 boxes, <= 50 corners, 3 levels, 21x21",
+                  p.frame0, p.frame1, p.boxes, 50, 3, 21, None))
+    clip = synth.affine_clip(n_frames=2)
+    cases.append(("workload 2: 1920x1080 clip frames 0 -> 1, 16 boxes, <= 100 corners, 4 levels, "
+                  "21x21", clip.frames[0], clip.frames[1], clip.gt_boxes[0], 100, 4, 21, None))
+    pr = synth.rigid_pair()
+    cases.append(("workload 4: 3840x2160 pair, 200 boxes, <= 250 corners, 5 levels, 31x31; LK on "
+                  "a seeded 2,000-corner sample", pr.frame0, pr.frame1, pr.boxes, 250, 5, 31, 2000))
+    legs = []
+    for name, f0, f1, boxes, cap, levels, win, sample in cases:
+        for threads in (1, 0):
+            t0 = time.perf_counter()
+            P0, P1 = O.Pyramid(f0, levels), O.Pyramid(f1, levels)
+            pts, cnt = O.select_corners(f0, boxes, cap)
+            allp = np.concatenate([pts[i, :cnt[i]] for i in range(len(cnt))])
+            off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+            ub = boxes
+            if sample:
+                rng = np.random.default_rng(20191006 + 4)
+                allp = allp[np.sort(rng.choice(len(allp), min(sample, len(allp)), replace=False))]
+                off = np.array([0, len(allp)], np.int32)
+                ub = np.array([[0, 0, f0.shape[1], f0.shape[0]]], np.float32)
+            t1 = time.perf_counter()
+            out, st = O.lk_track(P0, P1, allp, win=win, nthreads=threads)
+            t2 = time.perf_counter()
+            O.update_boxes(ub, off, allp, out.astype(np.float32), st)
+            t3 = time.perf_counter()
+            ok = int(((st & 1) > 0).sum())
+            legs.append({"workload": name, "threads": threads or O.max_threads(),
+                         "path_s": round(t3 - t0, 3), "lk_s": round(t2 - t1, 3), "ok_points": ok,
+                         "lk_points_per_s": ok / (t2 - t1)})
+    return legs
+
+
 def cpu_baseline_sample():
     class A:
         steps, warmup = 1, 0
-    return run_reference(A, 1, 0)["cpu_baseline"]
+    cb = run_reference(A, 1, 0)["cpu_baseline"]
+    cb["cpu_model"] = cpu_model()
+    cb["affinity_cores"] = len(os.sched_getaffinity(0))
+    cb["legs"] = oracle_legs()
+    return cb
 
 
 def main():
@@ -582,6 +881,15 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="keep the default LK launch shape instead of autotuning it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", dest="serve", action="store_false",
+                    help="skip the serving-loop capacity search (served)")
+    ap.add_argument("--serve-s", type=float, default=2.0,
+                    help="seconds of arrivals per probe of the capacity search")
+    ap.add_argument("--match", action="store_true", help="time the matching phase (IoU + assignment)")
+    ap.add_argument("--overlap", action="store_true",
+                    help="tracking and a stub detector on two CUDA streams (Section V-B)")
+    ap.add_argument("--working-level", action="store_true",
+                    help="tracking on the working level chosen by resolution")
     ap.add_argument("--flow", action="store_true",
                     help="the dense flow engine (TV-L1) on 1920x1080 frames instead of the tracker")
     ap.add_argument("--fb", type=float, default=None, metavar="MAX",
@@ -590,6 +898,12 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "omt":
         args.warmup = max(args.warmup, 3)
+    for flag, fn in (("match", run_match), ("overlap", run_overlap),
+                     ("working_level", run_working_level)):
+        if getattr(args, flag):
+            if rank == 0:
+                fn(args)
+            return
     if args.flow:
         if rank != 0:
             return

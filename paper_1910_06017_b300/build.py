@@ -1,7 +1,8 @@
 """Builds libomt.so, the CUDA library of the tracking hot path, in-tree.
 
 nvcc compiles every csrc/*.cu for sm_103a (B300) only; the objects are
-linked into paper_1910_06017_b300/libomt.so.  Usage:
+linked into paper_1910_06017_b300/libomt.so.  probe/fma_peak.cu becomes
+probe/libomt_probe.so, the benchmark's FP32 throughput probe.  Usage:
     python -m paper_1910_06017_b300.build [--force]
 """
 from __future__ import annotations
@@ -48,7 +49,22 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
+PROBE_SRC = os.path.join(PKG, "probe", "fma_peak.cu")
+PROBE_LIB = os.path.join(PKG, "probe", "libomt_probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """libomt_probe.so: the FP32 multiply-add throughput probe the benchmark
+    uses as the LK kernel's roofline (not part of the tracking library)."""
+    if force or not os.path.exists(PROBE_LIB) or os.path.getmtime(PROBE_LIB) < os.path.getmtime(PROBE_SRC):
+        tmp = PROBE_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([NVCC, *ARCH, *FLAGS, "-shared", "-o", tmp, PROBE_SRC, "-lcudart"])
+        os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+    build_probe(force)
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
