@@ -338,7 +338,8 @@ int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt
                 lw = (lw + 1) >> 1;
                 lh = (lh + 1) >> 1;
             }
-            return from_cuda(launch_pyramid_batch(dt, prm->levels, prm->storage, max_tiles, s));
+            return from_cuda(launch_pyramid_batch(dt, prm->levels, prm->storage, max_tiles,
+                                                  caps->max_streams, s));
         }
         case OMT_PHASE_CORNERS:
             return from_cuda(launch_corners_batch(

@@ -5,14 +5,15 @@
 // walks the (win+1) texel rows of its window: each lane loads the texel of
 // its column, takes the right neighbour from lane c+1 with a shuffle, and
 // interpolates horizontally, then vertically reusing the previous row.  The
-// frame-t window keeps only (Ix, Iy) per tap in registers (its rows are
-// loaded in batches of 8); b = sum (I - J) grad I is formed as
-// c - sum J grad I with the level constant c = sum I grad I, so an iteration
-// reads one frame-(t+1) texel per lane and row.  The sums of b (and of G, c)
-// are warp butterfly reductions.
-// All lanes end with identical sums, so the control flow stays uniform, and
-// the reduction order is fixed: a point's result does not depend on the
-// launch shape or on its neighbours in the batch.
+// frame-t window keeps only (Ix, Iy) per tap in registers; b = sum (I - J)
+// grad I is formed as c - sum J grad I with the level constant c = sum I
+// grad I.  Bilinear sampling of frame t+1 is the weighted sum of four
+// integer-shift correlations per lane, kept for the last window position,
+// so an iteration at a position already correlated only recombines them.
+// The sums of b (and of G, c) are warp reductions.  All lanes end with
+// identical sums, so the control flow stays uniform, and the reduction
+// order is fixed: a point's result does not depend on the launch shape or
+// on its neighbours in the batch.
 //
 // Solve: det = Gxx Gyy - Gxy^2 by Kahan's fused form, lambda_min =
 // det / lambda_max (no cancellation), eta = G^-1 b by the 2x2 adjugate.
@@ -123,16 +124,17 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 // holds OMT_PT_LOST_TIMEOUT and takes no more work.
 struct Fills {
     uint64_t *bar;   // bar[b]: mbarrier of buffer b
-    unsigned pend;   // bit b: a fill of buffer b is in flight
+    unsigned pend;   // bit b: a fill of buffer b is in flight; FILL_FAILED: a
+                     // wait ran out (warp-uniform)
     unsigned phase;  // bit b: parity of buffer b's current phase
-    bool failed;     // a wait ran out (warp-uniform)
 };
+constexpr unsigned FILL_FAILED = 8u;
+__device__ __forceinline__ bool fills_failed(const Fills &f) { return (f.pend & FILL_FAILED) != 0; }
 
 __device__ __forceinline__ void fills_init(Fills &f, unsigned *W_bar, int lane) {
     f.bar = (uint64_t *)W_bar;
     f.pend = 0;
     f.phase = 0;
-    f.failed = false;
     if (lane == 0) {
 #pragma unroll
         for (int b = 0; b < 3; ++b)
@@ -213,7 +215,7 @@ __device__ __forceinline__ bool fill_wait(Fills &f, int b) {
     f.pend &= ~(1u << b);
     if (__any_sync(FULL_MASK, late)) {
         if ((threadIdx.x & 31) == 0) atomicAdd(&lk_wait_timeouts, 1u);
-        f.failed = true;
+        f.pend |= FILL_FAILED;
         return false;
     }
     f.phase ^= 1u << b;
@@ -402,7 +404,8 @@ __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
 // Four warp sums at once: halving exchanges leave each quarter of the warp
 // (lane bits 4 and 3) with one of the four partial sums, butterflies within
 // the quarter finish it, and every lane reads the four totals back.  Fixed
-// order, as warp_sum2.
+// order: every lane gets the same bits, and equal inputs give equal outputs
+// whatever they are paired with.
 __device__ __forceinline__ void warp_sum4(float &a, float &b, float &c, float &d, int lane) {
     const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
     float k0 = h4 ? c : a, k1 = h4 ? d : b;
@@ -671,9 +674,9 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
                                          const CUtensorMap *tm, unsigned *W, Fills &f,
                                          Prefetch &pf, bool has_next, float2 u_next,
                                          const LevelView *P_next_point,
-                                         const CUtensorMap *tm_next, bool force_fail) {
+                                         const CUtensorMap *tm_next, int gid) {
     const int lane = threadIdx.x & 31;
-    if (f.failed) {
+    if (fills_failed(f)) {
         lost_timeout(u, i, out, status, iters, levels, lane);
         return;
     }
@@ -695,6 +698,7 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         return;
     }
     has_next = has_next && fabsf(u_next.x) <= 16777216.f && fabsf(u_next.y) <= 16777216.f;
+    const bool force_fail = (long long)gid == lk_fail_point;   // the test hook
 
     for (int L = levels - 1; L >= 0; --L) {
         const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact
@@ -723,8 +727,8 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
                                   lane, L == 0, level_maps(tm, L), W, f, pf, nx, nux, nuy,
                                   k, conv, force_fail && L == levels - 1);
         if (st == OMT_PT_LOST_TIMEOUT) {
-            // land what else is in flight (bounded), then give the point up
-            fill_drain(f);
+            // give the point up; the kernel lands what else is in flight
+            // (bounded) before it exits
             pf.valid = false;
             lost_timeout(u, i, out, status, iters, levels, lane);
             return;
@@ -818,7 +822,6 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_kernel(const __grid_constant_
     Fills f;
     fills_init(f, W + Dims<ST, WIN>::BAR, threadIdx.x & 31);
     const CUtensorMap *tm = all_maps(a.tm_ok, a.levels) ? a.tm : nullptr;
-    const long long fail_at = lk_fail_point;
     Prefetch pf;
     pf.valid = false;
     // a warp whose wait ran out marks its remaining points (lk_point)
@@ -827,9 +830,30 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_kernel(const __grid_constant_
         const bool has_next = nxt < n;
         const float2 un = has_next ? a.pts[nxt] : make_float2(0.f, 0.f);
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters, tm, W, f, pf, has_next, un, a.P, tm, i == fail_at);
+                          a.status, a.iters, tm, W, f, pf, has_next, un, a.P, tm, i);
     }
     fill_drain(f);
+}
+
+// Queue positions [lo, hi) of a batch that a failed warp holds: reported
+// OMT_PT_LOST_TIMEOUT (out of line: only a failed warp gets here).
+template <bool backward>
+__device__ __noinline__ void give_up_batch(const uint8_t *table, const int32_t *pre, int lo,
+                                           int hi, int lane) {
+    const BatchView t(table);
+    const BatchHeader &h = t.hdr();
+    for (int q = lo; q < hi; ++q) {
+        const int sq = find_segment(pre, h.nstreams, q);
+        const StreamEntry &eq = t.stream(sq);
+        const int iq = q - pre[sq];
+        if constexpr (backward) {
+            lost_timeout(eq.pts_out[iq], iq, eq.pts_back, eq.status_back, nullptr, h.levels, lane);
+            if (lane == 0)
+                fb_apply(eq.pts[iq], eq.pts_back[iq], eq.status_back[iq], h.fb_max, eq.status[iq]);
+        } else {
+            lost_timeout(eq.pts[iq], iq, eq.pts_out, eq.status, eq.iters, h.levels, lane);
+        }
+    }
 }
 
 // All points of all streams of a batch: the per-stream counts come from the
@@ -862,24 +886,30 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *t
     }
     __syncthreads();
     const int total = pre[ns];
-    auto take = [&]() -> int {
-        unsigned b = 0;
-        if (lane == 0) b = atomicAdd(queue, (unsigned)chunk);
-        b = __shfl_sync(FULL_MASK, b, 0);
+    // One chunk is always claimed ahead: its atomic is issued a whole point
+    // before the warp reads the result, which hides the atomic's latency.
+    unsigned claim = 0;   // lane 0: the chunk claimed ahead
+    auto issue = [&]() {
+        if (lane == 0) claim = atomicAdd(queue, (unsigned)chunk);
+    };
+    auto collect = [&]() -> int {
+        const unsigned b = __shfl_sync(FULL_MASK, claim, 0);
         return b < (unsigned)total ? (int)b : total;
     };
     Fills f;
     fills_init(f, W + Dims<ST, WIN>::BAR, lane);
-    const long long fail_at = lk_fail_point;
     Prefetch pf;
     pf.valid = false;
-    int g = take(), end = g + chunk;
+    issue();
+    int g = collect(), end = g + chunk;
+    issue();
     int s = g < total ? find_segment(pre, ns, g) : 0;
     while (g < total) {
         int gn = g + 1;
         if (gn >= end || gn >= total) {
-            gn = take();
+            gn = collect();
             end = gn + chunk;
+            issue();
         }
         const StreamEntry &e = t.stream(s);
         const int i = g - pre[s];
@@ -896,29 +926,17 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *t
                           backward ? e.pts_back : e.pts_out, backward ? e.status_back : e.status,
                           backward ? nullptr : e.iters, stream_maps(t, s, h.levels, backward), W,
                           f, pf, has_next, un, backward ? en.P_next : en.P,
-                          stream_maps(t, sn, h.levels, backward), g == fail_at);
+                          stream_maps(t, sn, h.levels, backward), g);
         if constexpr (backward) {
             if (lane == 0) fb_apply(e.pts[i], e.pts_back[i], e.status_back[i], h.fb_max, e.status[i]);
         }
-        if (f.failed) {
+        if (fills_failed(f)) {
             // a wait ran out: the points this warp holds (the rest of its
-            // chunk, or the chunk it took next) are given up, and it takes
-            // no more work
-            const int stop = end < total ? end : total;
-            for (int q = gn; q < stop; ++q) {
-                const int sq = find_segment(pre, ns, q);
-                const StreamEntry &eq = t.stream(sq);
-                const int iq = q - pre[sq];
-                if constexpr (backward) {
-                    lost_timeout(eq.pts_out[iq], iq, eq.pts_back, eq.status_back, nullptr,
-                                 h.levels, lane);
-                    if (lane == 0)
-                        fb_apply(eq.pts[iq], eq.pts_back[iq], eq.status_back[iq], h.fb_max,
-                                 eq.status[iq]);
-                } else {
-                    lost_timeout(eq.pts[iq], iq, eq.pts_out, eq.status, eq.iters, h.levels, lane);
-                }
-            }
+            // chunk or the chunk it took next, and the chunk claimed ahead)
+            // are given up, and it takes no more work
+            give_up_batch<backward>(table, pre, gn, end < total ? end : total, lane);
+            const int c = collect();
+            give_up_batch<backward>(table, pre, c, c + chunk < total ? c + chunk : total, lane);
             break;
         }
         g = gn;

@@ -208,7 +208,7 @@ void assign_max_iou(const double *iou, int na, int nb, const uint8_t *active, do
                     void *ws, int32_t *match_a, int32_t *match_b);   // K1 tiles of a level of this size
 int response_tiles(int w, int h);  // K2 response tiles of a frame of this size
 cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
-                                 cudaStream_t s);
+                                 int max_streams, cudaStream_t s);
 cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_resp_tiles,
                                  int max_boxes, int max_corners, cudaStream_t s);
 // LK over every point of a batch: warps per CTA, CTAs per SM and work-queue

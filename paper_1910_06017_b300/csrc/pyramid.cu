@@ -208,6 +208,110 @@ __device__ __forceinline__ void store_next_stored(const LevelArgs &a, int Y, int
     }
 }
 
+// ------------------------------------------------------- level 0 in SWAR
+// Level 0 is integer: every sum the level needs fits 16 bits (the raw
+// Scharr gradients in [-4080, 4080], the 5-tap binomial of a row at most
+// 4080 and of five rows at most 65280), so it runs on pairs of pixels held
+// as the two 16-bit halves of a 32-bit register -- pixels (c, c+2): the
+// even pair (4g, 4g+2) and the odd pair (4g+1, 4g+3) of a thread's four
+// columns -- with 32-bit integer instructions.  Differences carry a bias
+// (256, then 4096 after the vertical pass) so that no half goes negative
+// and no carry crosses between halves.  The results convert to float
+// exactly (2^23 + v from the bits, then one fused multiply-add), so the
+// stored values are those of compute_tile bit for bit.
+constexpr unsigned SW_BIAS1 = 0x01000100u;   // 256 in each half
+constexpr unsigned SW_BIAS2 = 0x10001000u;   // 4096 in each half
+constexpr unsigned SW_MAGIC = 0x4B000000u;   // the bits of 2^23
+
+struct SwRow {
+    unsigned de, dof;   // biased horizontal differences, even / odd pair
+    unsigned se, so;    // horizontal Scharr smoothing 3, 10, 3
+    unsigned be;        // horizontal binomial 1, 4, 6, 4, 1 (even pair)
+};
+
+// The horizontal sums for columns x .. x+3 of one row, from the words of
+// its columns x-4 .. x-1, x .. x+3 and x+4 .. x+7.
+__device__ __forceinline__ SwRow sw_row(unsigned w0, unsigned w1, unsigned w2) {
+    const unsigned E0 = w0 & 0x00FF00FFu, E1 = w1 & 0x00FF00FFu, E2 = w2 & 0x00FF00FFu;
+    const unsigned O0 = __byte_perm(w0, 0u, 0x4341), O1 = __byte_perm(w1, 0u, 0x4341);
+    // (x[c + k], x[c + 2 + k]) for the even pair c = 4g at k = -2 .. 2 are
+    // A, B, E1, O1, C; for the odd pair c = 4g + 1 (k = -1 .. 1) B... E1,
+    // O1, C
+    const unsigned A = __byte_perm(E0, E1, 0x5432), B = __byte_perm(O0, O1, 0x5432);
+    const unsigned C = __byte_perm(E1, E2, 0x5432);
+    SwRow o;
+    o.de = O1 + SW_BIAS1 - B;
+    o.dof = C + SW_BIAS1 - E1;
+    const unsigned te = B + O1, to = E1 + C;
+    o.se = 3u * te + 10u * E1;
+    o.so = 3u * to + 10u * O1;
+    o.be = A + C + 4u * te + 6u * E1;
+    return o;
+}
+
+// The lane of v (0: low half, 1: high half) as the float 2^23 + v.
+__device__ __forceinline__ float sw_float(unsigned v, int half) {
+    return __uint_as_float(__byte_perm(v, SW_MAGIC, half ? 0x7632 : 0x7610));
+}
+
+// This thread's share of a staged 128x32 level-0 tile, in SWAR (staged
+// row bytes 4g-4 .. 4g+7 of the tile are words g+3 .. g+5 of the row).
+template <int ST>
+__device__ __forceinline__ void compute_tile_u8(const LevelArgs &a, int ox, int oy, const uint8_t *st) {
+    const int g = threadIdx.x & 31;   // columns 4g .. 4g+3 of the tile
+    const int q = threadIdx.x >> 5;   // rows RPT q .. RPT q + RPT-1 of the tile
+    const int x = ox + 4 * g;
+    if (x >= a.w) return;
+    const int y0 = oy + RPT * q;
+    SwRow h[RPT + 3];
+    const float2 g_scale = make_float2(1.0f / 32.0f, 1.0f / 32.0f);
+    const float2 g_off = make_float2(-(8388608.0f + 4096.0f) / 32.0f, -(8388608.0f + 4096.0f) / 32.0f);
+#pragma unroll
+    for (int k = 0; k < RPT + 3; ++k) {
+        const unsigned *w = (const unsigned *)(st + (RPT * q + k) * Stage<FMT_U8>::RB) + g + 3;
+        const unsigned w0 = w[0], w1 = w[1], w2 = w[2];
+        h[k] = sw_row(w0, w1, w2);
+        // the u8 copy of rows y0 .. y0+RPT-1
+        if (a.copy && k >= 2 && k < RPT + 2 && y0 + k - 2 < a.h) {
+            uint8_t *dst = a.copy + (int64_t)(y0 + k - 2) * a.copy_pitch + x;
+            if (x + 3 < a.w) {
+                *(unsigned *)dst = w1;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (x + c < a.w) dst[c] = (uint8_t)(w1 >> (8 * c));
+            }
+        }
+        // gradients of row y0 + k - 3 (rows k-2 .. k are in): 4096 + raw
+        if (k >= 3 && y0 + k - 3 < a.h) {
+            const unsigned gxe = 3u * (h[k - 2].de + h[k].de) + 10u * h[k - 1].de;
+            const unsigned gxo = 3u * (h[k - 2].dof + h[k].dof) + 10u * h[k - 1].dof;
+            const unsigned gye = h[k].se + SW_BIAS2 - h[k - 2].se;
+            const unsigned gyo = h[k].so + SW_BIAS2 - h[k - 2].so;
+            // pixels 4g, 4g+1, 4g+2, 4g+3: (even lo, odd lo, even hi, odd hi)
+            float gx[4], gy[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const unsigned vx = (c & 1) ? gxo : gxe, vy = (c & 1) ? gyo : gye;
+                const float2 p = __ffma2_rn(make_float2(sw_float(vx, c >> 1), sw_float(vy, c >> 1)),
+                                            g_scale, g_off);
+                gx[c] = p.x;
+                gy[c] = p.y;
+            }
+            store_grads<ST>(a, y0 + k - 3, x, gx, gy);
+        }
+        // level 1 row (y0 + k - 4) / 2 at even rows (rows k-4 .. k are in):
+        // columns 2g, 2g+1 from the even pair
+        if (a.next && k >= 4 && ((k & 1) == 0)) {
+            const unsigned L1 = (h[k - 4].be + h[k].be) + 4u * (h[k - 3].be + h[k - 1].be) + 6u * h[k - 2].be;
+            const float2 v = __ffma2_rn(make_float2(sw_float(L1, 0), sw_float(L1, 1)),
+                                        make_float2(1.0f / 256.0f, 1.0f / 256.0f),
+                                        make_float2(-32768.0f, -32768.0f));   // exact: L1 / 256
+            store_next<ST>(a, (y0 >> 1) + (k - 4) / 2, x >> 1, v.x, v.y);
+        }
+    }
+}
+
 // This thread's share of the staged 128x32 tile of level L at (ox, oy).
 template <int ST, int FMT>
 __device__ __forceinline__ void compute_tile(const LevelArgs &a, int ox, int oy, const uint8_t *st) {
@@ -503,7 +607,8 @@ __device__ __forceinline__ void tile_pipeline(int total, Resolve resolve) {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();  // tile g is staged by every thread
-        if constexpr (PATH == PATH_INT64) compute_tile_fixed<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
+        if constexpr (FMT == FMT_U8) compute_tile_u8<ST>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
+        else if constexpr (PATH == PATH_INT64) compute_tile_fixed<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
         else if constexpr (PATH == PATH_SPLIT) compute_tile_split<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
         else compute_tile<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
     }
@@ -557,18 +662,32 @@ __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int 
 
 // Level L of every stream of a batch: the CTAs stride over the batch's
 // tiles (tile prefix per stream in the table).
+// Shared memory of a batch launch: the two staging buffers, then every
+// stream's level arguments and the tile prefix (copied from the table once
+// per CTA, so that naming a tile reads no global memory).
+template <int FMT>
+__host__ __device__ constexpr size_t batch_smem_bytes(int max_streams) {
+    return 2 * (size_t)Stage<FMT>::BYTES + (size_t)max_streams * sizeof(LevelArgs) +
+           ((size_t)max_streams + 1) * sizeof(int);
+}
+
 template <int ST, int FMT, int PATH>
 __global__ void __launch_bounds__(NT) pyramid_batch_kernel(const uint8_t *table, int L) {
+    extern __shared__ __align__(16) uint8_t pyr_smem[];
     const BatchView t(table);
-    const int *pre = t.pyr_prefix(L);
-    const int total = pre[t.nstreams()];
+    const int ns = t.nstreams();
+    LevelArgs *sa = (LevelArgs *)(pyr_smem + 2 * (size_t)Stage<FMT>::BYTES);
+    int *spre = (int *)(sa + t.hdr().max_streams);
+    for (int i = threadIdx.x; i < ns; i += NT) level_args_from_entry(t.stream(i), L, t.levels(), sa[i]);
+    for (int i = threadIdx.x; i <= ns; i += NT) spre[i] = t.pyr_prefix(L)[i];
+    __syncthreads();
+    const int total = spre[ns];
     tile_pipeline<ST, FMT, PATH>(total, [&](int g, Tile &tile) {
-        const int si = find_segment(pre, t.nstreams(), g);
-        const StreamEntry &e = t.stream(si);
-        const int tiles_x = (e.P_next[L].w + TX - 1) / TX;
-        const int local = g - pre[si];
+        const int si = find_segment(spre, ns, g);
+        tile.a = sa[si];
+        const int tiles_x = (tile.a.w + TX - 1) / TX;
+        const int local = g - spre[si];
         const int ty = local / tiles_x, tx = local - ty * tiles_x;
-        level_args_from_entry(e, L, t.levels(), tile.a);
         tile.ox = tx * TX;
         tile.oy = ty * TY;
     });
@@ -576,22 +695,25 @@ __global__ void __launch_bounds__(NT) pyramid_batch_kernel(const uint8_t *table,
 
 // CTAs for `tiles` tiles: at most the number resident on the device at
 // once (the kernels stride over the rest).  Sets the kernel's dynamic shared
-// memory limit the first time per device; cap is the caller's per-kernel
-// cache of resident CTAs per device.
+// memory limit whenever a launch needs more than the last one set on the
+// device; cap and cap_smem are the caller's per-kernel caches of resident
+// CTAs and of that limit, per device.
 template <typename K>
-cudaError_t grid_for(K kernel, int tiles, size_t smem, int *cap, int &grid) {
+cudaError_t grid_for(K kernel, int tiles, size_t smem, int *cap, size_t *cap_smem, int &grid,
+                     int nt = NT) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (cap[dev] == 0) {
+    if (cap[dev] == 0 || smem > cap_smem[dev]) {
         int sms = 0, per_sm = 0;
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nt, smem);
         if (e != cudaSuccess) return e;
         cap[dev] = sms * (per_sm < 1 ? 1 : per_sm);
+        cap_smem[dev] = smem;
     }
     grid = tiles < 1 ? 1 : (tiles < cap[dev] ? tiles : cap[dev]);
     return cudaSuccess;
@@ -602,8 +724,9 @@ cudaError_t launch_level_k(const LevelArgs &a, cudaStream_t s) {
     const int tiles_x = (a.w + TX - 1) / TX, total = tiles_x * ((a.h + TY - 1) / TY);
     const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
     static int cap[64] = {0};
+    static size_t cap_smem[64] = {0};
     int grid = 0;
-    cudaError_t e = grid_for(pyramid_level_kernel<ST, FMT, PATH>, total, smem, cap, grid);
+    cudaError_t e = grid_for(pyramid_level_kernel<ST, FMT, PATH>, total, smem, cap, cap_smem, grid);
     if (e != cudaSuccess) return e;
     pyramid_level_kernel<ST, FMT, PATH><<<grid, NT, smem, s>>>(a, tiles_x, total);
     return cudaGetLastError();
@@ -630,25 +753,28 @@ cudaError_t launch_level(const LevelArgs &a, cudaStream_t s) {
 }
 
 template <int ST, int FMT, int PATH>
-cudaError_t launch_batch_level_k(const uint8_t *table, int L, int max_tiles, cudaStream_t s) {
-    const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
+cudaError_t launch_batch_level_k(const uint8_t *table, int L, int max_tiles, int max_streams,
+                                 cudaStream_t s) {
+    const size_t smem = batch_smem_bytes<FMT>(max_streams);
     static int cap[64] = {0};
+    static size_t cap_smem[64] = {0};
     int grid = 0;
-    cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT, PATH>, max_tiles, smem, cap, grid);
+    cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT, PATH>, max_tiles, smem, cap, cap_smem, grid);
     if (e != cudaSuccess) return e;
     pyramid_batch_kernel<ST, FMT, PATH><<<grid, NT, smem, s>>>(table, L);
     return cudaGetLastError();
 }
 
 template <int ST, int FMT>
-cudaError_t launch_batch_level(const uint8_t *table, int L, int max_tiles, cudaStream_t s) {
+cudaError_t launch_batch_level(const uint8_t *table, int L, int max_tiles, int max_streams,
+                               cudaStream_t s) {
     if constexpr (FMT == FMT_U8) {
-        return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, s);
+        return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, max_streams, s);
     } else {
         switch (level_path(level_frac(L))) {
-            case PATH_SPLIT: return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, s);
-            case PATH_INT64: return launch_batch_level_k<ST, FMT, PATH_INT64>(table, L, max_tiles, s);
-            default: return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, s);
+            case PATH_SPLIT: return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, max_streams, s);
+            case PATH_INT64: return launch_batch_level_k<ST, FMT, PATH_INT64>(table, L, max_tiles, max_streams, s);
+            default: return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, max_streams, s);
         }
     }
 }
@@ -700,16 +826,16 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
 }
 
 cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
-                                 cudaStream_t s) {
+                                 int max_streams, cudaStream_t s) {
     for (int L = 0; L < levels; ++L) {
         const int mt = max_tiles[L] > 0 ? max_tiles[L] : 1;
         cudaError_t e;
         if (storage == OMT_F32)
-            e = L == 0 ? launch_batch_level<OMT_F32, FMT_U8>(table, L, mt, s)
-                       : launch_batch_level<OMT_F32, FMT_F32>(table, L, mt, s);
+            e = L == 0 ? launch_batch_level<OMT_F32, FMT_U8>(table, L, mt, max_streams, s)
+                       : launch_batch_level<OMT_F32, FMT_F32>(table, L, mt, max_streams, s);
         else
-            e = L == 0 ? launch_batch_level<OMT_F16, FMT_U8>(table, L, mt, s)
-                       : launch_batch_level<OMT_F16, FMT_H16>(table, L, mt, s);
+            e = L == 0 ? launch_batch_level<OMT_F16, FMT_U8>(table, L, mt, max_streams, s)
+                       : launch_batch_level<OMT_F16, FMT_H16>(table, L, mt, max_streams, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
