@@ -298,6 +298,14 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
                        sizeof(CUtensorMap) * (size_t)i * 2 * OMT_MAX_LEVELS * LK_MAPS,
                    tm, sizeof(tm));
         }
+        {
+            alignas(64) CUtensorMap fm;
+            memset(&fm, 0, sizeof(fm));
+            e.frame_map_ok = encode_u8_map(b.frame, P.w, P.h, (int64_t)b.frame_pitch, L0_BOX_W,
+                                           L0_BOX_H, &fm) ? 1u : 0u;
+            memcpy(base + batch_frame_maps_offset(caps->max_streams) + sizeof(CUtensorMap) * (size_t)i,
+                   &fm, sizeof(fm));
+        }
         for (int L = 0; L < prm->levels; ++L)
             pyr_pre[L][i + 1] = pyr_pre[L][i] + pyramid_tiles(P.lv[L].w, P.lv[L].h);
         resp_pre[i + 1] = resp_pre[i] + response_tiles(P.w, P.h);
@@ -485,8 +493,10 @@ int omt_scale_boxes(const float *boxes, int32_t n, float scale, float *boxes_out
 
 int omt_lk_wait_timeouts(uint32_t *count) {
     if (!count) return OMT_EINVAL;
-    unsigned c = 0;
-    const int r = from_cuda(lk_wait_timeouts_take(&c));
+    unsigned c = 0, cp = 0;
+    int r = from_cuda(lk_wait_timeouts_take(&c));
+    if (r == OMT_OK) r = from_cuda(pyr_wait_timeouts_take(&cp));
+    c += cp;
     *count = c;
     if (r != OMT_OK) return r;
     return c ? OMT_ETIMEOUT : OMT_OK;

@@ -112,6 +112,7 @@ struct StreamEntry {
     int32_t *pad_counts;               // scratch: per-box counts
     int32_t w, h, nboxes, maxc;
     uint32_t tm_ok, tm_ok_back;        // bit 3L + m: LK map m of level L (forward, backward) valid
+    uint32_t frame_map_ok;             // the level-0 tile map of frame t+1 is valid
 };
 
 // Tensor maps of the LK window copies, per level: the template frame's
@@ -146,9 +147,14 @@ __host__ __device__ inline size_t batch_maps_offset(int max_streams) {
     return (off + 127) & ~(size_t)127;
 }
 
-__host__ __device__ inline size_t batch_table_bytes(int max_streams) {
+// The level-0 tile maps of the frames t+1 follow the LK maps, one per stream.
+__host__ __device__ inline size_t batch_frame_maps_offset(int max_streams) {
     return batch_maps_offset(max_streams) +
            sizeof(CUtensorMap) * (size_t)max_streams * 2 * OMT_MAX_LEVELS * LK_MAPS;
+}
+
+__host__ __device__ inline size_t batch_table_bytes(int max_streams) {
+    return batch_frame_maps_offset(max_streams) + sizeof(CUtensorMap) * (size_t)max_streams;
 }
 
 struct BatchView {
@@ -164,6 +170,10 @@ struct BatchView {
     __host__ __device__ const int32_t *box_prefix() const { return pyr_prefix(OMT_MAX_LEVELS + 1); }
     __host__ __device__ const StreamEntry &stream(int s) const {
         return ((const StreamEntry *)(base + batch_entries_offset(hdr().max_streams)))[s];
+    }
+    // stream s's level-0 tile map of frame t+1
+    __host__ __device__ const CUtensorMap *frame_map(int s) const {
+        return (const CUtensorMap *)(base + batch_frame_maps_offset(hdr().max_streams)) + s;
     }
     // stream s's LK maps of direction d (0 forward, 1 backward), LK_MAPS per level
     __host__ __device__ const CUtensorMap *maps(int s, int d) const {
@@ -219,8 +229,20 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
 // driver) leaves its bit clear and the kernels copy that level row by row.
 uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensorMap *out);
 
+// A 2D tensor map of a u8 plane (w x h, pitch bytes apart) read in boxes of
+// box_w x box_h bytes, zero-filled outside; false when the plane's base or
+// pitch is not a multiple of 16 bytes (the map cannot describe it).
+bool encode_u8_map(const uint8_t *base, int w, int h, int64_t pitch, int box_w, int box_h,
+                   CUtensorMap *out);
+
+// Box of the level-0 pyramid tiles' tensor copies (pyramid.cu): 16 columns
+// either side of a 128-column tile (the copy's x must be a multiple of 16
+// bytes) and 2 rows above and below a 32-row tile.
+constexpr int L0_BOX_W = 160, L0_BOX_H = 36;
+
 // Reads and clears the count of LK staging waits that hit their limit.
 cudaError_t lk_wait_timeouts_take(unsigned *count);
+cudaError_t pyr_wait_timeouts_take(unsigned *count);
 cudaError_t lk_fail_point_set(long long point);
 
 // backward = 0: the LK phase (frame t -> t+1); 1: the backward run of the

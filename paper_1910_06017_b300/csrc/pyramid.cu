@@ -24,6 +24,8 @@
 // value is the correctly rounded result of the definition applied to the
 // level above as stored, in both storages (half outputs go through a
 // round-to-odd FP32 value, which makes the second rounding exact).
+#include <cstring>
+
 #include "omt_internal.cuh"
 
 namespace omt {
@@ -256,10 +258,11 @@ __device__ __forceinline__ float sw_float(unsigned v, int half) {
 
 // This thread's share of a staged 128x32 level-0 tile, in SWAR (staged
 // row bytes 4g-4 .. 4g+7 of the tile are words g+3 .. g+5 of the row).
-template <int ST>
-__device__ __forceinline__ void compute_tile_u8(const LevelArgs &a, int ox, int oy, const uint8_t *st) {
+template <int ST, int RPT = omt::RPT>
+__device__ __forceinline__ void compute_tile_u8(const LevelArgs &a, int ox, int oy, const uint8_t *st,
+                                                int q = threadIdx.x >> 5) {
     const int g = threadIdx.x & 31;   // columns 4g .. 4g+3 of the tile
-    const int q = threadIdx.x >> 5;   // rows RPT q .. RPT q + RPT-1 of the tile
+    // q: rows RPT q .. RPT q + RPT-1 of the tile
     const int x = ox + 4 * g;
     if (x >= a.w) return;
     const int y0 = oy + RPT * q;
@@ -693,6 +696,244 @@ __global__ void __launch_bounds__(NT) pyramid_batch_kernel(const uint8_t *table,
     });
 }
 
+// ------------------------------------------------------ level 0, TMA ring
+// Level 0 (the u8 frame: the pyramid's bulk) streams through a ring of
+// L0_STAGES staged tiles per CTA: one producer warp copies each 128 x 32
+// tile with its halo (the L0_BOX_W x L0_BOX_H box) global -> shared by one
+// 2D tensor copy, whose completion the stage's "full" mbarrier counts; four
+// consumer warps compute the tile (8 rows each, in SWAR) and release the
+// stage on its "empty" mbarrier.  No CTA-wide barrier in the steady state:
+// the producer runs up to L0_STAGES tiles ahead.  A frame whose base or
+// pitch is not 16-byte aligned (no tensor map) is copied by the producer
+// warp's plain loads instead.  Outside the frame the copy holds zeros;
+// tiles at the frame's edge replace the halo texels that outputs read by
+// their reflect-101 images (rows, then columns) before computing.  Every
+// wait gives up after one second (counted in pyr_wait_timeouts), and a CTA
+// whose wait ran out stops, after landing its copies in flight.
+constexpr int L0_STAGES = 4;
+constexpr int L0_CONS = 4;                  // consumer warps
+constexpr int L0_NT = 32 * (L0_CONS + 1);   // and the producer warp
+constexpr int L0_RPT = TY / L0_CONS;        // rows per consumer thread
+constexpr unsigned L0_TILE_BYTES = L0_BOX_W * L0_BOX_H;
+static_assert(L0_BOX_W == Stage<FMT_U8>::RB && L0_BOX_H == SROWS, "a ring stage is a staged tile");
+static_assert(L0_TILE_BYTES % 128 == 0, "stages on 128-byte boundaries");
+constexpr unsigned long long L0_WAIT_NS = 1000000000ull;
+
+__device__ unsigned pyr_wait_timeouts;
+
+struct L0Ring {
+    uint8_t tile[L0_STAGES][L0_TILE_BYTES];
+    uint64_t full[L0_STAGES], empty[L0_STAGES];
+    int ok[2];   // consumers: tile k's stage landed, in slot k & 1 (set by thread 0)
+};
+
+__device__ __forceinline__ unsigned l0_smem(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool l0_try_wait(const uint64_t *bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(l0_smem(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long l0_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// One thread's bounded wait for the phase of parity `parity` to complete.
+__device__ __forceinline__ bool l0_wait(const uint64_t *bar, unsigned parity) {
+    if (l0_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = l0_ns();
+    while (!l0_try_wait(bar, parity))
+        if (l0_ns() - t0 > L0_WAIT_NS) {
+            atomicAdd(&pyr_wait_timeouts, 1u);
+            return false;
+        }
+    return true;
+}
+__device__ __forceinline__ void l0_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(l0_smem(bar)) : "memory");
+}
+__device__ __forceinline__ void l0_consumers_sync() {
+    asm volatile("bar.sync 1, %0;\n" ::"n"(32 * L0_CONS) : "memory");
+}
+
+// The producer warp fills stage `st` with the box of tile (ox, oy): by the
+// tensor map, or (no map) by plain loads, zero outside the frame.
+__device__ __forceinline__ void l0_fill(const LevelArgs &a, const CUtensorMap *map, int ox, int oy,
+                                        uint8_t *st, uint64_t *full, int lane) {
+    if (map) {
+        if (lane == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(l0_smem(full)),
+                         "r"(L0_TILE_BYTES)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(l0_smem(st)),
+                "l"((unsigned long long)map), "r"(ox - 16), "r"(oy - 2), "r"(l0_smem(full))
+                : "memory");
+        }
+        return;
+    }
+    for (int i = lane; i < L0_BOX_H * (L0_BOX_W / 4); i += 32) {
+        const int r = i / (L0_BOX_W / 4), c = i - r * (L0_BOX_W / 4);
+        const int y = oy - 2 + r, x = ox - 16 + 4 * c;
+        unsigned v = 0;
+        if (y >= 0 && y < a.h) {
+            const uint8_t *row = a.src + (int64_t)y * a.src_pitch;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (x + b >= 0 && x + b < a.w) v |= (unsigned)row[x + b] << (8 * b);
+        }
+        *(unsigned *)(st + r * L0_BOX_W + 4 * c) = v;
+    }
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) l0_arrive(full);
+}
+
+// Halo texels of an edge tile that outputs read (rows -2, -1, h, h+1 and
+// columns -2, -1, w, w+1) take their reflect-101 images from inside the
+// box: rows first, then columns (so corners reflect both ways).  The four
+// consumer warps share the work; the box's rows and columns stay in range
+// for every nonempty tile.
+__device__ __forceinline__ void l0_fix_edges(const LevelArgs &a, int ox, int oy, uint8_t *st, int t) {
+    const int y0 = oy - 2, x0 = ox - 16;
+    for (int i = t; i < 4 * (L0_BOX_W / 4); i += 32 * L0_CONS) {
+        const int k = i / (L0_BOX_W / 4), c = i - k * (L0_BOX_W / 4);
+        const int y = k < 2 ? k - 2 : a.h + (k - 2);   // -2, -1, h, h+1
+        const int r = y - y0;
+        if (r < 0 || r >= L0_BOX_H) continue;
+        const int rr = reflect101(y, a.h) - y0;
+        ((unsigned *)(st + r * L0_BOX_W))[c] = ((const unsigned *)(st + rr * L0_BOX_W))[c];
+    }
+    l0_consumers_sync();
+    for (int i = t; i < 4 * L0_BOX_H; i += 32 * L0_CONS) {
+        const int k = i / L0_BOX_H, r = i - k * L0_BOX_H;
+        const int x = k < 2 ? k - 2 : a.w + (k - 2);   // -2, -1, w, w+1
+        const int c = x - x0;
+        if (c < 0 || c >= L0_BOX_W) continue;
+        st[r * L0_BOX_W + c] = st[r * L0_BOX_W + reflect101(x, a.w) - x0];
+    }
+    l0_consumers_sync();
+}
+
+// The ring over the CTA's tiles g = blockIdx.x, += gridDim.x, < total;
+// resolve(g, args, ox, oy, map) names a tile (map: its frame's tensor map or
+// null) and is called by every thread for every tile.
+template <int ST, typename Resolve>
+__device__ __forceinline__ void l0_ring(L0Ring &R, int total, Resolve resolve) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < L0_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(l0_smem(&R.full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(l0_smem(&R.empty[s])),
+                         "r"(L0_CONS)
+                         : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == L0_CONS) {
+        // producer
+        int k = 0;
+        for (int g = blockIdx.x; g < total; g += gridDim.x, ++k) {
+            const int s = k % L0_STAGES;
+            if (k >= L0_STAGES) {
+                bool ok = true;
+                if (lane == 0) ok = l0_wait(&R.empty[s], ((k / L0_STAGES) - 1) & 1);
+                if (!__shfl_sync(FULL_MASK, ok, 0)) break;
+            }
+            LevelArgs a;
+            int ox, oy;
+            const CUtensorMap *map;
+            resolve(g, a, ox, oy, map);
+            l0_fill(a, map, ox, oy, R.tile[s], &R.full[s], lane);
+        }
+        // land the copies still in flight (bounded) before the CTA exits
+        if (lane == 0)
+            for (int j = k - L0_STAGES > 0 ? k - L0_STAGES : 0; j < k; ++j)
+                l0_wait(&R.full[j % L0_STAGES], (j / L0_STAGES) & 1);
+        return;
+    }
+    // consumers: warp 0 lane 0 waits for each stage, the four warps follow
+    int k = 0;
+    for (int g = blockIdx.x; g < total; g += gridDim.x, ++k) {
+        const int s = k % L0_STAGES;
+        // two slots: thread 0 writes tile k+1's only after every consumer
+        // has passed tile k's barrier, i.e. read tile k's
+        if (threadIdx.x == 0) R.ok[k & 1] = l0_wait(&R.full[s], (k / L0_STAGES) & 1);
+        l0_consumers_sync();
+        if (!R.ok[k & 1]) break;
+        LevelArgs a;
+        int ox, oy;
+        const CUtensorMap *map;
+        resolve(g, a, ox, oy, map);
+        uint8_t *st = R.tile[s];
+        if (ox == 0 || oy == 0 || ox + TX + 2 > a.w || oy + TY + 2 > a.h) {
+            l0_fix_edges(a, ox, oy, st, threadIdx.x);
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // before the next copy
+        }
+        compute_tile_u8<ST, L0_RPT>(a, ox, oy, st, warp);
+        __syncwarp();
+        if (lane == 0) l0_arrive(&R.empty[s]);
+    }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(L0_NT) pyramid_l0_kernel(const LevelArgs a, int tiles_x, int total,
+                                                           const __grid_constant__ CUtensorMap map,
+                                                           int map_ok) {
+    extern __shared__ __align__(128) uint8_t l0_smem_raw[];
+    L0Ring &R = *(L0Ring *)l0_smem_raw;
+    l0_ring<ST>(R, total, [&](int g, LevelArgs &t, int &ox, int &oy, const CUtensorMap *&m) {
+        const int ty = g / tiles_x, tx = g - ty * tiles_x;
+        t = a;
+        ox = tx * TX;
+        oy = ty * TY;
+        m = map_ok ? &map : nullptr;
+    });
+}
+
+// The batch form: every stream's level-0 arguments, tile prefix and map
+// flag are copied into shared memory once per CTA.
+__host__ __device__ constexpr size_t l0_batch_smem_bytes(int max_streams) {
+    return sizeof(L0Ring) + (size_t)max_streams * sizeof(LevelArgs) +
+           ((size_t)max_streams + 1) * sizeof(int) + (size_t)max_streams * sizeof(int);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(L0_NT) pyramid_l0_batch_kernel(const uint8_t *table) {
+    extern __shared__ __align__(128) uint8_t l0_smem_raw[];
+    L0Ring &R = *(L0Ring *)l0_smem_raw;
+    const BatchView t(table);
+    const int ns = t.nstreams(), cap = t.hdr().max_streams;
+    LevelArgs *sa = (LevelArgs *)(l0_smem_raw + sizeof(L0Ring));
+    int *spre = (int *)(sa + cap);
+    int *sok = spre + cap + 1;
+    for (int i = threadIdx.x; i < ns; i += L0_NT) {
+        level_args_from_entry(t.stream(i), 0, t.levels(), sa[i]);
+        sok[i] = (int)t.stream(i).frame_map_ok;
+    }
+    for (int i = threadIdx.x; i <= ns; i += L0_NT) spre[i] = t.pyr_prefix(0)[i];
+    __syncthreads();
+    l0_ring<ST>(R, spre[ns], [&](int g, LevelArgs &a, int &ox, int &oy, const CUtensorMap *&m) {
+        const int si = find_segment(spre, ns, g);
+        a = sa[si];
+        const int tiles_x = (a.w + TX - 1) / TX;
+        const int local = g - spre[si];
+        const int ty = local / tiles_x, tx = local - ty * tiles_x;
+        ox = tx * TX;
+        oy = ty * TY;
+        m = sok[si] ? t.frame_map(si) : nullptr;
+    });
+}
+
 // CTAs for `tiles` tiles: at most the number resident on the device at
 // once (the kernels stride over the rest).  Sets the kernel's dynamic shared
 // memory limit whenever a launch needs more than the last one set on the
@@ -739,10 +980,25 @@ __host__ __device__ __forceinline__ int level_path(int frac) {
     return frac == 0 ? PATH_FLOAT : (frac <= 24 ? PATH_SPLIT : PATH_INT64);
 }
 
+template <int ST>
+cudaError_t launch_l0(const LevelArgs &a, cudaStream_t s) {
+    const int tiles_x = (a.w + TX - 1) / TX, total = tiles_x * ((a.h + TY - 1) / TY);
+    alignas(64) CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    const int map_ok = encode_u8_map(a.src, a.w, a.h, a.src_pitch, L0_BOX_W, L0_BOX_H, &map) ? 1 : 0;
+    static int cap[64] = {0};
+    static size_t cap_smem[64] = {0};
+    int grid = 0;
+    cudaError_t e = grid_for(pyramid_l0_kernel<ST>, total, sizeof(L0Ring), cap, cap_smem, grid, L0_NT);
+    if (e != cudaSuccess) return e;
+    pyramid_l0_kernel<ST><<<grid, L0_NT, sizeof(L0Ring), s>>>(a, tiles_x, total, map, map_ok);
+    return cudaGetLastError();
+}
+
 template <int ST, int FMT>
 cudaError_t launch_level(const LevelArgs &a, cudaStream_t s) {
     if constexpr (FMT == FMT_U8) {
-        return launch_level_k<ST, FMT, PATH_FLOAT>(a, s);
+        return launch_l0<ST>(a, s);
     } else {
         switch (level_path(a.frac)) {
             case PATH_SPLIT: return launch_level_k<ST, FMT, PATH_SPLIT>(a, s);
@@ -765,11 +1021,23 @@ cudaError_t launch_batch_level_k(const uint8_t *table, int L, int max_tiles, int
     return cudaGetLastError();
 }
 
+template <int ST>
+cudaError_t launch_l0_batch(const uint8_t *table, int max_tiles, int max_streams, cudaStream_t s) {
+    const size_t smem = l0_batch_smem_bytes(max_streams);
+    static int cap[64] = {0};
+    static size_t cap_smem[64] = {0};
+    int grid = 0;
+    cudaError_t e = grid_for(pyramid_l0_batch_kernel<ST>, max_tiles, smem, cap, cap_smem, grid, L0_NT);
+    if (e != cudaSuccess) return e;
+    pyramid_l0_batch_kernel<ST><<<grid, L0_NT, smem, s>>>(table);
+    return cudaGetLastError();
+}
+
 template <int ST, int FMT>
 cudaError_t launch_batch_level(const uint8_t *table, int L, int max_tiles, int max_streams,
                                cudaStream_t s) {
     if constexpr (FMT == FMT_U8) {
-        return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, max_streams, s);
+        return launch_l0_batch<ST>(table, max_tiles, max_streams, s);
     } else {
         switch (level_path(level_frac(L))) {
             case PATH_SPLIT: return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, max_streams, s);
@@ -839,6 +1107,13 @@ cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, 
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t pyr_wait_timeouts_take(unsigned *count) {
+    unsigned zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(count, pyr_wait_timeouts, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(pyr_wait_timeouts, &zero, sizeof(unsigned));
+    return e;
 }
 
 int pyramid_tiles(int w, int h) { return ((w + TX - 1) / TX) * ((h + TY - 1) / TY); }
