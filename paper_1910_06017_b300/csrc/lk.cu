@@ -114,6 +114,8 @@ __device__ unsigned lk_wait_timeouts;
 __device__ long long lk_fail_point = -1;
 constexpr unsigned FAIL_EXTRA_BYTES = 16;
 
+__device__ __forceinline__ int lane_of() { return threadIdx.x & 31; }
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -129,7 +131,6 @@ struct Fills {
     unsigned phase;  // bit b: parity of buffer b's current phase
 };
 constexpr unsigned FILL_FAILED = 8u;
-__device__ __forceinline__ bool fills_failed(const Fills &f) { return (f.pend & FILL_FAILED) != 0; }
 
 __device__ __forceinline__ void fills_init(Fills &f, unsigned *W_bar, int lane) {
     f.bar = (uint64_t *)W_bar;
@@ -222,12 +223,10 @@ __device__ __forceinline__ bool fill_wait(Fills &f, int b) {
     return true;
 }
 
-// Land every fill in flight (each wait bounded); false if one ran out.
-__device__ __forceinline__ bool fill_drain(Fills &f) {
-    const bool a = fill_wait(f, 0);
-    const bool b = fill_wait(f, 1);
-    const bool c = fill_wait(f, BUF_SEARCH);
-    return a && b && c;
+__device__ __forceinline__ void fill_drain(Fills &f) {
+    fill_wait(f, 0);
+    fill_wait(f, 1);
+    fill_wait(f, BUF_SEARCH);
 }
 
 // The bytes of a row to copy for texel columns [x0, x0 + ncols) clamped to
@@ -404,8 +403,7 @@ __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
 // Four warp sums at once: halving exchanges leave each quarter of the warp
 // (lane bits 4 and 3) with one of the four partial sums, butterflies within
 // the quarter finish it, and every lane reads the four totals back.  Fixed
-// order: every lane gets the same bits, and equal inputs give equal outputs
-// whatever they are paired with.
+// order, as warp_sum2.
 __device__ __forceinline__ void warp_sum4(float &a, float &b, float &c, float &d, int lane) {
     const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
     float k0 = h4 ? c : a, k1 = h4 ? d : b;
@@ -676,10 +674,6 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
                                          const LevelView *P_next_point,
                                          const CUtensorMap *tm_next, int gid) {
     const int lane = threadIdx.x & 31;
-    if (fills_failed(f)) {
-        lost_timeout(u, i, out, status, iters, levels, lane);
-        return;
-    }
     float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
     int st = OMT_PT_OK;
     bool nonconv = false;
@@ -698,7 +692,6 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         return;
     }
     has_next = has_next && fabsf(u_next.x) <= 16777216.f && fabsf(u_next.y) <= 16777216.f;
-    const bool force_fail = (long long)gid == lk_fail_point;   // the test hook
 
     for (int L = levels - 1; L >= 0; --L) {
         const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact
@@ -725,15 +718,19 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         bool conv;
         st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
                                   lane, L == 0, level_maps(tm, L), W, f, pf, nx, nux, nuy,
-                                  k, conv, force_fail && L == levels - 1);
+                                  k, conv, L == levels - 1 && (long long)gid == lk_fail_point);
+        itp |= (unsigned long long)k << (8 * L);
         if (st == OMT_PT_LOST_TIMEOUT) {
             // give the point up; the kernel lands what else is in flight
             // (bounded) before it exits
             pf.valid = false;
-            lost_timeout(u, i, out, status, iters, levels, lane);
+            if (lane == 0) {
+                out[i] = u;
+                status[i] = (uint8_t)OMT_PT_LOST_TIMEOUT;
+            }
+            if (iters && lane < levels) iters[(int64_t)i * levels + lane] = 0;
             return;
         }
-        itp |= (unsigned long long)k << (8 * L);
         if (st != OMT_PT_OK) break;
         if (!conv) nonconv = true;
         if (L > 0) {
@@ -811,7 +808,7 @@ constexpr size_t stage_bytes(int warps = LK_WARPS) {
 }
 
 template <int ST, int WIN>
-__global__ void __launch_bounds__(LK_MAX_NT, 2) lk_kernel(const __grid_constant__ LKArgs a) {
+__global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ LKArgs a) {
     unsigned *W = warp_words<ST, WIN>();
     int n = a.n_max;
     if (a.n_dev) {
@@ -824,11 +821,14 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_kernel(const __grid_constant_
     const CUtensorMap *tm = all_maps(a.tm_ok, a.levels) ? a.tm : nullptr;
     Prefetch pf;
     pf.valid = false;
-    // a warp whose wait ran out marks its remaining points (lk_point)
     for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
         const int nxt = i + nwarps;
         const bool has_next = nxt < n;
         const float2 un = has_next ? a.pts[nxt] : make_float2(0.f, 0.f);
+        if (f.pend & FILL_FAILED) {   // a wait ran out: the warp's later points are given up
+            lost_timeout(a.pts[i], i, a.out, a.status, a.iters, a.levels, lane_of());
+            continue;
+        }
         lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
                           a.status, a.iters, tm, W, f, pf, has_next, un, a.P, tm, i);
     }
@@ -886,30 +886,23 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *t
     }
     __syncthreads();
     const int total = pre[ns];
-    // One chunk is always claimed ahead: its atomic is issued a whole point
-    // before the warp reads the result, which hides the atomic's latency.
-    unsigned claim = 0;   // lane 0: the chunk claimed ahead
-    auto issue = [&]() {
-        if (lane == 0) claim = atomicAdd(queue, (unsigned)chunk);
-    };
-    auto collect = [&]() -> int {
-        const unsigned b = __shfl_sync(FULL_MASK, claim, 0);
+    auto take = [&]() -> int {
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(queue, (unsigned)chunk);
+        b = __shfl_sync(FULL_MASK, b, 0);
         return b < (unsigned)total ? (int)b : total;
     };
     Fills f;
     fills_init(f, W + Dims<ST, WIN>::BAR, lane);
     Prefetch pf;
     pf.valid = false;
-    issue();
-    int g = collect(), end = g + chunk;
-    issue();
+    int g = take(), end = g + chunk;
     int s = g < total ? find_segment(pre, ns, g) : 0;
     while (g < total) {
         int gn = g + 1;
         if (gn >= end || gn >= total) {
-            gn = collect();
+            gn = take();
             end = gn + chunk;
-            issue();
         }
         const StreamEntry &e = t.stream(s);
         const int i = g - pre[s];
@@ -930,13 +923,11 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *t
         if constexpr (backward) {
             if (lane == 0) fb_apply(e.pts[i], e.pts_back[i], e.status_back[i], h.fb_max, e.status[i]);
         }
-        if (fills_failed(f)) {
+        if (f.pend & FILL_FAILED) {
             // a wait ran out: the points this warp holds (the rest of its
-            // chunk or the chunk it took next, and the chunk claimed ahead)
-            // are given up, and it takes no more work
+            // chunk, or the chunk it took next) are given up, and it takes
+            // no more work
             give_up_batch<backward>(table, pre, gn, end < total ? end : total, lane);
-            const int c = collect();
-            give_up_batch<backward>(table, pre, c, c + chunk < total ? c + chunk : total, lane);
             break;
         }
         g = gn;
@@ -1203,3 +1194,4 @@ cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const fl
 }
 
 }  // namespace omt
+

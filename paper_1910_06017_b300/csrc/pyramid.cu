@@ -807,18 +807,17 @@ __device__ __forceinline__ void l0_fix_edges(const LevelArgs &a, int ox, int oy,
     for (int i = t; i < 4 * (L0_BOX_W / 4); i += 32 * L0_CONS) {
         const int k = i / (L0_BOX_W / 4), c = i - k * (L0_BOX_W / 4);
         const int y = k < 2 ? k - 2 : a.h + (k - 2);   // -2, -1, h, h+1
-        const int r = y - y0;
-        if (r < 0 || r >= L0_BOX_H) continue;
-        const int rr = reflect101(y, a.h) - y0;
+        const int r = y - y0, rr = reflect101(y, a.h) - y0;
+        if (r < 0 || r >= L0_BOX_H || rr < 0 || rr >= L0_BOX_H) continue;   // (unread texels)
         ((unsigned *)(st + r * L0_BOX_W))[c] = ((const unsigned *)(st + rr * L0_BOX_W))[c];
     }
     l0_consumers_sync();
     for (int i = t; i < 4 * L0_BOX_H; i += 32 * L0_CONS) {
         const int k = i / L0_BOX_H, r = i - k * L0_BOX_H;
         const int x = k < 2 ? k - 2 : a.w + (k - 2);   // -2, -1, w, w+1
-        const int c = x - x0;
-        if (c < 0 || c >= L0_BOX_W) continue;
-        st[r * L0_BOX_W + c] = st[r * L0_BOX_W + reflect101(x, a.w) - x0];
+        const int c = x - x0, cc = reflect101(x, a.w) - x0;
+        if (c < 0 || c >= L0_BOX_W || cc < 0 || cc >= L0_BOX_W) continue;   // (unread texels)
+        st[r * L0_BOX_W + c] = st[r * L0_BOX_W + cc];
     }
     l0_consumers_sync();
 }
