@@ -299,12 +299,12 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
                    tm, sizeof(tm));
         }
         {
-            alignas(64) CUtensorMap fm;
-            memset(&fm, 0, sizeof(fm));
-            e.frame_map_ok = encode_u8_map(b.frame, P.w, P.h, (int64_t)b.frame_pitch, L0_BOX_W,
-                                           L0_BOX_H, &fm) ? 1u : 0u;
-            memcpy(base + batch_frame_maps_offset(caps->max_streams) + sizeof(CUtensorMap) * (size_t)i,
-                   &fm, sizeof(fm));
+            alignas(64) CUtensorMap pm[OMT_MAX_LEVELS];
+            memset(pm, 0, sizeof(pm));
+            e.pyr_maps_ok = encode_pyramid_maps(b.frame, (int64_t)b.frame_pitch, N, pm);
+            memcpy(base + batch_pyr_maps_offset(caps->max_streams) +
+                       sizeof(CUtensorMap) * (size_t)i * OMT_MAX_LEVELS,
+                   pm, sizeof(pm));
         }
         for (int L = 0; L < prm->levels; ++L)
             pyr_pre[L][i + 1] = pyr_pre[L][i] + pyramid_tiles(P.lv[L].w, P.lv[L].h);

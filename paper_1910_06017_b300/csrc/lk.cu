@@ -1112,10 +1112,13 @@ uint32_t encode_st(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensor
 
 }  // namespace
 
-bool encode_u8_map(const uint8_t *base, int w, int h, int64_t pitch, int box_w, int box_h,
-                   CUtensorMap *out) {
+bool encode_plane_map(const void *base, int esz, int w, int h, int64_t pitch, int box_w, int box_h,
+                      CUtensorMap *out) {
     if (((uintptr_t)base & 15) || (pitch & 15) || w < 1 || h < 1) return false;
-    return encode_2d(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, base, w, h, pitch, box_w, box_h);
+    const CUtensorMapDataType dt = esz == 1   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                              : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+    return encode_2d(out, dt, base, w, h, pitch, box_w, box_h);
 }
 
 uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensorMap *out) {

@@ -112,7 +112,7 @@ struct StreamEntry {
     int32_t *pad_counts;               // scratch: per-box counts
     int32_t w, h, nboxes, maxc;
     uint32_t tm_ok, tm_ok_back;        // bit 3L + m: LK map m of level L (forward, backward) valid
-    uint32_t frame_map_ok;             // the level-0 tile map of frame t+1 is valid
+    uint32_t pyr_maps_ok;              // bit L: the tile map of level L of frame t+1's pyramid
 };
 
 // Tensor maps of the LK window copies, per level: the template frame's
@@ -147,14 +147,15 @@ __host__ __device__ inline size_t batch_maps_offset(int max_streams) {
     return (off + 127) & ~(size_t)127;
 }
 
-// The level-0 tile maps of the frames t+1 follow the LK maps, one per stream.
-__host__ __device__ inline size_t batch_frame_maps_offset(int max_streams) {
+// The pyramid tile maps of the frames t+1 (level 0: the frame; level L:
+// the plane of level L) follow the LK maps, OMT_MAX_LEVELS per stream.
+__host__ __device__ inline size_t batch_pyr_maps_offset(int max_streams) {
     return batch_maps_offset(max_streams) +
            sizeof(CUtensorMap) * (size_t)max_streams * 2 * OMT_MAX_LEVELS * LK_MAPS;
 }
 
 __host__ __device__ inline size_t batch_table_bytes(int max_streams) {
-    return batch_frame_maps_offset(max_streams) + sizeof(CUtensorMap) * (size_t)max_streams;
+    return batch_pyr_maps_offset(max_streams) + sizeof(CUtensorMap) * (size_t)max_streams * OMT_MAX_LEVELS;
 }
 
 struct BatchView {
@@ -171,9 +172,10 @@ struct BatchView {
     __host__ __device__ const StreamEntry &stream(int s) const {
         return ((const StreamEntry *)(base + batch_entries_offset(hdr().max_streams)))[s];
     }
-    // stream s's level-0 tile map of frame t+1
-    __host__ __device__ const CUtensorMap *frame_map(int s) const {
-        return (const CUtensorMap *)(base + batch_frame_maps_offset(hdr().max_streams)) + s;
+    // stream s's tile map of level L of frame t+1's pyramid
+    __host__ __device__ const CUtensorMap *pyr_map(int s, int L) const {
+        return (const CUtensorMap *)(base + batch_pyr_maps_offset(hdr().max_streams)) +
+               (size_t)s * OMT_MAX_LEVELS + L;
     }
     // stream s's LK maps of direction d (0 forward, 1 backward), LK_MAPS per level
     __host__ __device__ const CUtensorMap *maps(int s, int d) const {
@@ -229,11 +231,18 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
 // driver) leaves its bit clear and the kernels copy that level row by row.
 uint32_t encode_lk_maps(const omt_pyramid &P, const omt_pyramid &J, int win, CUtensorMap *out);
 
-// A 2D tensor map of a u8 plane (w x h, pitch bytes apart) read in boxes of
-// box_w x box_h bytes, zero-filled outside; false when the plane's base or
-// pitch is not a multiple of 16 bytes (the map cannot describe it).
-bool encode_u8_map(const uint8_t *base, int w, int h, int64_t pitch, int box_w, int box_h,
-                   CUtensorMap *out);
+// A 2D tensor map of a plane of esz-byte texels (w x h, pitch bytes apart)
+// read in boxes of box_w x box_h texels, zero-filled outside; false when the
+// plane's base or pitch is not a multiple of 16 bytes (the map cannot
+// describe it).
+bool encode_plane_map(const void *base, int esz, int w, int h, int64_t pitch, int box_w, int box_h,
+                      CUtensorMap *out);
+
+// The tensor maps of the pyramid tiles' copies (pyramid.cu) for a frame and
+// the pyramid built from it: out[0] for the frame, out[L] for level L >= 1
+// (up to levels - 1); returns the mask of valid maps (bit L).
+uint32_t encode_pyramid_maps(const uint8_t *frame, int64_t frame_pitch, const omt_pyramid &pyr,
+                             CUtensorMap *out);
 
 // Box of the level-0 pyramid tiles' tensor copies (pyramid.cu): 16 columns
 // either side of a 128-column tile (the copy's x must be a multiple of 16

@@ -1,18 +1,17 @@
 // pyramid.cu -- K1: Gaussian pyramid and Scharr gradients (Section V-A,
 // preprocessing).
 //
-// One launch per level L; CTAs stride over 128x32 tiles of level L (of every
-// stream, in the batched form), two tiles in flight per CTA.  A tile is staged in shared memory with
-// 16-byte cp.async copies of its rows plus a 2-texel reflect-101 halo
-// (rounded out to 16-byte chunks; chunks that cross the frame edge are
-// filled texel by texel through the reflect-101 map) in its stored format:
-// u8, half or float.  Each thread then owns 4 adjacent columns and 4
-// consecutive rows of the tile: it reads the 7 staged rows it needs (3-4
-// 32-bit, 64-bit or 128-bit shared loads per row, conflict-free), forms the
-// horizontal Scharr difference and smoothing and the horizontal binomial sums
-// in registers, combines them vertically, and stores 4 gradient pairs per
-// row with one 16-byte (F16) or two (F32) stores, 2 texels of level L+1 at
-// each of its two even rows, and at level 0 the u8 copy of its 4x4 texels.
+// One launch per level L; each CTA streams 128x32 tiles of level L (of every
+// stream, in the batched form) through a ring of staged tiles in shared
+// memory (tile_ring): a producer warp copies a tile and its halo (2 rows,
+// and on the left the texels up to a 16-byte boundary) by one 2D tensor
+// copy per tile, four consumer warps compute it.  Each consumer thread owns
+// 4 adjacent columns and 8 consecutive rows of the tile: it reads the 11
+// staged rows it needs, forms the horizontal Scharr difference and
+// smoothing and the horizontal binomial sums, combines them vertically, and
+// stores 4 gradient pairs per row, 2 texels of level L+1 at each even row,
+// and at level 0 the u8 copy.  Level 0 (u8) computes on pairs of pixels in
+// the halves of 32-bit registers (SWAR).
 //
 // Exactness: the Scharr weights 3/32 and 10/32 and the integer binomial
 // weights with a final 1/256 keep every value that is dyadic-exact in FP32
@@ -47,7 +46,6 @@ struct Stage {
     // staged columns start at the 16-byte boundary at or below column ox-4
     static constexpr int LEAD = FMT == FMT_U8 ? 16 : (FMT == FMT_H16 ? 8 : 4);  // texels before ox
     static constexpr int RB = ((LEAD + TX + 4) * ESZ + 15) / 16 * 16;            // bytes per staged row
-    static constexpr int BYTES = SROWS * RB;
 };
 
 struct LevelArgs {
@@ -69,44 +67,11 @@ struct LevelArgs {
 // Fixed-point fraction bits for the sums over level L (see the header).
 __host__ __device__ __forceinline__ int level_frac(int L) { return L < 2 ? 0 : (L > 5 ? 40 : 8 * L); }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
 template <int FMT>
 __device__ __forceinline__ float texel_value(unsigned bits) {
     if (FMT == FMT_U8) return (float)bits;
     if (FMT == FMT_H16) return __half2float(__ushort_as_half((unsigned short)bits)) + 128.0f;
     return __uint_as_float(bits);
-}
-
-// Start staging level rows oy-2 .. oy+TY+1, columns from ox-LEAD, into st
-// (one cp.async group per thread; chunks crossing the frame edge are
-// written directly).
-template <int FMT>
-__device__ __forceinline__ void stage_tile(const LevelArgs &a, int ox, int oy, uint8_t *st) {
-    using S = Stage<FMT>;
-    constexpr int NCH = S::RB / 16, PER = 16 / S::ESZ;  // chunks per row, texels per chunk
-    const int c_first = ox - S::LEAD;
-    for (int k = threadIdx.x; k < SROWS * NCH; k += NT) {
-        const int r = k / NCH, c = k - r * NCH;
-        const uint8_t *row = a.src + (int64_t)reflect101(oy - 2 + r, a.h) * a.src_pitch;
-        const int col0 = c_first + c * PER;
-        uint8_t *dst = st + r * S::RB + 16 * c;
-        if (a.vec_ok && col0 >= 0 && col0 + PER <= a.w) {
-            cp_async16(dst, row + (int64_t)col0 * S::ESZ);
-        } else {
-#pragma unroll
-            for (int e = 0; e < PER; ++e) {
-                const int col = reflect101(col0 + e, a.w);
-                if (FMT == FMT_U8) dst[e] = row[col];
-                else if (FMT == FMT_H16) ((unsigned short *)dst)[e] = ((const unsigned short *)row)[col];
-                else ((unsigned *)dst)[e] = ((const unsigned *)row)[col];
-            }
-        }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
 // Values of tile columns 4g-2 .. 4g+5 of staged row r.
@@ -316,10 +281,11 @@ __device__ __forceinline__ void compute_tile_u8(const LevelArgs &a, int ox, int 
 }
 
 // This thread's share of the staged 128x32 tile of level L at (ox, oy).
-template <int ST, int FMT>
-__device__ __forceinline__ void compute_tile(const LevelArgs &a, int ox, int oy, const uint8_t *st) {
+template <int ST, int FMT, int RPT = omt::RPT>
+__device__ __forceinline__ void compute_tile(const LevelArgs &a, int ox, int oy, const uint8_t *st,
+                                             int q = threadIdx.x >> 5) {
     const int g = threadIdx.x & 31;   // columns 4g .. 4g+3 of the tile
-    const int q = threadIdx.x >> 5;   // rows RPT q .. RPT q + RPT-1 of the tile
+    // q: rows RPT q .. RPT q + RPT-1 of the tile
     const int x = ox + 4 * g;
     if (x >= a.w) return;
     const int y0 = oy + RPT * q;
@@ -422,11 +388,10 @@ __device__ __forceinline__ void store_grads_fixed(const LevelArgs &a, int y, int
 }
 
 // compute_tile with the sums in 64-bit fixed point (levels >= 2).
-template <int ST, int FMT>
+template <int ST, int FMT, int RPT = omt::RPT>
 __device__ __forceinline__ void compute_tile_fixed(const LevelArgs &a, int ox, int oy,
-                                                   const uint8_t *st) {
+                                                   const uint8_t *st, int q = threadIdx.x >> 5) {
     const int g = threadIdx.x & 31;
-    const int q = threadIdx.x >> 5;
     const int x = ox + 4 * g;
     if (x >= a.w) return;
     const int y0 = oy + RPT * q;
@@ -518,11 +483,10 @@ __device__ __forceinline__ void staged_row_split(const uint8_t *st, int r, int g
 }
 
 // compute_tile with every sum formed on the hi and lo parts (levels 2-3).
-template <int ST, int FMT>
+template <int ST, int FMT, int RPT = omt::RPT>
 __device__ __forceinline__ void compute_tile_split(const LevelArgs &a, int ox, int oy,
-                                                   const uint8_t *st) {
+                                                   const uint8_t *st, int q = threadIdx.x >> 5) {
     const int g = threadIdx.x & 31;
-    const int q = threadIdx.x >> 5;
     const int x = ox + 4 * g;
     if (x >= a.w) return;
     const int y0 = oy + RPT * q;
@@ -574,60 +538,6 @@ __device__ __forceinline__ void compute_tile_split(const LevelArgs &a, int ox, i
     }
 }
 
-// A tile to process: its level arguments and origin.
-struct Tile {
-    LevelArgs a;
-    int ox, oy;
-};
-
-// The CTA's tiles g = blockIdx.x, += gridDim.x, < total, two at a time in
-// flight: while the CTA computes tile g from one shared buffer, the copies
-// of the next tile land in the other.  resolve(g, Tile&) names a tile
-// (thread 0 only; the result is shared through a ring of three slots, so
-// the slot being written is never one that a thread may still read: slot
-// i % 3 serves the CTA's i-th tile, written at the top of trip i - 1 and
-// read until the end of trip i, and trip i + 1 writes slot (i + 2) % 3).
-template <int ST, int FMT, int PATH, typename Resolve>
-__device__ __forceinline__ void tile_pipeline(int total, Resolve resolve) {
-    extern __shared__ __align__(16) uint8_t pyr_smem[];
-    uint8_t *st[2] = {pyr_smem, pyr_smem + Stage<FMT>::BYTES};
-    __shared__ Tile tl[3];
-    int g = blockIdx.x;
-    if (g >= total) return;
-    if (threadIdx.x == 0) resolve(g, tl[0]);
-    __syncthreads();
-    stage_tile<FMT>(tl[0].a, tl[0].ox, tl[0].oy, st[0]);
-    int i = 0;  // this CTA's tile count
-    for (; g < total; g += gridDim.x, ++i) {
-        const int gn = g + gridDim.x;
-        const int cur = i % 3, nxt = (i + 1) % 3, b = i & 1;
-        if (threadIdx.x == 0 && gn < total) resolve(gn, tl[nxt]);
-        __syncthreads();  // tl[nxt] is set; every thread is done with st[b ^ 1]
-        if (gn < total) {
-            stage_tile<FMT>(tl[nxt].a, tl[nxt].ox, tl[nxt].oy, st[b ^ 1]);
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        }
-        __syncthreads();  // tile g is staged by every thread
-        if constexpr (FMT == FMT_U8) compute_tile_u8<ST>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
-        else if constexpr (PATH == PATH_INT64) compute_tile_fixed<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
-        else if constexpr (PATH == PATH_SPLIT) compute_tile_split<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
-        else compute_tile<ST, FMT>(tl[cur].a, tl[cur].ox, tl[cur].oy, st[b]);
-    }
-}
-
-template <int ST, int FMT, int PATH>
-__global__ void __launch_bounds__(NT) pyramid_level_kernel(const LevelArgs a, int tiles_x,
-                                                           int total) {
-    tile_pipeline<ST, FMT, PATH>(total, [&](int g, Tile &t) {
-        const int ty = g / tiles_x, tx = g - ty * tiles_x;
-        t.a = a;
-        t.ox = tx * TX;
-        t.oy = ty * TY;
-    });
-}
-
 // Arguments of level L of the pyramid a batch entry builds (frame t+1).
 __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int L, int levels,
                                                       LevelArgs &a) {
@@ -663,274 +573,267 @@ __device__ __forceinline__ void level_args_from_entry(const StreamEntry &e, int 
     }
 }
 
-// Level L of every stream of a batch: the CTAs stride over the batch's
-// tiles (tile prefix per stream in the table).
-// Shared memory of a batch launch: the two staging buffers, then every
-// stream's level arguments and the tile prefix (copied from the table once
-// per CTA, so that naming a tile reads no global memory).
+// -------------------------------------------------------------- TMA ring
+// Every level streams through a ring of RING_STAGES staged tiles per CTA:
+// one producer warp copies each 128 x 32 tile with its halo (Stage<FMT>'s
+// box: LEAD texels left, 2 rows above, RB bytes x SROWS rows) global ->
+// shared by one 2D tensor copy, whose completion the stage's "full"
+// mbarrier counts; four consumer warps compute the tile (8 rows each) and
+// release the stage on its "empty" mbarrier.  No CTA-wide barrier in the
+// steady state: the producer runs up to RING_STAGES tiles ahead.  A plane
+// without a tensor map (a frame whose base or pitch is not 16-byte aligned)
+// is copied by the producer warp's plain loads instead.  Outside the plane
+// the copy holds zeros; tiles at the plane's edge replace the halo texels
+// that outputs read by their reflect-101 images (rows, then columns) before
+// computing.  Every wait gives up after one second (counted in
+// pyr_wait_timeouts), and a CTA whose wait ran out stops, after landing its
+// copies in flight.
+constexpr int RING_STAGES = 4;
+constexpr int RING_CONS = 4;                    // consumer warps
+constexpr int RING_NT = 32 * (RING_CONS + 1);   // and the producer warp
+constexpr int RING_RPT = TY / RING_CONS;        // rows per consumer thread
+constexpr unsigned long long RING_WAIT_NS = 1000000000ull;
+static_assert(L0_BOX_W == Stage<FMT_U8>::RB && L0_BOX_H == SROWS, "the level-0 box is a staged tile");
+
 template <int FMT>
-__host__ __device__ constexpr size_t batch_smem_bytes(int max_streams) {
-    return 2 * (size_t)Stage<FMT>::BYTES + (size_t)max_streams * sizeof(LevelArgs) +
-           ((size_t)max_streams + 1) * sizeof(int);
-}
+struct Ring {
+    static constexpr int ESZ = Stage<FMT>::ESZ;
+    static constexpr int LEAD = Stage<FMT>::LEAD;
+    static constexpr int RB = Stage<FMT>::RB;            // bytes per staged row
+    static constexpr int BOX_W = RB / ESZ;                // texels per staged row
+    static constexpr unsigned TILE = (unsigned)RB * SROWS;
+    static_assert(TILE % 128 == 0, "stages on 128-byte boundaries");
+};
 
-template <int ST, int FMT, int PATH>
-__global__ void __launch_bounds__(NT) pyramid_batch_kernel(const uint8_t *table, int L) {
-    extern __shared__ __align__(16) uint8_t pyr_smem[];
-    const BatchView t(table);
-    const int ns = t.nstreams();
-    LevelArgs *sa = (LevelArgs *)(pyr_smem + 2 * (size_t)Stage<FMT>::BYTES);
-    int *spre = (int *)(sa + t.hdr().max_streams);
-    for (int i = threadIdx.x; i < ns; i += NT) level_args_from_entry(t.stream(i), L, t.levels(), sa[i]);
-    for (int i = threadIdx.x; i <= ns; i += NT) spre[i] = t.pyr_prefix(L)[i];
-    __syncthreads();
-    const int total = spre[ns];
-    tile_pipeline<ST, FMT, PATH>(total, [&](int g, Tile &tile) {
-        const int si = find_segment(spre, ns, g);
-        tile.a = sa[si];
-        const int tiles_x = (tile.a.w + TX - 1) / TX;
-        const int local = g - spre[si];
-        const int ty = local / tiles_x, tx = local - ty * tiles_x;
-        tile.ox = tx * TX;
-        tile.oy = ty * TY;
-    });
-}
-
-// ------------------------------------------------------ level 0, TMA ring
-// Level 0 (the u8 frame: the pyramid's bulk) streams through a ring of
-// L0_STAGES staged tiles per CTA: one producer warp copies each 128 x 32
-// tile with its halo (the L0_BOX_W x L0_BOX_H box) global -> shared by one
-// 2D tensor copy, whose completion the stage's "full" mbarrier counts; four
-// consumer warps compute the tile (8 rows each, in SWAR) and release the
-// stage on its "empty" mbarrier.  No CTA-wide barrier in the steady state:
-// the producer runs up to L0_STAGES tiles ahead.  A frame whose base or
-// pitch is not 16-byte aligned (no tensor map) is copied by the producer
-// warp's plain loads instead.  Outside the frame the copy holds zeros;
-// tiles at the frame's edge replace the halo texels that outputs read by
-// their reflect-101 images (rows, then columns) before computing.  Every
-// wait gives up after one second (counted in pyr_wait_timeouts), and a CTA
-// whose wait ran out stops, after landing its copies in flight.
-constexpr int L0_STAGES = 4;
-constexpr int L0_CONS = 4;                  // consumer warps
-constexpr int L0_NT = 32 * (L0_CONS + 1);   // and the producer warp
-constexpr int L0_RPT = TY / L0_CONS;        // rows per consumer thread
-constexpr unsigned L0_TILE_BYTES = L0_BOX_W * L0_BOX_H;
-static_assert(L0_BOX_W == Stage<FMT_U8>::RB && L0_BOX_H == SROWS, "a ring stage is a staged tile");
-static_assert(L0_TILE_BYTES % 128 == 0, "stages on 128-byte boundaries");
-constexpr unsigned long long L0_WAIT_NS = 1000000000ull;
-
-__device__ unsigned pyr_wait_timeouts;
-
-struct L0Ring {
-    uint8_t tile[L0_STAGES][L0_TILE_BYTES];
-    uint64_t full[L0_STAGES], empty[L0_STAGES];
+struct RingBars {
+    uint64_t full[RING_STAGES], empty[RING_STAGES];
     int ok[2];   // consumers: tile k's stage landed, in slot k & 1 (set by thread 0)
 };
 
-__device__ __forceinline__ unsigned l0_smem(const void *p) {
+template <int FMT>
+__host__ __device__ constexpr size_t ring_bytes() {
+    return (size_t)RING_STAGES * Ring<FMT>::TILE + sizeof(RingBars);
+}
+
+__device__ unsigned pyr_wait_timeouts;
+
+__device__ __forceinline__ unsigned ring_smem(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ bool l0_try_wait(const uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool ring_try_wait(const uint64_t *bar, unsigned parity) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(l0_smem(bar)), "r"(parity)
+        : "r"(ring_smem(bar)), "r"(parity)
         : "memory");
     return done != 0;
 }
-__device__ __forceinline__ unsigned long long l0_ns() {
+__device__ __forceinline__ unsigned long long ring_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
     return t;
 }
 // One thread's bounded wait for the phase of parity `parity` to complete.
-__device__ __forceinline__ bool l0_wait(const uint64_t *bar, unsigned parity) {
-    if (l0_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = l0_ns();
-    while (!l0_try_wait(bar, parity))
-        if (l0_ns() - t0 > L0_WAIT_NS) {
+__device__ __forceinline__ bool ring_wait(const uint64_t *bar, unsigned parity) {
+    if (ring_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = ring_ns();
+    while (!ring_try_wait(bar, parity))
+        if (ring_ns() - t0 > RING_WAIT_NS) {
             atomicAdd(&pyr_wait_timeouts, 1u);
             return false;
         }
     return true;
 }
-__device__ __forceinline__ void l0_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(l0_smem(bar)) : "memory");
+__device__ __forceinline__ void ring_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(ring_smem(bar)) : "memory");
 }
-__device__ __forceinline__ void l0_consumers_sync() {
-    asm volatile("bar.sync 1, %0;\n" ::"n"(32 * L0_CONS) : "memory");
+__device__ __forceinline__ void ring_consumers_sync() {
+    asm volatile("bar.sync 1, %0;\n" ::"n"(32 * RING_CONS) : "memory");
 }
 
 // The producer warp fills stage `st` with the box of tile (ox, oy): by the
-// tensor map, or (no map) by plain loads, zero outside the frame.
-__device__ __forceinline__ void l0_fill(const LevelArgs &a, const CUtensorMap *map, int ox, int oy,
-                                        uint8_t *st, uint64_t *full, int lane) {
+// tensor map, or (no map) by plain loads, zero outside the plane.
+template <int FMT>
+__device__ __forceinline__ void ring_fill(const LevelArgs &a, const CUtensorMap *map, int ox, int oy,
+                                          uint8_t *st, uint64_t *full, int lane) {
+    using RG = Ring<FMT>;
     if (map) {
         if (lane == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(l0_smem(full)),
-                         "r"(L0_TILE_BYTES)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ring_smem(full)),
+                         "r"(RG::TILE)
                          : "memory");
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(l0_smem(st)),
-                "l"((unsigned long long)map), "r"(ox - 16), "r"(oy - 2), "r"(l0_smem(full))
+                " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(ring_smem(st)),
+                "l"((unsigned long long)map), "r"(ox - RG::LEAD), "r"(oy - 2), "r"(ring_smem(full))
                 : "memory");
         }
         return;
     }
-    for (int i = lane; i < L0_BOX_H * (L0_BOX_W / 4); i += 32) {
-        const int r = i / (L0_BOX_W / 4), c = i - r * (L0_BOX_W / 4);
-        const int y = oy - 2 + r, x = ox - 16 + 4 * c;
-        unsigned v = 0;
-        if (y >= 0 && y < a.h) {
-            const uint8_t *row = a.src + (int64_t)y * a.src_pitch;
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (x + b >= 0 && x + b < a.w) v |= (unsigned)row[x + b] << (8 * b);
-        }
-        *(unsigned *)(st + r * L0_BOX_W + 4 * c) = v;
+    for (int i = lane; i < SROWS * RG::BOX_W; i += 32) {
+        const int r = i / RG::BOX_W, c = i - r * RG::BOX_W;
+        const int y = oy - 2 + r, x = ox - RG::LEAD + c;
+        const bool in = y >= 0 && y < a.h && x >= 0 && x < a.w;
+        const uint8_t *src = a.src + (int64_t)(in ? y : 0) * a.src_pitch + (int64_t)(in ? x : 0) * RG::ESZ;
+        uint8_t *dst = st + r * RG::RB + c * RG::ESZ;
+        if (RG::ESZ == 1) *dst = in ? *src : 0;
+        else if (RG::ESZ == 2) *(unsigned short *)dst = in ? *(const unsigned short *)src : 0;
+        else *(unsigned *)dst = in ? *(const unsigned *)src : 0u;
     }
     __threadfence_block();
     __syncwarp();
-    if (lane == 0) l0_arrive(full);
+    if (lane == 0) ring_arrive(full);
 }
 
 // Halo texels of an edge tile that outputs read (rows -2, -1, h, h+1 and
 // columns -2, -1, w, w+1) take their reflect-101 images from inside the
 // box: rows first, then columns (so corners reflect both ways).  The four
-// consumer warps share the work; the box's rows and columns stay in range
-// for every nonempty tile.
-__device__ __forceinline__ void l0_fix_edges(const LevelArgs &a, int ox, int oy, uint8_t *st, int t) {
-    const int y0 = oy - 2, x0 = ox - 16;
-    for (int i = t; i < 4 * (L0_BOX_W / 4); i += 32 * L0_CONS) {
-        const int k = i / (L0_BOX_W / 4), c = i - k * (L0_BOX_W / 4);
+// consumer warps share the work; sources outside the box are never read
+// texels, and are skipped.
+template <int FMT>
+__device__ __forceinline__ void ring_fix_edges(const LevelArgs &a, int ox, int oy, uint8_t *st, int t) {
+    using RG = Ring<FMT>;
+    const int y0 = oy - 2, x0 = ox - RG::LEAD;
+    for (int i = t; i < 4 * (RG::RB / 4); i += 32 * RING_CONS) {
+        const int k = i / (RG::RB / 4), c = i - k * (RG::RB / 4);
         const int y = k < 2 ? k - 2 : a.h + (k - 2);   // -2, -1, h, h+1
         const int r = y - y0, rr = reflect101(y, a.h) - y0;
-        if (r < 0 || r >= L0_BOX_H || rr < 0 || rr >= L0_BOX_H) continue;   // (unread texels)
-        ((unsigned *)(st + r * L0_BOX_W))[c] = ((const unsigned *)(st + rr * L0_BOX_W))[c];
+        if (r < 0 || r >= SROWS || rr < 0 || rr >= SROWS) continue;
+        ((unsigned *)(st + r * RG::RB))[c] = ((const unsigned *)(st + rr * RG::RB))[c];
     }
-    l0_consumers_sync();
-    for (int i = t; i < 4 * L0_BOX_H; i += 32 * L0_CONS) {
-        const int k = i / L0_BOX_H, r = i - k * L0_BOX_H;
+    ring_consumers_sync();
+    for (int i = t; i < 4 * SROWS; i += 32 * RING_CONS) {
+        const int k = i / SROWS, r = i - k * SROWS;
         const int x = k < 2 ? k - 2 : a.w + (k - 2);   // -2, -1, w, w+1
         const int c = x - x0, cc = reflect101(x, a.w) - x0;
-        if (c < 0 || c >= L0_BOX_W || cc < 0 || cc >= L0_BOX_W) continue;   // (unread texels)
-        st[r * L0_BOX_W + c] = st[r * L0_BOX_W + cc];
+        if (c < 0 || c >= RG::BOX_W || cc < 0 || cc >= RG::BOX_W) continue;
+        uint8_t *row = st + r * RG::RB;
+        if (RG::ESZ == 1) row[c] = row[cc];
+        else if (RG::ESZ == 2) ((unsigned short *)row)[c] = ((const unsigned short *)row)[cc];
+        else ((unsigned *)row)[c] = ((const unsigned *)row)[cc];
     }
-    l0_consumers_sync();
+    ring_consumers_sync();
 }
 
 // The ring over the CTA's tiles g = blockIdx.x, += gridDim.x, < total;
-// resolve(g, args, ox, oy, map) names a tile (map: its frame's tensor map or
-// null) and is called by every thread for every tile.
-template <int ST, typename Resolve>
-__device__ __forceinline__ void l0_ring(L0Ring &R, int total, Resolve resolve) {
+// resolve(g, args, ox, oy, map) names a tile (map: its plane's tensor map
+// or null) and is called by every thread for every tile.
+template <int ST, int FMT, int PATH, typename Resolve>
+__device__ __forceinline__ void tile_ring(uint8_t *smem, int total, Resolve resolve) {
+    using RG = Ring<FMT>;
+    RingBars &R = *(RingBars *)(smem + (size_t)RING_STAGES * RG::TILE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < L0_STAGES; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(l0_smem(&R.full[s])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(l0_smem(&R.empty[s])),
-                         "r"(L0_CONS)
+        for (int s = 0; s < RING_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ring_smem(&R.full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(ring_smem(&R.empty[s])),
+                         "r"(RING_CONS)
                          : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    if (warp == L0_CONS) {
+    if (warp == RING_CONS) {
         // producer
         int k = 0;
         for (int g = blockIdx.x; g < total; g += gridDim.x, ++k) {
-            const int s = k % L0_STAGES;
-            if (k >= L0_STAGES) {
+            const int s = k % RING_STAGES;
+            if (k >= RING_STAGES) {
                 bool ok = true;
-                if (lane == 0) ok = l0_wait(&R.empty[s], ((k / L0_STAGES) - 1) & 1);
+                if (lane == 0) ok = ring_wait(&R.empty[s], ((k / RING_STAGES) - 1) & 1);
                 if (!__shfl_sync(FULL_MASK, ok, 0)) break;
             }
             LevelArgs a;
             int ox, oy;
             const CUtensorMap *map;
             resolve(g, a, ox, oy, map);
-            l0_fill(a, map, ox, oy, R.tile[s], &R.full[s], lane);
+            ring_fill<FMT>(a, map, ox, oy, smem + (size_t)s * RG::TILE, &R.full[s], lane);
         }
         // land the copies still in flight (bounded) before the CTA exits
         if (lane == 0)
-            for (int j = k - L0_STAGES > 0 ? k - L0_STAGES : 0; j < k; ++j)
-                l0_wait(&R.full[j % L0_STAGES], (j / L0_STAGES) & 1);
+            for (int j = k - RING_STAGES > 0 ? k - RING_STAGES : 0; j < k; ++j)
+                ring_wait(&R.full[j % RING_STAGES], (j / RING_STAGES) & 1);
         return;
     }
-    // consumers: warp 0 lane 0 waits for each stage, the four warps follow
+    // consumers: thread 0 waits for each stage, the four warps follow
     int k = 0;
     for (int g = blockIdx.x; g < total; g += gridDim.x, ++k) {
-        const int s = k % L0_STAGES;
+        const int s = k % RING_STAGES;
         // two slots: thread 0 writes tile k+1's only after every consumer
         // has passed tile k's barrier, i.e. read tile k's
-        if (threadIdx.x == 0) R.ok[k & 1] = l0_wait(&R.full[s], (k / L0_STAGES) & 1);
-        l0_consumers_sync();
+        if (threadIdx.x == 0) R.ok[k & 1] = ring_wait(&R.full[s], (k / RING_STAGES) & 1);
+        ring_consumers_sync();
         if (!R.ok[k & 1]) break;
         LevelArgs a;
         int ox, oy;
         const CUtensorMap *map;
         resolve(g, a, ox, oy, map);
-        uint8_t *st = R.tile[s];
+        uint8_t *st = smem + (size_t)s * RG::TILE;
         if (ox == 0 || oy == 0 || ox + TX + 2 > a.w || oy + TY + 2 > a.h) {
-            l0_fix_edges(a, ox, oy, st, threadIdx.x);
+            ring_fix_edges<FMT>(a, ox, oy, st, threadIdx.x);
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // before the next copy
         }
-        compute_tile_u8<ST, L0_RPT>(a, ox, oy, st, warp);
+        if constexpr (FMT == FMT_U8) compute_tile_u8<ST, RING_RPT>(a, ox, oy, st, warp);
+        else if constexpr (PATH == PATH_INT64) compute_tile_fixed<ST, FMT, RING_RPT>(a, ox, oy, st, warp);
+        else if constexpr (PATH == PATH_SPLIT) compute_tile_split<ST, FMT, RING_RPT>(a, ox, oy, st, warp);
+        else compute_tile<ST, FMT, RING_RPT>(a, ox, oy, st, warp);
         __syncwarp();
-        if (lane == 0) l0_arrive(&R.empty[s]);
+        if (lane == 0) ring_arrive(&R.empty[s]);
     }
 }
 
-template <int ST>
-__global__ void __launch_bounds__(L0_NT) pyramid_l0_kernel(const LevelArgs a, int tiles_x, int total,
-                                                           const __grid_constant__ CUtensorMap map,
-                                                           int map_ok) {
-    extern __shared__ __align__(128) uint8_t l0_smem_raw[];
-    L0Ring &R = *(L0Ring *)l0_smem_raw;
-    l0_ring<ST>(R, total, [&](int g, LevelArgs &t, int &ox, int &oy, const CUtensorMap *&m) {
-        const int ty = g / tiles_x, tx = g - ty * tiles_x;
-        t = a;
-        ox = tx * TX;
-        oy = ty * TY;
-        m = map_ok ? &map : nullptr;
-    });
+// One level of one frame (plain call).
+template <int ST, int FMT, int PATH>
+__global__ void __launch_bounds__(RING_NT) pyramid_level_kernel(const LevelArgs a, int tiles_x, int total,
+                                                                const __grid_constant__ CUtensorMap map,
+                                                                int map_ok) {
+    extern __shared__ __align__(128) uint8_t ring_smem_raw[];
+    tile_ring<ST, FMT, PATH>(ring_smem_raw, total,
+                             [&](int g, LevelArgs &t, int &ox, int &oy, const CUtensorMap *&m) {
+                                 const int ty = g / tiles_x, tx = g - ty * tiles_x;
+                                 t = a;
+                                 ox = tx * TX;
+                                 oy = ty * TY;
+                                 m = map_ok ? &map : nullptr;
+                             });
 }
 
-// The batch form: every stream's level-0 arguments, tile prefix and map
-// flag are copied into shared memory once per CTA.
-__host__ __device__ constexpr size_t l0_batch_smem_bytes(int max_streams) {
-    return sizeof(L0Ring) + (size_t)max_streams * sizeof(LevelArgs) +
+// Level L of every stream of a batch: every stream's level arguments, tile
+// prefix and map flag are copied into shared memory once per CTA, so
+// naming a tile reads no global memory.
+template <int FMT>
+__host__ __device__ constexpr size_t batch_smem_bytes(int max_streams) {
+    return ring_bytes<FMT>() + (size_t)max_streams * sizeof(LevelArgs) +
            ((size_t)max_streams + 1) * sizeof(int) + (size_t)max_streams * sizeof(int);
 }
 
-template <int ST>
-__global__ void __launch_bounds__(L0_NT) pyramid_l0_batch_kernel(const uint8_t *table) {
-    extern __shared__ __align__(128) uint8_t l0_smem_raw[];
-    L0Ring &R = *(L0Ring *)l0_smem_raw;
+template <int ST, int FMT, int PATH>
+__global__ void __launch_bounds__(RING_NT) pyramid_batch_kernel(const uint8_t *table, int L) {
+    extern __shared__ __align__(128) uint8_t ring_smem_raw[];
     const BatchView t(table);
     const int ns = t.nstreams(), cap = t.hdr().max_streams;
-    LevelArgs *sa = (LevelArgs *)(l0_smem_raw + sizeof(L0Ring));
+    LevelArgs *sa = (LevelArgs *)(ring_smem_raw + ring_bytes<FMT>());
     int *spre = (int *)(sa + cap);
     int *sok = spre + cap + 1;
-    for (int i = threadIdx.x; i < ns; i += L0_NT) {
-        level_args_from_entry(t.stream(i), 0, t.levels(), sa[i]);
-        sok[i] = (int)t.stream(i).frame_map_ok;
+    for (int i = threadIdx.x; i < ns; i += RING_NT) {
+        level_args_from_entry(t.stream(i), L, t.levels(), sa[i]);
+        sok[i] = (int)((t.stream(i).pyr_maps_ok >> L) & 1u);
     }
-    for (int i = threadIdx.x; i <= ns; i += L0_NT) spre[i] = t.pyr_prefix(0)[i];
+    for (int i = threadIdx.x; i <= ns; i += RING_NT) spre[i] = t.pyr_prefix(L)[i];
     __syncthreads();
-    l0_ring<ST>(R, spre[ns], [&](int g, LevelArgs &a, int &ox, int &oy, const CUtensorMap *&m) {
-        const int si = find_segment(spre, ns, g);
-        a = sa[si];
-        const int tiles_x = (a.w + TX - 1) / TX;
-        const int local = g - spre[si];
-        const int ty = local / tiles_x, tx = local - ty * tiles_x;
-        ox = tx * TX;
-        oy = ty * TY;
-        m = sok[si] ? t.frame_map(si) : nullptr;
-    });
+    tile_ring<ST, FMT, PATH>(ring_smem_raw, spre[ns],
+                             [&](int g, LevelArgs &a, int &ox, int &oy, const CUtensorMap *&m) {
+                                 const int si = find_segment(spre, ns, g);
+                                 a = sa[si];
+                                 const int tiles_x = (a.w + TX - 1) / TX;
+                                 const int local = g - spre[si];
+                                 const int ty = local / tiles_x, tx = local - ty * tiles_x;
+                                 ox = tx * TX;
+                                 oy = ty * TY;
+                                 m = sok[si] ? t.pyr_map(si, L) : nullptr;
+                             });
 }
 
 // CTAs for `tiles` tiles: at most the number resident on the device at
@@ -940,7 +843,7 @@ __global__ void __launch_bounds__(L0_NT) pyramid_l0_batch_kernel(const uint8_t *
 // CTAs and of that limit, per device.
 template <typename K>
 cudaError_t grid_for(K kernel, int tiles, size_t smem, int *cap, size_t *cap_smem, int &grid,
-                     int nt = NT) {
+                     int nt) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -959,17 +862,12 @@ cudaError_t grid_for(K kernel, int tiles, size_t smem, int *cap, size_t *cap_sme
     return cudaSuccess;
 }
 
-template <int ST, int FMT, int PATH>
-cudaError_t launch_level_k(const LevelArgs &a, cudaStream_t s) {
-    const int tiles_x = (a.w + TX - 1) / TX, total = tiles_x * ((a.h + TY - 1) / TY);
-    const size_t smem = 2 * (size_t)Stage<FMT>::BYTES;
-    static int cap[64] = {0};
-    static size_t cap_smem[64] = {0};
-    int grid = 0;
-    cudaError_t e = grid_for(pyramid_level_kernel<ST, FMT, PATH>, total, smem, cap, cap_smem, grid);
-    if (e != cudaSuccess) return e;
-    pyramid_level_kernel<ST, FMT, PATH><<<grid, NT, smem, s>>>(a, tiles_x, total);
-    return cudaGetLastError();
+bool encode_level_map(const uint8_t *base, int esz, int w, int h, int64_t pitch, CUtensorMap *out) {
+    switch (esz) {
+        case 1: return encode_plane_map(base, 1, w, h, pitch, Ring<FMT_U8>::BOX_W, SROWS, out);
+        case 2: return encode_plane_map(base, 2, w, h, pitch, Ring<FMT_H16>::BOX_W, SROWS, out);
+        default: return encode_plane_map(base, 4, w, h, pitch, Ring<FMT_F32>::BOX_W, SROWS, out);
+    }
 }
 
 // Level 0 reads the u8 frame; level 1 sums in FP32 (exact); levels 2-3
@@ -979,31 +877,28 @@ __host__ __device__ __forceinline__ int level_path(int frac) {
     return frac == 0 ? PATH_FLOAT : (frac <= 24 ? PATH_SPLIT : PATH_INT64);
 }
 
-template <int ST>
-cudaError_t launch_l0(const LevelArgs &a, cudaStream_t s) {
+template <int ST, int FMT, int PATH>
+cudaError_t launch_level_k(const LevelArgs &a, cudaStream_t s) {
     const int tiles_x = (a.w + TX - 1) / TX, total = tiles_x * ((a.h + TY - 1) / TY);
     alignas(64) CUtensorMap map;
     memset(&map, 0, sizeof(map));
-    const int map_ok = encode_u8_map(a.src, a.w, a.h, a.src_pitch, L0_BOX_W, L0_BOX_H, &map) ? 1 : 0;
+    const int map_ok = encode_level_map(a.src, Ring<FMT>::ESZ, a.w, a.h, a.src_pitch, &map) ? 1 : 0;
+    const size_t smem = ring_bytes<FMT>();
     static int cap[64] = {0};
     static size_t cap_smem[64] = {0};
     int grid = 0;
-    cudaError_t e = grid_for(pyramid_l0_kernel<ST>, total, sizeof(L0Ring), cap, cap_smem, grid, L0_NT);
+    cudaError_t e = grid_for(pyramid_level_kernel<ST, FMT, PATH>, total, smem, cap, cap_smem, grid, RING_NT);
     if (e != cudaSuccess) return e;
-    pyramid_l0_kernel<ST><<<grid, L0_NT, sizeof(L0Ring), s>>>(a, tiles_x, total, map, map_ok);
+    pyramid_level_kernel<ST, FMT, PATH><<<grid, RING_NT, smem, s>>>(a, tiles_x, total, map, map_ok);
     return cudaGetLastError();
 }
 
 template <int ST, int FMT>
 cudaError_t launch_level(const LevelArgs &a, cudaStream_t s) {
-    if constexpr (FMT == FMT_U8) {
-        return launch_l0<ST>(a, s);
-    } else {
-        switch (level_path(a.frac)) {
-            case PATH_SPLIT: return launch_level_k<ST, FMT, PATH_SPLIT>(a, s);
-            case PATH_INT64: return launch_level_k<ST, FMT, PATH_INT64>(a, s);
-            default: return launch_level_k<ST, FMT, PATH_FLOAT>(a, s);
-        }
+    switch (FMT == FMT_U8 ? PATH_FLOAT : level_path(a.frac)) {
+        case PATH_SPLIT: return launch_level_k<ST, FMT, PATH_SPLIT>(a, s);
+        case PATH_INT64: return launch_level_k<ST, FMT, PATH_INT64>(a, s);
+        default: return launch_level_k<ST, FMT, PATH_FLOAT>(a, s);
     }
 }
 
@@ -1014,35 +909,19 @@ cudaError_t launch_batch_level_k(const uint8_t *table, int L, int max_tiles, int
     static int cap[64] = {0};
     static size_t cap_smem[64] = {0};
     int grid = 0;
-    cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT, PATH>, max_tiles, smem, cap, cap_smem, grid);
+    cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT, PATH>, max_tiles, smem, cap, cap_smem, grid, RING_NT);
     if (e != cudaSuccess) return e;
-    pyramid_batch_kernel<ST, FMT, PATH><<<grid, NT, smem, s>>>(table, L);
-    return cudaGetLastError();
-}
-
-template <int ST>
-cudaError_t launch_l0_batch(const uint8_t *table, int max_tiles, int max_streams, cudaStream_t s) {
-    const size_t smem = l0_batch_smem_bytes(max_streams);
-    static int cap[64] = {0};
-    static size_t cap_smem[64] = {0};
-    int grid = 0;
-    cudaError_t e = grid_for(pyramid_l0_batch_kernel<ST>, max_tiles, smem, cap, cap_smem, grid, L0_NT);
-    if (e != cudaSuccess) return e;
-    pyramid_l0_batch_kernel<ST><<<grid, L0_NT, smem, s>>>(table);
+    pyramid_batch_kernel<ST, FMT, PATH><<<grid, RING_NT, smem, s>>>(table, L);
     return cudaGetLastError();
 }
 
 template <int ST, int FMT>
 cudaError_t launch_batch_level(const uint8_t *table, int L, int max_tiles, int max_streams,
                                cudaStream_t s) {
-    if constexpr (FMT == FMT_U8) {
-        return launch_l0_batch<ST>(table, max_tiles, max_streams, s);
-    } else {
-        switch (level_path(level_frac(L))) {
-            case PATH_SPLIT: return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, max_streams, s);
-            case PATH_INT64: return launch_batch_level_k<ST, FMT, PATH_INT64>(table, L, max_tiles, max_streams, s);
-            default: return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, max_streams, s);
-        }
+    switch (FMT == FMT_U8 ? PATH_FLOAT : level_path(level_frac(L))) {
+        case PATH_SPLIT: return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, max_streams, s);
+        case PATH_INT64: return launch_batch_level_k<ST, FMT, PATH_INT64>(table, L, max_tiles, max_streams, s);
+        default: return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, max_streams, s);
     }
 }
 
@@ -1106,6 +985,20 @@ cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, 
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+uint32_t encode_pyramid_maps(const uint8_t *frame, int64_t frame_pitch, const omt_pyramid &pyr,
+                             CUtensorMap *out) {
+    uint32_t ok = 0;
+    if (encode_level_map(frame, 1, pyr.w, pyr.h, frame_pitch, &out[0])) ok |= 1u;
+    const int esz = pyr.storage == OMT_F32 ? 4 : 2;
+    for (int L = 1; L < pyr.levels && L < OMT_MAX_LEVELS; ++L) {
+        const omt_level &lv = pyr.lv[L];
+        if (encode_level_map((const uint8_t *)pyr.base + lv.img_off, esz, lv.w, lv.h, lv.img_pitch,
+                             &out[L]))
+            ok |= 1u << L;
+    }
+    return ok;
 }
 
 cudaError_t pyr_wait_timeouts_take(unsigned *count) {
