@@ -301,7 +301,8 @@ struct LevelCopy {
 // The template window to prefetch after this level's template compute.
 struct NextTemplate {
     bool has;
-    const LevelView *P;
+    const LevelView *P;     // read only by row copies
+    int w, h;               // its level size
     const CUtensorMap *tm;  // the level's maps, or null
     bool u8;
     int ipx, ipy;
@@ -316,65 +317,73 @@ struct Prefetch {
 
 // Start copying the template window of the level at (ipx, ipy) into buffer
 // `buf` (I and gradient rows, one fill); returns its column origins.  tm
-// points at the level's maps when they are valid, else null.
+// points at the level's maps when they are valid, else null.  The level is
+// w x h texels; its view P is read only by the row copies.
 template <int ST, int WIN>
-__device__ __forceinline__ void issue_template(const LevelView &P, const CUtensorMap *tm, bool u8,
-                                               int ipx, int ipy, int buf, int lane, unsigned *W,
-                                               Fills &f, int &tcol_i, int &tcol_g) {
+__device__ __forceinline__ void issue_template(const LevelView *P, int w, int h,
+                                               const CUtensorMap *tm, bool u8, int ipx, int ipy,
+                                               int buf, int lane, unsigned *W, Fills &f,
+                                               int &tcol_i, int &tcol_g) {
     using D = Dims<ST, WIN>;
     unsigned *TI = W + buf * D::TRAW, *TGr = TI + D::TG;
     const int esz = u8 ? 1 : D::ESZ;
-    const Span si = row_span(P.w, esz, ipx - D::R, D::T);
-    const Span sg = row_span(P.w, D::GSZ, ipx - D::R, D::T);
+    const Span si = row_span(w, esz, ipx - D::R, D::T);
+    const Span sg = row_span(w, D::GSZ, ipx - D::R, D::T);
     const int y0 = ipy - D::R;
     tcol_i = si.b0 >> esz_shift(esz);
     tcol_g = sg.b0 >> esz_shift(D::GSZ);
-    if (fill_mode(tm, y0, D::T, P.h) != VIA_ROWS) {
+    if (fill_mode(tm, y0, D::T, h) != VIA_ROWS) {
         fill_begin(f, buf, D::T * 4 * (D::RWI + D::RWG), lane);
         tensor_box(TI, tm + LK_MAP_TI, tcol_i, y0, f.bar + buf, lane);
         tensor_box(TGr, tm + LK_MAP_TG, tcol_g, y0, f.bar + buf, lane);
     } else {
         fill_begin(f, buf, D::T * (si.bytes + sg.bytes), lane);
         if (lane < D::T) {
-            const int64_t y = clampi(y0 + lane, 0, P.h - 1);
-            bulk_row(TI + lane * D::RWI, P.img + y * P.img_pitch + si.b0, si.bytes, f.bar + buf);
-            bulk_row(TGr + lane * D::RWG, P.grad + y * P.grad_pitch + sg.b0, sg.bytes, f.bar + buf);
+            const uint8_t *img = P->img, *grad = P->grad;
+            const int64_t ip = P->img_pitch, gp = P->grad_pitch;
+            const int64_t y = clampi(y0 + lane, 0, h - 1);
+            bulk_row(TI + lane * D::RWI, img + y * ip + si.b0, si.bytes, f.bar + buf);
+            bulk_row(TGr + lane * D::RWG, grad + y * gp + sg.b0, sg.bytes, f.bar + buf);
         }
     }
 }
 
-// Start copying frame t+1's search region around (jx, jy); tm as above.
+// Start copying frame t+1's search region around (jx, jy); tm, w, h and
+// the view J as above.
 template <int ST, int WIN>
-__device__ __forceinline__ void copy_search(const LevelView &J, const CUtensorMap *tm, bool u8,
-                                            int jx, int jy, int lane, unsigned *W, Fills &f,
-                                            LevelCopy &lc, unsigned extra = 0) {
+__device__ __forceinline__ void copy_search(const LevelView *J, int w, int h,
+                                            const CUtensorMap *tm, bool u8, int jx, int jy,
+                                            int lane, unsigned *W, Fills &f, LevelCopy &lc,
+                                            unsigned extra = 0) {
     using D = Dims<ST, WIN>;
     const int esz = u8 ? 1 : D::ESZ;
     lc.sx0 = jx - D::R - MARGIN;
     lc.sy0 = jy - D::R - MARGIN;
-    const Span ss = row_span(J.w, esz, lc.sx0, D::SP + 1);
+    const Span ss = row_span(w, esz, lc.sx0, D::SP + 1);
     lc.scol = ss.b0 >> esz_shift(esz);
     unsigned *S = W + D::UNION;
-    if (fill_mode(tm, lc.sy0, D::SH, J.h) != VIA_ROWS) {
+    if (fill_mode(tm, lc.sy0, D::SH, h) != VIA_ROWS) {
         fill_begin(f, BUF_SEARCH, D::SH * 4 * D::RWJ + extra, lane);
         tensor_box(S, tm, lc.scol, lc.sy0, f.bar + BUF_SEARCH, lane);
     } else {
         fill_begin(f, BUF_SEARCH, D::SH * ss.bytes + extra, lane);
+        const uint8_t *img = J->img;
+        const int64_t ip = J->img_pitch;
         for (int r = lane; r < D::SH; r += 32) {
-            const int64_t y = clampi(lc.sy0 + r, 0, J.h - 1);
-            bulk_row(S + r * D::RWJ, J.img + y * J.img_pitch + ss.b0, ss.bytes, f.bar + BUF_SEARCH);
+            const int64_t y = clampi(lc.sy0 + r, 0, h - 1);
+            bulk_row(S + r * D::RWJ, img + y * ip + ss.b0, ss.bytes, f.bar + BUF_SEARCH);
         }
     }
 }
 
 // Edge rows of a search region that a tensor copy only overlapped.
 template <int ST, int WIN>
-__device__ __forceinline__ void search_edges(const LevelView &J, const CUtensorMap *tm, unsigned *W,
+__device__ __forceinline__ void search_edges(int h, const CUtensorMap *tm, unsigned *W,
                                              const LevelCopy &lc, int lane) {
     using D = Dims<ST, WIN>;
-    if (fill_mode(tm ? tm + LK_MAP_S : nullptr, lc.sy0, D::SH, J.h) == VIA_TMA_EDGE) {
+    if (fill_mode(tm, lc.sy0, D::SH, h) == VIA_TMA_EDGE) {
         __syncwarp();
-        fix_rows<D::RWJ>(W + D::UNION, lc.sy0, D::SH, J.h, lane);
+        fix_rows<D::RWJ>(W + D::UNION, lc.sy0, D::SH, h, lane);
     }
 }
 
@@ -426,14 +435,14 @@ __device__ __forceinline__ void warp_sum4(float &a, float &b, float &c, float &d
 // l < WIN owns tap column l; lane WIN holds the column right of the window,
 // so every lane's right-hand texel comes from the next lane by a shuffle.
 template <int ST, int WIN>
-__device__ __forceinline__ void template_window(const LevelView &P, int tx0, float ax, float ay,
+__device__ __forceinline__ void template_window(int w, int tx0, float ax, float ay,
                                                 int lane, const unsigned *W, const LevelCopy &lc,
                                                 float2 (&XY)[WIN], float &sxx, float &sxy,
                                                 float &syy) {
     using D = Dims<ST, WIN>;
     const unsigned *rawG = W + D::TG;
     const bool tapcol = lane < WIN;
-    const int cg0 = clampi(tx0 + (lane < WIN ? lane : WIN), 0, P.w - 1) - lc.tcol_g;
+    const int cg0 = clampi(tx0 + (lane < WIN ? lane : WIN), 0, w - 1) - lc.tcol_g;
     const float2 ax2 = f2(ax, ax), ay2 = f2(ay, ay);
     float2 prev = f2(0.f, 0.f), sq = f2(0.f, 0.f);  // sq = (sxx, syy)
     sxy = 0.f;
@@ -519,10 +528,13 @@ __device__ __forceinline__ const CUtensorMap *stream_maps(const BatchView &t, in
 }
 
 // One level of the pyramidal iteration for one point (the whole warp).
-// Returns the status after this level; nu is the level's increment.
+// Returns the status after this level; nu is the level's increment.  Both
+// frames' level is w x h texels; the views P and J are read only by row
+// copies.  Every branch below depends on warp sums or on values every lane
+// holds alike, so the warp never diverges.
 template <int ST, int WIN>
-__device__ __forceinline__ int track_level(const LevelView &P, const LevelView &J, float px,
-                                           float py, float gx, float gy, int max_iter,
+__device__ __forceinline__ int track_level(const LevelView *P, const LevelView *J, int w, int h,
+                                           float px, float py, float gx, float gy, int max_iter,
                                            float eps2, float tau_n, int lane, bool u8,
                                            const CUtensorMap *tm, unsigned *W, Fills &f,
                                            Prefetch &pf, const NextTemplate &nx, float &nux,
@@ -535,6 +547,7 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     nux = nuy = 0.f;
     k = 0;
     conv = false;
+    const CUtensorMap *tms = tm ? tm + LK_MAP_S : nullptr;
 
     // The template window was prefetched while the previous level (or the
     // previous point) iterated, unless this is the warp's first level; the
@@ -549,34 +562,35 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     } else {
         buf = 0;
         __syncwarp();
-        issue_template<ST, WIN>(P, tm, u8, ipx, ipy, buf, lane, W, f, lc.tcol_i, lc.tcol_g);
+        issue_template<ST, WIN>(P, w, h, tm, u8, ipx, ipy, buf, lane, W, f, lc.tcol_i, lc.tcol_g);
     }
     pf.valid = false;
-    const float c0x = ax + gx, c0y = ay + gy;
-    const bool c0_ok = fabsf(c0x) < 1.0e8f && fabsf(c0y) < 1.0e8f;
+    // The centre c = (ipx, ipy) + (a + g + nu); agx, agy = a + g.
+    const float agx = ax + gx, agy = ay + gy;
+    const bool c0_ok = fabsf(agx) < 1.0e8f && fabsf(agy) < 1.0e8f;
     int sjx = 0, sjy = 0;
     if (c0_ok) {
-        sjx = ipx + (int)floorf(c0x);
-        sjy = ipy + (int)floorf(c0y);
-        copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, sjx, sjy, lane, W, f, lc,
+        sjx = ipx + (int)floorf(agx);
+        sjy = ipy + (int)floorf(agy);
+        copy_search<ST, WIN>(J, w, h, tms, u8, sjx, sjy, lane, W, f, lc,
                              force_fail ? FAIL_EXTRA_BYTES : 0u);
     }
     // the template has landed; the search may still run
     if (!fill_wait(f, buf)) return OMT_PT_LOST_TIMEOUT;
-    if (fill_mode(tm, ipy - R, D::T, P.h) == VIA_TMA_EDGE) {
+    if (fill_mode(tm, ipy - R, D::T, h) == VIA_TMA_EDGE) {
         __syncwarp();
-        fix_rows<D::RWI>(W + buf * D::TRAW, ipy - R, D::T, P.h, lane);
-        fix_rows<D::RWG>(W + buf * D::TRAW + D::TG, ipy - R, D::T, P.h, lane);
+        fix_rows<D::RWI>(W + buf * D::TRAW, ipy - R, D::T, h, lane);
+        fix_rows<D::RWG>(W + buf * D::TRAW + D::TG, ipy - R, D::T, h, lane);
     }
     __syncwarp();
 
     float2 XY[WIN];
     float sxx, sxy, syy, cx, cy;
-    template_window<ST, WIN>(P, ipx - R, ax, ay, lane, W + buf * D::TRAW, lc, XY, sxx, sxy, syy);
+    template_window<ST, WIN>(w, ipx - R, ax, ay, lane, W + buf * D::TRAW, lc, XY, sxx, sxy, syy);
     float2 S[4];  // integer-shift correlations at the last position visited
     {
         // c = sum I(p + tap) (Ix, Iy), through the same path as J below
-        const int ci0 = clampi(ipx - R + (lane < WIN ? lane : WIN), 0, P.w - 1) - lc.tcol_i;
+        const int ci0 = clampi(ipx - R + (lane < WIN ? lane : WIN), 0, w - 1) - lc.tcol_i;
         if (u8) corr4<ST, true, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, XY, S);
         else corr4<ST, false, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, XY, S);
         combine4(S, ax, ay, cx, cy);
@@ -593,45 +607,48 @@ __device__ __forceinline__ int track_level(const LevelView &P, const LevelView &
     // into the other buffer while this level iterates.
     if (nx.has) {
         __syncwarp();
-        issue_template<ST, WIN>(*nx.P, nx.tm, nx.u8, nx.ipx, nx.ipy, 1 - buf, lane, W, f,
-                                pf.tcol_i, pf.tcol_g);
+        issue_template<ST, WIN>(nx.P, nx.w, nx.h, nx.tm, nx.u8, nx.ipx, nx.ipy, 1 - buf, lane, W,
+                                f, pf.tcol_i, pf.tcol_g);
         pf.valid = true;
         pf.buf = 1 - buf;
     }
     // the search region has landed; the prefetch may still run
     if (!fill_wait(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
-    if (c0_ok) search_edges<ST, WIN>(J, tm, W, lc, lane);
+    if (c0_ok) search_edges<ST, WIN>(h, tms, W, lc, lane);
     __syncwarp();
+    // The window stays inside the tracking bounds while its integer centre
+    // j = ip + floor(a + g + nu) satisfies -R <= j <= w - 1 + R (at the
+    // upper bound only with a zero fraction): in terms of a + g + nu, the
+    // closed interval [lo, hi] below (integers, exact in float).  A
+    // non-finite centre fails the test too.
+    const float lox = (float)(-R - ipx), hix = (float)(w - 1 + R - ipx);
+    const float loy = (float)(-R - ipy), hiy = (float)(h - 1 + R - ipy);
     bool staged = c0_ok;
-    int cjx = 0, cjy = 0;
-    bool cached = false;  // S holds the correlations at (cjx, cjy)
+    float cfx = 0.f, cfy = 0.f;  // floor of a + g + nu where S was correlated
+    bool cached = false;
     while (k < max_iter) {
-        // Centre c = p + g + nu, held as (ipx, ipy) + (ccx, ccy).
-        const float ccx = ax + gx + nux, ccy = ay + gy + nuy;
-        if (!(fabsf(ccx) < 1.0e8f) || !(fabsf(ccy) < 1.0e8f)) return OMT_PT_LOST_OOB;
+        const float ccx = agx + nux, ccy = agy + nuy;
+        if (!(ccx >= lox && ccx <= hix && ccy >= loy && ccy <= hiy)) return OMT_PT_LOST_OOB;
         const float fcx = floorf(ccx), fcy = floorf(ccy);
-        const int jx = ipx + (int)fcx, jy = ipy + (int)fcy;
         const float bx = ccx - fcx, by = ccy - fcy;
-        if (jx < -R || jx > J.w - 1 + R || (jx == J.w - 1 + R && bx > 0.f) || jy < -R ||
-            jy > J.h - 1 + R || (jy == J.h - 1 + R && by > 0.f))
-            return OMT_PT_LOST_OOB;
-        if (!cached || jx != cjx || jy != cjy) {
+        if (!cached || fcx != cfx || fcy != cfy) {
+            const int jx = ipx + (int)fcx, jy = ipy + (int)fcy;
             if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
                 __syncwarp();
-                copy_search<ST, WIN>(J, tm ? tm + LK_MAP_S : nullptr, u8, jx, jy, lane, W, f, lc);
+                copy_search<ST, WIN>(J, w, h, tms, u8, jx, jy, lane, W, f, lc);
                 if (!fill_wait(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
-                search_edges<ST, WIN>(J, tm, W, lc, lane);
+                search_edges<ST, WIN>(h, tms, W, lc, lane);
                 __syncwarp();
                 sjx = jx;
                 sjy = jy;
                 staged = true;
             }
-            const int col0 = clampi(jx - R + (lane < WIN ? lane : WIN), 0, J.w - 1) - lc.scol;
+            const int col0 = clampi(jx - R + (lane < WIN ? lane : WIN), 0, w - 1) - lc.scol;
             const int oy = jy - sjy + MARGIN;
             if (u8) corr4<ST, true, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, XY, S);
             else corr4<ST, false, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, XY, S);
-            cjx = jx;
-            cjy = jy;
+            cfx = fcx;
+            cfy = fcy;
             cached = true;
         }
         float sx, sy;
@@ -665,71 +682,91 @@ __device__ __forceinline__ void lost_timeout(float2 u, int i, float2 *out, uint8
     if (iters && lane < levels) iters[(int64_t)i * levels + lane] = 0;
 }
 
-template <int ST, int WIN>
-__device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J, int levels,
-                                         int max_iter, float eps2, float tau_n, float2 u,
-                                         int i, float2 *out, uint8_t *status, uint8_t *iters,
-                                         const CUtensorMap *tm, unsigned *W, Fills &f,
-                                         Prefetch &pf, bool has_next, float2 u_next,
-                                         const LevelView *P_next_point,
-                                         const CUtensorMap *tm_next, int gid) {
+// What tracking one point gives: its position, status and iterations per
+// level (8 bits each).  The caller writes them out, so that no output
+// pointer stays live while the point is tracked.
+struct PointResult {
+    float2 v;
+    int st;
+    unsigned long long itp;
+};
+
+// The next point's top-level template for the prefetch of the finest level.
+template <int WIN>
+__device__ __forceinline__ NextTemplate next_top(bool has, float2 un, const LevelView *Pn,
+                                                 const CUtensorMap *tmn, int levels) {
+    NextTemplate nx;
+    const float st0 = __int_as_float((127 - (levels - 1)) << 23);
+    nx.has = has && fabsf(un.x) <= 16777216.f && fabsf(un.y) <= 16777216.f;
+    nx.P = &Pn[levels - 1];
+    nx.w = nx.has ? Pn[levels - 1].w : 1;
+    nx.h = nx.has ? Pn[levels - 1].h : 1;
+    nx.tm = level_maps(tmn, levels - 1);
+    nx.u8 = levels - 1 == 0;
+    nx.ipx = (int)floorf(un.x * st0);
+    nx.ipy = (int)floorf(un.y * st0);
+    return nx;
+}
+
+// The whole pyramidal iteration for one point u (the whole warp); P, J are
+// the frame-t and frame-(t+1) level views, tm their maps (or null).
+// next() gives the next point's top-level template (NextTemplate), called
+// at the finest level only.  A point with a non-finite coordinate or one
+// beyond 2^24 px is lost outside the frame without a window (its integer
+// positions would not fit); a point whose wait ran out comes back
+// OMT_PT_LOST_TIMEOUT at its input position with no iterations.
+template <int ST, int WIN, class NextFn>
+__device__ __forceinline__ PointResult lk_point(const LevelView *P, const LevelView *J, int levels,
+                                                int max_iter, float eps2, float tau_n, float2 u,
+                                                const CUtensorMap *tm, unsigned *W, Fills &f,
+                                                Prefetch &pf, NextFn next, bool force_fail) {
     const int lane = threadIdx.x & 31;
-    float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
-    int st = OMT_PT_OK;
-    bool nonconv = false;
-    unsigned long long itp = 0ull;  // iterations per level, 8 bits each
-    // A point with a non-finite coordinate or one beyond 2^24 px is lost
-    // outside the frame without a window (its integer positions would not
-    // fit); such a next point gets no prefetch either.
+    PointResult r;
+    r.v = u;
+    r.itp = 0ull;
     if (!(fabsf(u.x) <= 16777216.f) || !(fabsf(u.y) <= 16777216.f)) {
         fill_drain(f);
         pf.valid = false;
-        if (lane == 0) {
-            out[i] = u;
-            status[i] = (uint8_t)OMT_PT_LOST_OOB;
-        }
-        if (iters && lane < levels) iters[(int64_t)i * levels + lane] = 0;
-        return;
+        r.st = OMT_PT_LOST_OOB;
+        return r;
     }
-    has_next = has_next && fabsf(u_next.x) <= 16777216.f && fabsf(u_next.y) <= 16777216.f;
+    float gx = 0.f, gy = 0.f, dx = 0.f, dy = 0.f;
+    int st = OMT_PT_OK;
+    bool nonconv = false;
+    // level sizes, read once (both frames share them)
+    const int w0 = P[0].w, h0 = P[0].h;
 
     for (int L = levels - 1; L >= 0; --L) {
         const float sc = __int_as_float((127 - L) << 23);  // 2^-L, exact
+        const int wl = ((w0 - 1) >> L) + 1, hl = ((h0 - 1) >> L) + 1;  // (w + 1) >> 1 per level
         NextTemplate nx;
         if (L > 0) {
             const float s1 = __int_as_float((127 - (L - 1)) << 23);
             nx.has = true;
             nx.P = &P[L - 1];
+            nx.w = ((w0 - 1) >> (L - 1)) + 1;
+            nx.h = ((h0 - 1) >> (L - 1)) + 1;
             nx.tm = level_maps(tm, L - 1);
             nx.u8 = L - 1 == 0;
             nx.ipx = (int)floorf(u.x * s1);
             nx.ipy = (int)floorf(u.y * s1);
         } else {
-            const float st0 = __int_as_float((127 - (levels - 1)) << 23);
-            nx.has = has_next;
-            nx.P = &P_next_point[levels - 1];
-            nx.tm = level_maps(tm_next, levels - 1);
-            nx.u8 = levels - 1 == 0;
-            nx.ipx = (int)floorf(u_next.x * st0);
-            nx.ipy = (int)floorf(u_next.y * st0);
+            nx = next();
         }
         float nux, nuy;
         int k;
         bool conv;
-        st = track_level<ST, WIN>(P[L], J[L], u.x * sc, u.y * sc, gx, gy, max_iter, eps2, tau_n,
-                                  lane, L == 0, level_maps(tm, L), W, f, pf, nx, nux, nuy,
-                                  k, conv, L == levels - 1 && (long long)gid == lk_fail_point);
-        itp |= (unsigned long long)k << (8 * L);
+        st = track_level<ST, WIN>(&P[L], &J[L], wl, hl, u.x * sc, u.y * sc, gx, gy, max_iter,
+                                  eps2, tau_n, lane, L == 0, level_maps(tm, L), W, f, pf, nx,
+                                  nux, nuy, k, conv, L == levels - 1 && force_fail);
+        r.itp |= (unsigned long long)k << (8 * L);
         if (st == OMT_PT_LOST_TIMEOUT) {
             // give the point up; the kernel lands what else is in flight
             // (bounded) before it exits
             pf.valid = false;
-            if (lane == 0) {
-                out[i] = u;
-                status[i] = (uint8_t)OMT_PT_LOST_TIMEOUT;
-            }
-            if (iters && lane < levels) iters[(int64_t)i * levels + lane] = 0;
-            return;
+            r.st = OMT_PT_LOST_TIMEOUT;
+            r.itp = 0ull;
+            return r;
         }
         if (st != OMT_PT_OK) break;
         if (!conv) nonconv = true;
@@ -747,22 +784,27 @@ __device__ __forceinline__ void lk_point(const LevelView *P, const LevelView *J,
         // forget them
         fill_drain(f);
         pf.valid = false;
-    }
-
-    float2 v = u;
-    if (st == OMT_PT_OK) {
+    } else {
         const float ox = u.x + dx, oy = u.y + dy;
-        if (!(ox >= 0.f && ox <= (float)(P[0].w - 1) && oy >= 0.f && oy <= (float)(P[0].h - 1)))
+        if (!(ox >= 0.f && ox <= (float)(w0 - 1) && oy >= 0.f && oy <= (float)(h0 - 1)))
             st = OMT_PT_LOST_OOB;
         else
-            v = make_float2(ox, oy);
+            r.v = make_float2(ox, oy);
     }
     if (st == OMT_PT_OK && nonconv) st |= OMT_PT_NONCONV;
+    r.st = st;
+    return r;
+}
+
+// Writes a point's result: position and status by lane 0, the iterations
+// of level L by lane L.
+__device__ __forceinline__ void put_point(const PointResult &r, int i, float2 *out,
+                                          uint8_t *status, uint8_t *iters, int levels, int lane) {
     if (lane == 0) {
-        out[i] = v;
-        status[i] = (uint8_t)st;
+        out[i] = r.v;
+        status[i] = (uint8_t)r.st;
     }
-    if (iters && lane < levels) iters[(int64_t)i * levels + lane] = (uint8_t)(itp >> (8 * lane));
+    if (iters && lane < levels) iters[(int64_t)i * levels + lane] = (uint8_t)(r.itp >> (8 * lane));
 }
 
 // ------------------------------------------------------ forward-backward
@@ -822,15 +864,19 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
     Prefetch pf;
     pf.valid = false;
     for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
-        const int nxt = i + nwarps;
-        const bool has_next = nxt < n;
-        const float2 un = has_next ? a.pts[nxt] : make_float2(0.f, 0.f);
         if (f.pend & FILL_FAILED) {   // a wait ran out: the warp's later points are given up
             lost_timeout(a.pts[i], i, a.out, a.status, a.iters, a.levels, lane_of());
             continue;
         }
-        lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n, a.pts[i], i, a.out,
-                          a.status, a.iters, tm, W, f, pf, has_next, un, a.P, tm, i);
+        const int nxt = i + nwarps;
+        auto next = [&]() {
+            const bool has = nxt < n;
+            return next_top<WIN>(has, has ? a.pts[nxt] : make_float2(0.f, 0.f), a.P, tm, a.levels);
+        };
+        const PointResult r = lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n,
+                                                a.pts[i], tm, W, f, pf, next,
+                                                (long long)i == lk_fail_point);
+        put_point(r, i, a.out, a.status, a.iters, a.levels, lane_of());
     }
     fill_drain(f);
 }
@@ -904,24 +950,36 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *t
             gn = take();
             end = gn + chunk;
         }
-        const StreamEntry &e = t.stream(s);
         const int i = g - pre[s];
         const bool has_next = gn < total;
         const int sn = has_next ? find_segment(pre, ns, gn) : s;
-        const StreamEntry &en = t.stream(sn);
-        // forward: frame t -> t+1 from the corners; backward: frame t+1 -> t
-        // from the forward results
-        const float2 *in = backward ? e.pts_out : e.pts;
-        const float2 *in_next = backward ? en.pts_out : en.pts;
-        const float2 un = has_next ? in_next[gn - pre[sn]] : make_float2(0.f, 0.f);
-        lk_point<ST, WIN>(backward ? e.P_next : e.P, backward ? e.P : e.P_next, h.levels,
-                          h.max_iter, h.eps2, h.tau_n, in[i], i,
-                          backward ? e.pts_back : e.pts_out, backward ? e.status_back : e.status,
-                          backward ? nullptr : e.iters, stream_maps(t, s, h.levels, backward), W,
-                          f, pf, has_next, un, backward ? en.P_next : en.P,
-                          stream_maps(t, sn, h.levels, backward), g);
-        if constexpr (backward) {
-            if (lane == 0) fb_apply(e.pts[i], e.pts_back[i], e.status_back[i], h.fb_max, e.status[i]);
+        PointResult r;
+        {
+            const StreamEntry &e = t.stream(s);
+            // forward: frame t -> t+1 from the corners; backward: frame t+1 -> t
+            // from the forward results
+            const float2 u = (backward ? e.pts_out : e.pts)[i];
+            auto next = [&]() {
+                const StreamEntry &en = t.stream(sn);
+                const float2 un = has_next ? (backward ? en.pts_out : en.pts)[gn - pre[sn]]
+                                           : make_float2(0.f, 0.f);
+                return next_top<WIN>(has_next, un, backward ? en.P_next : en.P,
+                                     stream_maps(t, sn, h.levels, backward), h.levels);
+            };
+            r = lk_point<ST, WIN>(backward ? e.P_next : e.P, backward ? e.P : e.P_next, h.levels,
+                                  h.max_iter, h.eps2, h.tau_n, u,
+                                  stream_maps(t, s, h.levels, backward), W, f, pf, next,
+                                  (long long)g == lk_fail_point);
+        }
+        {
+            const StreamEntry &e = t.stream(s);
+            if constexpr (backward) {
+                put_point(r, i, e.pts_back, e.status_back, nullptr, h.levels, lane);
+                if (lane == 0)
+                    fb_apply(e.pts[i], e.pts_back[i], e.status_back[i], h.fb_max, e.status[i]);
+            } else {
+                put_point(r, i, e.pts_out, e.status, e.iters, h.levels, lane);
+            }
         }
         if (f.pend & FILL_FAILED) {
             // a wait ran out: the points this warp holds (the rest of its
