@@ -430,74 +430,154 @@ __device__ __forceinline__ void warp_sum4(float &a, float &b, float &c, float &d
     d = __shfl_sync(FULL_MASK, keep, 24);
 }
 
-// Frame-t window from the raw template rows: (Ix, Iy) per tap row stay in
-// registers as one pair, with the level constants G (three sums).  Lane
-// l < WIN owns tap column l; lane WIN holds the column right of the window,
-// so every lane's right-hand texel comes from the next lane by a shuffle.
+// How a warp's lanes cover a window of WIN x WIN taps (texel footprint
+// (WIN + 1)^2): four row bands of eight lanes.  Lane k of band g holds texel
+// columns CPL k .. CPL k + CPL - 1 (taps where the column is below WIN; the
+// column right of its last one comes from lane k + 1 by a shuffle) and walks
+// the band's tap rows r0 .. r0 + nr - 1: the WIN rows split into bands of
+// Q + 1 rows (the first REM bands) and Q rows.  A band walks RB rows; a
+// band of Q rows reads its last texel row again at step Q, where its taps
+// are zero.  Every lane then holds RB x CPL taps, and all 32 lanes take part
+// in every row step (a lane per texel column left 10 of 32 lanes idle at
+// WIN = 21).
+template <int WIN>
+struct Lanes {
+    static constexpr int CPL = (WIN + 1 + 7) / 8;       // texel columns per lane
+    static constexpr int Q = WIN / 4, REM = WIN % 4;    // band rows: Q + (g < REM)
+    static constexpr int RB = Q + (REM > 0 ? 1 : 0);    // row steps of a band
+    // a lane holds taps and columns right of the window at once
+    static constexpr bool PARTIAL = WIN % CPL != 0;
+};
+
+__device__ __forceinline__ int band_r0(int g, int q, int rem) { return g * q + (g < rem ? g : rem); }
+
+// This lane's texel columns of a window whose first column is level column
+// x0, clamped to the window's footprint and to the level (w columns), as
+// offsets into raw rows that start at level column c0.
+template <int WIN>
+__device__ __forceinline__ void lane_cols(int x0, int w, int c0, int lane,
+                                          int (&col)[Lanes<WIN>::CPL]) {
+    using M = Lanes<WIN>;
+    const int k = lane & 7;
+#pragma unroll
+    for (int j = 0; j < M::CPL; ++j) {
+        const int c = min(M::CPL * k + j, WIN);
+        col[j] = clampi(x0 + c, 0, w - 1) - c0;
+    }
+}
+
+// Whether this lane holds any tap (lanes whose columns all lie right of the
+// window only supply texels to their left neighbour).
+template <int WIN>
+__device__ __forceinline__ bool lane_owns(int lane) {
+    return (lane & 7) * Lanes<WIN>::CPL < WIN;
+}
+
+// Frame-t window from the raw template rows: the interpolated (Ix, Iy) of
+// this lane's taps stay in registers, with its share of the level constants
+// G (three sums).  Taps a lane does not hold (the repeated last row of a
+// short band; columns right of the window when a lane straddles its edge)
+// are zero; a lane that holds no tap ends with zero sums.
 template <int ST, int WIN>
 __device__ __forceinline__ void template_window(int w, int tx0, float ax, float ay,
                                                 int lane, const unsigned *W, const LevelCopy &lc,
-                                                float2 (&XY)[WIN], float &sxx, float &sxy,
-                                                float &syy) {
+                                                float2 (&XY)[Lanes<WIN>::RB][Lanes<WIN>::CPL],
+                                                float &sxx, float &sxy, float &syy) {
     using D = Dims<ST, WIN>;
+    using M = Lanes<WIN>;
+    constexpr int C = M::CPL;
+    const int g = lane >> 3, k = lane & 7;
+    const int r0 = band_r0(g, M::Q, M::REM);
+    const bool long_band = g < M::REM;
     const unsigned *rawG = W + D::TG;
-    const bool tapcol = lane < WIN;
-    const int cg0 = clampi(tx0 + (lane < WIN ? lane : WIN), 0, w - 1) - lc.tcol_g;
+    int cg[C];
+    lane_cols<WIN>(tx0, w, lc.tcol_g, lane, cg);
     const float2 ax2 = f2(ax, ax), ay2 = f2(ay, ay);
-    float2 prev = f2(0.f, 0.f), sq = f2(0.f, 0.f);  // sq = (sxx, syy)
+    float2 prev[C], sq = f2(0.f, 0.f);  // sq = (sxx, syy)
     sxy = 0.f;
+    // horizontal interpolation of texel row r of the footprint
+    auto hrow = [&](const unsigned *row, float2 (&h)[C]) {
+        float2 t[C];
 #pragma unroll
-    for (int tr = 0; tr <= WIN; ++tr) {
-        const float2 g0 = raw_grad<ST>(rawG + tr * D::RWG, cg0);
-        const float2 g1 = f2(__shfl_down_sync(FULL_MASK, g0.x, 1),
-                             __shfl_down_sync(FULL_MASK, g0.y, 1));
-        const float2 h = __ffma2_rn(ax2, f2sub(g1, g0), g0);   // horizontal
-        if (tr > 0) {
-            const float2 v = __ffma2_rn(ay2, f2sub(h, prev), prev);  // vertical
-            XY[tr - 1] = v;
+        for (int j = 0; j < C; ++j) t[j] = raw_grad<ST>(row, cg[j]);
+        const float2 tn = f2(__shfl_down_sync(FULL_MASK, t[0].x, 1),
+                             __shfl_down_sync(FULL_MASK, t[0].y, 1));
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const float2 t1 = j + 1 < C ? t[j + 1] : tn;
+            h[j] = __ffma2_rn(ax2, f2sub(t1, t[j]), t[j]);
+        }
+    };
+    hrow(rawG + r0 * D::RWG, prev);
+#pragma unroll
+    for (int i = 0; i < M::RB; ++i) {
+        const int tr = i < M::Q ? r0 + i + 1 : min(r0 + M::Q + 1, WIN);
+        float2 h[C];
+        hrow(rawG + tr * D::RWG, h);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            float2 v = __ffma2_rn(ay2, f2sub(h[j], prev[j]), prev[j]);  // vertical
+            if (i == M::Q && !long_band) v = f2(0.f, 0.f);
+            if (M::PARTIAL && C * k + j >= WIN) v = f2(0.f, 0.f);
+            XY[i][j] = v;
             sq = __ffma2_rn(v, v, sq);
             sxy = fmaf(v.x, v.y, sxy);
+            prev[j] = h[j];
         }
-        prev = h;
     }
     sxx = sq.x;
     syy = sq.y;
-    if (!tapcol) sxx = sxy = syy = 0.f;
+    if (!lane_owns<WIN>(lane)) sxx = sxy = syy = 0.f;
 }
 
 // The four integer-shift correlations of a raw image window with the
-// template gradients: S[s] = sum over taps of V(tap + (b, a)) (Ix, Iy)(tap),
-// s = 2a + b, for the window whose top-left tap sits at raw row oy, raw
-// column col0 of this lane (lanes as in template_window).  Bilinear
+// template gradients: S[s] = sum over this lane's taps of V(tap + (b, a))
+// (Ix, Iy)(tap), s = 2a + b, for the window whose top tap row sits at raw
+// row oy, with this lane's texel columns col (lane_cols).  Bilinear
 // sampling at fraction (bx, by) is then the weighted sum (1-bx)(1-by) S0 +
 // bx(1-by) S1 + (1-bx)by S2 + bx by S3 (combine4), so a window position is
 // correlated once however many iterations revisit it.  The frame-t template
 // and the frame-(t+1) search window go through this same code, so equal
-// frames give exactly equal sums.
+// frames give exactly equal sums.  A lane that holds no tap has zero taps
+// only when PARTIAL; otherwise its sums are garbage and the caller drops
+// them (lane_owns).
 template <int ST, bool U8, int WIN>
-__device__ __forceinline__ void corr4(const unsigned *raw, int rw, int oy, int col0, int lane,
-                                      const float2 (&XY)[WIN], float2 (&S)[4]) {
-    const unsigned *base = raw + oy * rw;
+__device__ __forceinline__ void corr4(const unsigned *raw, int rw, int oy,
+                                      const int (&col)[Lanes<WIN>::CPL], int lane,
+                                      const float2 (&XY)[Lanes<WIN>::RB][Lanes<WIN>::CPL],
+                                      float2 (&S)[4]) {
+    using M = Lanes<WIN>;
+    constexpr int C = M::CPL;
+    const int g = lane >> 3;
+    const int r0 = band_r0(g, M::Q, M::REM);
+    const unsigned *base = raw + (oy + r0) * rw;
 #pragma unroll
     for (int q = 0; q < 4; ++q) S[q] = f2(0.f, 0.f);
-    float p0 = 0.f, p1 = 0.f;
+    float p[C], pn;
 #pragma unroll
-    for (int tr = 0; tr <= WIN; ++tr) {
-        const float v0 = raw_texel<ST>(base + tr * rw, col0, U8);
-        const float v1 = __shfl_down_sync(FULL_MASK, v0, 1);
-        if (tr > 0) {
-            const float2 g = XY[tr - 1];
-            S[0] = __ffma2_rn(f2(p0, p0), g, S[0]);
-            S[1] = __ffma2_rn(f2(p1, p1), g, S[1]);
-            S[2] = __ffma2_rn(f2(v0, v0), g, S[2]);
-            S[3] = __ffma2_rn(f2(v1, v1), g, S[3]);
+    for (int j = 0; j < C; ++j) p[j] = raw_texel<ST>(base, col[j], U8);
+    pn = __shfl_down_sync(FULL_MASK, p[0], 1);
+#pragma unroll
+    for (int i = 0; i < M::RB; ++i) {
+        const unsigned *row = i < M::Q ? base + (i + 1) * rw
+                                       : raw + (oy + min(r0 + M::Q + 1, WIN)) * rw;
+        float v[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = raw_texel<ST>(row, col[j], U8);
+        const float vn = __shfl_down_sync(FULL_MASK, v[0], 1);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            const float pr = j + 1 < C ? p[j + 1] : pn;
+            const float vr = j + 1 < C ? v[j + 1] : vn;
+            const float2 gg = XY[i][j];
+            S[0] = __ffma2_rn(f2(p[j], p[j]), gg, S[0]);
+            S[1] = __ffma2_rn(f2(pr, pr), gg, S[1]);
+            S[2] = __ffma2_rn(f2(v[j], v[j]), gg, S[2]);
+            S[3] = __ffma2_rn(f2(vr, vr), gg, S[3]);
         }
-        p0 = v0;
-        p1 = v1;
-    }
-    if (lane >= WIN) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) S[q] = f2(0.f, 0.f);
+        for (int j = 0; j < C; ++j) p[j] = v[j];
+        pn = vn;
     }
 }
 
@@ -584,16 +664,20 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
     }
     __syncwarp();
 
-    float2 XY[WIN];
+    using M = Lanes<WIN>;
+    const bool owns = lane_owns<WIN>(lane);
+    float2 XY[M::RB][M::CPL];
     float sxx, sxy, syy, cx, cy;
     template_window<ST, WIN>(w, ipx - R, ax, ay, lane, W + buf * D::TRAW, lc, XY, sxx, sxy, syy);
     float2 S[4];  // integer-shift correlations at the last position visited
     {
         // c = sum I(p + tap) (Ix, Iy), through the same path as J below
-        const int ci0 = clampi(ipx - R + (lane < WIN ? lane : WIN), 0, w - 1) - lc.tcol_i;
-        if (u8) corr4<ST, true, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, XY, S);
-        else corr4<ST, false, WIN>(W + buf * D::TRAW, D::RWI, 0, ci0, lane, XY, S);
+        int ci[M::CPL];
+        lane_cols<WIN>(ipx - R, w, lc.tcol_i, lane, ci);
+        if (u8) corr4<ST, true, WIN>(W + buf * D::TRAW, D::RWI, 0, ci, lane, XY, S);
+        else corr4<ST, false, WIN>(W + buf * D::TRAW, D::RWI, 0, ci, lane, XY, S);
         combine4(S, ax, ay, cx, cy);
+        if (!owns) cx = cy = 0.f;
     }
     warp_sum4(sxx, syy, cx, cy, lane);
     sxy = warp_sum(sxy);
@@ -643,16 +727,18 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
                 sjy = jy;
                 staged = true;
             }
-            const int col0 = clampi(jx - R + (lane < WIN ? lane : WIN), 0, w - 1) - lc.scol;
+            int cj[M::CPL];
+            lane_cols<WIN>(jx - R, w, lc.scol, lane, cj);
             const int oy = jy - sjy + MARGIN;
-            if (u8) corr4<ST, true, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, XY, S);
-            else corr4<ST, false, WIN>(W + D::UNION, D::RWJ, oy, col0, lane, XY, S);
+            if (u8) corr4<ST, true, WIN>(W + D::UNION, D::RWJ, oy, cj, lane, XY, S);
+            else corr4<ST, false, WIN>(W + D::UNION, D::RWJ, oy, cj, lane, XY, S);
             cfx = fcx;
             cfy = fcy;
             cached = true;
         }
         float sx, sy;
         combine4(S, bx, by, sx, sy);
+        if (!owns) sx = sy = 0.f;
         warp_sum2(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
         const float ex = (syy * bbx - sxy * bby) * inv_det;
