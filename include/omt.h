@@ -27,10 +27,14 @@
  *   - Arguments are validated on the host before anything is launched; an
  *     invalid call returns OMT_EINVAL and launches nothing.  A failed launch
  *     returns OMT_ECUDA.
- *   - The only device-side waits are the LK kernels' waits for their window
- *     copies (omt_lk_track and the batched LK phase).  Each gives up after
- *     one second; the points it concerns come back OMT_PT_LOST_TIMEOUT and
- *     omt_lk_wait_timeouts reports OMT_ETIMEOUT.  No kernel can hang.
+ *   - The only device-side waits are waits for tensor copies into shared
+ *     memory: the LK kernels' window copies (omt_lk_track and the batched LK
+ *     phase) and the pyramid kernels' tile copies (omt_build_pyramid and the
+ *     batched pyramid phase).  Each gives up after one second and is
+ *     counted; omt_lk_wait_timeouts then reports OMT_ETIMEOUT.  The LK points
+ *     it concerns come back OMT_PT_LOST_TIMEOUT; a pyramid CTA whose wait ran
+ *     out stops after landing its copies in flight, leaving its remaining
+ *     tiles unwritten, so that pyramid must not be used.  No kernel can hang.
  *   - Calls on different streams may run concurrently from different host
  *     threads.  Mutable global state, all of it named here: the count of LK
  *     waits that ran out (omt_lk_wait_timeouts), the LK test hook
@@ -167,7 +171,10 @@ int omt_build_pyramid(const uint8_t *frame, int32_t w, int32_t h, size_t pitch,
  *       of its 8 neighbours (non-strict 3x3 maximum). */
 int omt_corner_response(const omt_pyramid *pyr, uint32_t *out, void *stream);
 
-/* Scratch bytes omt_select_corners needs for this frame size and box set. */
+/* Scratch bytes omt_select_corners needs for this frame size and box set:
+ * the frame's response map (4 bytes per pixel; written only where a box has
+ * more than 1,024 candidates), 8 bytes per box-corner slot, and per box a
+ * list of up to 1,024 candidate keys (8 KiB) and two counters. */
 size_t omt_corner_scratch_bytes(int32_t w, int32_t h, int32_t nboxes, int32_t max_corners);
 
 /* Section V-A (feature calculation, sparse form): Shi-Tomasi corners of
@@ -204,14 +211,16 @@ int omt_select_corners(const omt_pyramid *pyr, const float *boxes, int32_t nboxe
  * allocator, or a real-time loop that must not call cudaMalloc (which can
  * synchronise the whole device).  Same arguments and result as
  * omt_select_corners, minus the scratch: the scratch is one fixed array
- * (OMT_STATIC_SCRATCH_BYTES) inside the library.
- *   - Returns OMT_ENOMEM when omt_corner_scratch_bytes(w, h, nboxes,
- *     max_corners) exceeds OMT_STATIC_SCRATCH_BYTES (16 MiB).  The frame's
- *     response map takes 4 bytes per pixel and each box-corner slot
- *     (nboxes x max_corners) 8 more: a 1920x1080 frame leaves room for about
- *     1.05 million slots (for example 1,000 boxes of 1,000 corners), a
- *     3840x2160 frame for none; the caller must then use omt_select_corners
- *     with its own scratch.
+ * (OMT_STATIC_SCRATCH_BYTES) inside the library.  It selects through the
+ * whole response map (no candidate lists), which needs less scratch.
+ *   - Returns OMT_ENOMEM when the scratch it needs exceeds
+ *     OMT_STATIC_SCRATCH_BYTES (16 MiB): the frame's response map takes 4
+ *     bytes per pixel, each box-corner slot (nboxes x max_corners) 8 more
+ *     and each box 4 more (each of the three parts rounded up to 256
+ *     bytes, plus one word): a 1920x1080 frame leaves room for about 1.05
+ *     million slots (for example 1,000 boxes of 1,000 corners), a 3840x2160
+ *     frame for none; the caller must then use omt_select_corners with its
+ *     own scratch.
  *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  *     routine.
  *   - The first call on each device looks up the array's device address
@@ -531,8 +540,10 @@ int omt_update_tracks(const float *boxes_s, const uint8_t *active_s, int32_t ns,
  * iterations (in the plain call, all its later points too; in the batched
  * step, the rest of its queue chunk, after which it takes no more work; a
  * point whose backward run was lost so becomes OMT_PT_LOST_TIMEOUT in the
- * forward-backward check).  The count is process-global.  OMT_EINVAL if
- * count is NULL; OMT_ECUDA on a CUDA error. */
+ * forward-backward check).  The count also includes the pyramid kernels'
+ * tile waits that ran out (their CTA stopped, leaving tiles of that pyramid
+ * unwritten).  The count is process-global.  OMT_EINVAL if count is NULL;
+ * OMT_ECUDA on a CUDA error. */
 int omt_lk_wait_timeouts(uint32_t *count);
 
 /* Test hook of the wait-failure path (synchronous, current device): from

@@ -56,6 +56,22 @@ int from_cuda(cudaError_t e) { return e == cudaSuccess ? OMT_OK : OMT_ECUDA; }
 
 }  // namespace
 
+namespace omt {
+int select_corners_entry(const omt_pyramid *pyr, const float *boxes, int32_t nboxes,
+                         const omt_params *prm, void *scratch, size_t scratch_bytes, float *pts,
+                         int32_t *offsets, bool lists, void *stream) {
+    if (omt_validate_params(prm) != OMT_OK || !pyr_ok(pyr) || nboxes < 0) return OMT_EINVAL;
+    if (nboxes > 0 && (!boxes || !aligned(boxes, 16) || !pts || !aligned(pts, 8)))
+        return OMT_EINVAL;
+    if (!offsets || !scratch || !aligned(scratch, 256)) return OMT_EINVAL;
+    if ((int64_t)nboxes * prm->max_corners > ((int64_t)1 << 31) - 1) return OMT_EINVAL;
+    if (scratch_bytes < select_scratch_bytes(pyr->w, pyr->h, nboxes, prm->max_corners, lists))
+        return OMT_ENOMEM;
+    return from_cuda(launch_select_corners(*pyr, (const float4 *)boxes, nboxes, *prm, scratch,
+                                           (float2 *)pts, offsets, lists, (cudaStream_t)stream));
+}
+}  // namespace omt
+
 extern "C" {
 
 void omt_default_params(omt_params *p) {
@@ -133,18 +149,12 @@ size_t omt_corner_scratch_bytes(int32_t w, int32_t h, int32_t nboxes, int32_t ma
     return select_scratch_bytes(w, h, nboxes, max_corners);
 }
 
+
 int omt_select_corners(const omt_pyramid *pyr, const float *boxes, int32_t nboxes,
                        const omt_params *prm, void *scratch, size_t scratch_bytes, float *pts,
                        int32_t *offsets, void *stream) {
-    if (omt_validate_params(prm) != OMT_OK || !pyr_ok(pyr) || nboxes < 0) return OMT_EINVAL;
-    if (nboxes > 0 && (!boxes || !aligned(boxes, 16) || !pts || !aligned(pts, 8)))
-        return OMT_EINVAL;
-    if (!offsets || !scratch || !aligned(scratch, 256)) return OMT_EINVAL;
-    if ((int64_t)nboxes * prm->max_corners > ((int64_t)1 << 31) - 1) return OMT_EINVAL;
-    if (scratch_bytes < select_scratch_bytes(pyr->w, pyr->h, nboxes, prm->max_corners))
-        return OMT_ENOMEM;
-    return from_cuda(launch_select_corners(*pyr, (const float4 *)boxes, nboxes, *prm, scratch,
-                                           (float2 *)pts, offsets, (cudaStream_t)stream));
+    return select_corners_entry(pyr, boxes, nboxes, prm, scratch, scratch_bytes, pts, offsets,
+                                true, stream);
 }
 
 int omt_lk_track(const omt_pyramid *prev, const omt_pyramid *next, const float *pts,
@@ -276,12 +286,15 @@ int omt_batch_pack(const omt_batch_stream *streams, int32_t nstreams, const omt_
         e.pts_back = h.fb_on ? (float2 *)b.pts_back : nullptr;
         e.status_back = h.fb_on ? b.status_back : nullptr;
         e.offsets = b.offsets;
-        uint8_t *sp = (uint8_t *)b.scratch;
-        e.rmap = (uint32_t *)sp;
-        sp += align_up((size_t)P.w * P.h * 4, 256);
-        e.pad_pts = (float2 *)sp;
-        sp += align_up((size_t)b.nboxes * b.max_corners * 8, 256);
-        e.pad_counts = (int32_t *)sp;
+        {
+            SelectScratch sc;
+            select_scratch_split(b.scratch, P.w, P.h, b.nboxes, b.max_corners, true, sc);
+            e.rmap = sc.rmap;
+            e.pad_pts = sc.pad_pts;
+            e.pad_counts = sc.pad_counts;
+            e.cand = sc.cand;
+            e.cstate = sc.cstate;
+        }
         e.w = P.w;
         e.h = P.h;
         e.nboxes = b.nboxes;

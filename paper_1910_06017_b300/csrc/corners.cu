@@ -1,21 +1,32 @@
 // corners.cu -- K2: Shi-Tomasi response and per-box corner selection.
 //
-// Three launches per call:
-//   1. response_kernel   28x64 strips of level 0, one warp each (only
-//                        strips that touch an eligible pixel of some box
-//                        when boxes are given), all in registers:
-//                        integer Scharr -> 3x3 structure tensor -> exact
-//                        R = (a+c) - isqrt((a-c)^2 + 4b^2) -> non-strict 3x3
-//                        maximum flag, packed as R | flag << 30 into a
-//                        frame-sized uint32 map.
-//   2. select_kernel     one CTA per box: R_max, candidate keys
-//                        (R << 32 | ~(y*W + x)), bitonic sort in shared memory,
-//                        greedy minimum-distance acceptance by one warp.  Boxes
-//                        with more candidates than fit in shared memory are
-//                        consumed in descending chunks found by an exact MSD
-//                        radix select over the keys.
-//   3. compact_kernel    exclusive scan of the per-box counts into the CSR
+// The response walk: 28x64 strips of level 0, one warp each (only strips
+// that touch an eligible pixel of some box when boxes are given), all in
+// registers: integer Scharr -> 3x3 structure tensor -> exact
+// R = (a+c) - isqrt((a-c)^2 + 4b^2) -> non-strict 3x3 maximum flag, the
+// value R | flag << 30 of every pixel.
+//
+// Corner selection, per call (four launches after a reset of the per-box
+// counters):
+//   1. list_kernel       the response walk into a shared-memory copy of the
+//                        strip; then, for every box the strip overlaps, R_max
+//                        of the box's pixels in the strip (atomic max) and
+//                        the keys (R << 32 | ~(y*W + x)) of its local maxima
+//                        with R > 0, appended to the box's candidate list
+//                        (CAND_CAP keys, one atomic per box and strip).
+//   2. overflow_kernel   the response walk into the frame-sized uint32 map,
+//                        only for strips that touch a box whose list
+//                        overflowed (none on ordinary frames).
+//   3. select_kernel     one CTA per box: the candidates from its list (or,
+//                        after an overflow, from one pass over its map),
+//                        bitonic sort in shared memory, greedy minimum-
+//                        distance acceptance by one warp.  Boxes with more
+//                        candidates than fit in shared memory are consumed in
+//                        descending chunks found by an exact MSD radix select
+//                        over the keys.
+//   4. compact_kernel    exclusive scan of the per-box counts into the CSR
 //                        offsets and a copy of the kept points, box by box.
+// omt_corner_response runs the walk into the map alone.
 // Everything is integer arithmetic, so the result equals the definition bit
 // for bit, and the atomics only change the order in which unique keys are
 // gathered, never the sorted order.
@@ -64,6 +75,12 @@ __device__ __forceinline__ uint32_t isqrt_est(uint64_t D, float f) {
 // gradient of its reflect-101 image (a lane shuffle for columns; for rows the
 // three texel rows are reflected around the reflected row).
 constexpr int RW = 28, RH = 64, RNT = 256, RWARPS = RNT / 32;
+// The list kernel keeps one strip's values (RW x RH words) per warp in
+// shared memory: 4 warps per CTA.
+constexpr int LNT = 128, LWARPS = LNT / 32;
+// Keys a box's candidate list holds; a box with more candidates takes the
+// map path (the select kernel's shared key capacity).
+constexpr int CAND_CAP = 1024;
 
 struct RespArgs {
     const uint8_t *img;
@@ -72,17 +89,27 @@ struct RespArgs {
     uint32_t *out;        // w*h, row-major, no padding
     const float4 *boxes;  // nullptr: whole frame
     int nboxes;
+    uint64_t *cand;       // nboxes x CAND_CAP candidate keys
+    uint32_t *cstate;     // per box: key count, R_max; then the overflow word
 };
 
+// A candidate's sort key: R above the complemented pixel index, so that
+// descending keys run by R descending, then raster index ascending.
+__device__ __forceinline__ uint64_t make_key(uint32_t R, uint32_t idx) {
+    return ((uint64_t)R << 32) | (uint64_t)(0xFFFFFFFFu - idx);
+}
+
 // Whether the strip tile at (x0, y0) holds an eligible pixel of some box
-// (always, without boxes).  Warp-uniform.
-__device__ __forceinline__ bool strip_needed(const RespArgs &a, int x0, int y0, int lane) {
+// (always, without boxes); with only_overflow, of some box whose candidate
+// list overflowed.  Warp-uniform.
+__device__ __forceinline__ bool strip_needed(const RespArgs &a, int x0, int y0, int lane,
+                                             bool only_overflow = false) {
     if (!a.boxes) return true;
     const int x1 = min(x0 + RW - 1, a.w - 1), y1 = min(y0 + RH - 1, a.h - 1);
     for (int b0 = 0; b0 < a.nboxes; b0 += 32) {
         const int b = b0 + lane;
         bool hit = false;
-        if (b < a.nboxes) {
+        if (b < a.nboxes && (!only_overflow || a.cstate[2 * b] > (uint32_t)CAND_CAP)) {
             int xlo, xhi, ylo, yhi;
             if (box_pixel_range(a.boxes[b], a.w, a.h, xlo, xhi, ylo, yhi))
                 hit = xlo <= x1 && xhi >= x0 && ylo <= y1 && yhi >= y0;
@@ -92,7 +119,13 @@ __device__ __forceinline__ bool strip_needed(const RespArgs &a, int x0, int y0, 
     return false;
 }
 
-__device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy, int lane) {
+// The response walk of the strip whose first output column is x0 and first
+// output row oy; every pixel of the strip inside the frame is handed to
+// put(yf, x, R | flag) exactly once, by the lane that owns its column
+// (lanes 2 .. 29).
+template <class Put>
+__device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy, int lane,
+                                               Put put) {
     const int x = x0 - 2 + lane;
     const bool inx = x >= 0 && x < a.w;
     const int cx = reflect101(x, a.w);
@@ -191,8 +224,7 @@ __device__ __forceinline__ void response_strip(const RespArgs &a, int x0, int oy
         const int yf = g - 2;
         const bool interior = x >= 1 && x <= a.w - 2 && yf >= 1 && yf <= a.h - 2;
         const uint32_t flag = interior && Rp >= max(M2, max(M1, Mn)) ? MAX_FLAG : 0u;
-        if (s >= 4 && yf < a.h && lane >= 2 && lane <= 29 && inx)
-            a.out[(int64_t)yf * a.w + x] = Rp | flag;
+        if (s >= 4 && yf < a.h && lane >= 2 && lane <= 29 && inx) put(yf, x, Rp | flag);
         Ha2 = Ha1;
         Hb2 = Hb1;
         Hc2 = Hc1;
@@ -230,40 +262,185 @@ __device__ __forceinline__ void strip_origin(int t, int w, int &x0, int &y0) {
     y0 = ty * RH;
 }
 
+// The map form: every value into the frame-sized map.
+__device__ __forceinline__ void strip_to_map(const RespArgs &a, int x0, int y0, int lane) {
+    response_strip(a, x0, y0, lane,
+                   [&](int yf, int x, uint32_t v) { a.out[(int64_t)yf * a.w + x] = v; });
+}
+
+// The list form: the strip's values into this warp's shared copy, then, for
+// each box the strip overlaps, its part of the box's R_max (atomic max) and
+// the keys of its local maxima with R > 0, appended to the box's list (one
+// atomic per box and strip: count, reserve, write).  Appends past CAND_CAP
+// are dropped; the count still grows, marking the overflow, and the
+// stream's overflow word is set.  Every pixel of the frame lies in exactly
+// one strip, so a box's list ends with the keys of exactly its candidates
+// whenever it did not overflow (in an order that depends on the schedule;
+// the select kernel sorts them).
+__device__ __forceinline__ void strip_to_lists(const RespArgs &a, int x0, int y0, int lane,
+                                               uint32_t *buf) {
+    response_strip(a, x0, y0, lane,
+                   [&](int yf, int x, uint32_t v) { buf[(yf - y0) * RW + (x - x0)] = v; });
+    __syncwarp();
+    const int x1 = min(x0 + RW - 1, a.w - 1), y1 = min(y0 + RH - 1, a.h - 1);
+    const int x = x0 + lane;  // lane c reads strip column c
+    const uint32_t *cp = buf + (lane < RW ? lane : 0);
+    for (int b0 = 0; b0 < a.nboxes; b0 += 32) {
+        const int b = b0 + lane;
+        int xlo = 0, xhi = -1, ylo = 0, yhi = -1;
+        bool hit = false;
+        if (b < a.nboxes && box_pixel_range(a.boxes[b], a.w, a.h, xlo, xhi, ylo, yhi))
+            hit = xlo <= x1 && xhi >= x0 && ylo <= y1 && yhi >= y0;
+        unsigned m = __ballot_sync(FULL_MASK, hit);
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const int bx0 = max(__shfl_sync(FULL_MASK, xlo, j), x0);
+            const int bx1 = min(__shfl_sync(FULL_MASK, xhi, j), x1);
+            const int by0 = max(__shfl_sync(FULL_MASK, ylo, j), y0);
+            const int by1 = min(__shfl_sync(FULL_MASK, yhi, j), y1);
+            const int box = b0 + j;
+            const bool col = lane < RW && x >= bx0 && x <= bx1;
+            uint32_t rm = 0;
+            int c = 0;
+            for (int y = by0; y <= by1; ++y) {
+                const uint32_t v = col ? cp[(y - y0) * RW] : 0u;
+                const uint32_t R = v & R_MASK;
+                rm = max(rm, R);
+                c += (v & MAX_FLAG) && R > 0;
+            }
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL_MASK, incl, o);
+                if (lane >= o) incl += t;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rm = max(rm, __shfl_xor_sync(FULL_MASK, rm, o));
+            const int total = __shfl_sync(FULL_MASK, incl, 31);
+            uint32_t base = 0;
+            if (lane == 0) {
+                uint32_t *st = a.cstate + 2 * box;
+                if (rm) atomicMax(st + 1, rm);
+                if (total) {
+                    base = atomicAdd(st, (uint32_t)total);
+                    if (base + (uint32_t)total > (uint32_t)CAND_CAP) a.cstate[2 * a.nboxes] = 1u;
+                }
+            }
+            base = __shfl_sync(FULL_MASK, base, 0);
+            if (total && base < (uint32_t)CAND_CAP) {
+                uint32_t pos = base + (uint32_t)(incl - c);
+                uint64_t *out = a.cand + (int64_t)box * CAND_CAP;
+                for (int y = by0; y <= by1 && c > 0; ++y) {
+                    const uint32_t v = col ? cp[(y - y0) * RW] : 0u;
+                    const uint32_t R = v & R_MASK;
+                    if ((v & MAX_FLAG) && R > 0) {
+                        if (pos < (uint32_t)CAND_CAP) out[pos] = make_key(R, (uint32_t)(y * a.w + x));
+                        ++pos;
+                        --c;
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(RNT) response_kernel(RespArgs a, int total) {
     const int lane = threadIdx.x & 31;
     for (int t = blockIdx.x * RWARPS + (threadIdx.x >> 5); t < total; t += gridDim.x * RWARPS) {
         int x0, y0;
         strip_origin(t, a.w, x0, y0);
-        if (strip_needed(a, x0, y0, lane)) response_strip(a, x0, y0, lane);
+        if (strip_needed(a, x0, y0, lane)) strip_to_map(a, x0, y0, lane);
     }
 }
 
-__global__ void __launch_bounds__(RNT) response_batch_kernel(const uint8_t *table) {
+// The strips of a frame for the candidate lists (boxes given).
+__global__ void __launch_bounds__(LNT) list_kernel(RespArgs a, int total) {
+    __shared__ uint32_t strip[LWARPS][RW * RH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = blockIdx.x * LWARPS + warp; t < total; t += gridDim.x * LWARPS) {
+        int x0, y0;
+        strip_origin(t, a.w, x0, y0);
+        if (strip_needed(a, x0, y0, lane)) strip_to_lists(a, x0, y0, lane, strip[warp]);
+    }
+}
+
+// The map, only where a box's list overflowed (the stream's overflow word).
+__global__ void __launch_bounds__(RNT) overflow_kernel(RespArgs a, int total) {
+    if (a.cstate[2 * a.nboxes] == 0u) return;
+    const int lane = threadIdx.x & 31;
+    for (int t = blockIdx.x * RWARPS + (threadIdx.x >> 5); t < total; t += gridDim.x * RWARPS) {
+        int x0, y0;
+        strip_origin(t, a.w, x0, y0);
+        if (strip_needed(a, x0, y0, lane, true)) strip_to_map(a, x0, y0, lane);
+    }
+}
+
+__device__ __forceinline__ RespArgs stream_resp_args(const StreamEntry &e) {
+    RespArgs a;
+    a.img = e.P[0].img;
+    a.pitch = e.P[0].img_pitch;
+    a.w = e.w;
+    a.h = e.h;
+    a.out = e.rmap;
+    a.boxes = e.boxes;
+    a.nboxes = e.nboxes;
+    a.cand = e.cand;
+    a.cstate = e.cstate;
+    return a;
+}
+
+// Per-box counters and R_max, and the overflow word, of every stream back
+// to zero (a CTA per stream).
+__global__ void reset_lists_batch_kernel(const uint8_t *table) {
+    const BatchView t(table);
+    const int si = blockIdx.x;
+    if (si >= t.nstreams()) return;
+    const StreamEntry &e = t.stream(si);
+    for (int i = threadIdx.x; i <= 2 * e.nboxes; i += blockDim.x) e.cstate[i] = 0u;
+}
+
+__global__ void __launch_bounds__(LNT) list_batch_kernel(const uint8_t *table) {
+    __shared__ uint32_t strip[LWARPS][RW * RH];
     const BatchView t(table);
     const int32_t *pre = t.resp_prefix();
     const int total = pre[t.nstreams()];
-    const int lane = threadIdx.x & 31;
-    for (int gi = blockIdx.x * RWARPS + (threadIdx.x >> 5); gi < total; gi += gridDim.x * RWARPS) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int gi = blockIdx.x * LWARPS + warp; gi < total; gi += gridDim.x * LWARPS) {
         const int si = find_segment(pre, t.nstreams(), gi);
         const StreamEntry &e = t.stream(si);
-        RespArgs a;
-        a.img = e.P[0].img;
-        a.pitch = e.P[0].img_pitch;
-        a.w = e.w;
-        a.h = e.h;
-        a.out = e.rmap;
-        a.boxes = e.boxes;
-        a.nboxes = e.nboxes;
+        if (e.nboxes == 0) continue;
+        const RespArgs a = stream_resp_args(e);
         int x0, y0;
         strip_origin(gi - pre[si], e.w, x0, y0);
-        if (strip_needed(a, x0, y0, lane)) response_strip(a, x0, y0, lane);
+        if (strip_needed(a, x0, y0, lane)) strip_to_lists(a, x0, y0, lane, strip[warp]);
+    }
+}
+
+// Stream blockIdx.y's strips, gridDim.x CTAs per stream; a stream without
+// an overflowed list leaves at once.
+__global__ void __launch_bounds__(RNT) overflow_batch_kernel(const uint8_t *table) {
+    const BatchView t(table);
+    const int si = blockIdx.y;
+    if (si >= t.nstreams()) return;
+    const StreamEntry &e = t.stream(si);
+    if (e.nboxes == 0 || e.cstate[2 * e.nboxes] == 0u) return;
+    const int32_t *pre = t.resp_prefix();
+    const int n = pre[si + 1] - pre[si];
+    const int lane = threadIdx.x & 31;
+    const RespArgs a = stream_resp_args(e);
+    for (int ti = blockIdx.x * RWARPS + (threadIdx.x >> 5); ti < n; ti += gridDim.x * RWARPS) {
+        int x0, y0;
+        strip_origin(ti, e.w, x0, y0);
+        if (strip_needed(a, x0, y0, lane, true)) strip_to_map(a, x0, y0, lane);
     }
 }
 
 // ------------------------------------------------------------ select kernel
 constexpr int SNT = 128;
 constexpr int SCAP = 1024;   // candidate keys held in shared memory
+static_assert(CAND_CAP == SCAP, "a box's whole list fits the shared keys");
 constexpr int GCAP = 4096;   // cells of the accepted-point grid in shared memory
 
 // Keys sorted per chunk for a box keeping up to maxc corners: enough for the
@@ -292,11 +469,9 @@ struct SelectArgs {
     int cell;       // side of the accepted-point grid cells, max(1, floor(sqrt(md2c / 2)))
     float2 *pad_pts;
     int32_t *pad_counts;
+    const uint64_t *cand;   // per box: CAND_CAP candidate keys (list_kernel)
+    const uint32_t *cstate; // per box: key count, R_max; null: map path only
 };
-
-__device__ __forceinline__ uint64_t make_key(uint32_t R, uint32_t idx) {
-    return ((uint64_t)R << 32) | (uint64_t)(0xFFFFFFFFu - idx);
-}
 
 // One compare-exchange of the bitonic network for the key at index i, held
 // by this lane, against index i ^ j in the same warp (j < 32).
@@ -580,10 +755,22 @@ __device__ void select_box(const SelectArgs &a, int box, int acc_cap) {
         s_nacc = 0;
     }
     __syncthreads();
-    uint32_t m = gather_keys<false>(a, xlo, xhi, ylo, yhi, 0, keys, &s_count);
+    // The box's candidates: from its list when it holds them all (with R_max
+    // from the list kernel), else from one pass over its map.
+    const uint32_t listed = a.cstate ? a.cstate[2 * box] : 0xFFFFFFFFu;
+    if (listed <= (uint32_t)CAND_CAP) {
+        const uint64_t *src = a.cand + (int64_t)box * CAND_CAP;
+        for (int i = tid; i < (int)listed; i += SNT) keys[i] = src[i];
+        if (tid == 0) {
+            s_rmax = a.cstate[2 * box + 1];
+            s_count = (int)listed;
+        }
+    } else {
+        uint32_t m = gather_keys<false>(a, xlo, xhi, ylo, yhi, 0, keys, &s_count);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
-    if (lane == 0) atomicMax(&s_rmax, m);
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
+        if (lane == 0) atomicMax(&s_rmax, m);
+    }
     __syncthreads();
     const int64_t thr = (int64_t)a.qnum * (int64_t)s_rmax;
     int total = s_count;
@@ -745,6 +932,8 @@ __global__ void __launch_bounds__(SNT, 8) select_batch_kernel(const uint8_t *tab
         a.cell = h.cell;
         a.pad_pts = e.pad_pts;
         a.pad_counts = e.pad_counts;
+        a.cand = e.cand;
+        a.cstate = e.cstate;
         select_box(a, gb - pre[si], acc_cap);
     }
 }
@@ -814,9 +1003,25 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t select_scratch_bytes(int w, int h, int nboxes, int max_corners) {
-    return align256((size_t)w * h * 4) + align256((size_t)nboxes * max_corners * 8) +
-           align256((size_t)nboxes * 4 + 4);
+size_t select_scratch_bytes(int w, int h, int nboxes, int max_corners, bool lists) {
+    const size_t map = align256((size_t)w * h * 4) + align256((size_t)nboxes * max_corners * 8) +
+                       align256((size_t)nboxes * 4 + 4);
+    if (!lists) return map;
+    return map + align256((size_t)nboxes * CAND_CAP * 8) + align256((size_t)nboxes * 8 + 4);
+}
+
+void select_scratch_split(void *scratch, int w, int h, int nboxes, int max_corners, bool lists,
+                          SelectScratch &out) {
+    uint8_t *sp = (uint8_t *)scratch;
+    out.rmap = (uint32_t *)sp;
+    sp += align256((size_t)w * h * 4);
+    out.pad_pts = (float2 *)sp;
+    sp += align256((size_t)nboxes * max_corners * 8);
+    out.pad_counts = (int32_t *)sp;
+    sp += align256((size_t)nboxes * 4 + 4);
+    out.cand = lists ? (uint64_t *)sp : nullptr;
+    sp += align256((size_t)nboxes * CAND_CAP * 8);
+    out.cstate = lists ? (uint32_t *)sp : nullptr;
 }
 
 cudaError_t launch_corner_response(const omt_pyramid &pyr, uint32_t *out, const float4 *boxes,
@@ -836,18 +1041,41 @@ cudaError_t launch_corner_response(const omt_pyramid &pyr, uint32_t *out, const 
 
 cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, int nboxes,
                                   const omt_params &prm, void *scratch, float2 *pts,
-                                  int32_t *offsets, cudaStream_t s) {
-    uint8_t *sp = (uint8_t *)scratch;
-    uint32_t *rmap = (uint32_t *)sp;
-    sp += align256((size_t)pyr.w * pyr.h * 4);
-    float2 *pad_pts = (float2 *)sp;
-    sp += align256((size_t)nboxes * prm.max_corners * 8);
-    int32_t *pad_counts = (int32_t *)sp;
+                                  int32_t *offsets, bool lists, cudaStream_t s) {
+    SelectScratch sc;
+    select_scratch_split(scratch, pyr.w, pyr.h, nboxes, prm.max_corners, lists, sc);
+    uint32_t *rmap = sc.rmap;
+    float2 *pad_pts = sc.pad_pts;
+    int32_t *pad_counts = sc.pad_counts;
 
     cudaError_t e;
-    if (nboxes > 0) {
+    if (nboxes > 0 && !lists) {
+        // the map of every strip that touches a box
         e = launch_corner_response(pyr, rmap, boxes, nboxes, s);
         if (e != cudaSuccess) return e;
+    } else if (nboxes > 0) {
+        // candidate lists, then the map where a list overflowed
+        e = cudaMemsetAsync(sc.cstate, 0, ((size_t)nboxes * 2 + 1) * 4, s);
+        if (e != cudaSuccess) return e;
+        RespArgs r;
+        r.img = (const uint8_t *)pyr.base + pyr.lv[0].img_off;
+        r.pitch = pyr.lv[0].img_pitch;
+        r.w = pyr.w;
+        r.h = pyr.h;
+        r.out = rmap;
+        r.boxes = boxes;
+        r.nboxes = nboxes;
+        r.cand = sc.cand;
+        r.cstate = sc.cstate;
+        const int tiles = response_tiles(pyr.w, pyr.h);
+        list_kernel<<<(tiles + LWARPS - 1) / LWARPS, LNT, 0, s>>>(r, tiles);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        overflow_kernel<<<(tiles + RWARPS - 1) / RWARPS, RNT, 0, s>>>(r, tiles);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (nboxes > 0) {
         SelectArgs a;
         a.rmap = rmap;
         a.w = pyr.w;
@@ -864,6 +1092,8 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
         while (2 * (int64_t)(a.cell + 1) * (a.cell + 1) <= a.md2c) ++a.cell;
         a.pad_pts = pad_pts;
         a.pad_counts = pad_counts;
+        a.cand = sc.cand;
+        a.cstate = sc.cstate;
         const size_t smem = select_smem_bytes(prm.max_corners);
         e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
@@ -883,10 +1113,16 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = (max_resp_tiles + RWARPS - 1) / RWARPS;
-    grid = grid < sms * 8 ? grid : sms * 8;
-    response_batch_kernel<<<grid > 0 ? grid : 1, RNT, 0, s>>>(table);
+    reset_lists_batch_kernel<<<max_streams > 0 ? max_streams : 1, 256, 0, s>>>(table);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int grid = (max_resp_tiles + LWARPS - 1) / LWARPS;
+    grid = grid < sms * 16 ? grid : sms * 16;
+    list_batch_kernel<<<grid > 0 ? grid : 1, LNT, 0, s>>>(table);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    overflow_batch_kernel<<<dim3(8, max_streams > 0 ? max_streams : 1), RNT, 0, s>>>(table);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (max_boxes > 0) {
         const size_t smem = select_smem_bytes(max_corners);

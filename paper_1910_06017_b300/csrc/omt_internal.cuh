@@ -110,6 +110,8 @@ struct StreamEntry {
     uint32_t *rmap;                    // scratch: response map
     float2 *pad_pts;                   // scratch: per-box corner lists
     int32_t *pad_counts;               // scratch: per-box counts
+    uint64_t *cand;                    // scratch: per-box candidate keys
+    uint32_t *cstate;                  // scratch: per-box key count and R_max, overflow word
     int32_t w, h, nboxes, maxc;
     uint32_t tm_ok, tm_ok_back;        // bit 3L + m: LK map m of level L (forward, backward) valid
     uint32_t pyr_maps_ok;              // bit L: the tile map of level L of frame t+1's pyramid
@@ -204,11 +206,31 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
 cudaError_t launch_corner_response(const omt_pyramid &pyr, uint32_t *out, const float4 *boxes,
                                    int nboxes, cudaStream_t s);
 
+// lists: the candidate-list path (list, overflow, select kernels); false:
+// the map path alone (the map of every strip touching a box, then select),
+// whose scratch is smaller.
 cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, int nboxes,
                                   const omt_params &prm, void *scratch, float2 *pts,
-                                  int32_t *offsets, cudaStream_t s);
+                                  int32_t *offsets, bool lists, cudaStream_t s);
 
-size_t select_scratch_bytes(int w, int h, int nboxes, int max_corners);
+size_t select_scratch_bytes(int w, int h, int nboxes, int max_corners, bool lists = true);
+
+// omt_select_corners with the path chosen: lists as in launch_select_corners
+// (the public call uses the lists; omt_select_corners_static the map path).
+int select_corners_entry(const omt_pyramid *pyr, const float *boxes, int32_t nboxes,
+                         const omt_params *prm, void *scratch, size_t scratch_bytes, float *pts,
+                         int32_t *offsets, bool lists, void *stream);
+
+// The parts of a corner-selection scratch buffer (select_scratch_bytes).
+struct SelectScratch {
+    uint32_t *rmap;      // w x h response map (written only where a list overflowed)
+    float2 *pad_pts;     // nboxes x max_corners selected corners
+    int32_t *pad_counts; // nboxes counts
+    uint64_t *cand;      // nboxes x 1024 candidate keys (null on the map path)
+    uint32_t *cstate;    // nboxes x (count, R_max), then one overflow word (null on the map path)
+};
+void select_scratch_split(void *scratch, int w, int h, int nboxes, int max_corners, bool lists,
+                          SelectScratch &out);
 
 // Batched forms: every launch covers all streams of the table in `table`
 // (device memory); grids depend only on the capacities.

@@ -48,10 +48,13 @@ extern "C" int omt_select_corners_static(const omt_pyramid *pyr, const float *bo
         return OMT_EINVAL;
     if (!offsets) return OMT_EINVAL;
     if (pyr->w < 1 || pyr->h < 1) return OMT_EINVAL;
-    const size_t need = omt_corner_scratch_bytes(pyr->w, pyr->h, nboxes, prm->max_corners);
+    // the map path: its scratch is the response map and the per-box corner
+    // slots, without the candidate lists
+    const size_t need = omt::select_scratch_bytes(pyr->w, pyr->h, nboxes, prm->max_corners, false);
     if (need == 0 || need > (size_t)OMT_STATIC_SCRATCH_BYTES) return OMT_ENOMEM;
     void *scratch = nullptr;
     const int rc = scratch_address(&scratch);
     if (rc != OMT_OK) return rc;
-    return omt_select_corners(pyr, boxes, nboxes, prm, scratch, need, pts, offsets, stream);
+    return omt::select_corners_entry(pyr, boxes, nboxes, prm, scratch, need, pts, offsets, false,
+                                     stream);
 }

@@ -103,11 +103,19 @@ def test_static_matches_caller_scratch_twice(omt):
     _same((pts, off), _with_scratch(omt, P1, prm1, b1))
 
 
+def _static_need(w, h, nboxes, max_corners):
+    """The array bytes a call needs, by the rule the header states: the
+    response map (4 bytes per pixel), 8 bytes per box-corner slot and 4 per
+    box (plus one word), each part rounded up to 256 bytes."""
+    up = lambda v: (v + 255) // 256 * 256
+    return up(w * h * 4) + up(nboxes * max_corners * 8) + up(nboxes * 4 + 4)
+
+
 def test_static_rejects_frames_beyond_its_array(omt):
     # a 4K frame's response map alone (3840*2160*4 bytes) exceeds the array
     f = np.zeros((2160, 3840), np.uint8)
     P, prm, b = _case(omt, f, np.array([[0, 0, 100, 100]], np.float32), 10)
-    assert omt.corner_scratch_bytes(3840, 2160, 1, 10) > omt.STATIC_SCRATCH_BYTES
+    assert _static_need(3840, 2160, 1, 10) > omt.STATIC_SCRATCH_BYTES
     rc, pts, off = _static_abi(omt, P, prm, b)
     assert rc == omt.ENOMEM
     assert np.all(off == -1)  # nothing was launched
@@ -116,8 +124,8 @@ def test_static_rejects_frames_beyond_its_array(omt):
 def test_static_capacity_at_1080p(omt):
     # a 1920x1080 frame leaves the array room for about 1.05 million
     # box-corner slots: 1,000 boxes of 1,000 corners fit, 1,100 do not
-    assert omt.corner_scratch_bytes(1920, 1080, 1000, 1000) <= omt.STATIC_SCRATCH_BYTES
-    assert omt.corner_scratch_bytes(1920, 1080, 1100, 1000) > omt.STATIC_SCRATCH_BYTES
+    assert _static_need(1920, 1080, 1000, 1000) <= omt.STATIC_SCRATCH_BYTES
+    assert _static_need(1920, 1080, 1100, 1000) > omt.STATIC_SCRATCH_BYTES
     clip = synth.affine_clip(n_frames=1)
     rng = np.random.default_rng(8)
     boxes = synth.uniform_boxes(rng, 1920, 1080, 1000)
