@@ -424,7 +424,15 @@ def run_omt(args, ws, rank, local):
             "l2": "working set > L2 (126 MB): no flush", "parallelism": f"replicas x{ws}",
             "lk_launch": {"warps_per_cta": B.caps.lk_warps or 4, "queue_chunk": B.caps.lk_chunk or 1,
                           "autotuned": bool(tune_ms),
-                          "candidates_ms": {f"{w}x{c}": round(t, 4) for (w, c), t in tune_ms.items()}}},
+                          "candidates_ms": {f"{w}x{c}": round(t, 4)
+                                            for (w, c), t in tune_ms.get("lk", {}).items()}},
+            "pyramid_launch": {"ctas_per_sm": B.caps.pyr_ctas_per_sm,
+                               "candidates_ms": {str(c): round(t, 4)
+                                                 for c, t in tune_ms.get("pyramid", {}).items()}},
+            "corner_launch": {"list_ctas_per_sm": B.caps.corner_ctas_per_sm,
+                              "select_ctas_per_sm": B.caps.select_ctas_per_sm,
+                              "candidates_ms": {f"{c}x{s}": round(t, 4)
+                                                for (c, s), t in tune_ms.get("corners", {}).items()}}},
         "e2e": {"value": ok_total / e2e_s, "unit": "points/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "roofline": {"kernel": "lk_batch_kernel", "bound": "alu", "achieved": achieved,

@@ -377,6 +377,10 @@ typedef struct omt_batch_caps {
      * warp in a fixed order), so a tuner may pick any; an autotuner in the
      * Python binding times the candidates on the caller's own batch. */
     int32_t lk_warps, lk_ctas_per_sm, lk_chunk;
+    /* CTAs per SM (0..32; 0 = as many as fit) of the pyramid kernels, of the
+     * corner-list kernel and of the select kernel: fewer CTAs take more
+     * tiles, strips or boxes each.  No result depends on them either. */
+    int32_t pyr_ctas_per_sm, corner_ctas_per_sm, select_ctas_per_sm;
     int32_t reserved;     /* 0 */
 } omt_batch_caps;
 

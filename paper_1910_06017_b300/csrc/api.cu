@@ -9,7 +9,7 @@ using namespace omt;
 
 namespace {
 
-constexpr int32_t kVersion = 300;  // 0.3.0: OMT_PT_LOST_TIMEOUT, omt_debug_fail_lk_wait
+constexpr int32_t kVersion = 400;  // 0.4.0: K1/K2 launch shapes in omt_batch_caps
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -195,7 +195,10 @@ bool caps_ok(const omt_batch_caps *c) {
            c->max_boxes >= 0 && c->max_w >= 1 && c->max_h >= 1 && c->max_w <= (1 << 16) &&
            c->max_h <= (1 << 16) && c->max_corners >= 0 && c->max_corners <= OMT_MAX_CORNERS &&
            c->lk_warps >= 0 && c->lk_warps <= 8 && c->lk_ctas_per_sm >= 0 &&
-           c->lk_ctas_per_sm <= 32 && c->lk_chunk >= 0 && c->lk_chunk <= 16 && c->reserved == 0;
+           c->lk_ctas_per_sm <= 32 && c->lk_chunk >= 0 && c->lk_chunk <= 16 &&
+           c->pyr_ctas_per_sm >= 0 && c->pyr_ctas_per_sm <= 32 && c->corner_ctas_per_sm >= 0 &&
+           c->corner_ctas_per_sm <= 32 && c->select_ctas_per_sm >= 0 &&
+           c->select_ctas_per_sm <= 32 && c->reserved == 0;
 }
 
 void fill_levels(const omt_pyramid &p, LevelView *out) {
@@ -360,12 +363,13 @@ int omt_batch_phase(const void *dev_table, const omt_batch_caps *caps, const omt
                 lh = (lh + 1) >> 1;
             }
             return from_cuda(launch_pyramid_batch(dt, prm->levels, prm->storage, max_tiles,
-                                                  caps->max_streams, s));
+                                                  caps->max_streams, caps->pyr_ctas_per_sm, s));
         }
         case OMT_PHASE_CORNERS:
             return from_cuda(launch_corners_batch(
                 dt, caps->max_streams, caps->max_streams * response_tiles(caps->max_w, caps->max_h),
-                caps->max_boxes, caps->max_corners, s));
+                caps->max_boxes, caps->max_corners, caps->corner_ctas_per_sm,
+                caps->select_ctas_per_sm, s));
         case OMT_PHASE_FB:
             if (!(prm->fb_max >= 0.0f)) return OMT_OK;
             return from_cuda(launch_lk_batch(dt, prm->storage, prm->win, caps->lk_warps,

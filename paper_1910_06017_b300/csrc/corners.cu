@@ -1109,7 +1109,8 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
 int response_tiles(int w, int h) { return ((w + RW - 1) / RW) * ((h + RH - 1) / RH); }
 
 cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_resp_tiles,
-                                 int max_boxes, int max_corners, cudaStream_t s) {
+                                 int max_boxes, int max_corners, int list_ctas_per_sm,
+                                 int select_ctas_per_sm, cudaStream_t s) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1117,7 +1118,8 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int grid = (max_resp_tiles + LWARPS - 1) / LWARPS;
-    grid = grid < sms * 16 ? grid : sms * 16;
+    const int list_cap = sms * (list_ctas_per_sm > 0 ? list_ctas_per_sm : 16);
+    grid = grid < list_cap ? grid : list_cap;
     list_batch_kernel<<<grid > 0 ? grid : 1, LNT, 0, s>>>(table);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1132,6 +1134,7 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_batch_kernel, SNT, smem);
         if (per_sm < 1) per_sm = 1;
+        if (select_ctas_per_sm > 0 && select_ctas_per_sm < per_sm) per_sm = select_ctas_per_sm;
         grid = max_boxes < sms * per_sm ? max_boxes : sms * per_sm;
         select_batch_kernel<<<grid, SNT, smem, s>>>(table, max_corners);
         e = cudaGetLastError();

@@ -241,10 +241,12 @@ size_t assign_workspace(int n);   // host bytes of the assignment's work arrays
 void assign_max_iou(const double *iou, int na, int nb, const uint8_t *active, double iou_min,
                     void *ws, int32_t *match_a, int32_t *match_b);   // K1 tiles of a level of this size
 int response_tiles(int w, int h);  // K2 response tiles of a frame of this size
+// ctas_per_sm (0 = as many as fit): the launch shapes of omt_batch_caps.
 cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
-                                 int max_streams, cudaStream_t s);
+                                 int max_streams, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_resp_tiles,
-                                 int max_boxes, int max_corners, cudaStream_t s);
+                                 int max_boxes, int max_corners, int list_ctas_per_sm,
+                                 int select_ctas_per_sm, cudaStream_t s);
 // LK over every point of a batch: warps per CTA, CTAs per SM and work-queue
 // chunk as in omt_batch_caps (0 = default).
 // Encodes the LK window maps of every level of P (frame t) and J (frame

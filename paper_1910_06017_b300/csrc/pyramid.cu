@@ -904,24 +904,33 @@ cudaError_t launch_level(const LevelArgs &a, cudaStream_t s) {
 
 template <int ST, int FMT, int PATH>
 cudaError_t launch_batch_level_k(const uint8_t *table, int L, int max_tiles, int max_streams,
-                                 cudaStream_t s) {
+                                 int ctas_per_sm, cudaStream_t s) {
     const size_t smem = batch_smem_bytes<FMT>(max_streams);
     static int cap[64] = {0};
     static size_t cap_smem[64] = {0};
     int grid = 0;
     cudaError_t e = grid_for(pyramid_batch_kernel<ST, FMT, PATH>, max_tiles, smem, cap, cap_smem, grid, RING_NT);
     if (e != cudaSuccess) return e;
+    if (ctas_per_sm > 0) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (grid > sms * ctas_per_sm) grid = sms * ctas_per_sm;
+    }
     pyramid_batch_kernel<ST, FMT, PATH><<<grid, RING_NT, smem, s>>>(table, L);
     return cudaGetLastError();
 }
 
 template <int ST, int FMT>
 cudaError_t launch_batch_level(const uint8_t *table, int L, int max_tiles, int max_streams,
-                               cudaStream_t s) {
+                               int ctas_per_sm, cudaStream_t s) {
     switch (FMT == FMT_U8 ? PATH_FLOAT : level_path(level_frac(L))) {
-        case PATH_SPLIT: return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, max_streams, s);
-        case PATH_INT64: return launch_batch_level_k<ST, FMT, PATH_INT64>(table, L, max_tiles, max_streams, s);
-        default: return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, max_streams, s);
+        case PATH_SPLIT:
+            return launch_batch_level_k<ST, FMT, PATH_SPLIT>(table, L, max_tiles, max_streams, ctas_per_sm, s);
+        case PATH_INT64:
+            return launch_batch_level_k<ST, FMT, PATH_INT64>(table, L, max_tiles, max_streams, ctas_per_sm, s);
+        default:
+            return launch_batch_level_k<ST, FMT, PATH_FLOAT>(table, L, max_tiles, max_streams, ctas_per_sm, s);
     }
 }
 
@@ -972,16 +981,17 @@ cudaError_t launch_pyramid(const uint8_t *frame, int w, int h, size_t pitch,
 }
 
 cudaError_t launch_pyramid_batch(const uint8_t *table, int levels, int storage, int max_tiles[],
-                                 int max_streams, cudaStream_t s) {
+                                 int max_streams, int ctas_per_sm, cudaStream_t s) {
     for (int L = 0; L < levels; ++L) {
         const int mt = max_tiles[L] > 0 ? max_tiles[L] : 1;
+        const int c = ctas_per_sm;
         cudaError_t e;
         if (storage == OMT_F32)
-            e = L == 0 ? launch_batch_level<OMT_F32, FMT_U8>(table, L, mt, max_streams, s)
-                       : launch_batch_level<OMT_F32, FMT_F32>(table, L, mt, max_streams, s);
+            e = L == 0 ? launch_batch_level<OMT_F32, FMT_U8>(table, L, mt, max_streams, c, s)
+                       : launch_batch_level<OMT_F32, FMT_F32>(table, L, mt, max_streams, c, s);
         else
-            e = L == 0 ? launch_batch_level<OMT_F16, FMT_U8>(table, L, mt, max_streams, s)
-                       : launch_batch_level<OMT_F16, FMT_H16>(table, L, mt, max_streams, s);
+            e = L == 0 ? launch_batch_level<OMT_F16, FMT_U8>(table, L, mt, max_streams, c, s)
+                       : launch_batch_level<OMT_F16, FMT_H16>(table, L, mt, max_streams, c, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

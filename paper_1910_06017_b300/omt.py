@@ -13,7 +13,7 @@ from ctypes import POINTER, Structure, c_float, c_int32, c_int64, c_size_t, c_ui
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libomt.so")
-ABI_VERSION = 300   # the library version whose structure layouts this binding mirrors
+ABI_VERSION = 400   # the library version whose structure layouts this binding mirrors
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECHECK = 0, -1, -2, -3, -4, -5
 F32, F16 = 0, 1
@@ -90,7 +90,8 @@ class BatchCaps(Structure):
     _fields_ = [("max_streams", c_int32), ("max_boxes", c_int32), ("max_w", c_int32),
                 ("max_h", c_int32), ("max_corners", c_int32),
                 ("lk_warps", c_int32), ("lk_ctas_per_sm", c_int32), ("lk_chunk", c_int32),
-                ("reserved", c_int32)]
+                ("pyr_ctas_per_sm", c_int32), ("corner_ctas_per_sm", c_int32),
+                ("select_ctas_per_sm", c_int32), ("reserved", c_int32)]
 
 
 _lib = None
@@ -729,39 +730,61 @@ class BatchTracker:
 
     # Launch shapes the autotuner tries: (warps per CTA, points per work-queue take).
     TUNE_CANDIDATES = tuple((w, c) for w in (2, 4, 8) for c in (1, 2, 4))
+    # CTAs per SM of the pyramid kernels, and (list kernel, select kernel) of
+    # the corner phase; 0 = as many as fit
+    TUNE_PYRAMID = (0, 1, 2, 4)
+    TUNE_CORNERS = tuple((c, s) for c in (0, 4, 8) for s in (0, 2, 4))
+
+    def _time_phase(self, phase, reps, stream, setup=()):
+        """Median CUDA-event time (ms) of `phase` over `reps` runs after one
+        untimed run; the phases in `setup` run before each (not timed)."""
+        import torch
+        par = self.cur
+        ms = []
+        for k in range(reps + 1):
+            for p in setup:
+                batch_phase(self.dev_tables[par], self.caps, self.params, p, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            batch_phase(self.dev_tables[par], self.caps, self.params, phase, stream)
+            e1.record()
+            e1.synchronize()
+            if k:
+                ms.append(e0.elapsed_time(e1))
+        return sorted(ms)[len(ms) // 2]
 
     def autotune(self, candidates=None, reps: int = 3, stream=None) -> dict:
-        """Pick the batched LK launch shape that is fastest on this batch.
+        """Pick the batched launch shapes that are fastest on this batch.
 
-        Runs the pyramid and corner phases of the next step once (so the
-        points exist), then times the LK phase for every candidate (warps
-        per CTA, work-queue chunk) with CUDA events, the median of `reps`
-        runs after one untimed run, and keeps the fastest in self.caps.  No
-        result depends on the shape.  The state afterwards is as before the
+        Each phase's shape is timed alone with CUDA events on the caller's
+        own batch (the median of `reps` runs after one untimed run) and the
+        fastest is kept in self.caps: CTAs per SM of the pyramid kernels
+        (TUNE_PYRAMID), CTAs per SM of the corner-list and select kernels
+        (TUNE_CORNERS, with the counters reset by the phase itself), then,
+        with the corners of frame t selected, warps per CTA and work-queue
+        chunk of the LK kernel (`candidates`, default TUNE_CANDIDATES).  No
+        result depends on any shape.  The state afterwards is as before the
         call except for the rebuilt frame t+1 pyramids; captured graphs are
-        dropped (capture again).  Returns {(warps, chunk): ms}."""
-        import torch
-        cands = list(candidates or self.TUNE_CANDIDATES)
-        par = self.cur
-        for phase in (PHASE_PYRAMID, PHASE_CORNERS):
-            batch_phase(self.dev_tables[par], self.caps, self.params, phase, stream)
-        times = {}
-        for w, c in cands:
+        dropped (capture again).  Returns {"lk": {(warps, chunk): ms},
+        "pyramid": {ctas: ms}, "corners": {(list_ctas, select_ctas): ms}}."""
+        out = {"pyramid": {}, "corners": {}, "lk": {}}
+        for c in self.TUNE_PYRAMID:
+            self.caps.pyr_ctas_per_sm = int(c)
+            out["pyramid"][int(c)] = self._time_phase(PHASE_PYRAMID, reps, stream)
+        self.caps.pyr_ctas_per_sm = min(out["pyramid"], key=out["pyramid"].get)
+        for c, s in self.TUNE_CORNERS:
+            self.caps.corner_ctas_per_sm, self.caps.select_ctas_per_sm = int(c), int(s)
+            out["corners"][(int(c), int(s))] = self._time_phase(PHASE_CORNERS, reps, stream)
+        self.caps.corner_ctas_per_sm, self.caps.select_ctas_per_sm = min(
+            out["corners"], key=out["corners"].get)
+        batch_phase(self.dev_tables[self.cur], self.caps, self.params, PHASE_PYRAMID, stream)
+        batch_phase(self.dev_tables[self.cur], self.caps, self.params, PHASE_CORNERS, stream)
+        for w, c in list(candidates or self.TUNE_CANDIDATES):
             self.caps.lk_warps, self.caps.lk_chunk = int(w), int(c)
-            batch_phase(self.dev_tables[par], self.caps, self.params, PHASE_LK, stream)
-            ms = []
-            for _ in range(reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                batch_phase(self.dev_tables[par], self.caps, self.params, PHASE_LK, stream)
-                e1.record()
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            times[(int(w), int(c))] = sorted(ms)[len(ms) // 2]
-        best = min(times, key=times.get)
-        self.caps.lk_warps, self.caps.lk_chunk = best
+            out["lk"][(int(w), int(c))] = self._time_phase(PHASE_LK, reps, stream)
+        self.caps.lk_warps, self.caps.lk_chunk = min(out["lk"], key=out["lk"].get)
         self.graphs = [None, None]
-        return times
+        return out
 
     def count(self, s: int) -> int:
         return int(self.offsets[s][self.nboxes[s]].item())

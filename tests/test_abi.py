@@ -204,11 +204,14 @@ def test_batch_pack_validation():
     assert lib.omt_batch_pack(arr, 5, ctypes.byref(prm), ctypes.byref(caps), tp, n) == omt.EINVAL
     # launch-shape fields out of range are rejected
     for field, value in [("lk_warps", 9), ("lk_warps", -1), ("lk_ctas_per_sm", 33), ("lk_chunk", 17),
-                         ("reserved", 1)]:
+                         ("pyr_ctas_per_sm", 33), ("pyr_ctas_per_sm", -1),
+                         ("corner_ctas_per_sm", 33), ("select_ctas_per_sm", -1), ("reserved", 1)]:
         bad_caps = omt.BatchCaps(4, 100, 1920, 1080, 64)
         setattr(bad_caps, field, value)
         assert omt.batch_table_bytes(bad_caps) == 0, field
     good = omt.BatchCaps(4, 100, 1920, 1080, 64, 8, 2, 16)
+    assert omt.batch_table_bytes(good) == n
+    good = omt.BatchCaps(4, 100, 1920, 1080, 64, 8, 2, 16, 32, 32, 32)
     assert omt.batch_table_bytes(good) == n
     assert lib.omt_batch_pack(arr, 1, ctypes.byref(prm), ctypes.byref(caps), tp, n - 1) == omt.ENOMEM
 
@@ -308,4 +311,4 @@ def test_working_level_arguments_rejected_before_launch():
 def test_library_version_matches_the_binding():
     # the binding's ctypes structures mirror one library version's layouts;
     # loading another version raises instead of misreading a structure
-    assert omt.lib().omt_version() == omt.ABI_VERSION == 300
+    assert omt.lib().omt_version() == omt.ABI_VERSION == 400

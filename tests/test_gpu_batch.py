@@ -235,28 +235,37 @@ def test_run_pipelined_equals_stepwise(omt):
 
 
 def test_lk_launch_shape_does_not_change_results(omt):
-    """Every launch shape the tuner may pick (warps per CTA, work-queue
-    chunk) gives the same points, statuses, iterations and boxes bit for bit,
-    and autotune keeps one of its candidates."""
+    """Every launch shape the tuner may pick (LK warps per CTA and
+    work-queue chunk; CTAs per SM of the pyramid, corner-list and select
+    kernels) gives the same pyramids, corners, points, statuses, iterations
+    and boxes bit for bit, and autotune keeps one of its candidates."""
     sps = _streams(4, first=100)
     params = omt.default_params(levels=4, win=21, min_dist=3.0, storage=1,
                                 max_corners=max(_cap(sp) for sp in sps))
     boxes_list = [sp.boxes for sp in sps]
     ref = None
-    for warps, chunk in [(4, 1), (2, 4), (8, 2), (1, 16)]:
+    for warps, chunk, pyr, lst, sel in [(4, 1, 0, 0, 0), (2, 4, 1, 1, 1), (8, 2, 2, 8, 4),
+                                        (1, 16, 4, 4, 2)]:
         B = _make_batch(omt, sps, params, boxes_list)
         B.caps.lk_warps, B.caps.lk_chunk = warps, chunk
+        B.caps.pyr_ctas_per_sm, B.caps.corner_ctas_per_sm, B.caps.select_ctas_per_sm = pyr, lst, sel
         B.step()
         torch.cuda.synchronize()
         got = _batch_results(B, sps)
         if ref is None:
             ref = got
         else:
-            for a, b in zip(ref, got):
+            for a, b, sp in zip(ref, got, sps):
                 _assert_same(a, b, pyramids=False)
+                w, h = sp.size
+                for x, y in zip(_pyr_planes(omt, a["pyr"], w, h, 4, 1),
+                                _pyr_planes(omt, b["pyr"], w, h, 4, 1)):
+                    np.testing.assert_array_equal(x, y)
     B = _make_batch(omt, sps, params, boxes_list)
     times = B.autotune(reps=2)
-    assert (B.caps.lk_warps, B.caps.lk_chunk) in times and min(times.values()) > 0
+    assert (B.caps.lk_warps, B.caps.lk_chunk) in times["lk"] and min(times["lk"].values()) > 0
+    assert B.caps.pyr_ctas_per_sm in times["pyramid"] and min(times["pyramid"].values()) > 0
+    assert (B.caps.corner_ctas_per_sm, B.caps.select_ctas_per_sm) in times["corners"]
     B.step()
     torch.cuda.synchronize()
     for a, b in zip(ref, _batch_results(B, sps)):
