@@ -197,6 +197,32 @@ __host__ __device__ __forceinline__ int find_segment(const int32_t *pre, int n, 
     return lo;
 }
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may be
+// scheduled while its predecessor in the stream drains; it calls
+// pdl_begin() before touching memory its predecessor writes (griddepcontrol
+// waits for that grid to complete and its writes to be visible), which also
+// lets its own successor be scheduled.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------- launchers
 // Each returns the cudaError_t of cudaGetLastError() after its launches.
 

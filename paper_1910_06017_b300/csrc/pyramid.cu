@@ -823,6 +823,9 @@ __global__ void __launch_bounds__(RING_NT) pyramid_batch_kernel(const uint8_t *t
     }
     for (int i = threadIdx.x; i <= ns; i += RING_NT) spre[i] = t.pyr_prefix(L)[i];
     __syncthreads();
+    // levels >= 1 are launched dependent on the level above: the table
+    // reads above overlap its tail; its planes are read only after this
+    pdl_begin();
     tile_ring<ST, FMT, PATH>(ring_smem_raw, spre[ns],
                              [&](int g, LevelArgs &a, int &ox, int &oy, const CUtensorMap *&m) {
                                  const int si = find_segment(spre, ns, g);
@@ -916,6 +919,12 @@ cudaError_t launch_batch_level_k(const uint8_t *table, int L, int max_tiles, int
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (grid > sms * ctas_per_sm) grid = sms * ctas_per_sm;
+    }
+    if (L > 0) {
+        // scheduled while level L-1 drains (pdl_begin waits for it)
+        e = launch_pdl(pyramid_batch_kernel<ST, FMT, PATH>, dim3(grid), dim3(RING_NT), smem, s,
+                       table, L);
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     pyramid_batch_kernel<ST, FMT, PATH><<<grid, RING_NT, smem, s>>>(table, L);
     return cudaGetLastError();

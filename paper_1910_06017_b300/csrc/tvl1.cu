@@ -79,30 +79,6 @@ __device__ __forceinline__ void sweep(F &&fn) {
     }
 }
 
-// Programmatic dependent launch: every kernel of the chain below is launched
-// so that it may be scheduled while its predecessor in the stream drains;
-// it waits for that grid to complete (and its writes to be visible) before
-// touching global memory, then lets its own successor be scheduled.
-__device__ __forceinline__ void pdl_begin() {
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-
-template <class... KArgs, class... Args>
-cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = g;
-    cfg.blockDim = b;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
-}
-
 // ------------------------------------------------------ structure-texture
 struct StArgs {
     const uint8_t *img;
@@ -655,10 +631,10 @@ cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t 
     const dim3 g = grid2(w, h), gs = grid_th(w, h, ST_TH), b(TBX, TBY);
     for (int it = 0; it < fp.st_iters;) {
         if (fp.block == 2 && it + 1 < fp.st_iters) {
-            e = launch_pdl(st_step2_kernel<ST_TH>, gs, b, s, a);
+            e = launch_pdl(st_step2_kernel<ST_TH>, gs, b, 0, s, a);
             it += 2;
         } else {
-            e = launch_pdl(st_step_kernel<ST_TH>, gs, b, s, a);
+            e = launch_pdl(st_step_kernel<ST_TH>, gs, b, 0, s, a);
             it += 1;
         }
         if (e != cudaSuccess) return e;
@@ -666,7 +642,7 @@ cudaError_t launch_structure_texture(const uint8_t *frame, int w, int h, size_t 
         a.p = a.p_out;
         a.p_out = const_cast<float *>(t);
     }
-    e = launch_pdl(st_texture_kernel, g, b, s, a, fp.st_alpha, fp.st_k, tex, (int64_t)tpitch);
+    e = launch_pdl(st_texture_kernel, g, b, 0, s, a, fp.st_alpha, fp.st_k, tex, (int64_t)tpitch);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -714,7 +690,7 @@ cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_
         float2 *partner = L == 0 ? other_flow : flow;
         float2 *ucur = odd_flips ? partner : dst, *unext = odd_flips ? dst : partner;
         const dim3 g = grid2(f.w, f.h), gp = grid_th(f.w, f.h, PD_TH), b(TBX, TBY);
-        e = launch_pdl(upsample_kernel, g, b, s, coarse, cw, ch, ucur, f.w, f.h);
+        e = launch_pdl(upsample_kernel, g, b, 0, s, coarse, cw, ch, ucur, f.w, f.h);
         if (e != cudaSuccess) return e;
         int cur = 0;  // the p / ub buffers holding the current fields
         e = cudaMemsetAsync(pbuf[cur], 0, sizeof(float4) * (size_t)f.w * f.h, s);
@@ -722,7 +698,7 @@ cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_
         for (int wp = 0; wp < fp.warps; ++wp) {
             f.u = ucur;
             f.ub = ubuf[cur];
-            e = launch_pdl(warp_kernel, g, b, s, f, I0, I1);
+            e = launch_pdl(warp_kernel, g, b, 0, s, f, I0, I1);
             if (e != cudaSuccess) return e;
             for (int it = 0; it < pairs + singles; ++it) {
                 f.p = pbuf[cur];
@@ -732,12 +708,12 @@ cudaError_t launch_tvl1(const omt_pyramid &P0, const omt_pyramid &P1, const omt_
                 f.u = ucur;
                 if (it < pairs) {
                     f.u_out = unext;
-                    e = launch_pdl(pd2_kernel<PD_TH>, gp, b, s, f, sigma, rden, tau, fp.lambda);
+                    e = launch_pdl(pd2_kernel<PD_TH>, gp, b, 0, s, f, sigma, rden, tau, fp.lambda);
                     float2 *t = ucur;
                     ucur = unext;
                     unext = t;
                 } else {
-                    e = launch_pdl(pd_kernel, g, b, s, f, sigma, rden, tau, fp.lambda);
+                    e = launch_pdl(pd_kernel, g, b, 0, s, f, sigma, rden, tau, fp.lambda);
                 }
                 if (e != cudaSuccess) return e;
                 cur = 1 - cur;
