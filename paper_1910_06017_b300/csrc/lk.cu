@@ -1007,14 +1007,26 @@ __global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *t
     unsigned *queue = const_cast<unsigned *>(&h.work[0]);
     const int ns = h.nstreams;
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // the streams' point counts, a lane per stream, and their prefix
         int acc = 0;
-        pre[0] = 0;
-        for (int s = 0; s < ns; ++s) {
-            const StreamEntry &e = t.stream(s);
-            acc += e.offsets[e.nboxes];
-            pre[s + 1] = acc;
+        for (int b = 0; b < ns; b += 32) {
+            const int s = b + lane;
+            int c = 0;
+            if (s < ns) {
+                const StreamEntry &e = t.stream(s);
+                c = e.offsets[e.nboxes];
+            }
+            int v = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(FULL_MASK, v, o);
+                if (lane >= o) v += u;
+            }
+            if (s < ns) pre[s + 1] = acc + v;
+            acc += __shfl_sync(FULL_MASK, v, 31);
         }
+        if (lane == 0) pre[0] = 0;
     }
     __syncthreads();
     const int total = pre[ns];
