@@ -684,9 +684,10 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
     const float det = det2(sxx, syy, sxy);
     const float dd = sxx - syy;
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
-    const float lmin = det / lmax;
+    // lambda_min = det / lambda_max >= tau_n and > 0, decided without the
+    // division (lambda_max > 0 whenever lambda_min > 0; non-finite sums fail)
+    if (!(det >= tau_n * lmax) || !(det > 0.f)) return OMT_PT_LOST_EIG;
     const float inv_det = 1.0f / det;
-    if (!(lmin >= tau_n) || !(lmin > 0.f)) return OMT_PT_LOST_EIG;
     // Prefetch the next template (next level, or the next point's top level)
     // into the other buffer while this level iterates.
     if (nx.has) {
