@@ -2,7 +2,8 @@
 //
 // One CTA per box.  The median of dx (and of dy) over the box's OK points is
 // an exact order statistic: for up to 2048 OK points the displacements are
-// gathered in shared memory and the element of rank k is found by counting;
+// gathered in shared memory and the elements of the two middle ranks of dx
+// and of dy are found by counting, all four in one pass;
 // larger boxes use an MSD radix select on order-preserving 32-bit keys of the
 // FP32 displacements (four 8-bit digits, shared-memory histograms).  Neither
 // needs a sort or scratch; an even count averages the two middle values.  The mean flag sums
@@ -127,18 +128,25 @@ constexpr int SCALE_POINTS = 64;
 // elements before it in the order (value, gather position).
 constexpr int SMALL = 2048;
 
-__device__ float rank_pick(const float *v, int m, int k, float *s_out) {
+// The elements of ranks k1 <= k2 of vx and of vy (m each) in one pass: each
+// thread ranks its elements of both arrays; out = (x1, x2, y1, y2).
+__device__ float4 rank_pick2(const float *vx, const float *vy, int m, int k1, int k2,
+                             float *s_out) {
     for (int i = threadIdx.x; i < m; i += BNT) {
-        const float x = v[i];
-        int r = 0;
+        const float x = vx[i], y = vy[i];
+        int rx = 0, ry = 0;
         for (int j = 0; j < m; ++j) {
-            const float y = v[j];
-            r += (y < x) || (y == x && j < i);
+            const float u = vx[j], w = vy[j];
+            rx += (u < x) || (u == x && j < i);
+            ry += (w < y) || (w == y && j < i);
         }
-        if (r == k) *s_out = x;
+        if (rx == k1) s_out[0] = x;
+        if (rx == k2) s_out[1] = x;
+        if (ry == k1) s_out[2] = y;
+        if (ry == k2) s_out[3] = y;
     }
     __syncthreads();
-    const float out = *s_out;
+    const float4 out = make_float4(s_out[0], s_out[1], s_out[2], s_out[3]);
     __syncthreads();
     return out;
 }
@@ -151,7 +159,7 @@ __device__ void box_update_one(const BoxArgs &a, int b) {
     __shared__ float red[2][BNT / 32];
     __shared__ int cnt[BNT / 32];
     __shared__ int s_sel, s_k, s_n;
-    __shared__ float s_val;
+    __shared__ float s_pick[4];
     __shared__ float vx[SMALL], vy[SMALL];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int lo = a.offsets[b], hi = a.offsets[b + 1];
@@ -202,16 +210,13 @@ __device__ void box_update_one(const BoxArgs &a, int b) {
             }
             __syncthreads();
             const int k1 = (total - 1) / 2, k2 = total / 2;
-            const float x1 = rank_pick(vx, total, k1, &s_val);
-            const float y1 = rank_pick(vy, total, k1, &s_val);
+            const float4 r = rank_pick2(vx, vy, total, k1, k2, s_pick);
             if (k2 != k1) {
-                const float x2 = rank_pick(vx, total, k2, &s_val);
-                const float y2 = rank_pick(vy, total, k2, &s_val);
-                mx = 0.5f * (x1 + x2);
-                my = 0.5f * (y1 + y2);
+                mx = 0.5f * (r.x + r.y);
+                my = 0.5f * (r.z + r.w);
             } else {
-                mx = x1;
-                my = y1;
+                mx = r.x;
+                my = r.z;
             }
         } else {
             const int k1 = (total - 1) / 2, k2 = total / 2;
