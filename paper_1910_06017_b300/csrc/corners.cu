@@ -91,6 +91,7 @@ struct RespArgs {
     int nboxes;
     uint64_t *cand;       // nboxes x CAND_CAP candidate keys
     uint32_t *cstate;     // per box: key count, R_max; then the overflow word
+    uint32_t *any_overflow;  // batched step: set when any stream's list overflows, or null
 };
 
 // A candidate's sort key: R above the complemented pixel index, so that
@@ -324,7 +325,10 @@ __device__ __forceinline__ void strip_to_lists(const RespArgs &a, int x0, int y0
                 if (rm) atomicMax(st + 1, rm);
                 if (total) {
                     base = atomicAdd(st, (uint32_t)total);
-                    if (base + (uint32_t)total > (uint32_t)CAND_CAP) a.cstate[2 * a.nboxes] = 1u;
+                    if (base + (uint32_t)total > (uint32_t)CAND_CAP) {
+                        a.cstate[2 * a.nboxes] = 1u;
+                        if (a.any_overflow) *a.any_overflow = 1u;
+                    }
                 }
             }
             base = __shfl_sync(FULL_MASK, base, 0);
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(RNT) overflow_kernel(RespArgs a, int total) {
     }
 }
 
-__device__ __forceinline__ RespArgs stream_resp_args(const StreamEntry &e) {
+__device__ __forceinline__ RespArgs stream_resp_args(const StreamEntry &e, uint32_t *any_overflow) {
     RespArgs a;
     a.img = e.P[0].img;
     a.pitch = e.P[0].img_pitch;
@@ -388,6 +392,7 @@ __device__ __forceinline__ RespArgs stream_resp_args(const StreamEntry &e) {
     a.nboxes = e.nboxes;
     a.cand = e.cand;
     a.cstate = e.cstate;
+    a.any_overflow = any_overflow;
     return a;
 }
 
@@ -399,6 +404,7 @@ __global__ void reset_lists_batch_kernel(const uint8_t *table) {
     if (si >= t.nstreams()) return;
     const StreamEntry &e = t.stream(si);
     for (int i = threadIdx.x; i <= 2 * e.nboxes; i += blockDim.x) e.cstate[i] = 0u;
+    if (si == 0 && threadIdx.x == 0) const_cast<uint32_t *>(t.hdr().work)[1] = 0u;
 }
 
 __global__ void __launch_bounds__(LNT) list_batch_kernel(const uint8_t *table) {
@@ -411,28 +417,28 @@ __global__ void __launch_bounds__(LNT) list_batch_kernel(const uint8_t *table) {
         const int si = find_segment(pre, t.nstreams(), gi);
         const StreamEntry &e = t.stream(si);
         if (e.nboxes == 0) continue;
-        const RespArgs a = stream_resp_args(e);
+        const RespArgs a = stream_resp_args(e, const_cast<uint32_t *>(t.hdr().work) + 1);
         int x0, y0;
         strip_origin(gi - pre[si], e.w, x0, y0);
         if (strip_needed(a, x0, y0, lane)) strip_to_lists(a, x0, y0, lane, strip[warp]);
     }
 }
 
-// Stream blockIdx.y's strips, gridDim.x CTAs per stream; a stream without
-// an overflowed list leaves at once.
+// Every stream's strips that touch an overflowed box; a step without an
+// overflow leaves after one load per CTA.
 __global__ void __launch_bounds__(RNT) overflow_batch_kernel(const uint8_t *table) {
     const BatchView t(table);
-    const int si = blockIdx.y;
-    if (si >= t.nstreams()) return;
-    const StreamEntry &e = t.stream(si);
-    if (e.nboxes == 0 || e.cstate[2 * e.nboxes] == 0u) return;
+    if (t.hdr().work[1] == 0u) return;
     const int32_t *pre = t.resp_prefix();
-    const int n = pre[si + 1] - pre[si];
+    const int total = pre[t.nstreams()];
     const int lane = threadIdx.x & 31;
-    const RespArgs a = stream_resp_args(e);
-    for (int ti = blockIdx.x * RWARPS + (threadIdx.x >> 5); ti < n; ti += gridDim.x * RWARPS) {
+    for (int gi = blockIdx.x * RWARPS + (threadIdx.x >> 5); gi < total; gi += gridDim.x * RWARPS) {
+        const int si = find_segment(pre, t.nstreams(), gi);
+        const StreamEntry &e = t.stream(si);
+        if (e.nboxes == 0 || e.cstate[2 * e.nboxes] == 0u) continue;
+        const RespArgs a = stream_resp_args(e, nullptr);
         int x0, y0;
-        strip_origin(ti, e.w, x0, y0);
+        strip_origin(gi - pre[si], e.w, x0, y0);
         if (strip_needed(a, x0, y0, lane, true)) strip_to_map(a, x0, y0, lane);
     }
 }
@@ -1034,6 +1040,9 @@ cudaError_t launch_corner_response(const omt_pyramid &pyr, uint32_t *out, const 
     a.out = out;
     a.boxes = boxes;
     a.nboxes = nboxes;
+    a.cand = nullptr;
+    a.cstate = nullptr;
+    a.any_overflow = nullptr;
     const int total = response_tiles(pyr.w, pyr.h);
     response_kernel<<<(total + RWARPS - 1) / RWARPS, RNT, 0, s>>>(a, total);
     return cudaGetLastError();
@@ -1067,6 +1076,7 @@ cudaError_t launch_select_corners(const omt_pyramid &pyr, const float4 *boxes, i
         r.nboxes = nboxes;
         r.cand = sc.cand;
         r.cstate = sc.cstate;
+        r.any_overflow = nullptr;
         const int tiles = response_tiles(pyr.w, pyr.h);
         list_kernel<<<(tiles + LWARPS - 1) / LWARPS, LNT, 0, s>>>(r, tiles);
         e = cudaGetLastError();
@@ -1123,7 +1133,9 @@ cudaError_t launch_corners_batch(const uint8_t *table, int max_streams, int max_
     list_batch_kernel<<<grid > 0 ? grid : 1, LNT, 0, s>>>(table);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    overflow_batch_kernel<<<dim3(8, max_streams > 0 ? max_streams : 1), RNT, 0, s>>>(table);
+    grid = (max_resp_tiles + RWARPS - 1) / RWARPS;
+    grid = grid < sms * 8 ? grid : sms * 8;
+    overflow_batch_kernel<<<grid > 0 ? grid : 1, RNT, 0, s>>>(table);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (max_boxes > 0) {

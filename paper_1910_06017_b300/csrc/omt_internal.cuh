@@ -131,8 +131,10 @@ struct BatchHeader {
     int32_t fb_on;  // fb_max >= 0
     int64_t md2c;
     int64_t bytes;  // size of the packed table
-    // work[0]: next point of the batched LK launch's work queue (reset to 0
-    // on the device before each LK launch; the only field a kernel writes)
+    // Words the kernels write: work[0], the next point of the batched LK
+    // launch's work queue (reset to 0 on the device before each LK launch);
+    // work[1], non-zero when some box's candidate list overflowed in this
+    // step's corner phase (reset by the phase's first kernel).
     uint32_t work[4];
 };
 
