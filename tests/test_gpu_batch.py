@@ -355,3 +355,49 @@ def test_lk_staging_waits_never_time_out(omt):
     torch.cuda.synchronize()
     assert omt.lk_wait_timeouts() == 0
     assert omt.lk_wait_timeouts() == 0  # the read restarts the count
+
+
+def test_candidate_list_overflow_in_the_batch(omt, oracle):
+    """A box with more than 1,024 candidate corners (noise of full amplitude,
+    quality 0: every positive local maximum is a candidate) overflows its
+    candidate list: the batched step then selects it through the response
+    map of the strips that touch it, and still equals the plain calls bit
+    for bit.  The next step, without that box, equals the plain calls too
+    (the step-wide overflow word is reset)."""
+    from paper_1910_06017_b300.synth import StreamPair
+    rng = np.random.default_rng(77)
+    base = synth.stream_pair(3, workload=13, n_range=(300, 3000))
+    f0 = base.frame0.copy()
+    f0[40:260, 60:360] = rng.integers(0, 256, size=(220, 300)).astype(np.uint8)
+    box = [60, 40, 360, 260]
+    R = oracle.corner_response(f0)
+    Rc = R[1:-1, 1:-1]
+    nb = np.stack([R[1 + dy:R.shape[0] - 1 + dy, 1 + dx:R.shape[1] - 1 + dx]
+                   for dy in (-1, 0, 1) for dx in (-1, 0, 1)]).max(axis=0)
+    lm = np.zeros_like(R, bool)
+    lm[1:-1, 1:-1] = (Rc >= nb) & (Rc > 0)
+    assert lm[40:260, 60:360].sum() > 1024   # more candidates than a list holds
+    noisy = StreamPair(f0, base.frame1, np.concatenate([base.boxes[:20], [box]]).astype(np.float32),
+                       base.n_target, base.size)
+    sps = _streams(2, first=60) + [noisy]
+    params = omt.default_params(levels=4, win=21, min_dist=0.0, storage=1, quality=(0, 1),
+                                max_corners=max(_cap(sp) for sp in sps))
+    boxes_list = [sp.boxes for sp in sps]
+    plain = _run_plain(omt, sps, params, boxes_list)
+    B = _make_batch(omt, sps, params, boxes_list)
+    B.step()
+    torch.cuda.synchronize()
+    for a, b in zip(plain, _batch_results(B, sps)):
+        _assert_same(a, b, pyramids=False)
+    # second step (frame 1 -> frame 0 in the other slot): the noisy box is gone
+    boxes2 = [sp.boxes for sp in sps[:2]] + [noisy.boxes[:20]]
+    for s, (sp, b) in enumerate(zip(sps, boxes2)):
+        B.slot(s).copy_(torch.from_numpy(sp.frame0))
+        B.set_boxes(s, torch.from_numpy(np.ascontiguousarray(b, np.float32)))
+    B.pack()
+    B.step()
+    torch.cuda.synchronize()
+    back = [StreamPair(sp.frame1, sp.frame0, b, sp.n_target, sp.size) for sp, b in zip(sps, boxes2)]
+    plain2 = _run_plain(omt, back, params, boxes2)
+    for a, b in zip(plain2, _batch_results(B, back)):
+        _assert_same(a, b, pyramids=False)
