@@ -603,25 +603,42 @@ __device__ void greedy(const SelectArgs &a, int box, const uint64_t *keys, int N
                 }
             }
         }
-        unsigned m = __ballot_sync(FULL_MASK, ok);
-        while (m && nacc < a.maxc) {
-            const int src = __ffs(m) - 1;
-            const int xs = __shfl_sync(FULL_MASK, x, src), ys = __shfl_sync(FULL_MASK, y, src);
-            if (lane == 0) {
-                acc[nacc] = make_int2(xs, ys);
-                if (g.bits)
-                    g.bits[(ys - g.ylo) * g.wpr + ((xs - g.xlo) >> 5)] |= 1u << ((xs - g.xlo) & 31);
-                else if (g.cells)
-                    g.cells[((ys - g.ylo) / a.cell) * g.gx + (xs - g.xlo) / a.cell] = (int16_t)nacc;
-                a.pad_pts[(int64_t)box * a.maxc + nacc] = make_float2((float)xs, (float)ys);
+        // The group in order: a candidate is kept iff it passed the test
+        // against the points kept before the group (ok) and no earlier kept
+        // candidate of the group lies within the minimum distance.  Each
+        // lane first forms the mask of the group's earlier candidates within
+        // that distance of its own (all lanes at once); the scan then keeps
+        // the first undecided candidate and drops the later ones its lane
+        // conflicts with, until none is left or max_corners is reached.
+        unsigned undecided = __ballot_sync(FULL_MASK, ok);
+        unsigned earlier = 0;  // bit q: candidate q < lane lies within the minimum distance
+        if (a.md2c > 0 && (undecided & (undecided - 1u))) {
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {
+                const int xq = __shfl_sync(FULL_MASK, x, q), yq = __shfl_sync(FULL_MASK, y, q);
+                const int64_t dx = x - xq, dy = y - yq;
+                if (q < lane && dx * dx + dy * dy < a.md2c) earlier |= 1u << q;
             }
-            ++nacc;
-            if (ok && lane > src) {
-                const int64_t dx = x - xs, dy = y - ys;
-                if (dx * dx + dy * dy < a.md2c) ok = false;
-            }
-            m = __ballot_sync(FULL_MASK, ok && lane > src);
         }
+        unsigned kept = 0;
+        int room = a.maxc - nacc;
+        while (undecided && room > 0) {
+            const int src = __ffs(undecided) - 1;
+            kept |= 1u << src;
+            --room;
+            undecided &= ~(1u << src) & ~__ballot_sync(FULL_MASK, (earlier >> src) & 1u);
+        }
+        // the kept candidates, written by their own lanes in the group's order
+        if ((kept >> lane) & 1u) {
+            const int slot = nacc + __popc(kept & ((1u << lane) - 1u));
+            acc[slot] = make_int2(x, y);
+            if (g.bits)
+                atomicOr(&g.bits[(y - g.ylo) * g.wpr + ((x - g.xlo) >> 5)], 1u << ((x - g.xlo) & 31));
+            else if (g.cells)
+                g.cells[((y - g.ylo) / a.cell) * g.gx + (x - g.xlo) / a.cell] = (int16_t)slot;
+            a.pad_pts[(int64_t)box * a.maxc + slot] = make_float2((float)x, (float)y);
+        }
+        nacc += __popc(kept);
         __syncwarp();
     }
     if (lane == 0) *s_nacc = nacc;
