@@ -1,9 +1,10 @@
 // lk.cu -- K3: pyramidal iterative Lucas-Kanade (Bouguet), the sparse
 // stand-in for the dense motion field of Section V-A (feature calculation).
 //
-// One warp per point, lane c owning window column c.  Per level the warp
-// walks the (win+1) texel rows of its window: each lane loads the texel of
-// its column, takes the right neighbour from lane c+1 with a shuffle, and
+// One warp per point.  The warp covers the window in four row bands of
+// eight lanes, each lane a few adjacent texel columns of its band (Lanes):
+// per level it walks its band's texel rows, loads its columns' texels, takes
+// the column right of its last from the next lane with a shuffle, and
 // interpolates horizontally, then vertically reusing the previous row.  The
 // frame-t window keeps only (Ix, Iy) per tap in registers; b = sum (I - J)
 // grad I is formed as c - sum J grad I with the level constant c = sum I
@@ -15,8 +16,9 @@
 // order is fixed: a point's result does not depend on the launch shape or
 // on its neighbours in the batch.
 //
-// Solve: det = Gxx Gyy - Gxy^2 by Kahan's fused form, lambda_min =
-// det / lambda_max (no cancellation), eta = G^-1 b by the 2x2 adjugate.
+// Solve: det = Gxx Gyy - Gxy^2 by Kahan's fused form; lambda_min =
+// det / lambda_max >= tau is tested as det >= tau lambda_max (no
+// cancellation, no division); eta = G^-1 b by the 2x2 adjugate.
 #include <cudaTypedefs.h>
 
 #include <mutex>

@@ -1,8 +1,10 @@
 // pyramid.cu -- K1: Gaussian pyramid and Scharr gradients (Section V-A,
 // preprocessing).
 //
-// One launch per level L; each CTA streams 128x32 tiles of level L (of every
-// stream, in the batched form) through a ring of staged tiles in shared
+// One launch per level L (in the batched form, levels >= 1 launched as
+// programmatic dependents of the level above); each CTA streams 128x32
+// tiles of level L (of every stream, in the batched form) through a ring of
+// staged tiles in shared
 // memory (tile_ring): a producer warp copies a tile and its halo (2 rows,
 // and on the left the texels up to a 16-byte boundary) by one 2D tensor
 // copy per tile, four consumer warps compute it.  Each consumer thread owns
