@@ -404,7 +404,11 @@ __global__ void reset_lists_batch_kernel(const uint8_t *table) {
     if (si >= t.nstreams()) return;
     const StreamEntry &e = t.stream(si);
     for (int i = threadIdx.x; i <= 2 * e.nboxes; i += blockDim.x) e.cstate[i] = 0u;
-    if (si == 0 && threadIdx.x == 0) const_cast<uint32_t *>(t.hdr().work)[1] = 0u;
+    if (si == 0 && threadIdx.x == 0) {
+        uint32_t *work = const_cast<uint32_t *>(t.hdr().work);
+        work[1] = 0u;
+        work[2] = 0u;
+    }
 }
 
 __global__ void __launch_bounds__(LNT) list_batch_kernel(const uint8_t *table) {
@@ -413,7 +417,14 @@ __global__ void __launch_bounds__(LNT) list_batch_kernel(const uint8_t *table) {
     const int32_t *pre = t.resp_prefix();
     const int total = pre[t.nstreams()];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int gi = blockIdx.x * LWARPS + warp; gi < total; gi += gridDim.x * LWARPS) {
+    uint32_t *queue = const_cast<uint32_t *>(t.hdr().work) + 2;
+    for (;;) {
+        // the next strip, one atomic per warp and strip (strips differ in
+        // cost, so a static stride leaves a tail of warps with one strip more)
+        uint32_t take = 0;
+        if (lane == 0) take = atomicAdd(queue, 1u);
+        const int gi = (int)__shfl_sync(FULL_MASK, take, 0);
+        if (gi >= total) break;
         const int si = find_segment(pre, t.nstreams(), gi);
         const StreamEntry &e = t.stream(si);
         if (e.nboxes == 0) continue;

@@ -134,7 +134,8 @@ struct BatchHeader {
     // Words the kernels write: work[0], the next point of the batched LK
     // launch's work queue (reset to 0 on the device before each LK launch);
     // work[1], non-zero when some box's candidate list overflowed in this
-    // step's corner phase (reset by the phase's first kernel).
+    // step's corner phase; work[2], the next strip of the corner-list
+    // kernel's queue (both reset by the corner phase's first kernel).
     uint32_t work[4];
 };
 
