@@ -33,6 +33,16 @@ constexpr int LK_NT = 128;               // CTA size of the plain launch (and th
 constexpr int LK_WARPS = LK_NT / 32;
 constexpr int LK_MAX_NT = 256;           // largest CTA a launch may use
 
+// Registers a thread of the batched kernel may use: 128 (two 256-thread
+// CTAs per SM) up to 23x23, where nothing spills; the larger windows hold
+// more taps per lane and spilled at 128, so they get 168 (12 resident warps
+// per SM instead of 16).  On four 3840x2160 streams at 31x31 (106 k points,
+// 5 levels) that took the batched LK from 3.52 to 2.97 ms (F16 storage) and
+// from 5.44 to 4.50 ms (F32); at 21x21 the time is the same at 128, 168 or
+// 255.
+template <int WIN>
+constexpr int lk_batch_regs() { return WIN >= 25 ? 168 : 128; }
+
 struct LKArgs {
     CUtensorMap tm[OMT_MAX_LEVELS * LK_MAPS];  // window maps (encode_lk_maps)
     uint32_t tm_ok;                              // valid maps, bit 3L + m
@@ -999,7 +1009,8 @@ __device__ __noinline__ void give_up_batch(const uint8_t *table, const int32_t *
 // before the last point of the current one, whose finest level then
 // prefetches the next point's top-level template.
 template <int ST, int WIN, bool backward>
-__global__ void __launch_bounds__(LK_MAX_NT, 2) lk_batch_kernel(const uint8_t *table, int chunk) {
+__global__ void __launch_bounds__(LK_MAX_NT) __maxnreg__(lk_batch_regs<WIN>())
+    lk_batch_kernel(const uint8_t *table, int chunk) {
     __shared__ int32_t pre[OMT_BATCH_MAX_STREAMS + 1];
     unsigned *W = warp_words<ST, WIN>();
     const BatchView t(table);
