@@ -43,6 +43,22 @@ constexpr int LK_MAX_NT = 256;           // largest CTA a launch may use
 template <int WIN>
 constexpr int lk_batch_regs() { return WIN >= 25 ? 168 : 128; }
 
+// Lanes that track one point together: G = 32 (the whole warp) or 16 (each
+// half-warp its own point, the two halves in step).  Collectives run on the
+// group's mask, copies are issued by the group's lane 0, and every group
+// has its own staging buffers and mbarriers.
+template <int WIN>
+constexpr int lk_group() { return 32; }
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G == 32) return FULL_MASK;
+    else return 0xFFFFu << (threadIdx.x & 16);
+}
+
+template <int G>
+__device__ __forceinline__ int group_lane() { return (int)(threadIdx.x & (G - 1)); }
+
 struct LKArgs {
     CUtensorMap tm[OMT_MAX_LEVELS * LK_MAPS];  // window maps (encode_lk_maps)
     uint32_t tm_ok;                              // valid maps, bit 3L + m
@@ -126,8 +142,6 @@ __device__ unsigned lk_wait_timeouts;
 __device__ long long lk_fail_point = -1;
 constexpr unsigned FAIL_EXTRA_BYTES = 16;
 
-__device__ __forceinline__ int lane_of() { return threadIdx.x & 31; }
-
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -144,6 +158,7 @@ struct Fills {
 };
 constexpr unsigned FILL_FAILED = 8u;
 
+template <int G>
 __device__ __forceinline__ void fills_init(Fills &f, unsigned *W_bar, int lane) {
     f.bar = (uint64_t *)W_bar;
     f.pend = 0;
@@ -154,11 +169,12 @@ __device__ __forceinline__ void fills_init(Fills &f, unsigned *W_bar, int lane) 
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(f.bar + b)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    __syncwarp();
+    __syncwarp(group_mask<G>());
 }
 
 // Open a fill of buffer b that will land `bytes` bytes: lane 0 arrives and
 // sets the expected count; the copies follow after the warp syncs.
+template <int G>
 __device__ __forceinline__ void fill_begin(Fills &f, int b, unsigned bytes, int lane) {
     // predicated on lane 0 inside the asm: no divergent branch
     asm volatile(
@@ -167,7 +183,7 @@ __device__ __forceinline__ void fill_begin(Fills &f, int b, unsigned bytes, int 
         "r"(bytes), "r"(lane)
         : "memory");
     f.pend |= 1u << b;
-    __syncwarp();
+    __syncwarp(group_mask<G>());
 }
 
 // One row (bytes a multiple of 16, both ends 16-byte aligned).
@@ -210,8 +226,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Wait (bounded) until buffer b's fill in flight, if any, has landed.
-// Returns false, for the whole warp, when the wait ran out its limit: the
-// warp is then failed (Fills) and the buffer is never waited on again.
+// Returns false, for the whole group, when the wait ran out its limit: the
+// group is then failed (Fills) and the buffer is never waited on again.
+template <int G>
 __device__ __forceinline__ bool fill_wait(Fills &f, int b) {
     if (!((f.pend >> b) & 1u)) return true;
     const unsigned a = smem_u32(f.bar + b), par = (f.phase >> b) & 1u;
@@ -226,8 +243,8 @@ __device__ __forceinline__ bool fill_wait(Fills &f, int b) {
         }
     }
     f.pend &= ~(1u << b);
-    if (__any_sync(FULL_MASK, late)) {
-        if ((threadIdx.x & 31) == 0) atomicAdd(&lk_wait_timeouts, 1u);
+    if (__any_sync(group_mask<G>(), late)) {
+        if (group_lane<G>() == 0) atomicAdd(&lk_wait_timeouts, 1u);
         f.pend |= FILL_FAILED;
         return false;
     }
@@ -235,10 +252,11 @@ __device__ __forceinline__ bool fill_wait(Fills &f, int b) {
     return true;
 }
 
+template <int G>
 __device__ __forceinline__ void fill_drain(Fills &f) {
-    fill_wait(f, 0);
-    fill_wait(f, 1);
-    fill_wait(f, BUF_SEARCH);
+    fill_wait<G>(f, 0);
+    fill_wait<G>(f, 1);
+    fill_wait<G>(f, BUF_SEARCH);
 }
 
 // The bytes of a row to copy for texel columns [x0, x0 + ncols) clamped to
@@ -273,12 +291,12 @@ __device__ __forceinline__ FillMode fill_mode(const CUtensorMap *tm, int y0, int
 // After a tensor copy of rows [y0, y0 + rows) that overlaps a level of h
 // rows, the rows above the level (zero-filled) take the level's first row
 // and those below take its last, as a copy of clamped rows would hold.
-template <int RW>
+template <int RW, int G>
 __device__ __forceinline__ void fix_rows(unsigned *blk, int y0, int rows, int h, int lane) {
     const int top = y0 < 0 ? -y0 : 0;                   // rows above the level, < rows
     const int below = h - y0 < rows ? h - y0 : rows;    // first row below the level, > top
     const int n = (top + rows - below) * RW;
-    for (int k = lane; k < n; k += 32) {
+    for (int k = lane; k < n; k += G) {
         const int j = k / RW, c = k - j * RW;
         const int r = j < top ? j : below + (j - top);
         const int src = j < top ? top : below - 1;
@@ -337,6 +355,7 @@ __device__ __forceinline__ void issue_template(const LevelView *P, int w, int h,
                                                int buf, int lane, unsigned *W, Fills &f,
                                                int &tcol_i, int &tcol_g) {
     using D = Dims<ST, WIN>;
+    constexpr int G = lk_group<WIN>();
     unsigned *TI = W + buf * D::TRAW, *TGr = TI + D::TG;
     const int esz = u8 ? 1 : D::ESZ;
     const Span si = row_span(w, esz, ipx - D::R, D::T);
@@ -345,17 +364,17 @@ __device__ __forceinline__ void issue_template(const LevelView *P, int w, int h,
     tcol_i = si.b0 >> esz_shift(esz);
     tcol_g = sg.b0 >> esz_shift(D::GSZ);
     if (fill_mode(tm, y0, D::T, h) != VIA_ROWS) {
-        fill_begin(f, buf, D::T * 4 * (D::RWI + D::RWG), lane);
+        fill_begin<G>(f, buf, D::T * 4 * (D::RWI + D::RWG), lane);
         tensor_box(TI, tm + LK_MAP_TI, tcol_i, y0, f.bar + buf, lane);
         tensor_box(TGr, tm + LK_MAP_TG, tcol_g, y0, f.bar + buf, lane);
     } else {
-        fill_begin(f, buf, D::T * (si.bytes + sg.bytes), lane);
-        if (lane < D::T) {
-            const uint8_t *img = P->img, *grad = P->grad;
-            const int64_t ip = P->img_pitch, gp = P->grad_pitch;
-            const int64_t y = clampi(y0 + lane, 0, h - 1);
-            bulk_row(TI + lane * D::RWI, img + y * ip + si.b0, si.bytes, f.bar + buf);
-            bulk_row(TGr + lane * D::RWG, grad + y * gp + sg.b0, sg.bytes, f.bar + buf);
+        fill_begin<G>(f, buf, D::T * (si.bytes + sg.bytes), lane);
+        const uint8_t *img = P->img, *grad = P->grad;
+        const int64_t ip = P->img_pitch, gp = P->grad_pitch;
+        for (int r = lane; r < D::T; r += G) {
+            const int64_t y = clampi(y0 + r, 0, h - 1);
+            bulk_row(TI + r * D::RWI, img + y * ip + si.b0, si.bytes, f.bar + buf);
+            bulk_row(TGr + r * D::RWG, grad + y * gp + sg.b0, sg.bytes, f.bar + buf);
         }
     }
 }
@@ -368,6 +387,7 @@ __device__ __forceinline__ void copy_search(const LevelView *J, int w, int h,
                                             int lane, unsigned *W, Fills &f, LevelCopy &lc,
                                             unsigned extra = 0) {
     using D = Dims<ST, WIN>;
+    constexpr int G = lk_group<WIN>();
     const int esz = u8 ? 1 : D::ESZ;
     lc.sx0 = jx - D::R - MARGIN;
     lc.sy0 = jy - D::R - MARGIN;
@@ -375,13 +395,13 @@ __device__ __forceinline__ void copy_search(const LevelView *J, int w, int h,
     lc.scol = ss.b0 >> esz_shift(esz);
     unsigned *S = W + D::UNION;
     if (fill_mode(tm, lc.sy0, D::SH, h) != VIA_ROWS) {
-        fill_begin(f, BUF_SEARCH, D::SH * 4 * D::RWJ + extra, lane);
+        fill_begin<G>(f, BUF_SEARCH, D::SH * 4 * D::RWJ + extra, lane);
         tensor_box(S, tm, lc.scol, lc.sy0, f.bar + BUF_SEARCH, lane);
     } else {
-        fill_begin(f, BUF_SEARCH, D::SH * ss.bytes + extra, lane);
+        fill_begin<G>(f, BUF_SEARCH, D::SH * ss.bytes + extra, lane);
         const uint8_t *img = J->img;
         const int64_t ip = J->img_pitch;
-        for (int r = lane; r < D::SH; r += 32) {
+        for (int r = lane; r < D::SH; r += G) {
             const int64_t y = clampi(lc.sy0 + r, 0, h - 1);
             bulk_row(S + r * D::RWJ, img + y * ip + ss.b0, ss.bytes, f.bar + BUF_SEARCH);
         }
@@ -393,25 +413,37 @@ template <int ST, int WIN>
 __device__ __forceinline__ void search_edges(int h, const CUtensorMap *tm, unsigned *W,
                                              const LevelCopy &lc, int lane) {
     using D = Dims<ST, WIN>;
+    constexpr int G = lk_group<WIN>();
     if (fill_mode(tm, lc.sy0, D::SH, h) == VIA_TMA_EDGE) {
-        __syncwarp();
-        fix_rows<D::RWJ>(W + D::UNION, lc.sy0, D::SH, h, lane);
+        __syncwarp(group_mask<G>());
+        fix_rows<D::RWJ, G>(W + D::UNION, lc.sy0, D::SH, h, lane);
     }
 }
 
-// Two warp sums at once: lanes 0-15 end with the total of a, lanes 16-31
-// with the total of b (one exchange, then butterflies within each half);
-// returns both totals in every lane.  Fixed order: every lane gets the same
-// bits, and equal inputs give equal outputs whatever they are paired with.
-__device__ __forceinline__ void warp_sum2(float &a, float &b, int lane) {
-    const bool hi = (lane & 16) != 0;
+// Two group sums at once: the lower half of the group ends with the total
+// of a, the upper half with the total of b (one exchange, then butterflies
+// within each half); returns both totals in every lane of the group.  Fixed
+// order: every lane gets the same bits, and equal inputs give equal outputs
+// whatever they are paired with.
+template <int G>
+__device__ __forceinline__ void group_sum2(float &a, float &b, int lane) {
+    const unsigned m = group_mask<G>();
+    const bool hi = (lane & (G / 2)) != 0;
     float keep = hi ? b : a;
     const float give = hi ? a : b;
-    keep += __shfl_xor_sync(FULL_MASK, give, 16);
+    keep += __shfl_xor_sync(m, give, G / 2, G);
 #pragma unroll
-    for (int m = 8; m > 0; m >>= 1) keep += __shfl_xor_sync(FULL_MASK, keep, m);
-    a = __shfl_sync(FULL_MASK, keep, 0);
-    b = __shfl_sync(FULL_MASK, keep, 16);
+    for (int o = G / 4; o > 0; o >>= 1) keep += __shfl_xor_sync(m, keep, o, G);
+    a = __shfl_sync(m, keep, 0, G);
+    b = __shfl_sync(m, keep, G / 2, G);
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+    const unsigned m = group_mask<G>();
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o, G);
+    return v;
 }
 
 // Packed FP32 arithmetic: two lanes of one instruction, each rounded as
@@ -421,41 +453,44 @@ __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);  // a - b, one rounding
 }
 
-// Four warp sums at once: halving exchanges leave each quarter of the warp
-// (lane bits 4 and 3) with one of the four partial sums, butterflies within
-// the quarter finish it, and every lane reads the four totals back.  Fixed
-// order, as warp_sum2.
-__device__ __forceinline__ void warp_sum4(float &a, float &b, float &c, float &d, int lane) {
-    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0;
-    float k0 = h4 ? c : a, k1 = h4 ? d : b;
-    const float g0 = h4 ? a : c, g1 = h4 ? b : d;
-    k0 += __shfl_xor_sync(FULL_MASK, g0, 16);
-    k1 += __shfl_xor_sync(FULL_MASK, g1, 16);
-    float keep = h3 ? k1 : k0;
-    const float give = h3 ? k0 : k1;
-    keep += __shfl_xor_sync(FULL_MASK, give, 8);
+// Four group sums at once: halving exchanges leave each quarter of the
+// group with one of the four partial sums, butterflies within the quarter
+// finish it, and every lane reads the four totals back.  Fixed order, as
+// group_sum2.
+template <int G>
+__device__ __forceinline__ void group_sum4(float &a, float &b, float &c, float &d, int lane) {
+    const unsigned m = group_mask<G>();
+    const bool hh = (lane & (G / 2)) != 0, hq = (lane & (G / 4)) != 0;
+    float k0 = hh ? c : a, k1 = hh ? d : b;
+    const float g0 = hh ? a : c, g1 = hh ? b : d;
+    k0 += __shfl_xor_sync(m, g0, G / 2, G);
+    k1 += __shfl_xor_sync(m, g1, G / 2, G);
+    float keep = hq ? k1 : k0;
+    const float give = hq ? k0 : k1;
+    keep += __shfl_xor_sync(m, give, G / 4, G);
 #pragma unroll
-    for (int m = 4; m > 0; m >>= 1) keep += __shfl_xor_sync(FULL_MASK, keep, m);
-    a = __shfl_sync(FULL_MASK, keep, 0);
-    b = __shfl_sync(FULL_MASK, keep, 8);
-    c = __shfl_sync(FULL_MASK, keep, 16);
-    d = __shfl_sync(FULL_MASK, keep, 24);
+    for (int o = G / 8; o > 0; o >>= 1) keep += __shfl_xor_sync(m, keep, o, G);
+    a = __shfl_sync(m, keep, 0, G);
+    b = __shfl_sync(m, keep, G / 4, G);
+    c = __shfl_sync(m, keep, G / 2, G);
+    d = __shfl_sync(m, keep, 3 * G / 4, G);
 }
 
-// How a warp's lanes cover a window of WIN x WIN taps (texel footprint
-// (WIN + 1)^2): four row bands of eight lanes.  Lane k of band g holds texel
-// columns CPL k .. CPL k + CPL - 1 (taps where the column is below WIN; the
-// column right of its last one comes from lane k + 1 by a shuffle) and walks
-// the band's tap rows r0 .. r0 + nr - 1: the WIN rows split into bands of
-// Q + 1 rows (the first REM bands) and Q rows.  A band walks RB rows; a
-// band of Q rows reads its last texel row again at step Q, where its taps
-// are zero.  Every lane then holds RB x CPL taps, and all 32 lanes take part
-// in every row step (a lane per texel column left 10 of 32 lanes idle at
-// WIN = 21).
+// How a group's lanes cover a window of WIN x WIN taps (texel footprint
+// (WIN + 1)^2): NB = G / 8 row bands of eight lanes (four for a warp, two
+// for a half-warp).  Lane k of band g holds texel columns CPL k .. CPL k +
+// CPL - 1 (taps where the column is below WIN; the column right of its last
+// one comes from lane k + 1 by a shuffle) and walks the band's tap rows r0
+// .. r0 + nr - 1: the WIN rows split into bands of Q + 1 rows (the first
+// REM bands) and Q rows.  A band walks RB rows; a band of Q rows reads its
+// last texel row again at step Q, where its taps are zero.  Every lane then
+// holds RB x CPL taps, and all lanes take part in every row step (a lane
+// per texel column left 10 of 32 lanes idle at WIN = 21).
 template <int WIN>
 struct Lanes {
+    static constexpr int NB = lk_group<WIN>() / 8;       // row bands
     static constexpr int CPL = (WIN + 1 + 7) / 8;       // texel columns per lane
-    static constexpr int Q = WIN / 4, REM = WIN % 4;    // band rows: Q + (g < REM)
+    static constexpr int Q = WIN / NB, REM = WIN % NB;  // band rows: Q + (g < REM)
     static constexpr int RB = Q + (REM > 0 ? 1 : 0);    // row steps of a band
     // a lane holds taps and columns right of the window at once
     static constexpr bool PARTIAL = WIN % CPL != 0;
@@ -499,6 +534,7 @@ __device__ __forceinline__ void template_window(int w, int tx0, float ax, float 
     using M = Lanes<WIN>;
     constexpr int C = M::CPL;
     const int g = lane >> 3, k = lane & 7;
+    const unsigned gm = group_mask<lk_group<WIN>()>();
     const int r0 = band_r0(g, M::Q, M::REM);
     const bool long_band = g < M::REM;
     const unsigned *rawG = W + D::TG;
@@ -512,8 +548,8 @@ __device__ __forceinline__ void template_window(int w, int tx0, float ax, float 
         float2 t[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) t[j] = raw_grad<ST>(row, cg[j]);
-        const float2 tn = f2(__shfl_down_sync(FULL_MASK, t[0].x, 1),
-                             __shfl_down_sync(FULL_MASK, t[0].y, 1));
+        const float2 tn = f2(__shfl_down_sync(gm, t[0].x, 1, 8),
+                             __shfl_down_sync(gm, t[0].y, 1, 8));
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const float2 t1 = j + 1 < C ? t[j + 1] : tn;
@@ -561,6 +597,7 @@ __device__ __forceinline__ void corr4(const unsigned *raw, int rw, int oy,
     using M = Lanes<WIN>;
     constexpr int C = M::CPL;
     const int g = lane >> 3;
+    const unsigned gm = group_mask<lk_group<WIN>()>();
     const int r0 = band_r0(g, M::Q, M::REM);
     const unsigned *base = raw + (oy + r0) * rw;
 #pragma unroll
@@ -568,7 +605,7 @@ __device__ __forceinline__ void corr4(const unsigned *raw, int rw, int oy,
     float p[C], pn;
 #pragma unroll
     for (int j = 0; j < C; ++j) p[j] = raw_texel<ST>(base, col[j], U8);
-    pn = __shfl_down_sync(FULL_MASK, p[0], 1);
+    pn = __shfl_down_sync(gm, p[0], 1, 8);
 #pragma unroll
     for (int i = 0; i < M::RB; ++i) {
         const unsigned *row = i < M::Q ? base + (i + 1) * rw
@@ -576,7 +613,7 @@ __device__ __forceinline__ void corr4(const unsigned *raw, int rw, int oy,
         float v[C];
 #pragma unroll
         for (int j = 0; j < C; ++j) v[j] = raw_texel<ST>(row, col[j], U8);
-        const float vn = __shfl_down_sync(FULL_MASK, v[0], 1);
+        const float vn = __shfl_down_sync(gm, v[0], 1, 8);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
             const float pr = j + 1 < C ? p[j + 1] : pn;
@@ -633,6 +670,8 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
                                            float &nuy, int &k, bool &conv, bool force_fail) {
     using D = Dims<ST, WIN>;
     constexpr int R = D::R;
+    constexpr int G = lk_group<WIN>();
+    const unsigned gm = group_mask<G>();
     const float fpx = floorf(px), fpy = floorf(py);
     const int ipx = (int)fpx, ipy = (int)fpy;
     const float ax = px - fpx, ay = py - fpy;
@@ -653,7 +692,7 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
         lc.tcol_g = pf.tcol_g;
     } else {
         buf = 0;
-        __syncwarp();
+        __syncwarp(gm);
         issue_template<ST, WIN>(P, w, h, tm, u8, ipx, ipy, buf, lane, W, f, lc.tcol_i, lc.tcol_g);
     }
     pf.valid = false;
@@ -668,13 +707,13 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
                              force_fail ? FAIL_EXTRA_BYTES : 0u);
     }
     // the template has landed; the search may still run
-    if (!fill_wait(f, buf)) return OMT_PT_LOST_TIMEOUT;
+    if (!fill_wait<G>(f, buf)) return OMT_PT_LOST_TIMEOUT;
     if (fill_mode(tm, ipy - R, D::T, h) == VIA_TMA_EDGE) {
-        __syncwarp();
-        fix_rows<D::RWI>(W + buf * D::TRAW, ipy - R, D::T, h, lane);
-        fix_rows<D::RWG>(W + buf * D::TRAW + D::TG, ipy - R, D::T, h, lane);
+        __syncwarp(gm);
+        fix_rows<D::RWI, G>(W + buf * D::TRAW, ipy - R, D::T, h, lane);
+        fix_rows<D::RWG, G>(W + buf * D::TRAW + D::TG, ipy - R, D::T, h, lane);
     }
-    __syncwarp();
+    __syncwarp(gm);
 
     using M = Lanes<WIN>;
     const bool owns = lane_owns<WIN>(lane);
@@ -691,8 +730,8 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
         combine4(S, ax, ay, cx, cy);
         if (!owns) cx = cy = 0.f;
     }
-    warp_sum4(sxx, syy, cx, cy, lane);
-    sxy = warp_sum(sxy);
+    group_sum4<G>(sxx, syy, cx, cy, lane);
+    sxy = group_sum<G>(sxy);
     const float det = det2(sxx, syy, sxy);
     const float dd = sxx - syy;
     const float lmax = 0.5f * ((sxx + syy) + sqrtf(fmaf(dd, dd, 4.0f * sxy * sxy)));
@@ -703,16 +742,16 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
     // Prefetch the next template (next level, or the next point's top level)
     // into the other buffer while this level iterates.
     if (nx.has) {
-        __syncwarp();
+        __syncwarp(gm);
         issue_template<ST, WIN>(nx.P, nx.w, nx.h, nx.tm, nx.u8, nx.ipx, nx.ipy, 1 - buf, lane, W,
                                 f, pf.tcol_i, pf.tcol_g);
         pf.valid = true;
         pf.buf = 1 - buf;
     }
     // the search region has landed; the prefetch may still run
-    if (!fill_wait(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
+    if (!fill_wait<G>(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
     if (c0_ok) search_edges<ST, WIN>(h, tms, W, lc, lane);
-    __syncwarp();
+    __syncwarp(gm);
     // The window stays inside the tracking bounds while its integer centre
     // j = ip + floor(a + g + nu) satisfies -R <= j <= w - 1 + R (at the
     // upper bound only with a zero fraction): in terms of a + g + nu, the
@@ -731,11 +770,11 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
         if (!cached || fcx != cfx || fcy != cfy) {
             const int jx = ipx + (int)fcx, jy = ipy + (int)fcy;
             if (!staged || abs(jx - sjx) > MARGIN || abs(jy - sjy) > MARGIN) {
-                __syncwarp();
+                __syncwarp(gm);
                 copy_search<ST, WIN>(J, w, h, tms, u8, jx, jy, lane, W, f, lc);
-                if (!fill_wait(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
+                if (!fill_wait<G>(f, BUF_SEARCH)) return OMT_PT_LOST_TIMEOUT;
                 search_edges<ST, WIN>(h, tms, W, lc, lane);
-                __syncwarp();
+                __syncwarp(gm);
                 sjx = jx;
                 sjy = jy;
                 staged = true;
@@ -752,7 +791,7 @@ __device__ __forceinline__ int track_level(const LevelView *P, const LevelView *
         float sx, sy;
         combine4(S, bx, by, sx, sy);
         if (!owns) sx = sy = 0.f;
-        warp_sum2(sx, sy, lane);
+        group_sum2<G>(sx, sy, lane);
         const float bbx = cx - sx, bby = cy - sy;  // b = sum (I - J) grad I
         const float ex = (syy * bbx - sxy * bby) * inv_det;
         const float ey = (sxx * bby - sxy * bbx) * inv_det;
@@ -819,12 +858,13 @@ __device__ __forceinline__ PointResult lk_point(const LevelView *P, const LevelV
                                                 int max_iter, float eps2, float tau_n, float2 u,
                                                 const CUtensorMap *tm, unsigned *W, Fills &f,
                                                 Prefetch &pf, NextFn next, bool force_fail) {
-    const int lane = threadIdx.x & 31;
+    constexpr int G = lk_group<WIN>();
+    const int lane = group_lane<G>();
     PointResult r;
     r.v = u;
     r.itp = 0ull;
     if (!(fabsf(u.x) <= 16777216.f) || !(fabsf(u.y) <= 16777216.f)) {
-        fill_drain(f);
+        fill_drain<G>(f);
         pf.valid = false;
         r.st = OMT_PT_LOST_OOB;
         return r;
@@ -881,7 +921,7 @@ __device__ __forceinline__ PointResult lk_point(const LevelView *P, const LevelV
         // a lost point leaves its prefetch (for a level it will not reach)
         // unused, and maybe its search region in flight: land them and
         // forget them
-        fill_drain(f);
+        fill_drain<G>(f);
         pf.valid = false;
     } else {
         const float ox = u.x + dx, oy = u.y + dy;
@@ -934,18 +974,19 @@ __global__ void fb_check_kernel(const float2 *pts, const float2 *pts_back,
     }
 }
 
-// This warp's staging words in the block's dynamic shared memory, from its
-// first 128-byte boundary (tensor copies land on 128-byte boundaries).
+// This group's staging words in the block's dynamic shared memory, from its
+// first 128-byte boundary (tensor copies land on 128-byte boundaries; every
+// group's share is a multiple of 128 bytes).
 template <int ST, int WIN>
 __device__ __forceinline__ unsigned *warp_words() {
     extern __shared__ __align__(128) unsigned lk_smem[];
     const unsigned lead = (128u - (smem_u32(lk_smem) & 127u)) & 127u;
-    return lk_smem + lead / 4 + (size_t)(threadIdx.x >> 5) * Dims<ST, WIN>::WORDS;
+    return lk_smem + lead / 4 + (size_t)(threadIdx.x / lk_group<WIN>()) * Dims<ST, WIN>::WORDS;
 }
 
 template <int ST, int WIN>
 constexpr size_t stage_bytes(int warps = LK_WARPS) {
-    return (size_t)warps * Dims<ST, WIN>::WORDS * 4 + 128;
+    return (size_t)warps * (32 / lk_group<WIN>()) * Dims<ST, WIN>::WORDS * 4 + 128;
 }
 
 template <int ST, int WIN>
@@ -956,18 +997,20 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
         const int m = *a.n_dev;
         n = m < n ? m : n;
     }
-    const int nwarps = gridDim.x * LK_WARPS;
+    constexpr int G = lk_group<WIN>();
+    const int glane = group_lane<G>();
+    const int ngroups = gridDim.x * (LK_NT / G);
     Fills f;
-    fills_init(f, W + Dims<ST, WIN>::BAR, threadIdx.x & 31);
+    fills_init<G>(f, W + Dims<ST, WIN>::BAR, glane);
     const CUtensorMap *tm = all_maps(a.tm_ok, a.levels) ? a.tm : nullptr;
     Prefetch pf;
     pf.valid = false;
-    for (int i = blockIdx.x * LK_WARPS + (threadIdx.x >> 5); i < n; i += nwarps) {
-        if (f.pend & FILL_FAILED) {   // a wait ran out: the warp's later points are given up
-            lost_timeout(a.pts[i], i, a.out, a.status, a.iters, a.levels, lane_of());
+    for (int i = blockIdx.x * (LK_NT / G) + (int)(threadIdx.x / G); i < n; i += ngroups) {
+        if (f.pend & FILL_FAILED) {   // a wait ran out: the group's later points are given up
+            lost_timeout(a.pts[i], i, a.out, a.status, a.iters, a.levels, glane);
             continue;
         }
-        const int nxt = i + nwarps;
+        const int nxt = i + ngroups;
         auto next = [&]() {
             const bool has = nxt < n;
             return next_top<WIN>(has, has ? a.pts[nxt] : make_float2(0.f, 0.f), a.P, tm, a.levels);
@@ -975,9 +1018,9 @@ __global__ void __launch_bounds__(LK_MAX_NT) lk_kernel(const __grid_constant__ L
         const PointResult r = lk_point<ST, WIN>(a.P, a.J, a.levels, a.max_iter, a.eps2, a.tau_n,
                                                 a.pts[i], tm, W, f, pf, next,
                                                 (long long)i == lk_fail_point);
-        put_point(r, i, a.out, a.status, a.iters, a.levels, lane_of());
+        put_point(r, i, a.out, a.status, a.iters, a.levels, glane);
     }
-    fill_drain(f);
+    fill_drain<G>(f);
 }
 
 // Queue positions [lo, hi) of a batch that a failed warp holds: reported
@@ -1044,14 +1087,16 @@ __global__ void __launch_bounds__(LK_MAX_NT) __maxnreg__(lk_batch_regs<WIN>())
     }
     __syncthreads();
     const int total = pre[ns];
+    constexpr int G = lk_group<WIN>();
+    const int glane = group_lane<G>();
     auto take = [&]() -> int {
         unsigned b = 0;
-        if (lane == 0) b = atomicAdd(queue, (unsigned)chunk);
-        b = __shfl_sync(FULL_MASK, b, 0);
+        if (glane == 0) b = atomicAdd(queue, (unsigned)chunk);
+        b = __shfl_sync(group_mask<G>(), b, 0, G);
         return b < (unsigned)total ? (int)b : total;
     };
     Fills f;
-    fills_init(f, W + Dims<ST, WIN>::BAR, lane);
+    fills_init<G>(f, W + Dims<ST, WIN>::BAR, glane);
     Prefetch pf;
     pf.valid = false;
     int g = take(), end = g + chunk;
@@ -1086,36 +1131,45 @@ __global__ void __launch_bounds__(LK_MAX_NT) __maxnreg__(lk_batch_regs<WIN>())
         {
             const StreamEntry &e = t.stream(s);
             if constexpr (backward) {
-                put_point(r, i, e.pts_back, e.status_back, nullptr, h.levels, lane);
-                if (lane == 0)
+                put_point(r, i, e.pts_back, e.status_back, nullptr, h.levels, glane);
+                if (glane == 0)
                     fb_apply(e.pts[i], e.pts_back[i], e.status_back[i], h.fb_max, e.status[i]);
             } else {
-                put_point(r, i, e.pts_out, e.status, e.iters, h.levels, lane);
+                put_point(r, i, e.pts_out, e.status, e.iters, h.levels, glane);
             }
         }
         if (f.pend & FILL_FAILED) {
-            // a wait ran out: the points this warp holds (the rest of its
+            // a wait ran out: the points this group holds (the rest of its
             // chunk, or the chunk it took next) are given up, and it takes
             // no more work
-            give_up_batch<backward>(table, pre, gn, end < total ? end : total, lane);
+            give_up_batch<backward>(table, pre, gn, end < total ? end : total, glane);
             break;
         }
         g = gn;
         s = sn;
     }
-    fill_drain(f);
+    fill_drain<G>(f);
+}
+
+// A CTA of LK_NT threads tracks LK_NT / G points at a time; the grid
+// covers the points once, at most 32 CTAs per SM.
+template <int ST, int W>
+cudaError_t launch_plain(const LKArgs &a, int sms, cudaStream_t s) {
+    if (cudaFuncSetAttribute(lk_kernel<ST, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)stage_bytes<ST, W>()) != cudaSuccess)
+        return cudaGetLastError();
+    const int per = LK_NT / lk_group<W>();
+    const int need = (a.n_max + per - 1) / per, cap = sms * 32;
+    lk_kernel<ST, W><<<need < cap ? need : cap, LK_NT, stage_bytes<ST, W>(), s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int ST>
-cudaError_t launch_st(const LKArgs &a, int win, int grid, cudaStream_t s) {
+cudaError_t launch_st(const LKArgs &a, int win, int sms, cudaStream_t s) {
     switch (win) {
 #define OMT_LK_CASE(W)                                                                    \
     case W:                                                                               \
-        if (cudaFuncSetAttribute(lk_kernel<ST, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)stage_bytes<ST, W>()) != cudaSuccess)                  \
-            return cudaGetLastError();                                                    \
-        lk_kernel<ST, W><<<grid, LK_NT, stage_bytes<ST, W>(), s>>>(a);                        \
-        break;
+        return launch_plain<ST, W>(a, sms, s);
         OMT_LK_CASE(3) OMT_LK_CASE(5) OMT_LK_CASE(7) OMT_LK_CASE(9) OMT_LK_CASE(11)
         OMT_LK_CASE(13) OMT_LK_CASE(15) OMT_LK_CASE(17) OMT_LK_CASE(19) OMT_LK_CASE(21)
         OMT_LK_CASE(23) OMT_LK_CASE(25) OMT_LK_CASE(27) OMT_LK_CASE(29) OMT_LK_CASE(31)
@@ -1359,11 +1413,8 @@ cudaError_t launch_lk(const omt_pyramid &prev, const omt_pyramid &next, const fl
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int need = (n_max + LK_WARPS - 1) / LK_WARPS;
-    const int cap = sms * 32;
-    const int grid = need < cap ? need : cap;
-    if (prev.storage == OMT_F32) return launch_st<OMT_F32>(a, prm.win, grid, s);
-    return launch_st<OMT_F16>(a, prm.win, grid, s);
+    if (prev.storage == OMT_F32) return launch_st<OMT_F32>(a, prm.win, sms, s);
+    return launch_st<OMT_F16>(a, prm.win, sms, s);
 }
 
 }  // namespace omt
