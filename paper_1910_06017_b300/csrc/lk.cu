@@ -41,12 +41,19 @@ constexpr int LK_MAX_NT = 256;           // largest CTA a launch may use
 // from 5.44 to 4.50 ms (F32); at 21x21 the time is the same at 128, 168 or
 // 255.
 template <int WIN>
-constexpr int lk_batch_regs() { return WIN >= 25 ? 168 : 128; }
+constexpr int lk_group();
+
+template <int WIN>
+constexpr int lk_batch_regs() { return WIN >= 25 || lk_group<WIN>() == 16 ? 168 : 128; }
 
 // Lanes that track one point together: G = 32 (the whole warp) or 16 (each
-// half-warp its own point, the two halves in step).  Collectives run on the
-// group's mask, copies are issued by the group's lane 0, and every group
-// has its own staging buffers and mbarriers.
+// half-warp its own point).  Collectives run on the group's mask, copies
+// are issued by the group's lane 0, and every group has its own staging
+// buffers and mbarriers.  Every window uses the warp: half-warps measured
+// slower at 21x21 (8 streams: 4,952 warp instructions per point instead of
+// 5,838, but the two halves' iterations diverge, leaving 24 of 32 lanes
+// active per instruction, and at twice the staging per warp only 8 to 10
+// warps fit on an SM, which halved the issue rate: 0.717 ms against 0.423).
 template <int WIN>
 constexpr int lk_group() { return 32; }
 
