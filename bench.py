@@ -768,6 +768,117 @@ def run_overlap(args):
                       **res}))
 
 
+def _median_ms(fn, steps, stream):
+    """Median CUDA-event time (ms) of fn() on `stream` over `steps` runs,
+    after three untimed runs."""
+    import torch
+    for _ in range(3):
+        fn()
+    ms = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms))
+
+
+def run_phases(args):
+    """Where the batched step's time goes, on the bench workload: each phase
+    of the step alone (pyramid, corners, LK, boxes), the pyramid and corner
+    phases on their two streams as the step runs them, the eager step and
+    the graph step.  Median CUDA-event times over the steps, launch shapes
+    from the tuner.  One JSON line."""
+    import torch
+    from paper_1910_06017_b300 import omt
+    dev = torch.device("cuda", 0)
+    storage = omt.F16 if args.storage == "f16" else omt.F32
+    streams = make_streams(args.streams, 0)
+    caps = [cap_of(sp) for sp in streams]
+    B = omt.BatchTracker([sp.size for sp in streams], params_for(omt, storage, max(caps)),
+                         max_boxes=[len(sp.boxes) for sp in streams], max_corners=caps, device=dev)
+    for s, sp in enumerate(streams):
+        B.prime(s, torch.from_numpy(sp.frame0).to(dev))
+        B.frame[s][0].copy_(torch.from_numpy(sp.frame1))
+        B.frame[s][1].copy_(torch.from_numpy(sp.frame0))
+        B.set_boxes(s, torch.from_numpy(sp.boxes))
+    B.pack()
+    for _ in range(args.warmup):
+        B.step()
+    if args.tune:
+        B.autotune()
+    torch.cuda.synchronize()
+    main = torch.cuda.current_stream(dev)
+    # the phases of the step that was just run (its table, frames and corners)
+    dt = B.dev_tables[1 - B.cur]
+
+    def phase(p):
+        return lambda: omt.batch_phase(dt, B.caps, B.params, p, main)
+
+    def side_by_side():
+        B.side.wait_stream(main)
+        omt.batch_phase(dt, B.caps, B.params, omt.PHASE_PYRAMID, main)
+        omt.batch_phase(dt, B.caps, B.params, omt.PHASE_CORNERS, B.side)
+        main.wait_stream(B.side)
+
+    res = {name: _median_ms(fn, args.steps, main) for name, fn in (
+        ("pyramid_ms", phase(omt.PHASE_PYRAMID)), ("corners_ms", phase(omt.PHASE_CORNERS)),
+        ("pyramid_beside_corners_ms", side_by_side), ("lk_ms", phase(omt.PHASE_LK)),
+        ("boxes_ms", phase(omt.PHASE_BOXES)))}
+    res["eager_step_ms"] = _median_ms(B.step, args.steps, main)
+    B.capture()
+    res["graph_step_ms"] = _median_ms(B.step, args.steps, main)
+    print(json.dumps({"workload": f"{args.streams} streams (bench workload), {args.storage} storage",
+                      "caps": {"pyramid_ctas_per_sm": B.caps.pyr_ctas_per_sm,
+                               "list_ctas_per_sm": B.caps.corner_ctas_per_sm,
+                               "select_ctas_per_sm": B.caps.select_ctas_per_sm,
+                               "lk_warps": B.caps.lk_warps, "lk_chunk": B.caps.lk_chunk},
+                      **res}))
+
+
+def run_lk_4k(args):
+    """The batched LK phase at 31x31 and 5 levels on four streams of the
+    3840x2160 large-motion pair (workload 4's frames, boxes and corner
+    cap), F16 and F32 storage, for each of the tuner's LK launch shapes:
+    median CUDA-event time over the steps.  One JSON line."""
+    import torch
+    from paper_1910_06017_b300 import omt, synth
+    dev = torch.device("cuda", 0)
+    pr = synth.rigid_pair()
+    H, W = pr.frame0.shape
+    ns = 4
+    boxes = torch.from_numpy(np.ascontiguousarray(pr.boxes, np.float32))
+    out = {"workload": f"{ns} streams of the 3840x2160 pair, {len(pr.boxes)} boxes, <= 250 corners "
+                       "per box, 5 levels, 31x31"}
+    for storage, name in ((omt.F16, "f16"), (omt.F32, "f32")):
+        prm = omt.default_params(levels=5, win=31, max_corners=250, storage=storage)
+        B = omt.BatchTracker([(W, H)] * ns, prm, max_boxes=len(pr.boxes), max_corners=[250] * ns,
+                             device=dev)
+        for s in range(ns):
+            B.prime(s, torch.from_numpy(pr.frame0).to(dev))
+            B.frame[s][0].copy_(torch.from_numpy(pr.frame1))
+            B.frame[s][1].copy_(torch.from_numpy(pr.frame0))
+            B.set_boxes(s, boxes)
+        B.pack()
+        B.step()
+        torch.cuda.synchronize()
+        main = torch.cuda.current_stream(dev)
+        dt = B.dev_tables[1 - B.cur]
+        ms = {}
+        for w, c in B.TUNE_CANDIDATES:
+            B.caps.lk_warps, B.caps.lk_chunk = w, c
+            ms[f"{w}x{c}"] = _median_ms(
+                lambda: omt.batch_phase(dt, B.caps, B.params, omt.PHASE_LK, main), args.steps, main)
+        out[name] = {"points": sum(B.count(s) for s in range(ns)), "lk_ms_by_shape": ms,
+                     "lk_ms": min(ms.values())}
+        del B
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
+
+
 def run_working_level(args):
     """Tracking on the working level (Section V-A preprocessing: a pyramid
     level chosen by resolution is processed).  For the 3840x2160 pair with
@@ -902,12 +1013,17 @@ def main():
                     help="the dense flow engine (TV-L1) on 1920x1080 frames instead of the tracker")
     ap.add_argument("--fb", type=float, default=None, metavar="MAX",
                     help="forward-backward check in every step, threshold MAX px (default off)")
+    ap.add_argument("--phases", action="store_true",
+                    help="each phase of the batched step alone and side by side")
+    ap.add_argument("--lk-4k", action="store_true",
+                    help="the batched LK at 31x31 on four streams of the 4K pair")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "omt":
         args.warmup = max(args.warmup, 3)
     for flag, fn in (("match", run_match), ("overlap", run_overlap),
-                     ("working_level", run_working_level)):
+                     ("working_level", run_working_level), ("phases", run_phases),
+                     ("lk_4k", run_lk_4k)):
         if getattr(args, flag):
             if rank == 0:
                 fn(args)
